@@ -1,0 +1,47 @@
+"""Write the compact self-avoiding random-walk starts of the long-chain workloads.
+
+Run from the repository root:  python tests/golden/make_starts.py
+Each start is the oracle's residue-by-residue growth (phi, psi uniform, redrawn until no heavy-atom
+pair more than three bonds apart is closer than 2.5 A, backing up five residues after 100 failed
+draws), stored as 16-bit angle codes (theta = code * 2 pi / 65536, exact in float64). Only the
+oracle and the input generator are called.
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from oracle import oracle as O  # noqa: E402
+from paper_1712_05012_b300 import synth  # noqa: E402
+
+STARTS = [
+    # name, workload index, residues
+    ("chain1000", 2, 1000),
+    ("chain8000", 3, 8000),
+]
+
+
+def main():
+    table = synth.type_table()
+    manifest = {}
+    for name, k, m in STARTS:
+        wl = synth.workload(k)
+        seed = synth.chain_seed(wl.seed, 0)
+        seq = synth.sequence(m, seed)
+        ch = O.OracleChain(seq, table, synth.GEOMETRY)
+        codes = ch.grow_start(seed, min_dist=2.5, max_retries=100, backtrack=5)
+        np.save(os.path.join(HERE, f"start_{name}.npy"), codes)
+        manifest[name] = {"workload": k, "residues": m, "sequence_seed": seed, "grow_seed": seed,
+                          "min_dist": 2.5, "max_retries": 100, "backtrack": 5, "atoms": ch.n}
+        print(name, ch.n, "atoms")
+    with open(os.path.join(HERE, "starts.json"), "w") as f:
+        json.dump(manifest, f, indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main()
