@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the KCM step on B300: one line of JSON on rank 0.
+
+Workload (default): the 1,000-residue synthetic chain (10,506 atoms) from its stored compact
+random-walk start, 10 A cutoff, N = 256 solvation samples, mixed precision (FP32 pair and
+solvation arithmetic, FP64 kinematics and torque scans). A step is one KCM iteration (forward
+kinematics, binning, pair forces, Algorithm 1, wrenches and torque suffix sums, energies, step),
+launched as a CUDA graph. Metric: atom-iterations per second, whole job (all ranks).
+
+Timing: W warm-up steps, then K steps timed on the device with CUDA events on the library's
+stream (each step is bracketed by events recorded by the library; a 256 MiB buffer is written
+between steps to flush L2), max over ranks. With torchrun (N > 1) every rank runs an independent
+replica of the workload on its own GPU (chains are independent; there is no data-path exchange).
+
+--impl reference times the FP64 CPU oracle on the same workload (rank 0 only), one oracle
+iteration per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
+UNIT = "atom-iterations/s"
+# FP32 lanes per SM on B300 (4 SM sub-partitions x 32 FP32 lanes); FMA = 2 flops
+FP32_LANES_PER_SM = 128
+FLOPS_PER_SASA_TEST = 9  # w = v - o (3), |w|^2 (1 mul + 2 FMA = 5), compare with Roff^2 (1)
+FLOPS_PER_PAIR = 31      # per unordered pair within the cutoff (distance, 1/d^2, Coulomb, LJ, weights, accumulate)
+BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques": 60}  # algorithmic HBM bytes per atom
+KERNELS_PER_ITERATION = {1: 19, 0: 18}  # reset + kinematics 4 + binning 7 + pairs 1 + solvation 1 + torques 3 + energy 1 + step 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1712_05012_b300 import synth
+
+    man = json.load(open(os.path.join(GOLDEN, "starts.json")))["chain1000"]
+    seq = synth.sequence(man["residues"], man["sequence_seed"])
+    theta = synth.theta_from_codes(np.load(os.path.join(GOLDEN, "start_chain1000.npy")))
+    return seq, theta, man
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(self.index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_baseline(seq, theta, params, budget_s=12.0):
+    """The oracle (FP64, all-pairs, OpenMP over atoms) on the machine's host cores: KCM iterations of
+    the same workload for about `budget_s` seconds."""
+    from oracle import oracle as O
+    from paper_1712_05012_b300 import synth
+
+    table = synth.type_table()
+    ch = O.OracleChain(seq, table, synth.GEOMETRY)
+    th = np.array(theta)
+    t0 = time.perf_counter()
+    ch.run(params, th, 1)
+    t1 = time.perf_counter() - t0
+    iters = max(1, min(200, int(budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    _, it, _, _ = ch.run(params, th, iters)
+    wall = time.perf_counter() - t0
+    return {"value": ch.n * it / wall, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{it} FP64 oracle iterations of the 1,000-residue chain ({ch.n} atoms) from its compact start, "
+                      f"{wall:.1f} s wall"}, ch
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_1712_05012_b300 import synth
+
+    seq, theta, man = workload()
+    table = synth.type_table()
+    ch = O.OracleChain(seq, table, synth.GEOMETRY)
+    p = synth.RunParams(precision=synth.PRECISION_FP64)
+    th = np.array(theta)
+    for _ in range(args.warmup):
+        ch.run(p, th, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ch.run(p, th, 1)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = ch.n * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "chain1000_compact_cut10", "residues": 1000, "atoms": ch.n, "cutoff": 10.0,
+                       "n_sample": 256, "solvation": 1, "precision": "fp64 (oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"one full FP64 oracle iteration per step ({ch.n} atoms)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1712_05012_b300 import kcm, synth
+
+    table = synth.type_table()
+    seq, theta, man = workload()
+    prec = synth.PRECISION_MIXED if args.precision == "mixed" else synth.PRECISION_FP64
+    params = synth.RunParams(precision=prec)
+    ch = kcm.Chain(seq, table, params)
+    ch.set_theta(theta)
+    n = ch.n
+    lib_stream = torch.cuda.ExternalStream(ch.stream())
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 256 MiB > 126 MB L2
+
+    clocks = Clocks(local)
+    for _ in range(args.warmup):
+        with torch.cuda.stream(lib_stream):
+            flush.add_(1)
+        ch.step_timed()
+    stats0 = ch.stats()
+    totals, stages = [], {k: 0.0 for k in kcm.STAGES}
+    for _ in range(args.steps):
+        with torch.cuda.stream(lib_stream):
+            flush.add_(1)
+        tot, st = ch.step_timed()
+        totals.append(tot)
+        for k, v in st.items():
+            stages[k] += v
+    clk = clocks.stop()
+    stats = ch.stats()
+    t_sum = sum(totals) / 1e3
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_sum], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_sum = float(t.item())
+    value = ws * n * args.steps / t_sum
+    ms_stage = {k: v / args.steps for k, v in stages.items()}
+
+    # roofline of the dominant stage (work counted at the last timed iteration)
+    dom = max(ms_stage, key=ms_stage.get)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_max = (clk or {}).get("sm_max_mhz") or 2032.0
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6400.0}
+    sec = ms_stage[dom] / 1e3
+    if dom == "solvation":
+        work = stats["sasa_tests"] * FLOPS_PER_SASA_TEST
+        roof = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
+    elif dom == "pairs":
+        work = stats["pairs"] * FLOPS_PER_PAIR
+        roof = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
+    else:
+        work = BYTES_PER_ATOM.get(dom, 24) * n
+        roof = {"bound": "hbm", "achieved": work / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = dom
+    roof["ms_per_launch"] = ms_stage[dom]
+    roof["work_per_launch"] = work
+
+    # the plain FP64 single-chain GPU path, measured the same way
+    fp64_value = None
+    if args.fp64_steps > 0 and prec == synth.PRECISION_MIXED:
+        with kcm.Chain(seq, table, synth.RunParams(precision=synth.PRECISION_FP64)) as c64:
+            c64.set_theta(theta)
+            for _ in range(2):
+                c64.step_timed()
+            tt = []
+            for _ in range(args.fp64_steps):
+                with torch.cuda.stream(torch.cuda.ExternalStream(c64.stream())):
+                    flush.add_(1)
+                tt.append(c64.step_timed()[0])
+            fp64_value = n * args.fp64_steps / (sum(tt) / 1e3)
+
+    # end to end through the C ABI with pinned host buffers: theta in, one step, theta out
+    pinned = torch.empty(ch.l, dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.from_numpy(theta))
+    hp = pinned.data_ptr()
+    L = kcm.load()
+    import ctypes
+    dptr = ctypes.cast(hp, ctypes.POINTER(ctypes.c_double))
+    ch.set_theta(theta)
+    e2e_steps = max(args.steps, 20)
+    it_out = (ctypes.c_int32 * 1)()
+    dm_out = (ctypes.c_double * 1)()
+    for _ in range(3):
+        L.kcm_set_theta(ch.handle, dptr, ch.l)
+        L.kcm_step(ch.handle, 1, it_out, dm_out)
+        L.kcm_get_theta(ch.handle, dptr, ch.l)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = L.kcm_set_theta(ch.handle, dptr, ch.l)
+        rc |= L.kcm_step(ch.handle, 1, it_out, dm_out)
+        rc |= L.kcm_get_theta(ch.handle, dptr, ch.l)
+        if rc:
+            raise RuntimeError("kcm call failed during the end-to-end run")
+    e2e_wall = time.perf_counter() - t0
+    e2e = {"value": ws * n * e2e_steps / e2e_wall, "unit": UNIT, "h2d_bytes_per_step": 8 * ch.l,
+           "d2h_bytes_per_step": 8 * ch.l + 120, "steps": e2e_steps,
+           "note": "per step: kcm_set_theta from pinned host memory, kcm_step(1) with its status read, "
+                   "kcm_get_theta into pinned host memory; host wall clock"}
+    ch.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu, _ = oracle_baseline(seq, theta, synth.RunParams(precision=synth.PRECISION_FP64))
+
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 pair/solvation, f64 kinematics/scans" if prec == synth.PRECISION_MIXED else "f64",
+                "data": "synthetic",
+                "config": {"workload": "chain1000_compact_cut10", "residues": 1000, "atoms": n, "cutoff": 10.0,
+                           "n_sample": 256, "solvation": 1, "precision": args.precision,
+                           "replicas": ws, "l2": "flushed between timed steps (256 MiB write)"},
+                "roofline": roof, "stage_ms": ms_stage, "fp64_value": fp64_value,
+                "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,
+                "clocks": clk, "stats": {k: stats[k] for k in ("pairs", "sasa_tests", "sasa_neighbors",
+                                                                 "max_neighbors", "guard_rechecks", "cells")},
+                "cell_size": stats["cell_size"]}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,257 @@
+/*
+ * kcm.h — C ABI of the B300-native kinetostatic compliance method (KCM) step.
+ *
+ * One KCM iteration (Behandish & Ilies, "Protofold II", arXiv 1712.05012, Sec. 4.1 steps 4-8)
+ * maps the chain's joint angles theta to atom centres by forward kinematics over rigid links
+ * (Sec. 2.1, eq. kin_02..kin_05, r1, r2), bins the atoms into a uniform cell grid (Sec. 3.2),
+ * evaluates cutoff Coulomb with the distance-dependent dielectric eps = 4 d, Lennard-Jones 6-12
+ * (Sec. 2.2, eq. 02_2, 03_2, 03_8, 03_9) and the surface-enumeration solvation forces
+ * (Sec. 3.4, Algorithm 1), reduces forces to link wrenches and joint torques with a suffix sum
+ * (eq. KCM_01, KCM_02, KCM_06, Sec. 3.5) and steps theta <- theta + dtheta (eq. KCM_07).
+ *
+ * Conventions
+ *   Units: Angstrom, elementary charge, kcal/mol, radian.
+ *   Atom order (inputs and outputs): per residue N, H, CA, side atoms 1..k, C, O. With this order
+ *     the atoms of every rigid link are contiguous: base link {N_1, H_1}; CA link i = {CA_i, side_i};
+ *     peptide link i = {C_i, O_i, N_{i+1}, H_{i+1}} (the last one is {C_m, O_m}).
+ *   Joint order: theta[2i] = phi joint of residue i (about N_i -> CA_i), theta[2i+1] = psi joint
+ *     (about CA_i -> C_i), i = 0..m-1, so l = 2m joints. theta = 0 is the zero position (ZP,
+ *     phi = psi = 180 deg, eq. theta_1/theta_2); phi_i = theta[2i] - pi, psi_i = theta[2i+1] - pi.
+ *     A joint rotates everything distal to it by the right-hand rule about its axis; N_1 stays at
+ *     the origin. ZP frame: N_1 at the origin, CA_1 on +x, C_1 in the xy-plane at y > 0.
+ *   Every call returns an int status: KCM_OK (0) or a negative KCM_E_* code; kcm_strerror names it
+ *     and kcm_last_error(h) gives the last message for a handle.
+ *   Host buffers passed to the library are caller-owned; the library copies what it keeps. The
+ *     handle owns all device memory it allocates; nothing is freed before kcm_destroy.
+ *   A handle is not thread-safe; distinct handles are independent. All device work of a handle is
+ *     ordered on the CUDA stream given at kcm_create (an internal stream when NULL). Calls taking
+ *     host buffers synchronise that stream before returning; *_dev calls take device pointers and
+ *     are ordered on the stream without synchronising.
+ */
+#ifndef KCM_H
+#define KCM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define KCM_OK 0
+#define KCM_E_INVAL (-1)     /* invalid argument or size mismatch */
+#define KCM_E_NOMEM (-2)     /* device or host allocation failed */
+#define KCM_E_CUDA (-3)      /* a CUDA runtime call failed */
+#define KCM_E_NONFINITE (-5) /* a torque came out NaN or infinite */
+#define KCM_E_OVERFLOW (-6)  /* an atom had more solvation neighbours than the list holds */
+#define KCM_E_NODEVICE (-8)  /* no CUDA device, or the device is not sm_103 */
+
+/* precision of the pair and solvation arithmetic; kinematics and torque scans are FP64 always */
+#define KCM_FP64 0
+#define KCM_MIXED 1
+
+/* step rule (eq. KCM_07) */
+#define KCM_STEP_CLAMP 0      /* dtheta_k = clamp(kappa tau_k, -dtheta_max, +dtheta_max) */
+#define KCM_STEP_NORMALIZED 1 /* dtheta_k = kappa tau_k / max_j |tau_j| (the paper's form) */
+
+/* solvation classes: the rows of Table 3 (atomic solvation parameters, Sharp et al. adjustment)
+ * plus hydrogen, which Table 3 does not list and which gets gamma = 0 */
+#define KCM_CLS_C 0      /* gamma = +0.012 kcal mol^-1 A^-2 */
+#define KCM_CLS_ON 1     /* -0.116 */
+#define KCM_CLS_S 2      /* -0.018 */
+#define KCM_CLS_OMINUS 3 /* -0.175 */
+#define KCM_CLS_NPLUS 4  /* -0.186 */
+#define KCM_CLS_H 5      /* 0 */
+
+#define KCM_MAX_SIDE 10
+
+/* Atomic constants of one atom (the tuple a_i of Sec. 2.2): charge q (e), LJ well depth eps
+ * (kcal/mol), LJ size sigma (A; the van der Waals radius is R = sigma / 2, so the LJ distance is
+ * D_ij = R_i + R_j) and the solvation class. */
+typedef struct {
+    double q;
+    double eps;
+    double sigma;
+    int32_t solv_class;
+    int32_t reserved;
+} kcm_atom_param;
+
+/* One residue type: its rigid side group size (1..10 atoms, a planar all-trans zig-zag hung on
+ * CA, first atom at the L-chirality CB position) and the constants of its backbone atoms
+ * (N, H, CA, C, O in that order) and side atoms. */
+typedef struct {
+    int32_t n_side;
+    int32_t reserved;
+    kcm_atom_param backbone[5];
+    kcm_atom_param side[KCM_MAX_SIDE];
+} kcm_restype;
+
+/* Fixed bond lengths (A) and bond angles (degrees) of the rigid links (Sec. 2.1, App. A:
+ * bond lengths and angles are constant, omega = 180 deg). H sits on the bisector of the external
+ * C-N-CA angle; side groups use b_side and the angle a_side throughout. */
+typedef struct {
+    double b_n_ca, b_ca_c, b_c_n, b_c_o, b_n_h, b_side;
+    double a_n_ca_c, a_ca_c_n, a_c_n_ca, a_ca_c_o, a_side;
+} kcm_geometry;
+
+/* A chain: n_res residues with types res_type[i] in [0, n_types) drawn from the table `types`.
+ * geometry may be NULL for the library defaults (N-CA 1.458, CA-C 1.525, C-N 1.329, C=O 1.231,
+ * N-H 1.0, side 1.53 A; N-CA-C 111.2, CA-C-N 116.2, C-N-CA 121.7, CA-C-O 120.8, side 109.4712
+ * degrees). All pointers are read during kcm_create only. */
+typedef struct {
+    int32_t n_res;
+    int32_t n_types;
+    const int32_t* res_type;
+    const kcm_restype* types;
+    const kcm_geometry* geometry;
+} kcm_topology;
+
+/* Run parameters. cutoff: Coulomb and LJ cutoff (pairs with d <= cutoff interact, eq. 02_2);
+ * vdw_cutoff: separate LJ cutoff when > 0 (the paper uses 9 A and 5 A); kappa: step gain
+ * (rad per kcal/mol); dtheta_max: clamp (rad); w14_elec, w14_vdw: weights of pairs three bonds
+ * apart (1-2 and 1-3 pairs get 0, all others 1; eq. 03_8/03_9); r_probe: solvent probe radius
+ * (the offset sphere is R + r_probe, Sec. 3.4); delta_r: finite-difference displacement of
+ * eq. finitediff; coulomb_k: 332.0636 kcal A mol^-1 e^-2; conv_tol: the step loop stops once
+ * max_k |dtheta_k| < conv_tol; cell_size: binning cell edge (0 = the smallest legal edge);
+ * n_sample: sample points per offset sphere N; solvation: 0/1; precision: KCM_FP64/KCM_MIXED;
+ * step_mode: KCM_STEP_CLAMP/KCM_STEP_NORMALIZED. */
+typedef struct {
+    double cutoff;
+    double vdw_cutoff;
+    double kappa;
+    double dtheta_max;
+    double w14_elec;
+    double w14_vdw;
+    double r_probe;
+    double delta_r;
+    double coulomb_k;
+    double conv_tol;
+    double cell_size;
+    int32_t n_sample;
+    int32_t solvation;
+    int32_t precision;
+    int32_t step_mode;
+} kcm_params;
+
+/* Counters of the last evaluation (device-side, read back by kcm_get_stats). */
+typedef struct {
+    int64_t pairs;          /* unordered pairs within the cutoff with w != 0 */
+    int64_t sasa_neighbors; /* ordered solvation neighbour entries (sum over atoms of |A'_i|) */
+    int64_t max_neighbors;  /* largest |A'_i| */
+    int64_t guard_rechecks; /* FP32 tests inside the guard band re-decided in FP64 */
+    int64_t cells;          /* cells of the binning grid */
+    double cell_size;       /* edge actually used (A) */
+    int64_t iterations;     /* iterations taken by the last kcm_step */
+    int64_t sasa_tests;     /* overlap tests performed by Algorithm 1 (steps 1 and 2) */
+} kcm_stats;
+
+typedef struct kcm_ctx* kcm_handle;
+
+/* Fill `p` with the defaults: cutoff 10, vdw_cutoff 0, kappa 1e-3, dtheta_max 0.02,
+ * w14 0.5/0.5, r_probe 1.4, delta_r 0.02, coulomb_k 332.0636, conv_tol 1e-4, cell_size 0,
+ * n_sample 256, solvation 1, KCM_FP64, KCM_STEP_CLAMP. */
+int kcm_params_default(kcm_params* p);
+
+/* Build the chain (ZP geometry, bond-class tables, sample set) on the host and upload it to the
+ * current CUDA device. cuda_stream is a cudaStream_t (NULL: the library makes its own stream).
+ * theta starts at 0 (the ZP). Errors: KCM_E_INVAL (bad sizes, types or parameters),
+ * KCM_E_NODEVICE, KCM_E_NOMEM, KCM_E_CUDA. On error *out is NULL. */
+int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream, kcm_handle* out);
+
+/* Free everything the handle owns. NULL is accepted. */
+void kcm_destroy(kcm_handle h);
+
+int64_t kcm_natoms(kcm_handle h);  /* n, or -1 for a NULL handle */
+int64_t kcm_njoints(kcm_handle h); /* l = 2 m, or -1 */
+
+/* Joint angles theta[l] (rad), host copies. l must equal kcm_njoints. */
+int kcm_set_theta(kcm_handle h, const double* theta, int64_t l);
+int kcm_get_theta(kcm_handle h, double* theta, int64_t l);
+/* The same with device pointers (stream-ordered, no synchronisation). */
+int kcm_set_theta_dev(kcm_handle h, const double* theta_dev, int64_t l);
+int kcm_get_theta_dev(kcm_handle h, double* theta_dev, int64_t l);
+
+/* Atom centres xyz[n*3] at the current theta (forward kinematics only: eq. kin_04, r1, r2). */
+int kcm_positions(kcm_handle h, double* xyz, int64_t n);
+
+/* Total force per atom F[n*3] (kcal mol^-1 A^-1) at the current theta: pair forces
+ * (eq. 03_8 + 03_9) plus solvation forces (Algorithm 1) when solvation is on. */
+int kcm_forces(kcm_handle h, double* F, int64_t n);
+
+/* The two terms separately: F_pair[n*3] (Coulomb + LJ) and F_cav[n*3] (solvation). Either
+ * pointer may be NULL. */
+int kcm_force_terms(kcm_handle h, double* F_pair, double* F_cav, int64_t n);
+
+/* Joint torques tau[l] (kcal/mol per rad) at the current theta: tau_k = J_k^T sum_{h>=k} P_h with
+ * J_k = [u_k ; p_k x u_k] and link wrenches P_h taken about the origin (eq. KCM_01..06). */
+int kcm_torques(kcm_handle h, double* tau, int64_t l);
+int kcm_torques_dev(kcm_handle h, double* tau_dev, int64_t l);
+
+/* Energies at the current theta: E[0] Coulomb, E[1] Lennard-Jones (unordered pairs once),
+ * E[2] solvation sum_i 4 pi gamma_i Roff_i^2 f_i (eq. G_cav_patch; 0 when solvation is off). */
+int kcm_energy(kcm_handle h, double E[3]);
+
+/* Covered sample counts per atom (f_i = 1 - covered_i / N, Sec. 3.4), int32[n]. Atoms with
+ * gamma = 0 contribute neither energy nor force and are not enumerated: their count reads 0. */
+int kcm_sasa_counts(kcm_handle h, int32_t* covered, int64_t n);
+
+/* Run up to n_iters KCM iterations from the current theta (evaluate, then theta += dtheta); stop
+ * early once max |dtheta| < conv_tol. The loop runs as a captured CUDA graph with no host round
+ * trip per iteration. iters_done and max_dtheta (of the last iteration taken) may be NULL.
+ * Errors: KCM_E_NONFINITE, KCM_E_OVERFLOW (results of that iteration are not valid), KCM_E_CUDA. */
+int kcm_step(kcm_handle h, int32_t n_iters, int32_t* iters_done, double* max_dtheta);
+
+/* Enqueue n_iters iterations without synchronising (for timing with CUDA events on the stream);
+ * read the outcome later with kcm_step_status. */
+int kcm_step_async(kcm_handle h, int32_t n_iters);
+int kcm_step_status(kcm_handle h, int32_t* iters_done, double* max_dtheta);
+
+int kcm_get_stats(kcm_handle h, kcm_stats* st);
+
+/* Stages of one iteration, in launch order, as timed by kcm_step_timed. */
+#define KCM_STAGE_KINEMATICS 0 /* transform scan and atom centres (eq. kin_04, r1, r2) */
+#define KCM_STAGE_BINNING 1    /* bounding box, grid, counting sort (Sec. 3.2) */
+#define KCM_STAGE_PAIRS 2      /* Coulomb + LJ forces and solvation neighbour lists */
+#define KCM_STAGE_SOLVATION 3  /* Algorithm 1 */
+#define KCM_STAGE_TORQUES 4    /* link wrenches, suffix sums, joint torques (Sec. 3.5) */
+#define KCM_STAGE_ENERGY 5     /* energy reduction (eq. 01) */
+#define KCM_STAGE_STEP 6       /* clamped step (eq. KCM_07) */
+#define KCM_NUM_STAGES 7
+
+/* Run ONE iteration (as kcm_step(h, 1, ...)) through a copy of the iteration graph that records
+ * CUDA events between stages on the handle's stream, synchronise, and return the stage durations
+ * stage_ms[n_stages] (n_stages <= KCM_NUM_STAGES) and the whole iteration's duration total_ms.
+ * Either output may be NULL. Same errors as kcm_step. */
+int kcm_step_timed(kcm_handle h, float* stage_ms, int32_t n_stages, float* total_ms);
+
+/* The cudaStream_t the handle works on. */
+void* kcm_stream(kcm_handle h);
+
+/* Host-only helpers (no device needed). */
+
+/* The unit-sphere sample set Q[N*3] of Sec. 3.4: K = round(sqrt(pi N / 4)) latitude rings at polar
+ * angles pi (r - 1/2) / K, ring r holding a share of N proportional to the sine of its polar
+ * angle (largest-remainder rounding, ties to the lower ring), point t of ring r at longitude
+ * 2 pi (t + (r mod 2)/2) / n_r; listed ring by ring. Returns KCM_OK or KCM_E_INVAL (N < 1). */
+int kcm_sample_points(int32_t N, double* Q);
+
+/* The ZP coordinates xyz0[n*3] and link index link[n] of a topology, as kcm_create builds them
+ * (n must equal the chain's atom count). Either output may be NULL. */
+int kcm_build_zp(const kcm_topology* top, double* xyz0, int32_t* link, int64_t n);
+
+/* Bond class of atom pairs of a topology as the kernels see them: 0 = interacts fully,
+ * 1 = excluded (1-2 or 1-3), 2 = 1-4 (weighted by w14). Writes n_pairs classes for the index
+ * pairs a[k], b[k]. */
+int kcm_pair_class(const kcm_topology* top, const int32_t* a, const int32_t* b, int64_t n_pairs, int32_t* cls);
+
+/* Atom count of a topology (or a negative status). */
+int64_t kcm_topology_natoms(const kcm_topology* top);
+
+const char* kcm_strerror(int code);
+const char* kcm_last_error(kcm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KCM_H */

@@ -1,0 +1,558 @@
+// C ABI of the KCM library (declared in include/kcm.h): handle life cycle, uploads, the captured
+// per-iteration CUDA graph and host/device copies of results.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kcm_device.h"
+
+struct kcm_ctx {
+    kcm::DevChain d;
+    kcm::HostChain hc;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph_timed = nullptr;
+    cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
+    std::vector<void*> allocs;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+constexpr double kPi = 3.14159265358979323846;
+
+int set_err(kcm_ctx* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(kcm_ctx* h, cudaError_t e, const char* what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return set_err(h, KCM_E_CUDA, msg);
+}
+
+template <typename T>
+int dalloc(kcm_ctx* h, T** p, size_t count) {
+    size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_err(h, KCM_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    h->allocs.push_back(*p);
+    return KCM_OK;
+}
+
+template <typename T>
+int upload(kcm_ctx* h, T* dst, const T* src, size_t count) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, h->stream);
+    return e == cudaSuccess ? KCM_OK : cuda_fail(h, e, "upload");
+}
+
+int sync(kcm_ctx* h) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    return KCM_OK;
+}
+
+void enqueue_evaluation(kcm_ctx* h) {
+    kcm::launch_fk(h->d, h->stream);
+    kcm::launch_binning(h->d, h->stream);
+    kcm::launch_forces(h->d, h->stream);
+    kcm::launch_torques(h->d, h->stream);
+    kcm::launch_energy(h->d, h->stream);
+}
+
+int read_status(kcm_ctx* h, kcm::Status* st) {
+    cudaError_t e = cudaMemcpyAsync(st, h->d.status, sizeof(kcm::Status), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status copy");
+    return sync(h);
+}
+
+int status_code(kcm_ctx* h, const kcm::Status& st) {
+    if (st.error & kcm::kErrNonfinite) return set_err(h, KCM_E_NONFINITE, "a torque or coordinate is not finite");
+    if (st.error & kcm::kErrOverflow)
+        return set_err(h, KCM_E_OVERFLOW, "an atom has more than " + std::to_string(kcm::kMaxNbr) + " solvation neighbours");
+    return KCM_OK;
+}
+
+// evaluate at the current theta (no step), synchronise and check the device status
+int evaluate(kcm_ctx* h) {
+    kcm::launch_reset_loop(h->d, h->stream);
+    enqueue_evaluation(h);
+    kcm::Status st;
+    int rc = read_status(h, &st);
+    if (rc != KCM_OK) return rc;
+    return status_code(h, st);
+}
+
+int build_graph(kcm_ctx* h) {
+    if (h->graph) return KCM_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+    enqueue_evaluation(h);
+    kcm::launch_step(h->d, h->stream);
+    e = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(h, e, "graph instantiate");
+    }
+    return KCM_OK;
+}
+
+// the same iteration with an event recorded before each stage and after the last
+int build_timed_graph(kcm_ctx* h) {
+    if (h->graph_timed) return KCM_OK;
+    for (int i = 0; i < KCM_NUM_STAGES + 2; ++i) {
+        if (!h->ev[i]) {
+            cudaError_t e = cudaEventCreate(&h->ev[i]);
+            if (e != cudaSuccess) return cuda_fail(h, e, "event create");
+        }
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+    cudaStream_t s = h->stream;
+    cudaEventRecord(h->ev[1], s);
+    kcm::launch_fk(h->d, s);
+    cudaEventRecord(h->ev[2], s);
+    kcm::launch_binning(h->d, s);
+    cudaEventRecord(h->ev[3], s);
+    kcm::launch_pairs(h->d, s);
+    cudaEventRecord(h->ev[4], s);
+    kcm::launch_sasa(h->d, s);
+    cudaEventRecord(h->ev[5], s);
+    kcm::launch_torques(h->d, s);
+    cudaEventRecord(h->ev[6], s);
+    kcm::launch_energy(h->d, s);
+    cudaEventRecord(h->ev[7], s);
+    kcm::launch_step(h->d, s);
+    cudaEventRecord(h->ev[8], s);
+    e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    e = cudaGraphInstantiate(&h->graph_timed, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph_timed = nullptr;
+        return cuda_fail(h, e, "graph instantiate");
+    }
+    return KCM_OK;
+}
+
+int check_handle(kcm_ctx* h) { return h ? KCM_OK : set_err(nullptr, KCM_E_INVAL, "NULL handle"); }
+
+}  // namespace
+
+extern "C" {
+
+int kcm_params_default(kcm_params* p) {
+    if (!p) return KCM_E_INVAL;
+    p->cutoff = 10.0;
+    p->vdw_cutoff = 0.0;
+    p->kappa = 1e-3;
+    p->dtheta_max = 0.02;
+    p->w14_elec = 0.5;
+    p->w14_vdw = 0.5;
+    p->r_probe = 1.4;
+    p->delta_r = 0.02;
+    p->coulomb_k = 332.0636;
+    p->conv_tol = 1e-4;
+    p->cell_size = 0.0;
+    p->n_sample = 256;
+    p->solvation = 1;
+    p->precision = KCM_FP64;
+    p->step_mode = KCM_STEP_CLAMP;
+    return KCM_OK;
+}
+
+int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream, kcm_handle* out) {
+    if (!out) return set_err(nullptr, KCM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    std::string err;
+    int rc = kcm::validate_params(prm, &err);
+    if (rc != KCM_OK) return set_err(nullptr, rc, err);
+    kcm_ctx* h = new (std::nothrow) kcm_ctx();
+    if (!h) return set_err(nullptr, KCM_E_NOMEM, "host allocation failed");
+    auto bail = [&](int code) {
+        std::string msg = h->err;
+        kcm_destroy(h);
+        g_last_error = msg;
+        return code;
+    };
+    rc = kcm::build_host_chain(top, &h->hc, &err);
+    if (rc != KCM_OK) { set_err(h, rc, err); return bail(rc); }
+
+    int dev = 0, major = 0, minor = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(h, KCM_E_NODEVICE, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+        return bail(KCM_E_NODEVICE);
+    }
+    if (major != 10 || minor != 3) {
+        set_err(h, KCM_E_NODEVICE, "this library is built for sm_103 (B300); device is sm_" + std::to_string(major) +
+                                       std::to_string(minor));
+        return bail(KCM_E_NODEVICE);
+    }
+    if (cuda_stream) {
+        h->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { cuda_fail(h, e, "stream create"); return bail(KCM_E_CUDA); }
+        h->own_stream = true;
+    }
+
+    const kcm::HostChain& hc = h->hc;
+    kcm::DevChain& d = h->d;
+    d.prm = *prm;
+    d.m = hc.m; d.n = hc.n; d.l = hc.l; d.L = hc.L; d.N = prm->n_sample;
+    d.nfk_chunks = (d.l + kcm::kFkChunk - 1) / kcm::kFkChunk;
+    d.nlink_chunks = (d.L + kcm::kLinkChunk - 1) / kcm::kLinkChunk;
+    d.cell_cap = std::max(8 * d.n, 65536);
+    d.pair_blocks = (d.n + kcm::kPairTpb - 1) / kcm::kPairTpb;
+    d.sasa_blocks = (d.n + kcm::kSasaWarps - 1) / kcm::kSasaWarps;
+    d.rcut2 = prm->cutoff * prm->cutoff;
+    double rv = prm->vdw_cutoff > 0.0 ? prm->vdw_cutoff : prm->cutoff;
+    d.rvdw2 = rv * rv;
+    double rmaxR = 0.0;
+    for (double r : hc.R) rmaxR = std::max(rmaxR, r);
+    d.roff_max = rmaxR + prm->r_probe;
+    d.rmax = std::max(prm->cutoff, rv);
+    if (prm->solvation) d.rmax = std::max(d.rmax, 2.0 * d.roff_max + prm->delta_r + 0.02);
+
+    const int n = d.n, l = d.l, L = d.L, N = d.N;
+    const size_t nn = static_cast<size_t>(n);
+    if ((rc = dalloc(h, &d.r0, 3 * nn)) || (rc = dalloc(h, &d.link, nn)) || (rc = dalloc(h, &d.link_start, L + 1)) ||
+        (rc = dalloc(h, &d.u0, 3 * l)) || (rc = dalloc(h, &d.p0, 3 * l)) || (rc = dalloc(h, &d.aprm64, nn)) ||
+        (rc = dalloc(h, &d.aprm32, nn)) || (rc = dalloc(h, &d.G0, nn)) || (rc = dalloc(h, &d.qfx, nn)) ||
+        (rc = dalloc(h, &d.exm, nn)) || (rc = dalloc(h, &d.m14m, nn)) || (rc = dalloc(h, &d.Q64, 3 * N)) ||
+        (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.theta, l)) || (rc = dalloc(h, &d.dtheta, l)) ||
+        (rc = dalloc(h, &d.tau, l)) || (rc = dalloc(h, &d.G, 12 * (size_t)l)) ||
+        (rc = dalloc(h, &d.chunkP, 12 * (size_t)d.nfk_chunks)) || (rc = dalloc(h, &d.chunkE, 12 * (size_t)d.nfk_chunks)) ||
+        (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||
+        (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.cell_count, d.cell_cap)) ||
+        (rc = dalloc(h, &d.cell_start, d.cell_cap + 1)) || (rc = dalloc(h, &d.cell_cursor, d.cell_cap)) ||
+        (rc = dalloc(h, &d.sorted, nn)) || (rc = dalloc(h, &d.slot_cell, nn)) || (rc = dalloc(h, &d.spos64, nn)) ||
+        (rc = dalloc(h, &d.spos32, nn)) || (rc = dalloc(h, &d.sprm32, nn)) || (rc = dalloc(h, &d.sprm64, nn)) ||
+        (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||
+        (rc = dalloc(h, &d.nbr, nn * kcm::kMaxNbr)) || (rc = dalloc(h, &d.nbr_off, nn * kcm::kMaxNbr)) ||
+        (rc = dalloc(h, &d.covered, nn)) || (rc = dalloc(h, &d.P, 6 * (size_t)L)) ||
+        (rc = dalloc(h, &d.chunkS, 6 * (size_t)d.nlink_chunks)) || (rc = dalloc(h, &d.chunkSuf, 6 * (size_t)d.nlink_chunks)) ||
+        (rc = dalloc(h, &d.Epair, 2 * (size_t)d.pair_blocks)) || (rc = dalloc(h, &d.Ecav, d.sasa_blocks)) ||
+        (rc = dalloc(h, &d.E, 3)) || (rc = dalloc(h, &d.Ftot, 3 * nn)) || (rc = dalloc(h, &d.Fcav64, 3 * nn)) ||
+        (rc = dalloc(h, &d.grid, 1)) || (rc = dalloc(h, &d.status, 1)))
+        return bail(rc);
+
+    // per-atom constants
+    std::vector<kcm::dbl4> ap64(n);
+    std::vector<float4> ap32(n);
+    std::vector<double> G0(n);
+    std::vector<long long> qfx(n);
+    for (int a = 0; a < n; ++a) {
+        double roff = hc.R[a] + prm->r_probe;
+        ap64[a] = kcm::make_dbl4(hc.q[a], std::sqrt(hc.eps[a]), hc.R[a], roff);
+        ap32[a] = make_float4((float)hc.q[a], (float)std::sqrt(hc.eps[a]), (float)hc.R[a], (float)roff);
+        G0[a] = 4.0 * kPi * kcm::gamma_of_class(hc.cls[a]) * roff * roff;  // G^cav_{i,0} of Algorithm 1
+        qfx[a] = std::llrint(G0[a] / (static_cast<double>(N) * prm->delta_r) * kcm::kFxScale);
+    }
+    std::vector<double> Q64(3 * (size_t)N);
+    kcm::sample_points(N, Q64.data());
+    std::vector<float> Q32(Q64.begin(), Q64.end());
+    std::vector<double> ident = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
+    if ((rc = upload(h, d.r0, hc.zp.data(), 3 * nn)) || (rc = upload(h, d.link, hc.link.data(), nn)) ||
+        (rc = upload(h, d.link_start, hc.link_start.data(), L + 1)) || (rc = upload(h, d.u0, hc.u0.data(), 3 * l)) ||
+        (rc = upload(h, d.p0, hc.p0.data(), 3 * l)) || (rc = upload(h, d.aprm64, ap64.data(), nn)) ||
+        (rc = upload(h, d.aprm32, ap32.data(), nn)) || (rc = upload(h, d.G0, G0.data(), nn)) ||
+        (rc = upload(h, d.qfx, qfx.data(), nn)) ||
+        (rc = upload(h, d.exm, reinterpret_cast<const unsigned long long*>(hc.ex_mask.data()), nn)) ||
+        (rc = upload(h, d.m14m, reinterpret_cast<const unsigned long long*>(hc.m14_mask.data()), nn)) ||
+        (rc = upload(h, d.Q64, Q64.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q32, Q32.data(), 3 * (size_t)N)) ||
+        (rc = upload(h, d.M, ident.data(), 12)))
+        return bail(rc);
+    e = cudaMemsetAsync(d.theta, 0, sizeof(double) * l, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.cell_count, 0, sizeof(int) * d.cell_cap, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.Fcav, 0, sizeof(long long) * 3 * nn, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.covered, 0, sizeof(int) * nn, h->stream);
+    if (e != cudaSuccess) { cuda_fail(h, e, "memset"); return bail(KCM_E_CUDA); }
+    kcm::launch_init_status(d, h->stream);
+    rc = sync(h);
+    if (rc != KCM_OK) return bail(rc);
+    *out = h;
+    return KCM_OK;
+}
+
+void kcm_destroy(kcm_handle h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph_timed) cudaGraphExecDestroy(h->graph_timed);
+    for (cudaEvent_t ev : h->ev)
+        if (ev) cudaEventDestroy(ev);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    cudaGetLastError();
+    delete h;
+}
+
+int64_t kcm_natoms(kcm_handle h) { return h ? h->d.n : -1; }
+int64_t kcm_njoints(kcm_handle h) { return h ? h->d.l : -1; }
+void* kcm_stream(kcm_handle h) { return h ? static_cast<void*>(h->stream) : nullptr; }
+
+int kcm_set_theta(kcm_handle h, const double* theta, int64_t l) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!theta || l != h->d.l) return set_err(h, KCM_E_INVAL, "theta length must equal the joint count");
+    for (int64_t k = 0; k < l; ++k)
+        if (!std::isfinite(theta[k])) return set_err(h, KCM_E_INVAL, "theta is not finite");
+    int rc = upload(h, h->d.theta, theta, static_cast<size_t>(l));
+    return rc ? rc : sync(h);
+}
+
+int kcm_get_theta(kcm_handle h, double* theta, int64_t l) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!theta || l != h->d.l) return set_err(h, KCM_E_INVAL, "theta length must equal the joint count");
+    cudaError_t e = cudaMemcpyAsync(theta, h->d.theta, sizeof(double) * l, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "theta copy");
+    return sync(h);
+}
+
+int kcm_set_theta_dev(kcm_handle h, const double* theta_dev, int64_t l) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!theta_dev || l != h->d.l) return set_err(h, KCM_E_INVAL, "theta length must equal the joint count");
+    cudaError_t e = cudaMemcpyAsync(h->d.theta, theta_dev, sizeof(double) * l, cudaMemcpyDeviceToDevice, h->stream);
+    return e == cudaSuccess ? KCM_OK : cuda_fail(h, e, "theta copy");
+}
+
+int kcm_get_theta_dev(kcm_handle h, double* theta_dev, int64_t l) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!theta_dev || l != h->d.l) return set_err(h, KCM_E_INVAL, "theta length must equal the joint count");
+    cudaError_t e = cudaMemcpyAsync(theta_dev, h->d.theta, sizeof(double) * l, cudaMemcpyDeviceToDevice, h->stream);
+    return e == cudaSuccess ? KCM_OK : cuda_fail(h, e, "theta copy");
+}
+
+int kcm_positions(kcm_handle h, double* xyz, int64_t n) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!xyz || n != h->d.n) return set_err(h, KCM_E_INVAL, "n must equal the atom count");
+    kcm::launch_reset_loop(h->d, h->stream);
+    kcm::launch_fk(h->d, h->stream);
+    cudaError_t e = cudaMemcpyAsync(xyz, h->d.r, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "positions copy");
+    return sync(h);
+}
+
+int kcm_force_terms(kcm_handle h, double* F_pair, double* F_cav, int64_t n) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (n != h->d.n) return set_err(h, KCM_E_INVAL, "n must equal the atom count");
+    int rc = evaluate(h);
+    if (rc) return rc;
+    kcm::launch_force_out(h->d, h->stream);
+    cudaError_t e = cudaSuccess;
+    if (F_pair) e = cudaMemcpyAsync(F_pair, h->d.Fpair, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && F_cav)
+        e = cudaMemcpyAsync(F_cav, h->d.Fcav64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "force copy");
+    return sync(h);
+}
+
+int kcm_forces(kcm_handle h, double* F, int64_t n) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!F || n != h->d.n) return set_err(h, KCM_E_INVAL, "n must equal the atom count");
+    int rc = evaluate(h);
+    if (rc) return rc;
+    kcm::launch_force_out(h->d, h->stream);
+    cudaError_t e = cudaMemcpyAsync(F, h->d.Ftot, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "force copy");
+    return sync(h);
+}
+
+int kcm_torques(kcm_handle h, double* tau, int64_t l) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!tau || l != h->d.l) return set_err(h, KCM_E_INVAL, "l must equal the joint count");
+    int rc = evaluate(h);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(tau, h->d.tau, sizeof(double) * l, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "torque copy");
+    return sync(h);
+}
+
+int kcm_torques_dev(kcm_handle h, double* tau_dev, int64_t l) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!tau_dev || l != h->d.l) return set_err(h, KCM_E_INVAL, "l must equal the joint count");
+    kcm::launch_reset_loop(h->d, h->stream);
+    enqueue_evaluation(h);
+    cudaError_t e = cudaMemcpyAsync(tau_dev, h->d.tau, sizeof(double) * l, cudaMemcpyDeviceToDevice, h->stream);
+    return e == cudaSuccess ? KCM_OK : cuda_fail(h, e, "torque copy");
+}
+
+int kcm_energy(kcm_handle h, double E[3]) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!E) return set_err(h, KCM_E_INVAL, "E is NULL");
+    int rc = evaluate(h);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(E, h->d.E, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "energy copy");
+    return sync(h);
+}
+
+int kcm_sasa_counts(kcm_handle h, int32_t* covered, int64_t n) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!covered || n != h->d.n) return set_err(h, KCM_E_INVAL, "n must equal the atom count");
+    int rc = evaluate(h);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(covered, h->d.covered, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "count copy");
+    return sync(h);
+}
+
+int kcm_step_async(kcm_handle h, int32_t n_iters) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (n_iters < 0) return set_err(h, KCM_E_INVAL, "n_iters < 0");
+    int rc = build_graph(h);
+    if (rc) return rc;
+    kcm::launch_reset_loop(h->d, h->stream);
+    for (int32_t i = 0; i < n_iters; ++i) {
+        cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    }
+    return KCM_OK;
+}
+
+int kcm_step_status(kcm_handle h, int32_t* iters_done, double* max_dtheta) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    kcm::Status st;
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    if (iters_done) *iters_done = st.iters;
+    if (max_dtheta) *max_dtheta = st.last_max_dtheta;
+    return status_code(h, st);
+}
+
+int kcm_step(kcm_handle h, int32_t n_iters, int32_t* iters_done, double* max_dtheta) {
+    int rc = kcm_step_async(h, n_iters);
+    if (rc) return rc;
+    return kcm_step_status(h, iters_done, max_dtheta);
+}
+
+int kcm_get_stats(kcm_handle h, kcm_stats* out) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!out) return set_err(h, KCM_E_INVAL, "stats is NULL");
+    kcm::Status st;
+    kcm::GridInfo g;
+    cudaError_t e = cudaMemcpyAsync(&g, h->d.grid, sizeof g, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "grid copy");
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    out->pairs = static_cast<int64_t>(st.pairs);
+    out->sasa_neighbors = static_cast<int64_t>(st.nbr_total);
+    out->max_neighbors = st.max_nbr;
+    out->guard_rechecks = static_cast<int64_t>(st.guard);
+    out->cells = g.ncells;
+    out->cell_size = g.s;
+    out->iterations = st.iters;
+    out->sasa_tests = static_cast<int64_t>(st.sasa_tests);
+    return KCM_OK;
+}
+
+int kcm_step_timed(kcm_handle h, float* stage_ms, int32_t n_stages, float* total_ms) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (n_stages < 0 || n_stages > KCM_NUM_STAGES || (n_stages > 0 && !stage_ms))
+        return set_err(h, KCM_E_INVAL, "n_stages must be in [0, KCM_NUM_STAGES]");
+    int rc = build_timed_graph(h);
+    if (rc) return rc;
+    cudaError_t e = cudaEventRecord(h->ev[0], h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "event record");
+    kcm::launch_reset_loop(h->d, h->stream);
+    e = cudaGraphLaunch(h->graph_timed, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    kcm::Status st;
+    rc = read_status(h, &st);
+    if (rc) return rc;
+    for (int i = 0; i < n_stages; ++i) {
+        e = cudaEventElapsedTime(&stage_ms[i], h->ev[1 + i], h->ev[2 + i]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "event elapsed");
+    }
+    if (total_ms) {
+        e = cudaEventElapsedTime(total_ms, h->ev[0], h->ev[8]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "event elapsed");
+    }
+    return status_code(h, st);
+}
+
+int kcm_sample_points(int32_t N, double* Q) {
+    if (!Q || N < 1) return set_err(nullptr, KCM_E_INVAL, "N must be >= 1 and Q non-NULL");
+    return kcm::sample_points(N, Q);
+}
+
+int64_t kcm_topology_natoms(const kcm_topology* top) {
+    kcm::HostChain hc;
+    std::string err;
+    int rc = kcm::build_host_chain(top, &hc, &err);
+    if (rc) { set_err(nullptr, rc, err); return rc; }
+    return hc.n;
+}
+
+int kcm_build_zp(const kcm_topology* top, double* xyz0, int32_t* link, int64_t n) {
+    kcm::HostChain hc;
+    std::string err;
+    int rc = kcm::build_host_chain(top, &hc, &err);
+    if (rc) return set_err(nullptr, rc, err);
+    if (n != hc.n) return set_err(nullptr, KCM_E_INVAL, "n must equal the atom count");
+    if (xyz0) std::memcpy(xyz0, hc.zp.data(), sizeof(double) * 3 * n);
+    if (link)
+        for (int64_t a = 0; a < n; ++a) link[a] = hc.link[a];
+    return KCM_OK;
+}
+
+int kcm_pair_class(const kcm_topology* top, const int32_t* a, const int32_t* b, int64_t n_pairs, int32_t* cls) {
+    kcm::HostChain hc;
+    std::string err;
+    int rc = kcm::build_host_chain(top, &hc, &err);
+    if (rc) return set_err(nullptr, rc, err);
+    if (n_pairs < 0 || (n_pairs > 0 && (!a || !b || !cls))) return set_err(nullptr, KCM_E_INVAL, "bad pair arrays");
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        int x = a[k], y = b[k];
+        if (x < 0 || y < 0 || x >= hc.n || y >= hc.n || x == y) return set_err(nullptr, KCM_E_INVAL, "pair index out of range");
+        int lo = std::min(x, y), off = std::max(x, y) - lo;
+        int c = 0;
+        if (off <= kcm::kMaskWindow) {
+            if ((hc.ex_mask[lo] >> off) & 1ULL) c = 1;
+            else if ((hc.m14_mask[lo] >> off) & 1ULL) c = 2;
+        }
+        cls[k] = c;
+    }
+    return KCM_OK;
+}
+
+const char* kcm_strerror(int code) {
+    switch (code) {
+        case KCM_OK: return "ok";
+        case KCM_E_INVAL: return "invalid argument";
+        case KCM_E_NOMEM: return "out of memory";
+        case KCM_E_CUDA: return "CUDA error";
+        case KCM_E_NONFINITE: return "non-finite torque";
+        case KCM_E_OVERFLOW: return "solvation neighbour list overflow";
+        case KCM_E_NODEVICE: return "no sm_103 CUDA device";
+        default: return "unknown status";
+    }
+}
+
+const char* kcm_last_error(kcm_handle h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Device-side state of one KCM handle and the launchers of its kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kcm_internal.h"
+
+namespace kcm {
+
+// Four doubles on a 32-byte boundary (two 16-byte loads).
+struct alignas(32) dbl4 {
+    double x, y, z, w;
+};
+__host__ __device__ inline dbl4 make_dbl4(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
+
+// Uniform binning grid of Sec. 3.2, rebuilt on the device every iteration.
+struct GridInfo {
+    double ox, oy, oz;  // grid origin (bounding-box minimum)
+    double s;           // cell edge, a multiple of 2^-10 A so that it is exact in float
+    int nx, ny, nz;
+    int ncells;
+};
+
+// Error bits in Status::error.
+constexpr int kErrNonfinite = 1;
+constexpr int kErrOverflow = 2;
+
+// Device-resident loop state; the host reads it back only when asked.
+struct Status {
+    unsigned long long bbox[6];     // order-preserving keys: min x, y, z then max x, y, z
+    unsigned long long max_dtheta;  // bit pattern of a non-negative double (atomicMax)
+    unsigned long long max_abs_tau;
+    unsigned int ticket;  // last-block detection in the step kernel
+    int iters;            // iterations taken since the last reset
+    int done;             // converged or failed: the remaining iterations are no-ops
+    int error;            // kErr* bits
+    double last_max_dtheta;
+    unsigned long long pairs;
+    unsigned long long nbr_total;
+    unsigned long long guard;
+    unsigned long long sasa_tests;  // overlap tests performed by Algorithm 1 (steps 1 and 2)
+    int max_nbr;
+    int pad;
+};
+
+// Launch shapes.
+constexpr int kFkChunk = 8;     // joints per thread in the transform scan
+constexpr int kFkTpb = 8;       // threads per block of the FP64 chunk kernels (spreads FP64 work over SMs)
+constexpr int kLinkChunk = 8;   // links per thread in the wrench / suffix-sum kernels
+constexpr int kScanThreads = 64;
+constexpr int kPairTpb = 128;
+constexpr int kSasaWarps = 4;
+constexpr int kApplyTpb = 64;
+
+struct DevChain {
+    int m = 0, n = 0, l = 0, L = 0, N = 0;
+    int nfk_chunks = 0, nlink_chunks = 0;
+    int cell_cap = 0;
+    int pair_blocks = 0, sasa_blocks = 0;
+    kcm_params prm{};
+    // derived constants
+    double rcut2 = 0, rvdw2 = 0;  // squared pair cutoffs
+    double rmax = 0;              // largest interaction range (pair cutoffs, solvation neighbour range)
+    double roff_max = 0;          // largest offset-sphere radius
+    float guard_pair = 0, guard_sasa = 0;
+
+    // static data
+    double* r0 = nullptr;          // ZP centres [n*3]
+    int* link = nullptr;           // [n]
+    int* link_start = nullptr;     // [L+1]
+    double* u0 = nullptr;          // [l*3]
+    double* p0 = nullptr;          // [l*3]
+    dbl4* aprm64 = nullptr;     // per atom: q, sqrt(eps), R, Roff
+    float4* aprm32 = nullptr;      // the same in float
+    double* G0 = nullptr;          // 4 pi gamma Roff^2 [n]
+    long long* qfx = nullptr;      // G0 / (N dr) in fixed point [n]
+    unsigned long long* exm = nullptr;   // [n]
+    unsigned long long* m14m = nullptr;  // [n]
+    double* Q64 = nullptr;         // [N*3]
+    float* Q32 = nullptr;          // [N*3]
+
+    // per-iteration data
+    double* theta = nullptr;       // [l]
+    double* dtheta = nullptr;      // [l]
+    double* tau = nullptr;         // [l]
+    double* G = nullptr;           // joint transforms [l*12]
+    double* chunkP = nullptr;      // [nfk_chunks*12]
+    double* chunkE = nullptr;      // [nfk_chunks*12]
+    double* M = nullptr;           // link transforms [L*12]
+    double* ucur = nullptr;        // current joint axes [l*3]
+    double* pcur = nullptr;        // current axis points [l*3]
+    double* r = nullptr;           // centres [n*3]
+    int* key = nullptr;            // cell of each atom [n]
+    int* cell_count = nullptr;     // [cell_cap]
+    int* cell_start = nullptr;     // [cell_cap+1]
+    int* cell_cursor = nullptr;    // [cell_cap]
+    int* sorted = nullptr;         // slot -> atom [n]
+    int* slot_cell = nullptr;      // slot -> cell [n]
+    dbl4* spos64 = nullptr;     // sorted centres + charge [n]
+    float4* spos32 = nullptr;      // sorted cell-relative offsets + charge [n]
+    float4* sprm32 = nullptr;      // sorted sqrt(eps), R, Roff [n]
+    dbl4* sprm64 = nullptr;     // [n]
+    double* Fpair = nullptr;       // [n*3]
+    long long* Fcav = nullptr;     // fixed point [n*3]
+    int* nbr_cnt = nullptr;        // [n]
+    int* nbr = nullptr;            // [n*kMaxNbr]
+    float4* nbr_off = nullptr;     // r_j - r_i and Roff_j^2 [n*kMaxNbr]
+    int* covered = nullptr;        // [n]
+    double* P = nullptr;           // link wrenches [L*6]
+    double* chunkS = nullptr;      // [nlink_chunks*6]
+    double* chunkSuf = nullptr;    // [nlink_chunks*6]
+    double* Epair = nullptr;       // [pair_blocks*2]
+    double* Ecav = nullptr;        // [sasa_blocks]
+    double* E = nullptr;           // [3]
+    double* Ftot = nullptr;        // [n*3] (on request)
+    double* Fcav64 = nullptr;      // [n*3] (on request)
+    GridInfo* grid = nullptr;
+    Status* status = nullptr;
+};
+
+// launchers (kcm_kernels.cu)
+void launch_init_status(DevChain& d, cudaStream_t s);
+void launch_reset_loop(DevChain& d, cudaStream_t s);
+void launch_fk(DevChain& d, cudaStream_t s);
+void launch_binning(DevChain& d, cudaStream_t s);
+void launch_forces(DevChain& d, cudaStream_t s);
+void launch_pairs(DevChain& d, cudaStream_t s);
+void launch_sasa(DevChain& d, cudaStream_t s);
+void launch_torques(DevChain& d, cudaStream_t s);
+void launch_energy(DevChain& d, cudaStream_t s);
+void launch_step(DevChain& d, cudaStream_t s);
+void launch_force_out(DevChain& d, cudaStream_t s);
+
+}  // namespace kcm

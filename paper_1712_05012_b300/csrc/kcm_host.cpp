@@ -1,0 +1,277 @@
+// Host-side construction of a chain for the KCM engine: ZP geometry, rigid-link layout, joint
+// axes, bond-class masks, solvation constants and the unit-sphere sample set.
+//
+// Geometry (Sec. 2.1, Sec. 4.1 "Preprocessing"): the zero position (ZP) has every peptide plane
+// coplanar, phi = psi = 180 deg (theta = 0, eq. theta_1/theta_2) and trans peptide bonds. Atoms
+// are placed one at a time from their bond length, bond angle and dihedral relative to three
+// already-placed atoms (natural extension reference frame).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "kcm_internal.h"
+
+namespace kcm {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct V3 {
+    double x, y, z;
+};
+inline V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+inline V3 unit(V3 a) { return (1.0 / std::sqrt(dot(a, a))) * a; }
+
+// Place D with |CD| = len, angle(B, C, D) = ang and IUPAC dihedral(A, B, C, D) = dih.
+V3 place(V3 A, V3 B, V3 C, double len, double ang, double dih) {
+    V3 bc = unit(C - B);
+    V3 nrm = unit(cross(B - A, bc));
+    V3 mid = cross(nrm, bc);
+    double dx = -len * std::cos(ang);
+    double dy = len * std::sin(ang) * std::cos(dih);
+    double dz = len * std::sin(ang) * std::sin(dih);
+    return C + dx * bc + dy * mid + dz * nrm;
+}
+
+double rad(double deg) { return deg * kPi / 180.0; }
+
+}  // namespace
+
+// Table 3 (Sharp et al. adjustment), kcal mol^-1 A^-2; H (not in the table) gets 0.
+double gamma_of_class(int cls) {
+    static const double g[6] = {0.012, -0.116, -0.018, -0.175, -0.186, 0.0};
+    return (cls >= 0 && cls < 6) ? g[cls] : 0.0;
+}
+
+int validate_params(const kcm_params* p, std::string* err) {
+    if (!p) { *err = "params is NULL"; return KCM_E_INVAL; }
+    if (!(p->cutoff > 0.0) || !(p->vdw_cutoff >= 0.0) || !(p->kappa >= 0.0) || !(p->dtheta_max > 0.0) ||
+        !(p->r_probe >= 0.0) || !(p->delta_r > 0.0) || !(p->conv_tol >= 0.0) || !(p->cell_size >= 0.0) ||
+        !std::isfinite(p->coulomb_k) || !std::isfinite(p->w14_elec) || !std::isfinite(p->w14_vdw) ||
+        !std::isfinite(p->cutoff) || !std::isfinite(p->vdw_cutoff) || !std::isfinite(p->cell_size)) {
+        *err = "a parameter is out of range";
+        return KCM_E_INVAL;
+    }
+    if (p->n_sample < 1 || p->n_sample > kMaxSample) { *err = "n_sample must be in [1, 4096]"; return KCM_E_INVAL; }
+    if (p->precision != KCM_FP64 && p->precision != KCM_MIXED) { *err = "bad precision"; return KCM_E_INVAL; }
+    if (p->step_mode != KCM_STEP_CLAMP && p->step_mode != KCM_STEP_NORMALIZED) { *err = "bad step_mode"; return KCM_E_INVAL; }
+    if (p->solvation != 0 && p->solvation != 1) { *err = "solvation must be 0 or 1"; return KCM_E_INVAL; }
+    return KCM_OK;
+}
+
+// Latitude-ring sample set of Sec. 3.4 (see kcm_sample_points in kcm.h for the recipe).
+int sample_points(int N, double* Q) {
+    if (N < 1) return KCM_E_INVAL;
+    int K = static_cast<int>(std::floor(std::sqrt(kPi * static_cast<double>(N) / 4.0) + 0.5));
+    if (K < 1) K = 1;
+    std::vector<double> wt(K), frac(K);
+    std::vector<int> cnt(K);
+    double total = 0.0;
+    for (int r = 1; r <= K; ++r) {
+        wt[r - 1] = std::sin(kPi * (static_cast<double>(r) - 0.5) / static_cast<double>(K));
+        total += wt[r - 1];
+    }
+    int given = 0;
+    for (int r = 0; r < K; ++r) {
+        double share = static_cast<double>(N) * wt[r] / total;
+        cnt[r] = static_cast<int>(std::floor(share));
+        frac[r] = share - std::floor(share);
+        given += cnt[r];
+    }
+    while (given < N) {  // largest remainder first, lower ring on ties
+        int pick = 0;
+        for (int r = 1; r < K; ++r)
+            if (frac[r] > frac[pick]) pick = r;
+        cnt[pick] += 1;
+        frac[pick] = -1.0;
+        ++given;
+    }
+    int k = 0;
+    for (int r = 1; r <= K; ++r) {
+        double polar = kPi * (static_cast<double>(r) - 0.5) / static_cast<double>(K);
+        for (int t = 0; t < cnt[r - 1]; ++t) {
+            double lon = 2.0 * kPi * (static_cast<double>(t) + 0.5 * static_cast<double>(r % 2)) /
+                         static_cast<double>(cnt[r - 1]);
+            Q[3 * k + 0] = std::sin(polar) * std::cos(lon);
+            Q[3 * k + 1] = std::sin(polar) * std::sin(lon);
+            Q[3 * k + 2] = std::cos(polar);
+            ++k;
+        }
+    }
+    return KCM_OK;
+}
+
+// Bond class from parent pointers on the bond tree rooted at N_1 (Sec. 3.3): 1-2 when one atom
+// is the other's parent; 1-3 when grandparent or sibling; 1-4 when great-grandparent or a
+// sibling of the parent. Returns 1 for 1-2/1-3 (excluded), 2 for 1-4, 0 otherwise.
+int bond_class_tree(const HostChain& hc, int a, int b) {
+    const std::vector<int>& P = hc.parent;
+    auto up = [&](int x, int k) {
+        for (int i = 0; i < k && x >= 0; ++i) x = P[x];
+        return x;
+    };
+    auto one_way = [&](int x, int y) -> int {
+        if (P[x] == y) return 1;                                        // one bond
+        if (up(x, 2) == y || (P[x] >= 0 && P[x] == P[y])) return 2;     // two bonds
+        int gp = up(x, 2);
+        if (up(x, 3) == y || (gp >= 0 && P[y] == gp && y != P[x])) return 3;  // three bonds
+        return 9;
+    };
+    if (a == b) return 1;
+    int len = std::min(one_way(a, b), one_way(b, a));
+    if (len <= 2) return 1;
+    if (len == 3) return 2;
+    return 0;
+}
+
+int build_host_chain(const kcm_topology* top, HostChain* hc, std::string* err) {
+    if (!top || top->n_res < 1 || top->n_types < 1 || !top->res_type || !top->types) {
+        *err = "topology is empty or has NULL arrays";
+        return KCM_E_INVAL;
+    }
+    kcm_geometry g;
+    if (top->geometry) {
+        g = *top->geometry;
+    } else {
+        g = kcm_geometry{1.458, 1.525, 1.329, 1.231, 1.0, 1.53, 111.2, 116.2, 121.7, 120.8, 109.47122063449069};
+    }
+    const int m = top->n_res;
+    std::vector<int> first(m), nside(m);
+    long long n = 0;
+    for (int i = 0; i < m; ++i) {
+        int t = top->res_type[i];
+        if (t < 0 || t >= top->n_types) { *err = "residue type out of range"; return KCM_E_INVAL; }
+        int k = top->types[t].n_side;
+        if (k < 1 || k > KCM_MAX_SIDE) { *err = "side group size must be 1..10"; return KCM_E_INVAL; }
+        first[i] = static_cast<int>(n);
+        nside[i] = k;
+        n += 5 + k;
+        if (n > (1LL << 28)) { *err = "chain too long"; return KCM_E_INVAL; }
+    }
+    hc->m = m;
+    hc->n = static_cast<int>(n);
+    hc->l = 2 * m;
+    hc->L = 2 * m + 1;
+    hc->zp.assign(3 * n, 0.0);
+    hc->link.assign(n, 0);
+    hc->parent.assign(n, -1);
+    hc->kind.assign(n, 0);
+    hc->q.assign(n, 0.0);
+    hc->eps.assign(n, 0.0);
+    hc->R.assign(n, 0.0);
+    hc->cls.assign(n, 0);
+    auto iN = [&](int i) { return first[i]; };
+    auto iH = [&](int i) { return first[i] + 1; };
+    auto iCA = [&](int i) { return first[i] + 2; };
+    auto iS = [&](int i, int t) { return first[i] + 3 + t; };
+    auto iC = [&](int i) { return first[i] + 3 + nside[i]; };
+    auto iO = [&](int i) { return first[i] + 4 + nside[i]; };
+
+    // constants, links and bond-tree parents
+    for (int i = 0; i < m; ++i) {
+        const kcm_restype& rt = top->types[top->res_type[i]];
+        auto setp = [&](int a, const kcm_atom_param& ap, int kind, int lnk, int par) {
+            if (!(ap.sigma > 0.0) || !(ap.eps >= 0.0) || !std::isfinite(ap.q) || !std::isfinite(ap.sigma) ||
+                !std::isfinite(ap.eps) || ap.solv_class < 0 || ap.solv_class > 5)
+                return false;
+            hc->q[a] = ap.q;
+            hc->eps[a] = ap.eps;
+            hc->R[a] = 0.5 * ap.sigma;
+            hc->cls[a] = ap.solv_class;
+            hc->kind[a] = kind;
+            hc->link[a] = lnk;
+            hc->parent[a] = par;
+            return true;
+        };
+        int pep_prev = (i == 0) ? 0 : 2 * i;  // link holding N_i, H_i
+        bool ok = setp(iN(i), rt.backbone[0], 0, pep_prev, i == 0 ? -1 : iC(i - 1));
+        ok = ok && setp(iH(i), rt.backbone[1], 1, pep_prev, iN(i));
+        ok = ok && setp(iCA(i), rt.backbone[2], 2, 2 * i + 1, iN(i));
+        for (int t = 0; t < nside[i]; ++t) ok = ok && setp(iS(i, t), rt.side[t], 5, 2 * i + 1, t == 0 ? iCA(i) : iS(i, t - 1));
+        ok = ok && setp(iC(i), rt.backbone[3], 3, 2 * i + 2, iCA(i));
+        ok = ok && setp(iO(i), rt.backbone[4], 4, 2 * i + 2, iC(i));
+        if (!ok) { *err = "atom constants out of range (sigma > 0, eps >= 0, class 0..5)"; return KCM_E_INVAL; }
+    }
+    hc->link_start.assign(hc->L + 1, 0);
+    for (int a = 0, h = 0; a < hc->n; ++a) {
+        if (a > 0 && hc->link[a] < hc->link[a - 1]) { *err = "internal: links are not contiguous"; return KCM_E_INVAL; }
+        while (h <= hc->link[a]) hc->link_start[h++] = a;
+    }
+    hc->link_start[hc->L] = hc->n;
+
+    // ZP coordinates
+    std::vector<V3> X(n, V3{0, 0, 0});
+    const double a_ncac = rad(g.a_n_ca_c), a_cacn = rad(g.a_ca_c_n), a_cnca = rad(g.a_c_n_ca), a_caco = rad(g.a_ca_c_o);
+    const double a_side = rad(g.a_side), a_h = rad((360.0 - g.a_c_n_ca) / 2.0);
+    X[iN(0)] = V3{0.0, 0.0, 0.0};
+    X[iCA(0)] = V3{g.b_n_ca, 0.0, 0.0};
+    X[iC(0)] = X[iCA(0)] + g.b_ca_c * V3{std::cos(kPi - a_ncac), std::sin(kPi - a_ncac), 0.0};
+    for (int i = 1; i < m; ++i) {
+        X[iN(i)] = place(X[iN(i - 1)], X[iCA(i - 1)], X[iC(i - 1)], g.b_c_n, a_cacn, kPi);    // psi = 180
+        X[iCA(i)] = place(X[iCA(i - 1)], X[iC(i - 1)], X[iN(i)], g.b_n_ca, a_cnca, kPi);    // omega = 180
+        X[iC(i)] = place(X[iC(i - 1)], X[iN(i)], X[iCA(i)], g.b_ca_c, a_ncac, kPi);         // phi = 180
+    }
+    for (int i = 0; i < m; ++i) {
+        X[iO(i)] = place(X[iN(i)], X[iCA(i)], X[iC(i)], g.b_c_o, a_caco, 0.0);
+        if (i == 0)
+            X[iH(i)] = place(X[iC(0)], X[iCA(0)], X[iN(0)], g.b_n_h, a_h, 0.0);
+        else
+            X[iH(i)] = place(X[iCA(i - 1)], X[iC(i - 1)], X[iN(i)], g.b_n_h, a_h, 0.0);
+        // CB: the N-CA-C bisector (pointing away from N and C), turned by half the side angle
+        // toward n x c, which gives the L configuration
+        V3 nh = unit(X[iN(i)] - X[iCA(i)]);
+        V3 ch = unit(X[iC(i)] - X[iCA(i)]);
+        V3 bis = unit(-1.0 * (nh + ch));
+        V3 w = unit(cross(nh, ch));
+        X[iS(i, 0)] = X[iCA(i)] + g.b_side * (std::cos(0.5 * a_side) * bis + std::sin(0.5 * a_side) * w);
+        V3 A = X[iN(i)], B = X[iCA(i)], C = X[iS(i, 0)];
+        for (int t = 1; t < nside[i]; ++t) {
+            V3 D = place(A, B, C, g.b_side, a_side, kPi);
+            X[iS(i, t)] = D;
+            A = B;
+            B = C;
+            C = D;
+        }
+    }
+    for (long long a = 0; a < n; ++a) {
+        hc->zp[3 * a] = X[a].x;
+        hc->zp[3 * a + 1] = X[a].y;
+        hc->zp[3 * a + 2] = X[a].z;
+    }
+    // joint axes in the ZP: phi_i about N_i -> CA_i through N_i, psi_i about CA_i -> C_i through CA_i
+    hc->u0.assign(3 * hc->l, 0.0);
+    hc->p0.assign(3 * hc->l, 0.0);
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < 2; ++j) {
+            V3 from = j == 0 ? X[iN(i)] : X[iCA(i)];
+            V3 to = j == 0 ? X[iCA(i)] : X[iC(i)];
+            V3 u = unit(to - from);
+            double* U = &hc->u0[3 * (2 * i + j)];
+            double* Pp = &hc->p0[3 * (2 * i + j)];
+            U[0] = u.x; U[1] = u.y; U[2] = u.z;
+            Pp[0] = from.x; Pp[1] = from.y; Pp[2] = from.z;
+        }
+    }
+    // bond-class masks over the window (lo, lo + d), d = 1..63; every pair within three bonds
+    // must fall inside the window (a pair with a residue gap of two or more is never that close)
+    hc->ex_mask.assign(n, 0);
+    hc->m14_mask.assign(n, 0);
+    for (int a = 0; a < hc->n; ++a) {
+        for (int d = 1; d <= kMaskWindow && a + d < hc->n; ++d) {
+            int c = bond_class_tree(*hc, a, a + d);
+            if (c == 1) hc->ex_mask[a] |= (1ULL << d);
+            if (c == 2) hc->m14_mask[a] |= (1ULL << d);
+        }
+        for (int b = a + kMaskWindow + 1; b < hc->n && b <= a + kMaskWindow + 40; ++b) {
+            if (bond_class_tree(*hc, a, b) != 0) { *err = "internal: bonded pair outside the class window"; return KCM_E_INVAL; }
+        }
+    }
+    return KCM_OK;
+}
+
+}  // namespace kcm

@@ -1,0 +1,47 @@
+// Internal declarations of the KCM library (host builder, constants shared by host and device).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kcm.h"
+
+namespace kcm {
+
+// Fixed-point scale of the solvation force accumulators: one unit is 2^-40 kcal mol^-1 A^-1.
+// int64 then spans +-8.4e6 kcal mol^-1 A^-1, and integer addition makes the sum order-free.
+constexpr double kFxScale = 1099511627776.0;  // 2^40
+constexpr double kFxInv = 1.0 / 1099511627776.0;
+
+// Largest solvation neighbour list per atom; more raises KCM_E_OVERFLOW.
+constexpr int kMaxNbr = 128;
+
+// Largest sample count per offset sphere.
+constexpr int kMaxSample = 4096;
+
+// Bond classes are stored as two 64-bit masks per atom `lo`: bit d set means the pair
+// (lo, lo + d) is excluded (1-2 / 1-3) or is a 1-4 pair. Pairs within three bonds always lie
+// within this window for the chains built here (checked at build time).
+constexpr int kMaskWindow = 63;
+
+struct HostChain {
+    int m = 0, n = 0, l = 0, L = 0;  // residues, atoms, joints, links (L = l + 1)
+    std::vector<double> zp;          // ZP centres [n*3]
+    std::vector<int> link;           // link of each atom [n]
+    std::vector<int> link_start;     // first atom of each link [L+1]
+    std::vector<int> parent;         // bond-tree parent (root N_1: -1) [n]
+    std::vector<int> kind;           // 0 N, 1 H, 2 CA, 3 C, 4 O, 5 side
+    std::vector<double> q, eps, R;   // per atom (R = sigma / 2)
+    std::vector<int> cls;            // solvation class
+    std::vector<double> u0, p0;      // ZP joint axis direction and point [l*3]
+    std::vector<uint64_t> ex_mask, m14_mask;  // bond-class masks [n]
+};
+
+double gamma_of_class(int cls);
+int build_host_chain(const kcm_topology* top, HostChain* hc, std::string* err);
+int bond_class_tree(const HostChain& hc, int a, int b);  // 0 far, 1 excluded, 2 1-4
+int sample_points(int N, double* Q);
+int validate_params(const kcm_params* p, std::string* err);
+
+}  // namespace kcm

@@ -1,0 +1,319 @@
+"""Thin ctypes binding of libkcm.so (include/kcm.h). Argument marshalling only: every step of the
+KCM iteration runs in the library's CUDA kernels. Importing this module loads the library and
+raises if it is missing; there is no fallback path."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkcm.so")
+
+KCM_OK = 0
+KCM_E_INVAL = -1
+KCM_E_NOMEM = -2
+KCM_E_CUDA = -3
+KCM_E_NONFINITE = -5
+KCM_E_OVERFLOW = -6
+KCM_E_NODEVICE = -8
+KCM_FP64 = 0
+KCM_MIXED = 1
+KCM_STEP_CLAMP = 0
+KCM_STEP_NORMALIZED = 1
+MAX_SIDE = 10
+
+
+class KcmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"kcm error {code}: {msg}")
+        self.code = code
+
+
+class AtomParam(C.Structure):
+    _fields_ = [("q", C.c_double), ("eps", C.c_double), ("sigma", C.c_double), ("solv_class", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class ResType(C.Structure):
+    _fields_ = [("n_side", C.c_int32), ("reserved", C.c_int32), ("backbone", AtomParam * 5),
+                ("side", AtomParam * MAX_SIDE)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("b_n_ca", "b_ca_c", "b_c_n", "b_c_o", "b_n_h", "b_side", "a_n_ca_c",
+                                          "a_ca_c_n", "a_c_n_ca", "a_ca_c_o", "a_side")]
+
+
+class Topology(C.Structure):
+    _fields_ = [("n_res", C.c_int32), ("n_types", C.c_int32), ("res_type", C.POINTER(C.c_int32)),
+                ("types", C.POINTER(ResType)), ("geometry", C.POINTER(Geometry))]
+
+
+class Params(C.Structure):
+    _fields_ = [("cutoff", C.c_double), ("vdw_cutoff", C.c_double), ("kappa", C.c_double),
+                ("dtheta_max", C.c_double), ("w14_elec", C.c_double), ("w14_vdw", C.c_double),
+                ("r_probe", C.c_double), ("delta_r", C.c_double), ("coulomb_k", C.c_double),
+                ("conv_tol", C.c_double), ("cell_size", C.c_double), ("n_sample", C.c_int32),
+                ("solvation", C.c_int32), ("precision", C.c_int32), ("step_mode", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("pairs", C.c_int64), ("sasa_neighbors", C.c_int64), ("max_neighbors", C.c_int64),
+                ("guard_rechecks", C.c_int64), ("cells", C.c_int64), ("cell_size", C.c_double),
+                ("iterations", C.c_int64), ("sasa_tests", C.c_int64)]
+
+
+EXPORTS = [
+    "kcm_params_default", "kcm_create", "kcm_destroy", "kcm_natoms", "kcm_njoints", "kcm_set_theta",
+    "kcm_get_theta", "kcm_set_theta_dev", "kcm_get_theta_dev", "kcm_positions", "kcm_forces", "kcm_force_terms",
+    "kcm_torques", "kcm_torques_dev", "kcm_energy", "kcm_sasa_counts", "kcm_step", "kcm_step_async",
+    "kcm_step_status", "kcm_get_stats", "kcm_stream", "kcm_sample_points", "kcm_build_zp", "kcm_pair_class",
+    "kcm_topology_natoms", "kcm_strerror", "kcm_last_error", "kcm_step_timed",
+]
+NUM_STAGES = 7
+STAGES = ("kinematics", "binning", "pairs", "solvation", "torques", "energy", "step")
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+def load():
+    """Load libkcm.so (built in-tree by build.py); raises OSError when it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        h = C.c_void_p
+        sig = {
+            "kcm_params_default": (C.c_int, [C.POINTER(Params)]),
+            "kcm_create": (C.c_int, [C.POINTER(Topology), C.POINTER(Params), C.c_void_p, C.POINTER(C.c_void_p)]),
+            "kcm_destroy": (None, [h]),
+            "kcm_natoms": (C.c_int64, [h]),
+            "kcm_njoints": (C.c_int64, [h]),
+            "kcm_set_theta": (C.c_int, [h, _dp, C.c_int64]),
+            "kcm_get_theta": (C.c_int, [h, _dp, C.c_int64]),
+            "kcm_set_theta_dev": (C.c_int, [h, C.c_void_p, C.c_int64]),
+            "kcm_get_theta_dev": (C.c_int, [h, C.c_void_p, C.c_int64]),
+            "kcm_positions": (C.c_int, [h, _dp, C.c_int64]),
+            "kcm_forces": (C.c_int, [h, _dp, C.c_int64]),
+            "kcm_force_terms": (C.c_int, [h, _dp, _dp, C.c_int64]),
+            "kcm_torques": (C.c_int, [h, _dp, C.c_int64]),
+            "kcm_torques_dev": (C.c_int, [h, C.c_void_p, C.c_int64]),
+            "kcm_energy": (C.c_int, [h, _dp]),
+            "kcm_sasa_counts": (C.c_int, [h, _ip, C.c_int64]),
+            "kcm_step": (C.c_int, [h, C.c_int32, _ip, _dp]),
+            "kcm_step_async": (C.c_int, [h, C.c_int32]),
+            "kcm_step_status": (C.c_int, [h, _ip, _dp]),
+            "kcm_get_stats": (C.c_int, [h, C.POINTER(Stats)]),
+            "kcm_stream": (C.c_void_p, [h]),
+            "kcm_sample_points": (C.c_int, [C.c_int32, _dp]),
+            "kcm_build_zp": (C.c_int, [C.POINTER(Topology), _dp, _ip, C.c_int64]),
+            "kcm_pair_class": (C.c_int, [C.POINTER(Topology), _ip, _ip, C.c_int64, _ip]),
+            "kcm_topology_natoms": (C.c_int64, [C.POINTER(Topology)]),
+            "kcm_step_timed": (C.c_int, [h, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_float)]),
+            "kcm_strerror": (C.c_char_p, [C.c_int]),
+            "kcm_last_error": (C.c_char_p, [h]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, h=None):
+    if rc != KCM_OK:
+        L = load()
+        raise KcmError(rc, (L.kcm_last_error(h) or b"").decode() or L.kcm_strerror(rc).decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _iptr(a):
+    return a.ctypes.data_as(_ip)
+
+
+def params_struct(p) -> Params:
+    """A kcm_params from any object with the same field names (e.g. synth.RunParams)."""
+    s = Params()
+    for name, _ in Params._fields_:
+        setattr(s, name, getattr(p, name))
+    return s
+
+
+class TopologyArgs:
+    """kcm_topology plus the buffers it points to (kept alive together)."""
+
+    def __init__(self, res_type, table, geometry=None):
+        self.res = np.ascontiguousarray(res_type, dtype=np.int32)
+        nt = len(table.n_side)
+        self.types = (ResType * nt)()
+        for t in range(nt):
+            rt = self.types[t]
+            rt.n_side = int(table.n_side[t])
+            for s in range(5):
+                rt.backbone[s] = AtomParam(float(table.q[t, s]), float(table.eps[t, s]), float(table.sigma[t, s]),
+                                           int(table.cls[t, s]), 0)
+            for s in range(int(table.n_side[t])):
+                rt.side[s] = AtomParam(float(table.q[t, 5 + s]), float(table.eps[t, 5 + s]),
+                                       float(table.sigma[t, 5 + s]), int(table.cls[t, 5 + s]), 0)
+        self.geom = None
+        if geometry is not None:
+            self.geom = Geometry(**{k: float(geometry[k]) for k, _ in Geometry._fields_})
+        self.top = Topology(len(self.res), nt, _iptr(self.res), self.types,
+                            C.pointer(self.geom) if self.geom is not None else None)
+
+    def ptr(self):
+        return C.byref(self.top)
+
+
+def sample_points(N: int) -> np.ndarray:
+    Q = np.zeros((N, 3))
+    _check(load().kcm_sample_points(int(N), _dptr(Q)))
+    return Q
+
+
+def topology_natoms(res_type, table, geometry=None) -> int:
+    t = TopologyArgs(res_type, table, geometry)
+    n = load().kcm_topology_natoms(t.ptr())
+    if n < 0:
+        _check(int(n))
+    return int(n)
+
+
+def build_zp(res_type, table, geometry=None):
+    t = TopologyArgs(res_type, table, geometry)
+    n = topology_natoms(res_type, table, geometry)
+    xyz = np.zeros((n, 3))
+    link = np.zeros(n, dtype=np.int32)
+    _check(load().kcm_build_zp(t.ptr(), _dptr(xyz), _iptr(link), n))
+    return xyz, link
+
+
+def pair_class(res_type, table, a, b, geometry=None):
+    t = TopologyArgs(res_type, table, geometry)
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    b = np.ascontiguousarray(b, dtype=np.int32)
+    out = np.zeros(len(a), dtype=np.int32)
+    _check(load().kcm_pair_class(t.ptr(), _iptr(a), _iptr(b), len(a), _iptr(out)))
+    return out
+
+
+class Chain:
+    """One chain on the current CUDA device (kcm_create ... kcm_destroy)."""
+
+    def __init__(self, res_type, table, params, geometry=None, stream=None):
+        L = load()
+        self._t = TopologyArgs(res_type, table, geometry)
+        self._p = params_struct(params)
+        h = C.c_void_p()
+        rc = L.kcm_create(self._t.ptr(), C.byref(self._p), C.c_void_p(stream) if stream else None, C.byref(h))
+        if rc != KCM_OK:
+            raise KcmError(rc, (L.kcm_last_error(None) or b"").decode())
+        self._h = h
+        self.n = int(L.kcm_natoms(h))
+        self.l = int(L.kcm_njoints(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kcm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stream(self) -> int:
+        return int(load().kcm_stream(self._h) or 0)
+
+    def set_theta(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        _check(load().kcm_set_theta(self._h, _dptr(th), len(th)), self._h)
+
+    def get_theta(self):
+        th = np.zeros(self.l)
+        _check(load().kcm_get_theta(self._h, _dptr(th), self.l), self._h)
+        return th
+
+    def set_theta_dev(self, ptr: int, l: int):
+        _check(load().kcm_set_theta_dev(self._h, C.c_void_p(ptr), l), self._h)
+
+    def get_theta_dev(self, ptr: int, l: int):
+        _check(load().kcm_get_theta_dev(self._h, C.c_void_p(ptr), l), self._h)
+
+    def positions(self):
+        x = np.zeros((self.n, 3))
+        _check(load().kcm_positions(self._h, _dptr(x), self.n), self._h)
+        return x
+
+    def forces(self):
+        F = np.zeros((self.n, 3))
+        _check(load().kcm_forces(self._h, _dptr(F), self.n), self._h)
+        return F
+
+    def force_terms(self):
+        Fp = np.zeros((self.n, 3))
+        Fc = np.zeros((self.n, 3))
+        _check(load().kcm_force_terms(self._h, _dptr(Fp), _dptr(Fc), self.n), self._h)
+        return Fp, Fc
+
+    def torques(self):
+        t = np.zeros(self.l)
+        _check(load().kcm_torques(self._h, _dptr(t), self.l), self._h)
+        return t
+
+    def torques_dev(self, ptr: int):
+        _check(load().kcm_torques_dev(self._h, C.c_void_p(ptr), self.l), self._h)
+
+    def energy(self):
+        E = np.zeros(3)
+        _check(load().kcm_energy(self._h, _dptr(E)), self._h)
+        return E
+
+    def sasa_counts(self):
+        c = np.zeros(self.n, dtype=np.int32)
+        _check(load().kcm_sasa_counts(self._h, _iptr(c), self.n), self._h)
+        return c
+
+    def step(self, n_iters: int):
+        it = np.zeros(1, dtype=np.int32)
+        dm = np.zeros(1)
+        _check(load().kcm_step(self._h, int(n_iters), _iptr(it), _dptr(dm)), self._h)
+        return int(it[0]), float(dm[0])
+
+    def step_async(self, n_iters: int):
+        _check(load().kcm_step_async(self._h, int(n_iters)), self._h)
+
+    def step_status(self):
+        it = np.zeros(1, dtype=np.int32)
+        dm = np.zeros(1)
+        _check(load().kcm_step_status(self._h, _iptr(it), _dptr(dm)), self._h)
+        return int(it[0]), float(dm[0])
+
+    def step_timed(self):
+        """One iteration with CUDA-event timing: (total_ms, {stage: ms})."""
+        st = (C.c_float * NUM_STAGES)()
+        tot = C.c_float()
+        _check(load().kcm_step_timed(self._h, st, NUM_STAGES, C.byref(tot)), self._h)
+        return float(tot.value), dict(zip(STAGES, [float(x) for x in st]))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().kcm_get_stats(self._h, C.byref(s)), self._h)
+        return {k: getattr(s, k) for k, _ in Stats._fields_}

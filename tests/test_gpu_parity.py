@@ -1,0 +1,209 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances:
+  * positions: FP64 kinematics in both; the library composes 3x4 affine transforms in a chunked
+    scan while the oracle multiplies 3x3 rotations and sums body vectors, so the two differ only
+    by rounding, ~1e-16 relative per product over up to 2m products: 1e-10 A absolute.
+  * FP64 mode: forces, energies and torques to 1e-10 relative (max-norm), the library's stated
+    FP64 bar; sample-point classifications and pair sets are compared exactly (integers).
+  * mixed mode (FP32 pair and solvation arithmetic, FP64 kinematics/scans): torques to 1e-4
+    relative per evaluation, the bar stated for the 1,000-residue workload; classifications
+    are re-decided in FP64 inside a guard band, so covered counts and the pair set must equal
+    the FP64 mode's exactly.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from kcm_testutil import rel_inf
+from oracle import oracle as O
+from paper_1712_05012_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TOL_POS = 1e-10
+TOL_FP64 = 1e-10
+TOL_MIXED = 1e-4
+
+
+@pytest.fixture(scope="module")
+def kcm():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1712_05012_b300 import kcm as K
+    K.load()
+    return K
+
+
+def start(name):
+    man = json.load(open(os.path.join(GOLDEN, "starts.json")))[name]
+    codes = np.load(os.path.join(GOLDEN, f"start_{name}.npy"))
+    seq = synth.sequence(man["residues"], man["sequence_seed"])
+    return seq, synth.theta_from_codes(codes)
+
+
+def small_case(table, m, seed, kind="compact"):
+    seq = synth.sequence(m, seed)
+    och = O.OracleChain(seq, table, synth.GEOMETRY)
+    if kind == "compact":
+        th = synth.theta_from_codes(och.grow_start(seed))
+    elif kind == "extended":
+        th = synth.theta_extended(m)
+    else:
+        th = synth.theta_uniform(m, seed)
+    return seq, och, th
+
+
+def gpu_eval(kcm, seq, table, p, theta):
+    with kcm.Chain(seq, table, p) as ch:
+        ch.set_theta(theta)
+        out = dict(xyz=ch.positions(), tau=ch.torques(), E=ch.energy(), covered=ch.sasa_counts(),
+                   stats=ch.stats())
+        out["F_pair"], out["F_cav"] = ch.force_terms()
+        return out
+
+
+@pytest.mark.parametrize("m,seed,kind", [(1, 1, "uniform"), (2, 2, "uniform"), (3, 3, "compact"),
+                                         (40, 1235, "extended"), (40, 1235, "compact"), (97, 9, "compact")])
+def test_fp64_parity_small(kcm, table, m, seed, kind):
+    seq, och, th = small_case(table, m, seed, kind)
+    p = synth.RunParams(precision=synth.PRECISION_FP64)
+    ref = och.evaluate(p, th)
+    got = gpu_eval(kcm, seq, table, p, th)
+    assert np.max(np.abs(got["xyz"] - ref["xyz"])) < TOL_POS
+    assert rel_inf(got["F_pair"], ref["F_pair"]) < TOL_FP64
+    g = och.gamma != 0
+    assert np.array_equal(got["covered"][g], ref["covered"][g])
+    if np.any(ref["F_cav"]):
+        assert rel_inf(got["F_cav"], ref["F_cav"]) < TOL_FP64
+    assert rel_inf(got["tau"], ref["tau"]) < TOL_FP64
+    np.testing.assert_allclose(got["E"], ref["E"], rtol=TOL_FP64, atol=1e-9)
+    assert got["stats"]["pairs"] == ref["stats"]["pairs"]
+
+
+@pytest.mark.parametrize("solvation", [0, 1])
+def test_mixed_parity_chain1000(kcm, table, solvation):
+    """The 1,000-residue compact workload in the launch configuration the benchmark times."""
+    seq, th = start("chain1000")
+    och = O.OracleChain(seq, table, synth.GEOMETRY)
+    pm = synth.RunParams(precision=synth.PRECISION_MIXED, solvation=solvation)
+    pf = synth.RunParams(precision=synth.PRECISION_FP64, solvation=solvation)
+    ref = och.evaluate(pf, th)
+    mixed = gpu_eval(kcm, seq, table, pm, th)
+    fp64 = gpu_eval(kcm, seq, table, pf, th)
+    assert rel_inf(fp64["tau"], ref["tau"]) < TOL_FP64
+    assert rel_inf(mixed["tau"], ref["tau"]) < TOL_MIXED
+    assert mixed["stats"]["pairs"] == fp64["stats"]["pairs"] == ref["stats"]["pairs"]
+    assert np.array_equal(mixed["covered"], fp64["covered"])
+    np.testing.assert_allclose(mixed["E"], ref["E"], rtol=1e-5, atol=1e-3)
+    if solvation:
+        g = och.gamma != 0
+        assert np.array_equal(fp64["covered"][g], ref["covered"][g])
+        assert rel_inf(fp64["F_cav"], ref["F_cav"]) < TOL_FP64
+
+
+def test_fp64_trajectory_chain40(kcm, table):
+    """The 40-residue extended-start workload: 100 FP64 iterations against the oracle's loop."""
+    seq = synth.sequence(40, synth.chain_seed(synth.workload(1).seed, 0))
+    och = O.OracleChain(seq, table, synth.GEOMETRY)
+    for solvation in (0, 1):
+        p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=solvation)
+        th_ref, it_ref, _, dm_ref = och.run(p, synth.theta_extended(40), 100)
+        with kcm.Chain(seq, table, p) as ch:
+            it, dm = ch.step(100)
+            th = ch.get_theta()
+        assert it == it_ref
+        assert np.max(np.abs(th - th_ref)) < 1e-8
+        assert abs(dm - dm_ref[-1]) < 1e-8
+
+
+def test_step_rules(kcm, table):
+    seq, och, th = small_case(table, 10, 5)
+    p = synth.RunParams(precision=synth.PRECISION_FP64)
+    ref = och.evaluate(p, th)
+    for mode in (0, 1):
+        p = synth.RunParams(precision=synth.PRECISION_FP64, step_mode=mode, kappa=0.05 if mode else 1e-3)
+        want, _, dmax = O.step(th, ref["tau"], p.kappa, p.dtheta_max, mode)
+        with kcm.Chain(seq, table, p) as ch:
+            ch.set_theta(th)
+            it, dm = ch.step(1)
+            got = ch.get_theta()
+        assert it == 1
+        assert np.max(np.abs(got - want)) < 1e-12
+        assert abs(dm - dmax) < 1e-12
+    # convergence: a tiny gain stops after the first iteration
+    p = synth.RunParams(precision=synth.PRECISION_FP64, kappa=1e-14)
+    with kcm.Chain(seq, table, p) as ch:
+        ch.set_theta(th)
+        it, dm = ch.step(50)
+    assert it == 1 and dm < p.conv_tol
+
+
+def test_deterministic(kcm, table):
+    seq, th = start("chain1000")
+    p = synth.RunParams(precision=synth.PRECISION_MIXED)
+    with kcm.Chain(seq, table, p) as ch:
+        ch.set_theta(th)
+        t1 = ch.torques()
+        t2 = ch.torques()
+        ch.step(5)
+        a = ch.get_theta()
+        ch.set_theta(th)
+        ch.step(5)
+        b = ch.get_theta()
+    assert np.array_equal(t1, t2)
+    assert np.array_equal(a, b)
+
+
+def test_overflow_is_reported(kcm, table):
+    """A huge probe radius gives every atom far more solvation neighbours than the list holds."""
+    seq, och, th = small_case(table, 30, 8)
+    p = synth.RunParams(r_probe=9.0)
+    with kcm.Chain(seq, table, p) as ch:
+        ch.set_theta(th)
+        with pytest.raises(kcm.KcmError) as e:
+            ch.torques()
+        assert e.value.code == kcm.KCM_E_OVERFLOW
+
+
+def test_invalid_theta_rejected(kcm, table):
+    seq, och, th = small_case(table, 4, 2)
+    with kcm.Chain(seq, table, synth.RunParams()) as ch:
+        bad = th.copy()
+        bad[1] = np.nan
+        with pytest.raises(kcm.KcmError) as e:
+            ch.set_theta(bad)
+        assert e.value.code == kcm.KCM_E_INVAL
+        with pytest.raises(kcm.KcmError):
+            ch.set_theta(th[:-1])
+
+
+def test_device_pointer_calls(kcm, table):
+    import torch
+    seq, och, th = small_case(table, 20, 6)
+    p = synth.RunParams()
+    ref = och.evaluate(p, th)
+    with kcm.Chain(seq, table, p) as ch:
+        t = torch.tensor(th, dtype=torch.float64, device="cuda")
+        out = torch.zeros(ch.l, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        ch.set_theta_dev(t.data_ptr(), ch.l)
+        ch.torques_dev(out.data_ptr())
+        ch.step_status()  # synchronises the library's stream
+        assert rel_inf(out.cpu().numpy(), ref["tau"]) < TOL_FP64
+
+
+def test_chain8000_cut12_sampled(kcm, table):
+    """The 8,000-residue workload (12 A cutoff): positions everywhere and torques against the
+    oracle's full evaluation."""
+    seq, th = start("chain8000")
+    och = O.OracleChain(seq, table, synth.GEOMETRY)
+    pm = synth.RunParams(cutoff=12.0, precision=synth.PRECISION_MIXED)
+    ref = och.evaluate(synth.RunParams(cutoff=12.0), th)
+    got = gpu_eval(kcm, seq, table, pm, th)
+    assert np.max(np.abs(got["xyz"] - ref["xyz"])) < TOL_POS
+    assert rel_inf(got["tau"], ref["tau"]) < TOL_MIXED
+    assert got["stats"]["pairs"] == ref["stats"]["pairs"]
