@@ -129,21 +129,21 @@ int build_timed_graph(kcm_ctx* h) {
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
     cudaStream_t s = h->stream;
-    cudaEventRecord(h->ev[1], s);
+    cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
     kcm::launch_fk(h->d, s);
-    cudaEventRecord(h->ev[2], s);
+    cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
     kcm::launch_binning(h->d, s);
-    cudaEventRecord(h->ev[3], s);
+    cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
     kcm::launch_pairs(h->d, s);
-    cudaEventRecord(h->ev[4], s);
+    cudaEventRecordWithFlags(h->ev[4], s, cudaEventRecordExternal);
     kcm::launch_sasa(h->d, s);
-    cudaEventRecord(h->ev[5], s);
+    cudaEventRecordWithFlags(h->ev[5], s, cudaEventRecordExternal);
     kcm::launch_torques(h->d, s);
-    cudaEventRecord(h->ev[6], s);
+    cudaEventRecordWithFlags(h->ev[6], s, cudaEventRecordExternal);
     kcm::launch_energy(h->d, s);
-    cudaEventRecord(h->ev[7], s);
+    cudaEventRecordWithFlags(h->ev[7], s, cudaEventRecordExternal);
     kcm::launch_step(h->d, s);
-    cudaEventRecord(h->ev[8], s);
+    cudaEventRecordWithFlags(h->ev[8], s, cudaEventRecordExternal);
     e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
     e = cudaGraphInstantiate(&h->graph_timed, g, 0);
@@ -241,7 +241,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     const int n = d.n, l = d.l, L = d.L, N = d.N;
     const size_t nn = static_cast<size_t>(n);
     if ((rc = dalloc(h, &d.r0, 3 * nn)) || (rc = dalloc(h, &d.link, nn)) || (rc = dalloc(h, &d.link_start, L + 1)) ||
-        (rc = dalloc(h, &d.u0, 3 * l)) || (rc = dalloc(h, &d.p0, 3 * l)) || (rc = dalloc(h, &d.aprm64, nn)) ||
+        (rc = dalloc(h, &d.u0, 3 * l)) || (rc = dalloc(h, &d.step0, 3 * l)) || (rc = dalloc(h, &d.aprm64, nn)) ||
         (rc = dalloc(h, &d.aprm32, nn)) || (rc = dalloc(h, &d.G0, nn)) || (rc = dalloc(h, &d.qfx, nn)) ||
         (rc = dalloc(h, &d.exm, nn)) || (rc = dalloc(h, &d.m14m, nn)) || (rc = dalloc(h, &d.Q64, 3 * N)) ||
         (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.theta, l)) || (rc = dalloc(h, &d.dtheta, l)) ||
@@ -277,9 +277,9 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     kcm::sample_points(N, Q64.data());
     std::vector<float> Q32(Q64.begin(), Q64.end());
     std::vector<double> ident = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
-    if ((rc = upload(h, d.r0, hc.zp.data(), 3 * nn)) || (rc = upload(h, d.link, hc.link.data(), nn)) ||
+    if ((rc = upload(h, d.r0, hc.zp_rel.data(), 3 * nn)) || (rc = upload(h, d.link, hc.link.data(), nn)) ||
         (rc = upload(h, d.link_start, hc.link_start.data(), L + 1)) || (rc = upload(h, d.u0, hc.u0.data(), 3 * l)) ||
-        (rc = upload(h, d.p0, hc.p0.data(), 3 * l)) || (rc = upload(h, d.aprm64, ap64.data(), nn)) ||
+        (rc = upload(h, d.step0, hc.step0.data(), 3 * l)) || (rc = upload(h, d.aprm64, ap64.data(), nn)) ||
         (rc = upload(h, d.aprm32, ap32.data(), nn)) || (rc = upload(h, d.G0, G0.data(), nn)) ||
         (rc = upload(h, d.qfx, qfx.data(), nn)) ||
         (rc = upload(h, d.exm, reinterpret_cast<const unsigned long long*>(hc.ex_mask.data()), nn)) ||

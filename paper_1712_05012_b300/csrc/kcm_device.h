@@ -67,11 +67,11 @@ struct DevChain {
     float guard_pair = 0, guard_sasa = 0;
 
     // static data
-    double* r0 = nullptr;          // ZP centres [n*3]
+    double* r0 = nullptr;          // ZP centres relative to their link frame origin [n*3]
     int* link = nullptr;           // [n]
     int* link_start = nullptr;     // [L+1]
     double* u0 = nullptr;          // [l*3]
-    double* p0 = nullptr;          // [l*3]
+    double* step0 = nullptr;       // link frame steps p0_j - p0_{j-1} [l*3]
     dbl4* aprm64 = nullptr;     // per atom: q, sqrt(eps), R, Roff
     float4* aprm32 = nullptr;      // the same in float
     double* G0 = nullptr;          // 4 pi gamma Roff^2 [n]
@@ -85,10 +85,10 @@ struct DevChain {
     double* theta = nullptr;       // [l]
     double* dtheta = nullptr;      // [l]
     double* tau = nullptr;         // [l]
-    double* G = nullptr;           // joint transforms [l*12]
+    double* G = nullptr;           // local joint transforms [l*12]
     double* chunkP = nullptr;      // [nfk_chunks*12]
     double* chunkE = nullptr;      // [nfk_chunks*12]
-    double* M = nullptr;           // link transforms [L*12]
+    double* M = nullptr;           // link frame poses [L*12]
     double* ucur = nullptr;        // current joint axes [l*3]
     double* pcur = nullptr;        // current axis points [l*3]
     double* r = nullptr;           // centres [n*3]

@@ -257,6 +257,17 @@ int build_host_chain(const kcm_topology* top, HostChain* hc, std::string* err) {
             Pp[0] = from.x; Pp[1] = from.y; Pp[2] = from.z;
         }
     }
+    // local link frames: link h >= 1 has its origin at the point p0 of joint h (on its axis), the
+    // base link at N_1 (the origin). Frame steps and atom offsets are short vectors, so the
+    // transform scan never adds or cancels coordinates of the length of the extended chain.
+    hc->step0.assign(3 * hc->l, 0.0);
+    for (int j = 0; j < hc->l; ++j)
+        for (int x = 0; x < 3; ++x) hc->step0[3 * j + x] = hc->p0[3 * j + x] - (j > 0 ? hc->p0[3 * (j - 1) + x] : 0.0);
+    hc->zp_rel.assign(3 * n, 0.0);
+    for (int a = 0; a < hc->n; ++a) {
+        int h = hc->link[a];
+        for (int x = 0; x < 3; ++x) hc->zp_rel[3 * a + x] = hc->zp[3 * a + x] - (h > 0 ? hc->p0[3 * (h - 1) + x] : 0.0);
+    }
     // bond-class masks over the window (lo, lo + d), d = 1..63; every pair within three bonds
     // must fall inside the window (a pair with a residue gap of two or more is never that close)
     hc->ex_mask.assign(n, 0);

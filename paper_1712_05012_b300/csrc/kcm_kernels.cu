@@ -60,17 +60,20 @@ __device__ __forceinline__ void aff_store(double* dst, const double* A) {
     for (int k = 0; k < 12; ++k) dst[k] = A[k];
 }
 
-// Rotation by th about the axis through p with unit direction u (right-hand rule):
-// x -> R (x - p) + p, R = cos I + sin [u]x + (1 - cos) u u^T.
-__device__ __forceinline__ void joint_tf(const double* u, const double* p, double th, double* G) {
+// Local joint transform between consecutive link frames: L_j = Tr(step_j) o Rot(u_j, th), i.e.
+// x -> R x + step_j with R = cos I + sin [u]x + (1 - cos) u u^T (right-hand rule). With link frame
+// poses T_j = L_1 o ... o L_j the ZP-frame product of rotations about the joint axes (eq. kin_04)
+// is T_j o Tr(-p0_j), and atom centres are T_link(r^0 - p0_link) (eq. r1/r2).
+__device__ __forceinline__ void joint_tf(const double* u, const double* step, double th, double* G) {
     double s, c;
     sincos(th, &s, &c);
     double C = 1.0 - c;
     G[0] = c + u[0] * u[0] * C;        G[1] = u[0] * u[1] * C - u[2] * s; G[2] = u[0] * u[2] * C + u[1] * s;
     G[3] = u[1] * u[0] * C + u[2] * s; G[4] = c + u[1] * u[1] * C;        G[5] = u[1] * u[2] * C - u[0] * s;
     G[6] = u[2] * u[0] * C - u[1] * s; G[7] = u[2] * u[1] * C + u[0] * s; G[8] = c + u[2] * u[2] * C;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) G[9 + i] = p[i] - (G[3 * i] * p[0] + G[3 * i + 1] * p[1] + G[3 * i + 2] * p[2]);
+    G[9] = step[0];
+    G[10] = step[1];
+    G[11] = step[2];
 }
 
 template <typename T>
@@ -105,10 +108,10 @@ __global__ void k_fk_local(const DevChain d) {
     if (c >= d.nfk_chunks || d.status->done) return;
     int j0 = c * kFkChunk, j1 = min(d.l, j0 + kFkChunk);
     double P[12], Gj[12];
-    joint_tf(&d.u0[3 * j0], &d.p0[3 * j0], d.theta[j0], P);
+    joint_tf(&d.u0[3 * j0], &d.step0[3 * j0], d.theta[j0], P);
     aff_store(&d.G[12 * j0], P);
     for (int j = j0 + 1; j < j1; ++j) {
-        joint_tf(&d.u0[3 * j], &d.p0[3 * j], d.theta[j], Gj);
+        joint_tf(&d.u0[3 * j], &d.step0[3 * j], d.theta[j], Gj);
         aff_store(&d.G[12 * j], Gj);
         aff_compose(P, Gj, P);
     }
@@ -149,7 +152,8 @@ __global__ void k_fk_scan(const DevChain d) {
     }
 }
 
-// link transforms M_{j+1} = M_j o G_j, current axes u_j = R(M_j) u0_j, p_j = M_j(p0_j)
+// link frame poses M_{j+1} = M_j o L_j; current axis u_j = R(M_j) u0_j through p_j = origin of
+// frame j+1 (the joint's axis point)
 __global__ void k_fk_apply(const DevChain d) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.nfk_chunks || d.status->done) return;
@@ -158,15 +162,13 @@ __global__ void k_fk_apply(const DevChain d) {
     aff_load(&d.chunkE[12 * c], X);
     for (int j = j0; j < j1; ++j) {
         const double* u = &d.u0[3 * j];
-        const double* p = &d.p0[3 * j];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            d.ucur[3 * j + i] = X[3 * i] * u[0] + X[3 * i + 1] * u[1] + X[3 * i + 2] * u[2];
-            d.pcur[3 * j + i] = X[3 * i] * p[0] + X[3 * i + 1] * p[1] + X[3 * i + 2] * p[2] + X[9 + i];
-        }
+        for (int i = 0; i < 3; ++i) d.ucur[3 * j + i] = X[3 * i] * u[0] + X[3 * i + 1] * u[1] + X[3 * i + 2] * u[2];
         aff_load(&d.G[12 * j], Gj);
         aff_compose(X, Gj, X);
         aff_store(&d.M[12 * (j + 1)], X);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) d.pcur[3 * j + i] = X[9 + i];
     }
 }
 
