@@ -46,6 +46,7 @@ def lib():
             L.orc_natoms.restype = C.c_int
             L.orc_atom_info.argtypes = [C.c_void_p, _ip, _ip, _ip, _dp, _dp, _dp, _dp]
             L.orc_zp.argtypes = [C.c_void_p, _dp]
+            L.orc_zp_local.argtypes = [C.c_void_p, _dp, _dp]
             L.orc_bond_distance.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_bond_distance.restype = C.c_int
             L.orc_bonds.argtypes = [C.c_void_p, C.c_void_p]
@@ -201,6 +202,13 @@ class OracleChain:
         x = np.zeros((self.n, 3))
         lib().orc_zp(self._h, x.reshape(-1))
         return x
+
+    def zp_local(self):
+        """ZP as short vectors: (offset of each atom from its residue's N [n,3], N_i -> N_{i+1} [m,3])."""
+        loc = np.zeros((self.n, 3))
+        nstep = np.zeros((self.m, 3))
+        lib().orc_zp_local(self._h, loc.reshape(-1), nstep.reshape(-1))
+        return loc, nstep
 
     def bonds(self):
         nb = lib().orc_bonds(self._h, None)

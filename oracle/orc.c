@@ -98,7 +98,9 @@ typedef struct {
     int* first;      /* first atom of residue i: N_i */
     int* nside;      /* side atoms of residue i */
     double* q; double* eps; double* R; int* cls;
-    double* zp;      /* ZP coordinates [n*3] */
+    double* zp;      /* ZP coordinates [n*3] (output only) */
+    double* loc;     /* ZP offset of each atom from its residue's N [n*3] */
+    double* nstep;   /* ZP vector N_i -> N_{i+1} [m*3] */
     int* adj_start;  /* bond graph CSR */
     int* adj;
     int* near_start; /* atoms within 3 bonds (excluding self): partner and bond distance */
@@ -119,57 +121,61 @@ static double deg(double d) { return d * ORC_PI / 180.0; }
 
 /* ZP geometry (Sec. 2.1): all peptide planes coplanar, phi = psi = omega = 180 deg. The backbone
  * is a planar zig-zag in the xy-plane, N_1 at the origin, CA_1 on +x, C_1 at y > 0; with every
- * backbone dihedral at 180 deg consecutive turns alternate in sign. */
+ * backbone dihedral at 180 deg consecutive turns alternate in sign, so the direction of the bond
+ * leaving backbone atom t depends on t mod 6 only. The ZP is kept the way eq. kin_03 uses it, as
+ * short vectors: loc[a] is atom a's offset from the N of its residue and nstep[i] = N_{i+1} - N_i.
+ * Absolute ZP centres (zp[], output only) are the running sums of nstep plus loc. */
 static void zp_build(Chain* c) {
     const double* g = c->geom;
     double b_n_ca = g[0], b_ca_c = g[1], b_c_n = g[2], b_c_o = g[3], b_n_h = g[4], b_side = g[5];
     double a_n_ca_c = deg(g[6]), a_ca_c_n = deg(g[7]), a_c_n_ca = deg(g[8]), a_ca_c_o = deg(g[9]), a_side = deg(g[10]);
     int m = c->m;
-    double pos[3] = {0, 0, 0};
+    /* heading of the bond leaving backbone atom t (t mod 6): left turn at CA_1, then alternate */
+    double hout[6];
     double heading = 0.0;
-    int nb = 3 * m;
-    double* hin = (double*)malloc(sizeof(double) * nb); /* heading of the bond arriving at backbone atom t */
-    for (int t = 0; t < nb; t++) {
-        int i = t / 3, kk = t % 3;
-        int a = kk == 0 ? at_N(c, i) : (kk == 1 ? at_CA(c, i) : at_C(c, i));
-        memcpy(&c->zp[3 * a], pos, sizeof pos);
+    hout[0] = 0.0;
+    for (int t = 1; t < 6; t++) {
+        int kk = t % 3;
         double interior = kk == 0 ? a_c_n_ca : (kk == 1 ? a_n_ca_c : a_ca_c_n);
-        double sign = (t % 2 == 1) ? 1.0 : -1.0; /* left turn at CA_1, then alternate */
-        if (t == 0) {
-            hin[0] = heading - sign * (ORC_PI - interior); /* virtual C_0 continuing the zig-zag */
-        } else {
-            hin[t] = heading;
-            heading += sign * (ORC_PI - interior);
-        }
-        double len = kk == 0 ? b_n_ca : (kk == 1 ? b_ca_c : b_c_n);
-        pos[0] += len * cos(heading);
-        pos[1] += len * sin(heading);
-        pos[2] = 0.0;
+        double sign = (t % 2 == 1) ? 1.0 : -1.0;
+        heading += sign * (ORC_PI - interior);
+        hout[t] = heading;
     }
+    /* the bond arriving at atom t left atom t - 1; for N_1 this continues the zig-zag backwards */
+#define HOUT(t) hout[((t) % 6 + 6) % 6]
+#define HIN(t) hout[(((t) - 1) % 6 + 6) % 6]
     for (int i = 0; i < m; i++) {
+        int tN = 3 * i, tCA = 3 * i + 1, tC = 3 * i + 2;
+        int aN = at_N(c, i), aH = at_H(c, i), aCA = at_CA(c, i), aC = at_C(c, i), aO = at_O(c, i);
+        double* L = c->loc;
+        for (int x = 0; x < 3; x++) L[3 * aN + x] = 0.0;
+        L[3 * aCA + 0] = b_n_ca * cos(HOUT(tN));
+        L[3 * aCA + 1] = b_n_ca * sin(HOUT(tN));
+        L[3 * aCA + 2] = 0.0;
+        L[3 * aC + 0] = L[3 * aCA + 0] + b_ca_c * cos(HOUT(tCA));
+        L[3 * aC + 1] = L[3 * aCA + 1] + b_ca_c * sin(HOUT(tCA));
+        L[3 * aC + 2] = 0.0;
+        c->nstep[3 * i + 0] = L[3 * aC + 0] + b_c_n * cos(HOUT(tC));
+        c->nstep[3 * i + 1] = L[3 * aC + 1] + b_c_n * sin(HOUT(tC));
+        c->nstep[3 * i + 2] = 0.0;
         /* O_i: in the plane at C_i, on the side away from N_{i+1}; angle CA-C-O fixed */
-        int tC = 3 * i + 2;
         double sC = (tC % 2 == 1) ? 1.0 : -1.0;
-        double hO = hin[tC] - sC * (ORC_PI - a_ca_c_o);
-        int aC = at_C(c, i), aO = at_O(c, i);
-        c->zp[3 * aO + 0] = c->zp[3 * aC + 0] + b_c_o * cos(hO);
-        c->zp[3 * aO + 1] = c->zp[3 * aC + 1] + b_c_o * sin(hO);
-        c->zp[3 * aO + 2] = 0.0;
+        double hO = HIN(tC) - sC * (ORC_PI - a_ca_c_o);
+        L[3 * aO + 0] = L[3 * aC + 0] + b_c_o * cos(hO);
+        L[3 * aO + 1] = L[3 * aC + 1] + b_c_o * sin(hO);
+        L[3 * aO + 2] = 0.0;
         /* H_i: on the bisector of the external C(prev)-N-CA angle */
-        int tN = 3 * i;
-        double hout = (i == 0) ? 0.0 : (hin[tN] + ((tN % 2 == 1) ? 1.0 : -1.0) * (ORC_PI - a_c_n_ca));
-        double u1[3] = {cos(hin[tN] + ORC_PI), sin(hin[tN] + ORC_PI), 0.0};
-        double u2[3] = {cos(hout), sin(hout), 0.0};
-        double s[3], d[3];
-        v_add(u1, u2, s);
-        v_scale(s, -1.0, s);
-        v_unit(s, d);
-        int aN = at_N(c, i), aH = at_H(c, i);
-        for (int x = 0; x < 3; x++) c->zp[3 * aH + x] = c->zp[3 * aN + x] + b_n_h * d[x];
+        double u1[3] = {cos(HIN(tN) + ORC_PI), sin(HIN(tN) + ORC_PI), 0.0};
+        double u2[3] = {cos(HOUT(tN)), sin(HOUT(tN)), 0.0};
+        double s_[3], d[3];
+        v_add(u1, u2, s_);
+        v_scale(s_, -1.0, s_);
+        v_unit(s_, d);
+        for (int x = 0; x < 3; x++) L[3 * aH + x] = b_n_h * d[x];
         /* side group: CB at the tetrahedral L position, then a planar all-trans zig-zag */
-        double* N = &c->zp[3 * aN];
-        double* CA = &c->zp[3 * at_CA(c, i)];
-        double* C = &c->zp[3 * aC];
+        double* N = &L[3 * aN];
+        double* CA = &L[3 * aCA];
+        double* C = &L[3 * aC];
         double nh[3], ch[3], bis[3], bh[3], w[3], wh[3], ax[3], tmp[3];
         v_sub(N, CA, tmp); v_unit(tmp, nh);
         v_sub(C, CA, tmp); v_unit(tmp, ch);
@@ -179,9 +185,9 @@ static void zp_build(Chain* c) {
         double dir[3];
         rodrigues(bh, ax, 0.5 * a_side, dir); /* bisector turned toward n x c by half the tetrahedral angle */
         int aS = at_S(c, i, 0);
-        for (int x = 0; x < 3; x++) c->zp[3 * aS + x] = CA[x] + b_side * dir[x];
+        for (int x = 0; x < 3; x++) L[3 * aS + x] = CA[x] + b_side * dir[x];
         double pn[3], cb[3];
-        v_sub(&c->zp[3 * aS], CA, cb);
+        v_sub(&L[3 * aS], CA, cb);
         v_sub(N, CA, tmp);
         v_cross(tmp, cb, pn); v_unit(pn, pn);
         for (int t = 1; t < c->nside[i]; t++) {
@@ -190,10 +196,18 @@ static void zp_build(Chain* c) {
             rodrigues(dir, pn, turn, nd);
             memcpy(dir, nd, sizeof nd);
             int prev = at_S(c, i, t - 1), cur = at_S(c, i, t);
-            for (int x = 0; x < 3; x++) c->zp[3 * cur + x] = c->zp[3 * prev + x] + b_side * dir[x];
+            for (int x = 0; x < 3; x++) L[3 * cur + x] = L[3 * prev + x] + b_side * dir[x];
         }
     }
-    free(hin);
+#undef HOUT
+#undef HIN
+    double Nabs[3] = {0, 0, 0};
+    for (int i = 0; i < m; i++) {
+        int a0 = at_N(c, i), a1 = at_O(c, i);
+        for (int a = a0; a <= a1; a++)
+            for (int x = 0; x < 3; x++) c->zp[3 * a + x] = Nabs[x] + c->loc[3 * a + x];
+        for (int x = 0; x < 3; x++) Nabs[x] += c->nstep[3 * i + x];
+    }
 }
 
 /* Bond graph of the chain: N-H, N-CA, CA-side1, side_t-side_{t+1}, CA-C, C-O, C-N(next). */
@@ -297,6 +311,8 @@ void* orc_chain_new(int m, const int* res_type, const int* n_side, const double*
     c->R = (double*)malloc(sizeof(double) * n);
     c->cls = (int*)malloc(sizeof(int) * n);
     c->zp = (double*)calloc(3 * (size_t)n, sizeof(double));
+    c->loc = (double*)calloc(3 * (size_t)n, sizeof(double));
+    c->nstep = (double*)calloc(3 * (size_t)m, sizeof(double));
     for (int i = 0; i < m; i++) {
         int t = res_type[i], k = c->nside[i];
         /* links: base link 0 = {N_1, H_1}; CA-link 2i+1 = {CA_i, side_i}; peptide link 2i+2 =
@@ -328,7 +344,7 @@ void orc_chain_free(void* p) {
     Chain* c = (Chain*)p;
     if (!c) return;
     free(c->res); free(c->kind); free(c->slot); free(c->link); free(c->first); free(c->nside);
-    free(c->q); free(c->eps); free(c->R); free(c->cls); free(c->zp);
+    free(c->q); free(c->eps); free(c->R); free(c->cls); free(c->zp); free(c->loc); free(c->nstep);
     free(c->adj_start); free(c->adj); free(c->near_start); free(c->near_j); free(c->near_d);
     free(c);
 }
@@ -351,6 +367,14 @@ void orc_atom_info(void* p, int* res, int* kind, int* link, double* q, double* e
 void orc_zp(void* p, double* xyz) {
     Chain* c = (Chain*)p;
     memcpy(xyz, c->zp, sizeof(double) * 3 * (size_t)c->n);
+}
+
+/* the ZP as short vectors: loc[n*3] (offset of each atom from its residue's N) and
+ * nstep[m*3] (N_i -> N_{i+1}; the last entry is where N_{m+1} would be) */
+void orc_zp_local(void* p, double* loc, double* nstep) {
+    Chain* c = (Chain*)p;
+    memcpy(loc, c->loc, sizeof(double) * 3 * (size_t)c->n);
+    memcpy(nstep, c->nstep, sizeof(double) * 3 * (size_t)c->m);
 }
 
 /* number of bonds between a and b on the bond graph, or 4 when more than 3 */
@@ -376,22 +400,29 @@ int orc_bonds(void* p, int* out_pairs) {
 }
 
 /* ---------------------------------------------------------------- forward kinematics */
-/* eq. kin_04: M_j = R_1 R_2 ... R_j with R_r the rotation by theta_r about the ZP axis u^0_r;
- * eq. kin_02/03: u = M u^0, b = M b^0; eq. r1/r2: atom centres as prefix sums of body vectors,
- * N_1 anchored at the origin. Joint 2i+1 (phi of residue i) turns about N_i -> CA_i, joint 2i+2
- * (psi) about CA_i -> C_i. Outputs: atom centres [n*3]; optionally the current joint axes
- * u [2m*3] and a point on each axis p [2m*3] (N_i for phi, CA_i for psi). */
 /* One residue of the forward kinematics: given M = M_{2i} (rotation through the previous psi)
  * and the current centre of N_i, place CA_i, the side group, C_i, O_i, N_{i+1}, H_{i+1}; return
  * M_{2i+2} in Mout and N_{i+1} in rN_out. Optionally writes the current axes and axis points of
  * joints 2i+1 (phi_i) and 2i+2 (psi_i). */
+/* ZP offset of atom a from CA_i, for atoms of residue i and the N, H of residue i+1 (short
+ * vectors built from loc and nstep, never from differences of absolute ZP centres) */
+static void zp_from_ca(const Chain* c, int i, int a, double* v) {
+    const double* ca = &c->loc[3 * at_CA(c, i)];
+    if (c->res[a] == i) {
+        v_sub(&c->loc[3 * a], ca, v);
+    } else { /* N_{i+1} or H_{i+1}: through N_i -> N_{i+1} */
+        double t[3];
+        v_add(&c->nstep[3 * i], &c->loc[3 * a], t);
+        v_sub(t, ca, v);
+    }
+}
+
 static void fk_residue(const Chain* c, int i, double th_phi, double th_psi, const double M[9], const double* rN,
                        double* xyz, double Mout[9], double* rN_out, double* u2, double* p2) {
-    const double* zp = c->zp;
-    int aN = at_N(c, i), aCA = at_CA(c, i), aC = at_C(c, i);
+    int aCA = at_CA(c, i), aC = at_C(c, i);
     double u0[3], b0[3], R[9], Mphi[9], Mpsi[9], b[3], rCA[3], v0[3], v[3];
     /* phi_i: rotation about the ZP axis N_i -> CA_i (eq. kin_04) */
-    v_sub(&zp[3 * aCA], &zp[3 * aN], b0);
+    memcpy(b0, &c->loc[3 * aCA], sizeof b0); /* ZP body vector N_i -> CA_i */
     v_unit(b0, u0);
     rot_matrix(u0, th_phi, R);
     mat_mul(M, R, Mphi);
@@ -402,12 +433,12 @@ static void fk_residue(const Chain* c, int i, double th_phi, double th_psi, cons
     memcpy(&xyz[3 * aCA], rCA, sizeof rCA);
     for (int s = 0; s < c->nside[i]; s++) { /* eq. r2 */
         int aS = at_S(c, i, s);
-        v_sub(&zp[3 * aS], &zp[3 * aCA], v0);
+        zp_from_ca(c, i, aS, v0);
         mat_vec(Mphi, v0, v);
         v_add(rCA, v, &xyz[3 * aS]);
     }
     /* psi_i: rotation about the ZP axis CA_i -> C_i */
-    v_sub(&zp[3 * aC], &zp[3 * aCA], v0);
+    zp_from_ca(c, i, aC, v0);
     v_unit(v0, u0);
     rot_matrix(u0, th_psi, R);
     mat_mul(Mphi, R, Mpsi);
@@ -418,7 +449,7 @@ static void fk_residue(const Chain* c, int i, double th_phi, double th_psi, cons
     pep[np_++] = at_O(c, i);
     if (i + 1 < c->m) { pep[np_++] = at_N(c, i + 1); pep[np_++] = at_H(c, i + 1); }
     for (int x = 0; x < np_; x++) { /* peptide-plane atoms, rigid with the psi link */
-        v_sub(&zp[3 * pep[x]], &zp[3 * aCA], v0);
+        zp_from_ca(c, i, pep[x], v0);
         mat_vec(Mpsi, v0, v);
         v_add(rCA, v, &xyz[3 * pep[x]]);
     }

@@ -68,52 +68,57 @@ def rel_inf(a, b):
 
 
 def tol_positions(l):
-    """Parity bound (A) on atom centres after l joints. The oracle multiplies l rotation matrices in
-    sequence (eq. kin_04) and sums body vectors of about 1.5 A (eq. r1); each product adds a
-    relative error of a few ulp, so the rotation after k joints is off by up to ~3 k eps and the
-    centre at the end of the chain by up to ~sum_k 3 k eps * 1.5 A = 2.25 eps l^2 A. The bound
-    takes twice that, plus 1e-12 A."""
+    """Parity bound (A) on atom centres after l joints. Each FP64 rotation product adds a relative
+    error of a few ulp; accumulated over k products it behaves like a random walk, ~eps sqrt(k), and
+    the centre at the end of the chain sums such errors times body vectors of about 1.5 A, ~eps
+    l^1.5 A. Measured against an 80-bit evaluation of the same definition (tests/
+    test_oracle_precision.py) the oracle stays near 1.5 eps l^1.5; the bound is 16 eps l^1.5 + 1e-12."""
     eps = 2.0 ** -52
-    return 1e-12 + 4.5 * eps * l * l
+    return 1e-12 + 16.0 * eps * l ** 1.5
 
 
 def fk_extended(och, theta):
     """Atom centres of an oracle chain evaluated in 80-bit long double, in the paper's form:
-    M_j = R_1 ... R_j about the ZP axes (eq. kin_04), centres as sums of rotated ZP offsets
-    (eq. r1, r2). A higher-precision evaluation of the same definition, used to bound the FP64
-    rounding of both implementations."""
+    M_j = R_1 ... R_j about the ZP axes (eq. kin_04), centres as sums of rotated ZP body vectors
+    (eq. kin_03, r1, r2), starting from the oracle's ZP short vectors. A higher-precision evaluation
+    of the same definition, used to bound the FP64 rounding of both implementations."""
     LD = np.longdouble
-    zp = och.zp().astype(LD)
-    link = och.link
-    l = och.l
-    byl = [[] for _ in range(l + 1)]
-    for a in range(och.n):
-        byl[link[a]].append(a)
-    # the first atom of link h >= 1 lies on joint h's axis (CA for phi links, C for psi links)
-    out = np.zeros_like(zp)
-    out[byl[0]] = zp[byl[0]]
-    M = np.eye(3, dtype=LD)
-    prev_anchor_zp = zp[byl[0][0]]     # N_1
-    prev_anchor_now = out[byl[0][0]]
-    for h in range(1, l + 1):
-        at = byl[h]
-        # the axis of joint h runs from the previous link's anchor to this link's first atom
-        first = at[0]
-        if h % 2 == 1:   # phi: N_i -> CA_i ; the N_i of residue i belongs to the previous link
-            axis_from = zp[first - 2]  # N_i (order N, H, CA)
-        else:            # psi: CA_i -> C_i
-            axis_from = zp[first - 1 - (len(byl[h - 1]) - 1)]  # CA_i, first atom of the previous link
-        u = zp[first] - axis_from
-        u = u / np.sqrt(np.sum(u * u))
-        th = LD(theta[h - 1])
+    loc, nstep = och.zp_local()
+    loc = loc.astype(LD)
+    nstep = nstep.astype(LD)
+    res = och.res
+    first = np.searchsorted(res, np.arange(och.m))
+    last = np.append(first[1:], och.n)
+    out = np.zeros((och.n, 3), dtype=LD)
+
+    def rot(u, th):
+        th = LD(th)
         c, s = np.cos(th), np.sin(th)
         C = LD(1) - c
-        R = np.array([[c + u[0] * u[0] * C, u[0] * u[1] * C - u[2] * s, u[0] * u[2] * C + u[1] * s],
-                      [u[1] * u[0] * C + u[2] * s, c + u[1] * u[1] * C, u[1] * u[2] * C - u[0] * s],
-                      [u[2] * u[0] * C - u[1] * s, u[2] * u[1] * C + u[0] * s, c + u[2] * u[2] * C]], dtype=LD)
-        # the anchor (a point on the axis, fixed by the rotation) moves with the previous links
-        anchor_now = prev_anchor_now + M @ (axis_from - prev_anchor_zp)
-        M = M @ R
-        out[at] = anchor_now + (M @ (zp[at] - axis_from).T).T
-        prev_anchor_zp, prev_anchor_now = axis_from, anchor_now
+        return np.array([[c + u[0] * u[0] * C, u[0] * u[1] * C - u[2] * s, u[0] * u[2] * C + u[1] * s],
+                         [u[1] * u[0] * C + u[2] * s, c + u[1] * u[1] * C, u[1] * u[2] * C - u[0] * s],
+                         [u[2] * u[0] * C - u[1] * s, u[2] * u[1] * C + u[0] * s, c + u[2] * u[2] * C]], dtype=LD)
+
+    M = np.eye(3, dtype=LD)
+    rN = np.zeros(3, dtype=LD)
+    out[first[0]] = loc[first[0]]          # N_1
+    out[first[0] + 1] = loc[first[0] + 1]  # H_1
+    for i in range(och.m):
+        f, e = first[i], last[i]
+        aCA, aC, aO = f + 2, e - 2, e - 1
+        b = loc[aCA]
+        M = M @ rot(b / np.sqrt(np.sum(b * b)), theta[2 * i])
+        rCA = rN + M @ b
+        out[aCA] = rCA
+        side = np.arange(f + 3, aC)
+        out[side] = rCA + (M @ (loc[side] - loc[aCA]).T).T
+        v = loc[aC] - loc[aCA]
+        M = M @ rot(v / np.sqrt(np.sum(v * v)), theta[2 * i + 1])
+        out[aC] = rCA + M @ v
+        out[aO] = rCA + M @ (loc[aO] - loc[aCA])
+        if i + 1 < och.m:
+            g = first[i + 1]
+            out[g] = rCA + M @ (nstep[i] - loc[aCA])
+            out[g + 1] = rCA + M @ (nstep[i] + loc[g + 1] - loc[aCA])
+            rN = out[g]
     return out

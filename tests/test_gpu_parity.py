@@ -2,7 +2,7 @@
 
 Tolerances:
   * positions: FP64 kinematics in both. The oracle multiplies the l rotations in sequence, whose
-    rounding grows with l (bound: kcm_testutil.tol_positions, 2 x 2.25 eps l^2 A, pinned against an
+    rounding grows with l (bound: kcm_testutil.tol_positions, 16 eps l^1.5 A, checked against an
     80-bit evaluation); the library composes local link-frame transforms in a chunked scan and is
     checked against the 80-bit evaluation directly, to 2e-10 A.
   * FP64 mode: forces, energies and torques to 1e-10 relative (max-norm), the library's stated

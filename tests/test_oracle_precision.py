@@ -21,10 +21,11 @@ def test_extended_reference_is_the_same_definition(table):
     assert np.max(np.abs(fk_extended(och, th).astype(np.float64) - x)) < 1e-13
 
 
-def test_oracle_rounding_chain1000(table):
-    man = json.load(open(os.path.join(GOLDEN, "starts.json")))["chain1000"]
+@pytest.mark.parametrize("name", ["chain1000", "chain8000"])
+def test_oracle_rounding_long_chains(table, name):
+    man = json.load(open(os.path.join(GOLDEN, "starts.json")))[name]
     seq = synth.sequence(man["residues"], man["sequence_seed"])
-    th = synth.theta_from_codes(np.load(os.path.join(GOLDEN, "start_chain1000.npy")))
+    th = synth.theta_from_codes(np.load(os.path.join(GOLDEN, f"start_{name}.npy")))
     och = O.OracleChain(seq, table, synth.GEOMETRY)
     x, _, _ = och.fk(th)
     err = float(np.max(np.abs(fk_extended(och, th) - x)))
