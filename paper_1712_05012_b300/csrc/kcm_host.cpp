@@ -204,69 +204,94 @@ int build_host_chain(const kcm_topology* top, HostChain* hc, std::string* err) {
     }
     hc->link_start[hc->L] = hc->n;
 
-    // ZP coordinates
-    std::vector<V3> X(n, V3{0, 0, 0});
+    // ZP, residue by residue, in a frame re-centred on each residue's N: every stored vector is
+    // short (atom offsets from N_i, the step N_i -> N_{i+1}), so nothing is recovered by
+    // subtracting coordinates of a ~3.8 A-per-residue extended chain.
+    std::vector<V3> loc(n, V3{0, 0, 0});
+    std::vector<V3> nstep(m, V3{0, 0, 0});
     const double a_ncac = rad(g.a_n_ca_c), a_cacn = rad(g.a_ca_c_n), a_cnca = rad(g.a_c_n_ca), a_caco = rad(g.a_ca_c_o);
     const double a_side = rad(g.a_side), a_h = rad((360.0 - g.a_c_n_ca) / 2.0);
-    X[iN(0)] = V3{0.0, 0.0, 0.0};
-    X[iCA(0)] = V3{g.b_n_ca, 0.0, 0.0};
-    X[iC(0)] = X[iCA(0)] + g.b_ca_c * V3{std::cos(kPi - a_ncac), std::sin(kPi - a_ncac), 0.0};
-    for (int i = 1; i < m; ++i) {
-        X[iN(i)] = place(X[iN(i - 1)], X[iCA(i - 1)], X[iC(i - 1)], g.b_c_n, a_cacn, kPi);    // psi = 180
-        X[iCA(i)] = place(X[iCA(i - 1)], X[iC(i - 1)], X[iN(i)], g.b_n_ca, a_cnca, kPi);    // omega = 180
-        X[iC(i)] = place(X[iC(i - 1)], X[iN(i)], X[iCA(i)], g.b_ca_c, a_ncac, kPi);         // phi = 180
-    }
+    V3 pN{0, 0, 0}, pCA{0, 0, 0}, pC{0, 0, 0};  // previous residue's N, CA, C relative to its N
     for (int i = 0; i < m; ++i) {
-        X[iO(i)] = place(X[iN(i)], X[iCA(i)], X[iC(i)], g.b_c_o, a_caco, 0.0);
-        if (i == 0)
-            X[iH(i)] = place(X[iC(0)], X[iCA(0)], X[iN(0)], g.b_n_h, a_h, 0.0);
-        else
-            X[iH(i)] = place(X[iCA(i - 1)], X[iC(i - 1)], X[iN(i)], g.b_n_h, a_h, 0.0);
+        V3 N{0, 0, 0}, CA, C, H;
+        if (i == 0) {
+            CA = V3{g.b_n_ca, 0.0, 0.0};
+            C = CA + g.b_ca_c * V3{std::cos(kPi - a_ncac), std::sin(kPi - a_ncac), 0.0};
+            H = place(C, CA, N, g.b_n_h, a_h, 0.0);
+        } else {
+            V3 Nn = place(pN, pCA, pC, g.b_c_n, a_cacn, kPi);     // psi = 180
+            V3 CAn = place(pCA, pC, Nn, g.b_n_ca, a_cnca, kPi);   // omega = 180
+            V3 Cn = place(pC, Nn, CAn, g.b_ca_c, a_ncac, kPi);    // phi = 180
+            nstep[i - 1] = Nn;
+            pCA = pCA - Nn;
+            pC = pC - Nn;
+            CA = CAn - Nn;
+            C = Cn - Nn;
+            H = place(pCA, pC, N, g.b_n_h, a_h, 0.0);
+        }
+        loc[iN(i)] = N;
+        loc[iH(i)] = H;
+        loc[iCA(i)] = CA;
+        loc[iC(i)] = C;
+        loc[iO(i)] = place(N, CA, C, g.b_c_o, a_caco, 0.0);
         // CB: the N-CA-C bisector (pointing away from N and C), turned by half the side angle
         // toward n x c, which gives the L configuration
-        V3 nh = unit(X[iN(i)] - X[iCA(i)]);
-        V3 ch = unit(X[iC(i)] - X[iCA(i)]);
+        V3 nh = unit(N - CA);
+        V3 ch = unit(C - CA);
         V3 bis = unit(-1.0 * (nh + ch));
         V3 w = unit(cross(nh, ch));
-        X[iS(i, 0)] = X[iCA(i)] + g.b_side * (std::cos(0.5 * a_side) * bis + std::sin(0.5 * a_side) * w);
-        V3 A = X[iN(i)], B = X[iCA(i)], C = X[iS(i, 0)];
+        loc[iS(i, 0)] = CA + g.b_side * (std::cos(0.5 * a_side) * bis + std::sin(0.5 * a_side) * w);
+        V3 A = N, B = CA, D = loc[iS(i, 0)];
         for (int t = 1; t < nside[i]; ++t) {
-            V3 D = place(A, B, C, g.b_side, a_side, kPi);
-            X[iS(i, t)] = D;
+            V3 E = place(A, B, D, g.b_side, a_side, kPi);
+            loc[iS(i, t)] = E;
             A = B;
-            B = C;
-            C = D;
+            B = D;
+            D = E;
         }
+        pN = N;
+        pCA = CA;
+        pC = C;
     }
-    for (long long a = 0; a < n; ++a) {
-        hc->zp[3 * a] = X[a].x;
-        hc->zp[3 * a + 1] = X[a].y;
-        hc->zp[3 * a + 2] = X[a].z;
-    }
-    // joint axes in the ZP: phi_i about N_i -> CA_i through N_i, psi_i about CA_i -> C_i through CA_i
-    hc->u0.assign(3 * hc->l, 0.0);
-    hc->p0.assign(3 * hc->l, 0.0);
+    if (m > 0) nstep[m - 1] = place(pN, pCA, pC, g.b_c_n, a_cacn, kPi);  // where N_{m+1} would be
+    // absolute ZP centres (reported by kcm_build_zp only)
+    V3 Nabs{0, 0, 0};
     for (int i = 0; i < m; ++i) {
-        for (int j = 0; j < 2; ++j) {
-            V3 from = j == 0 ? X[iN(i)] : X[iCA(i)];
-            V3 to = j == 0 ? X[iCA(i)] : X[iC(i)];
-            V3 u = unit(to - from);
-            double* U = &hc->u0[3 * (2 * i + j)];
-            double* Pp = &hc->p0[3 * (2 * i + j)];
-            U[0] = u.x; U[1] = u.y; U[2] = u.z;
-            Pp[0] = from.x; Pp[1] = from.y; Pp[2] = from.z;
+        for (int a = iN(i); a <= iO(i); ++a) {
+            V3 x = Nabs + loc[a];
+            hc->zp[3 * (size_t)a] = x.x;
+            hc->zp[3 * (size_t)a + 1] = x.y;
+            hc->zp[3 * (size_t)a + 2] = x.z;
         }
+        Nabs = Nabs + nstep[i];
     }
-    // local link frames: link h >= 1 has its origin at the point p0 of joint h (on its axis), the
-    // base link at N_1 (the origin). Frame steps and atom offsets are short vectors, so the
-    // transform scan never adds or cancels coordinates of the length of the extended chain.
+    // joint axes and local link frames: link 2i+1 (CA_i, side) has its origin at N_i on the phi_i
+    // axis, link 2i+2 (C_i, O_i, N_{i+1}, H_{i+1}) at CA_i on the psi_i axis, the base link at N_1
+    hc->u0.assign(3 * hc->l, 0.0);
     hc->step0.assign(3 * hc->l, 0.0);
-    for (int j = 0; j < hc->l; ++j)
-        for (int x = 0; x < 3; ++x) hc->step0[3 * j + x] = hc->p0[3 * j + x] - (j > 0 ? hc->p0[3 * (j - 1) + x] : 0.0);
     hc->zp_rel.assign(3 * n, 0.0);
-    for (int a = 0; a < hc->n; ++a) {
-        int h = hc->link[a];
-        for (int x = 0; x < 3; ++x) hc->zp_rel[3 * a + x] = hc->zp[3 * a + x] - (h > 0 ? hc->p0[3 * (h - 1) + x] : 0.0);
+    auto put = [](std::vector<double>& v, long long k, V3 x) {
+        v[3 * k] = x.x;
+        v[3 * k + 1] = x.y;
+        v[3 * k + 2] = x.z;
+    };
+    for (int i = 0; i < m; ++i) {
+        put(hc->u0, 2 * i, unit(loc[iCA(i)]));
+        put(hc->u0, 2 * i + 1, unit(loc[iC(i)] - loc[iCA(i)]));
+        put(hc->step0, 2 * i, i == 0 ? V3{0, 0, 0} : nstep[i - 1] - loc[iCA(i - 1)]);  // CA_{i-1} -> N_i
+        put(hc->step0, 2 * i + 1, loc[iCA(i)]);                                          // N_i -> CA_i
+        if (i == 0) {
+            put(hc->zp_rel, iN(0), loc[iN(0)]);
+            put(hc->zp_rel, iH(0), loc[iH(0)]);
+        }
+        put(hc->zp_rel, iCA(i), loc[iCA(i)]);
+        for (int t = 0; t < nside[i]; ++t) put(hc->zp_rel, iS(i, t), loc[iS(i, t)]);
+        put(hc->zp_rel, iC(i), loc[iC(i)] - loc[iCA(i)]);
+        put(hc->zp_rel, iO(i), loc[iO(i)] - loc[iCA(i)]);
+        if (i + 1 < m) {
+            put(hc->zp_rel, iN(i + 1), nstep[i] - loc[iCA(i)]);
+            put(hc->zp_rel, iH(i + 1), nstep[i] + loc[iH(i + 1)] - loc[iCA(i)]);
+        }
     }
     // bond-class masks over the window (lo, lo + d), d = 1..63; every pair within three bonds
     // must fall inside the window (a pair with a residue gap of two or more is never that close)

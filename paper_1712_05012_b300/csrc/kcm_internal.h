@@ -34,9 +34,9 @@ struct HostChain {
     std::vector<int> kind;           // 0 N, 1 H, 2 CA, 3 C, 4 O, 5 side
     std::vector<double> q, eps, R;   // per atom (R = sigma / 2)
     std::vector<int> cls;            // solvation class
-    std::vector<double> u0, p0;      // ZP joint axis direction and point [l*3]
-    std::vector<double> step0;       // p0_j - p0_{j-1} (p0_{-1} = origin): local frame steps [l*3]
-    std::vector<double> zp_rel;      // ZP centre minus its link's frame origin [n*3]
+    std::vector<double> u0;          // ZP joint axis directions [l*3]
+    std::vector<double> step0;       // frame step: axis point of joint j minus that of joint j-1 [l*3]
+    std::vector<double> zp_rel;      // ZP offset of each atom from its link frame origin [n*3]
     std::vector<uint64_t> ex_mask, m14_mask;  // bond-class masks [n]
 };
 
