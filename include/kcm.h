@@ -227,6 +227,37 @@ int kcm_step_timed(kcm_handle h, float* stage_ms, int32_t n_stages, float* total
 /* The cudaStream_t the handle works on. */
 void* kcm_stream(kcm_handle h);
 
+/* Joint torques from given atom forces without allocating device memory.
+ *
+ * The paper has no counterpart: this exists for callers that cannot allocate device memory when
+ * they need torques, such as a serving process that reserved all GPU memory up front for its own
+ * pool allocator (a cudaMalloc there fails or fragments the pool), or a latency-critical host
+ * loop that must not wait on the driver's allocator. The computation is the one kcm_torques runs
+ * (link wrenches about the origin, suffix sums over links, tau_k = u_k . T^agg_k +
+ * (p_k x u_k) . F^agg_k), on data the caller provides.
+ *
+ * Arguments (all device pointers; nothing is copied or allocated):
+ *   n_links      number of links L = l + 1 (the base link 0 plus one per joint), 2..KCM_NOALLOC_MAX_LINKS
+ *   link_start   int32[L+1]: the atoms of link h are link_start[h] .. link_start[h+1]-1
+ *   xyz, F       double[n*3]: atom centres and forces, n = link_start[L]
+ *   axis, point  double[l*3]: unit axis u_k and a point p_k on it for joint k (0-based), joint k
+ *                moving links k+1..l
+ *   tau          double[l]: output
+ *   cuda_stream  cudaStream_t the kernels are launched on (NULL: the legacy default stream)
+ * The call only enqueues work; synchronise the stream before reading tau. Returns KCM_E_INVAL for
+ * sizes beyond the limit or NULL pointers (nothing is launched), KCM_E_NODEVICE / KCM_E_CUDA when
+ * the scratch cannot be located or a launch fails.
+ *
+ * Scratch: a fixed array of about 2 MB that is part of the library image; every GPU that loads the
+ * library holds it until the process exits, which is what limits L. The first call on a device,
+ * with that device current, looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. All calls on a device share the array and each call
+ * writes every scratch word it reads, so nothing carries over from an earlier call; calls that
+ * overlap on the GPU (different streams, or different host threads) race on it. */
+#define KCM_NOALLOC_MAX_LINKS 32768
+int kcm_torques_noalloc(int32_t n_links, const int32_t* link_start, const double* xyz, const double* F,
+                        const double* axis, const double* point, double* tau, void* cuda_stream);
+
 /* Host-only helpers (no device needed). */
 
 /* The unit-sphere sample set Q[N*3] of Sec. 3.4: K = round(sqrt(pi N / 4)) latitude rings at polar

@@ -70,8 +70,9 @@ EXPORTS = [
     "kcm_get_theta", "kcm_set_theta_dev", "kcm_get_theta_dev", "kcm_positions", "kcm_forces", "kcm_force_terms",
     "kcm_torques", "kcm_torques_dev", "kcm_energy", "kcm_sasa_counts", "kcm_step", "kcm_step_async",
     "kcm_step_status", "kcm_get_stats", "kcm_stream", "kcm_sample_points", "kcm_build_zp", "kcm_pair_class",
-    "kcm_topology_natoms", "kcm_strerror", "kcm_last_error", "kcm_step_timed",
+    "kcm_topology_natoms", "kcm_strerror", "kcm_last_error", "kcm_step_timed", "kcm_torques_noalloc",
 ]
+NOALLOC_MAX_LINKS = 32768
 NUM_STAGES = 7
 STAGES = ("kinematics", "binning", "pairs", "solvation", "torques", "energy", "step")
 
@@ -115,6 +116,8 @@ def load():
             "kcm_pair_class": (C.c_int, [C.POINTER(Topology), _ip, _ip, C.c_int64, _ip]),
             "kcm_topology_natoms": (C.c_int64, [C.POINTER(Topology)]),
             "kcm_step_timed": (C.c_int, [h, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_float)]),
+            "kcm_torques_noalloc": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p]),
             "kcm_strerror": (C.c_char_p, [C.c_int]),
             "kcm_last_error": (C.c_char_p, [h]),
         }
@@ -204,6 +207,16 @@ def pair_class(res_type, table, a, b, geometry=None):
     out = np.zeros(len(a), dtype=np.int32)
     _check(load().kcm_pair_class(t.ptr(), _iptr(a), _iptr(b), len(a), _iptr(out)))
     return out
+
+
+def torques_noalloc(n_links: int, link_start_ptr: int, xyz_ptr: int, F_ptr: int, axis_ptr: int, point_ptr: int,
+                    tau_ptr: int, stream: int = 0) -> None:
+    """kcm_torques_noalloc on device pointers (stream-ordered; synchronise before reading tau)."""
+    rc = load().kcm_torques_noalloc(int(n_links), C.c_void_p(link_start_ptr), C.c_void_p(xyz_ptr), C.c_void_p(F_ptr),
+                                    C.c_void_p(axis_ptr), C.c_void_p(point_ptr), C.c_void_p(tau_ptr),
+                                    C.c_void_p(stream) if stream else None)
+    if rc != KCM_OK:
+        raise KcmError(rc, load().kcm_strerror(rc).decode())
 
 
 class Chain:
