@@ -9,7 +9,11 @@ launched as a CUDA graph. Metric: atom-iterations per second, whole job (all ran
 
 Timing: W warm-up steps, then K steps timed on the device with CUDA events on the library's
 stream (each step is bracketed by events recorded by the library; a 256 MiB buffer is written
-between steps to flush L2), max over ranks. With torchrun (N > 1) every rank runs an independent
+between steps to flush L2), max over ranks. Every step starts from the stored compact start: theta
+is restored by a device-to-device copy before the step's first event. (Consecutive steps with the
+configured clamp, kappa = 1e-3 and |dtheta| <= 0.02 rad on all 2,000 joints, push the unrelaxed
+chain into overlapping atoms within one or two iterations, after which the pair and solvation
+work is no longer that of the workload.) With torchrun (N > 1) every rank runs an independent
 replica of the workload on its own GPU (chains are independent; there is no data-path exchange).
 
 --impl reference times the FP64 CPU oracle on the same workload (rank 0 only), one oracle
@@ -193,17 +197,22 @@ def run_ours(args):
     n = ch.n
     lib_stream = torch.cuda.ExternalStream(ch.stream())
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 256 MiB > 126 MB L2
+    theta0 = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+
+    def prepare(c, stream):
+        # untimed: restore the start conformation and flush L2 on the library's stream
+        c.set_theta_dev(theta0.data_ptr(), c.l)
+        with torch.cuda.stream(stream):
+            flush.add_(1)
 
     clocks = Clocks(local)
     for _ in range(args.warmup):
-        with torch.cuda.stream(lib_stream):
-            flush.add_(1)
+        prepare(ch, lib_stream)
         ch.step_timed()
-    stats0 = ch.stats()
     totals, stages = [], {k: 0.0 for k in kcm.STAGES}
     for _ in range(args.steps):
-        with torch.cuda.stream(lib_stream):
-            flush.add_(1)
+        prepare(ch, lib_stream)
         tot, st = ch.step_timed()
         totals.append(tot)
         for k, v in st.items():
@@ -246,43 +255,43 @@ def run_ours(args):
     fp64_value = None
     if args.fp64_steps > 0 and prec == synth.PRECISION_MIXED:
         with kcm.Chain(seq, table, synth.RunParams(precision=synth.PRECISION_FP64)) as c64:
-            c64.set_theta(theta)
+            s64 = torch.cuda.ExternalStream(c64.stream())
             for _ in range(2):
+                prepare(c64, s64)
                 c64.step_timed()
             tt = []
             for _ in range(args.fp64_steps):
-                with torch.cuda.stream(torch.cuda.ExternalStream(c64.stream())):
-                    flush.add_(1)
+                prepare(c64, s64)
                 tt.append(c64.step_timed()[0])
             fp64_value = n * args.fp64_steps / (sum(tt) / 1e3)
 
-    # end to end through the C ABI with pinned host buffers: theta in, one step, theta out
-    pinned = torch.empty(ch.l, dtype=torch.float64, pin_memory=True)
-    pinned.copy_(torch.from_numpy(theta))
-    hp = pinned.data_ptr()
+    # end to end through the C ABI with pinned host buffers: the start theta in, one step, theta out
+    pin_in = torch.empty(ch.l, dtype=torch.float64, pin_memory=True)
+    pin_in.copy_(torch.from_numpy(theta))
+    pin_out = torch.empty(ch.l, dtype=torch.float64, pin_memory=True)
     L = kcm.load()
     import ctypes
-    dptr = ctypes.cast(hp, ctypes.POINTER(ctypes.c_double))
-    ch.set_theta(theta)
+    din = ctypes.cast(pin_in.data_ptr(), ctypes.POINTER(ctypes.c_double))
+    dout = ctypes.cast(pin_out.data_ptr(), ctypes.POINTER(ctypes.c_double))
     e2e_steps = max(args.steps, 20)
     it_out = (ctypes.c_int32 * 1)()
     dm_out = (ctypes.c_double * 1)()
     for _ in range(3):
-        L.kcm_set_theta(ch.handle, dptr, ch.l)
+        L.kcm_set_theta(ch.handle, din, ch.l)
         L.kcm_step(ch.handle, 1, it_out, dm_out)
-        L.kcm_get_theta(ch.handle, dptr, ch.l)
+        L.kcm_get_theta(ch.handle, dout, ch.l)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        rc = L.kcm_set_theta(ch.handle, dptr, ch.l)
+        rc = L.kcm_set_theta(ch.handle, din, ch.l)
         rc |= L.kcm_step(ch.handle, 1, it_out, dm_out)
-        rc |= L.kcm_get_theta(ch.handle, dptr, ch.l)
+        rc |= L.kcm_get_theta(ch.handle, dout, ch.l)
         if rc:
             raise RuntimeError("kcm call failed during the end-to-end run")
     e2e_wall = time.perf_counter() - t0
     e2e = {"value": ws * n * e2e_steps / e2e_wall, "unit": UNIT, "h2d_bytes_per_step": 8 * ch.l,
            "d2h_bytes_per_step": 8 * ch.l + 120, "steps": e2e_steps,
-           "note": "per step: kcm_set_theta from pinned host memory, kcm_step(1) with its status read, "
-                   "kcm_get_theta into pinned host memory; host wall clock"}
+           "note": "per step: kcm_set_theta of the start theta from pinned host memory, kcm_step(1) with "
+                   "its status read, kcm_get_theta into pinned host memory; host wall clock"}
     ch.close()
 
     cpu = None
@@ -300,7 +309,8 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": "chain1000_compact_cut10", "residues": 1000, "atoms": n, "cutoff": 10.0,
                            "n_sample": 256, "solvation": 1, "precision": args.precision,
-                           "replicas": ws, "l2": "flushed between timed steps (256 MiB write)"},
+                           "replicas": ws, "l2": "flushed between timed steps (256 MiB write)",
+                           "start": "every step from the stored compact start (theta restored untimed)"},
                 "roofline": roof, "stage_ms": ms_stage, "fp64_value": fp64_value,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,

@@ -227,7 +227,9 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     d.nfk_chunks = (d.l + kcm::kFkChunk - 1) / kcm::kFkChunk;
     d.nlink_chunks = (d.L + kcm::kLinkChunk - 1) / kcm::kLinkChunk;
     d.cell_cap = std::max(8 * d.n, 65536);
-    d.pair_blocks = (d.n + kcm::kPairTpb - 1) / kcm::kPairTpb;
+    d.pair_blocks = (d.n + kcm::kPairWarps - 1) / kcm::kPairWarps;
+    d.bbox_blocks = std::max(1, std::min((d.n + 255) / 256, 2 * 148));
+    d.scan_blocks = (d.cell_cap + kcm::kScanCells - 1) / kcm::kScanCells;
     d.sasa_blocks = (d.n + kcm::kSasaWarps - 1) / kcm::kSasaWarps;
     d.rcut2 = prm->cutoff * prm->cutoff;
     double rv = prm->vdw_cutoff > 0.0 ? prm->vdw_cutoff : prm->cutoff;
@@ -249,7 +251,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = dalloc(h, &d.chunkP, 12 * (size_t)d.nfk_chunks)) || (rc = dalloc(h, &d.chunkE, 12 * (size_t)d.nfk_chunks)) ||
         (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||
         (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.cell_count, d.cell_cap)) ||
-        (rc = dalloc(h, &d.cell_start, d.cell_cap + 1)) || (rc = dalloc(h, &d.cell_cursor, d.cell_cap)) ||
+        (rc = dalloc(h, &d.cell_start, d.cell_cap + 1)) || (rc = dalloc(h, &d.rank, nn)) || (rc = dalloc(h, &d.scan_part, d.scan_blocks)) ||
         (rc = dalloc(h, &d.sorted, nn)) || (rc = dalloc(h, &d.slot_cell, nn)) || (rc = dalloc(h, &d.spos64, nn)) ||
         (rc = dalloc(h, &d.spos32, nn)) || (rc = dalloc(h, &d.sprm32, nn)) || (rc = dalloc(h, &d.sprm64, nn)) ||
         (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||

@@ -19,6 +19,7 @@ __host__ __device__ inline dbl4 make_dbl4(double x, double y, double z, double w
 struct GridInfo {
     double ox, oy, oz;  // grid origin (bounding-box minimum)
     double s;           // cell edge, a multiple of 2^-10 A so that it is exact in float
+    float sf, inv_sf;   // the edge in float and its reciprocal
     int nx, ny, nz;
     int ncells;
 };
@@ -33,6 +34,7 @@ struct Status {
     unsigned long long max_dtheta;  // bit pattern of a non-negative double (atomicMax)
     unsigned long long max_abs_tau;
     unsigned int ticket;  // last-block detection in the step kernel
+    unsigned int ticket_bbox;  // last-block detection in the bounding-box kernel
     int iters;            // iterations taken since the last reset
     int done;             // converged or failed: the remaining iterations are no-ops
     int error;            // kErr* bits
@@ -50,7 +52,12 @@ constexpr int kFkChunk = 8;     // joints per thread in the transform scan
 constexpr int kFkTpb = 8;       // threads per block of the FP64 chunk kernels (spreads FP64 work over SMs)
 constexpr int kLinkChunk = 8;   // links per thread in the wrench / suffix-sum kernels
 constexpr int kScanThreads = 64;
-constexpr int kPairTpb = 128;
+constexpr int kPairWarps = 4;         // home atoms (warps) per block of the pair kernel
+constexpr int kScanCells = 2048;      // cells per block of the cell-count scan
+constexpr int kScanThreadsBig = 256;
+constexpr int kPairFx = 24;           // fixed-point fraction bits of mixed-mode pair forces and energies
+constexpr double kPairFxInv = 1.0 / 16777216.0;
+constexpr float kPairFxMax = 1.0e10f;  // |pair term| limit of the fixed-point sums (2^63 / 2^24 = 5.5e11)
 constexpr int kSasaWarps = 4;
 constexpr int kApplyTpb = 64;
 
@@ -58,13 +65,12 @@ struct DevChain {
     int m = 0, n = 0, l = 0, L = 0, N = 0;
     int nfk_chunks = 0, nlink_chunks = 0;
     int cell_cap = 0;
-    int pair_blocks = 0, sasa_blocks = 0;
+    int pair_blocks = 0, sasa_blocks = 0, bbox_blocks = 0, scan_blocks = 0;
     kcm_params prm{};
     // derived constants
     double rcut2 = 0, rvdw2 = 0;  // squared pair cutoffs
     double rmax = 0;              // largest interaction range (pair cutoffs, solvation neighbour range)
     double roff_max = 0;          // largest offset-sphere radius
-    float guard_pair = 0, guard_sasa = 0;
 
     // static data
     double* r0 = nullptr;          // ZP centres relative to their link frame origin [n*3]
@@ -95,7 +101,8 @@ struct DevChain {
     int* key = nullptr;            // cell of each atom [n]
     int* cell_count = nullptr;     // [cell_cap]
     int* cell_start = nullptr;     // [cell_cap+1]
-    int* cell_cursor = nullptr;    // [cell_cap]
+    int* rank = nullptr;           // rank of each atom within its cell [n]
+    int* scan_part = nullptr;      // block sums of the cell scan [scan_blocks]
     int* sorted = nullptr;         // slot -> atom [n]
     int* slot_cell = nullptr;      // slot -> cell [n]
     dbl4* spos64 = nullptr;     // sorted centres + charge [n]

@@ -88,6 +88,11 @@ __device__ __forceinline__ int warp_max(int v) {
     return v;
 }
 
+// FP32 pair term to int64 fixed point with kPairFx fractional bits (round to nearest, symmetric in
+// sign, so the terms of (i, j) and (j, i) stay exact negatives); |v| < kPairFxMax keeps a sum of
+// tens of terms inside int64
+__device__ __forceinline__ long long to_fixed(float v) { return __float2ll_rn(v * 16777216.0f); }
+
 // The FP64 overlap test of Algorithm 1: || (r_a + Roff_a q_k) - r_b - dr e_s ||^2 <= Roff_b^2,
 // written with explicit roundings so that the FP64 kernel and the FP32 guard-band recheck take
 // identical decisions.
@@ -182,56 +187,67 @@ __global__ void k_fk_atoms(const DevChain d) {
 }
 
 // ================================================================ A2: binning
+// Bounding box as order-preserving integer keys (no FP64 min/max); the last block to finish
+// derives the grid, so no separate launch is needed.
 __global__ void k_bbox(const DevChain d) {
-    __shared__ double smin[3][8], smax[3][8];
-    if (d.status->done) return;
-    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    __shared__ unsigned long long smin[3][8], smax[3][8];
+    __shared__ bool last;
+    Status* st = d.status;
+    if (st->done) return;
+    unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0ULL, 0ULL, 0ULL};
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < d.n; a += gridDim.x * blockDim.x) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            double v = d.r[3 * a + i];
-            mn[i] = fmin(mn[i], v);
-            mx[i] = fmax(mx[i], v);
+            unsigned long long key = dkey(d.r[3 * a + i]);
+            mn[i] = min(mn[i], key);
+            mx[i] = max(mx[i], key);
         }
     }
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         for (int o = 16; o > 0; o >>= 1) {
-            mn[i] = fmin(mn[i], __shfl_down_sync(0xffffffffu, mn[i], o));
-            mx[i] = fmax(mx[i], __shfl_down_sync(0xffffffffu, mx[i], o));
+            mn[i] = min(mn[i], __shfl_down_sync(0xffffffffu, mn[i], o));
+            mx[i] = max(mx[i], __shfl_down_sync(0xffffffffu, mx[i], o));
         }
         if (lane == 0) { smin[i][w] = mn[i]; smax[i][w] = mx[i]; }
     }
     __syncthreads();
     if (threadIdx.x < 3) {
         int i = threadIdx.x;
-        double a = INFINITY, b = -INFINITY;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a = fmin(a, smin[i][k]); b = fmax(b, smax[i][k]); }
-        atomicMin(&d.status->bbox[i], dkey(a));
-        atomicMax(&d.status->bbox[3 + i], dkey(b));
+        unsigned long long a = ~0ULL, b = 0ULL;
+        for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) { a = min(a, smin[i][k2]); b = max(b, smax[i][k2]); }
+        atomicMin(&st->bbox[i], a);
+        atomicMax(&st->bbox[3 + i], b);
     }
-}
-
-// grid from the bounding box; resets the box and the per-evaluation counters for the next pass
-__global__ void k_grid_setup(const DevChain d) {
-    Status* st = d.status;
-    if (st->done) return;
-    double mn[3], mx[3];
-    for (int i = 0; i < 3; ++i) { mn[i] = dkey_inv(st->bbox[i]); mx[i] = dkey_inv(st->bbox[3 + i]); }
-    double s = fmax(d.rmax * (1.0 + 1e-12) + 1e-9, d.prm.cell_size);
-    s = ceil(s * 1024.0) / 1024.0;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->ticket_bbox, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    // grid: cube cells of edge s >= every interaction range (plus a margin that absorbs FP32 cell
+    // assignment), s a multiple of 2^-10 A so that it is exact in float; coarsened when the
+    // bounding box would need more cells than the arrays hold
+    double lo[3], hi[3];
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = dkey_inv(atomicAdd(&st->bbox[i], 0ULL));
+        hi[i] = dkey_inv(atomicAdd(&st->bbox[3 + i], 0ULL));
+    }
     GridInfo g;
-    bool finite = isfinite(mx[0] - mn[0]) && isfinite(mx[1] - mn[1]) && isfinite(mx[2] - mn[2]);
+    bool finite = isfinite(hi[0] - lo[0]) && isfinite(hi[1] - lo[1]) && isfinite(hi[2] - lo[2]);
     if (!finite) {
         atomicOr(&st->error, kErrNonfinite);
         st->done = 1;
-        for (int i = 0; i < 3; ++i) { mn[i] = 0.0; mx[i] = 0.0; }
+        for (int i = 0; i < 3; ++i) { lo[i] = 0.0; hi[i] = 0.0; }
     }
+    double ext = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
+    double s = fmax(d.rmax * (1.0 + 1e-5) + 0.01 + 1e-6 * ext, d.prm.cell_size);
+    s = ceil(s * 1024.0) / 1024.0;
     for (;;) {
-        long long nx = (long long)floor((mx[0] - mn[0]) / s) + 1;
-        long long ny = (long long)floor((mx[1] - mn[1]) / s) + 1;
-        long long nz = (long long)floor((mx[2] - mn[2]) / s) + 1;
+        long long nx = (long long)floor((hi[0] - lo[0]) / s) + 1;
+        long long ny = (long long)floor((hi[1] - lo[1]) / s) + 1;
+        long long nz = (long long)floor((hi[2] - lo[2]) / s) + 1;
         if (nx * ny * nz <= (long long)d.cell_cap) {
             g.nx = (int)nx; g.ny = (int)ny; g.nz = (int)nz;
             g.ncells = (int)(nx * ny * nz);
@@ -239,10 +255,13 @@ __global__ void k_grid_setup(const DevChain d) {
         }
         s = ceil(s * 1.25 * 1024.0) / 1024.0;
     }
-    g.ox = mn[0]; g.oy = mn[1]; g.oz = mn[2];
+    g.ox = lo[0]; g.oy = lo[1]; g.oz = lo[2];
     g.s = s;
+    g.sf = (float)s;
+    g.inv_sf = 1.0f / (float)s;
     *d.grid = g;
     for (int i = 0; i < 3; ++i) { st->bbox[i] = ~0ULL; st->bbox[3 + i] = 0ULL; }
+    st->ticket_bbox = 0u;
     st->pairs = 0;
     st->nbr_total = 0;
     st->guard = 0;
@@ -250,206 +269,241 @@ __global__ void k_grid_setup(const DevChain d) {
     st->max_nbr = 0;
 }
 
-__device__ __forceinline__ int cell_of(const GridInfo& g, double x, double y, double z) {
-    int cx = min(max((int)floor((x - g.ox) / g.s), 0), g.nx - 1);
-    int cy = min(max((int)floor((y - g.oy) / g.s), 0), g.ny - 1);
-    int cz = min(max((int)floor((z - g.oz) / g.s), 0), g.nz - 1);
-    return (cz * g.ny + cy) * g.nx + cx;
-}
-
-// cell counts with one atomic per group of lanes that share a cell (consecutive atoms of a chain
-// mostly share one)
+// Cell of each atom (FP32 from the FP64 offset to the grid origin; the cell-edge margin makes
+// the one-cell neighbourhood exact) and its rank within the cell, from one atomic per group of
+// lanes that share a cell. Ranks depend on timing; nothing downstream depends on the order.
 __global__ void k_bin_count(const DevChain d) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= d.n || d.status->done) return;
     const GridInfo g = *d.grid;
-    int key = cell_of(g, d.r[3 * a], d.r[3 * a + 1], d.r[3 * a + 2]);
+    int cx = min(max((int)floorf((float)(d.r[3 * a] - g.ox) * g.inv_sf), 0), g.nx - 1);
+    int cy = min(max((int)floorf((float)(d.r[3 * a + 1] - g.oy) * g.inv_sf), 0), g.ny - 1);
+    int cz = min(max((int)floorf((float)(d.r[3 * a + 2] - g.oz) * g.inv_sf), 0), g.nz - 1);
+    int key = (cz * g.ny + cy) * g.nx + cx;
     d.key[a] = key;
     unsigned peers = __match_any_sync(__activemask(), key);
     int lane = threadIdx.x & 31;
-    if (lane == __ffs(peers) - 1) atomicAdd(&d.cell_count[key], __popc(peers));
+    int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&d.cell_count[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    d.rank[a] = base + __popc(peers & ((1u << lane) - 1u));
 }
 
-// exclusive scan of the cell counts (one block); zeroes the counts for the next pass
-__global__ void k_bin_scan(const DevChain d) {
-    __shared__ int wsum[32];
+// exclusive scan of the cell counts in two passes over blocks of kScanCells cells: block sums,
+// then each block adds the sums of the blocks before it and scans its own cells (and zeroes the
+// counts for the next iteration)
+__global__ void k_scan_sums(const DevChain d) {
+    __shared__ int ws[32];
     if (d.status->done) return;
     int nc = d.grid->ncells;
-    int t = threadIdx.x, T = blockDim.x;
-    int per = (nc + T - 1) / T;
-    int c0 = min(nc, t * per), c1 = min(nc, c0 + per);
+    int c0 = blockIdx.x * kScanCells;
+    if (c0 >= nc) return;
+    int s = 0;
+    for (int c = c0 + threadIdx.x; c < min(nc, c0 + kScanCells); c += blockDim.x) s += d.cell_count[c];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) t += ws[k2];
+        d.scan_part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_scan_cells(const DevChain d) {
+    __shared__ int ws[32];
+    __shared__ int base_s;
+    if (d.status->done) return;
+    int nc = d.grid->ncells;
+    int c0 = blockIdx.x * kScanCells;
+    if (c0 >= nc) return;
+    // sum of the previous blocks' counts
+    int s = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) s += d.scan_part[b];
+    s = warp_sum(s);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) ws[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k2 = 0; k2 < nw; ++k2) t += ws[k2];
+        base_s = t;
+    }
+    __syncthreads();
+    int base = base_s;
+    // each thread owns kScanCells / blockDim.x consecutive cells
+    const int per = kScanCells / kScanThreadsBig;
+    int cb = c0 + threadIdx.x * per;
+    int cnt[kScanCells / kScanThreadsBig];
     int local = 0;
-    for (int c = c0; c < c1; ++c) local += d.cell_count[c];
-    int lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        int c = cb + q;
+        cnt[q] = c < nc ? d.cell_count[c] : 0;
+        local += cnt[q];
+    }
     int v = local;
     for (int o = 1; o < 32; o <<= 1) {
         int y = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += y;
     }
-    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (lane == 31) ws[w] = v;
     __syncthreads();
     if (w == 0) {
-        int x = (lane < (T >> 5)) ? wsum[lane] : 0;
+        int x = lane < nw ? ws[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        wsum[lane] = x;  // inclusive over warps
+        ws[lane] = x;
     }
     __syncthreads();
-    int base = v - local + (w > 0 ? wsum[w - 1] : 0);
-    for (int c = c0; c < c1; ++c) {
-        int cnt = d.cell_count[c];
-        d.cell_start[c] = base;
-        d.cell_cursor[c] = base;
-        d.cell_count[c] = 0;
-        base += cnt;
+    int run = base + v - local + (w > 0 ? ws[w - 1] : 0);
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        int c = cb + q;
+        if (c < nc) {
+            d.cell_start[c] = run;
+            d.cell_count[c] = 0;
+            run += cnt[q];
+            if (c == nc - 1) d.cell_start[nc] = run;
+        }
     }
-    if (t == T - 1) d.cell_start[nc] = base;
 }
 
-__global__ void k_bin_scatter(const DevChain d) {
+// sorted slot = start of the cell + rank; sorted copies: FP64 centres, or FP32 offsets from the
+// cell corner (|offset| <= s plus the assignment margin, rounding below s 2^-24)
+template <bool MIXED>
+__global__ void k_bin_place(const DevChain d) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= d.n || d.status->done) return;
-    int key = d.key[a];
-    unsigned peers = __match_any_sync(__activemask(), key);
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&d.cell_cursor[key], __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    int rank = __popc(peers & ((1u << lane) - 1u));
-    d.sorted[base + rank] = a;
-}
-
-// order each cell by atom index (the scatter order depends on timing)
-__global__ void k_bin_sortcells(const DevChain d) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d.status->done || c >= d.grid->ncells) return;
-    int b0 = d.cell_start[c], b1 = d.cell_start[c + 1];
-    for (int i = b0 + 1; i < b1; ++i) {
-        int v = d.sorted[i];
-        int j = i - 1;
-        while (j >= b0 && d.sorted[j] > v) {
-            d.sorted[j + 1] = d.sorted[j];
-            --j;
-        }
-        d.sorted[j + 1] = v;
-    }
-}
-
-// sorted copies: FP64 centres, or FP32 offsets from the cell corner (|offset| < s, so the FP32
-// rounding error is below s * 2^-24)
-template <bool MIXED>
-__global__ void k_bin_gather(const DevChain d) {
-    int sl = blockIdx.x * blockDim.x + threadIdx.x;
-    if (sl >= d.n || d.status->done) return;
     const GridInfo g = *d.grid;
-    int a = d.sorted[sl];
     int key = d.key[a];
+    int sl = d.cell_start[key] + d.rank[a];
+    d.sorted[sl] = a;
     d.slot_cell[sl] = key;
     double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
-    dbl4 pa = d.aprm64[a];
     if (MIXED) {
         int cx = key % g.nx, cy = (key / g.nx) % g.ny, cz = key / (g.nx * g.ny);
         float ox = (float)(x - (g.ox + cx * g.s));
         float oy = (float)(y - (g.oy + cy * g.s));
         float oz = (float)(z - (g.oz + cz * g.s));
-        d.spos32[sl] = make_float4(ox, oy, oz, (float)pa.x);
-        d.sprm32[sl] = d.aprm32[a];
+        float4 p = d.aprm32[a];
+        d.spos32[sl] = make_float4(ox, oy, oz, p.x);
+        d.sprm32[sl] = p;
     } else {
-        d.spos64[sl] = make_dbl4(x, y, z, pa.x);
-        d.sprm64[sl] = pa;
+        dbl4 p = d.aprm64[a];
+        d.spos64[sl] = make_dbl4(x, y, z, p.x);
+        d.sprm64[sl] = p;
     }
 }
 
 // ================================================================ A3-A5: pair forces + lists
+// One warp per home atom i (sorted slot). Lane t < 27 reads neighbour cell t of the home cell;
+// the candidates of the 27 cells are then taken in strides of 32 over their concatenation, so
+// every lane has the same trip count. Each ordered pair (i, j) is evaluated by i's warp; the pair
+// term is computed symmetrically, so the term j's warp gets is exactly its negative. Mixed mode
+// sums the FP32 terms as int64 fixed point (2^-24): the sum is exact and order-free, and the
+// forces of a pair cancel exactly, so no net force or moment builds up over the chain. Terms of
+// 1e10 kcal/mol/A or more (near-overlapping atoms) go to a float side sum instead.
 template <bool MIXED>
-__global__ void __launch_bounds__(kPairTpb) k_pair(const DevChain d) {
+__global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     typedef typename std::conditional<MIXED, float, double>::type R;
-    __shared__ double sE[2][kPairTpb / 32];
-    __shared__ unsigned long long sC[3][kPairTpb / 32];
-    __shared__ int sM[kPairTpb / 32];
-    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = sl < d.n && !d.status->done;
+    __shared__ int s_beg[kPairWarps][32];
+    __shared__ int s_off[kPairWarps][32];
+    __shared__ double sE[2][kPairWarps];
+    __shared__ unsigned long long sC[3][kPairWarps];
+    __shared__ int sM[kPairWarps];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sl = blockIdx.x * kPairWarps + w;
     double Eel = 0.0, Evdw = 0.0;
     unsigned long long npairs = 0, nguard = 0;
     int ncount = 0;
-    if (active) {
+    if (sl < d.n && !d.status->done) {
         const GridInfo g = *d.grid;
         const int a = d.sorted[sl];
         const int cell = d.slot_cell[sl];
         const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
+        int beg = 0, len = 0;
+        if (lane < 27) {
+            int ncx = cx + lane % 3 - 1, ncy = cy + (lane / 3) % 3 - 1, ncz = cz + lane / 9 - 1;
+            if (ncx >= 0 && ncx < g.nx && ncy >= 0 && ncy < g.ny && ncz >= 0 && ncz < g.nz) {
+                int nc = (ncz * g.ny + ncy) * g.nx + ncx;
+                beg = d.cell_start[nc];
+                len = d.cell_start[nc + 1] - beg;
+            }
+        }
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        s_beg[w][lane] = beg;
+        s_off[w][lane] = incl - len;
+        __syncwarp();
         const R K = (R)d.prm.coulomb_k;
         const R w14e = (R)d.prm.w14_elec, w14v = (R)d.prm.w14_vdw;
         const R rc2 = (R)d.rcut2, rv2 = (R)d.rvdw2;
-        const R rall2 = (R)(d.rmax * d.rmax) + (R)d.guard_pair;
-        const R gp = (R)d.guard_pair;
+        const R rall2 = (R)(d.rmax * d.rmax) + (R)(MIXED ? 0.01 : 0.0);
+        const R gp = (R)(1e-3 + 2e-4 * g.s);
         const R dr = (R)d.prm.delta_r;
         const R pad = MIXED ? (R)0.01 : (R)0.0;
         const bool solv = d.prm.solvation != 0;
-        const R sf = (R)g.s;
+        const R sf = (R)g.sf;
         R px, py, pz, qi, sei, Ri, Roi;
-        if (MIXED) {
+        if constexpr (MIXED) {
             float4 p = d.spos32[sl], q = d.sprm32[sl];
-            px = p.x; py = p.y; pz = p.z; qi = p.w;
-            sei = q.y; Ri = q.z; Roi = q.w;
+            px = p.x; py = p.y; pz = p.z; qi = p.w; sei = q.y; Ri = q.z; Roi = q.w;
         } else {
             dbl4 p = d.spos64[sl], q = d.sprm64[sl];
-            px = p.x; py = p.y; pz = p.z; qi = p.w;
-            sei = q.y; Ri = q.z; Roi = q.w;
+            px = p.x; py = p.y; pz = p.z; qi = p.w; sei = q.y; Ri = q.z; Roi = q.w;
         }
         const unsigned long long exa = d.exm[a], m14a = d.m14m[a];
-        R fx = 0, fy = 0, fz = 0;
-        R eel = 0, evdw = 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-            int ncz = cz + dz;
-            if (ncz < 0 || ncz >= g.nz) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                int ncy = cy + dy;
-                if (ncy < 0 || ncy >= g.ny) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int ncx = cx + dx;
-                    if (ncx < 0 || ncx >= g.nx) continue;
-                    int nc = (ncz * g.ny + ncy) * g.nx + ncx;
-                    int t0 = d.cell_start[nc], t1 = d.cell_start[nc + 1];
-                    // r_i - r_j = (o_i - o_j) - (c_j - c_i) s for cell-relative offsets
-                    const R shx = MIXED ? (R)dx * sf : (R)0, shy = MIXED ? (R)dy * sf : (R)0, shz = MIXED ? (R)dz * sf : (R)0;
-                    for (int t = t0; t < t1; ++t) {
-                        if (t == sl) continue;
-                        R qj, sej, Rj, Roj, ddx, ddy, ddz;
-                        if (MIXED) {
-                            float4 p = d.spos32[t];
-                            ddx = (px - p.x) - shx; ddy = (py - p.y) - shy; ddz = (pz - p.z) - shz;
-                            qj = p.w;
-                        } else {
-                            dbl4 p = d.spos64[t];
-                            ddx = __dsub_rn(px, p.x); ddy = __dsub_rn(py, p.y); ddz = __dsub_rn(pz, p.z);
-                            qj = p.w;
-                        }
-                        R d2;
-                        if constexpr (MIXED) d2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        else d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-                        if (d2 > rall2) continue;
-                        const int b = d.sorted[t];
-                        if (MIXED) {
-                            float4 q = d.sprm32[t];
+        long long ffx = 0, ffy = 0, ffz = 0, fel = 0, fvd = 0;  // mixed: fixed point
+        float ovx = 0, ovy = 0, ovz = 0, ove = 0, ovv = 0;      // mixed: terms beyond the fixed-point range
+        double dfx = 0, dfy = 0, dfz = 0;                        // FP64 mode
+        int t = 0;
+        const unsigned lt = (1u << lane) - 1u;
+        for (int base = 0; base < total; base += 32) {
+            const int k2 = base + lane;
+            bool isn = false;
+            int b = -1;
+            R ddx = 0, ddy = 0, ddz = 0, Roj = 0;
+            if (k2 < total) {
+                while (t < 26 && s_off[w][t + 1] <= k2) ++t;
+                const int ts = s_beg[w][t] + (k2 - s_off[w][t]);
+                if (ts != sl) {
+                    R qj, sej, Rj;
+                    if constexpr (MIXED) {
+                        float4 p = d.spos32[ts];
+                        const R shx = (R)(t % 3 - 1) * sf, shy = (R)((t / 3) % 3 - 1) * sf, shz = (R)(t / 9 - 1) * sf;
+                        // r_i - r_j = (o_i - o_j) - (c_j - c_i) s
+                        ddx = (px - p.x) - shx; ddy = (py - p.y) - shy; ddz = (pz - p.z) - shz;
+                        qj = p.w;
+                    } else {
+                        dbl4 p = d.spos64[ts];
+                        ddx = __dsub_rn(px, p.x); ddy = __dsub_rn(py, p.y); ddz = __dsub_rn(pz, p.z);
+                        qj = p.w;
+                    }
+                    R d2;
+                    if constexpr (MIXED) d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    else d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+                    if (d2 <= rall2) {
+                        b = d.sorted[ts];
+                        if constexpr (MIXED) {
+                            float4 q = d.sprm32[ts];
                             sej = q.y; Rj = q.z; Roj = q.w;
                         } else {
-                            dbl4 q = d.sprm64[t];
+                            dbl4 q = d.sprm64[ts];
                             sej = q.y; Rj = q.z; Roj = q.w;
                         }
                         if (solv) {  // solvation neighbour A'_i: d_ij <= Roff_i + Roff_j + dr
                             R lim = Roi + Roj + dr + pad;
-                            if (d2 <= lim * lim) {
-                                if (ncount < kMaxNbr) {
-                                    d.nbr[(size_t)a * kMaxNbr + ncount] = b;
-                                    if (MIXED) d.nbr_off[(size_t)a * kMaxNbr + ncount] = make_float4(-(float)ddx, -(float)ddy, -(float)ddz, (float)(Roj * Roj));
-                                }
-                                ++ncount;
-                            }
+                            isn = d2 <= lim * lim;
                         }
-                        // bond class from the lower index's masks (Sec. 3.3)
                         int lo = min(a, b), off = max(a, b) - lo;
                         bool excl = false, is14 = false;
                         if (off <= kMaskWindow) {
@@ -458,10 +512,9 @@ __global__ void __launch_bounds__(kPairTpb) k_pair(const DevChain d) {
                             excl = (em >> off) & 1ULL;
                             is14 = (mm >> off) & 1ULL;
                         }
-                        if (excl) continue;
-                        bool inE = d2 <= rc2, inV = d2 <= rv2;
-                        if (MIXED && (fabs(d2 - rc2) <= gp || fabs(d2 - rv2) <= gp)) {
-                            // guard band: decide the cutoff in FP64 as the FP64 path does
+                        bool inE = !excl && d2 <= rc2, inV = !excl && d2 <= rv2;
+                        if (MIXED && !excl && (fabs(d2 - rc2) <= gp || fabs(d2 - rv2) <= gp)) {
+                            // guard band: decide the cutoff in FP64 exactly as the FP64 path does
                             double ex = __dsub_rn(d.r[3 * a], d.r[3 * b]), ey = __dsub_rn(d.r[3 * a + 1], d.r[3 * b + 1]),
                                    ez = __dsub_rn(d.r[3 * a + 2], d.r[3 * b + 2]);
                             double d64 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
@@ -469,54 +522,90 @@ __global__ void __launch_bounds__(kPairTpb) k_pair(const DevChain d) {
                             inV = d64 <= d.rvdw2;
                             ++nguard;
                         }
-                        if (!inE && !inV) continue;
-                        R we = is14 ? w14e : (R)1, wv = is14 ? w14v : (R)1;
-                        R inv2 = (R)1 / d2;
-                        R coef = 0;
-                        const bool count_e = a < b;
-                        if (inE) {
-                            R qq = we * K * qi * qj;
-                            coef += (R)0.5 * qq * inv2 * inv2;
-                            if (count_e) eel += (R)0.25 * qq * inv2;
+                        if (inE || inV) {
+                            // symmetric in (i, j): products of the two atoms' constants are formed first
+                            const R we = is14 ? w14e : (R)1, wv = is14 ? w14v : (R)1;
+                            const R inv2 = (R)1 / d2;
+                            R coef = 0, e_el = 0, e_vd = 0;
+                            if (inE) {
+                                const R qq = (we * K) * (qi * qj);
+                                coef += (R)0.5 * qq * (inv2 * inv2);
+                                e_el = (R)0.25 * qq * inv2;
+                            }
+                            if (inV) {
+                                const R D = Ri + Rj;
+                                const R D2 = D * D;
+                                const R x2 = D2 * inv2;
+                                const R t6 = x2 * x2 * x2;
+                                const R t12 = t6 * t6;
+                                const R eij = wv * (sei * sej);
+                                coef += (R)12 * eij * (t12 - t6) * inv2;
+                                e_vd = eij * (t12 - (R)2 * t6);
+                            }
+                            const bool count_e = a < b;
+                            if (count_e && (we != (R)0 || wv != (R)0)) ++npairs;
+                            if constexpr (MIXED) {
+                                const float fx1 = coef * ddx, fy1 = coef * ddy, fz1 = coef * ddz;
+                                if (fabsf(fx1) < kPairFxMax && fabsf(fy1) < kPairFxMax && fabsf(fz1) < kPairFxMax) {
+                                    ffx += to_fixed(fx1);
+                                    ffy += to_fixed(fy1);
+                                    ffz += to_fixed(fz1);
+                                } else {  // clash-sized (or non-finite) term: plain float sum
+                                    ovx += fx1; ovy += fy1; ovz += fz1;
+                                }
+                                if (count_e) {
+                                    if (fabsf(e_el) < kPairFxMax) fel += to_fixed(e_el); else ove += e_el;
+                                    if (fabsf(e_vd) < kPairFxMax) fvd += to_fixed(e_vd); else ovv += e_vd;
+                                }
+                            } else {
+                                dfx += coef * ddx; dfy += coef * ddy; dfz += coef * ddz;
+                                if (count_e) { Eel += e_el; Evdw += e_vd; }
+                            }
                         }
-                        if (inV) {
-                            R D = Ri + Rj;
-                            R D2 = D * D;
-                            R t6 = D2 * D2 * D2 * inv2 * inv2 * inv2;
-                            R t12 = t6 * t6;
-                            R eij = wv * sei * sej;
-                            coef += (R)12 * eij * (t12 - t6) * inv2;
-                            if (count_e) evdw += eij * (t12 - (R)2 * t6);
-                        }
-                        if (count_e && (we != (R)0 || wv != (R)0)) ++npairs;
-                        fx += coef * ddx; fy += coef * ddy; fz += coef * ddz;
                     }
                 }
             }
+            const unsigned bm = __ballot_sync(0xffffffffu, isn);
+            if (isn) {
+                const int slot = ncount + __popc(bm & lt);
+                if (slot < kMaxNbr) {
+                    d.nbr[(size_t)a * kMaxNbr + slot] = b;
+                    if (MIXED) d.nbr_off[(size_t)a * kMaxNbr + slot] = make_float4(-(float)ddx, -(float)ddy, -(float)ddz, (float)(Roj * Roj));
+                }
+            }
+            ncount += __popc(bm);
         }
-        d.Fpair[3 * a] = (double)fx;
-        d.Fpair[3 * a + 1] = (double)fy;
-        d.Fpair[3 * a + 2] = (double)fz;
-        d.nbr_cnt[a] = ncount;
-        if (ncount > kMaxNbr) atomicOr(&d.status->error, kErrOverflow);
-        Eel = (double)eel;
-        Evdw = (double)evdw;
+        if constexpr (MIXED) {
+            ffx = warp_sum(ffx); ffy = warp_sum(ffy); ffz = warp_sum(ffz);
+            fel = warp_sum(fel); fvd = warp_sum(fvd);
+            ovx = warp_sum(ovx); ovy = warp_sum(ovy); ovz = warp_sum(ovz);
+            ove = warp_sum(ove); ovv = warp_sum(ovv);
+            if (lane == 0) {
+                d.Fpair[3 * a] = (double)ffx * kPairFxInv + (double)ovx;
+                d.Fpair[3 * a + 1] = (double)ffy * kPairFxInv + (double)ovy;
+                d.Fpair[3 * a + 2] = (double)ffz * kPairFxInv + (double)ovz;
+            }
+            Eel = (double)fel * kPairFxInv + (double)ove;
+            Evdw = (double)fvd * kPairFxInv + (double)ovv;
+        } else {
+            dfx = warp_sum(dfx); dfy = warp_sum(dfy); dfz = warp_sum(dfz);
+            Eel = warp_sum(Eel); Evdw = warp_sum(Evdw);
+            if (lane == 0) { d.Fpair[3 * a] = dfx; d.Fpair[3 * a + 1] = dfy; d.Fpair[3 * a + 2] = dfz; }
+        }
+        npairs = warp_sum(npairs);
+        nguard = warp_sum(nguard);
+        if (lane == 0) {
+            d.nbr_cnt[a] = ncount;
+            if (ncount > kMaxNbr) atomicOr(&d.status->error, kErrOverflow);
+        }
     }
-    // block partials (fixed tree: deterministic)
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    Eel = warp_sum(Eel);
-    Evdw = warp_sum(Evdw);
-    npairs = warp_sum(npairs);
-    nguard = warp_sum(nguard);
-    unsigned long long nc64 = warp_sum((unsigned long long)ncount);
-    int mx = warp_max(ncount);
-    if (lane == 0) { sE[0][w] = Eel; sE[1][w] = Evdw; sC[0][w] = npairs; sC[1][w] = nguard; sC[2][w] = nc64; sM[w] = mx; }
+    if (lane == 0) { sE[0][w] = Eel; sE[1][w] = Evdw; sC[0][w] = npairs; sC[1][w] = nguard; sC[2][w] = (unsigned long long)ncount; sM[w] = ncount; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double e0 = 0, e1 = 0;
         unsigned long long c0 = 0, c1 = 0, c2 = 0;
         int m = 0;
-        for (int k = 0; k < kPairTpb / 32; ++k) { e0 += sE[0][k]; e1 += sE[1][k]; c0 += sC[0][k]; c1 += sC[1][k]; c2 += sC[2][k]; m = max(m, sM[k]); }
+        for (int k2 = 0; k2 < kPairWarps; ++k2) { e0 += sE[0][k2]; e1 += sE[1][k2]; c0 += sC[0][k2]; c1 += sC[1][k2]; c2 += sC[2][k2]; m = max(m, sM[k2]); }
         d.Epair[2 * blockIdx.x] = e0;
         d.Epair[2 * blockIdx.x + 1] = e1;
         if (c0) atomicAdd(&d.status->pairs, c0);
@@ -566,7 +655,9 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
             const float Raf = (float)Roa;
             const double dr = d.prm.delta_r;
             const float drf = (float)dr;
-            const float gs = d.guard_sasa;
+            // guard band of the FP32 overlap test (A^2): a bound of about 5e-5 A^2 at a 10 A cell edge,
+            // from the cell-relative offsets (error < 7 s 2^-24 per component) and the test's own rounding
+            const float gs = (float)(2e-4 + 4e-5 * d.grid->s);
             int ncov = 0, nguard = 0;
             unsigned long long ntest = 0;
             for (int k = lane; k < d.N; k += 32) {
@@ -811,6 +902,7 @@ __global__ void k_reset_loop(const DevChain d, int full) {
     st->max_abs_tau = 0ULL;
     st->last_max_dtheta = 0.0;
     if (full) {
+        st->ticket_bbox = 0u;
         for (int i = 0; i < 3; ++i) { st->bbox[i] = ~0ULL; st->bbox[3 + i] = 0ULL; }
         st->pairs = 0; st->nbr_total = 0; st->guard = 0; st->sasa_tests = 0; st->max_nbr = 0;
     }
@@ -839,23 +931,21 @@ void launch_fk(DevChain& d, cudaStream_t s) {
 }
 
 void launch_binning(DevChain& d, cudaStream_t s) {
-    k_bbox<<<std::min(blocks(d.n, 256), 4 * 148), 256, 0, s>>>(d);
-    k_grid_setup<<<1, 1, 0, s>>>(d);
+    k_bbox<<<d.bbox_blocks, 256, 0, s>>>(d);
     k_bin_count<<<blocks(d.n, 256), 256, 0, s>>>(d);
-    k_bin_scan<<<1, 1024, 0, s>>>(d);
-    k_bin_scatter<<<blocks(d.n, 256), 256, 0, s>>>(d);
-    k_bin_sortcells<<<blocks(d.cell_cap, 256), 256, 0, s>>>(d);
+    k_scan_sums<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
+    k_scan_cells<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
     if (d.prm.precision == KCM_MIXED)
-        k_bin_gather<true><<<blocks(d.n, 256), 256, 0, s>>>(d);
+        k_bin_place<true><<<blocks(d.n, 256), 256, 0, s>>>(d);
     else
-        k_bin_gather<false><<<blocks(d.n, 256), 256, 0, s>>>(d);
+        k_bin_place<false><<<blocks(d.n, 256), 256, 0, s>>>(d);
 }
 
 void launch_pairs(DevChain& d, cudaStream_t s) {
     if (d.prm.precision == KCM_MIXED)
-        k_pair<true><<<d.pair_blocks, kPairTpb, 0, s>>>(d);
+        k_pair<true><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
     else
-        k_pair<false><<<d.pair_blocks, kPairTpb, 0, s>>>(d);
+        k_pair<false><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
 }
 
 void launch_forces(DevChain& d, cudaStream_t s) {

@@ -207,6 +207,12 @@ def test_chain8000_cut12_sampled(kcm, table):
     pm = synth.RunParams(cutoff=12.0, precision=synth.PRECISION_MIXED)
     ref = och.evaluate(synth.RunParams(cutoff=12.0), th)
     got = gpu_eval(kcm, seq, table, pm, th)
+    f64 = gpu_eval(kcm, seq, table, synth.RunParams(cutoff=12.0), th)
+    g = och.gamma != 0
+    # FP32 overlap tests are re-decided in FP64 inside the guard band: identical classifications
+    assert np.array_equal(got["covered"], f64["covered"])
+    assert np.array_equal(f64["covered"][g], ref["covered"][g])
+    assert got["stats"]["guard_rechecks"] > 0
     assert np.max(np.abs(got["xyz"] - fk_extended(och, th))) < tol_positions(och.l)
     assert np.max(np.abs(got["xyz"] - ref["xyz"])) < tol_positions(och.l)
     assert rel_inf(got["tau"], ref["tau"]) < TOL_MIXED
