@@ -745,6 +745,152 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
     }
 }
 
+// Mixed-precision Algorithm 1. The test of sample point k of atom i against neighbour j,
+// |Roff_i Q_k - o_j|^2 <= Roff_j^2 with o_j = r_j - r_i, is for a unit Q_k the same as
+// Q_k . o_j >= h_j,  h_j = (Roff_i^2 + |o_j|^2 - Roff_j^2) / (2 Roff_i),
+// and with j displaced by dr e_s it is Q_k . o_j + dr Q_k,s >= h_js, h_js = h_j + (2 dr o_j,s + dr^2)
+// / (2 Roff_i). A displacement can change the state of a point only where the two squared
+// distances straddle Roff_j^2, i.e. within |Q.o - h_j| <= (2 dr Roff_j + 3 dr^2) / (2 Roff_i) of the cap
+// boundary; step 1 records those (point, neighbour) candidates and step 2 re-tests only them. That
+// gives exactly Algorithm 1's exchanges: an exposed point gains coverage only from a candidate, and a
+// critically overlapped point loses it only if its critical neighbour is a candidate. FP32 decisions
+// within the guard band gd of the boundary are re-decided in FP64 by covers64, as in the FP64 kernel.
+constexpr int kMaxCand = 4;
+
+__global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d) {
+    __shared__ float4 s_o[kSasaWarps][kMaxNbr];   // o_j, h_j
+    __shared__ float4 s_h[kSasaWarps][kMaxNbr];   // h_jx, h_jy, h_jz, band_j
+    __shared__ int s_idx[kSasaWarps][kMaxNbr];
+    __shared__ int s_cnt[kSasaWarps][3 * kMaxNbr];
+    __shared__ double s_E[kSasaWarps];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a = blockIdx.x * kSasaWarps + w;
+    double Ea = 0.0;
+    if (a < d.n && !d.status->done) {
+        const double G0a = d.G0[a];
+        if (G0a == 0.0) {
+            if (lane == 0) d.covered[a] = 0;
+        } else {
+            const int cnt = min(d.nbr_cnt[a], kMaxNbr);
+            const double Roa = d.aprm64[a].w;
+            const float Ra = (float)Roa;
+            const float inv2R = 0.5f / Ra;
+            const double dr = d.prm.delta_r;
+            const float drf = (float)dr;
+            const float s_edge = d.grid->sf;
+            const float gd = 1e-4f + 1.2e-5f * s_edge;  // guard band in Q.o units (A)
+            for (int j = lane; j < cnt; j += 32) {
+                const float4 o = d.nbr_off[(size_t)a * kMaxNbr + j];  // r_j - r_i, Roff_j^2
+                const float oo = o.x * o.x + o.y * o.y + o.z * o.z;
+                const float h = (Ra * Ra + oo - o.w) * inv2R;
+                const float dd = drf * drf;
+                const float hx = h + (2.0f * drf * o.x + dd) * inv2R;
+                const float hy = h + (2.0f * drf * o.y + dd) * inv2R;
+                const float hz = h + (2.0f * drf * o.z + dd) * inv2R;
+                const float band = (2.0f * drf * sqrtf(o.w) + 3.0f * dd) * inv2R + gd;
+                s_o[w][j] = make_float4(o.x, o.y, o.z, h);
+                s_h[w][j] = make_float4(hx, hy, hz, band);
+                s_idx[w][j] = d.nbr[(size_t)a * kMaxNbr + j];
+                s_cnt[w][3 * j] = 0; s_cnt[w][3 * j + 1] = 0; s_cnt[w][3 * j + 2] = 0;
+            }
+            __syncwarp();
+            const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
+            int ncov = 0, nguard = 0;
+            unsigned long long ntest = 0;
+            for (int k = lane; k < d.N; k += 32) {
+                const float Qx = d.Q32[3 * k], Qy = d.Q32[3 * k + 1], Qz = d.Q32[3 * k + 2];
+                // FP64 recheck of a decision inside the guard band (identical to the FP64 kernel)
+                auto recheck = [&](int j, int s) -> bool {
+                    ++nguard;
+                    const int b = s_idx[w][j];
+                    const double ro = d.aprm64[b].w;
+                    const double qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
+                    const double qy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
+                    const double qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
+                    return covers64(qx, qy, qz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
+                };
+                // displaced test of neighbour j along s
+                auto covers_s = [&](int j, int s) -> bool {
+                    ++ntest;
+                    const float4 o = s_o[w][j];
+                    const float4 hh = s_h[w][j];
+                    const float dot = Qx * o.x + Qy * o.y + Qz * o.z;
+                    const float m = s == 0 ? dot + drf * Qx - hh.x : (s == 1 ? dot + drf * Qy - hh.y : dot + drf * Qz - hh.z);
+                    if (fabsf(m) > gd) return m >= 0.0f;
+                    return recheck(j, s);
+                };
+                // step 1: C = number of covering neighbours, stopped at 2; critical neighbour; candidates
+                int C = 0, crit = -1, ncand = 0;
+                bool cand_overflow = false;
+                int cand[kMaxCand];
+                for (int j = 0; j < cnt; ++j) {
+                    ++ntest;
+                    const float4 o = s_o[w][j];
+                    const float m = Qx * o.x + Qy * o.y + Qz * o.z - o.w;
+                    if (fabsf(m) <= s_h[w][j].w) {
+                        if (ncand < kMaxCand) cand[ncand++] = j;
+                        else cand_overflow = true;
+                    }
+                    const bool inside = fabsf(m) > gd ? (m >= 0.0f) : recheck(j, -1);
+                    if (inside) {
+                        if (++C == 1) crit = j;
+                        else break;
+                    }
+                }
+                if (C >= 1) ++ncov;
+                // step 2
+                if (C == 0) {
+                    if (!cand_overflow) {
+                        for (int c = 0; c < ncand; ++c)
+                            for (int s = 0; s < 3; ++s)
+                                if (covers_s(cand[c], s)) atomicAdd(&s_cnt[w][3 * cand[c] + s], 1);
+                    } else {
+                        for (int j = 0; j < cnt; ++j)
+                            for (int s = 0; s < 3; ++s)
+                                if (covers_s(j, s)) atomicAdd(&s_cnt[w][3 * j + s], 1);
+                    }
+                } else if (C == 1) {
+                    bool near = cand_overflow;
+                    for (int c = 0; c < ncand; ++c) near |= (cand[c] == crit);
+                    if (near)
+                        for (int s = 0; s < 3; ++s)
+                            if (!covers_s(crit, s)) atomicAdd(&s_cnt[w][3 * crit + s], -1);
+                }
+            }
+            ncov = warp_sum(ncov);
+            nguard = warp_sum(nguard);
+            ntest = warp_sum(ntest);
+            __syncwarp();
+            const long long qa = d.qfx[a];
+            long long f0 = 0, f1 = 0, f2 = 0;
+            for (int j = lane; j < cnt; j += 32) {
+                const int b = s_idx[w][j];
+                const int c0 = s_cnt[w][3 * j], c1 = s_cnt[w][3 * j + 1], c2 = s_cnt[w][3 * j + 2];
+                if (c0) { atomicAdd((unsigned long long*)&d.Fcav[3 * b], (unsigned long long)(qa * c0)); f0 -= qa * c0; }
+                if (c1) { atomicAdd((unsigned long long*)&d.Fcav[3 * b + 1], (unsigned long long)(qa * c1)); f1 -= qa * c1; }
+                if (c2) { atomicAdd((unsigned long long*)&d.Fcav[3 * b + 2], (unsigned long long)(qa * c2)); f2 -= qa * c2; }
+            }
+            f0 = warp_sum(f0); f1 = warp_sum(f1); f2 = warp_sum(f2);
+            if (lane == 0) {
+                if (f0) atomicAdd((unsigned long long*)&d.Fcav[3 * a], (unsigned long long)f0);
+                if (f1) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 1], (unsigned long long)f1);
+                if (f2) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 2], (unsigned long long)f2);
+                d.covered[a] = ncov;
+                if (nguard) atomicAdd(&d.status->guard, (unsigned long long)nguard);
+                atomicAdd(&d.status->sasa_tests, ntest);
+                Ea = G0a - G0a * (double)ncov / (double)d.N;  // G^cav_i = G0_i f_i
+            }
+        }
+    }
+    if (lane == 0) s_E[w] = Ea;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (int q = 0; q < kSasaWarps; ++q) e += s_E[q];
+        d.Ecav[blockIdx.x] = e;
+    }
+}
+
 // ================================================================ A7-A8: wrenches, suffix sums, torques
 __global__ void k_wrench(const DevChain d) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -957,7 +1103,7 @@ void launch_sasa(DevChain& d, cudaStream_t s) {
     if (d.prm.solvation) {
         cudaMemsetAsync(d.Fcav, 0, sizeof(long long) * 3 * (size_t)d.n, s);
         if (d.prm.precision == KCM_MIXED)
-            k_sasa<true><<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
+            k_sasa_mixed<<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
         else
             k_sasa<false><<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
     }

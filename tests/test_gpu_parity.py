@@ -101,6 +101,8 @@ def test_mixed_parity_chain1000(kcm, table, solvation):
     assert np.max(np.abs(fp64["xyz"] - ref["xyz"])) < tol_positions(och.l)
     assert mixed["stats"]["pairs"] == fp64["stats"]["pairs"] == ref["stats"]["pairs"]
     assert np.array_equal(mixed["covered"], fp64["covered"])
+    # identical classifications and integer exchange counts: bitwise-equal solvation forces
+    assert np.array_equal(mixed["F_cav"], fp64["F_cav"])
     np.testing.assert_allclose(mixed["E"], ref["E"], rtol=1e-5, atol=1e-3)
     if solvation:
         g = och.gamma != 0
@@ -211,6 +213,7 @@ def test_chain8000_cut12_sampled(kcm, table):
     g = och.gamma != 0
     # FP32 overlap tests are re-decided in FP64 inside the guard band: identical classifications
     assert np.array_equal(got["covered"], f64["covered"])
+    assert np.array_equal(got["F_cav"], f64["F_cav"])
     assert np.array_equal(f64["covered"][g], ref["covered"][g])
     assert got["stats"]["guard_rechecks"] > 0
     assert np.max(np.abs(got["xyz"] - fk_extended(och, th))) < tol_positions(och.l)
