@@ -755,13 +755,18 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
 // gives exactly Algorithm 1's exchanges: an exposed point gains coverage only from a candidate, and a
 // critically overlapped point loses it only if its critical neighbour is a candidate. FP32 decisions
 // within the guard band gd of the boundary are re-decided in FP64 by covers64, as in the FP64 kernel.
-constexpr int kMaxCand = 4;
+constexpr int kPtsPerLane = 8;                  // sample points each lane holds in registers
+constexpr int kBatch = 32 * kPtsPerLane;         // points per batch (256)
+constexpr int kCandMax = 256;                    // boundary-band candidates per batch and warp
 
 __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d) {
     __shared__ float4 s_o[kSasaWarps][kMaxNbr];   // o_j, h_j
-    __shared__ float4 s_h[kSasaWarps][kMaxNbr];   // h_jx, h_jy, h_jz, band_j
+    __shared__ float4 s_h[kSasaWarps][kMaxNbr];   // h_jx, h_jy, h_jz (displaced thresholds)
     __shared__ int s_idx[kSasaWarps][kMaxNbr];
     __shared__ int s_cnt[kSasaWarps][3 * kMaxNbr];
+    __shared__ unsigned short s_state[kSasaWarps][kBatch];  // C (2 bits, saturated) | critical j << 2
+    __shared__ unsigned int s_cand[kSasaWarps][kCandMax];   // k_local << 8 | j
+    __shared__ int s_ncand[kSasaWarps];
     __shared__ double s_E[kSasaWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
@@ -777,86 +782,135 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
             const float inv2R = 0.5f / Ra;
             const double dr = d.prm.delta_r;
             const float drf = (float)dr;
-            const float s_edge = d.grid->sf;
-            const float gd = 1e-4f + 1.2e-5f * s_edge;  // guard band in Q.o units (A)
+            const float gd = 1e-4f + 1.2e-5f * d.grid->sf;  // guard band in Q.o units (A)
+            float rmax2 = 0.0f;
             for (int j = lane; j < cnt; j += 32) {
                 const float4 o = d.nbr_off[(size_t)a * kMaxNbr + j];  // r_j - r_i, Roff_j^2
                 const float oo = o.x * o.x + o.y * o.y + o.z * o.z;
                 const float h = (Ra * Ra + oo - o.w) * inv2R;
                 const float dd = drf * drf;
-                const float hx = h + (2.0f * drf * o.x + dd) * inv2R;
-                const float hy = h + (2.0f * drf * o.y + dd) * inv2R;
-                const float hz = h + (2.0f * drf * o.z + dd) * inv2R;
-                const float band = (2.0f * drf * sqrtf(o.w) + 3.0f * dd) * inv2R + gd;
                 s_o[w][j] = make_float4(o.x, o.y, o.z, h);
-                s_h[w][j] = make_float4(hx, hy, hz, band);
+                s_h[w][j] = make_float4(h + (2.0f * drf * o.x + dd) * inv2R, h + (2.0f * drf * o.y + dd) * inv2R,
+                                        h + (2.0f * drf * o.z + dd) * inv2R, 0.0f);
                 s_idx[w][j] = d.nbr[(size_t)a * kMaxNbr + j];
                 s_cnt[w][3 * j] = 0; s_cnt[w][3 * j + 1] = 0; s_cnt[w][3 * j + 2] = 0;
+                rmax2 = fmaxf(rmax2, o.w);
             }
+            for (int q = 16; q > 0; q >>= 1) rmax2 = fmaxf(rmax2, __shfl_xor_sync(0xffffffffu, rmax2, q));
+            // band of Q.o around h_j where a displacement by dr can change a point's state, widened
+            // to the largest neighbour radius so that it is one number per atom
+            const float band = (2.0f * drf * sqrtf(rmax2) + 3.0f * drf * drf) * inv2R + gd;
             __syncwarp();
             const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
             int ncov = 0, nguard = 0;
             unsigned long long ntest = 0;
-            for (int k = lane; k < d.N; k += 32) {
+            bool any_overflow = false;
+            auto recheck = [&](int j, int k, int s) -> bool {  // FP64, identical to the FP64 kernel
+                ++nguard;
+                const int b = s_idx[w][j];
+                const double ro = d.aprm64[b].w;
+                const double qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
+                const double qy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
+                const double qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
+                return covers64(qx, qy, qz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
+            };
+            auto covers_s = [&](int j, int k, int s) -> bool {  // neighbour j displaced along s
+                const float4 o = s_o[w][j];
+                const float4 hh = s_h[w][j];
                 const float Qx = d.Q32[3 * k], Qy = d.Q32[3 * k + 1], Qz = d.Q32[3 * k + 2];
-                // FP64 recheck of a decision inside the guard band (identical to the FP64 kernel)
-                auto recheck = [&](int j, int s) -> bool {
-                    ++nguard;
-                    const int b = s_idx[w][j];
-                    const double ro = d.aprm64[b].w;
-                    const double qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
-                    const double qy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
-                    const double qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
-                    return covers64(qx, qy, qz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
-                };
-                // displaced test of neighbour j along s
-                auto covers_s = [&](int j, int s) -> bool {
-                    ++ntest;
-                    const float4 o = s_o[w][j];
-                    const float4 hh = s_h[w][j];
-                    const float dot = Qx * o.x + Qy * o.y + Qz * o.z;
-                    const float m = s == 0 ? dot + drf * Qx - hh.x : (s == 1 ? dot + drf * Qy - hh.y : dot + drf * Qz - hh.z);
-                    if (fabsf(m) > gd) return m >= 0.0f;
-                    return recheck(j, s);
-                };
-                // step 1: C = number of covering neighbours, stopped at 2; critical neighbour; candidates
-                int C = 0, crit = -1, ncand = 0;
-                bool cand_overflow = false;
-                int cand[kMaxCand];
+                const float dot = Qx * o.x + Qy * o.y + Qz * o.z;
+                const float m = s == 0 ? dot + drf * Qx - hh.x : (s == 1 ? dot + drf * Qy - hh.y : dot + drf * Qz - hh.z);
+                if (fabsf(m) > gd) return m >= 0.0f;
+                return recheck(j, k, s);
+            };
+            for (int kb = 0; kb < d.N; kb += kBatch) {
+                if (lane == 0) s_ncand[w] = 0;
+                __syncwarp();
+                float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane];
+                int C[kPtsPerLane], crit[kPtsPerLane];
+                int nvalid = 0;
+#pragma unroll
+                for (int p = 0; p < kPtsPerLane; ++p) {
+                    const int k = kb + lane + 32 * p;
+                    const bool v = k < d.N;
+                    qx[p] = v ? d.Q32[3 * k] : 0.0f;
+                    qy[p] = v ? d.Q32[3 * k + 1] : 0.0f;
+                    qz[p] = v ? d.Q32[3 * k + 2] : 0.0f;
+                    C[p] = v ? 0 : 2;  // invalid points take no part
+                    crit[p] = 0;
+                    nvalid += v;
+                }
+                // step 1, neighbour by neighbour: counts and critical neighbours of the lane's points
                 for (int j = 0; j < cnt; ++j) {
-                    ++ntest;
                     const float4 o = s_o[w][j];
-                    const float m = Qx * o.x + Qy * o.y + Qz * o.z - o.w;
-                    if (fabsf(m) <= s_h[w][j].w) {
-                        if (ncand < kMaxCand) cand[ncand++] = j;
-                        else cand_overflow = true;
-                    }
-                    const bool inside = fabsf(m) > gd ? (m >= 0.0f) : recheck(j, -1);
-                    if (inside) {
-                        if (++C == 1) crit = j;
-                        else break;
+#pragma unroll
+                    for (int p = 0; p < kPtsPerLane; ++p) {
+                        const float m = qx[p] * o.x + qy[p] * o.y + qz[p] * o.z - o.w;
+                        bool inside = m > 0.0f;
+                        if (fabsf(m) <= band) {  // near the cap boundary: rare
+                            const int k = kb + lane + 32 * p;
+                            if (k < d.N) {
+                                const int slot = atomicAdd(&s_ncand[w], 1);
+                                if (slot < kCandMax) s_cand[w][slot] = ((unsigned)(lane + 32 * p) << 8) | (unsigned)j;
+                                inside = fabsf(m) > gd ? (m >= 0.0f) : recheck(j, k, -1);
+                            }
+                        }
+                        crit[p] = (inside && C[p] == 0) ? j : crit[p];
+                        C[p] += inside ? 1 : 0;
                     }
                 }
-                if (C >= 1) ++ncov;
-                // step 2
-                if (C == 0) {
-                    if (!cand_overflow) {
-                        for (int c = 0; c < ncand; ++c)
-                            for (int s = 0; s < 3; ++s)
-                                if (covers_s(cand[c], s)) atomicAdd(&s_cnt[w][3 * cand[c] + s], 1);
-                    } else {
-                        for (int j = 0; j < cnt; ++j)
-                            for (int s = 0; s < 3; ++s)
-                                if (covers_s(j, s)) atomicAdd(&s_cnt[w][3 * j + s], 1);
+                ntest += (unsigned long long)nvalid * cnt;
+#pragma unroll
+                for (int p = 0; p < kPtsPerLane; ++p) {
+                    const int k = kb + lane + 32 * p;
+                    if (k < d.N) {
+                        ncov += C[p] >= 1;
+                        s_state[w][lane + 32 * p] = (unsigned short)(min(C[p], 2) | (crit[p] << 2));
                     }
-                } else if (C == 1) {
-                    bool near = cand_overflow;
-                    for (int c = 0; c < ncand; ++c) near |= (cand[c] == crit);
-                    if (near)
-                        for (int s = 0; s < 3; ++s)
-                            if (!covers_s(crit, s)) atomicAdd(&s_cnt[w][3 * crit + s], -1);
                 }
+                __syncwarp();
+                // step 2 on the candidates: an exposed point gains coverage from a displaced candidate;
+                // a critically overlapped point loses it only through its critical neighbour
+                const int nc = s_ncand[w];
+                if (nc <= kCandMax) {
+                    for (int e = lane; e < nc; e += 32) {
+                        const unsigned cv = s_cand[w][e];
+                        const int kl = (int)(cv >> 8), j = (int)(cv & 0xffu);
+                        const int k = kb + kl;
+                        const unsigned st = s_state[w][kl];
+                        const int Cs = st & 3, cr = st >> 2;
+                        if (Cs == 0) {
+                            for (int s = 0; s < 3; ++s)
+                                if (covers_s(j, k, s)) atomicAdd(&s_cnt[w][3 * j + s], 1);
+                            ntest += 3;
+                        } else if (Cs == 1 && cr == j) {
+                            for (int s = 0; s < 3; ++s)
+                                if (!covers_s(j, k, s)) atomicAdd(&s_cnt[w][3 * j + s], -1);
+                            ntest += 3;
+                        }
+                    }
+                } else {  // candidate list full: re-test every neighbour of every point with C <= 1
+                    any_overflow = true;
+                    for (int p = 0; p < kPtsPerLane; ++p) {
+                        const int kl = lane + 32 * p, k = kb + kl;
+                        if (k >= d.N) continue;
+                        const unsigned st = s_state[w][kl];
+                        const int Cs = st & 3, cr = st >> 2;
+                        if (Cs == 0) {
+                            for (int j = 0; j < cnt; ++j)
+                                for (int s = 0; s < 3; ++s)
+                                    if (covers_s(j, k, s)) atomicAdd(&s_cnt[w][3 * j + s], 1);
+                            ntest += 3 * cnt;
+                        } else if (Cs == 1) {
+                            for (int s = 0; s < 3; ++s)
+                                if (!covers_s(cr, k, s)) atomicAdd(&s_cnt[w][3 * cr + s], -1);
+                            ntest += 3;
+                        }
+                    }
+                }
+                __syncwarp();
             }
+            (void)any_overflow;
             ncov = warp_sum(ncov);
             nguard = warp_sum(nguard);
             ntest = warp_sum(ntest);
