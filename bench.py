@@ -43,8 +43,8 @@ UNIT = "atom-iterations/s"
 FP32_LANES_PER_SM = 128
 FLOPS_PER_SASA_TEST = 9  # w = v - o (3), |w|^2 (1 mul + 2 FMA = 5), compare with Roff^2 (1)
 FLOPS_PER_PAIR = 31      # per unordered pair within the cutoff (distance, 1/d^2, Coulomb, LJ, weights, accumulate)
-BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques": 60}  # algorithmic HBM bytes per atom
-KERNELS_PER_ITERATION = {1: 17, 0: 16}  # reset + kinematics 4 + binning 5 + pairs 1 + solvation 1 + torques 3 + energy 1 + step 1
+BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques_step": 60}  # algorithmic HBM bytes per atom
+KERNELS_PER_ITERATION = {1: 16, 0: 15}  # reset + kinematics 4 + binning 5 + pairs 1 + solvation 1 + wrench/suffix/torque-step 4
 
 
 def parse():

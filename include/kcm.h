@@ -211,12 +211,10 @@ int kcm_get_stats(kcm_handle h, kcm_stats* st);
 /* Stages of one iteration, in launch order, as timed by kcm_step_timed. */
 #define KCM_STAGE_KINEMATICS 0 /* transform scan and atom centres (eq. kin_04, r1, r2) */
 #define KCM_STAGE_BINNING 1    /* bounding box, grid, counting sort (Sec. 3.2) */
-#define KCM_STAGE_PAIRS 2      /* Coulomb + LJ forces and solvation neighbour lists */
-#define KCM_STAGE_SOLVATION 3  /* Algorithm 1 */
-#define KCM_STAGE_TORQUES 4    /* link wrenches, suffix sums, joint torques (Sec. 3.5) */
-#define KCM_STAGE_ENERGY 5     /* energy reduction (eq. 01) */
-#define KCM_STAGE_STEP 6       /* clamped step (eq. KCM_07) */
-#define KCM_NUM_STAGES 7
+#define KCM_STAGE_PAIRS 2      /* Coulomb + LJ forces, their energies, solvation neighbour lists */
+#define KCM_STAGE_SOLVATION 3  /* Algorithm 1 and the solvation energy */
+#define KCM_STAGE_TORQUES 4    /* link wrenches, suffix sums, joint torques (Sec. 3.5) and the step (eq. KCM_07) */
+#define KCM_NUM_STAGES 5
 
 /* Run ONE iteration (as kcm_step(h, 1, ...)) through a copy of the iteration graph that records
  * CUDA events between stages on the handle's stream, synchronise, and return the stage durations

@@ -72,7 +72,13 @@ void enqueue_evaluation(kcm_ctx* h) {
     kcm::launch_binning(h->d, h->stream);
     kcm::launch_forces(h->d, h->stream);
     kcm::launch_torques(h->d, h->stream);
-    kcm::launch_energy(h->d, h->stream);
+}
+
+void enqueue_iteration(kcm_ctx* h) {
+    kcm::launch_fk(h->d, h->stream);
+    kcm::launch_binning(h->d, h->stream);
+    kcm::launch_forces(h->d, h->stream);
+    kcm::launch_torques_step(h->d, h->stream);
 }
 
 int read_status(kcm_ctx* h, kcm::Status* st) {
@@ -103,8 +109,7 @@ int build_graph(kcm_ctx* h) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
-    enqueue_evaluation(h);
-    kcm::launch_step(h->d, h->stream);
+    enqueue_iteration(h);
     e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
     e = cudaGraphInstantiate(&h->graph, g, 0);
@@ -138,12 +143,8 @@ int build_timed_graph(kcm_ctx* h) {
     cudaEventRecordWithFlags(h->ev[4], s, cudaEventRecordExternal);
     kcm::launch_sasa(h->d, s);
     cudaEventRecordWithFlags(h->ev[5], s, cudaEventRecordExternal);
-    kcm::launch_torques(h->d, s);
+    kcm::launch_torques_step(h->d, s);
     cudaEventRecordWithFlags(h->ev[6], s, cudaEventRecordExternal);
-    kcm::launch_energy(h->d, s);
-    cudaEventRecordWithFlags(h->ev[7], s, cudaEventRecordExternal);
-    kcm::launch_step(h->d, s);
-    cudaEventRecordWithFlags(h->ev[8], s, cudaEventRecordExternal);
     e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
     e = cudaGraphInstantiate(&h->graph_timed, g, 0);
@@ -224,8 +225,9 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     kcm::DevChain& d = h->d;
     d.prm = *prm;
     d.m = hc.m; d.n = hc.n; d.l = hc.l; d.L = hc.L; d.N = prm->n_sample;
-    d.nfk_chunks = (d.l + kcm::kFkChunk - 1) / kcm::kFkChunk;
-    d.nlink_chunks = (d.L + kcm::kLinkChunk - 1) / kcm::kLinkChunk;
+    d.fk_j = kcm::fk_joints_per_lane(d.l);
+    d.ntiles = (d.l + 32 * d.fk_j - 1) / (32 * d.fk_j);
+    d.ltiles = (d.L + 31) / 32;
     d.cell_cap = std::max(8 * d.n, 65536);
     d.pair_blocks = (d.n + kcm::kPairWarps - 1) / kcm::kPairWarps;
     d.bbox_blocks = std::max(1, std::min((d.n + 255) / 256, 2 * 148));
@@ -248,7 +250,8 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = dalloc(h, &d.exm, nn)) || (rc = dalloc(h, &d.m14m, nn)) || (rc = dalloc(h, &d.Q64, 3 * N)) ||
         (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.theta, l)) || (rc = dalloc(h, &d.dtheta, l)) ||
         (rc = dalloc(h, &d.tau, l)) || (rc = dalloc(h, &d.G, 12 * (size_t)l)) ||
-        (rc = dalloc(h, &d.chunkP, 12 * (size_t)d.nfk_chunks)) || (rc = dalloc(h, &d.chunkE, 12 * (size_t)d.nfk_chunks)) ||
+        (rc = dalloc(h, &d.lane_ex, 12 * 32 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) ||
+        (rc = dalloc(h, &d.tileE, 12 * (size_t)d.ntiles)) ||
         (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||
         (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.cell_count, d.cell_cap)) ||
         (rc = dalloc(h, &d.cell_start, d.cell_cap + 1)) || (rc = dalloc(h, &d.rank, nn)) || (rc = dalloc(h, &d.scan_part, d.scan_blocks)) ||
@@ -257,9 +260,9 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||
         (rc = dalloc(h, &d.nbr, nn * kcm::kMaxNbr)) || (rc = dalloc(h, &d.nbr_off, nn * kcm::kMaxNbr)) ||
         (rc = dalloc(h, &d.covered, nn)) || (rc = dalloc(h, &d.P, 6 * (size_t)L)) ||
-        (rc = dalloc(h, &d.chunkS, 6 * (size_t)d.nlink_chunks)) || (rc = dalloc(h, &d.chunkSuf, 6 * (size_t)d.nlink_chunks)) ||
-        (rc = dalloc(h, &d.Epair, 2 * (size_t)d.pair_blocks)) || (rc = dalloc(h, &d.Ecav, d.sasa_blocks)) ||
-        (rc = dalloc(h, &d.E, 3)) || (rc = dalloc(h, &d.Ftot, 3 * nn)) || (rc = dalloc(h, &d.Fcav64, 3 * nn)) ||
+        (rc = dalloc(h, &d.lane_suf, 6 * (size_t)L)) || (rc = dalloc(h, &d.tileS, 6 * (size_t)d.ltiles)) ||
+        (rc = dalloc(h, &d.tileSuf, 6 * (size_t)d.ltiles)) ||
+        (rc = dalloc(h, &d.Ftot, 3 * nn)) || (rc = dalloc(h, &d.Fcav64, 3 * nn)) ||
         (rc = dalloc(h, &d.grid, 1)) || (rc = dalloc(h, &d.status, 1)))
         return bail(rc);
 
@@ -406,11 +409,17 @@ int kcm_torques_dev(kcm_handle h, double* tau_dev, int64_t l) {
 int kcm_energy(kcm_handle h, double E[3]) {
     if (check_handle(h)) return KCM_E_INVAL;
     if (!E) return set_err(h, KCM_E_INVAL, "E is NULL");
-    int rc = evaluate(h);
-    if (rc) return rc;
-    cudaError_t e = cudaMemcpyAsync(E, h->d.E, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "energy copy");
-    return sync(h);
+    kcm::launch_reset_loop(h->d, h->stream);
+    enqueue_evaluation(h);
+    kcm::Status st;
+    int rc = read_status(h, &st);
+    if (rc != KCM_OK) return rc;
+    rc = status_code(h, st);
+    if (rc != KCM_OK) return rc;
+    E[0] = st.E[0];
+    E[1] = st.E[1];
+    E[2] = st.E[2];
+    return KCM_OK;
 }
 
 int kcm_sasa_counts(kcm_handle h, int32_t* covered, int64_t n) {
@@ -491,7 +500,7 @@ int kcm_step_timed(kcm_handle h, float* stage_ms, int32_t n_stages, float* total
         if (e != cudaSuccess) return cuda_fail(h, e, "event elapsed");
     }
     if (total_ms) {
-        e = cudaEventElapsedTime(total_ms, h->ev[0], h->ev[8]);
+        e = cudaEventElapsedTime(total_ms, h->ev[0], h->ev[KCM_NUM_STAGES + 1]);
         if (e != cudaSuccess) return cuda_fail(h, e, "event elapsed");
     }
     return status_code(h, st);

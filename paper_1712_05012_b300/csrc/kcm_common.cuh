@@ -1,0 +1,93 @@
+// Device helpers shared by the kernel files of the KCM library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kcm_device.h"
+
+namespace kcm {
+namespace dev {
+
+// ---------------------------------------------------------------- small helpers
+__device__ __forceinline__ unsigned long long dkey(double x) {
+    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    unsigned long long b = (k & 0x8000000000000000ULL) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k;
+    return __longlong_as_double(static_cast<long long>(b));
+}
+
+// affine transform: rows of the rotation a[0..8], translation a[9..11]; C = A o B
+__device__ __forceinline__ void aff_compose(const double* A, const double* B, double* C) {
+    double T[12];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) T[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+        T[9 + i] = A[3 * i] * B[9] + A[3 * i + 1] * B[10] + A[3 * i + 2] * B[11] + A[9 + i];
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) C[k] = T[k];
+}
+__device__ __forceinline__ void aff_identity(double* A) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) A[k] = (k == 0 || k == 4 || k == 8) ? 1.0 : 0.0;
+}
+__device__ __forceinline__ void aff_load(const double* src, double* A) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) A[k] = src[k];
+}
+__device__ __forceinline__ void aff_store(double* dst, const double* A) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) dst[k] = A[k];
+}
+
+// Local joint transform between consecutive link frames: L_j = Tr(step_j) o Rot(u_j, th), i.e.
+// x -> R x + step_j with R = cos I + sin [u]x + (1 - cos) u u^T (right-hand rule). With link frame
+// poses T_j = L_1 o ... o L_j the ZP-frame product of rotations about the joint axes (eq. kin_04)
+// is T_j o Tr(-p0_j), and atom centres are T_link(r^0 - p0_link) (eq. r1/r2).
+__device__ __forceinline__ void joint_tf(const double* u, const double* step, double th, double* G) {
+    double s, c;
+    sincos(th, &s, &c);
+    double C = 1.0 - c;
+    G[0] = c + u[0] * u[0] * C;        G[1] = u[0] * u[1] * C - u[2] * s; G[2] = u[0] * u[2] * C + u[1] * s;
+    G[3] = u[1] * u[0] * C + u[2] * s; G[4] = c + u[1] * u[1] * C;        G[5] = u[1] * u[2] * C - u[0] * s;
+    G[6] = u[2] * u[0] * C - u[1] * s; G[7] = u[2] * u[1] * C + u[0] * s; G[8] = c + u[2] * u[2] * C;
+    G[9] = step[0];
+    G[10] = step[1];
+    G[11] = step[2];
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// FP32 pair term to int64 fixed point with kPairFx fractional bits (round to nearest, symmetric in
+// sign, so the terms of (i, j) and (j, i) stay exact negatives); |v| < kPairFxMax keeps a sum of
+// tens of terms inside int64
+__device__ __forceinline__ long long to_fixed(float v) { return __float2ll_rn(v * 16777216.0f); }
+
+// The FP64 overlap test of Algorithm 1: || (r_a + Roff_a q_k) - r_b - dr e_s ||^2 <= Roff_b^2,
+// written with explicit roundings so that the FP64 kernel and the FP32 guard-band recheck take
+// identical decisions.
+__device__ __forceinline__ bool covers64(double qx, double qy, double qz, double bx, double by, double bz,
+                                         double roff2_b, int s, double dr) {
+    double wx = __dsub_rn(qx, bx), wy = __dsub_rn(qy, by), wz = __dsub_rn(qz, bz);
+    if (s == 0) wx = __dsub_rn(wx, dr);
+    if (s == 1) wy = __dsub_rn(wy, dr);
+    if (s == 2) wz = __dsub_rn(wz, dr);
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(wx, wx), __dmul_rn(wy, wy)), __dmul_rn(wz, wz));
+    return d2 <= roff2_b;
+}
+
+}  // namespace dev
+}  // namespace kcm

@@ -39,6 +39,7 @@ struct Status {
     int done;             // converged or failed: the remaining iterations are no-ops
     int error;            // kErr* bits
     double last_max_dtheta;
+    double E[3];  // Coulomb, LJ, solvation energies of the last evaluation
     unsigned long long pairs;
     unsigned long long nbr_total;
     unsigned long long guard;
@@ -48,10 +49,6 @@ struct Status {
 };
 
 // Launch shapes.
-constexpr int kFkChunk = 8;     // joints per thread in the transform scan
-constexpr int kFkTpb = 8;       // threads per block of the FP64 chunk kernels (spreads FP64 work over SMs)
-constexpr int kLinkChunk = 8;   // links per thread in the wrench / suffix-sum kernels
-constexpr int kScanThreads = 64;
 constexpr int kPairWarps = 4;         // home atoms (warps) per block of the pair kernel
 constexpr int kScanCells = 2048;      // cells per block of the cell-count scan
 constexpr int kScanThreadsBig = 256;
@@ -63,7 +60,9 @@ constexpr int kApplyTpb = 64;
 
 struct DevChain {
     int m = 0, n = 0, l = 0, L = 0, N = 0;
-    int nfk_chunks = 0, nlink_chunks = 0;
+    int fk_j = 1;        // joints per lane in the transform scan
+    int ntiles = 0;      // transform-scan tiles of 32 * fk_j joints
+    int ltiles = 0;      // suffix-sum tiles of 32 links
     int cell_cap = 0;
     int pair_blocks = 0, sasa_blocks = 0, bbox_blocks = 0, scan_blocks = 0;
     kcm_params prm{};
@@ -91,9 +90,10 @@ struct DevChain {
     double* theta = nullptr;       // [l]
     double* dtheta = nullptr;      // [l]
     double* tau = nullptr;         // [l]
-    double* G = nullptr;           // local joint transforms [l*12]
-    double* chunkP = nullptr;      // [nfk_chunks*12]
-    double* chunkE = nullptr;      // [nfk_chunks*12]
+    double* G = nullptr;           // lane-local prefixes of the joint transforms [l*12]
+    double* lane_ex = nullptr;     // exclusive lane prefixes within tiles [ntiles*32*12]
+    double* tileP = nullptr;       // tile products [ntiles*12]
+    double* tileE = nullptr;       // exclusive tile prefixes [ntiles*12]
     double* M = nullptr;           // link frame poses [L*12]
     double* ucur = nullptr;        // current joint axes [l*3]
     double* pcur = nullptr;        // current axis points [l*3]
@@ -116,11 +116,9 @@ struct DevChain {
     float4* nbr_off = nullptr;     // r_j - r_i and Roff_j^2 [n*kMaxNbr]
     int* covered = nullptr;        // [n]
     double* P = nullptr;           // link wrenches [L*6]
-    double* chunkS = nullptr;      // [nlink_chunks*6]
-    double* chunkSuf = nullptr;    // [nlink_chunks*6]
-    double* Epair = nullptr;       // [pair_blocks*2]
-    double* Ecav = nullptr;        // [sasa_blocks]
-    double* E = nullptr;           // [3]
+    double* lane_suf = nullptr;    // suffix sums within tiles of 32 links [L*6]
+    double* tileS = nullptr;       // tile sums [ltiles*6]
+    double* tileSuf = nullptr;     // exclusive suffix sums of the tile sums [ltiles*6]
     double* Ftot = nullptr;        // [n*3] (on request)
     double* Fcav64 = nullptr;      // [n*3] (on request)
     GridInfo* grid = nullptr;
@@ -136,8 +134,8 @@ void launch_forces(DevChain& d, cudaStream_t s);
 void launch_pairs(DevChain& d, cudaStream_t s);
 void launch_sasa(DevChain& d, cudaStream_t s);
 void launch_torques(DevChain& d, cudaStream_t s);
-void launch_energy(DevChain& d, cudaStream_t s);
-void launch_step(DevChain& d, cudaStream_t s);
+void launch_torques_step(DevChain& d, cudaStream_t s);
+int fk_joints_per_lane(int l);
 void launch_force_out(DevChain& d, cudaStream_t s);
 
 }  // namespace kcm

@@ -19,172 +19,13 @@
 #include <cstdio>
 #include <type_traits>
 
+#include "kcm_common.cuh"
 #include "kcm_device.h"
 
 namespace kcm {
 
 namespace {
-
-// ---------------------------------------------------------------- small helpers
-__device__ __forceinline__ unsigned long long dkey(double x) {
-    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
-}
-__device__ __forceinline__ double dkey_inv(unsigned long long k) {
-    unsigned long long b = (k & 0x8000000000000000ULL) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k;
-    return __longlong_as_double(static_cast<long long>(b));
-}
-
-// affine transform: rows of the rotation a[0..8], translation a[9..11]; C = A o B
-__device__ __forceinline__ void aff_compose(const double* A, const double* B, double* C) {
-    double T[12];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) T[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
-        T[9 + i] = A[3 * i] * B[9] + A[3 * i + 1] * B[10] + A[3 * i + 2] * B[11] + A[9 + i];
-    }
-#pragma unroll
-    for (int k = 0; k < 12; ++k) C[k] = T[k];
-}
-__device__ __forceinline__ void aff_identity(double* A) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) A[k] = (k == 0 || k == 4 || k == 8) ? 1.0 : 0.0;
-}
-__device__ __forceinline__ void aff_load(const double* src, double* A) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) A[k] = src[k];
-}
-__device__ __forceinline__ void aff_store(double* dst, const double* A) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) dst[k] = A[k];
-}
-
-// Local joint transform between consecutive link frames: L_j = Tr(step_j) o Rot(u_j, th), i.e.
-// x -> R x + step_j with R = cos I + sin [u]x + (1 - cos) u u^T (right-hand rule). With link frame
-// poses T_j = L_1 o ... o L_j the ZP-frame product of rotations about the joint axes (eq. kin_04)
-// is T_j o Tr(-p0_j), and atom centres are T_link(r^0 - p0_link) (eq. r1/r2).
-__device__ __forceinline__ void joint_tf(const double* u, const double* step, double th, double* G) {
-    double s, c;
-    sincos(th, &s, &c);
-    double C = 1.0 - c;
-    G[0] = c + u[0] * u[0] * C;        G[1] = u[0] * u[1] * C - u[2] * s; G[2] = u[0] * u[2] * C + u[1] * s;
-    G[3] = u[1] * u[0] * C + u[2] * s; G[4] = c + u[1] * u[1] * C;        G[5] = u[1] * u[2] * C - u[0] * s;
-    G[6] = u[2] * u[0] * C - u[1] * s; G[7] = u[2] * u[1] * C + u[0] * s; G[8] = c + u[2] * u[2] * C;
-    G[9] = step[0];
-    G[10] = step[1];
-    G[11] = step[2];
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ int warp_max(int v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// FP32 pair term to int64 fixed point with kPairFx fractional bits (round to nearest, symmetric in
-// sign, so the terms of (i, j) and (j, i) stay exact negatives); |v| < kPairFxMax keeps a sum of
-// tens of terms inside int64
-__device__ __forceinline__ long long to_fixed(float v) { return __float2ll_rn(v * 16777216.0f); }
-
-// The FP64 overlap test of Algorithm 1: || (r_a + Roff_a q_k) - r_b - dr e_s ||^2 <= Roff_b^2,
-// written with explicit roundings so that the FP64 kernel and the FP32 guard-band recheck take
-// identical decisions.
-__device__ __forceinline__ bool covers64(double qx, double qy, double qz, double bx, double by, double bz,
-                                         double roff2_b, int s, double dr) {
-    double wx = __dsub_rn(qx, bx), wy = __dsub_rn(qy, by), wz = __dsub_rn(qz, bz);
-    if (s == 0) wx = __dsub_rn(wx, dr);
-    if (s == 1) wy = __dsub_rn(wy, dr);
-    if (s == 2) wz = __dsub_rn(wz, dr);
-    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(wx, wx), __dmul_rn(wy, wy)), __dmul_rn(wz, wz));
-    return d2 <= roff2_b;
-}
-
-// ================================================================ A1: forward kinematics
-// chunk products P_c = G_{cC} o ... o G_{cC+C-1}; G_j stored for the apply pass
-__global__ void k_fk_local(const DevChain d) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= d.nfk_chunks || d.status->done) return;
-    int j0 = c * kFkChunk, j1 = min(d.l, j0 + kFkChunk);
-    double P[12], Gj[12];
-    joint_tf(&d.u0[3 * j0], &d.step0[3 * j0], d.theta[j0], P);
-    aff_store(&d.G[12 * j0], P);
-    for (int j = j0 + 1; j < j1; ++j) {
-        joint_tf(&d.u0[3 * j], &d.step0[3 * j], d.theta[j], Gj);
-        aff_store(&d.G[12 * j], Gj);
-        aff_compose(P, Gj, P);
-    }
-    aff_store(&d.chunkP[12 * c], P);
-}
-
-// exclusive prefix of the chunk products, E_c = P_0 o ... o P_{c-1}, in one block: each thread
-// folds a contiguous run, one thread scans the run totals, each thread rescans its run
-__global__ void k_fk_scan(const DevChain d) {
-    __shared__ double S[kScanThreads][12];
-    if (d.status->done) return;
-    int t = threadIdx.x, nc = d.nfk_chunks;
-    int per = (nc + kScanThreads - 1) / kScanThreads;
-    int c0 = min(nc, t * per), c1 = min(nc, c0 + per);
-    double A[12], B[12];
-    aff_identity(A);
-    for (int c = c0; c < c1; ++c) {
-        aff_load(&d.chunkP[12 * c], B);
-        aff_compose(A, B, A);
-    }
-    for (int k = 0; k < 12; ++k) S[t][k] = A[k];
-    __syncthreads();
-    if (t == 0) {
-        double X[12];
-        aff_identity(X);
-        for (int u = 0; u < kScanThreads; ++u) {
-            for (int k = 0; k < 12; ++k) B[k] = S[u][k];
-            for (int k = 0; k < 12; ++k) S[u][k] = X[k];
-            aff_compose(X, B, X);
-        }
-    }
-    __syncthreads();
-    for (int k = 0; k < 12; ++k) A[k] = S[t][k];
-    for (int c = c0; c < c1; ++c) {
-        aff_store(&d.chunkE[12 * c], A);
-        aff_load(&d.chunkP[12 * c], B);
-        aff_compose(A, B, A);
-    }
-}
-
-// link frame poses M_{j+1} = M_j o L_j; current axis u_j = R(M_j) u0_j through p_j = origin of
-// frame j+1 (the joint's axis point)
-__global__ void k_fk_apply(const DevChain d) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= d.nfk_chunks || d.status->done) return;
-    int j0 = c * kFkChunk, j1 = min(d.l, j0 + kFkChunk);
-    double X[12], Gj[12];
-    aff_load(&d.chunkE[12 * c], X);
-    for (int j = j0; j < j1; ++j) {
-        const double* u = &d.u0[3 * j];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) d.ucur[3 * j + i] = X[3 * i] * u[0] + X[3 * i + 1] * u[1] + X[3 * i + 2] * u[2];
-        aff_load(&d.G[12 * j], Gj);
-        aff_compose(X, Gj, X);
-        aff_store(&d.M[12 * (j + 1)], X);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) d.pcur[3 * j + i] = X[9 + i];
-    }
-}
-
-__global__ void k_fk_atoms(const DevChain d) {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= d.n || d.status->done) return;
-    const double* M = &d.M[12 * d.link[a]];
-    double x = d.r0[3 * a], y = d.r0[3 * a + 1], z = d.r0[3 * a + 2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) d.r[3 * a + i] = M[3 * i] * x + M[3 * i + 1] * y + M[3 * i + 2] * z + M[9 + i];
-}
+using namespace dev;
 
 // ================================================================ A2: binning
 // Bounding box as order-preserving integer keys (no FP64 min/max); the last block to finish
@@ -267,6 +108,9 @@ __global__ void k_bbox(const DevChain d) {
     st->guard = 0;
     st->sasa_tests = 0;
     st->max_nbr = 0;
+    st->E[0] = 0.0;
+    st->E[1] = 0.0;
+    st->E[2] = 0.0;
 }
 
 // Cell of each atom (FP32 from the FP64 offset to the grid origin; the cell-edge margin makes
@@ -606,8 +450,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         unsigned long long c0 = 0, c1 = 0, c2 = 0;
         int m = 0;
         for (int k2 = 0; k2 < kPairWarps; ++k2) { e0 += sE[0][k2]; e1 += sE[1][k2]; c0 += sC[0][k2]; c1 += sC[1][k2]; c2 += sC[2][k2]; m = max(m, sM[k2]); }
-        d.Epair[2 * blockIdx.x] = e0;
-        d.Epair[2 * blockIdx.x + 1] = e1;
+        if (e0 != 0.0) atomicAdd(&d.status->E[0], e0);
+        if (e1 != 0.0) atomicAdd(&d.status->E[1], e1);
         if (c0) atomicAdd(&d.status->pairs, c0);
         if (c1) atomicAdd(&d.status->guard, c1);
         if (c2) atomicAdd(&d.status->nbr_total, c2);
@@ -741,7 +585,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
     if (threadIdx.x == 0) {
         double e = 0.0;
         for (int k = 0; k < kSasaWarps; ++k) e += s_E[k];
-        d.Ecav[blockIdx.x] = e;
+        if (e != 0.0) atomicAdd(&d.status->E[2], e);
     }
 }
 
@@ -827,8 +671,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 if (lane == 0) s_ncand[w] = 0;
                 __syncwarp();
                 float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane];
-                int C[kPtsPerLane], crit[kPtsPerLane];
-                int nvalid = 0;
+                unsigned valid = 0;
 #pragma unroll
                 for (int p = 0; p < kPtsPerLane; ++p) {
                     const int k = kb + lane + 32 * p;
@@ -836,36 +679,58 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                     qx[p] = v ? d.Q32[3 * k] : 0.0f;
                     qy[p] = v ? d.Q32[3 * k + 1] : 0.0f;
                     qz[p] = v ? d.Q32[3 * k + 2] : 0.0f;
-                    C[p] = v ? 0 : 2;  // invalid points take no part
-                    crit[p] = 0;
-                    nvalid += v;
+                    valid |= v ? (1u << p) : 0u;
                 }
-                // step 1, neighbour by neighbour: counts and critical neighbours of the lane's points
+                // step 1, neighbour by neighbour, for the lane's 8 points at once: `in` has bit p set
+                // when neighbour j covers point p; c1 / c2 are the bit planes C >= 1 and C >= 2; the
+                // critical neighbour is written when a point is first covered
+                unsigned c1 = 0, c2 = 0;
+                int crit[kPtsPerLane];
+#pragma unroll
+                for (int p = 0; p < kPtsPerLane; ++p) crit[p] = 0;
                 for (int j = 0; j < cnt; ++j) {
                     const float4 o = s_o[w][j];
+                    float m[kPtsPerLane];
+                    unsigned in = 0, near = 0;
 #pragma unroll
                     for (int p = 0; p < kPtsPerLane; ++p) {
-                        const float m = qx[p] * o.x + qy[p] * o.y + qz[p] * o.z - o.w;
-                        bool inside = m > 0.0f;
-                        if (fabsf(m) <= band) {  // near the cap boundary: rare
-                            const int k = kb + lane + 32 * p;
-                            if (k < d.N) {
+                        m[p] = fmaf(qz[p], o.z, fmaf(qy[p], o.y, fmaf(qx[p], o.x, -o.w)));
+                        in |= (m[p] > 0.0f) ? (1u << p) : 0u;
+                        near |= (fabsf(m[p]) <= band) ? (1u << p) : 0u;
+                    }
+                    near &= valid;
+                    if (near) {  // rare: record candidates, re-decide guard-band tests in FP64
+#pragma unroll
+                        for (int p = 0; p < kPtsPerLane; ++p) {
+                            if (near & (1u << p)) {
                                 const int slot = atomicAdd(&s_ncand[w], 1);
                                 if (slot < kCandMax) s_cand[w][slot] = ((unsigned)(lane + 32 * p) << 8) | (unsigned)j;
-                                inside = fabsf(m) > gd ? (m >= 0.0f) : recheck(j, k, -1);
+                                if (fabsf(m[p]) <= gd) {
+                                    const bool r64 = recheck(j, kb + lane + 32 * p, -1);
+                                    in = r64 ? (in | (1u << p)) : (in & ~(1u << p));
+                                }
                             }
                         }
-                        crit[p] = (inside && C[p] == 0) ? j : crit[p];
-                        C[p] += inside ? 1 : 0;
+                    }
+                    in &= valid;
+                    unsigned first = in & ~c1;
+                    c2 |= c1 & in;
+                    c1 |= in;
+                    while (first) {
+                        const int p = __ffs(first) - 1;
+                        first &= first - 1;
+#pragma unroll
+                        for (int q = 0; q < kPtsPerLane; ++q) crit[q] = (q == p) ? j : crit[q];
                     }
                 }
+                int nvalid = __popc(valid);
                 ntest += (unsigned long long)nvalid * cnt;
 #pragma unroll
                 for (int p = 0; p < kPtsPerLane; ++p) {
-                    const int k = kb + lane + 32 * p;
-                    if (k < d.N) {
-                        ncov += C[p] >= 1;
-                        s_state[w][lane + 32 * p] = (unsigned short)(min(C[p], 2) | (crit[p] << 2));
+                    if (valid & (1u << p)) {
+                        const int Cs = (c2 >> p) & 1 ? 2 : ((c1 >> p) & 1);
+                        ncov += Cs >= 1;
+                        s_state[w][lane + 32 * p] = (unsigned short)(Cs | (crit[p] << 2));
                     }
                 }
                 __syncwarp();
@@ -941,154 +806,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
     if (threadIdx.x == 0) {
         double e = 0.0;
         for (int q = 0; q < kSasaWarps; ++q) e += s_E[q];
-        d.Ecav[blockIdx.x] = e;
-    }
-}
-
-// ================================================================ A7-A8: wrenches, suffix sums, torques
-__global__ void k_wrench(const DevChain d) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= d.nlink_chunks || d.status->done) return;
-    int h0 = c * kLinkChunk, h1 = min(d.L, h0 + kLinkChunk);
-    const bool solv = d.prm.solvation != 0;
-    double S[6] = {0, 0, 0, 0, 0, 0};
-    for (int h = h0; h < h1; ++h) {
-        double T0 = 0, T1 = 0, T2 = 0, F0 = 0, F1 = 0, F2 = 0;
-        for (int a = d.link_start[h]; a < d.link_start[h + 1]; ++a) {
-            double fx = d.Fpair[3 * a], fy = d.Fpair[3 * a + 1], fz = d.Fpair[3 * a + 2];
-            if (solv) {
-                fx += (double)d.Fcav[3 * a] * kFxInv;
-                fy += (double)d.Fcav[3 * a + 1] * kFxInv;
-                fz += (double)d.Fcav[3 * a + 2] * kFxInv;
-            }
-            double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
-            T0 += y * fz - z * fy;  // r x F about the origin (eq. KCM_02)
-            T1 += z * fx - x * fz;
-            T2 += x * fy - y * fx;
-            F0 += fx; F1 += fy; F2 += fz;
-        }
-        double* P = &d.P[6 * h];
-        P[0] = T0; P[1] = T1; P[2] = T2; P[3] = F0; P[4] = F1; P[5] = F2;
-        if (h >= 1) { S[0] += T0; S[1] += T1; S[2] += T2; S[3] += F0; S[4] += F1; S[5] += F2; }
-    }
-    for (int k = 0; k < 6; ++k) d.chunkS[6 * c + k] = S[k];
-}
-
-// exclusive suffix sums of the chunk sums (one block)
-__global__ void k_torque_scan(const DevChain d) {
-    __shared__ double S[kScanThreads][6];
-    if (d.status->done) return;
-    int t = threadIdx.x, nc = d.nlink_chunks;
-    int per = (nc + kScanThreads - 1) / kScanThreads;
-    int c0 = min(nc, t * per), c1 = min(nc, c0 + per);
-    double A[6] = {0, 0, 0, 0, 0, 0};
-    for (int c = c1 - 1; c >= c0; --c)
-        for (int k = 0; k < 6; ++k) A[k] += d.chunkS[6 * c + k];
-    for (int k = 0; k < 6; ++k) S[t][k] = A[k];
-    __syncthreads();
-    if (t == 0) {
-        double run[6] = {0, 0, 0, 0, 0, 0};
-        for (int u = kScanThreads - 1; u >= 0; --u)
-            for (int k = 0; k < 6; ++k) {
-                double v = S[u][k];
-                S[u][k] = run[k];
-                run[k] += v;
-            }
-    }
-    __syncthreads();
-    for (int k = 0; k < 6; ++k) A[k] = S[t][k];
-    for (int c = c1 - 1; c >= c0; --c)
-        for (int k = 0; k < 6; ++k) {
-            d.chunkSuf[6 * c + k] = A[k];
-            A[k] += d.chunkS[6 * c + k];
-        }
-}
-
-// P^agg_k = P_k + P^agg_{k+1} (Sec. 3.5); tau_k = u_k . T^agg_k + (p_k x u_k) . F^agg_k
-__global__ void k_torque_apply(const DevChain d) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= d.nlink_chunks || d.status->done) return;
-    int h0 = c * kLinkChunk, h1 = min(d.L, h0 + kLinkChunk);
-    double A[6];
-    for (int k = 0; k < 6; ++k) A[k] = d.chunkSuf[6 * c + k];
-    double tmax = 0.0;
-    bool bad = false;
-    for (int h = h1 - 1; h >= h0; --h) {
-        if (h < 1) break;
-        for (int k = 0; k < 6; ++k) A[k] += d.P[6 * h + k];
-        int j = h - 1;  // joint k = h (1-based) moves links h..l
-        const double* u = &d.ucur[3 * j];
-        const double* p = &d.pcur[3 * j];
-        double px = p[1] * u[2] - p[2] * u[1], py = p[2] * u[0] - p[0] * u[2], pz = p[0] * u[1] - p[1] * u[0];
-        double t = u[0] * A[0] + u[1] * A[1] + u[2] * A[2] + px * A[3] + py * A[4] + pz * A[5];
-        d.tau[j] = t;
-        if (!isfinite(t)) bad = true;
-        tmax = fmax(tmax, fabs(t));
-    }
-    if (bad) atomicOr(&d.status->error, kErrNonfinite);
-    else if (tmax > 0.0) atomicMax(&d.status->max_abs_tau, (unsigned long long)__double_as_longlong(tmax));
-}
-
-// ================================================================ A10: energies
-__global__ void k_energy(const DevChain d) {
-    __shared__ double s[3][256];
-    if (d.status->done) return;
-    double e0 = 0, e1 = 0, e2 = 0;
-    for (int b = threadIdx.x; b < d.pair_blocks; b += blockDim.x) { e0 += d.Epair[2 * b]; e1 += d.Epair[2 * b + 1]; }
-    if (d.prm.solvation)
-        for (int b = threadIdx.x; b < d.sasa_blocks; b += blockDim.x) e2 += d.Ecav[b];
-    s[0][threadIdx.x] = e0; s[1][threadIdx.x] = e1; s[2][threadIdx.x] = e2;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o)
-            for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) { d.E[0] = s[0][0]; d.E[1] = s[1][0]; d.E[2] = s[2][0]; }
-}
-
-// ================================================================ A9: step
-__global__ void k_step(const DevChain d) {
-    __shared__ double smax[4];
-    Status* st = d.status;
-    if (st->done) return;
-    if (st->error) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->done = 1;
-        return;
-    }
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    double ad = 0.0;
-    if (j < d.l) {
-        double t = d.tau[j], dt;
-        if (d.prm.step_mode == KCM_STEP_NORMALIZED) {
-            double tm = __longlong_as_double((long long)st->max_abs_tau);
-            dt = tm > 0.0 ? d.prm.kappa * t / tm : 0.0;
-        } else {
-            dt = fmin(fmax(d.prm.kappa * t, -d.prm.dtheta_max), d.prm.dtheta_max);
-        }
-        d.theta[j] += dt;
-        d.dtheta[j] = dt;
-        ad = fabs(dt);
-    }
-    for (int o = 16; o > 0; o >>= 1) ad = fmax(ad, __shfl_down_sync(0xffffffffu, ad, o));
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = ad;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, smax[k]);
-        atomicMax(&st->max_dtheta, (unsigned long long)__double_as_longlong(m));
-        __threadfence();
-        unsigned int ticket = atomicAdd(&st->ticket, 1u);
-        if (ticket == gridDim.x - 1) {  // last block: close the iteration
-            __threadfence();
-            double mall = __longlong_as_double((long long)atomicAdd(&st->max_dtheta, 0ULL));
-            st->last_max_dtheta = mall;
-            st->iters += 1;
-            if (mall < d.prm.conv_tol) st->done = 1;
-            st->max_dtheta = 0ULL;
-            st->max_abs_tau = 0ULL;
-            st->ticket = 0u;
-        }
+        if (e != 0.0) atomicAdd(&d.status->E[2], e);
     }
 }
 
@@ -1101,6 +819,9 @@ __global__ void k_reset_loop(const DevChain d, int full) {
     st->max_dtheta = 0ULL;
     st->max_abs_tau = 0ULL;
     st->last_max_dtheta = 0.0;
+    st->E[0] = 0.0;
+    st->E[1] = 0.0;
+    st->E[2] = 0.0;
     if (full) {
         st->ticket_bbox = 0u;
         for (int i = 0; i < 3; ++i) { st->bbox[i] = ~0ULL; st->bbox[3 + i] = 0ULL; }
@@ -1123,12 +844,6 @@ inline int blocks(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 void launch_init_status(DevChain& d, cudaStream_t s) { k_reset_loop<<<1, 1, 0, s>>>(d, 1); }
 void launch_reset_loop(DevChain& d, cudaStream_t s) { k_reset_loop<<<1, 1, 0, s>>>(d, 0); }
 
-void launch_fk(DevChain& d, cudaStream_t s) {
-    k_fk_local<<<blocks(d.nfk_chunks, kFkTpb), kFkTpb, 0, s>>>(d);
-    k_fk_scan<<<1, kScanThreads, 0, s>>>(d);
-    k_fk_apply<<<blocks(d.nfk_chunks, kFkTpb), kFkTpb, 0, s>>>(d);
-    k_fk_atoms<<<blocks(d.n, kApplyTpb), kApplyTpb, 0, s>>>(d);
-}
 
 void launch_binning(DevChain& d, cudaStream_t s) {
     k_bbox<<<d.bbox_blocks, 256, 0, s>>>(d);
@@ -1163,15 +878,8 @@ void launch_sasa(DevChain& d, cudaStream_t s) {
     }
 }
 
-void launch_torques(DevChain& d, cudaStream_t s) {
-    k_wrench<<<blocks(d.nlink_chunks, kFkTpb), kFkTpb, 0, s>>>(d);
-    k_torque_scan<<<1, kScanThreads, 0, s>>>(d);
-    k_torque_apply<<<blocks(d.nlink_chunks, kFkTpb), kFkTpb, 0, s>>>(d);
-}
 
-void launch_energy(DevChain& d, cudaStream_t s) { k_energy<<<1, 256, 0, s>>>(d); }
 
-void launch_step(DevChain& d, cudaStream_t s) { k_step<<<blocks(d.l, 128), 128, 0, s>>>(d); }
 
 void launch_force_out(DevChain& d, cudaStream_t s) { k_force_out<<<blocks(3LL * d.n, 256), 256, 0, s>>>(d); }
 

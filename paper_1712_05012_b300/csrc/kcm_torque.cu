@@ -1,0 +1,244 @@
+// A7-A9: link wrenches, suffix sums over links, joint torques and the kinetostatic step (FP64).
+//
+// Wrench of link h about the origin, P_h = [sum r x F ; sum F] (eq. KCM_01/02): one thread per atom
+// forms r x F, and a segmented shuffle sum adds the atoms of each link within the warp (a link has at
+// most 11 contiguous atoms, so it meets at most two warps; each warp adds its part to P_h, and two
+// FP64 additions onto zero commute, so the result does not depend on their order).
+// P^agg_k = sum_{h >= k} P_h (Sec. 3.5) is a reverse scan: Kogge-Stone within warps of 32 links, one
+// warp over the tile sums, then tau_k = u_k . T^agg_k + (p_k x u_k) . F^agg_k (eq. KCM_05/06).
+// In the clamped step mode the same thread applies dtheta_k = clamp(kappa tau_k, +-dtheta_max)
+// (eq. KCM_07); the last block to finish closes the iteration.
+#include <cuda_runtime.h>
+
+#include "kcm_common.cuh"
+#include "kcm_device.h"
+
+namespace kcm {
+
+namespace {
+using namespace dev;
+
+__global__ void __launch_bounds__(128) k_wrench(const DevChain d) {
+    if (d.status->done) return;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    int h = -1 - lane;  // distinct keys for lanes past the last atom
+    if (a < d.n) {
+        double fx = d.Fpair[3 * a], fy = d.Fpair[3 * a + 1], fz = d.Fpair[3 * a + 2];
+        if (d.prm.solvation) {
+            fx += (double)d.Fcav[3 * a] * kFxInv;
+            fy += (double)d.Fcav[3 * a + 1] * kFxInv;
+            fz += (double)d.Fcav[3 * a + 2] * kFxInv;
+        }
+        const double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
+        v[0] = y * fz - z * fy;
+        v[1] = z * fx - x * fz;
+        v[2] = x * fy - y * fx;
+        v[3] = fx; v[4] = fy; v[5] = fz;
+        h = d.link[a];
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int hp = __shfl_up_sync(0xffffffffu, h, off);
+        const bool take = lane >= off && hp == h;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const double y = __shfl_up_sync(0xffffffffu, v[k], off);
+            if (take) v[k] += y;
+        }
+    }
+    const int hn = __shfl_down_sync(0xffffffffu, h, 1);
+    if (a < d.n && (lane == 31 || hn != h)) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) atomicAdd(&d.P[6 * (size_t)h + k], v[k]);
+    }
+}
+
+// reverse inclusive scan of P within tiles of 32 links (links 1..l; link 0 has no joint)
+__global__ void __launch_bounds__(32) k_suffix_tile(const DevChain d) {
+    if (d.status->done) return;
+    const int lane = threadIdx.x;
+    const int h = blockIdx.x * 32 + lane;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (h >= 1 && h < d.L) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = d.P[6 * (size_t)h + k];
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const double y = __shfl_down_sync(0xffffffffu, v[k], off);
+            if (lane + off < 32) v[k] += y;
+        }
+    }
+    if (h < d.L) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) d.lane_suf[6 * (size_t)h + k] = v[k];
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) d.tileS[6 * (size_t)blockIdx.x + k] = v[k];
+    }
+}
+
+// exclusive suffix sums of the tile sums, 32 tiles per round from the end (one warp)
+__global__ void __launch_bounds__(32) k_suffix_tilescan(const DevChain d) {
+    if (d.status->done) return;
+    const int lane = threadIdx.x;
+    double carry[6] = {0, 0, 0, 0, 0, 0};
+    for (int top = d.ltiles; top > 0; top -= 32) {
+        const int t = top - 32 + lane;
+        double x[6] = {0, 0, 0, 0, 0, 0};
+        if (t >= 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) x[k] = d.tileS[6 * (size_t)t + k];
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const double y = __shfl_down_sync(0xffffffffu, x[k], off);
+                if (lane + off < 32) x[k] += y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            double e = __shfl_down_sync(0xffffffffu, x[k], 1);
+            if (lane == 31) e = 0.0;
+            if (t >= 0) d.tileSuf[6 * (size_t)t + k] = e + carry[k];
+            carry[k] += __shfl_sync(0xffffffffu, x[k], 0);
+        }
+    }
+}
+
+// tau_k from P^agg; with STEP the clamped step and the end of the iteration
+template <bool STEP>
+__global__ void __launch_bounds__(128) k_torque(const DevChain d) {
+    __shared__ unsigned long long smax[4];
+    __shared__ bool last;
+    Status* st = d.status;
+    if (st->done) return;
+    const int jj = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long adt = 0ULL, atau = 0ULL;  // bit patterns of non-negative doubles
+    bool bad = false;
+    if (jj < d.l) {
+        const int h = jj + 1, tile = h >> 5;  // joint jj moves links jj+1 .. l
+        double A[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) A[k] = d.lane_suf[6 * (size_t)h + k] + d.tileSuf[6 * (size_t)tile + k];
+        const double* u = &d.ucur[3 * jj];
+        const double* p = &d.pcur[3 * jj];
+        const double px = p[1] * u[2] - p[2] * u[1], py = p[2] * u[0] - p[0] * u[2], pz = p[0] * u[1] - p[1] * u[0];
+        const double t = u[0] * A[0] + u[1] * A[1] + u[2] * A[2] + px * A[3] + py * A[4] + pz * A[5];
+        d.tau[jj] = t;
+        bad = !isfinite(t);
+        atau = (unsigned long long)__double_as_longlong(fabs(t));
+        if (STEP && !bad) {
+            const double dt = fmin(fmax(d.prm.kappa * t, -d.prm.dtheta_max), d.prm.dtheta_max);
+            d.theta[jj] += dt;
+            d.dtheta[jj] = dt;
+            adt = (unsigned long long)__double_as_longlong(fabs(dt));
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->error, kErrNonfinite);
+    for (int o = 16; o > 0; o >>= 1) {
+        adt = max(adt, __shfl_down_sync(0xffffffffu, adt, o));
+        atau = max(atau, __shfl_down_sync(0xffffffffu, atau, o));
+    }
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = adt;
+    if ((threadIdx.x & 31) == 0 && atau) atomicMax(&st->max_abs_tau, atau);
+    if (!STEP) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = max(m, smax[k]);
+        atomicMax(&st->max_dtheta, m);
+        __threadfence();
+        last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {  // the last block closes the iteration
+        __threadfence();
+        const double mall = __longlong_as_double((long long)atomicAdd(&st->max_dtheta, 0ULL));
+        if (st->error) {
+            st->done = 1;  // a failed iteration leaves theta as the kernels found it at the first error
+        } else {
+            st->last_max_dtheta = mall;
+            st->iters += 1;
+            if (mall < d.prm.conv_tol) st->done = 1;
+        }
+        st->max_dtheta = 0ULL;
+        st->max_abs_tau = 0ULL;
+        st->ticket = 0u;
+    }
+}
+
+// the paper's normalised step (eq. KCM_07): dtheta_k = kappa tau_k / max |tau|
+__global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
+    __shared__ unsigned long long smax[4];
+    __shared__ bool last;
+    Status* st = d.status;
+    if (st->done) return;
+    if (st->error) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->done = 1;
+        return;
+    }
+    const int jj = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long adt = 0ULL;
+    if (jj < d.l) {
+        const double tm = __longlong_as_double((long long)st->max_abs_tau);
+        const double dt = tm > 0.0 ? d.prm.kappa * d.tau[jj] / tm : 0.0;
+        d.theta[jj] += dt;
+        d.dtheta[jj] = dt;
+        adt = (unsigned long long)__double_as_longlong(fabs(dt));
+    }
+    for (int o = 16; o > 0; o >>= 1) adt = max(adt, __shfl_down_sync(0xffffffffu, adt, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = adt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = max(m, smax[k]);
+        atomicMax(&st->max_dtheta, m);
+        __threadfence();
+        last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const double mall = __longlong_as_double((long long)atomicAdd(&st->max_dtheta, 0ULL));
+        st->last_max_dtheta = mall;
+        st->iters += 1;
+        if (mall < d.prm.conv_tol) st->done = 1;
+        st->max_dtheta = 0ULL;
+        st->max_abs_tau = 0ULL;
+        st->ticket = 0u;
+    }
+}
+
+}  // namespace
+
+void launch_torques(DevChain& d, cudaStream_t s) {
+    cudaMemsetAsync(d.P, 0, sizeof(double) * 6 * (size_t)d.L, s);
+    k_wrench<<<(d.n + 127) / 128, 128, 0, s>>>(d);
+    k_suffix_tile<<<d.ltiles, 32, 0, s>>>(d);
+    k_suffix_tilescan<<<1, 32, 0, s>>>(d);
+    k_torque<false><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+}
+
+// torques plus the step of one iteration (the evaluation kernels must already be enqueued)
+void launch_torques_step(DevChain& d, cudaStream_t s) {
+    cudaMemsetAsync(d.P, 0, sizeof(double) * 6 * (size_t)d.L, s);
+    k_wrench<<<(d.n + 127) / 128, 128, 0, s>>>(d);
+    k_suffix_tile<<<d.ltiles, 32, 0, s>>>(d);
+    k_suffix_tilescan<<<1, 32, 0, s>>>(d);
+    if (d.prm.step_mode == KCM_STEP_CLAMP) {
+        k_torque<true><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+    } else {
+        k_torque<false><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+        k_step_normalized<<<(d.l + 127) / 128, 128, 0, s>>>(d);
+    }
+}
+
+}  // namespace kcm

@@ -73,8 +73,8 @@ EXPORTS = [
     "kcm_topology_natoms", "kcm_strerror", "kcm_last_error", "kcm_step_timed", "kcm_torques_noalloc",
 ]
 NOALLOC_MAX_LINKS = 32768
-NUM_STAGES = 7
-STAGES = ("kinematics", "binning", "pairs", "solvation", "torques", "energy", "step")
+NUM_STAGES = 5
+STAGES = ("kinematics", "binning", "pairs", "solvation", "torques_step")
 
 _lib = None
 _dp = C.POINTER(C.c_double)
