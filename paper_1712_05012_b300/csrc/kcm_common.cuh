@@ -71,10 +71,21 @@ __device__ __forceinline__ int warp_max(int v) {
     return v;
 }
 
-// FP32 pair term to int64 fixed point with kPairFx fractional bits (round to nearest, symmetric in
-// sign, so the terms of (i, j) and (j, i) stay exact negatives); |v| < kPairFxMax keeps a sum of
-// tens of terms inside int64
-__device__ __forceinline__ long long to_fixed(float v) { return __float2ll_rn(v * 16777216.0f); }
+// Exact fixed-point pieces of an FP32 pair term v, |v| < 2^22, with FP32 adds and integer subtracts
+// only (B300 runs 64-bit conversions on its slow FP64 pipe). Adding 1.5 * 2^23 moves v into the
+// binade where the float spacing is 1, so the sum is v rounded to an integer (ties to even) and its
+// bit pattern minus that of 1.5 * 2^23 is that integer n; f = v - n is exact and |f| <= 1/2; the
+// same trick on f * 2^23 gives the fraction in units of 2^-23. Both roundings are symmetric in sign,
+// so the pieces of the (i, j) and (j, i) terms are exact negatives.
+constexpr float kMagic23 = 12582912.0f;  // 1.5 * 2^23
+constexpr int kMagic23Bits = 0x4B400000;
+__device__ __forceinline__ void fx_add(float v, int& hi, int& lo) {
+    const float t = v + kMagic23;
+    const float f = v - (t - kMagic23);
+    const float u = fmaf(f, 8388608.0f, kMagic23);
+    hi += __float_as_int(t) - kMagic23Bits;
+    lo += __float_as_int(u) - kMagic23Bits;
+}
 
 // The FP64 overlap test of Algorithm 1: || (r_a + Roff_a q_k) - r_b - dr e_s ||^2 <= Roff_b^2,
 // written with explicit roundings so that the FP64 kernel and the FP32 guard-band recheck take

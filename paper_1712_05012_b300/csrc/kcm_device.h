@@ -52,9 +52,9 @@ struct Status {
 constexpr int kPairWarps = 4;         // home atoms (warps) per block of the pair kernel
 constexpr int kScanCells = 2048;      // cells per block of the cell-count scan
 constexpr int kScanThreadsBig = 256;
-constexpr int kPairFx = 24;           // fixed-point fraction bits of mixed-mode pair forces and energies
-constexpr double kPairFxInv = 1.0 / 16777216.0;
-constexpr float kPairFxMax = 1.0e10f;  // |pair term| limit of the fixed-point sums (2^63 / 2^24 = 5.5e11)
+constexpr double kPairFxInv = 1.0 / 8388608.0;  // unit of the fraction sums of mixed-mode pair forces
+constexpr float kPairFxMax = 4194304.0f;        // |pair term| below which it is summed in fixed point (2^22)
+constexpr int kPairFoldRounds = 256;            // candidate rounds between folds of the int32 lane sums
 constexpr int kSasaWarps = 4;
 constexpr int kApplyTpb = 64;
 

@@ -306,12 +306,17 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             px = p.x; py = p.y; pz = p.z; qi = p.w; sei = q.y; Ri = q.z; Roi = q.w;
         }
         const unsigned long long exa = d.exm[a], m14a = d.m14m[a];
-        long long ffx = 0, ffy = 0, ffz = 0, fel = 0, fvd = 0;  // mixed: fixed point
-        float ovx = 0, ovy = 0, ovz = 0, ove = 0, ovv = 0;      // mixed: terms beyond the fixed-point range
+        long long Hx = 0, Hy = 0, Hz = 0, Lx = 0, Ly = 0, Lz = 0;  // mixed: folded fixed-point sums
+        int hix = 0, hiy = 0, hiz = 0;                           // mixed: integer parts (kcal/mol/A)
+        int lox = 0, loy = 0, loz = 0;                           // mixed: fractions in units of 2^-23
+        float ovx = 0, ovy = 0, ovz = 0, ove = 0, ovv = 0;      // mixed: oversized terms; energies
         double dfx = 0, dfy = 0, dfz = 0;                        // FP64 mode
         int t = 0;
         const unsigned lt = (1u << lane) - 1u;
-        for (int base = 0; base < total; base += 32) {
+        for (int cb = 0; cb < total; cb += 32 * kPairFoldRounds) {
+        // at most one term per lane and round: kPairFoldRounds terms of |piece| <= 2^22 fit in int32
+        const int ce = min(total, cb + 32 * kPairFoldRounds);
+        for (int base = cb; base < ce; base += 32) {
             const int k2 = base + lane;
             bool isn = false;
             int b = -1;
@@ -369,7 +374,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                         if (inE || inV) {
                             // symmetric in (i, j): products of the two atoms' constants are formed first
                             const R we = is14 ? w14e : (R)1, wv = is14 ? w14v : (R)1;
-                            const R inv2 = (R)1 / d2;
+                            R inv2;
+                            if constexpr (MIXED) inv2 = __frcp_rn(d2); else inv2 = 1.0 / d2;
                             R coef = 0, e_el = 0, e_vd = 0;
                             if (inE) {
                                 const R qq = (we * K) * (qi * qj);
@@ -391,16 +397,13 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                             if constexpr (MIXED) {
                                 const float fx1 = coef * ddx, fy1 = coef * ddy, fz1 = coef * ddz;
                                 if (fabsf(fx1) < kPairFxMax && fabsf(fy1) < kPairFxMax && fabsf(fz1) < kPairFxMax) {
-                                    ffx += to_fixed(fx1);
-                                    ffy += to_fixed(fy1);
-                                    ffz += to_fixed(fz1);
+                                    fx_add(fx1, hix, lox);
+                                    fx_add(fy1, hiy, loy);
+                                    fx_add(fz1, hiz, loz);
                                 } else {  // clash-sized (or non-finite) term: plain float sum
                                     ovx += fx1; ovy += fy1; ovz += fz1;
                                 }
-                                if (count_e) {
-                                    if (fabsf(e_el) < kPairFxMax) fel += to_fixed(e_el); else ove += e_el;
-                                    if (fabsf(e_vd) < kPairFxMax) fvd += to_fixed(e_vd); else ovv += e_vd;
-                                }
+                                if (count_e) { ove += e_el; ovv += e_vd; }
                             } else {
                                 dfx += coef * ddx; dfy += coef * ddy; dfz += coef * ddz;
                                 if (count_e) { Eel += e_el; Evdw += e_vd; }
@@ -420,17 +423,22 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             ncount += __popc(bm);
         }
         if constexpr (MIXED) {
-            ffx = warp_sum(ffx); ffy = warp_sum(ffy); ffz = warp_sum(ffz);
-            fel = warp_sum(fel); fvd = warp_sum(fvd);
+            Hx += hix; Hy += hiy; Hz += hiz; Lx += lox; Ly += loy; Lz += loz;
+            hix = hiy = hiz = lox = loy = loz = 0;
+        }
+        }
+        if constexpr (MIXED) {
+            Hx = warp_sum(Hx); Hy = warp_sum(Hy); Hz = warp_sum(Hz);
+            Lx = warp_sum(Lx); Ly = warp_sum(Ly); Lz = warp_sum(Lz);
             ovx = warp_sum(ovx); ovy = warp_sum(ovy); ovz = warp_sum(ovz);
             ove = warp_sum(ove); ovv = warp_sum(ovv);
             if (lane == 0) {
-                d.Fpair[3 * a] = (double)ffx * kPairFxInv + (double)ovx;
-                d.Fpair[3 * a + 1] = (double)ffy * kPairFxInv + (double)ovy;
-                d.Fpair[3 * a + 2] = (double)ffz * kPairFxInv + (double)ovz;
+                d.Fpair[3 * a] = (double)Hx + (double)Lx * kPairFxInv + (double)ovx;
+                d.Fpair[3 * a + 1] = (double)Hy + (double)Ly * kPairFxInv + (double)ovy;
+                d.Fpair[3 * a + 2] = (double)Hz + (double)Lz * kPairFxInv + (double)ovz;
             }
-            Eel = (double)fel * kPairFxInv + (double)ove;
-            Evdw = (double)fvd * kPairFxInv + (double)ovv;
+            Eel = (double)ove;
+            Evdw = (double)ovv;
         } else {
             dfx = warp_sum(dfx); dfy = warp_sum(dfy); dfz = warp_sum(dfz);
             Eel = warp_sum(Eel); Evdw = warp_sum(Evdw);
