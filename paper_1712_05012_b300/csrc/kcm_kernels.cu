@@ -599,29 +599,32 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
 
 // Mixed-precision Algorithm 1. The test of sample point k of atom i against neighbour j,
 // |Roff_i Q_k - o_j|^2 <= Roff_j^2 with o_j = r_j - r_i, is for a unit Q_k the same as
-// Q_k . o_j >= h_j,  h_j = (Roff_i^2 + |o_j|^2 - Roff_j^2) / (2 Roff_i),
+// m_kj = Q_k . o_j - h_j >= 0,  h_j = (Roff_i^2 + |o_j|^2 - Roff_j^2) / (2 Roff_i),
 // and with j displaced by dr e_s it is Q_k . o_j + dr Q_k,s >= h_js, h_js = h_j + (2 dr o_j,s + dr^2)
-// / (2 Roff_i). A displacement can change the state of a point only where the two squared
-// distances straddle Roff_j^2, i.e. within |Q.o - h_j| <= (2 dr Roff_j + 3 dr^2) / (2 Roff_i) of the cap
-// boundary; step 1 records those (point, neighbour) candidates and step 2 re-tests only them. That
-// gives exactly Algorithm 1's exchanges: an exposed point gains coverage only from a candidate, and a
-// critically overlapped point loses it only if its critical neighbour is a candidate. FP32 decisions
-// within the guard band gd of the boundary are re-decided in FP64 by covers64, as in the FP64 kernel.
+// / (2 Roff_i). A displacement can change a point's state only where the two squared distances
+// straddle Roff_j^2, i.e. within |m_kj| <= (2 dr Roff_j + 3 dr^2) / (2 Roff_i) of the cap boundary.
+//
+// Step 1 keeps, per point, only max_j m_kj (covered iff > 0) and min_j |m_kj|. A point whose minimum
+// is outside that band (plus the FP32 guard band gd) takes no part in step 2 and its coverage is
+// decided; the few points inside it are re-scanned one per lane, which gives their exact count C,
+// their critical neighbour, FP64 re-decisions of guard-band tests (covers64, as in the FP64
+// kernel), and step 2 on their near-boundary neighbours. The exchanges are exactly Algorithm 1's:
+// an exposed point gains coverage only from a near neighbour, and a critically overlapped point loses
+// it only if its critical neighbour is near.
 constexpr int kPtsPerLane = 8;                  // sample points each lane holds in registers
 constexpr int kBatch = 32 * kPtsPerLane;         // points per batch (256)
-constexpr int kCandMax = 256;                    // boundary-band candidates per batch and warp
 
 __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d) {
     __shared__ float4 s_o[kSasaWarps][kMaxNbr];   // o_j, h_j
-    __shared__ float4 s_h[kSasaWarps][kMaxNbr];   // h_jx, h_jy, h_jz (displaced thresholds)
     __shared__ int s_idx[kSasaWarps][kMaxNbr];
     __shared__ int s_cnt[kSasaWarps][3 * kMaxNbr];
-    __shared__ unsigned short s_state[kSasaWarps][kBatch];  // C (2 bits, saturated) | critical j << 2
-    __shared__ unsigned int s_cand[kSasaWarps][kCandMax];   // k_local << 8 | j
-    __shared__ int s_ncand[kSasaWarps];
+    __shared__ unsigned short s_near[kSasaWarps][kBatch];
     __shared__ double s_E[kSasaWarps];
+    __shared__ unsigned s_ticket;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
+    if (threadIdx.x == 0) s_ticket = 0u;
+    __syncthreads();
     double Ea = 0.0;
     if (a < d.n && !d.status->done) {
         const double G0a = d.G0[a];
@@ -639,24 +642,19 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
             for (int j = lane; j < cnt; j += 32) {
                 const float4 o = d.nbr_off[(size_t)a * kMaxNbr + j];  // r_j - r_i, Roff_j^2
                 const float oo = o.x * o.x + o.y * o.y + o.z * o.z;
-                const float h = (Ra * Ra + oo - o.w) * inv2R;
-                const float dd = drf * drf;
-                s_o[w][j] = make_float4(o.x, o.y, o.z, h);
-                s_h[w][j] = make_float4(h + (2.0f * drf * o.x + dd) * inv2R, h + (2.0f * drf * o.y + dd) * inv2R,
-                                        h + (2.0f * drf * o.z + dd) * inv2R, 0.0f);
+                s_o[w][j] = make_float4(o.x, o.y, o.z, (Ra * Ra + oo - o.w) * inv2R);
                 s_idx[w][j] = d.nbr[(size_t)a * kMaxNbr + j];
                 s_cnt[w][3 * j] = 0; s_cnt[w][3 * j + 1] = 0; s_cnt[w][3 * j + 2] = 0;
                 rmax2 = fmaxf(rmax2, o.w);
             }
             for (int q = 16; q > 0; q >>= 1) rmax2 = fmaxf(rmax2, __shfl_xor_sync(0xffffffffu, rmax2, q));
-            // band of Q.o around h_j where a displacement by dr can change a point's state, widened
-            // to the largest neighbour radius so that it is one number per atom
+            // band of m around 0 where a displacement by dr can change a point's state, widened to the
+            // largest neighbour radius so that it is one number per atom
             const float band = (2.0f * drf * sqrtf(rmax2) + 3.0f * drf * drf) * inv2R + gd;
             __syncwarp();
             const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
             int ncov = 0, nguard = 0;
             unsigned long long ntest = 0;
-            bool any_overflow = false;
             auto recheck = [&](int j, int k, int s) -> bool {  // FP64, identical to the FP64 kernel
                 ++nguard;
                 const int b = s_idx[w][j];
@@ -666,19 +664,8 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 const double qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
                 return covers64(qx, qy, qz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
             };
-            auto covers_s = [&](int j, int k, int s) -> bool {  // neighbour j displaced along s
-                const float4 o = s_o[w][j];
-                const float4 hh = s_h[w][j];
-                const float Qx = d.Q32[3 * k], Qy = d.Q32[3 * k + 1], Qz = d.Q32[3 * k + 2];
-                const float dot = Qx * o.x + Qy * o.y + Qz * o.z;
-                const float m = s == 0 ? dot + drf * Qx - hh.x : (s == 1 ? dot + drf * Qy - hh.y : dot + drf * Qz - hh.z);
-                if (fabsf(m) > gd) return m >= 0.0f;
-                return recheck(j, k, s);
-            };
             for (int kb = 0; kb < d.N; kb += kBatch) {
-                if (lane == 0) s_ncand[w] = 0;
-                __syncwarp();
-                float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane];
+                float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane], mx[kPtsPerLane], mn[kPtsPerLane];
                 unsigned valid = 0;
 #pragma unroll
                 for (int p = 0; p < kPtsPerLane; ++p) {
@@ -688,102 +675,79 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                     qy[p] = v ? d.Q32[3 * k + 1] : 0.0f;
                     qz[p] = v ? d.Q32[3 * k + 2] : 0.0f;
                     valid |= v ? (1u << p) : 0u;
+                    mx[p] = -INFINITY;
+                    mn[p] = INFINITY;
                 }
-                // step 1, neighbour by neighbour, for the lane's 8 points at once: `in` has bit p set
-                // when neighbour j covers point p; c1 / c2 are the bit planes C >= 1 and C >= 2; the
-                // critical neighbour is written when a point is first covered
-                unsigned c1 = 0, c2 = 0;
-                int crit[kPtsPerLane];
-#pragma unroll
-                for (int p = 0; p < kPtsPerLane; ++p) crit[p] = 0;
+                // step 1: max m and min |m| of each point over all neighbours
+#pragma unroll 2
                 for (int j = 0; j < cnt; ++j) {
                     const float4 o = s_o[w][j];
-                    float m[kPtsPerLane];
-                    unsigned in = 0, near = 0;
 #pragma unroll
                     for (int p = 0; p < kPtsPerLane; ++p) {
-                        m[p] = fmaf(qz[p], o.z, fmaf(qy[p], o.y, fmaf(qx[p], o.x, -o.w)));
-                        in |= (m[p] > 0.0f) ? (1u << p) : 0u;
-                        near |= (fabsf(m[p]) <= band) ? (1u << p) : 0u;
-                    }
-                    near &= valid;
-                    if (near) {  // rare: record candidates, re-decide guard-band tests in FP64
-#pragma unroll
-                        for (int p = 0; p < kPtsPerLane; ++p) {
-                            if (near & (1u << p)) {
-                                const int slot = atomicAdd(&s_ncand[w], 1);
-                                if (slot < kCandMax) s_cand[w][slot] = ((unsigned)(lane + 32 * p) << 8) | (unsigned)j;
-                                if (fabsf(m[p]) <= gd) {
-                                    const bool r64 = recheck(j, kb + lane + 32 * p, -1);
-                                    in = r64 ? (in | (1u << p)) : (in & ~(1u << p));
-                                }
-                            }
-                        }
-                    }
-                    in &= valid;
-                    unsigned first = in & ~c1;
-                    c2 |= c1 & in;
-                    c1 |= in;
-                    while (first) {
-                        const int p = __ffs(first) - 1;
-                        first &= first - 1;
-#pragma unroll
-                        for (int q = 0; q < kPtsPerLane; ++q) crit[q] = (q == p) ? j : crit[q];
+                        const float m = fmaf(qz[p], o.z, fmaf(qy[p], o.y, fmaf(qx[p], o.x, -o.w)));
+                        mx[p] = fmaxf(mx[p], m);
+                        mn[p] = fminf(mn[p], fabsf(m));
                     }
                 }
-                int nvalid = __popc(valid);
-                ntest += (unsigned long long)nvalid * cnt;
+                ntest += (unsigned long long)__popc(valid) * cnt;
+                // decided points are counted; near-boundary points are listed for the re-scan
+                int nnear = 0;
+                const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
                 for (int p = 0; p < kPtsPerLane; ++p) {
-                    if (valid & (1u << p)) {
-                        const int Cs = (c2 >> p) & 1 ? 2 : ((c1 >> p) & 1);
-                        ncov += Cs >= 1;
-                        s_state[w][lane + 32 * p] = (unsigned short)(Cs | (crit[p] << 2));
-                    }
+                    const bool v = (valid >> p) & 1u;
+                    const bool nr = v && mn[p] <= band;
+                    if (v && !nr) ncov += mx[p] > 0.0f;
+                    const unsigned bm = __ballot_sync(0xffffffffu, nr);
+                    if (nr) s_near[w][nnear + __popc(bm & lt)] = (unsigned short)(lane + 32 * p);
+                    nnear += __popc(bm);
                 }
                 __syncwarp();
-                // step 2 on the candidates: an exposed point gains coverage from a displaced candidate;
-                // a critically overlapped point loses it only through its critical neighbour
-                const int nc = s_ncand[w];
-                if (nc <= kCandMax) {
-                    for (int e = lane; e < nc; e += 32) {
-                        const unsigned cv = s_cand[w][e];
-                        const int kl = (int)(cv >> 8), j = (int)(cv & 0xffu);
-                        const int k = kb + kl;
-                        const unsigned st = s_state[w][kl];
-                        const int Cs = st & 3, cr = st >> 2;
-                        if (Cs == 0) {
-                            for (int s = 0; s < 3; ++s)
-                                if (covers_s(j, k, s)) atomicAdd(&s_cnt[w][3 * j + s], 1);
-                            ntest += 3;
-                        } else if (Cs == 1 && cr == j) {
-                            for (int s = 0; s < 3; ++s)
-                                if (!covers_s(j, k, s)) atomicAdd(&s_cnt[w][3 * j + s], -1);
-                            ntest += 3;
+                // re-scan of the near-boundary points, one per lane: exact step 1, then step 2
+                for (int e = lane; e < nnear; e += 32) {
+                    const int k = kb + s_near[w][e];
+                    const float Qx = d.Q32[3 * k], Qy = d.Q32[3 * k + 1], Qz = d.Q32[3 * k + 2];
+                    int C = 0, crit = -1;
+                    for (int j = 0; j < cnt; ++j) {
+                        const float4 o = s_o[w][j];
+                        const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, -o.w)));
+                        bool in = m > 0.0f;
+                        if (fabsf(m) <= gd) in = recheck(j, k, -1);
+                        if (in) {
+                            if (C == 0) crit = j;
+                            ++C;
                         }
                     }
-                } else {  // candidate list full: re-test every neighbour of every point with C <= 1
-                    any_overflow = true;
-                    for (int p = 0; p < kPtsPerLane; ++p) {
-                        const int kl = lane + 32 * p, k = kb + kl;
-                        if (k >= d.N) continue;
-                        const unsigned st = s_state[w][kl];
-                        const int Cs = st & 3, cr = st >> 2;
-                        if (Cs == 0) {
-                            for (int j = 0; j < cnt; ++j)
-                                for (int s = 0; s < 3; ++s)
-                                    if (covers_s(j, k, s)) atomicAdd(&s_cnt[w][3 * j + s], 1);
-                            ntest += 3 * cnt;
-                        } else if (Cs == 1) {
+                    ncov += C >= 1;
+                    // step 2 against neighbour j displaced along s; hs is h_js
+                    auto covers_s = [&](int j, int s) -> bool {
+                        const float4 o = s_o[w][j];
+                        const float os = s == 0 ? o.x : (s == 1 ? o.y : o.z);
+                        const float Qs = s == 0 ? Qx : (s == 1 ? Qy : Qz);
+                        const float hs = o.w + (2.0f * drf * os + drf * drf) * inv2R;
+                        const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, fmaf(drf, Qs, -hs))));
+                        ++ntest;
+                        if (fabsf(m) > gd) return m >= 0.0f;
+                        return recheck(j, k, s);
+                    };
+                    auto near_j = [&](int j) -> bool {
+                        const float4 o = s_o[w][j];
+                        const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, -o.w)));
+                        return fabsf(m) <= band;
+                    };
+                    if (C == 0) {
+                        for (int j = 0; j < cnt; ++j) {
+                            if (!near_j(j)) continue;
                             for (int s = 0; s < 3; ++s)
-                                if (!covers_s(cr, k, s)) atomicAdd(&s_cnt[w][3 * cr + s], -1);
-                            ntest += 3;
+                                if (covers_s(j, s)) atomicAdd(&s_cnt[w][3 * j + s], 1);
                         }
+                    } else if (C == 1 && near_j(crit)) {
+                        for (int s = 0; s < 3; ++s)
+                            if (!covers_s(crit, s)) atomicAdd(&s_cnt[w][3 * crit + s], -1);
                     }
                 }
                 __syncwarp();
             }
-            (void)any_overflow;
             ncov = warp_sum(ncov);
             nguard = warp_sum(nguard);
             ntest = warp_sum(ntest);
@@ -809,12 +773,16 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
             }
         }
     }
-    if (lane == 0) s_E[w] = Ea;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double e = 0.0;
-        for (int q = 0; q < kSasaWarps; ++q) e += s_E[q];
-        if (e != 0.0) atomicAdd(&d.status->E[2], e);
+    // the block's last warp to finish adds the block's energy (no block-wide wait)
+    if (lane == 0) {
+        s_E[w] = Ea;
+        __threadfence_block();
+        if (atomicAdd(&s_ticket, 1u) == kSasaWarps - 1) {
+            __threadfence_block();
+            double e = 0.0;
+            for (int q = 0; q < kSasaWarps; ++q) e += ((volatile double*)s_E)[q];
+            if (e != 0.0) atomicAdd(&d.status->E[2], e);
+        }
     }
 }
 
