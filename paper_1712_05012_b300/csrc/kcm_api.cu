@@ -241,6 +241,13 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     d.roff_max = rmaxR + prm->r_probe;
     d.rmax = std::max(prm->cutoff, rv);
     if (prm->solvation) d.rmax = std::max(d.rmax, 2.0 * d.roff_max + prm->delta_r + 0.02);
+    d.f_K = (float)prm->coulomb_k;
+    d.f_w14e = (float)prm->w14_elec;
+    d.f_w14v = (float)prm->w14_vdw;
+    d.f_rc2 = (float)d.rcut2;
+    d.f_rv2 = (float)d.rvdw2;
+    d.f_rall2 = (float)(d.rmax * d.rmax) + 0.01f;  // FP32 candidate range, padded for rounding
+    d.f_dr = (float)prm->delta_r;
 
     const int n = d.n, l = d.l, L = d.L, N = d.N;
     const size_t nn = static_cast<size_t>(n);
@@ -257,7 +264,8 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = dalloc(h, &d.cell_start, d.cell_cap + 1)) || (rc = dalloc(h, &d.rank, nn)) || (rc = dalloc(h, &d.scan_part, d.scan_blocks)) ||
         (rc = dalloc(h, &d.sorted, nn)) || (rc = dalloc(h, &d.slot_cell, nn)) || (rc = dalloc(h, &d.spos64, nn)) ||
         (rc = dalloc(h, &d.spos32, nn)) || (rc = dalloc(h, &d.sprm32, nn)) || (rc = dalloc(h, &d.sprm64, nn)) ||
-        (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||
+        (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fpx, 3 * nn)) || (rc = dalloc(h, &d.Fov, 3 * nn)) ||
+        (rc = dalloc(h, &d.gflag, nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||
         (rc = dalloc(h, &d.nbr, nn * kcm::kMaxNbr)) || (rc = dalloc(h, &d.nbr_off, nn * kcm::kMaxNbr)) ||
         (rc = dalloc(h, &d.covered, nn)) || (rc = dalloc(h, &d.P, 6 * (size_t)L)) ||
         (rc = dalloc(h, &d.lane_suf, 6 * (size_t)L)) || (rc = dalloc(h, &d.tileS, 6 * (size_t)d.ltiles)) ||
@@ -271,12 +279,14 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     std::vector<float4> ap32(n);
     std::vector<double> G0(n);
     std::vector<long long> qfx(n);
+    std::vector<int> gflag(n);
     for (int a = 0; a < n; ++a) {
         double roff = hc.R[a] + prm->r_probe;
         ap64[a] = kcm::make_dbl4(hc.q[a], std::sqrt(hc.eps[a]), hc.R[a], roff);
         ap32[a] = make_float4((float)hc.q[a], (float)std::sqrt(hc.eps[a]), (float)hc.R[a], (float)roff);
         G0[a] = 4.0 * kPi * kcm::gamma_of_class(hc.cls[a]) * roff * roff;  // G^cav_{i,0} of Algorithm 1
         qfx[a] = std::llrint(G0[a] / (static_cast<double>(N) * prm->delta_r) * kcm::kFxScale);
+        gflag[a] = G0[a] != 0.0;
     }
     std::vector<double> Q64(3 * (size_t)N);
     kcm::sample_points(N, Q64.data());
@@ -286,7 +296,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = upload(h, d.link_start, hc.link_start.data(), L + 1)) || (rc = upload(h, d.u0, hc.u0.data(), 3 * l)) ||
         (rc = upload(h, d.step0, hc.step0.data(), 3 * l)) || (rc = upload(h, d.aprm64, ap64.data(), nn)) ||
         (rc = upload(h, d.aprm32, ap32.data(), nn)) || (rc = upload(h, d.G0, G0.data(), nn)) ||
-        (rc = upload(h, d.qfx, qfx.data(), nn)) ||
+        (rc = upload(h, d.qfx, qfx.data(), nn)) || (rc = upload(h, d.gflag, gflag.data(), nn)) ||
         (rc = upload(h, d.exm, reinterpret_cast<const unsigned long long*>(hc.ex_mask.data()), nn)) ||
         (rc = upload(h, d.m14m, reinterpret_cast<const unsigned long long*>(hc.m14_mask.data()), nn)) ||
         (rc = upload(h, d.Q64, Q64.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q32, Q32.data(), 3 * (size_t)N)) ||

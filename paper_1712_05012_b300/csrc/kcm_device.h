@@ -20,6 +20,7 @@ struct GridInfo {
     double ox, oy, oz;  // grid origin (bounding-box minimum)
     double s;           // cell edge, a multiple of 2^-10 A so that it is exact in float
     float sf, inv_sf;   // the edge in float and its reciprocal
+    float gpf;          // guard band of the FP32 cutoff tests (A^2), grows with the cell edge
     int nx, ny, nz;
     int ncells;
 };
@@ -70,6 +71,8 @@ struct DevChain {
     double rcut2 = 0, rvdw2 = 0;  // squared pair cutoffs
     double rmax = 0;              // largest interaction range (pair cutoffs, solvation neighbour range)
     double roff_max = 0;          // largest offset-sphere radius
+    // the same constants in float for the mixed kernels (no FP64 instruction per warp)
+    float f_K = 0, f_w14e = 0, f_w14v = 0, f_rc2 = 0, f_rv2 = 0, f_rall2 = 0, f_dr = 0;
 
     // static data
     double* r0 = nullptr;          // ZP centres relative to their link frame origin [n*3]
@@ -80,6 +83,7 @@ struct DevChain {
     dbl4* aprm64 = nullptr;     // per atom: q, sqrt(eps), R, Roff
     float4* aprm32 = nullptr;      // the same in float
     double* G0 = nullptr;          // 4 pi gamma Roff^2 [n]
+    int* gflag = nullptr;          // G0 != 0 [n]
     long long* qfx = nullptr;      // G0 / (N dr) in fixed point [n]
     unsigned long long* exm = nullptr;   // [n]
     unsigned long long* m14m = nullptr;  // [n]
@@ -109,7 +113,9 @@ struct DevChain {
     float4* spos32 = nullptr;      // sorted cell-relative offsets + charge [n]
     float4* sprm32 = nullptr;      // sorted sqrt(eps), R, Roff [n]
     dbl4* sprm64 = nullptr;     // [n]
-    double* Fpair = nullptr;       // [n*3]
+    double* Fpair = nullptr;       // [n*3] (FP64 mode; mixed mode fills it on request)
+    long long* Fpx = nullptr;      // mixed mode: pair forces in fixed point, units of 2^-23 [n*3]
+    float* Fov = nullptr;          // mixed mode: pair terms beyond the fixed-point range [n*3]
     long long* Fcav = nullptr;     // fixed point [n*3]
     int* nbr_cnt = nullptr;        // [n]
     int* nbr = nullptr;            // [n*kMaxNbr]

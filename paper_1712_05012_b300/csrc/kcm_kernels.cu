@@ -99,6 +99,7 @@ __global__ void k_bbox(const DevChain d) {
     g.ox = lo[0]; g.oy = lo[1]; g.oz = lo[2];
     g.s = s;
     g.sf = (float)s;
+    g.gpf = (float)(1e-3 + 2e-4 * s);
     g.inv_sf = 1.0f / (float)s;
     *d.grid = g;
     for (int i = 0; i < 3; ++i) { st->bbox[i] = ~0ULL; st->bbox[3 + i] = 0ULL; }
@@ -249,20 +250,22 @@ __global__ void k_bin_place(const DevChain d) {
 // the candidates of the 27 cells are then taken in strides of 32 over their concatenation, so
 // every lane has the same trip count. Each ordered pair (i, j) is evaluated by i's warp; the pair
 // term is computed symmetrically, so the term j's warp gets is exactly its negative. Mixed mode
-// sums the FP32 terms as int64 fixed point (2^-24): the sum is exact and order-free, and the
-// forces of a pair cancel exactly, so no net force or moment builds up over the chain. Terms of
-// 1e10 kcal/mol/A or more (near-overlapping atoms) go to a float side sum instead.
+// sums the FP32 terms in fixed point (units of 2^-23, see fx_add): the sum is exact and
+// order-free, and the forces of a pair cancel exactly, so no net force or moment builds up over
+// the chain. Terms of 2^22 kcal/mol/A or more (near-overlapping atoms) go to a float side sum. The
+// per-atom results stay integers here; the thread-per-atom consumers convert them to FP64 (a
+// warp-per-atom kernel would spend a whole FP64 warp instruction on each atom's lane 0).
 template <bool MIXED>
 __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     typedef typename std::conditional<MIXED, float, double>::type R;
     __shared__ int s_beg[kPairWarps][32];
     __shared__ int s_off[kPairWarps][32];
-    __shared__ double sE[2][kPairWarps];
+    __shared__ R sE[2][kPairWarps];
     __shared__ unsigned long long sC[3][kPairWarps];
     __shared__ int sM[kPairWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sl = blockIdx.x * kPairWarps + w;
-    double Eel = 0.0, Evdw = 0.0;
+    R Eel = 0, Evdw = 0;
     unsigned long long npairs = 0, nguard = 0;
     int ncount = 0;
     if (sl < d.n && !d.status->done) {
@@ -288,13 +291,14 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         s_beg[w][lane] = beg;
         s_off[w][lane] = incl - len;
         __syncwarp();
-        const R K = (R)d.prm.coulomb_k;
-        const R w14e = (R)d.prm.w14_elec, w14v = (R)d.prm.w14_vdw;
-        const R rc2 = (R)d.rcut2, rv2 = (R)d.rvdw2;
-        const R rall2 = (R)(d.rmax * d.rmax) + (R)(MIXED ? 0.01 : 0.0);
-        const R gp = (R)(1e-3 + 2e-4 * g.s);
-        const R dr = (R)d.prm.delta_r;
-        const R pad = MIXED ? (R)0.01 : (R)0.0;
+        R K, w14e, w14v, rc2, rv2, rall2, gp, dr, pad;
+        if constexpr (MIXED) {
+            K = d.f_K; w14e = d.f_w14e; w14v = d.f_w14v; rc2 = d.f_rc2; rv2 = d.f_rv2; rall2 = d.f_rall2;
+            gp = g.gpf; dr = d.f_dr; pad = 0.01f;
+        } else {
+            K = d.prm.coulomb_k; w14e = d.prm.w14_elec; w14v = d.prm.w14_vdw; rc2 = d.rcut2; rv2 = d.rvdw2;
+            rall2 = d.rmax * d.rmax; gp = 0.0; dr = d.prm.delta_r; pad = 0.0;
+        }
         const bool solv = d.prm.solvation != 0;
         const R sf = (R)g.sf;
         R px, py, pz, qi, sei, Ri, Roi;
@@ -432,13 +436,14 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             Lx = warp_sum(Lx); Ly = warp_sum(Ly); Lz = warp_sum(Lz);
             ovx = warp_sum(ovx); ovy = warp_sum(ovy); ovz = warp_sum(ovz);
             ove = warp_sum(ove); ovv = warp_sum(ovv);
-            if (lane == 0) {
-                d.Fpair[3 * a] = (double)Hx + (double)Lx * kPairFxInv + (double)ovx;
-                d.Fpair[3 * a + 1] = (double)Hy + (double)Ly * kPairFxInv + (double)ovy;
-                d.Fpair[3 * a + 2] = (double)Hz + (double)Lz * kPairFxInv + (double)ovz;
+            if (lane == 0) {  // converted to FP64 by the thread-per-atom consumers
+                d.Fpx[3 * a] = Hx * 8388608LL + Lx;
+                d.Fpx[3 * a + 1] = Hy * 8388608LL + Ly;
+                d.Fpx[3 * a + 2] = Hz * 8388608LL + Lz;
+                d.Fov[3 * a] = ovx; d.Fov[3 * a + 1] = ovy; d.Fov[3 * a + 2] = ovz;
             }
-            Eel = (double)ove;
-            Evdw = (double)ovv;
+            Eel = ove;
+            Evdw = ovv;
         } else {
             dfx = warp_sum(dfx); dfy = warp_sum(dfy); dfz = warp_sum(dfz);
             Eel = warp_sum(Eel); Evdw = warp_sum(Evdw);
@@ -454,12 +459,12 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     if (lane == 0) { sE[0][w] = Eel; sE[1][w] = Evdw; sC[0][w] = npairs; sC[1][w] = nguard; sC[2][w] = (unsigned long long)ncount; sM[w] = ncount; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double e0 = 0, e1 = 0;
+        R e0 = 0, e1 = 0;
         unsigned long long c0 = 0, c1 = 0, c2 = 0;
         int m = 0;
         for (int k2 = 0; k2 < kPairWarps; ++k2) { e0 += sE[0][k2]; e1 += sE[1][k2]; c0 += sC[0][k2]; c1 += sC[1][k2]; c2 += sC[2][k2]; m = max(m, sM[k2]); }
-        if (e0 != 0.0) atomicAdd(&d.status->E[0], e0);
-        if (e1 != 0.0) atomicAdd(&d.status->E[1], e1);
+        if (e0 != (R)0) atomicAdd(&d.status->E[0], (double)e0);
+        if (e1 != (R)0) atomicAdd(&d.status->E[1], (double)e1);
         if (c0) atomicAdd(&d.status->pairs, c0);
         if (c1) atomicAdd(&d.status->guard, c1);
         if (c2) atomicAdd(&d.status->nbr_total, c2);
@@ -480,13 +485,10 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
     __shared__ int s_cnt[kSasaWarps][3 * kMaxNbr];
     __shared__ float4 s_off[kSasaWarps][MIXED ? kMaxNbr : 1];
     __shared__ dbl4 s_pos[kSasaWarps][MIXED ? 1 : kMaxNbr];
-    __shared__ double s_E[kSasaWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
-    double Ea = 0.0;
     if (a < d.n && !d.status->done) {
-        const double G0a = d.G0[a];
-        if (G0a == 0.0) {
+        if (!d.gflag[a]) {
             if (lane == 0) d.covered[a] = 0;
         } else {
             const int cnt = min(d.nbr_cnt[a], kMaxNbr);
@@ -584,16 +586,8 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
                 d.covered[a] = ncov;
                 if (nguard) atomicAdd(&d.status->guard, (unsigned long long)nguard);
                 atomicAdd(&d.status->sasa_tests, ntest);
-                Ea = G0a - G0a * (double)ncov / (double)d.N;  // G^cav_i = G0_i f_i
             }
         }
-    }
-    if (lane == 0) s_E[w] = Ea;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double e = 0.0;
-        for (int k = 0; k < kSasaWarps; ++k) e += s_E[k];
-        if (e != 0.0) atomicAdd(&d.status->E[2], e);
     }
 }
 
@@ -619,24 +613,16 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
     __shared__ int s_idx[kSasaWarps][kMaxNbr];
     __shared__ int s_cnt[kSasaWarps][3 * kMaxNbr];
     __shared__ unsigned short s_near[kSasaWarps][kBatch];
-    __shared__ double s_E[kSasaWarps];
-    __shared__ unsigned s_ticket;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
-    if (threadIdx.x == 0) s_ticket = 0u;
-    __syncthreads();
-    double Ea = 0.0;
     if (a < d.n && !d.status->done) {
-        const double G0a = d.G0[a];
-        if (G0a == 0.0) {
+        if (!d.gflag[a]) {
             if (lane == 0) d.covered[a] = 0;
         } else {
             const int cnt = min(d.nbr_cnt[a], kMaxNbr);
-            const double Roa = d.aprm64[a].w;
-            const float Ra = (float)Roa;
+            const float Ra = d.aprm32[a].w;
             const float inv2R = 0.5f / Ra;
-            const double dr = d.prm.delta_r;
-            const float drf = (float)dr;
+            const float drf = d.f_dr;
             const float gd = 1e-4f + 1.2e-5f * d.grid->sf;  // guard band in Q.o units (A)
             float rmax2 = 0.0f;
             for (int j = lane; j < cnt; j += 32) {
@@ -652,11 +638,12 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
             // largest neighbour radius so that it is one number per atom
             const float band = (2.0f * drf * sqrtf(rmax2) + 3.0f * drf * drf) * inv2R + gd;
             __syncwarp();
-            const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
             int ncov = 0, nguard = 0;
             unsigned long long ntest = 0;
             auto recheck = [&](int j, int k, int s) -> bool {  // FP64, identical to the FP64 kernel
                 ++nguard;
+                const double Roa = d.aprm64[a].w, dr = d.prm.delta_r;
+                const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
                 const int b = s_idx[w][j];
                 const double ro = d.aprm64[b].w;
                 const double qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
@@ -769,19 +756,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 d.covered[a] = ncov;
                 if (nguard) atomicAdd(&d.status->guard, (unsigned long long)nguard);
                 atomicAdd(&d.status->sasa_tests, ntest);
-                Ea = G0a - G0a * (double)ncov / (double)d.N;  // G^cav_i = G0_i f_i
             }
-        }
-    }
-    // the block's last warp to finish adds the block's energy (no block-wide wait)
-    if (lane == 0) {
-        s_E[w] = Ea;
-        __threadfence_block();
-        if (atomicAdd(&s_ticket, 1u) == kSasaWarps - 1) {
-            __threadfence_block();
-            double e = 0.0;
-            for (int q = 0; q < kSasaWarps; ++q) e += ((volatile double*)s_E)[q];
-            if (e != 0.0) atomicAdd(&d.status->E[2], e);
         }
     }
 }
@@ -810,6 +785,7 @@ __global__ void k_force_out(const DevChain d) {
     if (x >= 3 * d.n) return;
     double fc = d.prm.solvation ? (double)d.Fcav[x] * kFxInv : 0.0;
     d.Fcav64[x] = fc;
+    if (d.prm.precision == KCM_MIXED) d.Fpair[x] = (double)d.Fpx[x] * kPairFxInv + (double)d.Fov[x];
     d.Ftot[x] = d.Fpair[x] + fc;
 }
 

@@ -1,4 +1,6 @@
 // A7-A9: link wrenches, suffix sums over links, joint torques and the kinetostatic step (FP64).
+// The wrench kernel, which visits every atom once with one thread each, also converts the
+// mixed-mode fixed-point forces to FP64 and adds the cavity energy G0_i f_i of its atoms.
 //
 // Wrench of link h about the origin, P_h = [sum r x F ; sum F] (eq. KCM_01/02): one thread per atom
 // forms r x F, and a segmented shuffle sum adds the atoms of each link within the warp (a link has at
@@ -23,13 +25,23 @@ __global__ void __launch_bounds__(128) k_wrench(const DevChain d) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     double v[6] = {0, 0, 0, 0, 0, 0};
+    double Ecav = 0.0;
     int h = -1 - lane;  // distinct keys for lanes past the last atom
     if (a < d.n) {
-        double fx = d.Fpair[3 * a], fy = d.Fpair[3 * a + 1], fz = d.Fpair[3 * a + 2];
+        double fx, fy, fz;
+        if (d.prm.precision == KCM_MIXED) {  // pair forces in fixed point plus oversized terms
+            fx = (double)d.Fpx[3 * a] * kPairFxInv + (double)d.Fov[3 * a];
+            fy = (double)d.Fpx[3 * a + 1] * kPairFxInv + (double)d.Fov[3 * a + 1];
+            fz = (double)d.Fpx[3 * a + 2] * kPairFxInv + (double)d.Fov[3 * a + 2];
+        } else {
+            fx = d.Fpair[3 * a]; fy = d.Fpair[3 * a + 1]; fz = d.Fpair[3 * a + 2];
+        }
         if (d.prm.solvation) {
             fx += (double)d.Fcav[3 * a] * kFxInv;
             fy += (double)d.Fcav[3 * a + 1] * kFxInv;
             fz += (double)d.Fcav[3 * a + 2] * kFxInv;
+            const double G0a = d.G0[a];  // G^cav_i = G0_i f_i, f_i = 1 - covered_i / N (Sec. 3.4)
+            if (G0a != 0.0) Ecav = G0a - G0a * (double)d.covered[a] / (double)d.N;
         }
         const double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
         v[0] = y * fz - z * fy;
@@ -47,6 +59,10 @@ __global__ void __launch_bounds__(128) k_wrench(const DevChain d) {
             const double y = __shfl_up_sync(0xffffffffu, v[k], off);
             if (take) v[k] += y;
         }
+    }
+    if (d.prm.solvation) {  // cavity energy of the warp's atoms
+        Ecav = warp_sum(Ecav);
+        if (lane == 0 && Ecav != 0.0) atomicAdd(&d.status->E[2], Ecav);
     }
     const int hn = __shfl_down_sync(0xffffffffu, h, 1);
     if (a < d.n && (lane == 31 || hn != h)) {
