@@ -598,12 +598,14 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
 // / (2 Roff_i). A displacement can change a point's state only where the two squared distances
 // straddle Roff_j^2, i.e. within |m_kj| <= (2 dr Roff_j + 3 dr^2) / (2 Roff_i) of the cap boundary.
 //
-// Step 1 keeps, per point, only max_j m_kj (covered iff > 0) and min_j |m_kj|. A point whose minimum
-// is outside that band (plus the FP32 guard band gd) takes no part in step 2 and its coverage is
-// decided; the few points inside it are re-scanned one per lane, which gives their exact count C,
-// their critical neighbour, FP64 re-decisions of guard-band tests (covers64, as in the FP64
-// kernel), and step 2 on their near-boundary neighbours. The exchanges are exactly Algorithm 1's:
-// an exposed point gains coverage only from a near neighbour, and a critically overlapped point loses
+// Step 1 keeps, per point, min_j |m_kj| and the number of neighbours with m_kj > band (counted on the
+// FMA pipe as saturate((m - band) 2^100), which is exactly 0 or 1). A point whose minimum is outside
+// the band takes no part in step 2 and is covered iff that count is >= 1; a point inside the band
+// that still has two such neighbours has C >= 2 and takes no part in step 2 either. Only the few
+// remaining points are re-scanned, one at a time with the neighbours spread over the lanes: exact
+// C, the critical neighbour, FP64 re-decisions of guard-band tests (covers64, as in the FP64
+// kernel), and step 2 on the near-boundary neighbours. The exchanges are exactly Algorithm 1's: an
+// exposed point gains coverage only from a near neighbour, and a critically overlapped point loses
 // it only if its critical neighbour is near.
 constexpr int kPtsPerLane = 8;                  // sample points each lane holds in registers
 constexpr int kBatch = 32 * kPtsPerLane;         // points per batch (256)
@@ -652,7 +654,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 return covers64(qx, qy, qz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
             };
             for (int kb = 0; kb < d.N; kb += kBatch) {
-                float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane], mx[kPtsPerLane], mn[kPtsPerLane];
+                float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane], nc[kPtsPerLane], mn[kPtsPerLane];
                 unsigned valid = 0;
 #pragma unroll
                 for (int p = 0; p < kPtsPerLane; ++p) {
@@ -662,50 +664,53 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                     qy[p] = v ? d.Q32[3 * k + 1] : 0.0f;
                     qz[p] = v ? d.Q32[3 * k + 2] : 0.0f;
                     valid |= v ? (1u << p) : 0u;
-                    mx[p] = -INFINITY;
+                    nc[p] = 0.0f;
                     mn[p] = INFINITY;
                 }
-                // step 1: max m and min |m| of each point over all neighbours
+                // step 1: min |m| and the count of m > band of each point over all neighbours
+                const float bandx = -band * 0x1p100f;
 #pragma unroll 2
                 for (int j = 0; j < cnt; ++j) {
                     const float4 o = s_o[w][j];
 #pragma unroll
                     for (int p = 0; p < kPtsPerLane; ++p) {
                         const float m = fmaf(qz[p], o.z, fmaf(qy[p], o.y, fmaf(qx[p], o.x, -o.w)));
-                        mx[p] = fmaxf(mx[p], m);
+                        nc[p] += __saturatef(fmaf(m, 0x1p100f, bandx));
                         mn[p] = fminf(mn[p], fabsf(m));
                     }
                 }
                 ntest += (unsigned long long)__popc(valid) * cnt;
-                // decided points are counted; near-boundary points are listed for the re-scan
-                int nnear = 0;
+                // decided points are counted; the rest are listed for the re-scan
+                int nres = 0;
                 const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
                 for (int p = 0; p < kPtsPerLane; ++p) {
                     const bool v = (valid >> p) & 1u;
-                    const bool nr = v && mn[p] <= band;
-                    if (v && !nr) ncov += mx[p] > 0.0f;
-                    const unsigned bm = __ballot_sync(0xffffffffu, nr);
-                    if (nr) s_near[w][nnear + __popc(bm & lt)] = (unsigned short)(lane + 32 * p);
-                    nnear += __popc(bm);
+                    const bool res = v && mn[p] <= band && nc[p] < 2.0f;
+                    if (v && !res) ncov += nc[p] >= 1.0f;
+                    const unsigned bm = __ballot_sync(0xffffffffu, res);
+                    if (res) s_near[w][nres + __popc(bm & lt)] = (unsigned short)(lane + 32 * p);
+                    nres += __popc(bm);
                 }
                 __syncwarp();
-                // re-scan of the near-boundary points, one per lane: exact step 1, then step 2
-                for (int e = lane; e < nnear; e += 32) {
+                // re-scan, one point at a time; lane t takes neighbours t, t + 32, ... (at most 4)
+                for (int e = 0; e < nres; ++e) {
                     const int k = kb + s_near[w][e];
                     const float Qx = d.Q32[3 * k], Qy = d.Q32[3 * k + 1], Qz = d.Q32[3 * k + 2];
-                    int C = 0, crit = -1;
-                    for (int j = 0; j < cnt; ++j) {
-                        const float4 o = s_o[w][j];
-                        const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, -o.w)));
-                        bool in = m > 0.0f;
-                        if (fabsf(m) <= gd) in = recheck(j, k, -1);
-                        if (in) {
-                            if (C == 0) crit = j;
-                            ++C;
+                    unsigned inb = 0, nrb = 0;
+                    for (int r = 0; 32 * r < cnt; ++r) {
+                        const int j = 32 * r + lane;
+                        if (j < cnt) {
+                            const float4 o = s_o[w][j];
+                            const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, -o.w)));
+                            bool in = m > 0.0f;
+                            if (fabsf(m) <= gd) in = recheck(j, k, -1);
+                            inb |= in ? (1u << r) : 0u;
+                            nrb |= fabsf(m) <= band ? (1u << r) : 0u;
                         }
                     }
-                    ncov += C >= 1;
+                    const int C = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(inb));
+                    if (lane == 0) ncov += C >= 1;
                     // step 2 against neighbour j displaced along s; hs is h_js
                     auto covers_s = [&](int j, int s) -> bool {
                         const float4 o = s_o[w][j];
@@ -717,20 +722,16 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                         if (fabsf(m) > gd) return m >= 0.0f;
                         return recheck(j, k, s);
                     };
-                    auto near_j = [&](int j) -> bool {
-                        const float4 o = s_o[w][j];
-                        const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, -o.w)));
-                        return fabsf(m) <= band;
-                    };
-                    if (C == 0) {
-                        for (int j = 0; j < cnt; ++j) {
-                            if (!near_j(j)) continue;
+                    if (C == 0) {  // exposed: every near neighbour may cover it once displaced
+                        for (unsigned b = nrb; b; b &= b - 1) {
+                            const int j = 32 * (__ffs(b) - 1) + lane;
                             for (int s = 0; s < 3; ++s)
                                 if (covers_s(j, s)) atomicAdd(&s_cnt[w][3 * j + s], 1);
                         }
-                    } else if (C == 1 && near_j(crit)) {
+                    } else if (C == 1 && (inb & nrb)) {  // critically overlapped by a near neighbour
+                        const int j = 32 * (__ffs(inb) - 1) + lane;
                         for (int s = 0; s < 3; ++s)
-                            if (!covers_s(crit, s)) atomicAdd(&s_cnt[w][3 * crit + s], -1);
+                            if (!covers_s(j, s)) atomicAdd(&s_cnt[w][3 * j + s], -1);
                     }
                 }
                 __syncwarp();
