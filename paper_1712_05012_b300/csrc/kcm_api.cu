@@ -226,7 +226,8 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     d.prm = *prm;
     d.m = hc.m; d.n = hc.n; d.l = hc.l; d.L = hc.L; d.N = prm->n_sample;
     d.fk_j = kcm::fk_joints_per_lane(d.l);
-    d.ntiles = (d.l + 32 * d.fk_j - 1) / (32 * d.fk_j);
+    const int fkq = kcm::fk_block_joints();
+    d.ntiles = (d.l + fkq * d.fk_j - 1) / (fkq * d.fk_j);
     d.ltiles = (d.L + 31) / 32;
     d.cell_cap = std::max(8 * d.n, 65536);
     d.pair_blocks = (d.n + kcm::kPairWarps - 1) / kcm::kPairWarps;
@@ -257,7 +258,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = dalloc(h, &d.exm, nn)) || (rc = dalloc(h, &d.m14m, nn)) || (rc = dalloc(h, &d.Q64, 3 * N)) ||
         (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.theta, l)) || (rc = dalloc(h, &d.dtheta, l)) ||
         (rc = dalloc(h, &d.tau, l)) || (rc = dalloc(h, &d.G, 12 * (size_t)l)) ||
-        (rc = dalloc(h, &d.lane_ex, 12 * 32 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) ||
+        (rc = dalloc(h, &d.lane_ex, 12 * (size_t)fkq * d.ntiles)) || (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) ||
         (rc = dalloc(h, &d.tileE, 12 * (size_t)d.ntiles)) ||
         (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||
         (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.cell_count, d.cell_cap)) ||
@@ -267,7 +268,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fpx, 3 * nn)) || (rc = dalloc(h, &d.Fov, 3 * nn)) ||
         (rc = dalloc(h, &d.gflag, nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||
         (rc = dalloc(h, &d.nbr, nn * kcm::kMaxNbr)) || (rc = dalloc(h, &d.nbr_off, nn * kcm::kMaxNbr)) ||
-        (rc = dalloc(h, &d.covered, nn)) || (rc = dalloc(h, &d.P, 6 * (size_t)L)) ||
+        (rc = dalloc(h, &d.covered, nn)) ||
         (rc = dalloc(h, &d.lane_suf, 6 * (size_t)L)) || (rc = dalloc(h, &d.tileS, 6 * (size_t)d.ltiles)) ||
         (rc = dalloc(h, &d.tileSuf, 6 * (size_t)d.ltiles)) ||
         (rc = dalloc(h, &d.Ftot, 3 * nn)) || (rc = dalloc(h, &d.Fcav64, 3 * nn)) ||

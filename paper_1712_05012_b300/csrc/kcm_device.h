@@ -46,6 +46,8 @@ struct Status {
     unsigned long long guard;
     unsigned long long sasa_tests;  // overlap tests performed by Algorithm 1 (steps 1 and 2)
     int max_nbr;
+    unsigned int ticket_w;  // last-block detection in the wrench / suffix-scan kernel
+    unsigned int ticket_fk;  // last-block detection in the transform-scan kernel
     int pad;
 };
 
@@ -58,11 +60,12 @@ constexpr float kPairFxMax = 4194304.0f;        // |pair term| below which it is
 constexpr int kPairFoldRounds = 256;            // candidate rounds between folds of the int32 lane sums
 constexpr int kSasaWarps = 4;
 constexpr int kApplyTpb = 64;
+constexpr int kWrenchWarps = 6;        // warps per 32-link tile of the wrench kernel (one per wrench component in the scan)
 
 struct DevChain {
     int m = 0, n = 0, l = 0, L = 0, N = 0;
-    int fk_j = 1;        // joints per lane in the transform scan
-    int ntiles = 0;      // transform-scan tiles of 32 * fk_j joints
+    int fk_j = 1;        // joints per quad (four-lane transform slot) in the transform scan
+    int ntiles = 0;      // transform-scan blocks of 64 * fk_j joints
     int ltiles = 0;      // suffix-sum tiles of 32 links
     int cell_cap = 0;
     int pair_blocks = 0, sasa_blocks = 0, bbox_blocks = 0, scan_blocks = 0;
@@ -95,9 +98,9 @@ struct DevChain {
     double* dtheta = nullptr;      // [l]
     double* tau = nullptr;         // [l]
     double* G = nullptr;           // lane-local prefixes of the joint transforms [l*12]
-    double* lane_ex = nullptr;     // exclusive lane prefixes within tiles [ntiles*32*12]
-    double* tileP = nullptr;       // tile products [ntiles*12]
-    double* tileE = nullptr;       // exclusive tile prefixes [ntiles*12]
+    double* lane_ex = nullptr;     // exclusive quad prefixes within blocks [ntiles*64*12]
+    double* tileP = nullptr;       // block products [ntiles*12]
+    double* tileE = nullptr;       // exclusive block prefixes [ntiles*12]
     double* M = nullptr;           // link frame poses [L*12]
     double* ucur = nullptr;        // current joint axes [l*3]
     double* pcur = nullptr;        // current axis points [l*3]
@@ -121,7 +124,6 @@ struct DevChain {
     int* nbr = nullptr;            // [n*kMaxNbr]
     float4* nbr_off = nullptr;     // r_j - r_i and Roff_j^2 [n*kMaxNbr]
     int* covered = nullptr;        // [n]
-    double* P = nullptr;           // link wrenches [L*6]
     double* lane_suf = nullptr;    // suffix sums within tiles of 32 links [L*6]
     double* tileS = nullptr;       // tile sums [ltiles*6]
     double* tileSuf = nullptr;     // exclusive suffix sums of the tile sums [ltiles*6]
@@ -142,6 +144,7 @@ void launch_sasa(DevChain& d, cudaStream_t s);
 void launch_torques(DevChain& d, cudaStream_t s);
 void launch_torques_step(DevChain& d, cudaStream_t s);
 int fk_joints_per_lane(int l);
+int fk_block_joints();  // quads per transform-scan block
 void launch_force_out(DevChain& d, cudaStream_t s);
 
 }  // namespace kcm

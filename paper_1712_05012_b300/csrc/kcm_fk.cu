@@ -3,11 +3,20 @@
 // Link frame poses T_j = L_1 o ... o L_j with L_j = Tr(step_j) o Rot(u0_j, theta_j) (eq. kin_04 in
 // local frames; App. B prefix computation). Atom centres are T_link(r0 - frame origin) (eq. r1, r2).
 //
-// On B300 an FP64 instruction costs the SM's FP64 pipe about as much for one active lane as for 32,
-// and a dependent FP64 operation takes ~70 cycles, so the scan is done by full warps: each lane
-// composes J consecutive joints, a warp composes its 32 lane products with a Kogge-Stone shuffle scan
-// (the extra compositions of that scan are free), one warp scans the tile products, and each lane
-// then applies its tile and lane prefix. Tiles are one warp per block, which spreads them over SMs.
+// On B300 an FP64 warp instruction occupies a sub-partition's FP64 pipe for about 84 cycles however
+// many of its lanes are active, so the scan is laid out to need few of them on its critical path:
+// a transform [R | t] is held by a quad of four lanes, lane r of the quad holding row r (R_r0, R_r1,
+// R_r2, t_r) (the fourth lane repeats row 2). A composition A o B then costs each lane one row, 12
+// FP64 instructions, instead of 36 for a whole transform per lane, and a warp holds eight transforms.
+//
+// k_fk_scan: block b (four warps, one per SM sub-partition, 32 quads) takes joints [32 J b,
+// 32 J (b + 1)), J consecutive joints per quad. Each quad forms its joints' local transforms and their
+// running product (kept in G), the warp scans its eight quad products (Kogge-Stone, 3 levels), warp 0
+// scans the four warp products, and each quad stores its exclusive prefix within the block; the
+// block product goes to tileP. k_fk_apply: block b first reduces the block products 0 .. b-1 to its
+// block prefix (a tree over at most 64 products per round, every block at once), then composes block
+// prefix, quad prefix and running products into the link poses M_{j+1}, the current axes u_j and axis
+// points p_j, and moves the atoms of its links.
 #include <cuda_runtime.h>
 
 #include "kcm_common.cuh"
@@ -18,138 +27,264 @@ namespace kcm {
 namespace {
 using namespace dev;
 
-__device__ __forceinline__ void shfl_up12(const double* X, double* Y, int off) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) Y[k] = __shfl_up_sync(0xffffffffu, X[k], off);
+constexpr int kFkWarps = 4;               // warps per block of the transform scan (one per sub-partition)
+constexpr int kFkQuads = 8 * kFkWarps;    // quads (transform slots) per block
+
+// row rr of the identity
+__device__ __forceinline__ void row_identity(int rr, double* a) {
+    a[0] = rr == 0 ? 1.0 : 0.0;
+    a[1] = rr == 1 ? 1.0 : 0.0;
+    a[2] = rr == 2 ? 1.0 : 0.0;
+    a[3] = 0.0;
 }
 
-// inclusive Kogge-Stone scan of affine transforms over the 32 lanes (composition on the left)
-__device__ __forceinline__ void warp_scan_aff(double* X, int lane) {
-    double Y[12];
+// the three rows of the quad's transform b (lanes base, base + 1, base + 2), for every lane of the quad
+__device__ __forceinline__ void quad_rows(const double* b, int base, double* B) {
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        shfl_up12(X, Y, off);
-        if (lane >= off) aff_compose(Y, X, X);
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) B[4 * k + m] = __shfl_sync(0xffffffffu, b[m], base + k);
     }
 }
 
-// per lane: product of its J joints (each joint's lane-local inclusive prefix kept in G); per warp:
-// exclusive lane prefixes and the tile product
-template <int J>
-__global__ void __launch_bounds__(32) k_fk_tile(const DevChain d) {
-    if (d.status->done) return;
-    const int tile = blockIdx.x, lane = threadIdx.x;
-    const int j0 = (tile * 32 + lane) * J;
-    double A[12], Gj[12];
-    aff_identity(A);
+// row of C = A o B from row a of A and the full B (rows B[0..3], B[4..7], B[8..11])
+__device__ __forceinline__ void row_compose(const double* a, const double* B, double* c) {
+    double t[4];
 #pragma unroll
-    for (int q = 0; q < J; ++q) {
-        const int jj = j0 + q;
-        if (jj < d.l) {
-            joint_tf(&d.u0[3 * jj], &d.step0[3 * jj], d.theta[jj], Gj);
-            aff_compose(A, Gj, A);
-            aff_store(&d.G[12 * (size_t)jj], A);
+    for (int m = 0; m < 3; ++m) t[m] = fma(a[2], B[8 + m], fma(a[1], B[4 + m], a[0] * B[m]));
+    t[3] = fma(a[2], B[11], fma(a[1], B[7], fma(a[0], B[3], a[3])));
+#pragma unroll
+    for (int m = 0; m < 4; ++m) c[m] = t[m];
+}
+
+// row rr of the local joint transform L_j = Tr(step_j) o Rot(u_j, th) with
+// R = cos I + sin [u]x + (1 - cos) u u^T (right-hand rule); the same arithmetic as joint_tf
+__device__ __forceinline__ void joint_row(const double* u, const double* step, double th, int rr, double* g) {
+    double s, c;
+    sincos(th, &s, &c);
+    const double C = 1.0 - c;
+    if (rr == 0) {
+        g[0] = c + u[0] * u[0] * C; g[1] = u[0] * u[1] * C - u[2] * s; g[2] = u[0] * u[2] * C + u[1] * s;
+    } else if (rr == 1) {
+        g[0] = u[1] * u[0] * C + u[2] * s; g[1] = c + u[1] * u[1] * C; g[2] = u[1] * u[2] * C - u[0] * s;
+    } else {
+        g[0] = u[2] * u[0] * C - u[1] * s; g[1] = u[2] * u[1] * C + u[0] * s; g[2] = c + u[2] * u[2] * C;
+    }
+    g[3] = step[rr];
+}
+
+__device__ __forceinline__ void store_row(double* T, int rr, const double* a) {
+    T[3 * rr] = a[0];
+    T[3 * rr + 1] = a[1];
+    T[3 * rr + 2] = a[2];
+    T[9 + rr] = a[3];
+}
+__device__ __forceinline__ void load_row(const double* T, int rr, double* a) {
+    a[0] = T[3 * rr];
+    a[1] = T[3 * rr + 1];
+    a[2] = T[3 * rr + 2];
+    a[3] = T[9 + rr];
+}
+__device__ __forceinline__ void load_rows(const double* T, double* B) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        B[4 * k] = T[3 * k];
+        B[4 * k + 1] = T[3 * k + 1];
+        B[4 * k + 2] = T[3 * k + 2];
+        B[4 * k + 3] = T[9 + k];
+    }
+}
+
+// inclusive Kogge-Stone scan over the first NQ quads of a warp (composition on the left)
+template <int NQ = 8>
+__device__ __forceinline__ void warp_scan_quads(double* a, int q, int base) {
+#pragma unroll
+    for (int off = 1; off < NQ; off <<= 1) {
+        double y[4], B[12];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) y[m] = __shfl_up_sync(0xffffffffu, a[m], 4 * off);
+        quad_rows(a, base, B);
+        if (q >= off) row_compose(y, B, a);
+    }
+}
+
+// Scans the transforms held by the block's quads (row a of slot 8 w + q) in place into inclusive
+// block prefixes; the block total is returned in tot (row rr) on every lane. sW: [kFkWarps][12] shared.
+__device__ __forceinline__ void block_scan_quads(double* a, double* tot, double (*sW)[12], int w, int q, int rr,
+                                                 int base, int lane) {
+    warp_scan_quads(a, q, base);
+    if (q == 7 && (lane & 3) < 3) store_row(sW[w], rr, a);
+    __syncthreads();
+    if (w == 0) {  // scan of the warp totals, quad q <- warp q
+        double t[4];
+        if (q < kFkWarps) load_row(sW[q], rr, t);
+        else row_identity(rr, t);
+        warp_scan_quads<kFkWarps>(t, q, base);
+        __syncwarp();
+        if (q < kFkWarps && (lane & 3) < 3) store_row(sW[q], rr, t);  // inclusive prefix of warps 0..q
+    }
+    __syncthreads();
+    if (w > 0) {  // prefix of the earlier warps o own warp prefix
+        double P[4], B[12];
+        load_row(sW[w - 1], rr, P);
+        quad_rows(a, base, B);
+        row_compose(P, B, a);
+    }
+    load_row(sW[kFkWarps - 1], rr, tot);
+    __syncthreads();
+}
+
+template <int J>
+__global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
+    __shared__ double sW[kFkWarps][12];
+    if (d.status->done) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
+    const int slot = w * 8 + q;
+    const int j0 = (blockIdx.x * kFkQuads + slot) * J;
+    // running product of the quad's J joints; the inclusive local prefixes go to G
+    double a[4];
+    row_identity(rr, a);
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+        const int j = j0 + i;
+        double g[4];  // joints past the end act as the identity (every lane takes part in the shuffles)
+        if (j < d.l) joint_row(&d.u0[3 * j], &d.step0[3 * j], d.theta[j], rr, g);
+        else row_identity(rr, g);
+        if (i == 0) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) a[m] = g[m];
+        } else {
+            double B[12];
+            quad_rows(g, base, B);
+            row_compose(a, B, a);
+        }
+        if (j < d.l && (lane & 3) < 3) store_row(&d.G[12 * (size_t)j], rr, a);
+    }
+    // exclusive prefix of the quad within the block
+    double incl[4], tot[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) incl[m] = a[m];
+    block_scan_quads(incl, tot, sW, w, q, rr, base, lane);
+    double ex[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) ex[m] = __shfl_up_sync(0xffffffffu, incl[m], 4);
+    if (q == 0) {  // first quad of the warp: the inclusive prefix of the previous warp
+        if (w == 0) row_identity(rr, ex);
+        else load_row(sW[w - 1], rr, ex);  // still valid: written before the last barrier, not reused
+    }
+    if ((lane & 3) < 3) store_row(&d.lane_ex[12 * ((size_t)blockIdx.x * kFkQuads + slot)], rr, ex);
+    if (threadIdx.x < 32 && (lane & 3) < 3 && q == 0) store_row(&d.tileP[12 * (size_t)blockIdx.x], rr, tot);
+
+}
+
+// link poses M_{j+1} = (block prefix o quad prefix) o running product_j; current axis
+// u_j = R(M_j) u0_j through p_j = origin of frame j+1; then the atoms of the block's links
+// row rr of the product tileP[b0] o ... o tileP[b1 - 1] (identity when empty), all warps of the block
+// taking part: two products per quad, then a tree within each warp and over the warps
+__device__ __forceinline__ void block_prefix(const DevChain& d, int b0, int b1, double (*sW)[12], int w, int q, int rr,
+                                             int base, int lane, double* out) {
+    const int slot = w * 8 + q;
+    double a[4], B[12];
+    const int i0 = b0 + 2 * slot, i1 = i0 + 1;
+    if (i0 < b1) load_row(&d.tileP[12 * (size_t)i0], rr, a);
+    else row_identity(rr, a);
+    if (i1 < b1) {  // uniform within the quad
+        load_rows(&d.tileP[12 * (size_t)i1], B);
+        row_compose(a, B, a);
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {  // tree over the quads of the warp: quad q <- q o q + off
+        double y[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) y[m] = __shfl_down_sync(0xffffffffu, a[m], 4 * off);
+        quad_rows(y, base, B);
+        if ((q & (2 * off - 1)) == 0) row_compose(a, B, a);
+    }
+    if (q == 0 && (lane & 3) < 3) store_row(sW[w], rr, a);
+    __syncthreads();
+    load_row(sW[0], rr, out);
+#pragma unroll
+    for (int v = 1; v < kFkWarps; ++v) {
+        load_rows(sW[v], B);
+        row_compose(out, B, out);
+    }
+    __syncthreads();
+}
+
+template <int J>
+__global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
+    __shared__ double sW[kFkWarps][12];
+    if (d.status->done) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
+    const int slot = w * 8 + q;
+    const int j0 = (blockIdx.x * kFkQuads + slot) * J;
+    // block prefix: product of the block products before this block, 2 * kFkQuads per round
+    double bE[4];
+    row_identity(rr, bE);
+    for (int b0 = 0; b0 < (int)blockIdx.x; b0 += 2 * kFkQuads) {
+        double part[4], B[12];
+        block_prefix(d, b0, min(b0 + 2 * kFkQuads, (int)blockIdx.x), sW, w, q, rr, base, lane, part);
+        quad_rows(part, base, B);
+        row_compose(bE, B, bE);
+    }
+    if (j0 < d.l) {  // no shuffles below: quads past the end may leave
+        double X[12], P0[4], Mb[4];
+        load_rows(&d.lane_ex[12 * ((size_t)blockIdx.x * kFkQuads + slot)], X);
+        row_compose(bE, X, P0);  // row rr of the pose before joint j0
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Mb[m] = P0[m];
+#pragma unroll
+        for (int i = 0; i < J; ++i) {
+            const int j = j0 + i;
+            if (j < d.l) {
+                const double* u = &d.u0[3 * j];
+                const double uc = fma(Mb[2], u[2], fma(Mb[1], u[1], Mb[0] * u[0]));
+                double Gj[12], Ma[4];
+                load_rows(&d.G[12 * (size_t)j], Gj);
+                row_compose(P0, Gj, Ma);  // pose of link j + 1
+                if ((lane & 3) < 3) {
+                    d.ucur[3 * j + rr] = uc;
+                    store_row(&d.M[12 * ((size_t)j + 1)], rr, Ma);
+                    d.pcur[3 * j + rr] = Ma[3];
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) Mb[m] = Ma[m];
+            }
         }
     }
-    double X[12];
+    __syncthreads();  // the block's link poses are visible to the whole block
+    // atoms of the block's links 32 J b + 1 .. 32 J (b + 1) (block 0 also takes link 0, whose pose is the
+    // identity)
+    const int hfirst = blockIdx.x == 0 ? 0 : blockIdx.x * kFkQuads * J + 1;
+    const int hlast = min((blockIdx.x + 1) * kFkQuads * J + 1, d.L);
+    const int a1 = d.link_start[hlast];
+    for (int a = d.link_start[hfirst] + threadIdx.x; a < a1; a += blockDim.x) {
+        const double* M = &d.M[12 * (size_t)d.link[a]];
+        const double x = d.r0[3 * a], y = d.r0[3 * a + 1], z = d.r0[3 * a + 2];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) X[k] = A[k];
-    warp_scan_aff(X, lane);
-    double E[12];
-    shfl_up12(X, E, 1);
-    if (lane == 0) aff_identity(E);
-    aff_store(&d.lane_ex[12 * ((size_t)tile * 32 + lane)], E);
-    if (lane == 31) aff_store(&d.tileP[12 * (size_t)tile], X);
-}
-
-// exclusive prefix of the tile products, 32 tiles per round with a carried product (one warp)
-__global__ void __launch_bounds__(32) k_fk_tilescan(const DevChain d) {
-    if (d.status->done) return;
-    const int lane = threadIdx.x;
-    double carry[12];
-    aff_identity(carry);
-    for (int base = 0; base < d.ntiles; base += 32) {
-        const int t = base + lane;
-        double X[12], E[12], T[12];
-        if (t < d.ntiles) aff_load(&d.tileP[12 * (size_t)t], X);
-        else aff_identity(X);
-        warp_scan_aff(X, lane);
-        shfl_up12(X, E, 1);
-        if (lane == 0) aff_identity(E);
-        aff_compose(carry, E, E);
-        if (t < d.ntiles) aff_store(&d.tileE[12 * (size_t)t], E);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) T[k] = __shfl_sync(0xffffffffu, X[k], 31);
-        aff_compose(carry, T, carry);
+        for (int i = 0; i < 3; ++i) d.r[3 * a + i] = M[3 * i] * x + M[3 * i + 1] * y + M[3 * i + 2] * z + M[9 + i];
     }
-}
-
-// link poses M_{j+1} = (tile prefix o lane prefix) o lane-local prefix_j; current axis
-// u_j = R(M_j) u0_j through p_j = origin of frame j+1
-template <int J>
-__global__ void __launch_bounds__(32) k_fk_apply(const DevChain d) {
-    if (d.status->done) return;
-    const int tile = blockIdx.x, lane = threadIdx.x;
-    const int j0 = (tile * 32 + lane) * J;
-    if (j0 >= d.l) return;
-    double B[12], T[12], Mb[12], Ma[12], Gj[12];
-    aff_load(&d.tileE[12 * (size_t)tile], T);
-    aff_load(&d.lane_ex[12 * ((size_t)tile * 32 + lane)], B);
-    aff_compose(T, B, B);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) Mb[k] = B[k];
-#pragma unroll
-    for (int q = 0; q < J; ++q) {
-        const int jj = j0 + q;
-        if (jj < d.l) {
-            const double* u = &d.u0[3 * jj];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) d.ucur[3 * jj + i] = Mb[3 * i] * u[0] + Mb[3 * i + 1] * u[1] + Mb[3 * i + 2] * u[2];
-            aff_load(&d.G[12 * (size_t)jj], Gj);
-            aff_compose(B, Gj, Ma);
-            aff_store(&d.M[12 * ((size_t)jj + 1)], Ma);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) d.pcur[3 * jj + i] = Ma[9 + i];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) Mb[k] = Ma[k];
-        }
-    }
-}
-
-__global__ void k_fk_atoms(const DevChain d) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= d.n || d.status->done) return;
-    const double* M = &d.M[12 * (size_t)d.link[a]];
-    const double x = d.r0[3 * a], y = d.r0[3 * a + 1], z = d.r0[3 * a + 2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) d.r[3 * a + i] = M[3 * i] * x + M[3 * i + 1] * y + M[3 * i + 2] * z + M[9 + i];
 }
 
 template <int J>
 void launch_fk_j(DevChain& d, cudaStream_t s) {
-    k_fk_tile<J><<<d.ntiles, 32, 0, s>>>(d);
-    k_fk_tilescan<<<1, 32, 0, s>>>(d);
-    k_fk_apply<J><<<d.ntiles, 32, 0, s>>>(d);
-    k_fk_atoms<<<(d.n + 127) / 128, 128, 0, s>>>(d);
+    k_fk_scan<J><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+    k_fk_apply<J><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
 }
 
 }  // namespace
 
-// joints per lane: the J minimising the dependent compositions, J in the tile pass plus 6 per
-// 32-tile round of the tile scan plus J in the apply pass
+// joints per quad: the smallest J that keeps the block count within one round (2 * kFkQuads) of the
+// block-prefix reduction
 int fk_joints_per_lane(int l) {
-    int best = 1;
-    long long best_cost = -1;
-    for (int J = 1; J <= 32; J *= 2) {
-        long long ntiles = (l + 32LL * J - 1) / (32LL * J);
-        long long cost = 2LL * J + 6 * ((ntiles + 31) / 32);
-        if (best_cost < 0 || cost < best_cost) {
-            best = J;
-            best_cost = cost;
-        }
-    }
-    return best;
+    int J = 1;
+    while (J < 32 && (l + kFkQuads * J - 1) / (kFkQuads * J) > 2 * kFkQuads) J *= 2;
+    return J;
 }
+
+int fk_block_joints() { return kFkQuads; }
 
 void launch_fk(DevChain& d, cudaStream_t s) {
     switch (d.fk_j) {

@@ -768,6 +768,8 @@ __global__ void k_reset_loop(const DevChain d, int full) {
     st->done = 0;
     st->error = 0;
     st->ticket = 0u;
+    st->ticket_w = 0u;
+    st->ticket_fk = 0u;
     st->max_dtheta = 0ULL;
     st->max_abs_tau = 0ULL;
     st->last_max_dtheta = 0.0;
