@@ -57,7 +57,8 @@ constexpr int kScanCells = 2048;      // cells per block of the cell-count scan
 constexpr int kScanThreadsBig = 256;
 constexpr double kPairFxInv = 1.0 / 8388608.0;  // unit of the fraction sums of mixed-mode pair forces
 constexpr float kPairFxMax = 4194304.0f;        // |pair term| below which it is summed in fixed point (2^22)
-constexpr int kPairFoldRounds = 256;            // candidate rounds between folds of the int32 lane sums
+constexpr int kPairFoldRounds = 256;            // pair rounds between folds of the int32 lane sums
+constexpr int kPairQueue = 64;                  // ring of in-range candidates per warp of the pair kernel (power of 2)
 constexpr int kSasaWarps = 4;
 constexpr int kApplyTpb = 64;
 constexpr int kWrenchWarps = 6;        // warps per 32-link tile of the wrench kernel (one per wrench component in the scan)

@@ -258,8 +258,11 @@ __global__ void k_bin_place(const DevChain d) {
 template <bool MIXED>
 __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     typedef typename std::conditional<MIXED, float, double>::type R;
+    typedef typename std::conditional<MIXED, float4, dbl4>::type QV;
     __shared__ int s_beg[kPairWarps][32];
     __shared__ int s_off[kPairWarps][32];
+    __shared__ QV s_qv[kPairWarps][kPairQueue];   // queued pairs: r_i - r_j, d^2
+    __shared__ int s_qts[kPairWarps][kPairQueue];  // queued pairs: sorted slot of j
     __shared__ R sE[2][kPairWarps];
     __shared__ unsigned long long sC[3][kPairWarps];
     __shared__ int sM[kPairWarps];
@@ -317,102 +320,87 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         double dfx = 0, dfy = 0, dfz = 0;                        // FP64 mode
         int t = 0;
         const unsigned lt = (1u << lane) - 1u;
-        for (int cb = 0; cb < total; cb += 32 * kPairFoldRounds) {
-        // at most one term per lane and round: kPairFoldRounds terms of |piece| <= 2^22 fit in int32
-        const int ce = min(total, cb + 32 * kPairFoldRounds);
-        for (int base = cb; base < ce; base += 32) {
-            const int k2 = base + lane;
+        // Phase A filters the candidates by distance and queues the in-range ones, in candidate order,
+        // in a ring of kPairQueue; phase B evaluates 32 queued pairs at a time, so the pair terms run
+        // with every lane busy instead of the ~30 % of candidates that are in range.
+        int qhead = 0, qtail = 0, nround = 0;
+        auto phase_b = [&](int nvalid) {
+            const int e = (qhead + lane) & (kPairQueue - 1);
             bool isn = false;
             int b = -1;
             R ddx = 0, ddy = 0, ddz = 0, Roj = 0;
-            if (k2 < total) {
-                while (t < 26 && s_off[w][t + 1] <= k2) ++t;
-                const int ts = s_beg[w][t] + (k2 - s_off[w][t]);
-                if (ts != sl) {
-                    R qj, sej, Rj;
-                    if constexpr (MIXED) {
-                        float4 p = d.spos32[ts];
-                        const R shx = (R)(t % 3 - 1) * sf, shy = (R)((t / 3) % 3 - 1) * sf, shz = (R)(t / 9 - 1) * sf;
-                        // r_i - r_j = (o_i - o_j) - (c_j - c_i) s
-                        ddx = (px - p.x) - shx; ddy = (py - p.y) - shy; ddz = (pz - p.z) - shz;
-                        qj = p.w;
-                    } else {
-                        dbl4 p = d.spos64[ts];
-                        ddx = __dsub_rn(px, p.x); ddy = __dsub_rn(py, p.y); ddz = __dsub_rn(pz, p.z);
-                        qj = p.w;
+            if (lane < nvalid) {
+                const int ts = s_qts[w][e];
+                const QV v = s_qv[w][e];
+                ddx = v.x; ddy = v.y; ddz = v.z;
+                const R d2 = v.w;
+                R qj, sej, Rj;
+                b = d.sorted[ts];
+                if constexpr (MIXED) {
+                    float4 q = d.sprm32[ts];
+                    qj = q.x; sej = q.y; Rj = q.z; Roj = q.w;
+                } else {
+                    dbl4 q = d.sprm64[ts];
+                    qj = q.x; sej = q.y; Rj = q.z; Roj = q.w;
+                }
+                if (solv) {  // solvation neighbour A'_i: d_ij <= Roff_i + Roff_j + dr
+                    R lim = Roi + Roj + dr + pad;
+                    isn = d2 <= lim * lim;
+                }
+                int lo = min(a, b), off = max(a, b) - lo;
+                bool excl = false, is14 = false;
+                if (off <= kMaskWindow) {
+                    unsigned long long em = (lo == a) ? exa : d.exm[b];
+                    unsigned long long mm = (lo == a) ? m14a : d.m14m[b];
+                    excl = (em >> off) & 1ULL;
+                    is14 = (mm >> off) & 1ULL;
+                }
+                bool inE = !excl && d2 <= rc2, inV = !excl && d2 <= rv2;
+                if (MIXED && !excl && (fabs(d2 - rc2) <= gp || fabs(d2 - rv2) <= gp)) {
+                    // guard band: decide the cutoff in FP64 exactly as the FP64 path does
+                    double ex = __dsub_rn(d.r[3 * a], d.r[3 * b]), ey = __dsub_rn(d.r[3 * a + 1], d.r[3 * b + 1]),
+                           ez = __dsub_rn(d.r[3 * a + 2], d.r[3 * b + 2]);
+                    double d64 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+                    inE = d64 <= d.rcut2;
+                    inV = d64 <= d.rvdw2;
+                    ++nguard;
+                }
+                if (inE || inV) {
+                    // symmetric in (i, j): products of the two atoms' constants are formed first
+                    const R we = is14 ? w14e : (R)1, wv = is14 ? w14v : (R)1;
+                    R inv2;
+                    if constexpr (MIXED) inv2 = __frcp_rn(d2); else inv2 = 1.0 / d2;
+                    R coef = 0, e_el = 0, e_vd = 0;
+                    if (inE) {
+                        const R qq = (we * K) * (qi * qj);
+                        coef += (R)0.5 * qq * (inv2 * inv2);
+                        e_el = (R)0.25 * qq * inv2;
                     }
-                    R d2;
-                    if constexpr (MIXED) d2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    else d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-                    if (d2 <= rall2) {
-                        b = d.sorted[ts];
-                        if constexpr (MIXED) {
-                            float4 q = d.sprm32[ts];
-                            sej = q.y; Rj = q.z; Roj = q.w;
-                        } else {
-                            dbl4 q = d.sprm64[ts];
-                            sej = q.y; Rj = q.z; Roj = q.w;
+                    if (inV) {
+                        const R D = Ri + Rj;
+                        const R D2 = D * D;
+                        const R x2 = D2 * inv2;
+                        const R t6 = x2 * x2 * x2;
+                        const R t12 = t6 * t6;
+                        const R eij = wv * (sei * sej);
+                        coef += (R)12 * eij * (t12 - t6) * inv2;
+                        e_vd = eij * (t12 - (R)2 * t6);
+                    }
+                    const bool count_e = a < b;
+                    if (count_e && (we != (R)0 || wv != (R)0)) ++npairs;
+                    if constexpr (MIXED) {
+                        const float fx1 = coef * ddx, fy1 = coef * ddy, fz1 = coef * ddz;
+                        if (fabsf(fx1) < kPairFxMax && fabsf(fy1) < kPairFxMax && fabsf(fz1) < kPairFxMax) {
+                            fx_add(fx1, hix, lox);
+                            fx_add(fy1, hiy, loy);
+                            fx_add(fz1, hiz, loz);
+                        } else {  // clash-sized (or non-finite) term: plain float sum
+                            ovx += fx1; ovy += fy1; ovz += fz1;
                         }
-                        if (solv) {  // solvation neighbour A'_i: d_ij <= Roff_i + Roff_j + dr
-                            R lim = Roi + Roj + dr + pad;
-                            isn = d2 <= lim * lim;
-                        }
-                        int lo = min(a, b), off = max(a, b) - lo;
-                        bool excl = false, is14 = false;
-                        if (off <= kMaskWindow) {
-                            unsigned long long em = (lo == a) ? exa : d.exm[b];
-                            unsigned long long mm = (lo == a) ? m14a : d.m14m[b];
-                            excl = (em >> off) & 1ULL;
-                            is14 = (mm >> off) & 1ULL;
-                        }
-                        bool inE = !excl && d2 <= rc2, inV = !excl && d2 <= rv2;
-                        if (MIXED && !excl && (fabs(d2 - rc2) <= gp || fabs(d2 - rv2) <= gp)) {
-                            // guard band: decide the cutoff in FP64 exactly as the FP64 path does
-                            double ex = __dsub_rn(d.r[3 * a], d.r[3 * b]), ey = __dsub_rn(d.r[3 * a + 1], d.r[3 * b + 1]),
-                                   ez = __dsub_rn(d.r[3 * a + 2], d.r[3 * b + 2]);
-                            double d64 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-                            inE = d64 <= d.rcut2;
-                            inV = d64 <= d.rvdw2;
-                            ++nguard;
-                        }
-                        if (inE || inV) {
-                            // symmetric in (i, j): products of the two atoms' constants are formed first
-                            const R we = is14 ? w14e : (R)1, wv = is14 ? w14v : (R)1;
-                            R inv2;
-                            if constexpr (MIXED) inv2 = __frcp_rn(d2); else inv2 = 1.0 / d2;
-                            R coef = 0, e_el = 0, e_vd = 0;
-                            if (inE) {
-                                const R qq = (we * K) * (qi * qj);
-                                coef += (R)0.5 * qq * (inv2 * inv2);
-                                e_el = (R)0.25 * qq * inv2;
-                            }
-                            if (inV) {
-                                const R D = Ri + Rj;
-                                const R D2 = D * D;
-                                const R x2 = D2 * inv2;
-                                const R t6 = x2 * x2 * x2;
-                                const R t12 = t6 * t6;
-                                const R eij = wv * (sei * sej);
-                                coef += (R)12 * eij * (t12 - t6) * inv2;
-                                e_vd = eij * (t12 - (R)2 * t6);
-                            }
-                            const bool count_e = a < b;
-                            if (count_e && (we != (R)0 || wv != (R)0)) ++npairs;
-                            if constexpr (MIXED) {
-                                const float fx1 = coef * ddx, fy1 = coef * ddy, fz1 = coef * ddz;
-                                if (fabsf(fx1) < kPairFxMax && fabsf(fy1) < kPairFxMax && fabsf(fz1) < kPairFxMax) {
-                                    fx_add(fx1, hix, lox);
-                                    fx_add(fy1, hiy, loy);
-                                    fx_add(fz1, hiz, loz);
-                                } else {  // clash-sized (or non-finite) term: plain float sum
-                                    ovx += fx1; ovy += fy1; ovz += fz1;
-                                }
-                                if (count_e) { ove += e_el; ovv += e_vd; }
-                            } else {
-                                dfx += coef * ddx; dfy += coef * ddy; dfz += coef * ddz;
-                                if (count_e) { Eel += e_el; Evdw += e_vd; }
-                            }
-                        }
+                        if (count_e) { ove += e_el; ovv += e_vd; }
+                    } else {
+                        dfx += coef * ddx; dfy += coef * ddy; dfz += coef * ddz;
+                        if (count_e) { Eel += e_el; Evdw += e_vd; }
                     }
                 }
             }
@@ -425,11 +413,56 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                 }
             }
             ncount += __popc(bm);
+            qhead += 32;
+            if constexpr (MIXED) {
+                // at most one term per lane and round: kPairFoldRounds terms of |piece| <= 2^22 fit in int32
+                if (++nround == kPairFoldRounds) {
+                    Hx += hix; Hy += hiy; Hz += hiz; Lx += lox; Ly += loy; Lz += loz;
+                    hix = hiy = hiz = lox = loy = loz = 0;
+                    nround = 0;
+                }
+            }
+        };
+        for (int base = 0; base < total; base += 32) {
+            const int k2 = base + lane;
+            bool inr = false;
+            QV v;
+            int ts = 0;
+            if (k2 < total) {
+                while (t < 26 && s_off[w][t + 1] <= k2) ++t;
+                ts = s_beg[w][t] + (k2 - s_off[w][t]);
+                if (ts != sl) {
+                    R ddx, ddy, ddz;
+                    if constexpr (MIXED) {
+                        float4 p = d.spos32[ts];
+                        const R shx = (R)(t % 3 - 1) * sf, shy = (R)((t / 3) % 3 - 1) * sf, shz = (R)(t / 9 - 1) * sf;
+                        // r_i - r_j = (o_i - o_j) - (c_j - c_i) s
+                        ddx = (px - p.x) - shx; ddy = (py - p.y) - shy; ddz = (pz - p.z) - shz;
+                    } else {
+                        dbl4 p = d.spos64[ts];
+                        ddx = __dsub_rn(px, p.x); ddy = __dsub_rn(py, p.y); ddz = __dsub_rn(pz, p.z);
+                    }
+                    R d2;
+                    if constexpr (MIXED) d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    else d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+                    inr = d2 <= rall2;
+                    v.x = ddx; v.y = ddy; v.z = ddz; v.w = d2;
+                }
+            }
+            const unsigned bm = __ballot_sync(0xffffffffu, inr);
+            if (inr) {
+                const int e = (qtail + __popc(bm & lt)) & (kPairQueue - 1);
+                s_qv[w][e] = v;
+                s_qts[w][e] = ts;
+            }
+            qtail += __popc(bm);
+            __syncwarp();
+            if (qtail - qhead >= 32) phase_b(32);
+            __syncwarp();
         }
+        if (qtail > qhead) phase_b(qtail - qhead);
         if constexpr (MIXED) {
             Hx += hix; Hy += hiy; Hz += hiz; Lx += lox; Ly += loy; Lz += loz;
-            hix = hiy = hiz = lox = loy = loz = 0;
-        }
         }
         if constexpr (MIXED) {
             Hx = warp_sum(Hx); Hy = warp_sum(Hy); Hz = warp_sum(Hz);
