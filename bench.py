@@ -44,7 +44,7 @@ FP32_LANES_PER_SM = 128
 FLOPS_PER_SASA_TEST = 9  # w = v - o (3), |w|^2 (1 mul + 2 FMA = 5), compare with Roff^2 (1)
 FLOPS_PER_PAIR = 31      # per unordered pair within the cutoff (distance, 1/d^2, Coulomb, LJ, weights, accumulate)
 BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques_step": 60}  # algorithmic HBM bytes per atom
-KERNELS_PER_ITERATION = {1: 14, 0: 13}  # reset + kinematics 4 + binning 5 + pairs 1 + solvation 1 + wrench-tile 1 + torque-step 1
+KERNELS_PER_ITERATION = {1: 9, 0: 8}  # reset + kinematics 2 + binning 2 + pairs 1 + solvation 1 + wrench-tile 1 + torque-step 1
 
 
 def parse():

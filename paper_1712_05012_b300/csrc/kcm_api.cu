@@ -231,8 +231,8 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     d.ltiles = (d.L + 31) / 32;
     d.cell_cap = std::max(8 * d.n, 65536);
     d.pair_blocks = (d.n + kcm::kPairWarps - 1) / kcm::kPairWarps;
-    d.bbox_blocks = std::max(1, std::min((d.n + 255) / 256, 2 * 148));
     d.scan_blocks = (d.cell_cap + kcm::kScanCells - 1) / kcm::kScanCells;
+    d.scan_fused = d.cell_cap <= kcm::kScanFusedMaxCells;
     d.sasa_blocks = (d.n + kcm::kSasaWarps - 1) / kcm::kSasaWarps;
     d.rcut2 = prm->cutoff * prm->cutoff;
     double rv = prm->vdw_cutoff > 0.0 ? prm->vdw_cutoff : prm->cutoff;

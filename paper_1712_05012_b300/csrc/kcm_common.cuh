@@ -100,5 +100,56 @@ __device__ __forceinline__ bool covers64(double qx, double qy, double qz, double
     return d2 <= roff2_b;
 }
 
+
+// Grid of the cell list from the bounding box in st->bbox (order-preserving keys): cube cells of
+// edge s >= every interaction range (plus a margin that absorbs FP32 cell assignment), s a multiple
+// of 2^-10 A so that it is exact in float; coarsened when the bounding box would need more cells
+// than the arrays hold. Also clears the box and the per-evaluation counters. Run by one thread
+// after every block has added its atoms to the box.
+__device__ __forceinline__ void finish_grid(const DevChain& d, Status* st) {
+    double lo[3], hi[3];
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = dkey_inv(atomicAdd(&st->bbox[i], 0ULL));
+        hi[i] = dkey_inv(atomicAdd(&st->bbox[3 + i], 0ULL));
+    }
+    GridInfo g;
+    bool finite = isfinite(hi[0] - lo[0]) && isfinite(hi[1] - lo[1]) && isfinite(hi[2] - lo[2]);
+    if (!finite) {
+        atomicOr(&st->error, kErrNonfinite);
+        st->done = 1;
+        for (int i = 0; i < 3; ++i) { lo[i] = 0.0; hi[i] = 0.0; }
+    }
+    double ext = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
+    double s = fmax(d.rmax * (1.0 + 1e-5) + 0.01 + 1e-6 * ext, d.prm.cell_size);
+    s = ceil(s * 1024.0) / 1024.0;
+    for (;;) {
+        long long nx = (long long)floor((hi[0] - lo[0]) / s) + 1;
+        long long ny = (long long)floor((hi[1] - lo[1]) / s) + 1;
+        long long nz = (long long)floor((hi[2] - lo[2]) / s) + 1;
+        if (nx * ny * nz <= (long long)d.cell_cap) {
+            g.nx = (int)nx; g.ny = (int)ny; g.nz = (int)nz;
+            g.ncells = (int)(nx * ny * nz);
+            break;
+        }
+        s = ceil(s * 1.25 * 1024.0) / 1024.0;
+    }
+    g.ox = lo[0]; g.oy = lo[1]; g.oz = lo[2];
+    g.s = s;
+    g.sf = (float)s;
+    g.gpf = (float)(1e-3 + 2e-4 * s);
+    g.inv_sf = 1.0f / (float)s;
+    *d.grid = g;
+    for (int i = 0; i < 3; ++i) { st->bbox[i] = ~0ULL; st->bbox[3 + i] = 0ULL; }
+    st->ticket_bbox = 0u;
+    st->pairs = 0;
+    st->nbr_total = 0;
+    st->guard = 0;
+    st->sasa_tests = 0;
+    st->max_nbr = 0;
+    st->E[0] = 0.0;
+    st->E[1] = 0.0;
+    st->E[2] = 0.0;
+}
+
 }  // namespace dev
 }  // namespace kcm

@@ -47,7 +47,7 @@ struct Status {
     unsigned long long sasa_tests;  // overlap tests performed by Algorithm 1 (steps 1 and 2)
     int max_nbr;
     unsigned int ticket_w;  // last-block detection in the wrench / suffix-scan kernel
-    unsigned int ticket_fk;  // last-block detection in the transform-scan kernel
+    unsigned int ticket_bin;  // last-block detection in the cell-count kernel
     int pad;
 };
 
@@ -55,6 +55,8 @@ struct Status {
 constexpr int kPairWarps = 4;         // home atoms (warps) per block of the pair kernel
 constexpr int kScanCells = 2048;      // cells per block of the cell-count scan
 constexpr int kScanThreadsBig = 256;
+constexpr int kBinThreads = 1024;     // block of the cell-count kernel (its last block scans small grids)
+constexpr int kScanFusedMaxCells = 128 * kBinThreads;  // largest cell array scanned by one block
 constexpr double kPairFxInv = 1.0 / 8388608.0;  // unit of the fraction sums of mixed-mode pair forces
 constexpr float kPairFxMax = 4194304.0f;        // |pair term| below which it is summed in fixed point (2^22)
 constexpr int kPairFoldRounds = 256;            // pair rounds between folds of the int32 lane sums
@@ -69,7 +71,8 @@ struct DevChain {
     int ntiles = 0;      // transform-scan blocks of 64 * fk_j joints
     int ltiles = 0;      // suffix-sum tiles of 32 links
     int cell_cap = 0;
-    int pair_blocks = 0, sasa_blocks = 0, bbox_blocks = 0, scan_blocks = 0;
+    int pair_blocks = 0, sasa_blocks = 0, scan_blocks = 0;
+    int scan_fused = 0;  // cell scan by the last block of the count kernel (cell_cap <= kScanFusedMaxCells)
     kcm_params prm{};
     // derived constants
     double rcut2 = 0, rvdw2 = 0;  // squared pair cutoffs

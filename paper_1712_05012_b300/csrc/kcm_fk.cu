@@ -16,7 +16,8 @@
 // block product goes to tileP. k_fk_apply: block b first reduces the block products 0 .. b-1 to its
 // block prefix (a tree over at most 64 products per round, every block at once), then composes block
 // prefix, quad prefix and running products into the link poses M_{j+1}, the current axes u_j and axis
-// points p_j, and moves the atoms of its links.
+// points p_j, moves the atoms of its links and adds them to the bounding box; its last block to
+// finish (ticket, no waiting) sets the grid of the cell list.
 #include <cuda_runtime.h>
 
 #include "kcm_common.cuh"
@@ -215,6 +216,8 @@ __device__ __forceinline__ void block_prefix(const DevChain& d, int b0, int b1, 
 template <int J>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     __shared__ double sW[kFkWarps][12];
+    __shared__ unsigned long long sB[6][kFkWarps];
+    __shared__ bool sLast;
     if (d.status->done) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
@@ -260,11 +263,45 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     const int hfirst = blockIdx.x == 0 ? 0 : blockIdx.x * kFkQuads * J + 1;
     const int hlast = min((blockIdx.x + 1) * kFkQuads * J + 1, d.L);
     const int a1 = d.link_start[hlast];
+    unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0ULL, 0ULL, 0ULL};
     for (int a = d.link_start[hfirst] + threadIdx.x; a < a1; a += blockDim.x) {
         const double* M = &d.M[12 * (size_t)d.link[a]];
         const double x = d.r0[3 * a], y = d.r0[3 * a + 1], z = d.r0[3 * a + 2];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) d.r[3 * a + i] = M[3 * i] * x + M[3 * i + 1] * y + M[3 * i + 2] * z + M[9 + i];
+        for (int i = 0; i < 3; ++i) {
+            const double v = M[3 * i] * x + M[3 * i + 1] * y + M[3 * i + 2] * z + M[9 + i];
+            d.r[3 * a + i] = v;
+            const unsigned long long key = dkey(v);  // bounding box as order-preserving integer keys
+            mn[i] = min(mn[i], key);
+            mx[i] = max(mx[i], key);
+        }
+    }
+    // bounding box of all centres; the last block to finish sets the grid of the cell list
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[i] = min(mn[i], __shfl_down_sync(0xffffffffu, mn[i], o));
+            mx[i] = max(mx[i], __shfl_down_sync(0xffffffffu, mx[i], o));
+        }
+        if (lane == 0) { sB[i][w] = mn[i]; sB[3 + i][w] = mx[i]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int i = threadIdx.x;
+        unsigned long long v = sB[i][0];
+#pragma unroll
+        for (int k = 1; k < kFkWarps; ++k) v = i < 3 ? min(v, sB[i][k]) : max(v, sB[i][k]);
+        if (i < 3) atomicMin(&d.status->bbox[i], v);
+        else atomicMax(&d.status->bbox[i], v);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sLast = atomicAdd(&d.status->ticket_bbox, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (sLast && threadIdx.x == 0) {
+        __threadfence();
+        finish_grid(d, d.status);
     }
 }
 

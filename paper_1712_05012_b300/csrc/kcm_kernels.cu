@@ -28,111 +28,88 @@ namespace {
 using namespace dev;
 
 // ================================================================ A2: binning
-// Bounding box as order-preserving integer keys (no FP64 min/max); the last block to finish
-// derives the grid, so no separate launch is needed.
-__global__ void k_bbox(const DevChain d) {
-    __shared__ unsigned long long smin[3][8], smax[3][8];
-    __shared__ bool last;
-    Status* st = d.status;
-    if (st->done) return;
-    unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0ULL, 0ULL, 0ULL};
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < d.n; a += gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            unsigned long long key = dkey(d.r[3 * a + i]);
-            mn[i] = min(mn[i], key);
-            mx[i] = max(mx[i], key);
-        }
-    }
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[i] = min(mn[i], __shfl_down_sync(0xffffffffu, mn[i], o));
-            mx[i] = max(mx[i], __shfl_down_sync(0xffffffffu, mx[i], o));
-        }
-        if (lane == 0) { smin[i][w] = mn[i]; smax[i][w] = mx[i]; }
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        int i = threadIdx.x;
-        unsigned long long a = ~0ULL, b = 0ULL;
-        for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) { a = min(a, smin[i][k2]); b = max(b, smax[i][k2]); }
-        atomicMin(&st->bbox[i], a);
-        atomicMax(&st->bbox[3 + i], b);
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&st->ticket_bbox, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    __threadfence();
-    // grid: cube cells of edge s >= every interaction range (plus a margin that absorbs FP32 cell
-    // assignment), s a multiple of 2^-10 A so that it is exact in float; coarsened when the
-    // bounding box would need more cells than the arrays hold
-    double lo[3], hi[3];
-    for (int i = 0; i < 3; ++i) {
-        lo[i] = dkey_inv(atomicAdd(&st->bbox[i], 0ULL));
-        hi[i] = dkey_inv(atomicAdd(&st->bbox[3 + i], 0ULL));
-    }
-    GridInfo g;
-    bool finite = isfinite(hi[0] - lo[0]) && isfinite(hi[1] - lo[1]) && isfinite(hi[2] - lo[2]);
-    if (!finite) {
-        atomicOr(&st->error, kErrNonfinite);
-        st->done = 1;
-        for (int i = 0; i < 3; ++i) { lo[i] = 0.0; hi[i] = 0.0; }
-    }
-    double ext = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
-    double s = fmax(d.rmax * (1.0 + 1e-5) + 0.01 + 1e-6 * ext, d.prm.cell_size);
-    s = ceil(s * 1024.0) / 1024.0;
-    for (;;) {
-        long long nx = (long long)floor((hi[0] - lo[0]) / s) + 1;
-        long long ny = (long long)floor((hi[1] - lo[1]) / s) + 1;
-        long long nz = (long long)floor((hi[2] - lo[2]) / s) + 1;
-        if (nx * ny * nz <= (long long)d.cell_cap) {
-            g.nx = (int)nx; g.ny = (int)ny; g.nz = (int)nz;
-            g.ncells = (int)(nx * ny * nz);
-            break;
-        }
-        s = ceil(s * 1.25 * 1024.0) / 1024.0;
-    }
-    g.ox = lo[0]; g.oy = lo[1]; g.oz = lo[2];
-    g.s = s;
-    g.sf = (float)s;
-    g.gpf = (float)(1e-3 + 2e-4 * s);
-    g.inv_sf = 1.0f / (float)s;
-    *d.grid = g;
-    for (int i = 0; i < 3; ++i) { st->bbox[i] = ~0ULL; st->bbox[3 + i] = 0ULL; }
-    st->ticket_bbox = 0u;
-    st->pairs = 0;
-    st->nbr_total = 0;
-    st->guard = 0;
-    st->sasa_tests = 0;
-    st->max_nbr = 0;
-    st->E[0] = 0.0;
-    st->E[1] = 0.0;
-    st->E[2] = 0.0;
-}
+// (the bounding box and the grid are formed by the last block of the FK apply kernel)
 
 // Cell of each atom (FP32 from the FP64 offset to the grid origin; the cell-edge margin makes
 // the one-cell neighbourhood exact) and its rank within the cell, from one atomic per group of
 // lanes that share a cell. Ranks depend on timing; nothing downstream depends on the order.
-__global__ void k_bin_count(const DevChain d) {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= d.n || d.status->done) return;
-    const GridInfo g = *d.grid;
-    int cx = min(max((int)floorf((float)(d.r[3 * a] - g.ox) * g.inv_sf), 0), g.nx - 1);
-    int cy = min(max((int)floorf((float)(d.r[3 * a + 1] - g.oy) * g.inv_sf), 0), g.ny - 1);
-    int cz = min(max((int)floorf((float)(d.r[3 * a + 2] - g.oz) * g.inv_sf), 0), g.nz - 1);
-    int key = (cz * g.ny + cy) * g.nx + cx;
-    d.key[a] = key;
-    unsigned peers = __match_any_sync(__activemask(), key);
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&d.cell_count[key], __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    d.rank[a] = base + __popc(peers & ((1u << lane) - 1u));
+static_assert(kBinThreads == 1024, "the fused scan of k_bin_count scans 32 warp totals in one warp");
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
+    __shared__ int ws[kBinThreads / 32];
+    __shared__ bool last;
+    if (d.status->done) return;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (a < d.n) {
+        const GridInfo g = *d.grid;
+        int cx = min(max((int)floorf((float)(d.r[3 * a] - g.ox) * g.inv_sf), 0), g.nx - 1);
+        int cy = min(max((int)floorf((float)(d.r[3 * a + 1] - g.oy) * g.inv_sf), 0), g.ny - 1);
+        int cz = min(max((int)floorf((float)(d.r[3 * a + 2] - g.oz) * g.inv_sf), 0), g.nz - 1);
+        int key = (cz * g.ny + cy) * g.nx + cx;
+        d.key[a] = key;
+        unsigned peers = __match_any_sync(__activemask(), key);
+        int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&d.cell_count[key], __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        d.rank[a] = base + __popc(peers & ((1u << lane) - 1u));
+    }
+    if (!d.scan_fused) return;
+    // small grids: the last block scans the cell counts, 4 * kBinThreads cells per pass with coalesced
+    // int4 accesses and a carry between passes, and zeroes them for the next evaluation
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&d.status->ticket_bin, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nc = d.grid->ncells;
+    int carry = 0;
+    for (int base = 0; base < nc; base += 4 * kBinThreads) {
+        const int c = base + 4 * threadIdx.x;
+        int k[4] = {0, 0, 0, 0};
+        if (c + 3 < nc) {
+            const int4 v4 = __ldcg(reinterpret_cast<const int4*>(&d.cell_count[c]));
+            k[0] = v4.x; k[1] = v4.y; k[2] = v4.z; k[3] = v4.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c + q < nc) k[q] = __ldcg(&d.cell_count[c + q]);
+        }
+        const int local = k[0] + k[1] + k[2] + k[3];
+        int v = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) ws[w] = v;
+        __syncthreads();
+        if (w == 0) {
+            int x = ws[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            ws[lane] = x;
+        }
+        __syncthreads();
+        const int s0 = carry + v - local + (w > 0 ? ws[w - 1] : 0);
+        const int st[4] = {s0, s0 + k[0], s0 + k[0] + k[1], s0 + k[0] + k[1] + k[2]};
+        if (c + 3 < nc) {
+            *reinterpret_cast<int4*>(&d.cell_start[c]) = make_int4(st[0], st[1], st[2], st[3]);
+            *reinterpret_cast<int4*>(&d.cell_count[c]) = make_int4(0, 0, 0, 0);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c + q < nc) { d.cell_start[c + q] = st[q]; d.cell_count[c + q] = 0; }
+        }
+        carry += ws[kBinThreads / 32 - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) d.cell_start[nc] = carry;
+    if (threadIdx.x == 0) d.status->ticket_bin = 0u;
 }
 
 // exclusive scan of the cell counts in two passes over blocks of kScanCells cells: block sums,
@@ -802,7 +779,7 @@ __global__ void k_reset_loop(const DevChain d, int full) {
     st->error = 0;
     st->ticket = 0u;
     st->ticket_w = 0u;
-    st->ticket_fk = 0u;
+    st->ticket_bin = 0u;
     st->max_dtheta = 0ULL;
     st->max_abs_tau = 0ULL;
     st->last_max_dtheta = 0.0;
@@ -834,10 +811,11 @@ void launch_reset_loop(DevChain& d, cudaStream_t s) { k_reset_loop<<<1, 1, 0, s>
 
 
 void launch_binning(DevChain& d, cudaStream_t s) {
-    k_bbox<<<d.bbox_blocks, 256, 0, s>>>(d);
-    k_bin_count<<<blocks(d.n, 256), 256, 0, s>>>(d);
-    k_scan_sums<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
-    k_scan_cells<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
+    k_bin_count<<<blocks(d.n, kBinThreads), kBinThreads, 0, s>>>(d);
+    if (!d.scan_fused) {
+        k_scan_sums<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
+        k_scan_cells<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
+    }
     if (d.prm.precision == KCM_MIXED)
         k_bin_place<true><<<blocks(d.n, 256), 256, 0, s>>>(d);
     else
