@@ -158,6 +158,19 @@ int build_timed_graph(kcm_ctx* h) {
 
 int check_handle(kcm_ctx* h) { return h ? KCM_OK : set_err(nullptr, KCM_E_INVAL, "NULL handle"); }
 
+// each double as the float pair (hi, lo), hi = nearest float, lo = nearest float to the rest, stored
+// in the 8 bytes of a double slot (the mixed kernels' double-float format)
+std::vector<double> pack_df(const std::vector<double>& v) {
+    std::vector<double> out(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        float pr[2];
+        pr[0] = static_cast<float>(v[i]);
+        pr[1] = static_cast<float>(v[i] - static_cast<double>(pr[0]));
+        std::memcpy(&out[i], pr, sizeof(pr));
+    }
+    return out;
+}
+
 }  // namespace
 
 extern "C" {
@@ -258,8 +271,8 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = dalloc(h, &d.exm, nn)) || (rc = dalloc(h, &d.m14m, nn)) || (rc = dalloc(h, &d.Q64, 3 * N)) ||
         (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.theta, l)) || (rc = dalloc(h, &d.dtheta, l)) ||
         (rc = dalloc(h, &d.tau, l)) || (rc = dalloc(h, &d.G, 12 * (size_t)l)) ||
-        (rc = dalloc(h, &d.lane_ex, 12 * (size_t)fkq * d.ntiles)) || (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) ||
-        (rc = dalloc(h, &d.tileE, 12 * (size_t)d.ntiles)) ||
+        (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.u0df, 3 * l)) ||
+        (rc = dalloc(h, &d.step0df, 3 * l)) || (rc = dalloc(h, &d.r0df, 3 * nn)) || (rc = dalloc(h, &d.rdf, 3 * nn)) ||
         (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||
         (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.cell_count, d.cell_cap)) ||
         (rc = dalloc(h, &d.cell_start, d.cell_cap + 1)) || (rc = dalloc(h, &d.rank, nn)) || (rc = dalloc(h, &d.scan_part, d.scan_blocks)) ||
@@ -293,6 +306,8 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     kcm::sample_points(N, Q64.data());
     std::vector<float> Q32(Q64.begin(), Q64.end());
     std::vector<double> ident = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
+    if (prm->precision == KCM_MIXED) ident = pack_df(ident);  // M[0] in the mixed kernels' format
+    std::vector<double> u0df = pack_df(hc.u0), step0df = pack_df(hc.step0), r0df = pack_df(hc.zp_rel);
     if ((rc = upload(h, d.r0, hc.zp_rel.data(), 3 * nn)) || (rc = upload(h, d.link, hc.link.data(), nn)) ||
         (rc = upload(h, d.link_start, hc.link_start.data(), L + 1)) || (rc = upload(h, d.u0, hc.u0.data(), 3 * l)) ||
         (rc = upload(h, d.step0, hc.step0.data(), 3 * l)) || (rc = upload(h, d.aprm64, ap64.data(), nn)) ||
@@ -301,7 +316,8 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = upload(h, d.exm, reinterpret_cast<const unsigned long long*>(hc.ex_mask.data()), nn)) ||
         (rc = upload(h, d.m14m, reinterpret_cast<const unsigned long long*>(hc.m14_mask.data()), nn)) ||
         (rc = upload(h, d.Q64, Q64.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q32, Q32.data(), 3 * (size_t)N)) ||
-        (rc = upload(h, d.M, ident.data(), 12)))
+        (rc = upload(h, d.M, ident.data(), 12)) || (rc = upload(h, d.u0df, u0df.data(), 3 * l)) ||
+        (rc = upload(h, d.step0df, step0df.data(), 3 * l)) || (rc = upload(h, d.r0df, r0df.data(), 3 * nn)))
         return bail(rc);
     e = cudaMemsetAsync(d.theta, 0, sizeof(double) * l, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.cell_count, 0, sizeof(int) * d.cell_cap, h->stream);

@@ -86,6 +86,9 @@ struct DevChain {
     int* link = nullptr;           // [n]
     int* link_start = nullptr;     // [L+1]
     double* u0 = nullptr;          // [l*3]
+    double* u0df = nullptr;        // the same as double-float pairs (float hi, lo) for the mixed kernels [l*3]
+    double* step0df = nullptr;     // [l*3]
+    double* r0df = nullptr;        // [n*3]
     double* step0 = nullptr;       // link frame steps p0_j - p0_{j-1} [l*3]
     dbl4* aprm64 = nullptr;     // per atom: q, sqrt(eps), R, Roff
     float4* aprm32 = nullptr;      // the same in float
@@ -101,14 +104,13 @@ struct DevChain {
     double* theta = nullptr;       // [l]
     double* dtheta = nullptr;      // [l]
     double* tau = nullptr;         // [l]
-    double* G = nullptr;           // lane-local prefixes of the joint transforms [l*12]
-    double* lane_ex = nullptr;     // exclusive quad prefixes within blocks [ntiles*64*12]
-    double* tileP = nullptr;       // block products [ntiles*12]
-    double* tileE = nullptr;       // exclusive block prefixes [ntiles*12]
-    double* M = nullptr;           // link frame poses [L*12]
+    double* G = nullptr;           // pose of link j+1 relative to the first frame of its scan block [l*12]
+    double* tileP = nullptr;       // scan block products [ntiles*12]
+    double* M = nullptr;           // link frame poses [L*12] (double-float pairs in mixed mode)
     double* ucur = nullptr;        // current joint axes [l*3]
     double* pcur = nullptr;        // current axis points [l*3]
     double* r = nullptr;           // centres [n*3]
+    double* rdf = nullptr;         // mixed mode: centres as double-float pairs [n*3]
     int* key = nullptr;            // cell of each atom [n]
     int* cell_count = nullptr;     // [cell_cap]
     int* cell_start = nullptr;     // [cell_cap+1]

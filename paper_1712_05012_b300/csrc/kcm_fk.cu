@@ -4,7 +4,9 @@
 // local frames; App. B prefix computation). Atom centres are T_link(r0 - frame origin) (eq. r1, r2).
 //
 // On B300 an FP64 warp instruction occupies a sub-partition's FP64 pipe for about 84 cycles however
-// many of its lanes are active, so the scan is laid out to need few of them on its critical path:
+// many of its lanes are active, so the scan is laid out to need few of them on its critical path
+// (FP64 mode), and the mixed mode runs the same kernels in double-float arithmetic (kcm_df.cuh) on
+// the FP32 pipe, with positions rounded to double at the end:
 // a transform [R | t] is held by a quad of four lanes, lane r of the quad holding row r (R_r0, R_r1,
 // R_r2, t_r) (the fourth lane repeats row 2). A composition A o B then costs each lane one row, 12
 // FP64 instructions, instead of 36 for a whole transform per lane, and a warp holds eight transforms.
@@ -20,7 +22,10 @@
 // finish (ticket, no waiting) sets the grid of the cell list.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kcm_common.cuh"
+#include "kcm_df.cuh"
 #include "kcm_device.h"
 
 namespace kcm {
@@ -32,27 +37,30 @@ constexpr int kFkWarps = 4;               // warps per block of the transform sc
 constexpr int kFkQuads = 8 * kFkWarps;    // quads (transform slots) per block
 
 // row rr of the identity
-__device__ __forceinline__ void row_identity(int rr, double* a) {
-    a[0] = rr == 0 ? 1.0 : 0.0;
-    a[1] = rr == 1 ? 1.0 : 0.0;
-    a[2] = rr == 2 ? 1.0 : 0.0;
-    a[3] = 0.0;
+template <class T>
+__device__ __forceinline__ void row_identity(int rr, T* a) {
+    a[0] = num_f<T>(rr == 0 ? 1.0f : 0.0f);
+    a[1] = num_f<T>(rr == 1 ? 1.0f : 0.0f);
+    a[2] = num_f<T>(rr == 2 ? 1.0f : 0.0f);
+    a[3] = num_f<T>(0.0f);
 }
 
 // the three rows of the quad's transform b (lanes base, base + 1, base + 2), for every lane of the quad
-__device__ __forceinline__ void quad_rows(const double* b, int base, double* B) {
+template <class T>
+__device__ __forceinline__ void quad_rows(const T* b, int base, T* B) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) B[4 * k + m] = __shfl_sync(0xffffffffu, b[m], base + k);
+        for (int m = 0; m < 4; ++m) B[4 * k + m] = shfl(b[m], base + k);
     }
 }
 
 // row of C = A o B from row a of A and the full B (rows B[0..3], B[4..7], B[8..11])
-__device__ __forceinline__ void row_compose(const double* a, const double* B, double* c) {
-    double t[4];
+template <class T>
+__device__ __forceinline__ void row_compose(const T* a, const T* B, T* c) {
+    T t[4];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) t[m] = fma(a[2], B[8 + m], fma(a[1], B[4 + m], a[0] * B[m]));
+    for (int m = 0; m < 3; ++m) t[m] = fma(a[2], B[8 + m], fma(a[1], B[4 + m], mul(a[0], B[m])));
     t[3] = fma(a[2], B[11], fma(a[1], B[7], fma(a[0], B[3], a[3])));
 #pragma unroll
     for (int m = 0; m < 4; ++m) c[m] = t[m];
@@ -60,9 +68,10 @@ __device__ __forceinline__ void row_compose(const double* a, const double* B, do
 
 // row rr of the local joint transform L_j = Tr(step_j) o Rot(u_j, th) with
 // R = cos I + sin [u]x + (1 - cos) u u^T (right-hand rule); the same arithmetic as joint_tf
-__device__ __forceinline__ void joint_row(const double* u, const double* step, double th, int rr, double* g) {
+__device__ __forceinline__ void joint_row(const DevChain& d, int j, int rr, double* g) {
+    const double* u = &d.u0[3 * j];
     double s, c;
-    sincos(th, &s, &c);
+    sincos(d.theta[j], &s, &c);
     const double C = 1.0 - c;
     if (rr == 0) {
         g[0] = c + u[0] * u[0] * C; g[1] = u[0] * u[1] * C - u[2] * s; g[2] = u[0] * u[2] * C + u[1] * s;
@@ -71,39 +80,61 @@ __device__ __forceinline__ void joint_row(const double* u, const double* step, d
     } else {
         g[0] = u[2] * u[0] * C - u[1] * s; g[1] = u[2] * u[1] * C + u[0] * s; g[2] = c + u[2] * u[2] * C;
     }
-    g[3] = step[rr];
+    g[3] = d.step0[3 * j + rr];
+}
+__device__ __forceinline__ void joint_row(const DevChain& d, int j, int rr, df* g) {
+    const df* u = reinterpret_cast<const df*>(d.u0df) + 3 * j;
+    df s, c;
+    df_sincos(d.theta[j], &s, &c);
+    const df C = sub(df{1.0f, 0.0f}, c);
+    const df ur = u[rr];
+    const df urC = mul(ur, C);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) g[m] = mul(urC, u[m]);  // (1 - cos) u_r u_m
+    g[rr] = add(g[rr], c);
+    // + sin [u]x: row 0 (0, -u2, u1), row 1 (u2, 0, -u0), row 2 (-u1, u0, 0)
+    const int m1 = rr == 0 ? 2 : (rr == 1 ? 0 : 1);  // column with +sin u_k
+    const int m2 = rr == 0 ? 1 : (rr == 1 ? 2 : 0);  // column with -sin u_k
+    const int k1 = rr == 0 ? 1 : (rr == 1 ? 2 : 0);
+    const int k2 = rr == 0 ? 2 : (rr == 1 ? 0 : 1);
+    g[m1] = fma(s, u[k1], g[m1]);
+    g[m2] = fma(neg(s), u[k2], g[m2]);
+    g[3] = reinterpret_cast<const df*>(d.step0df)[3 * j + rr];
 }
 
-__device__ __forceinline__ void store_row(double* T, int rr, const double* a) {
-    T[3 * rr] = a[0];
-    T[3 * rr + 1] = a[1];
-    T[3 * rr + 2] = a[2];
-    T[9 + rr] = a[3];
+template <class T>
+__device__ __forceinline__ void store_row(T* M, int rr, const T* a) {
+    M[3 * rr] = a[0];
+    M[3 * rr + 1] = a[1];
+    M[3 * rr + 2] = a[2];
+    M[9 + rr] = a[3];
 }
-__device__ __forceinline__ void load_row(const double* T, int rr, double* a) {
-    a[0] = T[3 * rr];
-    a[1] = T[3 * rr + 1];
-    a[2] = T[3 * rr + 2];
-    a[3] = T[9 + rr];
+template <class T>
+__device__ __forceinline__ void load_row(const T* M, int rr, T* a) {
+    a[0] = M[3 * rr];
+    a[1] = M[3 * rr + 1];
+    a[2] = M[3 * rr + 2];
+    a[3] = M[9 + rr];
 }
-__device__ __forceinline__ void load_rows(const double* T, double* B) {
+template <class T>
+__device__ __forceinline__ void load_rows(const T* M, T* B) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        B[4 * k] = T[3 * k];
-        B[4 * k + 1] = T[3 * k + 1];
-        B[4 * k + 2] = T[3 * k + 2];
-        B[4 * k + 3] = T[9 + k];
+        B[4 * k] = M[3 * k];
+        B[4 * k + 1] = M[3 * k + 1];
+        B[4 * k + 2] = M[3 * k + 2];
+        B[4 * k + 3] = M[9 + k];
     }
 }
 
 // inclusive Kogge-Stone scan over the first NQ quads of a warp (composition on the left)
-template <int NQ = 8>
-__device__ __forceinline__ void warp_scan_quads(double* a, int q, int base) {
+template <int NQ = 8, class T>
+__device__ __forceinline__ void warp_scan_quads(T* a, int q, int base) {
 #pragma unroll
     for (int off = 1; off < NQ; off <<= 1) {
-        double y[4], B[12];
+        T y[4], B[12];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) y[m] = __shfl_up_sync(0xffffffffu, a[m], 4 * off);
+        for (int m = 0; m < 4; ++m) y[m] = shfl_up(a[m], 4 * off);
         quad_rows(a, base, B);
         if (q >= off) row_compose(y, B, a);
     }
@@ -111,13 +142,14 @@ __device__ __forceinline__ void warp_scan_quads(double* a, int q, int base) {
 
 // Scans the transforms held by the block's quads (row a of slot 8 w + q) in place into inclusive
 // block prefixes; the block total is returned in tot (row rr) on every lane. sW: [kFkWarps][12] shared.
-__device__ __forceinline__ void block_scan_quads(double* a, double* tot, double (*sW)[12], int w, int q, int rr,
-                                                 int base, int lane) {
+template <class T>
+__device__ __forceinline__ void block_scan_quads(T* a, T* tot, T (*sW)[12], int w, int q, int rr, int base,
+                                                 int lane) {
     warp_scan_quads(a, q, base);
     if (q == 7 && (lane & 3) < 3) store_row(sW[w], rr, a);
     __syncthreads();
     if (w == 0) {  // scan of the warp totals, quad q <- warp q
-        double t[4];
+        T t[4];
         if (q < kFkWarps) load_row(sW[q], rr, t);
         else row_identity(rr, t);
         warp_scan_quads<kFkWarps>(t, q, base);
@@ -126,7 +158,7 @@ __device__ __forceinline__ void block_scan_quads(double* a, double* tot, double 
     }
     __syncthreads();
     if (w > 0) {  // prefix of the earlier warps o own warp prefix
-        double P[4], B[12];
+        T P[4], B[12];
         load_row(sW[w - 1], rr, P);
         quad_rows(a, base, B);
         row_compose(P, B, a);
@@ -135,87 +167,116 @@ __device__ __forceinline__ void block_scan_quads(double* a, double* tot, double 
     __syncthreads();
 }
 
-template <int J>
+template <int J, class T>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
-    __shared__ double sW[kFkWarps][12];
+    __shared__ T sW[kFkWarps][12];
     if (d.status->done) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
     const int slot = w * 8 + q;
     const int j0 = (blockIdx.x * kFkQuads + slot) * J;
-    // running product of the quad's J joints; the inclusive local prefixes go to G
-    double a[4];
+    T* G = reinterpret_cast<T*>(d.G);
+    // running product of the quad's J joints (the first J - 1 kept in G until the block prefix is known)
+    T a[4];
     row_identity(rr, a);
 #pragma unroll
     for (int i = 0; i < J; ++i) {
         const int j = j0 + i;
-        double g[4];  // joints past the end act as the identity (every lane takes part in the shuffles)
-        if (j < d.l) joint_row(&d.u0[3 * j], &d.step0[3 * j], d.theta[j], rr, g);
+        T g[4];  // joints past the end act as the identity (every lane takes part in the shuffles)
+        if (j < d.l) joint_row(d, j, rr, g);
         else row_identity(rr, g);
         if (i == 0) {
 #pragma unroll
             for (int m = 0; m < 4; ++m) a[m] = g[m];
         } else {
-            double B[12];
+            T B[12];
             quad_rows(g, base, B);
             row_compose(a, B, a);
         }
-        if (j < d.l && (lane & 3) < 3) store_row(&d.G[12 * (size_t)j], rr, a);
+        if (i < J - 1 && j < d.l && (lane & 3) < 3) store_row(&G[12 * (size_t)j], rr, a);
     }
-    // exclusive prefix of the quad within the block
-    double incl[4], tot[4];
+    // block-inclusive prefix of the quad; G_j <- (block prefix before the quad) o running product
+    // through joint j, i.e. the pose of link j + 1 relative to the block's first frame
+    T incl[4], tot[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) incl[m] = a[m];
     block_scan_quads(incl, tot, sW, w, q, rr, base, lane);
-    double ex[4];
+    if (J > 1) {
+        T ex[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) ex[m] = __shfl_up_sync(0xffffffffu, incl[m], 4);
-    if (q == 0) {  // first quad of the warp: the inclusive prefix of the previous warp
-        if (w == 0) row_identity(rr, ex);
-        else load_row(sW[w - 1], rr, ex);  // still valid: written before the last barrier, not reused
+        for (int m = 0; m < 4; ++m) ex[m] = shfl_up(incl[m], 4);
+        if (q == 0) {  // first quad of the warp: the inclusive prefix of the previous warp
+            if (w == 0) row_identity(rr, ex);
+            else load_row(sW[w - 1], rr, ex);  // still valid: written before the last barrier, not reused
+        }
+#pragma unroll
+        for (int i = 0; i < J - 1; ++i) {  // uniform within the quad
+            const int j = j0 + i;
+            if (j < d.l) {
+                T B[12], y[4];
+                load_rows(&G[12 * (size_t)j], B);
+                row_compose(ex, B, y);
+                __syncwarp(0xfu << base);
+                if ((lane & 3) < 3) store_row(&G[12 * (size_t)j], rr, y);
+            }
+        }
     }
-    if ((lane & 3) < 3) store_row(&d.lane_ex[12 * ((size_t)blockIdx.x * kFkQuads + slot)], rr, ex);
-    if (threadIdx.x < 32 && (lane & 3) < 3 && q == 0) store_row(&d.tileP[12 * (size_t)blockIdx.x], rr, tot);
-
+    const int jl = j0 + J - 1;
+    if (jl < d.l && (lane & 3) < 3) store_row(&G[12 * (size_t)jl], rr, incl);
+    if (threadIdx.x < 32 && (lane & 3) < 3 && q == 0)
+        store_row(&reinterpret_cast<T*>(d.tileP)[12 * (size_t)blockIdx.x], rr, tot);
 }
 
-// link poses M_{j+1} = (block prefix o quad prefix) o running product_j; current axis
-// u_j = R(M_j) u0_j through p_j = origin of frame j+1; then the atoms of the block's links
 // row rr of the product tileP[b0] o ... o tileP[b1 - 1] (identity when empty), all warps of the block
-// taking part: two products per quad, then a tree within each warp and over the warps
-__device__ __forceinline__ void block_prefix(const DevChain& d, int b0, int b1, double (*sW)[12], int w, int q, int rr,
-                                             int base, int lane, double* out) {
+// taking part: two products per quad, a tree within each warp, then a tree over the warp products
+template <class T>
+__device__ __forceinline__ void block_prefix(const DevChain& d, int b0, int b1, T (*sW)[12], int w, int q, int rr,
+                                             int base, int lane, T* out) {
+    const T* P = reinterpret_cast<const T*>(d.tileP);
     const int slot = w * 8 + q;
-    double a[4], B[12];
+    T a[4], B[12];
     const int i0 = b0 + 2 * slot, i1 = i0 + 1;
-    if (i0 < b1) load_row(&d.tileP[12 * (size_t)i0], rr, a);
+    if (i0 < b1) load_row(&P[12 * (size_t)i0], rr, a);
     else row_identity(rr, a);
     if (i1 < b1) {  // uniform within the quad
-        load_rows(&d.tileP[12 * (size_t)i1], B);
+        load_rows(&P[12 * (size_t)i1], B);
         row_compose(a, B, a);
     }
 #pragma unroll
     for (int off = 1; off < 8; off <<= 1) {  // tree over the quads of the warp: quad q <- q o q + off
-        double y[4];
+        T y[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) y[m] = __shfl_down_sync(0xffffffffu, a[m], 4 * off);
+        for (int m = 0; m < 4; ++m) y[m] = shfl_down(a[m], 4 * off);
         quad_rows(y, base, B);
         if ((q & (2 * off - 1)) == 0) row_compose(a, B, a);
     }
     if (q == 0 && (lane & 3) < 3) store_row(sW[w], rr, a);
     __syncthreads();
-    load_row(sW[0], rr, out);
+    if (w == 0) {  // tree over the warp products in warp 0, quad q <- warp q
+        if (q < kFkWarps) load_row(sW[q], rr, a);
+        else row_identity(rr, a);
 #pragma unroll
-    for (int v = 1; v < kFkWarps; ++v) {
-        load_rows(sW[v], B);
-        row_compose(out, B, out);
+        for (int off = 1; off < kFkWarps; off <<= 1) {
+            T y[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) y[m] = shfl_down(a[m], 4 * off);
+            quad_rows(y, base, B);
+            if ((q & (2 * off - 1)) == 0) row_compose(a, B, a);
+        }
+        __syncwarp();
+        if (q == 0 && (lane & 3) < 3) store_row(sW[0], rr, a);
     }
+    __syncthreads();
+    load_row(sW[0], rr, out);
     __syncthreads();
 }
 
-template <int J>
+// link poses M_{j+1} = (product of the earlier blocks) o G_j; current axis u_j = R(M_{j+1}) u0_j
+// (the rotation about u0_j leaves u0_j fixed, so R(M_j) u0_j = R(M_{j+1}) u0_j) through p_j = origin
+// of frame j+1; then the atoms of the block's links and the bounding box
+template <int J, class T>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
-    __shared__ double sW[kFkWarps][12];
+    __shared__ T sW[kFkWarps][12];
     __shared__ unsigned long long sB[6][kFkWarps];
     __shared__ bool sLast;
     if (d.status->done) return;
@@ -223,37 +284,35 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
     const int slot = w * 8 + q;
     const int j0 = (blockIdx.x * kFkQuads + slot) * J;
+    T* M = reinterpret_cast<T*>(d.M);
+    const T* G = reinterpret_cast<const T*>(d.G);
     // block prefix: product of the block products before this block, 2 * kFkQuads per round
-    double bE[4];
+    T bE[4];
     row_identity(rr, bE);
     for (int b0 = 0; b0 < (int)blockIdx.x; b0 += 2 * kFkQuads) {
-        double part[4], B[12];
+        T part[4], B[12];
         block_prefix(d, b0, min(b0 + 2 * kFkQuads, (int)blockIdx.x), sW, w, q, rr, base, lane, part);
-        quad_rows(part, base, B);
-        row_compose(bE, B, bE);
+        if (b0 == 0) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) bE[m] = part[m];
+        } else {
+            quad_rows(part, base, B);
+            row_compose(bE, B, bE);
+        }
     }
-    if (j0 < d.l) {  // no shuffles below: quads past the end may leave
-        double X[12], P0[4], Mb[4];
-        load_rows(&d.lane_ex[12 * ((size_t)blockIdx.x * kFkQuads + slot)], X);
-        row_compose(bE, X, P0);  // row rr of the pose before joint j0
 #pragma unroll
-        for (int m = 0; m < 4; ++m) Mb[m] = P0[m];
-#pragma unroll
-        for (int i = 0; i < J; ++i) {
-            const int j = j0 + i;
-            if (j < d.l) {
+    for (int i = 0; i < J; ++i) {
+        const int j = j0 + i;
+        if (j < d.l) {  // uniform within the quad; no shuffles here
+            T Gj[12], Ma[4];
+            load_rows(&G[12 * (size_t)j], Gj);
+            row_compose(bE, Gj, Ma);  // pose of link j + 1
+            if ((lane & 3) < 3) {
                 const double* u = &d.u0[3 * j];
-                const double uc = fma(Mb[2], u[2], fma(Mb[1], u[1], Mb[0] * u[0]));
-                double Gj[12], Ma[4];
-                load_rows(&d.G[12 * (size_t)j], Gj);
-                row_compose(P0, Gj, Ma);  // pose of link j + 1
-                if ((lane & 3) < 3) {
-                    d.ucur[3 * j + rr] = uc;
-                    store_row(&d.M[12 * ((size_t)j + 1)], rr, Ma);
-                    d.pcur[3 * j + rr] = Ma[3];
-                }
-#pragma unroll
-                for (int m = 0; m < 4; ++m) Mb[m] = Ma[m];
+                const T uc = fma(Ma[2], num<T>(u[2]), fma(Ma[1], num<T>(u[1]), mul(Ma[0], num<T>(u[0]))));
+                d.ucur[3 * j + rr] = to_double(uc);
+                store_row(&M[12 * ((size_t)j + 1)], rr, Ma);
+                d.pcur[3 * j + rr] = to_double(Ma[3]);
             }
         }
     }
@@ -263,14 +322,17 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     const int hfirst = blockIdx.x == 0 ? 0 : blockIdx.x * kFkQuads * J + 1;
     const int hlast = min((blockIdx.x + 1) * kFkQuads * J + 1, d.L);
     const int a1 = d.link_start[hlast];
+    const T* r0 = reinterpret_cast<const T*>(std::is_same<T, double>::value ? (const void*)d.r0 : (const void*)d.r0df);
     unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0ULL, 0ULL, 0ULL};
     for (int a = d.link_start[hfirst] + threadIdx.x; a < a1; a += blockDim.x) {
-        const double* M = &d.M[12 * (size_t)d.link[a]];
-        const double x = d.r0[3 * a], y = d.r0[3 * a + 1], z = d.r0[3 * a + 2];
+        const T* Ml = &M[12 * (size_t)d.link[a]];
+        const T x = r0[3 * a], y = r0[3 * a + 1], z = r0[3 * a + 2];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const double v = M[3 * i] * x + M[3 * i + 1] * y + M[3 * i + 2] * z + M[9 + i];
+            const T vt = fma(Ml[3 * i + 2], z, fma(Ml[3 * i + 1], y, fma(Ml[3 * i], x, Ml[9 + i])));
+            const double v = to_double(vt);
             d.r[3 * a + i] = v;
+            if constexpr (!std::is_same<T, double>::value) reinterpret_cast<T*>(d.rdf)[3 * a + i] = vt;
             const unsigned long long key = dkey(v);  // bounding box as order-preserving integer keys
             mn[i] = min(mn[i], key);
             mx[i] = max(mx[i], key);
@@ -307,8 +369,13 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
 
 template <int J>
 void launch_fk_j(DevChain& d, cudaStream_t s) {
-    k_fk_scan<J><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
-    k_fk_apply<J><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+    if (d.prm.precision == KCM_MIXED) {
+        k_fk_scan<J, df><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+        k_fk_apply<J, df><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+    } else {
+        k_fk_scan<J, double><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+        k_fk_apply<J, double><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+    }
 }
 
 }  // namespace
