@@ -238,6 +238,11 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     kcm::DevChain& d = h->d;
     d.prm = *prm;
     d.m = hc.m; d.n = hc.n; d.l = hc.l; d.L = hc.L; d.N = prm->n_sample;
+    for (int h0 = 0; h0 < hc.L; h0 += 32) {  // the wrench kernel stages one 32-link tile in shared memory
+        const int h1 = std::min(h0 + 32, hc.L);
+        if (hc.link_start[h1] - hc.link_start[h0] > kcm::kWrenchTileAtoms)
+            return bail(set_err(h, KCM_E_INVAL, "32 consecutive links hold more atoms than the wrench tile"));
+    }
     d.fk_j = kcm::fk_joints_per_lane(d.l);
     const int fkq = kcm::fk_block_joints();
     d.ntiles = (d.l + fkq * d.fk_j - 1) / (fkq * d.fk_j);
@@ -262,6 +267,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     d.f_rv2 = (float)d.rvdw2;
     d.f_rall2 = (float)(d.rmax * d.rmax) + 0.01f;  // FP32 candidate range, padded for rounding
     d.f_dr = (float)prm->delta_r;
+    d.f_invN = 1.0f / (float)d.N;
 
     const int n = d.n, l = d.l, L = d.L, N = d.N;
     const size_t nn = static_cast<size_t>(n);
@@ -273,6 +279,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = dalloc(h, &d.tau, l)) || (rc = dalloc(h, &d.G, 12 * (size_t)l)) ||
         (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.u0df, 3 * l)) ||
         (rc = dalloc(h, &d.step0df, 3 * l)) || (rc = dalloc(h, &d.r0df, 3 * nn)) || (rc = dalloc(h, &d.rdf, 3 * nn)) ||
+        (rc = dalloc(h, &d.ucurdf, 3 * l)) || (rc = dalloc(h, &d.pcurdf, 3 * l)) || (rc = dalloc(h, &d.G0f, nn)) ||
         (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||
         (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.cell_count, d.cell_cap)) ||
         (rc = dalloc(h, &d.cell_start, d.cell_cap + 1)) || (rc = dalloc(h, &d.rank, nn)) || (rc = dalloc(h, &d.scan_part, d.scan_blocks)) ||
@@ -294,6 +301,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     std::vector<double> G0(n);
     std::vector<long long> qfx(n);
     std::vector<int> gflag(n);
+    std::vector<float> G0f(n);
     for (int a = 0; a < n; ++a) {
         double roff = hc.R[a] + prm->r_probe;
         ap64[a] = kcm::make_dbl4(hc.q[a], std::sqrt(hc.eps[a]), hc.R[a], roff);
@@ -301,6 +309,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         G0[a] = 4.0 * kPi * kcm::gamma_of_class(hc.cls[a]) * roff * roff;  // G^cav_{i,0} of Algorithm 1
         qfx[a] = std::llrint(G0[a] / (static_cast<double>(N) * prm->delta_r) * kcm::kFxScale);
         gflag[a] = G0[a] != 0.0;
+        G0f[a] = static_cast<float>(G0[a]);
     }
     std::vector<double> Q64(3 * (size_t)N);
     kcm::sample_points(N, Q64.data());
@@ -312,7 +321,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = upload(h, d.link_start, hc.link_start.data(), L + 1)) || (rc = upload(h, d.u0, hc.u0.data(), 3 * l)) ||
         (rc = upload(h, d.step0, hc.step0.data(), 3 * l)) || (rc = upload(h, d.aprm64, ap64.data(), nn)) ||
         (rc = upload(h, d.aprm32, ap32.data(), nn)) || (rc = upload(h, d.G0, G0.data(), nn)) ||
-        (rc = upload(h, d.qfx, qfx.data(), nn)) || (rc = upload(h, d.gflag, gflag.data(), nn)) ||
+        (rc = upload(h, d.qfx, qfx.data(), nn)) || (rc = upload(h, d.gflag, gflag.data(), nn)) || (rc = upload(h, d.G0f, G0f.data(), nn)) ||
         (rc = upload(h, d.exm, reinterpret_cast<const unsigned long long*>(hc.ex_mask.data()), nn)) ||
         (rc = upload(h, d.m14m, reinterpret_cast<const unsigned long long*>(hc.m14_mask.data()), nn)) ||
         (rc = upload(h, d.Q64, Q64.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q32, Q32.data(), 3 * (size_t)N)) ||

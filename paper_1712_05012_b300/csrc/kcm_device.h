@@ -63,6 +63,7 @@ constexpr int kPairFoldRounds = 256;            // pair rounds between folds of 
 constexpr int kPairQueue = 64;                  // ring of in-range candidates per warp of the pair kernel (power of 2)
 constexpr int kSasaWarps = 4;
 constexpr int kApplyTpb = 64;
+constexpr int kWrenchTileAtoms = 352;  // atoms of 32 links of at most 11 atoms (checked at creation)
 constexpr int kWrenchWarps = 6;        // warps per 32-link tile of the wrench kernel (one per wrench component in the scan)
 
 struct DevChain {
@@ -79,7 +80,7 @@ struct DevChain {
     double rmax = 0;              // largest interaction range (pair cutoffs, solvation neighbour range)
     double roff_max = 0;          // largest offset-sphere radius
     // the same constants in float for the mixed kernels (no FP64 instruction per warp)
-    float f_K = 0, f_w14e = 0, f_w14v = 0, f_rc2 = 0, f_rv2 = 0, f_rall2 = 0, f_dr = 0;
+    float f_K = 0, f_w14e = 0, f_w14v = 0, f_rc2 = 0, f_rv2 = 0, f_rall2 = 0, f_dr = 0, f_invN = 0;
 
     // static data
     double* r0 = nullptr;          // ZP centres relative to their link frame origin [n*3]
@@ -94,6 +95,7 @@ struct DevChain {
     float4* aprm32 = nullptr;      // the same in float
     double* G0 = nullptr;          // 4 pi gamma Roff^2 [n]
     int* gflag = nullptr;          // G0 != 0 [n]
+    float* G0f = nullptr;          // G0 in float (mixed-mode energies) [n]
     long long* qfx = nullptr;      // G0 / (N dr) in fixed point [n]
     unsigned long long* exm = nullptr;   // [n]
     unsigned long long* m14m = nullptr;  // [n]
@@ -109,6 +111,8 @@ struct DevChain {
     double* M = nullptr;           // link frame poses [L*12] (double-float pairs in mixed mode)
     double* ucur = nullptr;        // current joint axes [l*3]
     double* pcur = nullptr;        // current axis points [l*3]
+    double* ucurdf = nullptr;      // mixed mode: the same as double-float pairs [l*3]
+    double* pcurdf = nullptr;      // [l*3]
     double* r = nullptr;           // centres [n*3]
     double* rdf = nullptr;         // mixed mode: centres as double-float pairs [n*3]
     int* key = nullptr;            // cell of each atom [n]

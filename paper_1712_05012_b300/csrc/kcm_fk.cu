@@ -313,6 +313,10 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
                 d.ucur[3 * j + rr] = to_double(uc);
                 store_row(&M[12 * ((size_t)j + 1)], rr, Ma);
                 d.pcur[3 * j + rr] = to_double(Ma[3]);
+                if constexpr (!std::is_same<T, double>::value) {  // for the double-float torque kernel
+                    reinterpret_cast<T*>(d.ucurdf)[3 * j + rr] = uc;
+                    reinterpret_cast<T*>(d.pcurdf)[3 * j + rr] = Ma[3];
+                }
             }
         }
     }

@@ -1,6 +1,7 @@
-// A7-A9: link wrenches, suffix sums over links, joint torques and the kinetostatic step (FP64).
-// The wrench kernel, which visits every atom once with one thread each, also converts the
-// mixed-mode fixed-point forces to FP64 and adds the cavity energy G0_i f_i of its atoms.
+// A7-A9: link wrenches, suffix sums over links, joint torques and the kinetostatic step: FP64 in
+// FP64 mode, double-float (kcm_df.cuh) in mixed mode; the step itself updates theta in FP64. The
+// wrench kernel, which visits every atom once with one thread each, also converts the mixed-mode
+// fixed-point forces and adds the cavity energy G0_i f_i of its atoms.
 //
 // Wrench of link h about the origin, P_h = [sum r x F ; sum F] (eq. KCM_01/02), and
 // P^agg_k = sum_{h >= k} P_h (Sec. 3.5) as a reverse scan: k_wrench_tile forms P_h from the atoms of
@@ -10,7 +11,10 @@
 // (eq. KCM_07); the last block to finish closes the iteration.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kcm_common.cuh"
+#include "kcm_df.cuh"
 #include "kcm_device.h"
 
 namespace kcm {
@@ -18,82 +22,83 @@ namespace kcm {
 namespace {
 using namespace dev;
 
-// One block per tile of 32 links h in [32 t, 32 t + 32). The block's warps take the tile's atoms in
-// chunks of 32 (one thread per atom: r x F and F, and the conversion of the mixed-mode fixed-point
-// forces); a shuffle sum segmented by link adds each link's atoms within the chunk. A link (at most
-// 11 atoms) meets at most two chunks, so its wrench P_h is part 0 + part 1 in shared memory, in a
-// fixed order. Warp q then scans component q of the tile's P_h from the end (Kogge-Stone), and the
-// last block to finish (ticket, no waiting) forms the exclusive suffix sums of the tile totals.
+// One block per tile of 32 links h in [32 t, 32 t + 32). The block's threads take the tile's atoms
+// (r x F and F, with the conversion of the mixed-mode fixed-point forces) into shared memory; one
+// thread per (component, link) adds the link's atoms in atom order; warp q then scans component q of
+// the tile's P_h from the end (Kogge-Stone), and the last block to finish (ticket, no waiting) forms
+// the exclusive suffix sums of the tile totals.
+template <class T>
 __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChain d) {
-    __shared__ double sP[32][2][6];
+    constexpr bool DF = std::is_same<T, df>::value;
+    __shared__ T sV[kWrenchTileAtoms][6];
+    __shared__ T sP[32][6];
     __shared__ bool last;
     Status* st = d.status;
     if (st->done) return;
     const int t = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h0 = 32 * t, h1 = min(h0 + 32, d.L);
-    for (int x = threadIdx.x; x < 32 * 2 * 6; x += blockDim.x) (&sP[0][0][0])[x] = 0.0;
-    __syncthreads();
     const int a0 = d.link_start[h0], a1 = d.link_start[h1];
-    double Ecav = 0.0;
-    for (int c = a0 + 32 * w; c < a1; c += 32 * kWrenchWarps) {
-        const int a = c + lane;
-        double v[6] = {0, 0, 0, 0, 0, 0};
-        int h = -1 - lane;  // distinct keys for lanes past the tile's last atom
-        if (a < a1) {
-            double fx, fy, fz;
-            if (d.prm.precision == KCM_MIXED) {  // pair forces in fixed point plus oversized terms
-                fx = (double)d.Fpx[3 * a] * kPairFxInv + (double)d.Fov[3 * a];
-                fy = (double)d.Fpx[3 * a + 1] * kPairFxInv + (double)d.Fov[3 * a + 1];
-                fz = (double)d.Fpx[3 * a + 2] * kPairFxInv + (double)d.Fov[3 * a + 2];
-            } else {
-                fx = d.Fpair[3 * a]; fy = d.Fpair[3 * a + 1]; fz = d.Fpair[3 * a + 2];
+    const T* rr = reinterpret_cast<const T*>(DF ? d.rdf : d.r);
+    double Ecav = 0.0;   // FP64 mode
+    float Ecavf = 0.0f;  // mixed mode
+    for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+        T f[3];
+        if constexpr (DF) {  // pair forces in fixed point (2^-23) plus oversized terms, solvation (2^-40)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                f[k] = add(ldexp2(df_from_i64(d.Fpx[3 * a + k]), 0x1p-23f), df{d.Fov[3 * a + k], 0.0f});
+                if (d.prm.solvation) f[k] = add(f[k], ldexp2(df_from_i64(d.Fcav[3 * a + k]), 0x1p-40f));
+            }
+            if (d.prm.solvation && d.gflag[a])  // G^cav_i = G0_i f_i, f_i = 1 - covered_i / N (Sec. 3.4)
+                Ecavf += d.G0f[a] * (1.0f - (float)d.covered[a] * d.f_invN);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                f[k] = d.Fpair[3 * a + k];
+                if (d.prm.solvation) f[k] += (double)d.Fcav[3 * a + k] * kFxInv;
             }
             if (d.prm.solvation) {
-                fx += (double)d.Fcav[3 * a] * kFxInv;
-                fy += (double)d.Fcav[3 * a + 1] * kFxInv;
-                fz += (double)d.Fcav[3 * a + 2] * kFxInv;
-                const double G0a = d.G0[a];  // G^cav_i = G0_i f_i, f_i = 1 - covered_i / N (Sec. 3.4)
+                const double G0a = d.G0[a];
                 if (G0a != 0.0) Ecav += G0a - G0a * (double)d.covered[a] / (double)d.N;
             }
-            const double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
-            v[0] = y * fz - z * fy;
-            v[1] = z * fx - x * fz;
-            v[2] = x * fy - y * fx;
-            v[3] = fx; v[4] = fy; v[5] = fz;
-            h = d.link[a];
         }
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int hp = __shfl_up_sync(0xffffffffu, h, off);
-            const bool take = lane >= off && hp == h;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const double y = __shfl_up_sync(0xffffffffu, v[k], off);
-                if (take) v[k] += y;
-            }
-        }
-        const int hn = __shfl_down_sync(0xffffffffu, h, 1);
-        if (a < a1 && (lane == 31 || hn != h)) {  // last lane of a segment: its sum is one part of P_h
-            const int part = d.link_start[h] < c ? 1 : 0;  // the link began in the previous chunk
-#pragma unroll
-            for (int k = 0; k < 6; ++k) sP[h - h0][part][k] = v[k];
-        }
+        const T x = rr[3 * a], y = rr[3 * a + 1], z = rr[3 * a + 2];
+        T* v = sV[a - a0];
+        v[0] = sub(mul(y, f[2]), mul(z, f[1]));
+        v[1] = sub(mul(z, f[0]), mul(x, f[2]));
+        v[2] = sub(mul(x, f[1]), mul(y, f[0]));
+        v[3] = f[0]; v[4] = f[1]; v[5] = f[2];
     }
     if (d.prm.solvation) {  // cavity energy of the block's atoms
-        Ecav = warp_sum(Ecav);
-        if (lane == 0 && Ecav != 0.0) atomicAdd(&st->E[2], Ecav);
+        if constexpr (DF) {
+            Ecavf = warp_sum(Ecavf);
+            if (lane == 0 && Ecavf != 0.0f) atomicAdd(&st->E[2], (double)Ecavf);
+        } else {
+            Ecav = warp_sum(Ecav);
+            if (lane == 0 && Ecav != 0.0) atomicAdd(&st->E[2], Ecav);
+        }
     }
     __syncthreads();
-    if (w < 6) {  // reverse inclusive scan of component w over the tile (links 1..l; link 0 has no joint)
+    for (int u = threadIdx.x; u < 6 * 32; u += blockDim.x) {  // P_h component u / 32 of link h0 + u % 32
+        const int k = u >> 5, h = h0 + (u & 31);
+        T s = num_f<T>(0.0f);
+        if (h >= 1 && h < h1)  // links 1..l (link 0 has no joint)
+            for (int a = d.link_start[h]; a < d.link_start[h + 1]; ++a) s = add(s, sV[a - a0][k]);
+        sP[u & 31][k] = s;
+    }
+    __syncthreads();
+    T* lane_suf = reinterpret_cast<T*>(d.lane_suf);
+    T* tileS = reinterpret_cast<T*>(d.tileS);
+    if (w < 6) {  // reverse inclusive scan of component w over the tile
         const int h = h0 + lane;
-        double x = (h >= 1 && h < h1) ? sP[lane][0][w] + sP[lane][1][w] : 0.0;
+        T x = sP[lane][w];
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const double y = __shfl_down_sync(0xffffffffu, x, off);
-            if (lane + off < 32) x += y;
+            const T y = shfl_down(x, off);
+            if (lane + off < 32) x = add(x, y);
         }
-        if (h < d.L) d.lane_suf[6 * (size_t)h + w] = x;
-        if (lane == 0) d.tileS[6 * (size_t)t + w] = x;
+        if (h < d.L) lane_suf[6 * (size_t)h + w] = x;
+        if (lane == 0) tileS[6 * (size_t)t + w] = x;
     }
     __threadfence();
     __syncthreads();
@@ -101,28 +106,34 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     __syncthreads();
     if (!last) return;
     __threadfence();
+    T* tileSuf = reinterpret_cast<T*>(d.tileSuf);
     if (w < 6) {  // exclusive suffix sums of the tile totals, 32 tiles per round from the end
-        double carry = 0.0;
+        T carry = num_f<T>(0.0f);
         for (int top = d.ltiles; top > 0; top -= 32) {
             const int tt = top - 32 + lane;
-            double x = tt >= 0 ? __ldcg(&d.tileS[6 * (size_t)tt + w]) : 0.0;
+            T x = num_f<T>(0.0f);
+            if (tt >= 0) {
+                const double raw = __ldcg(&d.tileS[6 * (size_t)tt + w]);  // the slot of a T, read past L1
+                x = *reinterpret_cast<const T*>(&raw);
+            }
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
-                const double y = __shfl_down_sync(0xffffffffu, x, off);
-                if (lane + off < 32) x += y;
+                const T y = shfl_down(x, off);
+                if (lane + off < 32) x = add(x, y);
             }
-            double e = __shfl_down_sync(0xffffffffu, x, 1);
-            if (lane == 31) e = 0.0;
-            if (tt >= 0) d.tileSuf[6 * (size_t)tt + w] = e + carry;
-            carry += __shfl_sync(0xffffffffu, x, 0);
+            T e = shfl_down(x, 1);
+            if (lane == 31) e = num_f<T>(0.0f);
+            if (tt >= 0) tileSuf[6 * (size_t)tt + w] = add(e, carry);
+            carry = add(carry, shfl(x, 0));
         }
     }
     if (threadIdx.x == 0) st->ticket_w = 0u;
 }
 
 // tau_k from P^agg; with STEP the clamped step and the end of the iteration
-template <bool STEP>
+template <bool STEP, class T>
 __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
+    constexpr bool DF = std::is_same<T, df>::value;
     __shared__ unsigned long long smax[4];
     __shared__ bool last;
     Status* st = d.status;
@@ -132,13 +143,19 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
     bool bad = false;
     if (jj < d.l) {
         const int h = jj + 1, tile = h >> 5;  // joint jj moves links jj+1 .. l
-        double A[6];
+        const T* ls = reinterpret_cast<const T*>(d.lane_suf);
+        const T* ts = reinterpret_cast<const T*>(d.tileSuf);
+        T A[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) A[k] = d.lane_suf[6 * (size_t)h + k] + d.tileSuf[6 * (size_t)tile + k];
-        const double* u = &d.ucur[3 * jj];
-        const double* p = &d.pcur[3 * jj];
-        const double px = p[1] * u[2] - p[2] * u[1], py = p[2] * u[0] - p[0] * u[2], pz = p[0] * u[1] - p[1] * u[0];
-        const double t = u[0] * A[0] + u[1] * A[1] + u[2] * A[2] + px * A[3] + py * A[4] + pz * A[5];
+        for (int k = 0; k < 6; ++k) A[k] = add(ls[6 * (size_t)h + k], ts[6 * (size_t)tile + k]);
+        const T* u = reinterpret_cast<const T*>(DF ? d.ucurdf : d.ucur) + 3 * jj;
+        const T* p = reinterpret_cast<const T*>(DF ? d.pcurdf : d.pcur) + 3 * jj;
+        const T px = sub(mul(p[1], u[2]), mul(p[2], u[1]));
+        const T py = sub(mul(p[2], u[0]), mul(p[0], u[2]));
+        const T pz = sub(mul(p[0], u[1]), mul(p[1], u[0]));
+        const T tt = add(add(add(mul(u[0], A[0]), mul(u[1], A[1])), add(mul(u[2], A[2]), mul(px, A[3]))),
+                         add(mul(py, A[4]), mul(pz, A[5])));
+        const double t = to_double(tt);
         d.tau[jj] = t;
         bad = !isfinite(t);
         atau = (unsigned long long)__double_as_longlong(fabs(t));
@@ -227,19 +244,30 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
 }  // namespace
 
 void launch_torques(DevChain& d, cudaStream_t s) {
-    k_wrench_tile<<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
-    k_torque<false><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+    if (d.prm.precision == KCM_MIXED) {
+        k_wrench_tile<df><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+        k_torque<false, df><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+    } else {
+        k_wrench_tile<double><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+        k_torque<false, double><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+    }
+}
+
+template <class T>
+void launch_torques_step_t(DevChain& d, cudaStream_t s) {
+    k_wrench_tile<T><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+    if (d.prm.step_mode == KCM_STEP_CLAMP) {
+        k_torque<true, T><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+    } else {
+        k_torque<false, T><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+        k_step_normalized<<<(d.l + 127) / 128, 128, 0, s>>>(d);
+    }
 }
 
 // torques plus the step of one iteration (the evaluation kernels must already be enqueued)
 void launch_torques_step(DevChain& d, cudaStream_t s) {
-    k_wrench_tile<<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
-    if (d.prm.step_mode == KCM_STEP_CLAMP) {
-        k_torque<true><<<(d.l + 127) / 128, 128, 0, s>>>(d);
-    } else {
-        k_torque<false><<<(d.l + 127) / 128, 128, 0, s>>>(d);
-        k_step_normalized<<<(d.l + 127) / 128, 128, 0, s>>>(d);
-    }
+    if (d.prm.precision == KCM_MIXED) launch_torques_step_t<df>(d, s);
+    else launch_torques_step_t<double>(d, s);
 }
 
 }  // namespace kcm
