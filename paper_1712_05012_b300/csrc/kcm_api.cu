@@ -260,6 +260,7 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     d.roff_max = rmaxR + prm->r_probe;
     d.rmax = std::max(prm->cutoff, rv);
     if (prm->solvation) d.rmax = std::max(d.rmax, 2.0 * d.roff_max + prm->delta_r + 0.02);
+    d.s_base = d.rmax * (1.0 + 1e-5) + 0.01;
     d.f_K = (float)prm->coulomb_k;
     d.f_w14e = (float)prm->w14_elec;
     d.f_w14v = (float)prm->w14_vdw;

@@ -119,19 +119,26 @@ __device__ __forceinline__ void finish_grid(const DevChain& d, Status* st) {
         st->done = 1;
         for (int i = 0; i < 3; ++i) { lo[i] = 0.0; hi[i] = 0.0; }
     }
-    double ext = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
-    double s = fmax(d.rmax * (1.0 + 1e-5) + 0.01 + 1e-6 * ext, d.prm.cell_size);
-    s = ceil(s * 1024.0) / 1024.0;
+    const double ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    double s = fmax(fma(1e-6, fmax(ext[0], fmax(ext[1], ext[2])), d.s_base), d.prm.cell_size);
+    s = ceil(s * 1024.0) * (1.0 / 1024.0);
     for (;;) {
-        long long nx = (long long)floor((hi[0] - lo[0]) / s) + 1;
-        long long ny = (long long)floor((hi[1] - lo[1]) / s) + 1;
-        long long nz = (long long)floor((hi[2] - lo[2]) / s) + 1;
-        if (nx * ny * nz <= (long long)d.cell_cap) {
-            g.nx = (int)nx; g.ny = (int)ny; g.nz = (int)nz;
-            g.ncells = (int)(nx * ny * nz);
+        // n_i = floor(ext_i / s) + 1 estimated in float, then raised until n_i s > ext_i holds exactly
+        // (n_i s is exact: s is a multiple of 2^-10), so the cells cover the box
+        const float inv = 1.0f / (float)s;
+        long long nn[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            long long k = (long long)floorf((float)ext[i] * inv) + 1;
+            while ((double)k * s <= ext[i]) ++k;
+            nn[i] = k;
+        }
+        if (nn[0] * nn[1] * nn[2] <= (long long)d.cell_cap) {
+            g.nx = (int)nn[0]; g.ny = (int)nn[1]; g.nz = (int)nn[2];
+            g.ncells = (int)(nn[0] * nn[1] * nn[2]);
             break;
         }
-        s = ceil(s * 1.25 * 1024.0) / 1024.0;
+        s = ceil(s * 1.25 * 1024.0) * (1.0 / 1024.0);
     }
     g.ox = lo[0]; g.oy = lo[1]; g.oz = lo[2];
     g.s = s;

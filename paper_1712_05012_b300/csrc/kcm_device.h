@@ -79,6 +79,7 @@ struct DevChain {
     double rcut2 = 0, rvdw2 = 0;  // squared pair cutoffs
     double rmax = 0;              // largest interaction range (pair cutoffs, solvation neighbour range)
     double roff_max = 0;          // largest offset-sphere radius
+    double s_base = 0;            // cell edge before its extent-dependent margin: rmax (1 + 1e-5) + 0.01 A
     // the same constants in float for the mixed kernels (no FP64 instruction per warp)
     float f_K = 0, f_w14e = 0, f_w14v = 0, f_rc2 = 0, f_rv2 = 0, f_rall2 = 0, f_dr = 0, f_invN = 0;
 

@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
     }
     if (!d.scan_fused) return;
     // small grids: the last block scans the cell counts, 4 * kBinThreads cells per pass with coalesced
-    // int4 accesses and a carry between passes, and zeroes them for the next evaluation
+    // int4 accesses (the loads of eight passes in flight together) and a carry between passes, and
+    // zeroes them for the next evaluation
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(&d.status->ticket_bin, 1u) == gridDim.x - 1;
@@ -64,49 +65,58 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
     if (!last) return;
     __threadfence();
     const int nc = d.grid->ncells;
+    constexpr int kPass = 4 * kBinThreads;  // cells per pass
+    constexpr int kPre = 8;                 // passes whose loads are in flight together
     int carry = 0;
-    for (int base = 0; base < nc; base += 4 * kBinThreads) {
-        const int c = base + 4 * threadIdx.x;
-        int k[4] = {0, 0, 0, 0};
-        if (c + 3 < nc) {
-            const int4 v4 = __ldcg(reinterpret_cast<const int4*>(&d.cell_count[c]));
-            k[0] = v4.x; k[1] = v4.y; k[2] = v4.z; k[3] = v4.w;
-        } else {
+    for (int g0 = 0; g0 < nc; g0 += kPre * kPass) {
+        int k[kPre][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (c + q < nc) k[q] = __ldcg(&d.cell_count[c + q]);
-        }
-        const int local = k[0] + k[1] + k[2] + k[3];
-        int v = local;
+        for (int p = 0; p < kPre; ++p) {
+            const int c = g0 + p * kPass + 4 * threadIdx.x;
+            if (c + 3 < nc) {
+                const int4 v4 = __ldcg(reinterpret_cast<const int4*>(&d.cell_count[c]));
+                k[p][0] = v4.x; k[p][1] = v4.y; k[p][2] = v4.z; k[p][3] = v4.w;
+            } else {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
+                for (int q = 0; q < 4; ++q) k[p][q] = c + q < nc ? __ldcg(&d.cell_count[c + q]) : 0;
+            }
         }
-        if (lane == 31) ws[w] = v;
-        __syncthreads();
-        if (w == 0) {
-            int x = ws[lane];
+#pragma unroll
+        for (int p = 0; p < kPre; ++p) {
+            if (g0 + p * kPass >= nc) break;  // uniform
+            const int c = g0 + p * kPass + 4 * threadIdx.x;
+            const int local = k[p][0] + k[p][1] + k[p][2] + k[p][3];
+            int v = local;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
+                const int y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
             }
-            ws[lane] = x;
-        }
-        __syncthreads();
-        const int s0 = carry + v - local + (w > 0 ? ws[w - 1] : 0);
-        const int st[4] = {s0, s0 + k[0], s0 + k[0] + k[1], s0 + k[0] + k[1] + k[2]};
-        if (c + 3 < nc) {
-            *reinterpret_cast<int4*>(&d.cell_start[c]) = make_int4(st[0], st[1], st[2], st[3]);
-            *reinterpret_cast<int4*>(&d.cell_count[c]) = make_int4(0, 0, 0, 0);
-        } else {
+            if (lane == 31) ws[w] = v;
+            __syncthreads();
+            if (w == 0) {
+                int x = ws[lane];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (c + q < nc) { d.cell_start[c + q] = st[q]; d.cell_count[c + q] = 0; }
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                ws[lane] = x;
+            }
+            __syncthreads();
+            const int s0 = carry + v - local + (w > 0 ? ws[w - 1] : 0);
+            const int st[4] = {s0, s0 + k[p][0], s0 + k[p][0] + k[p][1], s0 + k[p][0] + k[p][1] + k[p][2]};
+            if (c + 3 < nc) {
+                *reinterpret_cast<int4*>(&d.cell_start[c]) = make_int4(st[0], st[1], st[2], st[3]);
+                *reinterpret_cast<int4*>(&d.cell_count[c]) = make_int4(0, 0, 0, 0);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c + q < nc) { d.cell_start[c + q] = st[q]; d.cell_count[c + q] = 0; }
+            }
+            carry += ws[kBinThreads / 32 - 1];
+            __syncthreads();
         }
-        carry += ws[kBinThreads / 32 - 1];
-        __syncthreads();
     }
     if (threadIdx.x == 0) d.cell_start[nc] = carry;
     if (threadIdx.x == 0) d.status->ticket_bin = 0u;
