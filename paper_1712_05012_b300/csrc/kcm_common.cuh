@@ -65,6 +65,14 @@ __device__ __forceinline__ T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
+// exact warp sum of int32 values with |v| <= 2^30, as int64: 32-bit reductions of the two 16-bit
+// halves of v + 2^30 (each half-sum fits in 32 bits)
+__device__ __forceinline__ long long warp_sum_i32(int v) {
+    const unsigned u = (unsigned)(v + (1 << 30));
+    const unsigned hs = __reduce_add_sync(0xffffffffu, u >> 16);
+    const unsigned ls = __reduce_add_sync(0xffffffffu, u & 0xFFFFu);
+    return ((long long)hs << 16) + (long long)ls - 32LL * (1LL << 30);
+}
 __device__ __forceinline__ int warp_max(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));

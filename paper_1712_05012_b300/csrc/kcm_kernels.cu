@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     typedef typename std::conditional<MIXED, float4, dbl4>::type QV;
     __shared__ int s_beg[kPairWarps][32];
     __shared__ int s_off[kPairWarps][32];
+    __shared__ float4 s_sh[kPairWarps][27];
     __shared__ QV s_qv[kPairWarps][kPairQueue];   // queued pairs: r_i - r_j, d^2
     __shared__ int s_qts[kPairWarps][kPairQueue];  // queued pairs: sorted slot of j
     __shared__ R sE[2][kPairWarps];
@@ -256,16 +257,19 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sl = blockIdx.x * kPairWarps + w;
     R Eel = 0, Evdw = 0;
-    unsigned long long npairs = 0, nguard = 0;
+    unsigned npairs = 0, nguard = 0;
     int ncount = 0;
     if (sl < d.n && !d.status->done) {
         const GridInfo g = *d.grid;
         const int a = d.sorted[sl];
         const int cell = d.slot_cell[sl];
         const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
+        // the non-empty cells among the 27 neighbours, compacted in stencil order: first slot, offset
+        // of their candidates in the concatenation, and (mixed) the shift (c_j - c_i) s
         int beg = 0, len = 0;
+        const int dxc = lane % 3 - 1, dyc = (lane / 3) % 3 - 1, dzc = lane / 9 - 1;
         if (lane < 27) {
-            int ncx = cx + lane % 3 - 1, ncy = cy + (lane / 3) % 3 - 1, ncz = cz + lane / 9 - 1;
+            int ncx = cx + dxc, ncy = cy + dyc, ncz = cz + dzc;
             if (ncx >= 0 && ncx < g.nx && ncy >= 0 && ncy < g.ny && ncz >= 0 && ncz < g.nz) {
                 int nc = (ncz * g.ny + ncy) * g.nx + ncx;
                 beg = d.cell_start[nc];
@@ -278,8 +282,14 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        s_beg[w][lane] = beg;
-        s_off[w][lane] = incl - len;
+        const unsigned nem = __ballot_sync(0xffffffffu, len > 0);
+        const int nne = __popc(nem);
+        if (len > 0) {
+            const int cslot = __popc(nem & ((1u << lane) - 1u));
+            s_beg[w][cslot] = beg;
+            s_off[w][cslot] = incl - len;
+            s_sh[w][cslot] = make_float4((float)dxc * g.sf, (float)dyc * g.sf, (float)dzc * g.sf, 0.0f);
+        }
         __syncwarp();
         R K, w14e, w14v, rc2, rv2, rall2, gp, dr, pad;
         if constexpr (MIXED) {
@@ -311,6 +321,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         // in a ring of kPairQueue; phase B evaluates 32 queued pairs at a time, so the pair terms run
         // with every lane busy instead of the ~30 % of candidates that are in range.
         int qhead = 0, qtail = 0, nround = 0;
+        bool folded = false;  // uniform
         auto phase_b = [&](int nvalid) {
             const int e = (qhead + lane) & (kPairQueue - 1);
             bool isn = false;
@@ -407,6 +418,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                     Hx += hix; Hy += hiy; Hz += hiz; Lx += lox; Ly += loy; Lz += loz;
                     hix = hiy = hiz = lox = loy = loz = 0;
                     nround = 0;
+                    folded = true;
                 }
             }
         };
@@ -416,15 +428,15 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             QV v;
             int ts = 0;
             if (k2 < total) {
-                while (t < 26 && s_off[w][t + 1] <= k2) ++t;
+                while (t < nne - 1 && s_off[w][t + 1] <= k2) ++t;
                 ts = s_beg[w][t] + (k2 - s_off[w][t]);
                 if (ts != sl) {
                     R ddx, ddy, ddz;
                     if constexpr (MIXED) {
-                        float4 p = d.spos32[ts];
-                        const R shx = (R)(t % 3 - 1) * sf, shy = (R)((t / 3) % 3 - 1) * sf, shz = (R)(t / 9 - 1) * sf;
+                        const float4 p = d.spos32[ts];
+                        const float4 sh = s_sh[w][t];
                         // r_i - r_j = (o_i - o_j) - (c_j - c_i) s
-                        ddx = (px - p.x) - shx; ddy = (py - p.y) - shy; ddz = (pz - p.z) - shz;
+                        ddx = (px - p.x) - sh.x; ddy = (py - p.y) - sh.y; ddz = (pz - p.z) - sh.z;
                     } else {
                         dbl4 p = d.spos64[ts];
                         ddx = __dsub_rn(px, p.x); ddy = __dsub_rn(py, p.y); ddz = __dsub_rn(pz, p.z);
@@ -449,11 +461,16 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         }
         if (qtail > qhead) phase_b(qtail - qhead);
         if constexpr (MIXED) {
-            Hx += hix; Hy += hiy; Hz += hiz; Lx += lox; Ly += loy; Lz += loz;
-        }
-        if constexpr (MIXED) {
-            Hx = warp_sum(Hx); Hy = warp_sum(Hy); Hz = warp_sum(Hz);
-            Lx = warp_sum(Lx); Ly = warp_sum(Ly); Lz = warp_sum(Lz);
+            // lane sums: int32 pieces (|.| <= 2^30) by 32-bit warp reductions of their biased 16-bit
+            // halves; the int64 folds (more than kPairFoldRounds rounds) only where they happened
+            if (folded) {  // uniform
+                Hx = warp_sum(Hx); Hy = warp_sum(Hy); Hz = warp_sum(Hz);
+                Lx = warp_sum(Lx); Ly = warp_sum(Ly); Lz = warp_sum(Lz);
+            } else {
+                Hx = Hy = Hz = Lx = Ly = Lz = 0;
+            }
+            Hx += warp_sum_i32(hix); Hy += warp_sum_i32(hiy); Hz += warp_sum_i32(hiz);
+            Lx += warp_sum_i32(lox); Ly += warp_sum_i32(loy); Lz += warp_sum_i32(loz);
             ovx = warp_sum(ovx); ovy = warp_sum(ovy); ovz = warp_sum(ovz);
             ove = warp_sum(ove); ovv = warp_sum(ovv);
             if (lane == 0) {  // converted to FP64 by the thread-per-atom consumers
@@ -469,8 +486,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             Eel = warp_sum(Eel); Evdw = warp_sum(Evdw);
             if (lane == 0) { d.Fpair[3 * a] = dfx; d.Fpair[3 * a + 1] = dfy; d.Fpair[3 * a + 2] = dfz; }
         }
-        npairs = warp_sum(npairs);
-        nguard = warp_sum(nguard);
+        npairs = __reduce_add_sync(0xffffffffu, npairs);
+        nguard = __reduce_add_sync(0xffffffffu, nguard);
         if (lane == 0) {
             d.nbr_cnt[a] = ncount;
             if (ncount > kMaxNbr) atomicOr(&d.status->error, kErrOverflow);
