@@ -44,6 +44,9 @@ FP32_LANES_PER_SM = 128
 FLOPS_PER_SASA_TEST = 9  # w = v - o (3), |w|^2 (1 mul + 2 FMA = 5), compare with Roff^2 (1)
 FLOPS_PER_PAIR = 31      # per unordered pair within the cutoff (distance, 1/d^2, Coulomb, LJ, weights, accumulate)
 BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques_step": 60}  # algorithmic HBM bytes per atom
+# DRAM bytes (read + write) per launch of the stage's kernels on this workload, from one ncu capture
+# of the current kernels (profiles/k_sasa_mixed_chain1000.md); None where not captured
+DRAM_BYTES_PER_LAUNCH = {"solvation": 6.92e6}
 KERNELS_PER_ITERATION = {1: 9, 0: 8}  # reset + kinematics 2 + binning 2 + pairs 1 + solvation 1 + wrench-tile 1 + torque-step 1
 
 
@@ -122,25 +125,35 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_baseline(seq, theta, params, budget_s=12.0):
+def oracle_baseline(seq, theta, params, budget_s=12.0, budget_1core_s=8.0):
     """The oracle (FP64, all-pairs, OpenMP over atoms) on the machine's host cores: KCM iterations of
-    the same workload for about `budget_s` seconds."""
+    the same workload for about `budget_s` seconds on all cores, then about `budget_1core_s` on one."""
     from oracle import oracle as O
     from paper_1712_05012_b300 import synth
 
     table = synth.type_table()
     ch = O.OracleChain(seq, table, synth.GEOMETRY)
-    t0 = time.perf_counter()
-    ch.run(params, np.array(theta), 1)
-    t1 = time.perf_counter() - t0
-    iters = max(1, min(200, int(budget_s / max(t1, 1e-6))))
-    t0 = time.perf_counter()
-    for _ in range(iters):  # each iteration from the stored start, as the GPU steps are timed
+
+    def timed(budget):
+        t0 = time.perf_counter()
         ch.run(params, np.array(theta), 1)
-    wall = time.perf_counter() - t0
-    return {"value": ch.n * iters / wall, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{iters} FP64 oracle iterations of the 1,000-residue chain ({ch.n} atoms), each from its "
-                      f"compact start, {wall:.1f} s wall"}, ch
+        t1 = time.perf_counter() - t0
+        iters = max(1, min(200, int(budget / max(t1, 1e-6))))
+        t0 = time.perf_counter()
+        for _ in range(iters):  # each iteration from the stored start, as the GPU steps are timed
+            ch.run(params, np.array(theta), 1)
+        return iters, time.perf_counter() - t0
+
+    cores = O.num_threads()
+    iters, wall = timed(budget_s)
+    O.set_threads(1)
+    iters1, wall1 = timed(budget_1core_s)
+    O.set_threads(cores)
+    return {"value": ch.n * iters / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1core": ch.n * iters1 / wall1,
+            "sample": f"{iters} FP64 oracle iterations of the 1,000-residue chain ({ch.n} atoms) on {cores} threads, "
+                      f"{wall:.1f} s wall, and {iters1} on 1 thread, {wall1:.1f} s wall; each iteration from "
+                      f"the compact start"}, ch
 
 
 def run_reference(args):
@@ -228,28 +241,50 @@ def run_ours(args):
     value = ws * n * args.steps / t_sum
     ms_stage = {k: v / args.steps for k, v in stages.items()}
 
-    # roofline of the dominant stage (work counted at the last timed iteration)
-    dom = max(ms_stage, key=ms_stage.get)
+    # rooflines of every stage (work counted at the last timed iteration); the dominant one is the
+    # headline "roofline"
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sm_max = (clk or {}).get("sm_max_mhz") or 2032.0
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6400.0}
-    sec = ms_stage[dom] / 1e3
-    if dom == "solvation":
-        work = stats["sasa_tests"] * FLOPS_PER_SASA_TEST
-        roof = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
-    elif dom == "pairs":
-        work = stats["pairs"] * FLOPS_PER_PAIR
-        roof = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
-    else:
-        work = BYTES_PER_ATOM.get(dom, 24) * n
-        roof = {"bound": "hbm", "achieved": work / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    rooflines = {}
+    for stage, ms in ms_stage.items():
+        sec = ms / 1e3
+        if stage == "solvation":
+            work = stats["sasa_tests"] * FLOPS_PER_SASA_TEST
+            r = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"}
+        elif stage == "pairs":
+            work = stats["pairs"] * FLOPS_PER_PAIR
+            r = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"}
+        else:
+            work = BYTES_PER_ATOM[stage] * n
+            r = {"bound": "hbm", "achieved": work / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+        r["frac"] = r["achieved"] / r["peak"]
+        r["ms_per_launch"] = ms
+        r["work_per_launch"] = work
+        rooflines[stage] = r
+    dom = max(ms_stage, key=ms_stage.get)
+    roof = {k: v for k, v in rooflines[dom].items()}
     roof["kernel"] = dom
-    roof["ms_per_launch"] = ms_stage[dom]
-    roof["work_per_launch"] = work
+    roof["traffic"] = DRAM_BYTES_PER_LAUNCH.get(dom)
+
+    # the same step with solvation off (the paper's vacuum runs), measured the same way
+    vacuum_value = None
+    if args.fp64_steps > 0:
+        with kcm.Chain(seq, table, synth.RunParams(precision=prec, solvation=0)) as cv:
+            sv = torch.cuda.ExternalStream(cv.stream())
+            for _ in range(3):
+                prepare(cv, sv)
+                cv.step_timed()
+            tt = []
+            for _ in range(args.fp64_steps):
+                prepare(cv, sv)
+                tt.append(cv.step_timed()[0])
+            vacuum_value = n * args.fp64_steps / (sum(tt) / 1e3)
 
     # the plain FP64 single-chain GPU path, measured the same way
     fp64_value = None
@@ -311,7 +346,8 @@ def run_ours(args):
                            "n_sample": 256, "solvation": 1, "precision": args.precision,
                            "replicas": ws, "l2": "flushed between timed steps (256 MiB write)",
                            "start": "every step from the stored compact start (theta restored untimed)"},
-                "roofline": roof, "stage_ms": ms_stage, "fp64_value": fp64_value,
+                "roofline": roof, "rooflines": rooflines, "stage_ms": ms_stage, "fp64_value": fp64_value,
+                "vacuum_value": vacuum_value,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,
                 "clocks": clk, "stats": {k: stats[k] for k in ("pairs", "sasa_tests", "sasa_neighbors",

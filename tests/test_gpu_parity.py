@@ -127,6 +127,27 @@ def test_fp64_trajectory_chain40(kcm, table):
         assert abs(dm - dm_ref[-1]) < 1e-8
 
 
+def test_mixed_trajectory_rmsd_chain40(kcm, table):
+    """Trajectory gate of the mixed path: backbone (N, CA, C) RMSD against the FP64 path after 100
+    iterations of the 40-residue extended chain with solvation off (a smooth trajectory; measured
+    1.4e-4 A). From the compact 1,000-residue start the trajectory is chaotic: two FP64 runs that
+    differ only in the order of the pair sums already differ by 0.06 A after two iterations and by
+    hundreds of A after ten, so there the gate is per-iteration torque parity (same theta in)."""
+    seq = synth.sequence(40, synth.chain_seed(synth.workload(1).seed, 0))
+    och = O.OracleChain(seq, table, synth.GEOMETRY)
+    bb = np.isin(och.kind, (0, 2, 3))  # backbone N, CA, C
+    xyz = {}
+    for prec in (synth.PRECISION_MIXED, synth.PRECISION_FP64):
+        p = synth.RunParams(precision=prec, solvation=0)
+        with kcm.Chain(seq, table, p) as ch:
+            ch.set_theta(synth.theta_extended(40))
+            it, _ = ch.step(100)
+            assert it == 100
+            xyz[prec] = ch.positions()
+    d = xyz[synth.PRECISION_MIXED][bb] - xyz[synth.PRECISION_FP64][bb]
+    assert np.sqrt((d ** 2).sum(1).mean()) <= 1e-3
+
+
 def test_step_rules(kcm, table):
     seq, och, th = small_case(table, 10, 5)
     p = synth.RunParams(precision=synth.PRECISION_FP64)
