@@ -158,6 +158,35 @@ int kcm_params_default(kcm_params* p);
  * KCM_E_NODEVICE, KCM_E_NOMEM, KCM_E_CUDA. On error *out is NULL. */
 int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream, kcm_handle* out);
 
+/* A batch of n_chains independent chains tops[0..n_chains-1] in one handle, stepped together by the
+ * same kernels (one launch per stage for all chains; every scan is segmented at chain boundaries and
+ * every chain gets its own cell grid). The chains are concatenated: atoms, joints and theta of chain
+ * c follow those of chain c-1 (kcm_chain_offsets), so every per-atom and per-joint call of this
+ * header covers the whole batch. Each chain converges on its own (its max |dtheta| below conv_tol)
+ * and then takes no more steps; kcm_step returns when every chain has converged or after n_iters.
+ * kcm_energy returns the sums over the chains (kcm_chain_energies gives them per chain). The paper
+ * steps one chain; batching many independent chains is a throughput layer over the same
+ * iteration (Sec. 4.1). Errors as kcm_create, also KCM_E_INVAL for n_chains < 1. */
+int kcm_create_batch(const kcm_topology* tops, int32_t n_chains, const kcm_params* prm, void* cuda_stream,
+                     kcm_handle* out);
+
+/* Number of chains of the handle (1 for kcm_create), -1 for NULL. */
+int32_t kcm_nchains(kcm_handle h);
+
+/* Offsets of every chain: atoms of chain c are [atom_off[c], atom_off[c+1]), its joints (theta,
+ * tau) [joint_off[c], joint_off[c+1]); both arrays hold kcm_nchains + 1 entries (either may be
+ * NULL). Host memory, caller-owned. */
+int kcm_chain_offsets(kcm_handle h, int64_t* atom_off, int64_t* joint_off);
+
+/* Energies of every chain at the current theta (evaluates): E[3c..3c+2] = Coulomb, Lennard-Jones,
+ * solvation of chain c (eq. 01). E has 3 * kcm_nchains doubles, host memory. */
+int kcm_chain_energies(kcm_handle h, double* E);
+
+/* Loop state of every chain since the last kcm_step or kcm_step_async: iterations taken, whether it
+ * has converged (1) or is still running (0), and the max |dtheta| of its last step. Arrays of
+ * kcm_nchains entries, host memory, any may be NULL; waits for the handle's stream. */
+int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta);
+
 /* Free everything the handle owns. NULL is accepted. */
 void kcm_destroy(kcm_handle h);
 

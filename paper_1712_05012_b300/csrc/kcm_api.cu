@@ -195,9 +195,10 @@ int kcm_params_default(kcm_params* p) {
     return KCM_OK;
 }
 
-int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream, kcm_handle* out) {
+static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_params* prm, void* cuda_stream, kcm_handle* out) {
     if (!out) return set_err(nullptr, KCM_E_INVAL, "out is NULL");
     *out = nullptr;
+    if (!tops || n_chains < 1) return set_err(nullptr, KCM_E_INVAL, "need at least one topology");
     std::string err;
     int rc = kcm::validate_params(prm, &err);
     if (rc != KCM_OK) return set_err(nullptr, rc, err);
@@ -209,8 +210,17 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         g_last_error = msg;
         return code;
     };
-    rc = kcm::build_host_chain(top, &h->hc, &err);
-    if (rc != KCM_OK) { set_err(h, rc, err); return bail(rc); }
+    {
+        std::vector<kcm::HostChain> parts(n_chains);
+        for (int32_t c = 0; c < n_chains; ++c) {
+            rc = kcm::build_host_chain(&tops[c], &parts[c], &err);
+            if (rc != KCM_OK) {
+                set_err(h, rc, n_chains > 1 ? "chain " + std::to_string(c) + ": " + err : err);
+                return bail(rc);
+            }
+        }
+        kcm::concat_chains(parts, &h->hc);
+    }
 
     int dev = 0, major = 0, minor = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -247,7 +257,18 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     const int fkq = kcm::fk_block_joints();
     d.ntiles = (d.l + fkq * d.fk_j - 1) / (fkq * d.fk_j);
     d.ltiles = (d.L + 31) / 32;
-    d.cell_cap = std::max(8 * d.n, 65536);
+    d.nchains = hc.nchains;
+    std::vector<int> ccap(hc.nchains);
+    {
+        long long tot = 0;
+        for (int ch = 0; ch < hc.nchains; ++ch) {  // each chain's grid is coarsened to fit its own cap
+            const int nc = hc.atom_off[ch + 1] - hc.atom_off[ch];
+            ccap[ch] = hc.nchains == 1 ? std::max(8 * nc, 65536) : std::max(8 * nc, 4096);
+            tot += ccap[ch];
+        }
+        if (tot > (1LL << 30)) return bail(set_err(h, KCM_E_INVAL, "the batch needs more than 2^30 cells"));
+        d.cell_cap = static_cast<int>(tot);
+    }
     d.pair_blocks = (d.n + kcm::kPairWarps - 1) / kcm::kPairWarps;
     d.scan_blocks = (d.cell_cap + kcm::kScanCells - 1) / kcm::kScanCells;
     d.scan_fused = d.cell_cap <= kcm::kScanFusedMaxCells;
@@ -293,7 +314,14 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = dalloc(h, &d.lane_suf, 6 * (size_t)L)) || (rc = dalloc(h, &d.tileS, 6 * (size_t)d.ltiles)) ||
         (rc = dalloc(h, &d.tileSuf, 6 * (size_t)d.ltiles)) ||
         (rc = dalloc(h, &d.Ftot, 3 * nn)) || (rc = dalloc(h, &d.Fcav64, 3 * nn)) ||
-        (rc = dalloc(h, &d.grid, 1)) || (rc = dalloc(h, &d.status, 1)))
+        (rc = dalloc(h, &d.grid, hc.nchains)) || (rc = dalloc(h, &d.status, 1)) ||
+        (rc = dalloc(h, &d.atom_chain, nn)) || (rc = dalloc(h, &d.joint_chain, l)) || (rc = dalloc(h, &d.link_chain, L)) ||
+        (rc = dalloc(h, &d.joint_off, hc.nchains + 1)) || (rc = dalloc(h, &d.ccap, hc.nchains)) ||
+        (rc = dalloc(h, &d.cbox, 6 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.chain_done, hc.nchains)) ||
+        (rc = dalloc(h, &d.chain_iters, hc.nchains)) || (rc = dalloc(h, &d.chain_maxdt, hc.nchains)) ||
+        (rc = dalloc(h, &d.chain_maxtau, hc.nchains)) || (rc = dalloc(h, &d.chain_lastdt, hc.nchains)) ||
+        (rc = dalloc(h, &d.chain_E, 3 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.gseg, l)) ||
+        (rc = dalloc(h, &d.tileF, d.ntiles)) || (rc = dalloc(h, &d.ltail, L)) || (rc = dalloc(h, &d.tileT, d.ltiles)))
         return bail(rc);
 
     // per-atom constants
@@ -316,7 +344,13 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     kcm::sample_points(N, Q64.data());
     std::vector<float> Q32(Q64.begin(), Q64.end());
     std::vector<double> ident = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
-    if (prm->precision == KCM_MIXED) ident = pack_df(ident);  // M[0] in the mixed kernels' format
+    if (prm->precision == KCM_MIXED) ident = pack_df(ident);  // base-link poses in the mixed kernels' format
+    std::vector<int> atom_chain(n), joint_chain(l), link_chain(L);
+    for (int ch = 0; ch < hc.nchains; ++ch) {
+        for (int a = hc.atom_off[ch]; a < hc.atom_off[ch + 1]; ++a) atom_chain[a] = ch;
+        for (int j = hc.joint_off[ch]; j < hc.joint_off[ch + 1]; ++j) joint_chain[j] = ch;
+        for (int k = hc.link_off[ch]; k < hc.link_off[ch + 1]; ++k) link_chain[k] = ch;
+    }
     std::vector<double> u0df = pack_df(hc.u0), step0df = pack_df(hc.step0), r0df = pack_df(hc.zp_rel);
     if ((rc = upload(h, d.r0, hc.zp_rel.data(), 3 * nn)) || (rc = upload(h, d.link, hc.link.data(), nn)) ||
         (rc = upload(h, d.link_start, hc.link_start.data(), L + 1)) || (rc = upload(h, d.u0, hc.u0.data(), 3 * l)) ||
@@ -326,7 +360,9 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
         (rc = upload(h, d.exm, reinterpret_cast<const unsigned long long*>(hc.ex_mask.data()), nn)) ||
         (rc = upload(h, d.m14m, reinterpret_cast<const unsigned long long*>(hc.m14_mask.data()), nn)) ||
         (rc = upload(h, d.Q64, Q64.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q32, Q32.data(), 3 * (size_t)N)) ||
-        (rc = upload(h, d.M, ident.data(), 12)) || (rc = upload(h, d.u0df, u0df.data(), 3 * l)) ||
+        (rc = upload(h, d.atom_chain, atom_chain.data(), nn)) || (rc = upload(h, d.joint_chain, joint_chain.data(), l)) ||
+        (rc = upload(h, d.link_chain, link_chain.data(), L)) || (rc = upload(h, d.joint_off, hc.joint_off.data(), hc.nchains + 1)) ||
+        (rc = upload(h, d.ccap, ccap.data(), hc.nchains)) || (rc = upload(h, d.u0df, u0df.data(), 3 * l)) ||
         (rc = upload(h, d.step0df, step0df.data(), 3 * l)) || (rc = upload(h, d.r0df, r0df.data(), 3 * nn)))
         return bail(rc);
     e = cudaMemsetAsync(d.theta, 0, sizeof(double) * l, h->stream);
@@ -334,11 +370,57 @@ int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream
     if (e == cudaSuccess) e = cudaMemsetAsync(d.Fcav, 0, sizeof(long long) * 3 * nn, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.covered, 0, sizeof(int) * nn, h->stream);
     if (e != cudaSuccess) { cuda_fail(h, e, "memset"); return bail(KCM_E_CUDA); }
+    for (int ch = 0; ch < hc.nchains && rc == KCM_OK; ++ch)  // the base link of every chain stays at the origin
+        rc = upload(h, d.M + 12 * (size_t)hc.link_off[ch], ident.data(), 12);
+    if (rc) return bail(rc);
     kcm::launch_init_status(d, h->stream);
     rc = sync(h);
     if (rc != KCM_OK) return bail(rc);
     *out = h;
     return KCM_OK;
+}
+
+int kcm_create(const kcm_topology* top, const kcm_params* prm, void* cuda_stream, kcm_handle* out) {
+    return create_impl(top, 1, prm, cuda_stream, out);
+}
+
+int kcm_create_batch(const kcm_topology* tops, int32_t n_chains, const kcm_params* prm, void* cuda_stream,
+                     kcm_handle* out) {
+    return create_impl(tops, n_chains, prm, cuda_stream, out);
+}
+
+int32_t kcm_nchains(kcm_handle h) { return h ? h->d.nchains : -1; }
+
+int kcm_chain_offsets(kcm_handle h, int64_t* atom_off, int64_t* joint_off) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    for (int c = 0; c <= h->hc.nchains; ++c) {
+        if (atom_off) atom_off[c] = h->hc.atom_off[c];
+        if (joint_off) joint_off[c] = h->hc.joint_off[c];
+    }
+    return KCM_OK;
+}
+
+int kcm_chain_energies(kcm_handle h, double* E) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!E) return set_err(h, KCM_E_INVAL, "E is NULL");
+    int rc = evaluate(h);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(E, h->d.chain_E, sizeof(double) * 3 * h->d.nchains, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "energy copy");
+    return sync(h);
+}
+
+int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    const int C = h->d.nchains;
+    cudaError_t e = cudaSuccess;
+    if (iters) e = cudaMemcpyAsync(iters, h->d.chain_iters, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && converged)
+        e = cudaMemcpyAsync(converged, h->d.chain_done, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && max_dtheta)
+        e = cudaMemcpyAsync(max_dtheta, h->d.chain_lastdt, sizeof(double) * C, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "chain state copy");
+    return sync(h);
 }
 
 void kcm_destroy(kcm_handle h) {
@@ -453,9 +535,14 @@ int kcm_energy(kcm_handle h, double E[3]) {
     if (rc != KCM_OK) return rc;
     rc = status_code(h, st);
     if (rc != KCM_OK) return rc;
-    E[0] = st.E[0];
-    E[1] = st.E[1];
-    E[2] = st.E[2];
+    std::vector<double> ce(3 * (size_t)h->d.nchains);
+    cudaError_t e = cudaMemcpyAsync(ce.data(), h->d.chain_E, sizeof(double) * ce.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "energy copy");
+    rc = sync(h);
+    if (rc) return rc;
+    E[0] = E[1] = E[2] = 0.0;  // the sum over the chains of a batch
+    for (int c = 0; c < h->d.nchains; ++c)
+        for (int k = 0; k < 3; ++k) E[k] += ce[3 * c + k];
     return KCM_OK;
 }
 
@@ -503,7 +590,7 @@ int kcm_get_stats(kcm_handle h, kcm_stats* out) {
     if (!out) return set_err(h, KCM_E_INVAL, "stats is NULL");
     kcm::Status st;
     kcm::GridInfo g;
-    cudaError_t e = cudaMemcpyAsync(&g, h->d.grid, sizeof g, cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaMemcpyAsync(&g, h->d.grid, sizeof g, cudaMemcpyDeviceToHost, h->stream);  // chain 0
     if (e != cudaSuccess) return cuda_fail(h, e, "grid copy");
     int rc = read_status(h, &st);
     if (rc) return rc;
@@ -511,7 +598,7 @@ int kcm_get_stats(kcm_handle h, kcm_stats* out) {
     out->sasa_neighbors = static_cast<int64_t>(st.nbr_total);
     out->max_neighbors = st.max_nbr;
     out->guard_rechecks = static_cast<int64_t>(st.guard);
-    out->cells = g.ncells;
+    out->cells = st.ncells;
     out->cell_size = g.s;
     out->iterations = st.iters;
     out->sasa_tests = static_cast<int64_t>(st.sasa_tests);

@@ -109,27 +109,27 @@ __device__ __forceinline__ bool covers64(double qx, double qy, double qz, double
 }
 
 
-// Grid of the cell list from the bounding box in st->bbox (order-preserving keys): cube cells of
-// edge s >= every interaction range (plus a margin that absorbs FP32 cell assignment), s a multiple
-// of 2^-10 A so that it is exact in float; coarsened when the bounding box would need more cells
-// than the arrays hold. Also clears the box and the per-evaluation counters. Run by one thread
-// after every block has added its atoms to the box.
-__device__ __forceinline__ void finish_grid(const DevChain& d, Status* st) {
+// Grid of chain c's cell list from its bounding box d.cbox[6c..6c+5] (order-preserving keys):
+// cube cells of edge s >= every interaction range (plus a margin that absorbs FP32 cell
+// assignment), s a multiple of 2^-10 A so that it is exact in float; coarsened when the box would
+// need more cells than the chain's cap. Leaves cbase to the caller and clears the box. Returns
+// false for a non-finite box.
+__device__ __forceinline__ bool chain_grid(const DevChain& d, int c, GridInfo* out) {
     double lo[3], hi[3];
     for (int i = 0; i < 3; ++i) {
-        lo[i] = dkey_inv(atomicAdd(&st->bbox[i], 0ULL));
-        hi[i] = dkey_inv(atomicAdd(&st->bbox[3 + i], 0ULL));
+        lo[i] = dkey_inv(__ldcg(&d.cbox[6 * c + i]));
+        hi[i] = dkey_inv(__ldcg(&d.cbox[6 * c + 3 + i]));
+        d.cbox[6 * c + i] = ~0ULL;
+        d.cbox[6 * c + 3 + i] = 0ULL;
     }
     GridInfo g;
-    bool finite = isfinite(hi[0] - lo[0]) && isfinite(hi[1] - lo[1]) && isfinite(hi[2] - lo[2]);
-    if (!finite) {
-        atomicOr(&st->error, kErrNonfinite);
-        st->done = 1;
+    const bool finite = isfinite(hi[0] - lo[0]) && isfinite(hi[1] - lo[1]) && isfinite(hi[2] - lo[2]);
+    if (!finite)
         for (int i = 0; i < 3; ++i) { lo[i] = 0.0; hi[i] = 0.0; }
-    }
     const double ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
     double s = fmax(fma(1e-6, fmax(ext[0], fmax(ext[1], ext[2])), d.s_base), d.prm.cell_size);
     s = ceil(s * 1024.0) * (1.0 / 1024.0);
+    const long long cap = d.ccap[c];
     for (;;) {
         // n_i = floor(ext_i / s) + 1 estimated in float, then raised until n_i s > ext_i holds exactly
         // (n_i s is exact: s is a multiple of 2^-10), so the cells cover the box
@@ -141,7 +141,7 @@ __device__ __forceinline__ void finish_grid(const DevChain& d, Status* st) {
             while ((double)k * s <= ext[i]) ++k;
             nn[i] = k;
         }
-        if (nn[0] * nn[1] * nn[2] <= (long long)d.cell_cap) {
+        if (nn[0] * nn[1] * nn[2] <= cap) {
             g.nx = (int)nn[0]; g.ny = (int)nn[1]; g.nz = (int)nn[2];
             g.ncells = (int)(nn[0] * nn[1] * nn[2]);
             break;
@@ -153,17 +153,10 @@ __device__ __forceinline__ void finish_grid(const DevChain& d, Status* st) {
     g.sf = (float)s;
     g.gpf = (float)(1e-3 + 2e-4 * s);
     g.inv_sf = 1.0f / (float)s;
-    *d.grid = g;
-    for (int i = 0; i < 3; ++i) { st->bbox[i] = ~0ULL; st->bbox[3 + i] = 0ULL; }
-    st->ticket_bbox = 0u;
-    st->pairs = 0;
-    st->nbr_total = 0;
-    st->guard = 0;
-    st->sasa_tests = 0;
-    st->max_nbr = 0;
-    st->E[0] = 0.0;
-    st->E[1] = 0.0;
-    st->E[2] = 0.0;
+    g.cbase = 0;
+    g.pad = 0;
+    *out = g;
+    return finite;
 }
 
 }  // namespace dev

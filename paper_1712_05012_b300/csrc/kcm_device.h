@@ -15,7 +15,8 @@ struct alignas(32) dbl4 {
 };
 __host__ __device__ inline dbl4 make_dbl4(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
 
-// Uniform binning grid of Sec. 3.2, rebuilt on the device every iteration.
+// Uniform binning grid of Sec. 3.2 of one chain, rebuilt on the device every iteration. The cells
+// of all chains of a batch are numbered consecutively: chain c owns [cbase, cbase + ncells).
 struct GridInfo {
     double ox, oy, oz;  // grid origin (bounding-box minimum)
     double s;           // cell edge, a multiple of 2^-10 A so that it is exact in float
@@ -23,6 +24,8 @@ struct GridInfo {
     float gpf;          // guard band of the FP32 cutoff tests (A^2), grows with the cell edge
     int nx, ny, nz;
     int ncells;
+    int cbase;
+    int pad;
 };
 
 // Error bits in Status::error.
@@ -31,16 +34,13 @@ constexpr int kErrOverflow = 2;
 
 // Device-resident loop state; the host reads it back only when asked.
 struct Status {
-    unsigned long long bbox[6];     // order-preserving keys: min x, y, z then max x, y, z
-    unsigned long long max_dtheta;  // bit pattern of a non-negative double (atomicMax)
-    unsigned long long max_abs_tau;
     unsigned int ticket;  // last-block detection in the step kernel
     unsigned int ticket_bbox;  // last-block detection in the bounding-box kernel
-    int iters;            // iterations taken since the last reset
-    int done;             // converged or failed: the remaining iterations are no-ops
+    int iters;            // iterations of the batch loop since the last reset
+    int done;             // every chain converged, or failure: the remaining iterations are no-ops
     int error;            // kErr* bits
-    double last_max_dtheta;
-    double E[3];  // Coulomb, LJ, solvation energies of the last evaluation
+    int ncells;           // cells of all chains' grids
+    double last_max_dtheta;  // largest |dtheta| over the chains stepped in the last iteration
     unsigned long long pairs;
     unsigned long long nbr_total;
     unsigned long long guard;
@@ -135,12 +135,31 @@ struct DevChain {
     int* nbr = nullptr;            // [n*kMaxNbr]
     float4* nbr_off = nullptr;     // r_j - r_i and Roff_j^2 [n*kMaxNbr]
     int* covered = nullptr;        // [n]
+    // batches: chain of each atom, joint and link; joint offsets; per-chain cell caps, bounding
+    // boxes (order-preserving keys: min x, y, z then max x, y, z), loop state and energies
+    int nchains = 1;
+    int* atom_chain = nullptr;     // [n]
+    int* joint_chain = nullptr;    // [l]
+    int* link_chain = nullptr;     // [L]
+    int* joint_off = nullptr;      // [nchains + 1]
+    int* ccap = nullptr;           // [nchains]
+    unsigned long long* cbox = nullptr;       // [nchains * 6]
+    int* chain_done = nullptr;     // converged (the chain takes no more steps) [nchains]
+    int* chain_iters = nullptr;    // [nchains]
+    unsigned long long* chain_maxdt = nullptr;   // bits of max |dtheta| of the running iteration
+    unsigned long long* chain_maxtau = nullptr;  // bits of max |tau| of the running iteration
+    double* chain_lastdt = nullptr;              // max |dtheta| of the chain's last step
+    double* chain_E = nullptr;     // Coulomb, LJ, solvation energies [nchains * 3]
+    unsigned char* gseg = nullptr; // FK: a chain starts in the joint's scan block at or before it [l]
+    int* tileF = nullptr;          // FK: a chain starts in the scan block [ntiles]
+    unsigned char* ltail = nullptr;   // torques: a chain ends in the link's tile at or after it [L]
+    int* tileT = nullptr;          // torques: a chain ends in the tile [ltiles]
     double* lane_suf = nullptr;    // suffix sums within tiles of 32 links [L*6]
     double* tileS = nullptr;       // tile sums [ltiles*6]
     double* tileSuf = nullptr;     // exclusive suffix sums of the tile sums [ltiles*6]
     double* Ftot = nullptr;        // [n*3] (on request)
     double* Fcav64 = nullptr;      // [n*3] (on request)
-    GridInfo* grid = nullptr;
+    GridInfo* grid = nullptr;      // [nchains]
     Status* status = nullptr;
 };
 

@@ -17,9 +17,10 @@
 // scans the four warp products, and each quad stores its exclusive prefix within the block; the
 // block product goes to tileP. k_fk_apply: block b first reduces the block products 0 .. b-1 to its
 // block prefix (a tree over at most 64 products per round, every block at once), then composes block
-// prefix, quad prefix and running products into the link poses M_{j+1}, the current axes u_j and axis
-// points p_j, moves the atoms of its links and adds them to the bounding box; its last block to
-// finish (ticket, no waiting) sets the grid of the cell list.
+// prefix, quad prefix and running products into the link poses, the current axes u_j and axis
+// points p_j, moves the atoms of its links and adds them to their chain's bounding box; its last
+// block to finish (ticket, no waiting) sets the grids of the cell lists. A batch of chains is their
+// concatenation: every product is segmented at the first joint of a chain.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -127,178 +128,242 @@ __device__ __forceinline__ void load_rows(const T* M, T* B) {
     }
 }
 
-// inclusive Kogge-Stone scan over the first NQ quads of a warp (composition on the left)
+// Segmented products: a quad carries (f, A) with f set when a chain starts within the range A covers;
+// (f1, A1) followed by (f2, A2) combine to (f1 | f2, f2 ? A2 : A1 o A2), so products never reach
+// across the first joint of a chain.
+
+// inclusive segmented Kogge-Stone scan over the first NQ quads of a warp (composition on the left)
 template <int NQ = 8, class T>
-__device__ __forceinline__ void warp_scan_quads(T* a, int q, int base) {
+__device__ __forceinline__ void warp_scan_quads(T* a, bool& f, int q, int base) {
 #pragma unroll
     for (int off = 1; off < NQ; off <<= 1) {
         T y[4], B[12];
 #pragma unroll
         for (int m = 0; m < 4; ++m) y[m] = shfl_up(a[m], 4 * off);
+        const bool yf = __shfl_up_sync(0xffffffffu, f, 4 * off);
         quad_rows(a, base, B);
-        if (q >= off) row_compose(y, B, a);
+        if (q >= off) {
+            if (!f) row_compose(y, B, a);
+            f = f || yf;
+        }
     }
 }
 
-// Scans the transforms held by the block's quads (row a of slot 8 w + q) in place into inclusive
-// block prefixes; the block total is returned in tot (row rr) on every lane. sW: [kFkWarps][12] shared.
+// Scans the transforms held by the block's quads (row a of slot 8 w + q, flag f) in place into
+// inclusive segmented block prefixes; the block total is returned in (tf, tot) on every lane.
+// sW: [kFkWarps][12], sF: [kFkWarps] shared.
 template <class T>
-__device__ __forceinline__ void block_scan_quads(T* a, T* tot, T (*sW)[12], int w, int q, int rr, int base,
-                                                 int lane) {
-    warp_scan_quads(a, q, base);
+__device__ __forceinline__ void block_scan_quads(T* a, bool& f, T* tot, bool& tf, T (*sW)[12], int* sF, int w, int q,
+                                                 int rr, int base, int lane) {
+    warp_scan_quads(a, f, q, base);
     if (q == 7 && (lane & 3) < 3) store_row(sW[w], rr, a);
+    if (lane == 28) sF[w] = f;
     __syncthreads();
     if (w == 0) {  // scan of the warp totals, quad q <- warp q
         T t[4];
-        if (q < kFkWarps) load_row(sW[q], rr, t);
+        bool tfl = false;
+        if (q < kFkWarps) { load_row(sW[q], rr, t); tfl = sF[q] != 0; }
         else row_identity(rr, t);
-        warp_scan_quads<kFkWarps>(t, q, base);
+        warp_scan_quads<kFkWarps>(t, tfl, q, base);
         __syncwarp();
         if (q < kFkWarps && (lane & 3) < 3) store_row(sW[q], rr, t);  // inclusive prefix of warps 0..q
+        if (q < kFkWarps && (lane & 3) == 0) sF[q] = tfl;
     }
     __syncthreads();
-    if (w > 0) {  // prefix of the earlier warps o own warp prefix
+    if (w > 0) {  // prefix of the earlier warps o own warp prefix, unless a chain starts in between
         T P[4], B[12];
         load_row(sW[w - 1], rr, P);
-        quad_rows(a, base, B);
-        row_compose(P, B, a);
+        quad_rows(a, base, B);  // shuffles outside the per-quad condition
+        if (!f) row_compose(P, B, a);
+        f = f || sF[w - 1] != 0;
     }
     load_row(sW[kFkWarps - 1], rr, tot);
+    tf = sF[kFkWarps - 1] != 0;
     __syncthreads();
 }
 
 template <int J, class T>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
     __shared__ T sW[kFkWarps][12];
+    __shared__ int sF[kFkWarps];
     if (d.status->done) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
     const int slot = w * 8 + q;
     const int j0 = (blockIdx.x * kFkQuads + slot) * J;
     T* G = reinterpret_cast<T*>(d.G);
-    // running product of the quad's J joints (the first J - 1 kept in G until the block prefix is known)
+    // running product of the quad's J joints, restarted at the first joint of a chain (the first
+    // J - 1 kept in G until the block prefix is known); lf: a chain starts in the quad at or before
     T a[4];
     row_identity(rr, a);
+    bool lf = false;
+    unsigned lfbits = 0;
 #pragma unroll
     for (int i = 0; i < J; ++i) {
         const int j = j0 + i;
         T g[4];  // joints past the end act as the identity (every lane takes part in the shuffles)
-        if (j < d.l) joint_row(d, j, rr, g);
-        else row_identity(rr, g);
+        bool head = false;
+        if (j < d.l) {
+            joint_row(d, j, rr, g);
+            head = j == d.joint_off[d.joint_chain[j]];
+        } else {
+            row_identity(rr, g);
+        }
         if (i == 0) {
 #pragma unroll
             for (int m = 0; m < 4; ++m) a[m] = g[m];
         } else {
             T B[12];
-            quad_rows(g, base, B);
-            row_compose(a, B, a);
+            quad_rows(g, base, B);  // shuffles outside the per-quad condition
+            if (head) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) a[m] = g[m];
+            } else {
+                row_compose(a, B, a);
+            }
         }
+        lf = lf || head;
+        lfbits |= lf ? (1u << i) : 0u;
         if (i < J - 1 && j < d.l && (lane & 3) < 3) store_row(&G[12 * (size_t)j], rr, a);
     }
-    // block-inclusive prefix of the quad; G_j <- (block prefix before the quad) o running product
-    // through joint j, i.e. the pose of link j + 1 relative to the block's first frame
+    // block-inclusive segmented prefix of the quad; G_j <- (block prefix before the quad) o running
+    // product through joint j, the pose of link j + 1 relative to the block's first frame (or to its
+    // chain's first frame when the chain starts inside the block: gseg_j)
     T incl[4], tot[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) incl[m] = a[m];
-    block_scan_quads(incl, tot, sW, w, q, rr, base, lane);
-    if (J > 1) {
-        T ex[4];
+    bool f = lf, tf = false;
+    block_scan_quads(incl, f, tot, tf, sW, sF, w, q, rr, base, lane);
+    T ex[4];
+    bool exf;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) ex[m] = shfl_up(incl[m], 4);
-        if (q == 0) {  // first quad of the warp: the inclusive prefix of the previous warp
-            if (w == 0) row_identity(rr, ex);
-            else load_row(sW[w - 1], rr, ex);  // still valid: written before the last barrier, not reused
-        }
+    for (int m = 0; m < 4; ++m) ex[m] = shfl_up(incl[m], 4);
+    exf = __shfl_up_sync(0xffffffffu, f, 4);
+    if (q == 0) {  // first quad of the warp: the inclusive prefix of the previous warp
+        if (w == 0) { row_identity(rr, ex); exf = false; }
+        else { load_row(sW[w - 1], rr, ex); exf = sF[w - 1] != 0; }  // written before the last barrier, not reused
+    }
+    if (J > 1) {
 #pragma unroll
         for (int i = 0; i < J - 1; ++i) {  // uniform within the quad
             const int j = j0 + i;
             if (j < d.l) {
-                T B[12], y[4];
-                load_rows(&G[12 * (size_t)j], B);
-                row_compose(ex, B, y);
-                __syncwarp(0xfu << base);
-                if ((lane & 3) < 3) store_row(&G[12 * (size_t)j], rr, y);
+                const bool own = (lfbits >> i) & 1u;  // a chain starts in the quad at or before joint j
+                if (!own) {
+                    T B[12], y[4];
+                    load_rows(&G[12 * (size_t)j], B);
+                    row_compose(ex, B, y);
+                    __syncwarp(0xfu << base);
+                    if ((lane & 3) < 3) store_row(&G[12 * (size_t)j], rr, y);
+                }
+                if ((lane & 3) == 0) d.gseg[j] = (unsigned char)(own || exf);
             }
         }
     }
     const int jl = j0 + J - 1;
-    if (jl < d.l && (lane & 3) < 3) store_row(&G[12 * (size_t)jl], rr, incl);
-    if (threadIdx.x < 32 && (lane & 3) < 3 && q == 0)
-        store_row(&reinterpret_cast<T*>(d.tileP)[12 * (size_t)blockIdx.x], rr, tot);
+    if (jl < d.l) {
+        if ((lane & 3) < 3) store_row(&G[12 * (size_t)jl], rr, incl);
+        if ((lane & 3) == 0) d.gseg[jl] = (unsigned char)f;
+    }
+    if (threadIdx.x < 32 && q == 0) {
+        if ((lane & 3) < 3) store_row(&reinterpret_cast<T*>(d.tileP)[12 * (size_t)blockIdx.x], rr, tot);
+        if (lane == 0) d.tileF[blockIdx.x] = tf;
+    }
 }
 
-// row rr of the product tileP[b0] o ... o tileP[b1 - 1] (identity when empty), all warps of the block
-// taking part: two products per quad, a tree within each warp, then a tree over the warp products
+// row rr (and flag) of the segmented product of the block products b0 .. b1 - 1 (identity, no flag,
+// when empty), all warps of the block taking part: two products per quad, a tree within each warp,
+// then a tree over the warp products
 template <class T>
-__device__ __forceinline__ void block_prefix(const DevChain& d, int b0, int b1, T (*sW)[12], int w, int q, int rr,
-                                             int base, int lane, T* out) {
+__device__ __forceinline__ void block_prefix(const DevChain& d, int b0, int b1, T (*sW)[12], int* sF, int w, int q,
+                                             int rr, int base, int lane, T* out, bool& of) {
     const T* P = reinterpret_cast<const T*>(d.tileP);
     const int slot = w * 8 + q;
     T a[4], B[12];
+    bool f = false;
     const int i0 = b0 + 2 * slot, i1 = i0 + 1;
-    if (i0 < b1) load_row(&P[12 * (size_t)i0], rr, a);
+    if (i0 < b1) { load_row(&P[12 * (size_t)i0], rr, a); f = d.tileF[i0] != 0; }
     else row_identity(rr, a);
     if (i1 < b1) {  // uniform within the quad
         load_rows(&P[12 * (size_t)i1], B);
-        row_compose(a, B, a);
+        const bool f1 = d.tileF[i1] != 0;
+        if (f1) { T t[4]; load_row(&P[12 * (size_t)i1], rr, t); for (int m = 0; m < 4; ++m) a[m] = t[m]; }
+        else row_compose(a, B, a);
+        f = f || f1;
     }
 #pragma unroll
-    for (int off = 1; off < 8; off <<= 1) {  // tree over the quads of the warp: quad q <- q o q + off
+    for (int off = 1; off < 8; off <<= 1) {  // tree over the quads of the warp: quad q <- q (+) q + off
         T y[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) y[m] = shfl_down(a[m], 4 * off);
+        const bool yf = __shfl_down_sync(0xffffffffu, f, 4 * off);
         quad_rows(y, base, B);
-        if ((q & (2 * off - 1)) == 0) row_compose(a, B, a);
+        if ((q & (2 * off - 1)) == 0) {
+            if (yf) { for (int m = 0; m < 4; ++m) a[m] = y[m]; }
+            else row_compose(a, B, a);
+            f = f || yf;
+        }
     }
     if (q == 0 && (lane & 3) < 3) store_row(sW[w], rr, a);
+    if (lane == 0) sF[w] = f;
     __syncthreads();
     if (w == 0) {  // tree over the warp products in warp 0, quad q <- warp q
-        if (q < kFkWarps) load_row(sW[q], rr, a);
-        else row_identity(rr, a);
+        if (q < kFkWarps) { load_row(sW[q], rr, a); f = sF[q] != 0; }
+        else { row_identity(rr, a); f = false; }
 #pragma unroll
         for (int off = 1; off < kFkWarps; off <<= 1) {
             T y[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) y[m] = shfl_down(a[m], 4 * off);
+            const bool yf = __shfl_down_sync(0xffffffffu, f, 4 * off);
             quad_rows(y, base, B);
-            if ((q & (2 * off - 1)) == 0) row_compose(a, B, a);
+            if ((q & (2 * off - 1)) == 0) {
+                if (yf) { for (int m = 0; m < 4; ++m) a[m] = y[m]; }
+                else row_compose(a, B, a);
+                f = f || yf;
+            }
         }
         __syncwarp();
         if (q == 0 && (lane & 3) < 3) store_row(sW[0], rr, a);
+        if (lane == 0) sF[0] = f;
     }
     __syncthreads();
     load_row(sW[0], rr, out);
+    of = sF[0] != 0;
     __syncthreads();
 }
 
-// link poses M_{j+1} = (product of the earlier blocks) o G_j; current axis u_j = R(M_{j+1}) u0_j
-// (the rotation about u0_j leaves u0_j fixed, so R(M_j) u0_j = R(M_{j+1}) u0_j) through p_j = origin
-// of frame j+1; then the atoms of the block's links and the bounding box
+// link poses M_{h(j)} = (segmented product of the earlier blocks) o G_j, or G_j alone when the
+// joint's chain starts in this block (h(j) = j + chain + 1: each chain also owns its fixed base link);
+// current axis u_j = R(M_{h(j)}) u0_j (the rotation about u0_j leaves u0_j fixed) through p_j = origin
+// of that frame; then the atoms of the block's links, and the bounding box of every chain; the last
+// block to finish (ticket, no waiting) sets the chains' grids and their cell bases
 template <int J, class T>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     __shared__ T sW[kFkWarps][12];
-    __shared__ unsigned long long sB[6][kFkWarps];
+    __shared__ int sF[kFkWarps];
+    __shared__ int sScan[kFkWarps];
     __shared__ bool sLast;
-    if (d.status->done) return;
+    Status* st = d.status;
+    if (st->done) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
     const int slot = w * 8 + q;
     const int j0 = (blockIdx.x * kFkQuads + slot) * J;
     T* M = reinterpret_cast<T*>(d.M);
     const T* G = reinterpret_cast<const T*>(d.G);
-    // block prefix: product of the block products before this block, 2 * kFkQuads per round
+    // block prefix: segmented product of the block products before this block, 2 * kFkQuads per round
     T bE[4];
+    bool bf = false;
     row_identity(rr, bE);
     for (int b0 = 0; b0 < (int)blockIdx.x; b0 += 2 * kFkQuads) {
         T part[4], B[12];
-        block_prefix(d, b0, min(b0 + 2 * kFkQuads, (int)blockIdx.x), sW, w, q, rr, base, lane, part);
-        if (b0 == 0) {
-#pragma unroll
-            for (int m = 0; m < 4; ++m) bE[m] = part[m];
-        } else {
-            quad_rows(part, base, B);
-            row_compose(bE, B, bE);
-        }
+        bool pf;
+        block_prefix(d, b0, min(b0 + 2 * kFkQuads, (int)blockIdx.x), sW, sF, w, q, rr, base, lane, part, pf);
+        quad_rows(part, base, B);
+        if (b0 == 0 || pf) { for (int m = 0; m < 4; ++m) bE[m] = part[m]; }
+        else row_compose(bE, B, bE);
+        bf = bf || pf;
     }
 #pragma unroll
     for (int i = 0; i < J; ++i) {
@@ -306,12 +371,16 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
         if (j < d.l) {  // uniform within the quad; no shuffles here
             T Gj[12], Ma[4];
             load_rows(&G[12 * (size_t)j], Gj);
-            row_compose(bE, Gj, Ma);  // pose of link j + 1
+            if (d.gseg[j]) {
+                load_row(&G[12 * (size_t)j], rr, Ma);
+            } else {
+                row_compose(bE, Gj, Ma);
+            }
             if ((lane & 3) < 3) {
                 const double* u = &d.u0[3 * j];
                 const T uc = fma(Ma[2], num<T>(u[2]), fma(Ma[1], num<T>(u[1]), mul(Ma[0], num<T>(u[0]))));
                 d.ucur[3 * j + rr] = to_double(uc);
-                store_row(&M[12 * ((size_t)j + 1)], rr, Ma);
+                store_row(&M[12 * ((size_t)j + d.joint_chain[j] + 1)], rr, Ma);
                 d.pcur[3 * j + rr] = to_double(Ma[3]);
                 if constexpr (!std::is_same<T, double>::value) {  // for the double-float torque kernel
                     reinterpret_cast<T*>(d.ucurdf)[3 * j + rr] = uc;
@@ -321,14 +390,23 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
         }
     }
     __syncthreads();  // the block's link poses are visible to the whole block
-    // atoms of the block's links 32 J b + 1 .. 32 J (b + 1) (block 0 also takes link 0, whose pose is the
-    // identity)
-    const int hfirst = blockIdx.x == 0 ? 0 : blockIdx.x * kFkQuads * J + 1;
-    const int hlast = min((blockIdx.x + 1) * kFkQuads * J + 1, d.L);
+    // atoms of the block's links: those after the link of the previous block's last joint up to the
+    // link of this block's last joint (chains' base links included; their pose is the identity)
+    const int jb0 = blockIdx.x * kFkQuads * J, jb1 = min((int)(blockIdx.x + 1) * kFkQuads * J, d.l);
+    const int hfirst = blockIdx.x == 0 ? 0 : jb0 + d.joint_chain[jb0 - 1] + 1;
+    const int hlast = blockIdx.x == gridDim.x - 1 ? d.L : jb1 + d.joint_chain[jb1 - 1] + 1;
     const int a1 = d.link_start[hlast];
     const T* r0 = reinterpret_cast<const T*>(std::is_same<T, double>::value ? (const void*)d.r0 : (const void*)d.r0df);
     unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0ULL, 0ULL, 0ULL};
+    int cc = -1;  // chain of the keys held in mn, mx
     for (int a = d.link_start[hfirst] + threadIdx.x; a < a1; a += blockDim.x) {
+        const int ca = d.atom_chain[a];
+        if (ca != cc) {  // a thread's atoms move on to the next chain: hand in the box so far
+            if (cc >= 0)
+                for (int i = 0; i < 3; ++i) { atomicMin(&d.cbox[6 * cc + i], mn[i]); atomicMax(&d.cbox[6 * cc + 3 + i], mx[i]); }
+            cc = ca;
+            for (int i = 0; i < 3; ++i) { mn[i] = ~0ULL; mx[i] = 0ULL; }
+        }
         const T* Ml = &M[12 * (size_t)d.link[a]];
         const T x = r0[3 * a], y = r0[3 * a + 1], z = r0[3 * a + 2];
 #pragma unroll
@@ -342,32 +420,69 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
             mx[i] = max(mx[i], key);
         }
     }
-    // bounding box of all centres; the last block to finish sets the grid of the cell list
+    // warps whose threads all hold the same chain reduce first; the others hand in lane by lane
+    const int cw = __reduce_max_sync(0xffffffffu, cc);
+    if (__all_sync(0xffffffffu, cc == cw || cc < 0)) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < 3; ++i) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[i] = min(mn[i], __shfl_down_sync(0xffffffffu, mn[i], o));
-            mx[i] = max(mx[i], __shfl_down_sync(0xffffffffu, mx[i], o));
+            for (int o = 16; o > 0; o >>= 1) {
+                mn[i] = min(mn[i], __shfl_down_sync(0xffffffffu, mn[i], o));
+                mx[i] = max(mx[i], __shfl_down_sync(0xffffffffu, mx[i], o));
+            }
         }
-        if (lane == 0) { sB[i][w] = mn[i]; sB[3 + i][w] = mx[i]; }
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        const int i = threadIdx.x;
-        unsigned long long v = sB[i][0];
-#pragma unroll
-        for (int k = 1; k < kFkWarps; ++k) v = i < 3 ? min(v, sB[i][k]) : max(v, sB[i][k]);
-        if (i < 3) atomicMin(&d.status->bbox[i], v);
-        else atomicMax(&d.status->bbox[i], v);
+        if (lane == 0 && cw >= 0)
+            for (int i = 0; i < 3; ++i) { atomicMin(&d.cbox[6 * cw + i], mn[i]); atomicMax(&d.cbox[6 * cw + 3 + i], mx[i]); }
+    } else if (cc >= 0) {
+        for (int i = 0; i < 3; ++i) { atomicMin(&d.cbox[6 * cc + i], mn[i]); atomicMax(&d.cbox[6 * cc + 3 + i], mx[i]); }
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) sLast = atomicAdd(&d.status->ticket_bbox, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) sLast = atomicAdd(&st->ticket_bbox, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (sLast && threadIdx.x == 0) {
-        __threadfence();
-        finish_grid(d, d.status);
+    if (!sLast) return;
+    __threadfence();
+    // grids of all chains, one thread per chain; cell bases by a block scan over the chains
+    int cbase = 0;
+    bool bad = false;
+    for (int c0 = 0; c0 < d.nchains; c0 += blockDim.x) {
+        const int cch = c0 + threadIdx.x;
+        GridInfo g;
+        int ncl = 0;
+        if (cch < d.nchains) {
+            bad = bad || !chain_grid(d, cch, &g);
+            ncl = g.ncells;
+            d.chain_E[3 * cch] = 0.0; d.chain_E[3 * cch + 1] = 0.0; d.chain_E[3 * cch + 2] = 0.0;
+        }
+        int v = ncl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y2 = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y2;
+        }
+        if (lane == 31) sScan[w] = v;
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int k = 0; k < kFkWarps; ++k) { if (k < w) before += sScan[k]; total += sScan[k]; }
+        if (cch < d.nchains) {
+            g.cbase = cbase + before + v - ncl;
+            d.grid[cch] = g;
+        }
+        cbase += total;
+        __syncthreads();
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+        atomicOr(&st->error, kErrNonfinite);
+        st->done = 1;
+    }
+    if (threadIdx.x == 0) {
+        st->ncells = cbase;
+        st->ticket_bbox = 0u;
+        st->pairs = 0;
+        st->nbr_total = 0;
+        st->guard = 0;
+        st->sasa_tests = 0;
+        st->max_nbr = 0;
     }
 }
 

@@ -310,4 +310,41 @@ int build_host_chain(const kcm_topology* top, HostChain* hc, std::string* err) {
     return KCM_OK;
 }
 
+void concat_chains(const std::vector<HostChain>& parts, HostChain* out) {
+    HostChain& b = *out;
+    b = HostChain();
+    b.nchains = static_cast<int>(parts.size());
+    b.atom_off.assign(1, 0);
+    b.joint_off.assign(1, 0);
+    b.link_off.assign(1, 0);
+    for (const HostChain& p : parts) {
+        const int a0 = b.n, h0 = b.L;
+        b.m += p.m;
+        b.n += p.n;
+        b.l += p.l;
+        b.L += p.L;
+        b.atom_off.push_back(b.n);
+        b.joint_off.push_back(b.l);
+        b.link_off.push_back(b.L);
+        b.zp.insert(b.zp.end(), p.zp.begin(), p.zp.end());
+        for (int a = 0; a < p.n; ++a) {
+            b.link.push_back(p.link[a] + h0);
+            b.parent.push_back(p.parent[a] < 0 ? -1 : p.parent[a] + a0);
+        }
+        for (int h = 0; h < p.L; ++h) b.link_start.push_back(p.link_start[h] + a0);
+        b.kind.insert(b.kind.end(), p.kind.begin(), p.kind.end());
+        b.q.insert(b.q.end(), p.q.begin(), p.q.end());
+        b.eps.insert(b.eps.end(), p.eps.begin(), p.eps.end());
+        b.R.insert(b.R.end(), p.R.begin(), p.R.end());
+        b.cls.insert(b.cls.end(), p.cls.begin(), p.cls.end());
+        b.u0.insert(b.u0.end(), p.u0.begin(), p.u0.end());
+        b.step0.insert(b.step0.end(), p.step0.begin(), p.step0.end());
+        b.zp_rel.insert(b.zp_rel.end(), p.zp_rel.begin(), p.zp_rel.end());
+        // masks hold bits for partners at index offsets within the same chain, unchanged by the shift
+        b.ex_mask.insert(b.ex_mask.end(), p.ex_mask.begin(), p.ex_mask.end());
+        b.m14_mask.insert(b.m14_mask.end(), p.m14_mask.begin(), p.m14_mask.end());
+    }
+    b.link_start.push_back(b.n);
+}
+
 }  // namespace kcm

@@ -38,10 +38,16 @@ struct HostChain {
     std::vector<double> step0;       // frame step: axis point of joint j minus that of joint j-1 [l*3]
     std::vector<double> zp_rel;      // ZP offset of each atom from its link frame origin [n*3]
     std::vector<uint64_t> ex_mask, m14_mask;  // bond-class masks [n]
+    // a batch of chains is their concatenation (atoms, links and joints in chain order); chain c
+    // owns atoms [atom_off[c], atom_off[c+1]), joints [joint_off[c], ...) and links [link_off[c], ...)
+    int nchains = 1;
+    std::vector<int> atom_off, joint_off, link_off;  // [nchains + 1]
 };
 
 double gamma_of_class(int cls);
 int build_host_chain(const kcm_topology* top, HostChain* hc, std::string* err);
+// the batch of the given chains (each built by build_host_chain) in order
+void concat_chains(const std::vector<HostChain>& parts, HostChain* out);
 int bond_class_tree(const HostChain& hc, int a, int b);  // 0 far, 1 excluded, 2 1-4
 int sample_points(int N, double* Q);
 int validate_params(const kcm_params* p, std::string* err);

@@ -41,11 +41,11 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (a < d.n) {
-        const GridInfo g = *d.grid;
+        const GridInfo g = d.grid[d.atom_chain[a]];
         int cx = min(max((int)floorf((float)(d.r[3 * a] - g.ox) * g.inv_sf), 0), g.nx - 1);
         int cy = min(max((int)floorf((float)(d.r[3 * a + 1] - g.oy) * g.inv_sf), 0), g.ny - 1);
         int cz = min(max((int)floorf((float)(d.r[3 * a + 2] - g.oz) * g.inv_sf), 0), g.nz - 1);
-        int key = (cz * g.ny + cy) * g.nx + cx;
+        int key = g.cbase + (cz * g.ny + cy) * g.nx + cx;
         d.key[a] = key;
         unsigned peers = __match_any_sync(__activemask(), key);
         int leader = __ffs(peers) - 1;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const int nc = d.grid->ncells;
+    const int nc = d.status->ncells;
     constexpr int kPass = 4 * kBinThreads;  // cells per pass
     constexpr int kPre = 8;                 // passes whose loads are in flight together
     int carry = 0;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
 __global__ void k_scan_sums(const DevChain d) {
     __shared__ int ws[32];
     if (d.status->done) return;
-    int nc = d.grid->ncells;
+    int nc = d.status->ncells;
     int c0 = blockIdx.x * kScanCells;
     if (c0 >= nc) return;
     int s = 0;
@@ -147,7 +147,7 @@ __global__ void k_scan_cells(const DevChain d) {
     __shared__ int ws[32];
     __shared__ int base_s;
     if (d.status->done) return;
-    int nc = d.grid->ncells;
+    int nc = d.status->ncells;
     int c0 = blockIdx.x * kScanCells;
     if (c0 >= nc) return;
     // sum of the previous blocks' counts
@@ -211,14 +211,15 @@ template <bool MIXED>
 __global__ void k_bin_place(const DevChain d) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= d.n || d.status->done) return;
-    const GridInfo g = *d.grid;
+    const GridInfo g = d.grid[d.atom_chain[a]];
     int key = d.key[a];
     int sl = d.cell_start[key] + d.rank[a];
     d.sorted[sl] = a;
     d.slot_cell[sl] = key;
     double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
     if (MIXED) {
-        int cx = key % g.nx, cy = (key / g.nx) % g.ny, cz = key / (g.nx * g.ny);
+        const int lk = key - g.cbase;
+        int cx = lk % g.nx, cy = (lk / g.nx) % g.ny, cz = lk / (g.nx * g.ny);
         float ox = (float)(x - (g.ox + cx * g.s));
         float oy = (float)(y - (g.oy + cy * g.s));
         float oz = (float)(z - (g.oz + cz * g.s));
@@ -254,15 +255,18 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     __shared__ R sE[2][kPairWarps];
     __shared__ unsigned long long sC[3][kPairWarps];
     __shared__ int sM[kPairWarps];
+    __shared__ int sCh[kPairWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sl = blockIdx.x * kPairWarps + w;
     R Eel = 0, Evdw = 0;
     unsigned npairs = 0, nguard = 0;
     int ncount = 0;
+    int ca = -1;  // chain of the home atom
     if (sl < d.n && !d.status->done) {
-        const GridInfo g = *d.grid;
         const int a = d.sorted[sl];
-        const int cell = d.slot_cell[sl];
+        ca = d.atom_chain[a];
+        const GridInfo g = d.grid[ca];  // the home atom's chain: its candidates are that chain's atoms
+        const int cell = d.slot_cell[sl] - g.cbase;
         const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
         // the non-empty cells among the 27 neighbours, compacted in stencil order: first slot, offset
         // of their candidates in the concatenation, and (mixed) the shift (c_j - c_i) s
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         if (lane < 27) {
             int ncx = cx + dxc, ncy = cy + dyc, ncz = cz + dzc;
             if (ncx >= 0 && ncx < g.nx && ncy >= 0 && ncy < g.ny && ncz >= 0 && ncz < g.nz) {
-                int nc = (ncz * g.ny + ncy) * g.nx + ncx;
+                int nc = g.cbase + (ncz * g.ny + ncy) * g.nx + ncx;
                 beg = d.cell_start[nc];
                 len = d.cell_start[nc + 1] - beg;
             }
@@ -493,15 +497,27 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             if (ncount > kMaxNbr) atomicOr(&d.status->error, kErrOverflow);
         }
     }
-    if (lane == 0) { sE[0][w] = Eel; sE[1][w] = Evdw; sC[0][w] = npairs; sC[1][w] = nguard; sC[2][w] = (unsigned long long)ncount; sM[w] = ncount; }
+    if (lane == 0) { sE[0][w] = Eel; sE[1][w] = Evdw; sC[0][w] = npairs; sC[1][w] = nguard; sC[2][w] = (unsigned long long)ncount; sM[w] = ncount; sCh[w] = ca; }
     __syncthreads();
     if (threadIdx.x == 0) {
         R e0 = 0, e1 = 0;
         unsigned long long c0 = 0, c1 = 0, c2 = 0;
         int m = 0;
-        for (int k2 = 0; k2 < kPairWarps; ++k2) { e0 += sE[0][k2]; e1 += sE[1][k2]; c0 += sC[0][k2]; c1 += sC[1][k2]; c2 += sC[2][k2]; m = max(m, sM[k2]); }
-        if (e0 != (R)0) atomicAdd(&d.status->E[0], (double)e0);
-        if (e1 != (R)0) atomicAdd(&d.status->E[1], (double)e1);
+        bool one = true;  // all home atoms of the block in one chain: one atomic per energy
+        for (int k2 = 0; k2 < kPairWarps; ++k2) {
+            e0 += sE[0][k2]; e1 += sE[1][k2]; c0 += sC[0][k2]; c1 += sC[1][k2]; c2 += sC[2][k2]; m = max(m, sM[k2]);
+            one = one && (sCh[k2] == sCh[0] || sCh[k2] < 0);
+        }
+        if (one && sCh[0] >= 0) {
+            if (e0 != (R)0) atomicAdd(&d.chain_E[3 * sCh[0]], (double)e0);
+            if (e1 != (R)0) atomicAdd(&d.chain_E[3 * sCh[0] + 1], (double)e1);
+        } else if (!one) {
+            for (int k2 = 0; k2 < kPairWarps; ++k2) {
+                if (sCh[k2] < 0) continue;
+                if (sE[0][k2] != (R)0) atomicAdd(&d.chain_E[3 * sCh[k2]], (double)sE[0][k2]);
+                if (sE[1][k2] != (R)0) atomicAdd(&d.chain_E[3 * sCh[k2] + 1], (double)sE[1][k2]);
+            }
+        }
         if (c0) atomicAdd(&d.status->pairs, c0);
         if (c1) atomicAdd(&d.status->guard, c1);
         if (c2) atomicAdd(&d.status->nbr_total, c2);
@@ -548,7 +564,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
             const float drf = (float)dr;
             // guard band of the FP32 overlap test (A^2): a bound of about 5e-5 A^2 at a 10 A cell edge,
             // from the cell-relative offsets (error < 7 s 2^-24 per component) and the test's own rounding
-            const float gs = (float)(2e-4 + 4e-5 * d.grid->s);
+            const float gs = (float)(2e-4 + 4e-5 * d.grid[d.atom_chain[a]].s);
             int ncov = 0, nguard = 0;
             unsigned long long ntest = 0;
             for (int k = lane; k < d.N; k += 32) {
@@ -662,7 +678,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
             const float Ra = d.aprm32[a].w;
             const float inv2R = 0.5f / Ra;
             const float drf = d.f_dr;
-            const float gd = 1e-4f + 1.2e-5f * d.grid->sf;  // guard band in Q.o units (A)
+            const float gd = 1e-4f + 1.2e-5f * d.grid[d.atom_chain[a]].sf;  // guard band in Q.o units (A)
             float rmax2 = 0.0f;
             for (int j = lane; j < cnt; j += 32) {
                 const float4 o = d.nbr_off[(size_t)a * kMaxNbr + j];  // r_j - r_i, Roff_j^2
@@ -799,24 +815,32 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
     }
 }
 
+// loop state of a batch; with full, also the statistics and the chains' bounding boxes
 __global__ void k_reset_loop(const DevChain d, int full) {
     Status* st = d.status;
-    st->iters = 0;
-    st->done = 0;
-    st->error = 0;
-    st->ticket = 0u;
-    st->ticket_w = 0u;
-    st->ticket_bin = 0u;
-    st->max_dtheta = 0ULL;
-    st->max_abs_tau = 0ULL;
-    st->last_max_dtheta = 0.0;
-    st->E[0] = 0.0;
-    st->E[1] = 0.0;
-    st->E[2] = 0.0;
-    if (full) {
-        st->ticket_bbox = 0u;
-        for (int i = 0; i < 3; ++i) { st->bbox[i] = ~0ULL; st->bbox[3 + i] = 0ULL; }
-        st->pairs = 0; st->nbr_total = 0; st->guard = 0; st->sasa_tests = 0; st->max_nbr = 0;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) {
+        st->iters = 0;
+        st->done = 0;
+        st->error = 0;
+        st->ticket = 0u;
+        st->ticket_w = 0u;
+        st->ticket_bin = 0u;
+        st->last_max_dtheta = 0.0;
+        if (full) {
+            st->ticket_bbox = 0u;
+            st->pairs = 0; st->nbr_total = 0; st->guard = 0; st->sasa_tests = 0; st->max_nbr = 0;
+        }
+    }
+    if (c < d.nchains) {
+        d.chain_done[c] = 0;
+        d.chain_iters[c] = 0;
+        d.chain_maxdt[c] = 0ULL;
+        d.chain_maxtau[c] = 0ULL;
+        d.chain_lastdt[c] = 0.0;
+        d.chain_E[3 * c] = 0.0; d.chain_E[3 * c + 1] = 0.0; d.chain_E[3 * c + 2] = 0.0;
+        if (full)
+            for (int i = 0; i < 3; ++i) { d.cbox[6 * c + i] = ~0ULL; d.cbox[6 * c + 3 + i] = 0ULL; }
     }
 }
 
@@ -833,8 +857,8 @@ inline int blocks(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 
 }  // namespace
 
-void launch_init_status(DevChain& d, cudaStream_t s) { k_reset_loop<<<1, 1, 0, s>>>(d, 1); }
-void launch_reset_loop(DevChain& d, cudaStream_t s) { k_reset_loop<<<1, 1, 0, s>>>(d, 0); }
+void launch_init_status(DevChain& d, cudaStream_t s) { k_reset_loop<<<blocks(d.nchains, 256), 256, 0, s>>>(d, 1); }
+void launch_reset_loop(DevChain& d, cudaStream_t s) { k_reset_loop<<<blocks(d.nchains, 256), 256, 0, s>>>(d, 0); }
 
 
 void launch_binning(DevChain& d, cudaStream_t s) {

@@ -22,11 +22,34 @@ namespace kcm {
 namespace {
 using namespace dev;
 
+// Per-chain maxima of non-negative doubles (as bit patterns) and sums: one atomic per warp when the
+// warp's lanes agree on the chain (c < 0: no value), else one per lane.
+__device__ __forceinline__ void chain_max(unsigned long long* arr, int c, unsigned long long v) {
+    const int cw = __reduce_max_sync(0xffffffffu, c);
+    if (__all_sync(0xffffffffu, c == cw || c < 0)) {
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0 && cw >= 0 && v) atomicMax(&arr[cw], v);
+    } else if (c >= 0 && v) {
+        atomicMax(&arr[c], v);
+    }
+}
+template <class V>
+__device__ __forceinline__ void chain_add(double* arr, int stride, int c, V v) {
+    const int cw = __reduce_max_sync(0xffffffffu, c);
+    if (__all_sync(0xffffffffu, c == cw || c < 0)) {
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0 && cw >= 0 && v != (V)0) atomicAdd(&arr[stride * cw], (double)v);
+    } else if (c >= 0 && v != (V)0) {
+        atomicAdd(&arr[stride * c], (double)v);
+    }
+}
+
 // One block per tile of 32 links h in [32 t, 32 t + 32). The block's threads take the tile's atoms
 // (r x F and F, with the conversion of the mixed-mode fixed-point forces) into shared memory; one
 // thread per (component, link) adds the link's atoms in atom order; warp q then scans component q of
-// the tile's P_h from the end (Kogge-Stone), and the last block to finish (ticket, no waiting) forms
-// the exclusive suffix sums of the tile totals.
+// the tile's P_h from the end (Kogge-Stone, segmented at the last link of each chain: a chain's
+// sums never take in the next chain), and the last block to finish (ticket, no waiting) forms the
+// segmented exclusive suffix sums of the tile totals.
 template <class T>
 __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChain d) {
     constexpr bool DF = std::is_same<T, df>::value;
@@ -41,8 +64,19 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     const T* rr = reinterpret_cast<const T*>(DF ? d.rdf : d.r);
     double Ecav = 0.0;   // FP64 mode
     float Ecavf = 0.0f;  // mixed mode
+    int cc = -1;         // chain of the energy held
     for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
         T f[3];
+        const int ca = d.atom_chain[a];
+        if (ca != cc && d.prm.solvation) {  // the thread's atoms move on to the next chain
+            if (cc >= 0) {
+                if constexpr (DF) { if (Ecavf != 0.0f) atomicAdd(&d.chain_E[3 * cc + 2], (double)Ecavf); }
+                else { if (Ecav != 0.0) atomicAdd(&d.chain_E[3 * cc + 2], Ecav); }
+            }
+            Ecav = 0.0;
+            Ecavf = 0.0f;
+        }
+        cc = ca;
         if constexpr (DF) {  // pair forces in fixed point (2^-23) plus oversized terms, solvation (2^-40)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -69,36 +103,42 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
         v[2] = sub(mul(x, f[1]), mul(y, f[0]));
         v[3] = f[0]; v[4] = f[1]; v[5] = f[2];
     }
-    if (d.prm.solvation) {  // cavity energy of the block's atoms
-        if constexpr (DF) {
-            Ecavf = warp_sum(Ecavf);
-            if (lane == 0 && Ecavf != 0.0f) atomicAdd(&st->E[2], (double)Ecavf);
-        } else {
-            Ecav = warp_sum(Ecav);
-            if (lane == 0 && Ecav != 0.0) atomicAdd(&st->E[2], Ecav);
-        }
+    if (d.prm.solvation) {  // cavity energy of the block's atoms, per chain
+        if constexpr (DF) chain_add(d.chain_E + 2, 3, cc, Ecavf);
+        else chain_add(d.chain_E + 2, 3, cc, Ecav);
     }
     __syncthreads();
     for (int u = threadIdx.x; u < 6 * 32; u += blockDim.x) {  // P_h component u / 32 of link h0 + u % 32
         const int k = u >> 5, h = h0 + (u & 31);
         T s = num_f<T>(0.0f);
-        if (h >= 1 && h < h1)  // links 1..l (link 0 has no joint)
-            for (int a = d.link_start[h]; a < d.link_start[h + 1]; ++a) s = add(s, sV[a - a0][k]);
+        if (h < h1) {
+            const int ch = d.link_chain[h];
+            if (h != d.joint_off[ch] + ch)  // a chain's base link has no joint
+                for (int a = d.link_start[h]; a < d.link_start[h + 1]; ++a) s = add(s, sV[a - a0][k]);
+        }
         sP[u & 31][k] = s;
     }
     __syncthreads();
     T* lane_suf = reinterpret_cast<T*>(d.lane_suf);
     T* tileS = reinterpret_cast<T*>(d.tileS);
-    if (w < 6) {  // reverse inclusive scan of component w over the tile
+    if (w < 6) {  // segmented reverse inclusive scan of component w over the tile
         const int h = h0 + lane;
         T x = sP[lane][w];
+        bool tl = h >= d.L - 1 || (h < h1 && d.link_chain[h + 1] != d.link_chain[h]);  // last link of a chain
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const T y = shfl_down(x, off);
-            if (lane + off < 32) x = add(x, y);
+            const bool yt = __shfl_down_sync(0xffffffffu, tl, off);
+            if (lane + off < 32 && !tl) { x = add(x, y); tl = yt; }
         }
-        if (h < d.L) lane_suf[6 * (size_t)h + w] = x;
-        if (lane == 0) tileS[6 * (size_t)t + w] = x;
+        if (h < d.L) {
+            lane_suf[6 * (size_t)h + w] = x;
+            if (w == 0) d.ltail[h] = (unsigned char)tl;  // a chain ends in the tile at or after h
+        }
+        if (lane == 0) {
+            tileS[6 * (size_t)t + w] = x;
+            if (w == 0) d.tileT[t] = tl;
+        }
     }
     __threadfence();
     __syncthreads();
@@ -107,47 +147,90 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     if (!last) return;
     __threadfence();
     T* tileSuf = reinterpret_cast<T*>(d.tileSuf);
-    if (w < 6) {  // exclusive suffix sums of the tile totals, 32 tiles per round from the end
-        T carry = num_f<T>(0.0f);
+    if (w < 6) {  // segmented exclusive suffix sums of the tile totals, 32 tiles per round from the end
+        T carry = num_f<T>(0.0f);  // R of the first tile of the later round
         for (int top = d.ltiles; top > 0; top -= 32) {
             const int tt = top - 32 + lane;
             T x = num_f<T>(0.0f);
+            bool tl = true;
             if (tt >= 0) {
                 const double raw = __ldcg(&d.tileS[6 * (size_t)tt + w]);  // the slot of a T, read past L1
                 x = *reinterpret_cast<const T*>(&raw);
+                tl = __ldcg(&d.tileT[tt]) != 0;
             }
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const T y = shfl_down(x, off);
-                if (lane + off < 32) x = add(x, y);
+                const bool yt = __shfl_down_sync(0xffffffffu, tl, off);
+                if (lane + off < 32 && !tl) { x = add(x, y); tl = yt; }
             }
-            T e = shfl_down(x, 1);
-            if (lane == 31) e = num_f<T>(0.0f);
-            if (tt >= 0) tileSuf[6 * (size_t)tt + w] = add(e, carry);
-            carry = add(carry, shfl(x, 0));
+            const T R = tl ? x : add(x, carry);  // R_t = sum of tiles t .. the first chain end, across rounds
+            T e = shfl_down(R, 1);
+            if (lane == 31) e = carry;
+            if (tt >= 0) tileSuf[6 * (size_t)tt + w] = e;
+            carry = shfl(R, 0);
         }
     }
     if (threadIdx.x == 0) st->ticket_w = 0u;
 }
 
-// tau_k from P^agg; with STEP the clamped step and the end of the iteration
+// the last block of the step: close the iteration of every chain that took a step
+__device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
+    __shared__ int s_run;
+    __shared__ unsigned long long s_dm;
+    if (threadIdx.x == 0) { s_run = 0; s_dm = 0ULL; }
+    __syncthreads();
+    const bool failed = st->error != 0;
+    int run = 0;
+    unsigned long long dm = 0ULL;
+    for (int c = threadIdx.x; c < d.nchains; c += blockDim.x) {
+        const unsigned long long m = __ldcg(&d.chain_maxdt[c]);
+        d.chain_maxdt[c] = 0ULL;
+        d.chain_maxtau[c] = 0ULL;
+        if (failed || d.chain_done[c]) continue;
+        const double mc = __longlong_as_double((long long)m);
+        d.chain_lastdt[c] = mc;
+        d.chain_iters[c] += 1;
+        dm = max(dm, m);
+        if (mc < d.prm.conv_tol) d.chain_done[c] = 1;
+        else ++run;
+    }
+    if (run) atomicAdd(&s_run, run);
+    if (dm) atomicMax(&s_dm, dm);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (failed) {
+            st->done = 1;  // a failed iteration leaves theta as the kernels found it at the first error
+        } else {
+            st->last_max_dtheta = __longlong_as_double((long long)s_dm);
+            st->iters += 1;
+            if (s_run == 0) st->done = 1;  // every chain converged
+        }
+        st->ticket = 0u;
+    }
+}
+
+// tau_k from P^agg; with STEP the clamped step of the chains still running and the end of the
+// iteration
 template <bool STEP, class T>
 __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
     constexpr bool DF = std::is_same<T, df>::value;
-    __shared__ unsigned long long smax[4];
     __shared__ bool last;
     Status* st = d.status;
     if (st->done) return;
     const int jj = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long adt = 0ULL, atau = 0ULL;  // bit patterns of non-negative doubles
     bool bad = false;
+    int cj = -1;
     if (jj < d.l) {
-        const int h = jj + 1, tile = h >> 5;  // joint jj moves links jj+1 .. l
+        cj = d.joint_chain[jj];
+        const int h = jj + cj + 1, tile = h >> 5;  // joint jj moves links h .. the chain's last link
         const T* ls = reinterpret_cast<const T*>(d.lane_suf);
         const T* ts = reinterpret_cast<const T*>(d.tileSuf);
+        const bool own = d.ltail[h] != 0;  // the chain ends within this tile
         T A[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) A[k] = add(ls[6 * (size_t)h + k], ts[6 * (size_t)tile + k]);
+        for (int k = 0; k < 6; ++k) A[k] = own ? ls[6 * (size_t)h + k] : add(ls[6 * (size_t)h + k], ts[6 * (size_t)tile + k]);
         const T* u = reinterpret_cast<const T*>(DF ? d.ucurdf : d.ucur) + 3 * jj;
         const T* p = reinterpret_cast<const T*>(DF ? d.pcurdf : d.pcur) + 3 * jj;
         const T px = sub(mul(p[1], u[2]), mul(p[2], u[1]));
@@ -159,7 +242,9 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
         d.tau[jj] = t;
         bad = !isfinite(t);
         atau = (unsigned long long)__double_as_longlong(fabs(t));
-        if (STEP && !bad) {
+        if (d.chain_done[cj]) {
+            cj = -1;  // a converged chain takes no more steps
+        } else if (STEP && !bad) {
             const double dt = fmin(fmax(d.prm.kappa * t, -d.prm.dtheta_max), d.prm.dtheta_max);
             d.theta[jj] += dt;
             d.dtheta[jj] = dt;
@@ -167,78 +252,46 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
         }
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->error, kErrNonfinite);
-    for (int o = 16; o > 0; o >>= 1) {
-        adt = max(adt, __shfl_down_sync(0xffffffffu, adt, o));
-        atau = max(atau, __shfl_down_sync(0xffffffffu, atau, o));
-    }
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = adt;
-    if ((threadIdx.x & 31) == 0 && atau) atomicMax(&st->max_abs_tau, atau);
+    chain_max(d.chain_maxtau, cj, atau);
     if (!STEP) return;
+    chain_max(d.chain_maxdt, cj, adt);
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long m = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = max(m, smax[k]);
-        atomicMax(&st->max_dtheta, m);
-        __threadfence();
-        last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-    }
+    if (threadIdx.x == 0) last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (last && threadIdx.x == 0) {  // the last block closes the iteration
-        __threadfence();
-        const double mall = __longlong_as_double((long long)atomicAdd(&st->max_dtheta, 0ULL));
-        if (st->error) {
-            st->done = 1;  // a failed iteration leaves theta as the kernels found it at the first error
-        } else {
-            st->last_max_dtheta = mall;
-            st->iters += 1;
-            if (mall < d.prm.conv_tol) st->done = 1;
-        }
-        st->max_dtheta = 0ULL;
-        st->max_abs_tau = 0ULL;
-        st->ticket = 0u;
-    }
+    if (!last) return;
+    __threadfence();
+    close_iteration(d, st);
 }
 
-// the paper's normalised step (eq. KCM_07): dtheta_k = kappa tau_k / max |tau|
+// the paper's normalised step (eq. KCM_07): dtheta_k = kappa tau_k / max |tau| over the joint's chain
 __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
-    __shared__ unsigned long long smax[4];
     __shared__ bool last;
     Status* st = d.status;
     if (st->done) return;
-    if (st->error) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->done = 1;
-        return;
-    }
     const int jj = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long adt = 0ULL;
-    if (jj < d.l) {
-        const double tm = __longlong_as_double((long long)st->max_abs_tau);
-        const double dt = tm > 0.0 ? d.prm.kappa * d.tau[jj] / tm : 0.0;
-        d.theta[jj] += dt;
-        d.dtheta[jj] = dt;
-        adt = (unsigned long long)__double_as_longlong(fabs(dt));
+    int cj = -1;
+    if (jj < d.l && !st->error) {
+        cj = d.joint_chain[jj];
+        if (d.chain_done[cj]) {
+            cj = -1;
+        } else {
+            const double tm = __longlong_as_double((long long)__ldcg(&d.chain_maxtau[cj]));
+            const double dt = tm > 0.0 ? d.prm.kappa * d.tau[jj] / tm : 0.0;
+            d.theta[jj] += dt;
+            d.dtheta[jj] = dt;
+            adt = (unsigned long long)__double_as_longlong(fabs(dt));
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) adt = max(adt, __shfl_down_sync(0xffffffffu, adt, o));
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = adt;
+    chain_max(d.chain_maxdt, cj, adt);
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long m = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = max(m, smax[k]);
-        atomicMax(&st->max_dtheta, m);
-        __threadfence();
-        last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-    }
+    if (threadIdx.x == 0) last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        const double mall = __longlong_as_double((long long)atomicAdd(&st->max_dtheta, 0ULL));
-        st->last_max_dtheta = mall;
-        st->iters += 1;
-        if (mall < d.prm.conv_tol) st->done = 1;
-        st->max_dtheta = 0ULL;
-        st->max_abs_tau = 0ULL;
-        st->ticket = 0u;
-    }
+    if (!last) return;
+    __threadfence();
+    close_iteration(d, st);
 }
 
 }  // namespace

@@ -71,6 +71,7 @@ EXPORTS = [
     "kcm_torques", "kcm_torques_dev", "kcm_energy", "kcm_sasa_counts", "kcm_step", "kcm_step_async",
     "kcm_step_status", "kcm_get_stats", "kcm_stream", "kcm_sample_points", "kcm_build_zp", "kcm_pair_class",
     "kcm_topology_natoms", "kcm_strerror", "kcm_last_error", "kcm_step_timed", "kcm_torques_noalloc",
+    "kcm_create_batch", "kcm_nchains", "kcm_chain_offsets", "kcm_chain_energies", "kcm_chain_state",
 ]
 NOALLOC_MAX_LINKS = 32768
 NUM_STAGES = 5
@@ -120,6 +121,12 @@ def load():
                                              C.c_void_p, C.c_void_p]),
             "kcm_strerror": (C.c_char_p, [C.c_int]),
             "kcm_last_error": (C.c_char_p, [h]),
+            "kcm_create_batch": (C.c_int, [C.POINTER(Topology), C.c_int32, C.POINTER(Params), C.c_void_p,
+                                           C.POINTER(C.c_void_p)]),
+            "kcm_nchains": (C.c_int32, [h]),
+            "kcm_chain_offsets": (C.c_int, [h, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+            "kcm_chain_energies": (C.c_int, [h, _dp]),
+            "kcm_chain_state": (C.c_int, [h, _ip, _ip, _dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -230,9 +237,18 @@ class Chain:
         rc = L.kcm_create(self._t.ptr(), C.byref(self._p), C.c_void_p(stream) if stream else None, C.byref(h))
         if rc != KCM_OK:
             raise KcmError(rc, (L.kcm_last_error(None) or b"").decode())
+        self._init_handle(h)
+
+    def _init_handle(self, h):
+        L = load()
         self._h = h
         self.n = int(L.kcm_natoms(h))
         self.l = int(L.kcm_njoints(h))
+        self.nchains = int(L.kcm_nchains(h))
+        ao = np.zeros(self.nchains + 1, dtype=np.int64)
+        jo = np.zeros(self.nchains + 1, dtype=np.int64)
+        _check(L.kcm_chain_offsets(h, ao.ctypes.data_as(C.POINTER(C.c_int64)), jo.ctypes.data_as(C.POINTER(C.c_int64))), h)
+        self.atom_off, self.joint_off = ao, jo
 
     def close(self):
         if getattr(self, "_h", None):
@@ -330,3 +346,41 @@ class Chain:
         s = Stats()
         _check(load().kcm_get_stats(self._h, C.byref(s)), self._h)
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def chain_energies(self):
+        """Coulomb, LJ and solvation energies of every chain at the current theta: [nchains, 3]."""
+        E = np.zeros((self.nchains, 3))
+        _check(load().kcm_chain_energies(self._h, _dptr(E)), self._h)
+        return E
+
+    def chain_state(self):
+        """(iterations, converged, max |dtheta| of the last step) per chain since the last step call."""
+        it = np.zeros(self.nchains, dtype=np.int32)
+        cv = np.zeros(self.nchains, dtype=np.int32)
+        dm = np.zeros(self.nchains)
+        _check(load().kcm_chain_state(self._h, _iptr(it), _iptr(cv), _dptr(dm)), self._h)
+        return it, cv.astype(bool), dm
+
+
+class Batch(Chain):
+    """Independent chains stepped together in one handle (kcm_create_batch): atoms and joints of the
+    chains are concatenated in order (atom_off, joint_off); every per-atom or per-joint method of
+    Chain covers the whole batch."""
+
+    def __init__(self, seqs, table, params, geometry=None, stream=None):
+        L = load()
+        self._ts = [TopologyArgs(s, table, geometry) for s in seqs]
+        tops = (Topology * len(self._ts))(*[t.top for t in self._ts])
+        self._tops = tops
+        self._p = params_struct(params)
+        h = C.c_void_p()
+        rc = L.kcm_create_batch(tops, len(self._ts), C.byref(self._p), C.c_void_p(stream) if stream else None,
+                                C.byref(h))
+        if rc != KCM_OK:
+            raise KcmError(rc, (L.kcm_last_error(None) or b"").decode())
+        self._init_handle(h)
+
+    def split(self, x, per="atom"):
+        """The per-chain pieces of a batch array (per atom or per joint)."""
+        off = self.atom_off if per == "atom" else self.joint_off
+        return [x[off[c]:off[c + 1]] for c in range(self.nchains)]

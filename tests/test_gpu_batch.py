@@ -1,0 +1,129 @@
+"""Batches of chains (kcm_create_batch) against the same chains alone and against the oracle.
+
+A batch concatenates its chains; every scan is segmented at chain boundaries and every chain has
+its own cell grid, so each chain's results must equal its results alone up to rounding order
+(the scan blocks fall differently), and its iteration count and convergence must be its own."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1712_05012_b300 import synth
+
+from kcm_testutil import rel_inf, tol_positions
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kcm():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1712_05012_b300 import kcm as K
+    K.load()
+    return K
+
+# lengths from one residue up, starts of both kinds
+CASES = [(1, 11, "uniform"), (2, 12, "uniform"), (3, 13, "compact"), (17, 14, "compact"), (40, 15, "extended"),
+         (97, 16, "compact"), (5, 17, "uniform")]
+
+
+def chain_inputs(table):
+    seqs, thetas = [], []
+    for m, seed, kind in CASES:
+        seq = synth.sequence(m, seed)
+        if kind == "compact":
+            th = synth.theta_from_codes(O.OracleChain(seq, table, synth.GEOMETRY).grow_start(seed))
+        elif kind == "extended":
+            th = synth.theta_extended(m)
+        else:
+            th = synth.theta_uniform(m, seed)
+        seqs.append(seq)
+        thetas.append(th)
+    return seqs, thetas
+
+
+def alone(kcm, seq, table, p, th):
+    with kcm.Chain(seq, table, p) as ch:
+        ch.set_theta(th)
+        return dict(xyz=ch.positions(), tau=ch.torques(), E=ch.energy(), F=ch.forces())
+
+
+@pytest.mark.parametrize("precision", [synth.PRECISION_FP64, synth.PRECISION_MIXED])
+def test_batch_matches_alone(kcm, table, precision):
+    seqs, thetas = chain_inputs(table)
+    p = synth.RunParams(precision=precision)
+    with kcm.Batch(seqs, table, p) as b:
+        assert b.nchains == len(seqs)
+        b.set_theta(np.concatenate(thetas))
+        xyz = b.split(b.positions())
+        tau = b.split(b.torques(), per="joint")
+        F = b.split(b.forces())
+        E = b.chain_energies()
+        Etot = b.energy()
+    tol = 1e-10 if precision == synth.PRECISION_FP64 else 1e-9
+    for c, (seq, th) in enumerate(zip(seqs, thetas)):
+        ref = alone(kcm, seq, table, p, th)
+        assert np.max(np.abs(xyz[c] - ref["xyz"])) < 1e-9
+        assert rel_inf(tau[c], ref["tau"]) < tol, c
+        assert rel_inf(F[c], ref["F"]) < tol, c
+        np.testing.assert_allclose(E[c], ref["E"], rtol=1e-6 if precision else 1e-10, atol=1e-6)
+    # two evaluations: mixed-mode energies are FP32 per warp, summed by atomics in any order
+    np.testing.assert_allclose(Etot, E.sum(0), rtol=1e-12 if precision == synth.PRECISION_FP64 else 1e-6, atol=1e-9)
+
+
+def test_batch_fp64_matches_oracle(kcm, table):
+    seqs, thetas = chain_inputs(table)
+    p = synth.RunParams(precision=synth.PRECISION_FP64)
+    with kcm.Batch(seqs, table, p) as b:
+        b.set_theta(np.concatenate(thetas))
+        tau = b.split(b.torques(), per="joint")
+        xyz = b.split(b.positions())
+    for c in (2, 5):  # a 3-residue and the 97-residue compact chain
+        och = O.OracleChain(seqs[c], table, synth.GEOMETRY)
+        ref = och.evaluate(p, thetas[c])
+        assert np.max(np.abs(xyz[c] - ref["xyz"])) < tol_positions(och.l)
+        assert rel_inf(tau[c], ref["tau"]) < 1e-10
+
+
+def test_batch_steps_and_convergence_per_chain(kcm, table):
+    """Every chain stops when its own max |dtheta| falls below conv_tol; the batch loop ends when all
+    have. The iterations, theta and last step of each chain equal those of the chain stepped alone."""
+    seqs, thetas = chain_inputs(table)
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=0, kappa=2e-5, conv_tol=2e-3)
+    n = 60
+    with kcm.Batch(seqs, table, p) as b:
+        b.set_theta(np.concatenate(thetas))
+        it_b, _ = b.step(n)
+        th_b = b.split(b.get_theta(), per="joint")
+        iters, conv, dm = b.chain_state()
+    its = []
+    for c, (seq, th) in enumerate(zip(seqs, thetas)):
+        with kcm.Chain(seq, table, p) as ch:
+            ch.set_theta(th)
+            it, d1 = ch.step(n)
+            its.append(it)
+            assert iters[c] == it, c
+            assert conv[c] == (it < n or d1 < p.conv_tol), c
+            assert np.max(np.abs(th_b[c] - ch.get_theta())) < 1e-9, c
+            assert abs(dm[c] - d1) < 1e-9
+    assert it_b == max(its)
+    assert len(set(its)) > 1  # the chains converge at different iterations
+
+
+def test_batch_mixed_steps_match_alone(kcm, table):
+    """Mixed mode, three iterations: the double-float kinematics round differently in the batch
+    (its scan blocks fall elsewhere), by ~1e-13 A, which can move an FP32 rounding of the next
+    iteration's cell offsets and so the torques by ~1e-7 relative; kappa = 1e-3 makes that ~1e-7 rad
+    per step. The bound, 1e-5 rad after three steps, is far inside the mixed torque tolerance
+    (1e-4 of max |tau| per step)."""
+    seqs, thetas = chain_inputs(table)
+    p = synth.RunParams(precision=synth.PRECISION_MIXED)
+    with kcm.Batch(seqs, table, p) as b:
+        b.set_theta(np.concatenate(thetas))
+        b.step(3)
+        th_b = b.split(b.get_theta(), per="joint")
+    for c, (seq, th) in enumerate(zip(seqs, thetas)):
+        with kcm.Chain(seq, table, p) as ch:
+            ch.set_theta(th)
+            ch.step(3)
+            assert np.max(np.abs(th_b[c] - ch.get_theta())) < 1e-5, c
