@@ -321,6 +321,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.chain_iters, hc.nchains)) || (rc = dalloc(h, &d.chain_maxdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_maxtau, hc.nchains)) || (rc = dalloc(h, &d.chain_lastdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_E, 3 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.gseg, l)) ||
+        (rc = dalloc(h, &d.jhead, l)) || (rc = dalloc(h, &d.lflag, L)) ||
         (rc = dalloc(h, &d.tileF, d.ntiles)) || (rc = dalloc(h, &d.ltail, L)) || (rc = dalloc(h, &d.tileT, d.ltiles)))
         return bail(rc);
 
@@ -346,10 +347,14 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
     std::vector<double> ident = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
     if (prm->precision == KCM_MIXED) ident = pack_df(ident);  // base-link poses in the mixed kernels' format
     std::vector<int> atom_chain(n), joint_chain(l), link_chain(L);
+    std::vector<unsigned char> jhead(l, 0), lflag(L, 0);
     for (int ch = 0; ch < hc.nchains; ++ch) {
         for (int a = hc.atom_off[ch]; a < hc.atom_off[ch + 1]; ++a) atom_chain[a] = ch;
         for (int j = hc.joint_off[ch]; j < hc.joint_off[ch + 1]; ++j) joint_chain[j] = ch;
         for (int k = hc.link_off[ch]; k < hc.link_off[ch + 1]; ++k) link_chain[k] = ch;
+        jhead[hc.joint_off[ch]] = 1;
+        lflag[hc.link_off[ch]] |= 1;
+        lflag[hc.link_off[ch + 1] - 1] |= 2;
     }
     std::vector<double> u0df = pack_df(hc.u0), step0df = pack_df(hc.step0), r0df = pack_df(hc.zp_rel);
     if ((rc = upload(h, d.r0, hc.zp_rel.data(), 3 * nn)) || (rc = upload(h, d.link, hc.link.data(), nn)) ||
@@ -362,7 +367,8 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = upload(h, d.Q64, Q64.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q32, Q32.data(), 3 * (size_t)N)) ||
         (rc = upload(h, d.atom_chain, atom_chain.data(), nn)) || (rc = upload(h, d.joint_chain, joint_chain.data(), l)) ||
         (rc = upload(h, d.link_chain, link_chain.data(), L)) || (rc = upload(h, d.joint_off, hc.joint_off.data(), hc.nchains + 1)) ||
-        (rc = upload(h, d.ccap, ccap.data(), hc.nchains)) || (rc = upload(h, d.u0df, u0df.data(), 3 * l)) ||
+        (rc = upload(h, d.ccap, ccap.data(), hc.nchains)) || (rc = upload(h, d.jhead, jhead.data(), l)) ||
+        (rc = upload(h, d.lflag, lflag.data(), L)) || (rc = upload(h, d.u0df, u0df.data(), 3 * l)) ||
         (rc = upload(h, d.step0df, step0df.data(), 3 * l)) || (rc = upload(h, d.r0df, r0df.data(), 3 * nn)))
         return bail(rc);
     e = cudaMemsetAsync(d.theta, 0, sizeof(double) * l, h->stream);

@@ -9,6 +9,10 @@ namespace kcm {
 namespace dev {
 
 // ---------------------------------------------------------------- small helpers
+// chain of an atom or joint (no load for a single chain)
+__device__ __forceinline__ int atom_chain(const DevChain& d, int a) { return d.nchains == 1 ? 0 : d.atom_chain[a]; }
+__device__ __forceinline__ int joint_chain(const DevChain& d, int j) { return d.nchains == 1 ? 0 : d.joint_chain[j]; }
+
 __device__ __forceinline__ unsigned long long dkey(double x) {
     unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
     return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
         bool head = false;
         if (j < d.l) {
             joint_row(d, j, rr, g);
-            head = j == d.joint_off[d.joint_chain[j]];
+            head = d.jhead[j] != 0;
         } else {
             row_identity(rr, g);
         }
@@ -343,6 +343,8 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     __shared__ T sW[kFkWarps][12];
     __shared__ int sF[kFkWarps];
     __shared__ int sScan[kFkWarps];
+    __shared__ unsigned long long sB[6][kFkWarps];
+    __shared__ int sC[kFkWarps];
     __shared__ bool sLast;
     Status* st = d.status;
     if (st->done) return;
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
                 const double* u = &d.u0[3 * j];
                 const T uc = fma(Ma[2], num<T>(u[2]), fma(Ma[1], num<T>(u[1]), mul(Ma[0], num<T>(u[0]))));
                 d.ucur[3 * j + rr] = to_double(uc);
-                store_row(&M[12 * ((size_t)j + d.joint_chain[j] + 1)], rr, Ma);
+                store_row(&M[12 * ((size_t)j + joint_chain(d, j) + 1)], rr, Ma);
                 d.pcur[3 * j + rr] = to_double(Ma[3]);
                 if constexpr (!std::is_same<T, double>::value) {  // for the double-float torque kernel
                     reinterpret_cast<T*>(d.ucurdf)[3 * j + rr] = uc;
@@ -393,14 +395,14 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     // atoms of the block's links: those after the link of the previous block's last joint up to the
     // link of this block's last joint (chains' base links included; their pose is the identity)
     const int jb0 = blockIdx.x * kFkQuads * J, jb1 = min((int)(blockIdx.x + 1) * kFkQuads * J, d.l);
-    const int hfirst = blockIdx.x == 0 ? 0 : jb0 + d.joint_chain[jb0 - 1] + 1;
-    const int hlast = blockIdx.x == gridDim.x - 1 ? d.L : jb1 + d.joint_chain[jb1 - 1] + 1;
+    const int hfirst = blockIdx.x == 0 ? 0 : jb0 + joint_chain(d, jb0 - 1) + 1;
+    const int hlast = blockIdx.x == gridDim.x - 1 ? d.L : jb1 + joint_chain(d, jb1 - 1) + 1;
     const int a1 = d.link_start[hlast];
     const T* r0 = reinterpret_cast<const T*>(std::is_same<T, double>::value ? (const void*)d.r0 : (const void*)d.r0df);
     unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0ULL, 0ULL, 0ULL};
     int cc = -1;  // chain of the keys held in mn, mx
     for (int a = d.link_start[hfirst] + threadIdx.x; a < a1; a += blockDim.x) {
-        const int ca = d.atom_chain[a];
+        const int ca = atom_chain(d, a);
         if (ca != cc) {  // a thread's atoms move on to the next chain: hand in the box so far
             if (cc >= 0)
                 for (int i = 0; i < 3; ++i) { atomicMin(&d.cbox[6 * cc + i], mn[i]); atomicMax(&d.cbox[6 * cc + 3 + i], mx[i]); }
@@ -420,9 +422,11 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
             mx[i] = max(mx[i], key);
         }
     }
-    // warps whose threads all hold the same chain reduce first; the others hand in lane by lane
+    // warps whose threads all hold the same chain reduce first (and the block, when all its warps do);
+    // the others hand in lane by lane
     const int cw = __reduce_max_sync(0xffffffffu, cc);
-    if (__all_sync(0xffffffffu, cc == cw || cc < 0)) {
+    const bool wuni = __all_sync(0xffffffffu, cc == cw || cc < 0);
+    if (wuni) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
 #pragma unroll
@@ -431,10 +435,34 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
                 mx[i] = max(mx[i], __shfl_down_sync(0xffffffffu, mx[i], o));
             }
         }
-        if (lane == 0 && cw >= 0)
-            for (int i = 0; i < 3; ++i) { atomicMin(&d.cbox[6 * cw + i], mn[i]); atomicMax(&d.cbox[6 * cw + 3 + i], mx[i]); }
+        if (lane == 0)
+            for (int i = 0; i < 3; ++i) { sB[i][w] = mn[i]; sB[3 + i][w] = mx[i]; }
     } else if (cc >= 0) {
         for (int i = 0; i < 3; ++i) { atomicMin(&d.cbox[6 * cc + i], mn[i]); atomicMax(&d.cbox[6 * cc + 3 + i], mx[i]); }
+    }
+    if (lane == 0) sC[w] = wuni ? cw : -2;
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int i = threadIdx.x;
+        int cb = -1;
+        bool buni = true;
+        for (int k = 0; k < kFkWarps; ++k) {
+            if (sC[k] == -2 || (sC[k] >= 0 && cb >= 0 && sC[k] != cb)) buni = false;
+            if (sC[k] >= 0) cb = sC[k];
+        }
+        if (buni && cb >= 0) {  // one chain in the whole block: one atomic per component
+            unsigned long long v = i < 3 ? ~0ULL : 0ULL;
+            for (int k = 0; k < kFkWarps; ++k)
+                if (sC[k] >= 0) v = i < 3 ? min(v, sB[i][k]) : max(v, sB[i][k]);
+            if (i < 3) atomicMin(&d.cbox[6 * cb + i], v);
+            else atomicMax(&d.cbox[6 * cb + i], v);
+        } else if (!buni) {
+            for (int k = 0; k < kFkWarps; ++k) {
+                if (sC[k] < 0) continue;
+                if (i < 3) atomicMin(&d.cbox[6 * sC[k] + i], sB[i][k]);
+                else atomicMax(&d.cbox[6 * sC[k] + i], sB[i][k]);
+            }
+        }
     }
     __threadfence();
     __syncthreads();

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (a < d.n) {
-        const GridInfo g = d.grid[d.atom_chain[a]];
+        const GridInfo g = d.grid[atom_chain(d, a)];
         int cx = min(max((int)floorf((float)(d.r[3 * a] - g.ox) * g.inv_sf), 0), g.nx - 1);
         int cy = min(max((int)floorf((float)(d.r[3 * a + 1] - g.oy) * g.inv_sf), 0), g.ny - 1);
         int cz = min(max((int)floorf((float)(d.r[3 * a + 2] - g.oz) * g.inv_sf), 0), g.nz - 1);
@@ -211,7 +211,7 @@ template <bool MIXED>
 __global__ void k_bin_place(const DevChain d) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= d.n || d.status->done) return;
-    const GridInfo g = d.grid[d.atom_chain[a]];
+    const GridInfo g = d.grid[atom_chain(d, a)];
     int key = d.key[a];
     int sl = d.cell_start[key] + d.rank[a];
     d.sorted[sl] = a;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     int ca = -1;  // chain of the home atom
     if (sl < d.n && !d.status->done) {
         const int a = d.sorted[sl];
-        ca = d.atom_chain[a];
+        ca = atom_chain(d, a);
         const GridInfo g = d.grid[ca];  // the home atom's chain: its candidates are that chain's atoms
         const int cell = d.slot_cell[sl] - g.cbase;
         const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
             const float drf = (float)dr;
             // guard band of the FP32 overlap test (A^2): a bound of about 5e-5 A^2 at a 10 A cell edge,
             // from the cell-relative offsets (error < 7 s 2^-24 per component) and the test's own rounding
-            const float gs = (float)(2e-4 + 4e-5 * d.grid[d.atom_chain[a]].s);
+            const float gs = (float)(2e-4 + 4e-5 * d.grid[atom_chain(d, a)].s);
             int ncov = 0, nguard = 0;
             unsigned long long ntest = 0;
             for (int k = lane; k < d.N; k += 32) {
@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
             const float Ra = d.aprm32[a].w;
             const float inv2R = 0.5f / Ra;
             const float drf = d.f_dr;
-            const float gd = 1e-4f + 1.2e-5f * d.grid[d.atom_chain[a]].sf;  // guard band in Q.o units (A)
+            const float gd = 1e-4f + 1.2e-5f * d.grid[atom_chain(d, a)].sf;  // guard band in Q.o units (A)
             float rmax2 = 0.0f;
             for (int j = lane; j < cnt; j += 32) {
                 const float4 o = d.nbr_off[(size_t)a * kMaxNbr + j];  // r_j - r_i, Roff_j^2

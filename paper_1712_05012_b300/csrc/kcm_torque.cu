@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     int cc = -1;         // chain of the energy held
     for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
         T f[3];
-        const int ca = d.atom_chain[a];
+        const int ca = atom_chain(d, a);
         if (ca != cc && d.prm.solvation) {  // the thread's atoms move on to the next chain
             if (cc >= 0) {
                 if constexpr (DF) { if (Ecavf != 0.0f) atomicAdd(&d.chain_E[3 * cc + 2], (double)Ecavf); }
@@ -111,11 +111,8 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     for (int u = threadIdx.x; u < 6 * 32; u += blockDim.x) {  // P_h component u / 32 of link h0 + u % 32
         const int k = u >> 5, h = h0 + (u & 31);
         T s = num_f<T>(0.0f);
-        if (h < h1) {
-            const int ch = d.link_chain[h];
-            if (h != d.joint_off[ch] + ch)  // a chain's base link has no joint
-                for (int a = d.link_start[h]; a < d.link_start[h + 1]; ++a) s = add(s, sV[a - a0][k]);
-        }
+        if (h < h1 && !(d.lflag[h] & 1))  // a chain's base link has no joint
+            for (int a = d.link_start[h]; a < d.link_start[h + 1]; ++a) s = add(s, sV[a - a0][k]);
         sP[u & 31][k] = s;
     }
     __syncthreads();
@@ -124,7 +121,7 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     if (w < 6) {  // segmented reverse inclusive scan of component w over the tile
         const int h = h0 + lane;
         T x = sP[lane][w];
-        bool tl = h >= d.L - 1 || (h < h1 && d.link_chain[h + 1] != d.link_chain[h]);  // last link of a chain
+        bool tl = h >= d.L - 1 || (h < h1 && (d.lflag[h] & 2));  // last link of a chain
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const T y = shfl_down(x, off);
@@ -178,6 +175,25 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
 __device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
     __shared__ int s_run;
     __shared__ unsigned long long s_dm;
+    if (d.nchains == 1) {  // one chain: one thread closes it
+        if (threadIdx.x == 0) {
+            const unsigned long long m = __ldcg(&d.chain_maxdt[0]);
+            d.chain_maxdt[0] = 0ULL;
+            d.chain_maxtau[0] = 0ULL;
+            if (st->error) {
+                st->done = 1;
+            } else if (!d.chain_done[0]) {
+                const double mc = __longlong_as_double((long long)m);
+                d.chain_lastdt[0] = mc;
+                d.chain_iters[0] += 1;
+                st->last_max_dtheta = mc;
+                st->iters += 1;
+                if (mc < d.prm.conv_tol) { d.chain_done[0] = 1; st->done = 1; }
+            }
+            st->ticket = 0u;
+        }
+        return;
+    }
     if (threadIdx.x == 0) { s_run = 0; s_dm = 0ULL; }
     __syncthreads();
     const bool failed = st->error != 0;
@@ -223,7 +239,7 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
     bool bad = false;
     int cj = -1;
     if (jj < d.l) {
-        cj = d.joint_chain[jj];
+        cj = joint_chain(d, jj);
         const int h = jj + cj + 1, tile = h >> 5;  // joint jj moves links h .. the chain's last link
         const T* ls = reinterpret_cast<const T*>(d.lane_suf);
         const T* ts = reinterpret_cast<const T*>(d.tileSuf);
@@ -273,7 +289,7 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
     unsigned long long adt = 0ULL;
     int cj = -1;
     if (jj < d.l && !st->error) {
-        cj = d.joint_chain[jj];
+        cj = joint_chain(d, jj);
         if (d.chain_done[cj]) {
             cj = -1;
         } else {
