@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--batch-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -69,6 +70,16 @@ def workload():
     seq = synth.sequence(man["residues"], man["sequence_seed"])
     theta = synth.theta_from_codes(np.load(os.path.join(GOLDEN, "start_chain1000.npy")))
     return seq, theta, man
+
+
+def batch_workload():
+    """The 512-chain batch (lengths 30-600 residues) and its stored compact starts, concatenated."""
+    from paper_1712_05012_b300 import synth
+
+    wl = synth.workload(4)
+    seqs = [synth.sequence(m, synth.chain_seed(wl.seed, i)) for i, m in enumerate(wl.m)]
+    theta = synth.theta_from_codes(np.load(os.path.join(GOLDEN, "start_batch512.npy")))
+    return seqs, theta, wl
 
 
 def dist_env():
@@ -286,6 +297,37 @@ def run_ours(args):
                 tt.append(cv.step_timed()[0])
             vacuum_value = n * args.fp64_steps / (sum(tt) / 1e3)
 
+    # the batch workload: 512 chains stepped together, one launch per stage, measured the same way
+    batch = None
+    if args.batch_steps > 0:
+        bseqs, btheta, bwl = batch_workload()
+        with kcm.Batch(bseqs, table, synth.RunParams(precision=prec)) as bb:
+            sb = torch.cuda.ExternalStream(bb.stream())
+            bth0 = torch.tensor(btheta, dtype=torch.float64, device="cuda")
+
+            def prep_b():
+                bb.set_theta_dev(bth0.data_ptr(), bb.l)
+                with torch.cuda.stream(sb):
+                    flush.add_(1)
+
+            for _ in range(3):
+                prep_b()
+                bb.step_timed()
+            tt, stg = [], {k: 0.0 for k in kcm.STAGES}
+            for _ in range(args.batch_steps):
+                prep_b()
+                tot, st = bb.step_timed()
+                tt.append(tot)
+                for k, v in st.items():
+                    stg[k] += v
+            bst = bb.stats()
+            batch = {"workload": bwl.name, "chains": bb.nchains, "atoms": bb.n, "residues": int(sum(bwl.m)),
+                     "value": ws * bb.n * args.batch_steps / (sum(tt) / 1e3), "unit": UNIT,
+                     "ms_per_step": sum(tt) / args.batch_steps,
+                     "stage_ms": {k: v / args.batch_steps for k, v in stg.items()},
+                     "steps": args.batch_steps, "pairs": bst["pairs"], "sasa_tests": bst["sasa_tests"],
+                     "start": "every step from the stored compact starts (theta restored untimed)"}
+
     # the plain FP64 single-chain GPU path, measured the same way
     fp64_value = None
     if args.fp64_steps > 0 and prec == synth.PRECISION_MIXED:
@@ -347,7 +389,7 @@ def run_ours(args):
                            "replicas": ws, "l2": "flushed between timed steps (256 MiB write)",
                            "start": "every step from the stored compact start (theta restored untimed)"},
                 "roofline": roof, "rooflines": rooflines, "stage_ms": ms_stage, "fp64_value": fp64_value,
-                "vacuum_value": vacuum_value,
+                "vacuum_value": vacuum_value, "batch": batch,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,
                 "clocks": clk, "stats": {k: stats[k] for k in ("pairs", "sasa_tests", "sasa_neighbors",

@@ -1,4 +1,4 @@
-"""Write the compact self-avoiding random-walk starts of the long-chain workloads.
+"""Write the compact self-avoiding random-walk starts of the long-chain and batch workloads.
 
 Run from the repository root:  python tests/golden/make_starts.py
 Each start is the oracle's residue-by-residue growth (phi, psi uniform, redrawn until no heavy-atom
@@ -39,6 +39,20 @@ def main():
         manifest[name] = {"workload": k, "residues": m, "sequence_seed": seed, "grow_seed": seed,
                           "min_dist": 2.5, "max_retries": 100, "backtrack": 5, "atoms": ch.n}
         print(name, ch.n, "atoms")
+    # the batch workload: every chain grown the same way, codes concatenated in chain order
+    wl = synth.workload(4)
+    codes_all = []
+    natoms = 0
+    for i, m in enumerate(wl.m):
+        seed = synth.chain_seed(wl.seed, i)
+        ch = O.OracleChain(synth.sequence(m, seed), table, synth.GEOMETRY)
+        codes_all.append(ch.grow_start(seed, min_dist=2.5, max_retries=100, backtrack=5))
+        natoms += ch.n
+    np.save(os.path.join(HERE, "start_batch512.npy"), np.concatenate(codes_all))
+    manifest["batch512"] = {"workload": 4, "chains": len(wl.m), "residues_total": int(sum(wl.m)),
+                            "sequence_seed": "chain_seed(workload seed, chain index)", "grow_seed": "the same",
+                            "min_dist": 2.5, "max_retries": 100, "backtrack": 5, "atoms": natoms}
+    print("batch512", len(wl.m), "chains", natoms, "atoms")
     with open(os.path.join(HERE, "starts.json"), "w") as f:
         json.dump(manifest, f, indent=1, sort_keys=True)
 

@@ -127,3 +127,32 @@ def test_batch_mixed_steps_match_alone(kcm, table):
             ch.set_theta(th)
             ch.step(3)
             assert np.max(np.abs(th_b[c] - ch.get_theta())) < 1e-5, c
+
+
+def test_batch512_mixed_vs_fp64_and_oracle(kcm, table):
+    """The 512-chain batch workload from its stored compact starts: every chain's mixed torques
+    within 1e-4 (relative to the chain's largest) of the FP64 batch, and three chains (the shortest,
+    a middle one and the longest) against the oracle."""
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    wl = synth.workload(4)
+    seqs = [synth.sequence(m, synth.chain_seed(wl.seed, i)) for i, m in enumerate(wl.m)]
+    theta = synth.theta_from_codes(np.load(os.path.join(here, "golden", "start_batch512.npy")))
+    man = json.load(open(os.path.join(here, "golden", "starts.json")))["batch512"]
+    tau = {}
+    for prec in (synth.PRECISION_MIXED, synth.PRECISION_FP64):
+        with kcm.Batch(seqs, table, synth.RunParams(precision=prec)) as b:
+            assert b.n == man["atoms"]
+            b.set_theta(theta)
+            tau[prec] = b.split(b.torques(), per="joint")
+            joff = b.joint_off
+    worst = max(rel_inf(tm, tf) for tm, tf in zip(tau[synth.PRECISION_MIXED], tau[synth.PRECISION_FP64]))
+    assert worst < 1e-4
+    order = np.argsort(wl.m)
+    for c in (order[0], order[len(order) // 2], order[-1]):
+        och = O.OracleChain(seqs[c], table, synth.GEOMETRY)
+        ref = och.evaluate(synth.RunParams(precision=synth.PRECISION_FP64), theta[joff[c]:joff[c + 1]])
+        assert rel_inf(tau[synth.PRECISION_FP64][c], ref["tau"]) < 1e-10
+        assert rel_inf(tau[synth.PRECISION_MIXED][c], ref["tau"]) < 1e-4
+
