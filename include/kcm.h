@@ -187,6 +187,68 @@ int kcm_chain_energies(kcm_handle h, double* E);
  * kcm_nchains entries, host memory, any may be NULL; waits for the handle's stream. */
 int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta);
 
+/* Cap on the iterations every chain may take in each later kcm_step / kcm_step_async call:
+ * max_iters[c] for chain c (kcm_nchains entries, host memory; NULL removes every cap). A chain with
+ * a cap <= 0 takes no step at all and costs no pair or solvation work; a chain that reaches its cap
+ * stops like a converged one (kcm_chain_state reports converged = 1 and its iterations). The
+ * serving loop below uses it to advance chains of a batch by different amounts. */
+int kcm_set_chain_max_iters(kcm_handle h, const int32_t* max_iters);
+
+/* Device memory held by the handle, in bytes (-1 for NULL). */
+int64_t kcm_device_bytes(kcm_handle h);
+
+/* ---------------------------------------------------------------- serving loop
+ * A request loop for folding jobs (no counterpart in the paper, which folds one chain at a time):
+ * jobs of any chain length are submitted at any time, admitted as device memory frees up under a
+ * budget, stepped with all other admitted jobs on the device (continuous batching: every admission
+ * wave is a batch on a stream of its own; batches advance in chunks of iterations launched without
+ * waiting), and retired when they converge (max |dtheta| < conv_tol) or reach their iteration cap.
+ * Coordinates, cell lists and theta stay on the device from admission to retirement. Single-threaded:
+ * one thread calls the kcm_server_* functions of a server. Times are seconds since creation (host
+ * clock). */
+typedef struct kcm_server kcm_server;
+
+#define KCM_JOB_WAITING 0
+#define KCM_JOB_RUNNING 1
+#define KCM_JOB_DONE 2
+
+typedef struct {
+    int32_t state;       /* KCM_JOB_* */
+    int32_t error;       /* KCM_OK, or the status that ended the job (e.g. KCM_E_NONFINITE, KCM_E_NOMEM) */
+    int32_t iters;       /* iterations taken */
+    int32_t converged;   /* 1: stopped because max |dtheta| < conv_tol */
+    double max_dtheta;   /* max |dtheta| of its last step */
+    int64_t natoms;
+    double t_submit, t_admit, t_done;
+} kcm_job_info;
+
+/* params: as kcm_create (all jobs of a server share them); hbm_budget_bytes: device memory the
+ * server's batches may hold together (a job that cannot fit even alone ends with KCM_E_NOMEM);
+ * max_chains_per_batch: largest admission wave; chunk_iters: iterations a batch takes between two
+ * looks at its chains. Errors: KCM_E_INVAL, KCM_E_NOMEM. */
+int kcm_server_create(const kcm_params* params, int64_t hbm_budget_bytes, int32_t max_chains_per_batch,
+                      int32_t chunk_iters, kcm_server** out);
+void kcm_server_destroy(kcm_server* s);
+
+/* Queue a job: the chain `top` (copied), its start theta0[l] (l = 2 n_res, host memory, copied) and
+ * its iteration cap. *job_id > 0 names it. Errors: KCM_E_INVAL (bad topology, sizes or cap). */
+int kcm_server_submit(kcm_server* s, const kcm_topology* top, const double* theta0, int64_t l, int32_t max_iters,
+                      int64_t* job_id);
+
+/* Make progress without waiting for the device: collect the batches whose chunk has finished (retire
+ * their done jobs, launch their next chunk, free emptied batches) and admit waiting jobs as the
+ * budget allows. Reports the jobs still waiting and running (either pointer may be NULL). */
+int kcm_server_tick(kcm_server* s, int32_t* n_waiting, int32_t* n_running);
+
+/* Ids of jobs retired since the last poll (at most `capacity`; *n of them written to ids). */
+int kcm_server_poll(kcm_server* s, int64_t* ids, int32_t capacity, int32_t* n);
+
+/* State of a job and, once it is done, its final theta (theta may be NULL; l = 2 n_res). */
+int kcm_server_job(kcm_server* s, int64_t job_id, kcm_job_info* info, double* theta, int64_t l);
+
+/* Device memory held by the server's batches, in bytes (-1 for NULL). */
+int64_t kcm_server_device_bytes(kcm_server* s);
+
 /* Free everything the handle owns. NULL is accepted. */
 void kcm_destroy(kcm_handle h);
 

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -20,6 +21,7 @@ struct kcm_ctx {
     cudaGraphExec_t graph_timed = nullptr;
     cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
     std::vector<void*> allocs;
+    size_t bytes = 0;  // device memory held
     std::string err;
 };
 
@@ -50,6 +52,7 @@ int dalloc(kcm_ctx* h, T** p, size_t count) {
         return set_err(h, KCM_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
     }
     h->allocs.push_back(*p);
+    h->bytes += bytes;
     return KCM_OK;
 }
 
@@ -318,7 +321,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.atom_chain, nn)) || (rc = dalloc(h, &d.joint_chain, l)) || (rc = dalloc(h, &d.link_chain, L)) ||
         (rc = dalloc(h, &d.joint_off, hc.nchains + 1)) || (rc = dalloc(h, &d.ccap, hc.nchains)) ||
         (rc = dalloc(h, &d.cbox, 6 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.chain_done, hc.nchains)) ||
-        (rc = dalloc(h, &d.chain_iters, hc.nchains)) || (rc = dalloc(h, &d.chain_maxdt, hc.nchains)) ||
+        (rc = dalloc(h, &d.chain_iters, hc.nchains)) || (rc = dalloc(h, &d.chain_maxit, hc.nchains)) || (rc = dalloc(h, &d.chain_maxdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_maxtau, hc.nchains)) || (rc = dalloc(h, &d.chain_lastdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_E, 3 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.gseg, l)) ||
         (rc = dalloc(h, &d.jhead, l)) || (rc = dalloc(h, &d.lflag, L)) ||
@@ -376,6 +379,11 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
     if (e == cudaSuccess) e = cudaMemsetAsync(d.Fcav, 0, sizeof(long long) * 3 * nn, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.covered, 0, sizeof(int) * nn, h->stream);
     if (e != cudaSuccess) { cuda_fail(h, e, "memset"); return bail(KCM_E_CUDA); }
+    {
+        std::vector<int> maxit(hc.nchains, INT32_MAX);  // no cap until kcm_set_chain_max_iters
+        rc = upload(h, d.chain_maxit, maxit.data(), hc.nchains);
+        if (rc) return bail(rc);
+    }
     for (int ch = 0; ch < hc.nchains && rc == KCM_OK; ++ch)  // the base link of every chain stays at the origin
         rc = upload(h, d.M + 12 * (size_t)hc.link_off[ch], ident.data(), 12);
     if (rc) return bail(rc);
@@ -415,6 +423,17 @@ int kcm_chain_energies(kcm_handle h, double* E) {
     if (e != cudaSuccess) return cuda_fail(h, e, "energy copy");
     return sync(h);
 }
+
+int kcm_set_chain_max_iters(kcm_handle h, const int32_t* max_iters) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    std::vector<int> m(h->d.nchains, INT32_MAX);
+    if (max_iters)
+        for (int c = 0; c < h->d.nchains; ++c) m[c] = max_iters[c];
+    int rc = upload(h, h->d.chain_maxit, m.data(), m.size());
+    return rc ? rc : sync(h);
+}
+
+int64_t kcm_device_bytes(kcm_handle h) { return h ? static_cast<int64_t>(h->bytes) : -1; }
 
 int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta) {
     if (check_handle(h)) return KCM_E_INVAL;

@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     if (sl < d.n && !d.status->done) {
         const int a = d.sorted[sl];
         ca = atom_chain(d, a);
+        if (!d.chain_done[ca]) {  // a converged chain takes no more steps: no forces needed
         const GridInfo g = d.grid[ca];  // the home atom's chain: its candidates are that chain's atoms
         const int cell = d.slot_cell[sl] - g.cbase;
         const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
@@ -496,6 +497,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             d.nbr_cnt[a] = ncount;
             if (ncount > kMaxNbr) atomicOr(&d.status->error, kErrOverflow);
         }
+        }
     }
     if (lane == 0) { sE[0][w] = Eel; sE[1][w] = Evdw; sC[0][w] = npairs; sC[1][w] = nguard; sC[2][w] = (unsigned long long)ncount; sM[w] = ncount; sCh[w] = ca; }
     __syncthreads();
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
     __shared__ dbl4 s_pos[kSasaWarps][MIXED ? 1 : kMaxNbr];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
-    if (a < d.n && !d.status->done) {
+    if (a < d.n && !d.status->done && !d.chain_done[atom_chain(d, a)]) {
         if (!d.gflag[a]) {
             if (lane == 0) d.covered[a] = 0;
         } else {
@@ -670,7 +672,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
     __shared__ unsigned short s_near[kSasaWarps][kBatch];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
-    if (a < d.n && !d.status->done) {
+    if (a < d.n && !d.status->done && !d.chain_done[atom_chain(d, a)]) {
         if (!d.gflag[a]) {
             if (lane == 0) d.covered[a] = 0;
         } else {
@@ -833,7 +835,7 @@ __global__ void k_reset_loop(const DevChain d, int full) {
         }
     }
     if (c < d.nchains) {
-        d.chain_done[c] = 0;
+        d.chain_done[c] = d.chain_maxit[c] <= 0;  // a chain without iterations to take is done from the start
         d.chain_iters[c] = 0;
         d.chain_maxdt[c] = 0ULL;
         d.chain_maxtau[c] = 0ULL;

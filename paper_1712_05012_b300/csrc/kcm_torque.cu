@@ -188,8 +188,9 @@ __device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
                 d.chain_iters[0] += 1;
                 st->last_max_dtheta = mc;
                 st->iters += 1;
-                if (mc < d.prm.conv_tol) { d.chain_done[0] = 1; st->done = 1; }
+                if (mc < d.prm.conv_tol || d.chain_iters[0] >= d.chain_maxit[0]) d.chain_done[0] = 1;
             }
+            if (d.chain_done[0]) st->done = 1;
             st->ticket = 0u;
         }
         return;
@@ -206,9 +207,10 @@ __device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
         if (failed || d.chain_done[c]) continue;
         const double mc = __longlong_as_double((long long)m);
         d.chain_lastdt[c] = mc;
-        d.chain_iters[c] += 1;
+        const int it = d.chain_iters[c] + 1;
+        d.chain_iters[c] = it;
         dm = max(dm, m);
-        if (mc < d.prm.conv_tol) d.chain_done[c] = 1;
+        if (mc < d.prm.conv_tol || it >= d.chain_maxit[c]) d.chain_done[c] = 1;  // converged or out of iterations
         else ++run;
     }
     if (run) atomicAdd(&s_run, run);

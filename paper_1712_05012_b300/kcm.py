@@ -72,7 +72,10 @@ EXPORTS = [
     "kcm_step_status", "kcm_get_stats", "kcm_stream", "kcm_sample_points", "kcm_build_zp", "kcm_pair_class",
     "kcm_topology_natoms", "kcm_strerror", "kcm_last_error", "kcm_step_timed", "kcm_torques_noalloc",
     "kcm_create_batch", "kcm_nchains", "kcm_chain_offsets", "kcm_chain_energies", "kcm_chain_state",
+    "kcm_set_chain_max_iters", "kcm_device_bytes", "kcm_server_create", "kcm_server_destroy", "kcm_server_submit",
+    "kcm_server_tick", "kcm_server_poll", "kcm_server_job", "kcm_server_device_bytes",
 ]
+JOB_WAITING, JOB_RUNNING, JOB_DONE = 0, 1, 2
 NOALLOC_MAX_LINKS = 32768
 NUM_STAGES = 5
 STAGES = ("kinematics", "binning", "pairs", "solvation", "torques_step")
@@ -127,6 +130,17 @@ def load():
             "kcm_chain_offsets": (C.c_int, [h, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
             "kcm_chain_energies": (C.c_int, [h, _dp]),
             "kcm_chain_state": (C.c_int, [h, _ip, _ip, _dp]),
+            "kcm_set_chain_max_iters": (C.c_int, [h, _ip]),
+            "kcm_device_bytes": (C.c_int64, [h]),
+            "kcm_server_create": (C.c_int, [C.POINTER(Params), C.c_int64, C.c_int32, C.c_int32,
+                                            C.POINTER(C.c_void_p)]),
+            "kcm_server_destroy": (None, [C.c_void_p]),
+            "kcm_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Topology), _dp, C.c_int64, C.c_int32,
+                                            C.POINTER(C.c_int64)]),
+            "kcm_server_tick": (C.c_int, [C.c_void_p, _ip, _ip]),
+            "kcm_server_poll": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int32, _ip]),
+            "kcm_server_job": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(JobInfo), _dp, C.c_int64]),
+            "kcm_server_device_bytes": (C.c_int64, [C.c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -156,6 +170,12 @@ def params_struct(p) -> Params:
     for name, _ in Params._fields_:
         setattr(s, name, getattr(p, name))
     return s
+
+
+class JobInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("iters", C.c_int32), ("converged", C.c_int32),
+                ("max_dtheta", C.c_double), ("natoms", C.c_int64), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double)]
 
 
 class TopologyArgs:
@@ -353,6 +373,17 @@ class Chain:
         _check(load().kcm_chain_energies(self._h, _dptr(E)), self._h)
         return E
 
+    def set_chain_max_iters(self, caps=None):
+        """Per-chain iteration caps for later step calls (None removes them)."""
+        if caps is None:
+            _check(load().kcm_set_chain_max_iters(self._h, None), self._h)
+        else:
+            a = np.ascontiguousarray(caps, dtype=np.int32)
+            _check(load().kcm_set_chain_max_iters(self._h, _iptr(a)), self._h)
+
+    def device_bytes(self) -> int:
+        return int(load().kcm_device_bytes(self._h))
+
     def chain_state(self):
         """(iterations, converged, max |dtheta| of the last step) per chain since the last step call."""
         it = np.zeros(self.nchains, dtype=np.int32)
@@ -384,3 +415,65 @@ class Batch(Chain):
         """The per-chain pieces of a batch array (per atom or per joint)."""
         off = self.atom_off if per == "atom" else self.joint_off
         return [x[off[c]:off[c + 1]] for c in range(self.nchains)]
+
+
+class Server:
+    """The serving loop (kcm_server_*): submit jobs, tick, poll retired jobs, read their results."""
+
+    def __init__(self, params, hbm_budget_bytes: int, max_chains_per_batch: int = 512, chunk_iters: int = 50):
+        L = load()
+        self._p = params_struct(params)
+        s = C.c_void_p()
+        _check(L.kcm_server_create(C.byref(self._p), int(hbm_budget_bytes), int(max_chains_per_batch),
+                                   int(chunk_iters), C.byref(s)))
+        self._s = s
+        self._tops = {}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            load().kcm_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, res_type, table, theta0, max_iters: int, geometry=None) -> int:
+        t = TopologyArgs(res_type, table, geometry)
+        th = np.ascontiguousarray(theta0, dtype=np.float64)
+        jid = C.c_int64()
+        _check(load().kcm_server_submit(self._s, t.ptr(), _dptr(th), len(th), int(max_iters), C.byref(jid)))
+        self._tops[int(jid.value)] = len(th)
+        return int(jid.value)
+
+    def tick(self):
+        w = np.zeros(1, dtype=np.int32)
+        r = np.zeros(1, dtype=np.int32)
+        _check(load().kcm_server_tick(self._s, _iptr(w), _iptr(r)))
+        return int(w[0]), int(r[0])
+
+    def poll(self, capacity: int = 4096):
+        ids = np.zeros(capacity, dtype=np.int64)
+        n = np.zeros(1, dtype=np.int32)
+        _check(load().kcm_server_poll(self._s, ids.ctypes.data_as(C.POINTER(C.c_int64)), capacity, _iptr(n)))
+        return [int(x) for x in ids[:n[0]]]
+
+    def job(self, job_id: int, with_theta: bool = True):
+        info = JobInfo()
+        l = self._tops[job_id]
+        th = np.zeros(l) if with_theta else None
+        _check(load().kcm_server_job(self._s, int(job_id), C.byref(info), _dptr(th) if with_theta else None,
+                                     l if with_theta else 0))
+        d = {k: getattr(info, k) for k, _ in JobInfo._fields_}
+        if with_theta:
+            d["theta"] = th
+        return d
+
+    def device_bytes(self) -> int:
+        return int(load().kcm_server_device_bytes(self._s))
+

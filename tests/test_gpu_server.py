@@ -1,0 +1,138 @@
+"""The serving loop (kcm_server_*): jobs admitted in waves while others run, each result the same
+as the job run alone, per-job convergence and caps, admission under a memory budget."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1712_05012_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kcm():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1712_05012_b300 import kcm as K
+    K.load()
+    return K
+
+
+def jobs(n, seed0=31):
+    out = []
+    for i in range(n):
+        m = [1, 3, 12, 40, 25, 7, 60, 18][i % 8]
+        seq = synth.sequence(m, seed0 + i)
+        th = synth.theta_uniform(m, seed0 + i) * 0.05  # near the extended chain: smooth trajectories
+        out.append((seq, th))
+    return out
+
+
+def run_server(kcm, table, p, items, caps, budget=8 << 30, max_chains=4, chunk=7, waves=3):
+    """Submit the jobs in `waves` groups with ticks in between (later jobs arrive while earlier ones
+    run), then tick until every job is done."""
+    res = {}
+    with kcm.Server(p, budget, max_chains, chunk) as s:
+        ids = []
+        per = (len(items) + waves - 1) // waves
+        for w in range(waves):
+            for (seq, th), cap in zip(items[w * per:(w + 1) * per], caps[w * per:(w + 1) * per]):
+                ids.append(s.submit(seq, table, th, cap))
+            for _ in range(3):
+                s.tick()
+                time.sleep(0.002)
+        t0 = time.time()
+        while True:
+            wt, rn = s.tick()
+            if wt == 0 and rn == 0:
+                break
+            assert time.time() - t0 < 120
+            time.sleep(0.001)
+        done = set(s.poll())
+        assert done == set(ids)
+        for jid in ids:
+            res[jid] = s.job(jid)
+        assert s.device_bytes() == 0  # every batch freed
+    return [res[j] for j in ids]
+
+
+def alone(kcm, table, p, seq, th, n):
+    with kcm.Chain(seq, table, p) as ch:
+        ch.set_theta(th)
+        it, dm = ch.step(n)
+        return it, dm, ch.get_theta()
+
+
+def test_server_results_equal_alone(kcm, table):
+    """FP64: every job's theta after up to 30 iterations (caps spanning several chunks) equals the
+    job run alone to 1e-9 rad."""
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=0)
+    items = jobs(10)
+    caps = [20, 15, 30, 20, 9, 20, 25, 14, 20, 17]
+    got = run_server(kcm, table, p, items, caps)
+    for (seq, th), cap, r in zip(items, caps, got):
+        it, dm, th1 = alone(kcm, table, p, seq, th, cap)
+        assert r["state"] == kcm.JOB_DONE and r["error"] == 0
+        assert r["iters"] == it
+        assert np.max(np.abs(r["theta"] - th1)) < 1e-9
+        assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+
+
+def test_server_mixed_steps_equal_alone(kcm, table):
+    """Mixed mode, within its per-iteration tolerance: the torques of a job in the mix and alone may
+    differ by 1e-4 of the largest (rounding of the double-float kinematics depends on where the
+    chain sits in its batch), so after k clamped steps theta agrees to k kappa 1e-4 max|tau|."""
+    p = synth.RunParams(precision=synth.PRECISION_MIXED, solvation=1)
+    items = jobs(10, seed0=91)
+    caps = [2, 1, 2, 2, 1, 2, 2, 1, 2, 2]
+    got = run_server(kcm, table, p, items, caps, chunk=1)
+    for (seq, th), cap, r in zip(items, caps, got):
+        with kcm.Chain(seq, table, p) as ch:
+            ch.set_theta(th)
+            tmax = np.max(np.abs(ch.torques()))
+        it, dm, th1 = alone(kcm, table, p, seq, th, cap)
+        assert r["iters"] == it
+        assert np.max(np.abs(r["theta"] - th1)) <= cap * p.kappa * 1e-4 * tmax + 1e-12
+
+
+def test_server_convergence_per_job(kcm, table):
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=0, kappa=2e-5, conv_tol=2e-3)
+    items = jobs(8, seed0=57)
+    caps = [200] * 8
+    got = run_server(kcm, table, p, items, caps, chunk=5)
+    its = set()
+    for (seq, th), r in zip(items, got):
+        it, dm, th1 = alone(kcm, table, p, seq, th, 200)
+        assert r["iters"] == it
+        assert bool(r["converged"]) == (it < 200)
+        assert np.max(np.abs(r["theta"] - th1)) < 1e-9
+        its.add(it)
+    assert len(its) > 1
+
+
+def test_server_budget(kcm, table):
+    """Device memory of the server's batches stays within the budget; a job that can never fit is
+    refused with KCM_E_NOMEM while the others complete, with results equal to the jobs alone."""
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=0)
+    small = jobs(3, seed0=77)
+    budget = 24 << 20  # 8 MB per batch plus a few small chains
+    with kcm.Server(p, budget, 8, 5) as s:
+        ids = [s.submit(seq, table, th, 10) for seq, th in small]
+        big = synth.sequence(2000, 5)
+        bid = s.submit(big, table, synth.theta_extended(2000), 10)
+        peak = 0
+        t0 = time.time()
+        while True:
+            wt, rn = s.tick()
+            peak = max(peak, s.device_bytes())
+            if wt == 0 and rn == 0:
+                break
+            assert time.time() - t0 < 60
+        assert peak <= budget
+        assert s.job(bid, with_theta=False)["error"] == kcm.KCM_E_NOMEM
+        for jid, (seq, th) in zip(ids, small):
+            r = s.job(jid)
+            assert r["error"] == 0 and r["iters"] == 10
+            it, dm, th1 = alone(kcm, table, p, seq, th, 10)
+            assert np.max(np.abs(r["theta"] - th1)) < 1e-9
