@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-iters", type=int, default=200)
     return ap.parse_args()
 
 
@@ -80,6 +82,54 @@ def batch_workload():
     seqs = [synth.sequence(m, synth.chain_seed(wl.seed, i)) for i, m in enumerate(wl.m)]
     theta = synth.theta_from_codes(np.load(os.path.join(GOLDEN, "start_batch512.npy")))
     return seqs, theta, wl
+
+
+def serve_pool():
+    """The pool of serving jobs (lengths log-uniform in 20-2000 residues) and their stored starts."""
+    from paper_1712_05012_b300 import synth
+
+    wl = synth.workload(5)
+    lens = json.load(open(os.path.join(GOLDEN, "starts.json")))["serve256"]["residues"]
+    codes = np.load(os.path.join(GOLDEN, "start_serve256.npy"))
+    seqs, thetas, off = [], [], 0
+    for i, m in enumerate(lens):
+        seqs.append(synth.sequence(m, synth.chain_seed(wl.seed, i)))
+        thetas.append(synth.theta_from_codes(codes[off:off + 2 * m]))
+        off += 2 * m
+    return seqs, thetas, wl
+
+
+def run_serving(kcm, table, params, rate, seconds, max_iters, budget, chunk, seed=0):
+    """Poisson arrivals at `rate` jobs/s for `seconds` (jobs drawn from the pool), each run until
+    converged or `max_iters`; returns latencies and throughput from the server's own clock."""
+    seqs, thetas, _ = serve_pool()
+    rng = np.random.default_rng(seed)
+    t_arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds * 3) + 16))
+    t_arr = t_arr[t_arr < seconds]
+    pick = rng.integers(0, len(seqs), size=len(t_arr))
+    ids = []
+    with kcm.Server(params, budget, 512, chunk) as s:
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            now = time.perf_counter() - t0
+            while k < len(t_arr) and t_arr[k] <= now:
+                ids.append(s.submit(seqs[pick[k]], table, thetas[pick[k]], max_iters))
+                k += 1
+            waiting, running = s.tick()
+            if k == len(t_arr) and waiting == 0 and running == 0:
+                break
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        info = [s.job(j, with_theta=False) for j in ids]
+    lat = np.array([x["t_done"] - x["t_submit"] for x in info])
+    queue = np.array([x["t_admit"] - x["t_submit"] for x in info])
+    atom_its = sum(x["natoms"] * x["iters"] for x in info)
+    return {"jobs": len(ids), "rate_per_s": rate, "arrival_seconds": seconds, "max_iters": max_iters,
+            "wall_s": wall, "chains_per_s": len(ids) / wall, "atom_iterations_per_s": atom_its / wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "p50_queue_s": float(np.percentile(queue, 50)), "converged": int(sum(x["converged"] for x in info)),
+            "errors": int(sum(x["error"] != 0 for x in info))}
 
 
 def dist_env():
@@ -328,6 +378,30 @@ def run_ours(args):
                      "steps": args.batch_steps, "pairs": bst["pairs"], "sasa_tests": bst["sasa_tests"],
                      "start": "every step from the stored compact starts (theta restored untimed)"}
 
+    # serving: Poisson arrivals into the continuous-batching server, next to the same jobs one at a time
+    serving = None
+    if args.serve_seconds > 0:
+        sp = synth.RunParams(precision=prec)
+        serving = run_serving(kcm, table, sp, 200.0, args.serve_seconds, args.serve_iters, 120 << 30, 25)
+        seqs_p, thetas_p, _ = serve_pool()
+        rng = np.random.default_rng(1)
+        one = []  # one job at a time, plain FP64 single-chain path, a sample of the pool
+        for i in rng.integers(0, len(seqs_p), size=6):
+            t0 = time.perf_counter()
+            with kcm.Chain(seqs_p[i], table, synth.RunParams(precision=synth.PRECISION_FP64)) as c1:
+                c1.set_theta(thetas_p[i])
+                try:
+                    it1, _ = c1.step(args.serve_iters)
+                except kcm.KcmError:  # the job failed (e.g. its chain collapsed): count what it ran
+                    it1 = int(c1.chain_state()[0][0])
+                one.append((time.perf_counter() - t0, c1.n * it1))
+        serving["one_at_a_time_fp64"] = {
+            "jobs": len(one), "mean_latency_s": float(np.mean([x[0] for x in one])),
+            "atom_iterations_per_s": float(sum(x[1] for x in one) / sum(x[0] for x in one))}
+        serving["note"] = (f"jobs drawn from 256 stored compact starts, lengths log-uniform 20-2000 residues; "
+                           f"capped at {args.serve_iters} iterations (5,000 in the full stream); 120 GB budget; "
+                           f"server clock")
+
     # the plain FP64 single-chain GPU path, measured the same way
     fp64_value = None
     if args.fp64_steps > 0 and prec == synth.PRECISION_MIXED:
@@ -389,7 +463,7 @@ def run_ours(args):
                            "replicas": ws, "l2": "flushed between timed steps (256 MiB write)",
                            "start": "every step from the stored compact start (theta restored untimed)"},
                 "roofline": roof, "rooflines": rooflines, "stage_ms": ms_stage, "fp64_value": fp64_value,
-                "vacuum_value": vacuum_value, "batch": batch,
+                "vacuum_value": vacuum_value, "batch": batch, "serving": serving,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,
                 "clocks": clk, "stats": {k: stats[k] for k in ("pairs", "sasa_tests", "sasa_neighbors",

@@ -183,9 +183,11 @@ int kcm_chain_offsets(kcm_handle h, int64_t* atom_off, int64_t* joint_off);
 int kcm_chain_energies(kcm_handle h, double* E);
 
 /* Loop state of every chain since the last kcm_step or kcm_step_async: iterations taken, whether it
- * has converged (1) or is still running (0), and the max |dtheta| of its last step. Arrays of
- * kcm_nchains entries, host memory, any may be NULL; waits for the handle's stream. */
-int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta);
+ * has stopped (1: converged, reached its cap or failed) or is still running (0), the max |dtheta| of
+ * its last step, and its status (KCM_OK, KCM_E_OVERFLOW or KCM_E_NONFINITE). In a batch a failing
+ * chain stops alone (the others go on; kcm_step still reports the error); a single chain stops the
+ * loop. Arrays of kcm_nchains entries, host memory, any may be NULL; waits for the handle's stream. */
+int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta, int32_t* errors);
 
 /* Cap on the iterations every chain may take in each later kcm_step / kcm_step_async call:
  * max_iters[c] for chain c (kcm_nchains entries, host memory; NULL removes every cap). A chain with

@@ -321,7 +321,8 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.atom_chain, nn)) || (rc = dalloc(h, &d.joint_chain, l)) || (rc = dalloc(h, &d.link_chain, L)) ||
         (rc = dalloc(h, &d.joint_off, hc.nchains + 1)) || (rc = dalloc(h, &d.ccap, hc.nchains)) ||
         (rc = dalloc(h, &d.cbox, 6 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.chain_done, hc.nchains)) ||
-        (rc = dalloc(h, &d.chain_iters, hc.nchains)) || (rc = dalloc(h, &d.chain_maxit, hc.nchains)) || (rc = dalloc(h, &d.chain_maxdt, hc.nchains)) ||
+        (rc = dalloc(h, &d.chain_iters, hc.nchains)) || (rc = dalloc(h, &d.chain_maxit, hc.nchains)) ||
+        (rc = dalloc(h, &d.chain_err, hc.nchains)) || (rc = dalloc(h, &d.chain_maxdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_maxtau, hc.nchains)) || (rc = dalloc(h, &d.chain_lastdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_E, 3 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.gseg, l)) ||
         (rc = dalloc(h, &d.jhead, l)) || (rc = dalloc(h, &d.lflag, L)) ||
@@ -435,17 +436,23 @@ int kcm_set_chain_max_iters(kcm_handle h, const int32_t* max_iters) {
 
 int64_t kcm_device_bytes(kcm_handle h) { return h ? static_cast<int64_t>(h->bytes) : -1; }
 
-int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta) {
+int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta, int32_t* errors) {
     if (check_handle(h)) return KCM_E_INVAL;
     const int C = h->d.nchains;
     cudaError_t e = cudaSuccess;
+    std::vector<int32_t> bits(errors ? C : 0);
+    if (errors) e = cudaMemcpyAsync(bits.data(), h->d.chain_err, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, h->stream);
     if (iters) e = cudaMemcpyAsync(iters, h->d.chain_iters, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && converged)
         e = cudaMemcpyAsync(converged, h->d.chain_done, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && max_dtheta)
         e = cudaMemcpyAsync(max_dtheta, h->d.chain_lastdt, sizeof(double) * C, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "chain state copy");
-    return sync(h);
+    int rc = sync(h);
+    if (rc) return rc;
+    for (int c = 0; errors && c < C; ++c)
+        errors[c] = (bits[c] & kcm::kErrNonfinite) ? KCM_E_NONFINITE : (bits[c] & kcm::kErrOverflow) ? KCM_E_OVERFLOW : KCM_OK;
+    return KCM_OK;
 }
 
 void kcm_destroy(kcm_handle h) {

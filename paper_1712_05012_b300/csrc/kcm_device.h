@@ -147,6 +147,7 @@ struct DevChain {
     int* chain_done = nullptr;     // converged (the chain takes no more steps) [nchains]
     int* chain_iters = nullptr;    // [nchains]
     int* chain_maxit = nullptr;    // iterations a chain may take per step call (<= 0: none) [nchains]
+    int* chain_err = nullptr;      // kErr* bits of a chain; in a batch a failed chain stops alone [nchains]
     unsigned long long* chain_maxdt = nullptr;   // bits of max |dtheta| of the running iteration
     unsigned long long* chain_maxtau = nullptr;  // bits of max |tau| of the running iteration
     double* chain_lastdt = nullptr;              // max |dtheta| of the chain's last step

@@ -478,7 +478,11 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
         GridInfo g;
         int ncl = 0;
         if (cch < d.nchains) {
-            bad = bad || !chain_grid(d, cch, &g);
+            if (!chain_grid(d, cch, &g)) {  // non-finite centres: the chain fails (alone, in a batch)
+                bad = true;
+                d.chain_err[cch] |= kErrNonfinite;
+                d.chain_done[cch] = 1;
+            }
             ncl = g.ncells;
             d.chain_E[3 * cch] = 0.0; d.chain_E[3 * cch + 1] = 0.0; d.chain_E[3 * cch + 2] = 0.0;
         }
@@ -501,7 +505,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) {
         atomicOr(&st->error, kErrNonfinite);
-        st->done = 1;
+        if (d.nchains == 1) st->done = 1;
     }
     if (threadIdx.x == 0) {
         st->ncells = cbase;

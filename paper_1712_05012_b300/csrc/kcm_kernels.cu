@@ -495,7 +495,10 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         nguard = __reduce_add_sync(0xffffffffu, nguard);
         if (lane == 0) {
             d.nbr_cnt[a] = ncount;
-            if (ncount > kMaxNbr) atomicOr(&d.status->error, kErrOverflow);
+            if (ncount > kMaxNbr) {
+                atomicOr(&d.status->error, kErrOverflow);
+                atomicOr(&d.chain_err[ca], kErrOverflow);
+            }
         }
         }
     }
@@ -836,6 +839,7 @@ __global__ void k_reset_loop(const DevChain d, int full) {
     }
     if (c < d.nchains) {
         d.chain_done[c] = d.chain_maxit[c] <= 0;  // a chain without iterations to take is done from the start
+        d.chain_err[c] = 0;
         d.chain_iters[c] = 0;
         d.chain_maxdt[c] = 0ULL;
         d.chain_maxtau[c] = 0ULL;

@@ -122,14 +122,14 @@ int launch_chunk(kcm_server* s, Batch* b) {
 // a finished chunk: account every chain, retire the jobs that are done, launch the next chunk
 int collect(kcm_server* s, Batch* b) {
     const size_t C = b->jobs.size();
-    std::vector<int32_t> it(C), cv(C);
+    std::vector<int32_t> it(C), cv(C), er(C);
     std::vector<double> dm(C);
     int32_t dummy = 0;
     double dmax = 0.0;
-    int rc = kcm_step_status(b->h, &dummy, &dmax);  // the chunk's status (errors)
-    const int step_rc = rc;
-    if (rc == KCM_OK || rc == KCM_E_NONFINITE || rc == KCM_E_OVERFLOW) rc = kcm_chain_state(b->h, it.data(), cv.data(), dm.data());
+    int rc = kcm_step_status(b->h, &dummy, &dmax);  // chain failures are read per chain below
     if (rc != KCM_OK && rc != KCM_E_NONFINITE && rc != KCM_E_OVERFLOW) return rc;
+    rc = kcm_chain_state(b->h, it.data(), cv.data(), dm.data(), er.data());
+    if (rc != KCM_OK) return rc;
     std::vector<double> theta;
     bool any_done = false;
     for (size_t c = 0; c < C; ++c) {
@@ -138,7 +138,7 @@ int collect(kcm_server* s, Batch* b) {
         j->iters += it[c];
         if (it[c] > 0) j->last_dtheta = dm[c];
         const bool conv = cv[c] && j->last_dtheta < s->prm.conv_tol && it[c] > 0;
-        if (step_rc != KCM_OK || conv || j->iters >= j->max_iters) any_done = true;
+        if (er[c] != KCM_OK || conv || j->iters >= j->max_iters) any_done = true;
     }
     if (any_done) {
         const int64_t l = b->joff.back();
@@ -150,11 +150,11 @@ int collect(kcm_server* s, Batch* b) {
     for (size_t c = 0; c < C; ++c) {
         Job* j = b->jobs[c];
         if (j->state != KCM_JOB_RUNNING) continue;
-        const bool conv = cv[c] && j->last_dtheta < s->prm.conv_tol && it[c] > 0;
-        if (step_rc != KCM_OK || conv || j->iters >= j->max_iters) {
+        const bool conv = cv[c] && j->last_dtheta < s->prm.conv_tol && it[c] > 0 && er[c] == KCM_OK;
+        if (er[c] != KCM_OK || conv || j->iters >= j->max_iters) {
             j->converged = conv;
             std::copy(theta.begin() + b->joff[c], theta.begin() + b->joff[c + 1], j->theta.begin());
-            retire(s, j, step_rc);
+            retire(s, j, er[c]);
         } else {
             ++running;
         }

@@ -197,14 +197,14 @@ __device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
     }
     if (threadIdx.x == 0) { s_run = 0; s_dm = 0ULL; }
     __syncthreads();
-    const bool failed = st->error != 0;
     int run = 0;
     unsigned long long dm = 0ULL;
     for (int c = threadIdx.x; c < d.nchains; c += blockDim.x) {
         const unsigned long long m = __ldcg(&d.chain_maxdt[c]);
         d.chain_maxdt[c] = 0ULL;
         d.chain_maxtau[c] = 0ULL;
-        if (failed || d.chain_done[c]) continue;
+        if (__ldcg(&d.chain_err[c])) d.chain_done[c] = 1;  // a failed chain stops; the others go on
+        if (d.chain_done[c]) continue;
         const double mc = __longlong_as_double((long long)m);
         d.chain_lastdt[c] = mc;
         const int it = d.chain_iters[c] + 1;
@@ -217,13 +217,9 @@ __device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
     if (dm) atomicMax(&s_dm, dm);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (failed) {
-            st->done = 1;  // a failed iteration leaves theta as the kernels found it at the first error
-        } else {
-            st->last_max_dtheta = __longlong_as_double((long long)s_dm);
-            st->iters += 1;
-            if (s_run == 0) st->done = 1;  // every chain converged
-        }
+        st->last_max_dtheta = __longlong_as_double((long long)s_dm);
+        st->iters += 1;
+        if (s_run == 0) st->done = 1;  // every chain converged, reached its cap or failed
         st->ticket = 0u;
     }
 }
@@ -259,9 +255,10 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
         const double t = to_double(tt);
         d.tau[jj] = t;
         bad = !isfinite(t);
+        if (bad) atomicOr(&d.chain_err[cj], kErrNonfinite);
         atau = (unsigned long long)__double_as_longlong(fabs(t));
-        if (d.chain_done[cj]) {
-            cj = -1;  // a converged chain takes no more steps
+        if (d.chain_done[cj] || d.chain_err[cj]) {
+            cj = -1;  // a converged or failed chain takes no more steps
         } else if (STEP && !bad) {
             const double dt = fmin(fmax(d.prm.kappa * t, -d.prm.dtheta_max), d.prm.dtheta_max);
             d.theta[jj] += dt;

@@ -129,7 +129,7 @@ def load():
             "kcm_nchains": (C.c_int32, [h]),
             "kcm_chain_offsets": (C.c_int, [h, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
             "kcm_chain_energies": (C.c_int, [h, _dp]),
-            "kcm_chain_state": (C.c_int, [h, _ip, _ip, _dp]),
+            "kcm_chain_state": (C.c_int, [h, _ip, _ip, _dp, _ip]),
             "kcm_set_chain_max_iters": (C.c_int, [h, _ip]),
             "kcm_device_bytes": (C.c_int64, [h]),
             "kcm_server_create": (C.c_int, [C.POINTER(Params), C.c_int64, C.c_int32, C.c_int32,
@@ -384,13 +384,15 @@ class Chain:
     def device_bytes(self) -> int:
         return int(load().kcm_device_bytes(self._h))
 
-    def chain_state(self):
-        """(iterations, converged, max |dtheta| of the last step) per chain since the last step call."""
+    def chain_state(self, with_errors=False):
+        """(iterations, stopped, max |dtheta| of the last step[, status]) per chain since the last step
+        call."""
         it = np.zeros(self.nchains, dtype=np.int32)
         cv = np.zeros(self.nchains, dtype=np.int32)
         dm = np.zeros(self.nchains)
-        _check(load().kcm_chain_state(self._h, _iptr(it), _iptr(cv), _dptr(dm)), self._h)
-        return it, cv.astype(bool), dm
+        er = np.zeros(self.nchains, dtype=np.int32)
+        _check(load().kcm_chain_state(self._h, _iptr(it), _iptr(cv), _dptr(dm), _iptr(er)), self._h)
+        return (it, cv.astype(bool), dm, er) if with_errors else (it, cv.astype(bool), dm)
 
 
 class Batch(Chain):

@@ -53,6 +53,19 @@ def main():
                             "sequence_seed": "chain_seed(workload seed, chain index)", "grow_seed": "the same",
                             "min_dist": 2.5, "max_retries": 100, "backtrack": 5, "atoms": natoms}
     print("batch512", len(wl.m), "chains", natoms, "atoms")
+    # a pool of serving jobs: lengths log-uniform in 20..2000 residues, each grown the same way
+    wl = synth.workload(5)
+    rng = np.random.default_rng(wl.seed)
+    lens = np.exp(rng.uniform(np.log(20), np.log(2000), size=256)).astype(int).tolist()
+    codes_all = []
+    for i, m in enumerate(lens):
+        seed = synth.chain_seed(wl.seed, i)
+        ch = O.OracleChain(synth.sequence(m, seed), table, synth.GEOMETRY)
+        codes_all.append(ch.grow_start(seed, min_dist=2.5, max_retries=100, backtrack=5))
+    np.save(os.path.join(HERE, "start_serve256.npy"), np.concatenate(codes_all))
+    manifest["serve256"] = {"workload": 5, "residues": lens, "sequence_seed": "chain_seed(workload seed, index)",
+                            "grow_seed": "the same", "min_dist": 2.5, "max_retries": 100, "backtrack": 5}
+    print("serve256", len(lens), "chains", sum(lens), "residues")
     with open(os.path.join(HERE, "starts.json"), "w") as f:
         json.dump(manifest, f, indent=1, sort_keys=True)
 

@@ -156,3 +156,27 @@ def test_batch512_mixed_vs_fp64_and_oracle(kcm, table):
         assert rel_inf(tau[synth.PRECISION_FP64][c], ref["tau"]) < 1e-10
         assert rel_inf(tau[synth.PRECISION_MIXED][c], ref["tau"]) < 1e-4
 
+
+def test_batch_chain_fails_alone(kcm, table):
+    """A chain whose solvation lists overflow (probe radius 9 A: far more than 128 neighbours) stops
+    with KCM_E_OVERFLOW; a 3-residue chain in the same batch (fewer than 128 atoms, it cannot
+    overflow) takes all its iterations and ends where it ends alone."""
+    big = synth.sequence(30, 8)
+    small = synth.sequence(3, 13)
+    th_big = synth.theta_from_codes(O.OracleChain(big, table, synth.GEOMETRY).grow_start(8))
+    th_small = synth.theta_uniform(3, 13)
+    p = synth.RunParams(precision=synth.PRECISION_FP64, r_probe=9.0)
+    with kcm.Batch([big, small], table, p) as b:
+        b.set_theta(np.concatenate([th_big, th_small]))
+        with pytest.raises(kcm.KcmError) as e:
+            b.step(4)
+        assert e.value.code == kcm.KCM_E_OVERFLOW
+        iters, stopped, dm, err = b.chain_state(with_errors=True)
+        th = b.split(b.get_theta(), per="joint")
+    assert err[0] == kcm.KCM_E_OVERFLOW and err[1] == kcm.KCM_OK
+    assert iters[1] == 4
+    with kcm.Chain(small, table, p) as ch:
+        ch.set_theta(th_small)
+        ch.step(4)
+        assert np.max(np.abs(th[1] - ch.get_theta())) < 1e-9
+
