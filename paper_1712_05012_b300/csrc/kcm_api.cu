@@ -300,7 +300,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.u0, 3 * l)) || (rc = dalloc(h, &d.step0, 3 * l)) || (rc = dalloc(h, &d.aprm64, nn)) ||
         (rc = dalloc(h, &d.aprm32, nn)) || (rc = dalloc(h, &d.G0, nn)) || (rc = dalloc(h, &d.qfx, nn)) ||
         (rc = dalloc(h, &d.exm, nn)) || (rc = dalloc(h, &d.m14m, nn)) || (rc = dalloc(h, &d.Q64, 3 * N)) ||
-        (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.theta, l)) || (rc = dalloc(h, &d.dtheta, l)) ||
+        (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.Q4, N)) || (rc = dalloc(h, &d.theta, l)) || (rc = dalloc(h, &d.dtheta, l)) ||
         (rc = dalloc(h, &d.tau, l)) || (rc = dalloc(h, &d.G, 12 * (size_t)l)) ||
         (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.u0df, 3 * l)) ||
         (rc = dalloc(h, &d.step0df, 3 * l)) || (rc = dalloc(h, &d.r0df, 3 * nn)) || (rc = dalloc(h, &d.rdf, 3 * nn)) ||
@@ -348,6 +348,8 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
     std::vector<double> Q64(3 * (size_t)N);
     kcm::sample_points(N, Q64.data());
     std::vector<float> Q32(Q64.begin(), Q64.end());
+    std::vector<float4> Q4(N);
+    for (int k = 0; k < N; ++k) Q4[k] = make_float4(Q32[3 * k], Q32[3 * k + 1], Q32[3 * k + 2], 0.0f);
     std::vector<double> ident = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
     if (prm->precision == KCM_MIXED) ident = pack_df(ident);  // base-link poses in the mixed kernels' format
     std::vector<int> atom_chain(n), joint_chain(l), link_chain(L);
@@ -368,7 +370,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = upload(h, d.qfx, qfx.data(), nn)) || (rc = upload(h, d.gflag, gflag.data(), nn)) || (rc = upload(h, d.G0f, G0f.data(), nn)) ||
         (rc = upload(h, d.exm, reinterpret_cast<const unsigned long long*>(hc.ex_mask.data()), nn)) ||
         (rc = upload(h, d.m14m, reinterpret_cast<const unsigned long long*>(hc.m14_mask.data()), nn)) ||
-        (rc = upload(h, d.Q64, Q64.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q32, Q32.data(), 3 * (size_t)N)) ||
+        (rc = upload(h, d.Q64, Q64.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q32, Q32.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q4, Q4.data(), N)) ||
         (rc = upload(h, d.atom_chain, atom_chain.data(), nn)) || (rc = upload(h, d.joint_chain, joint_chain.data(), l)) ||
         (rc = upload(h, d.link_chain, link_chain.data(), L)) || (rc = upload(h, d.joint_off, hc.joint_off.data(), hc.nchains + 1)) ||
         (rc = upload(h, d.ccap, ccap.data(), hc.nchains)) || (rc = upload(h, d.jhead, jhead.data(), l)) ||

@@ -102,6 +102,7 @@ struct DevChain {
     unsigned long long* m14m = nullptr;  // [n]
     double* Q64 = nullptr;         // [N*3]
     float* Q32 = nullptr;          // [N*3]
+    float4* Q4 = nullptr;          // the same as (x, y, z, 0) [N]
 
     // per-iteration data
     double* theta = nullptr;       // [l]

@@ -718,9 +718,10 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 for (int p = 0; p < kPtsPerLane; ++p) {
                     const int k = kb + lane + 32 * p;
                     const bool v = k < d.N;
-                    qx[p] = v ? d.Q32[3 * k] : 0.0f;
-                    qy[p] = v ? d.Q32[3 * k + 1] : 0.0f;
-                    qz[p] = v ? d.Q32[3 * k + 2] : 0.0f;
+                    const float4 qk = v ? d.Q4[k] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    qx[p] = qk.x;
+                    qy[p] = qk.y;
+                    qz[p] = qk.z;
                     valid |= v ? (1u << p) : 0u;
                     nc[p] = 0.0f;
                     mn[p] = INFINITY;
@@ -754,7 +755,8 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 // re-scan, one point at a time; lane t takes neighbours t, t + 32, ... (at most 4)
                 for (int e = 0; e < nres; ++e) {
                     const int k = kb + s_near[w][e];
-                    const float Qx = d.Q32[3 * k], Qy = d.Q32[3 * k + 1], Qz = d.Q32[3 * k + 2];
+                    const float4 qk = d.Q4[k];
+                    const float Qx = qk.x, Qy = qk.y, Qz = qk.z;
                     unsigned inb = 0, nrb = 0;
                     for (int r = 0; 32 * r < cnt; ++r) {
                         const int j = 32 * r + lane;
@@ -794,27 +796,32 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 }
                 __syncwarp();
             }
-            ncov = warp_sum(ncov);
-            nguard = warp_sum(nguard);
-            ntest = warp_sum(ntest);
+            // counts of the warp by 32-bit reductions (each below 2^31: at most 4096 points x 128
+            // neighbours x 3 axes); atom i's force is minus the quantum times its net exchanges
+            ncov = (int)__reduce_add_sync(0xffffffffu, (unsigned)ncov);
+            nguard = (int)__reduce_add_sync(0xffffffffu, (unsigned)nguard);
+            const unsigned nt = __reduce_add_sync(0xffffffffu, (unsigned)ntest);
             __syncwarp();
             const long long qa = d.qfx[a];
-            long long f0 = 0, f1 = 0, f2 = 0;
+            int s0 = 0, s1 = 0, s2 = 0;
             for (int j = lane; j < cnt; j += 32) {
                 const int b = s_idx[w][j];
                 const int c0 = s_cnt[w][3 * j], c1 = s_cnt[w][3 * j + 1], c2 = s_cnt[w][3 * j + 2];
-                if (c0) { atomicAdd((unsigned long long*)&d.Fcav[3 * b], (unsigned long long)(qa * c0)); f0 -= qa * c0; }
-                if (c1) { atomicAdd((unsigned long long*)&d.Fcav[3 * b + 1], (unsigned long long)(qa * c1)); f1 -= qa * c1; }
-                if (c2) { atomicAdd((unsigned long long*)&d.Fcav[3 * b + 2], (unsigned long long)(qa * c2)); f2 -= qa * c2; }
+                if (c0) atomicAdd((unsigned long long*)&d.Fcav[3 * b], (unsigned long long)(qa * c0));
+                if (c1) atomicAdd((unsigned long long*)&d.Fcav[3 * b + 1], (unsigned long long)(qa * c1));
+                if (c2) atomicAdd((unsigned long long*)&d.Fcav[3 * b + 2], (unsigned long long)(qa * c2));
+                s0 += c0; s1 += c1; s2 += c2;
             }
-            f0 = warp_sum(f0); f1 = warp_sum(f1); f2 = warp_sum(f2);
+            s0 = __reduce_add_sync(0xffffffffu, s0);
+            s1 = __reduce_add_sync(0xffffffffu, s1);
+            s2 = __reduce_add_sync(0xffffffffu, s2);
             if (lane == 0) {
-                if (f0) atomicAdd((unsigned long long*)&d.Fcav[3 * a], (unsigned long long)f0);
-                if (f1) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 1], (unsigned long long)f1);
-                if (f2) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 2], (unsigned long long)f2);
+                if (s0) atomicAdd((unsigned long long*)&d.Fcav[3 * a], (unsigned long long)(-qa * s0));
+                if (s1) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 1], (unsigned long long)(-qa * s1));
+                if (s2) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 2], (unsigned long long)(-qa * s2));
                 d.covered[a] = ncov;
                 if (nguard) atomicAdd(&d.status->guard, (unsigned long long)nguard);
-                atomicAdd(&d.status->sasa_tests, ntest);
+                atomicAdd(&d.status->sasa_tests, (unsigned long long)nt);
             }
         }
     }
