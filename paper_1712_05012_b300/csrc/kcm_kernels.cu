@@ -271,14 +271,32 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
         // the non-empty cells among the 27 neighbours, compacted in stencil order: first slot, offset
         // of their candidates in the concatenation, and (mixed) the shift (c_j - c_i) s
+        // A neighbour cell whose box lies farther from the home atom than the largest interaction
+        // range (less a margin over the FP32 cell assignment) holds no candidate and is skipped:
+        // that drops about a quarter of the candidates (corner and edge cells).
         int beg = 0, len = 0;
         const int dxc = lane % 3 - 1, dyc = (lane / 3) % 3 - 1, dzc = lane / 9 - 1;
         if (lane < 27) {
             int ncx = cx + dxc, ncy = cy + dyc, ncz = cz + dzc;
             if (ncx >= 0 && ncx < g.nx && ncy >= 0 && ncy < g.ny && ncz >= 0 && ncz < g.nz) {
-                int nc = g.cbase + (ncz * g.ny + ncy) * g.nx + ncx;
-                beg = d.cell_start[nc];
-                len = d.cell_start[nc + 1] - beg;
+                R hx, hy, hz, es, reach2;
+                if constexpr (MIXED) {
+                    const float4 hp = d.spos32[sl];  // offset from the home cell's corner
+                    hx = hp.x; hy = hp.y; hz = hp.z; es = g.sf; reach2 = d.f_rall2;
+                } else {
+                    const dbl4 hp = d.spos64[sl];
+                    hx = hp.x - (g.ox + cx * g.s); hy = hp.y - (g.oy + cy * g.s); hz = hp.z - (g.oz + cz * g.s);
+                    es = g.s; reach2 = d.rmax * d.rmax;
+                }
+                const R mg = (R)0.02;
+                const R gx = fmax(dxc > 0 ? es - hx - mg : (dxc < 0 ? hx - mg : (R)0), (R)0);
+                const R gy = fmax(dyc > 0 ? es - hy - mg : (dyc < 0 ? hy - mg : (R)0), (R)0);
+                const R gz = fmax(dzc > 0 ? es - hz - mg : (dzc < 0 ? hz - mg : (R)0), (R)0);
+                if (gx * gx + gy * gy + gz * gz <= reach2) {
+                    int nc = g.cbase + (ncz * g.ny + ncy) * g.nx + ncx;
+                    beg = d.cell_start[nc];
+                    len = d.cell_start[nc + 1] - beg;
+                }
             }
         }
         int incl = len;
