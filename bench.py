@@ -132,6 +132,25 @@ def run_serving(kcm, table, params, rate, seconds, max_iters, budget, chunk, see
             "errors": int(sum(x["error"] != 0 for x in info))}
 
 
+def max_over_ranks(t_local: float, ws: int, device: str = "cuda") -> float:
+    """The largest of every rank's timed seconds (all_reduce MAX over the default process group;
+    the tensor lives on `device`: CUDA for NCCL, CPU for gloo)."""
+    if ws <= 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, units_per_rank: int, steps: int, t_max: float) -> float:
+    """Units processed by all ranks (every rank runs its own replica of the workload) per second of
+    the slowest rank."""
+    return ws * units_per_rank * steps / t_max
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -293,13 +312,8 @@ def run_ours(args):
             stages[k] += v
     clk = clocks.stop()
     stats = ch.stats()
-    t_sum = sum(totals) / 1e3
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_sum], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_sum = float(t.item())
-    value = ws * n * args.steps / t_sum
+    t_sum = max_over_ranks(sum(totals) / 1e3, ws)
+    value = whole_job_rate(ws, n, args.steps, t_sum)
     ms_stage = {k: v / args.steps for k, v in stages.items()}
 
     # rooflines of every stage (work counted at the last timed iteration); the dominant one is the
