@@ -124,6 +124,7 @@ struct DevChain {
     int* scan_part = nullptr;      // block sums of the cell scan [scan_blocks]
     int* sorted = nullptr;         // slot -> atom [n]
     int* slot_cell = nullptr;      // slot -> cell [n]
+    ulonglong2* smask = nullptr;   // slot -> bond-class masks (exm, m14m) [n]
     dbl4* spos64 = nullptr;     // sorted centres + charge [n]
     float4* spos32 = nullptr;      // sorted cell-relative offsets + charge [n]
     float4* sprm32 = nullptr;      // sorted sqrt(eps), R, Roff [n]

@@ -216,6 +216,7 @@ __global__ void k_bin_place(const DevChain d) {
     int sl = d.cell_start[key] + d.rank[a];
     d.sorted[sl] = a;
     d.slot_cell[sl] = key;
+    d.smask[sl] = make_ulonglong2(d.exm[a], d.m14m[a]);  // bond classes in slot order (no dependent load later)
     double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
     if (MIXED) {
         const int lk = key - g.cbase;
@@ -357,6 +358,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                 const R d2 = v.w;
                 R qj, sej, Rj;
                 b = d.sorted[ts];
+                const ulonglong2 mk = d.smask[ts];  // j's bond-class masks, loaded beside its index
                 if constexpr (MIXED) {
                     float4 q = d.sprm32[ts];
                     qj = q.x; sej = q.y; Rj = q.z; Roj = q.w;
@@ -371,8 +373,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                 int lo = min(a, b), off = max(a, b) - lo;
                 bool excl = false, is14 = false;
                 if (off <= kMaskWindow) {
-                    unsigned long long em = (lo == a) ? exa : d.exm[b];
-                    unsigned long long mm = (lo == a) ? m14a : d.m14m[b];
+                    unsigned long long em = (lo == a) ? exa : mk.x;
+                    unsigned long long mm = (lo == a) ? m14a : mk.y;
                     excl = (em >> off) & 1ULL;
                     is14 = (mm >> off) & 1ULL;
                 }
