@@ -112,7 +112,11 @@ typedef struct {
  * apart (1-2 and 1-3 pairs get 0, all others 1; eq. 03_8/03_9); r_probe: solvent probe radius
  * (the offset sphere is R + r_probe, Sec. 3.4); delta_r: finite-difference displacement of
  * eq. finitediff; coulomb_k: 332.0636 kcal A mol^-1 e^-2; conv_tol: the step loop stops once
- * max_k |dtheta_k| < conv_tol; cell_size: binning cell edge (0 = the smallest legal edge);
+ * max_k |dtheta_k| < conv_tol; cell_size: requested edge of the binning cells of Sec. 3.2 (0 =
+ * the smallest edge that covers the largest interaction range rmax with the 27 cells around an
+ * atom's cell; an edge below rmax switches the pair search to the 125 cells two cells out, and
+ * is raised to rmax / 2 plus a rounding margin if smaller; a grid that would exceed its cell cap
+ * is coarsened);
  * n_sample: sample points per offset sphere N; solvation: 0/1; precision: KCM_FP64/KCM_MIXED;
  * step_mode: KCM_STEP_CLAMP/KCM_STEP_NORMALIZED. */
 typedef struct {
@@ -300,6 +304,19 @@ int kcm_step_async(kcm_handle h, int32_t n_iters);
 int kcm_step_status(kcm_handle h, int32_t* iters_done, double* max_dtheta);
 
 int kcm_get_stats(kcm_handle h, kcm_stats* st);
+
+/* Cell-edge autotuner. For each candidate edge (A; meaning as kcm_params.cell_size, so 0 is the
+ * smallest 27-cell edge) evaluate the chain (forces and torques at the current theta, no step:
+ * theta is not changed) once to warm up and then `reps` times, timed with CUDA events on the
+ * handle's stream; keep the fastest edge for all later calls. The pair set, and so the result,
+ * does not depend on the edge: only the rounding of the FP32 cell offsets and the order of
+ * floating-point sums do. times_ms[n_candidates] (may be NULL) receives the mean time of one
+ * evaluation per candidate; *chosen (may be NULL) the winning candidate. Synchronises. Errors:
+ * KCM_E_INVAL (n_candidates not in [1, KCM_AUTOTUNE_MAX], reps not in [1, 1000], a negative
+ * or non-finite candidate), the errors of an evaluation (the previous edge is then restored). */
+#define KCM_AUTOTUNE_MAX 64
+int kcm_autotune_cell(kcm_handle h, const double* candidates, int32_t n_candidates, int32_t reps,
+                      double* times_ms, double* chosen);
 
 /* Stages of one iteration, in launch order, as timed by kcm_step_timed. */
 #define KCM_STAGE_KINEMATICS 0 /* transform scan and atom centres (eq. kin_04, r1, r2) */

@@ -174,6 +174,69 @@ std::vector<double> pack_df(const std::vector<double>& v) {
     return out;
 }
 
+void dfree(kcm_ctx* h, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
+    h->bytes -= bytes;
+}
+
+void drop_graphs(kcm_ctx* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph_timed) cudaGraphExecDestroy(h->graph_timed);
+    h->graph = nullptr;
+    h->graph_timed = nullptr;
+}
+
+// Applies a requested cell edge: the stencil (one cell on either side when the edge reaches the
+// largest interaction range, two when it is smaller; the device raises the edge to the smallest
+// legal one for that stencil), each chain's cell cap (a chain's grid is coarsened to fit it; half
+// the edge needs eight times the cells), the cell arrays (grown when the caps outgrow them), and
+// drops the captured graphs, which hold the old launch parameters.
+int set_cell_size(kcm_ctx* h, double cell_size) {
+    kcm::DevChain& d = h->d;
+    const kcm::HostChain& hc = h->hc;
+    const int stencil = (cell_size > 0.0 && cell_size < d.rmax) ? 2 : 1;
+    std::vector<int> ccap(hc.nchains);
+    long long tot = 0;
+    for (int ch = 0; ch < hc.nchains; ++ch) {
+        const long long nc = hc.atom_off[ch + 1] - hc.atom_off[ch];
+        long long cap = hc.nchains == 1 ? std::max(8 * nc, 65536LL) : std::max(8 * nc, 4096LL);
+        if (stencil == 2) cap *= 8;
+        if (cap > (1LL << 30)) cap = 1LL << 30;
+        ccap[ch] = static_cast<int>(cap);
+        tot += cap;
+    }
+    if (tot > (1LL << 30)) return set_err(h, KCM_E_INVAL, "the batch needs more than 2^30 cells");
+    if (h->stream) {  // nothing of the old configuration in flight
+        int rc = sync(h);
+        if (rc) return rc;
+    }
+    drop_graphs(h);
+    if (tot > d.cell_alloc) {  // grow the cell arrays (counts start at zero; the scan keeps them so)
+        dfree(h, d.cell_count, sizeof(int) * std::max<size_t>(d.cell_alloc, 1));
+        dfree(h, d.cell_start, sizeof(int) * (d.cell_alloc + 1));
+        dfree(h, d.scan_part, sizeof(int) * std::max<size_t>((d.cell_alloc + kcm::kScanCells - 1) / kcm::kScanCells, 1));
+        d.cell_count = d.cell_start = d.scan_part = nullptr;
+        d.cell_alloc = 0;
+        const size_t nb = (static_cast<size_t>(tot) + kcm::kScanCells - 1) / kcm::kScanCells;
+        int rc;
+        if ((rc = dalloc(h, &d.cell_count, static_cast<size_t>(tot))) || (rc = dalloc(h, &d.cell_start, static_cast<size_t>(tot) + 1)) ||
+            (rc = dalloc(h, &d.scan_part, nb)))
+            return rc;
+        cudaError_t e = cudaMemsetAsync(d.cell_count, 0, sizeof(int) * static_cast<size_t>(tot), h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+        d.cell_alloc = tot;
+    }
+    d.cell_cap = static_cast<int>(tot);
+    d.scan_blocks = (d.cell_cap + kcm::kScanCells - 1) / kcm::kScanCells;
+    d.scan_fused = d.cell_cap <= kcm::kScanFusedMaxCells;
+    d.stencil = stencil;
+    d.prm.cell_size = cell_size;
+    int rc = upload(h, d.ccap, ccap.data(), hc.nchains);
+    return rc ? rc : sync(h);
+}
+
 }  // namespace
 
 extern "C" {
@@ -261,20 +324,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
     d.ntiles = (d.l + fkq * d.fk_j - 1) / (fkq * d.fk_j);
     d.ltiles = (d.L + 31) / 32;
     d.nchains = hc.nchains;
-    std::vector<int> ccap(hc.nchains);
-    {
-        long long tot = 0;
-        for (int ch = 0; ch < hc.nchains; ++ch) {  // each chain's grid is coarsened to fit its own cap
-            const int nc = hc.atom_off[ch + 1] - hc.atom_off[ch];
-            ccap[ch] = hc.nchains == 1 ? std::max(8 * nc, 65536) : std::max(8 * nc, 4096);
-            tot += ccap[ch];
-        }
-        if (tot > (1LL << 30)) return bail(set_err(h, KCM_E_INVAL, "the batch needs more than 2^30 cells"));
-        d.cell_cap = static_cast<int>(tot);
-    }
     d.pair_blocks = (d.n + kcm::kPairWarps - 1) / kcm::kPairWarps;
-    d.scan_blocks = (d.cell_cap + kcm::kScanCells - 1) / kcm::kScanCells;
-    d.scan_fused = d.cell_cap <= kcm::kScanFusedMaxCells;
     d.sasa_blocks = (d.n + kcm::kSasaWarps - 1) / kcm::kSasaWarps;
     d.rcut2 = prm->cutoff * prm->cutoff;
     double rv = prm->vdw_cutoff > 0.0 ? prm->vdw_cutoff : prm->cutoff;
@@ -306,8 +356,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.step0df, 3 * l)) || (rc = dalloc(h, &d.r0df, 3 * nn)) || (rc = dalloc(h, &d.rdf, 3 * nn)) ||
         (rc = dalloc(h, &d.ucurdf, 3 * l)) || (rc = dalloc(h, &d.pcurdf, 3 * l)) || (rc = dalloc(h, &d.G0f, nn)) ||
         (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||
-        (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.cell_count, d.cell_cap)) ||
-        (rc = dalloc(h, &d.cell_start, d.cell_cap + 1)) || (rc = dalloc(h, &d.rank, nn)) || (rc = dalloc(h, &d.scan_part, d.scan_blocks)) ||
+        (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.rank, nn)) ||
         (rc = dalloc(h, &d.sorted, nn)) || (rc = dalloc(h, &d.slot_cell, nn)) || (rc = dalloc(h, &d.smask, nn)) || (rc = dalloc(h, &d.spos64, nn)) ||
         (rc = dalloc(h, &d.spos32, nn)) || (rc = dalloc(h, &d.sprm32, nn)) || (rc = dalloc(h, &d.sprm64, nn)) ||
         (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fpx, 3 * nn)) || (rc = dalloc(h, &d.Fov, 3 * nn)) ||
@@ -373,12 +422,12 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = upload(h, d.Q64, Q64.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q32, Q32.data(), 3 * (size_t)N)) || (rc = upload(h, d.Q4, Q4.data(), N)) ||
         (rc = upload(h, d.atom_chain, atom_chain.data(), nn)) || (rc = upload(h, d.joint_chain, joint_chain.data(), l)) ||
         (rc = upload(h, d.link_chain, link_chain.data(), L)) || (rc = upload(h, d.joint_off, hc.joint_off.data(), hc.nchains + 1)) ||
-        (rc = upload(h, d.ccap, ccap.data(), hc.nchains)) || (rc = upload(h, d.jhead, jhead.data(), l)) ||
+        (rc = upload(h, d.jhead, jhead.data(), l)) ||
         (rc = upload(h, d.lflag, lflag.data(), L)) || (rc = upload(h, d.u0df, u0df.data(), 3 * l)) ||
         (rc = upload(h, d.step0df, step0df.data(), 3 * l)) || (rc = upload(h, d.r0df, r0df.data(), 3 * nn)))
         return bail(rc);
+    if ((rc = set_cell_size(h, prm->cell_size))) return bail(rc);  // cell caps and arrays
     e = cudaMemsetAsync(d.theta, 0, sizeof(double) * l, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.cell_count, 0, sizeof(int) * d.cell_cap, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.Fcav, 0, sizeof(long long) * 3 * nn, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.covered, 0, sizeof(int) * nn, h->stream);
     if (e != cudaSuccess) { cuda_fail(h, e, "memset"); return bail(KCM_E_CUDA); }
@@ -460,8 +509,7 @@ int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* ma
 void kcm_destroy(kcm_handle h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->graph) cudaGraphExecDestroy(h->graph);
-    if (h->graph_timed) cudaGraphExecDestroy(h->graph_timed);
+    drop_graphs(h);
     for (cudaEvent_t ev : h->ev)
         if (ev) cudaEventDestroy(ev);
     for (void* p : h->allocs) cudaFree(p);
@@ -617,6 +665,68 @@ int kcm_step(kcm_handle h, int32_t n_iters, int32_t* iters_done, double* max_dth
     int rc = kcm_step_async(h, n_iters);
     if (rc) return rc;
     return kcm_step_status(h, iters_done, max_dtheta);
+}
+
+int kcm_autotune_cell(kcm_handle h, const double* candidates, int32_t n_candidates, int32_t reps, double* times_ms,
+                      double* chosen) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!candidates || n_candidates < 1 || n_candidates > KCM_AUTOTUNE_MAX)
+        return set_err(h, KCM_E_INVAL, "need 1 to KCM_AUTOTUNE_MAX candidate cell edges");
+    if (reps < 1 || reps > 1000) return set_err(h, KCM_E_INVAL, "reps must be in [1, 1000]");
+    for (int i = 0; i < n_candidates; ++i)
+        if (!(candidates[i] >= 0.0) || !std::isfinite(candidates[i]))
+            return set_err(h, KCM_E_INVAL, "a candidate cell edge is negative or not finite");
+    const double old = h->d.prm.cell_size;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(h, e, "event create");
+    }
+    std::vector<double> t(n_candidates, 0.0);
+    int rc = KCM_OK;
+    for (int i = 0; i < n_candidates && rc == KCM_OK; ++i) {
+        // one evaluation at the current theta (no step) per launch of a graph captured for this edge
+        rc = set_cell_size(h, candidates[i]);
+        if (rc) break;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            kcm::launch_reset_loop(h->d, h->stream);
+            enqueue_evaluation(h);
+            e = cudaStreamEndCapture(h->stream, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->stream);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(ge, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (ge) cudaGraphExecDestroy(ge);
+        if (e != cudaSuccess) { rc = cuda_fail(h, e, "autotune run"); break; }
+        kcm::Status st;
+        rc = read_status(h, &st);
+        if (rc == KCM_OK) rc = status_code(h, st);
+        t[i] = static_cast<double>(ms) / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        set_cell_size(h, old);
+        return rc;
+    }
+    int best = 0;
+    for (int i = 1; i < n_candidates; ++i)
+        if (t[i] < t[best]) best = i;
+    if (times_ms)
+        for (int i = 0; i < n_candidates; ++i) times_ms[i] = t[i];
+    if (chosen) *chosen = candidates[best];
+    return set_cell_size(h, candidates[best]);
 }
 
 int kcm_get_stats(kcm_handle h, kcm_stats* out) {

@@ -114,10 +114,11 @@ __device__ __forceinline__ bool covers64(double qx, double qy, double qz, double
 
 
 // Grid of chain c's cell list from its bounding box d.cbox[6c..6c+5] (order-preserving keys):
-// cube cells of edge s >= every interaction range (plus a margin that absorbs FP32 cell
-// assignment), s a multiple of 2^-10 A so that it is exact in float; coarsened when the box would
-// need more cells than the chain's cap. Leaves cbase to the caller and clears the box. Returns
-// false for a non-finite box.
+// cube cells of edge s with d.stencil * s >= every interaction range (plus a margin that absorbs
+// FP32 cell assignment, so that two atoms within range are at most d.stencil cells apart on every
+// axis), and s >= the requested edge; s a multiple of 2^-10 A so that it is exact in float;
+// coarsened when the box would need more cells than the chain's cap. Leaves cbase to the caller and
+// clears the box. Returns false for a non-finite box.
 __device__ __forceinline__ bool chain_grid(const DevChain& d, int c, GridInfo* out) {
     double lo[3], hi[3];
     for (int i = 0; i < 3; ++i) {
@@ -131,7 +132,7 @@ __device__ __forceinline__ bool chain_grid(const DevChain& d, int c, GridInfo* o
     if (!finite)
         for (int i = 0; i < 3; ++i) { lo[i] = 0.0; hi[i] = 0.0; }
     const double ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
-    double s = fmax(fma(1e-6, fmax(ext[0], fmax(ext[1], ext[2])), d.s_base), d.prm.cell_size);
+    double s = fmax(fma(1e-6, fmax(ext[0], fmax(ext[1], ext[2])), d.s_base) / d.stencil, d.prm.cell_size);
     s = ceil(s * 1024.0) * (1.0 / 1024.0);
     const long long cap = d.ccap[c];
     for (;;) {

@@ -71,15 +71,18 @@ struct DevChain {
     int fk_j = 1;        // joints per quad (four-lane transform slot) in the transform scan
     int ntiles = 0;      // transform-scan blocks of 64 * fk_j joints
     int ltiles = 0;      // suffix-sum tiles of 32 links
-    int cell_cap = 0;
+    int cell_cap = 0;     // cells of all chains' caps
+    long long cell_alloc = 0;  // cells the cell arrays hold
     int pair_blocks = 0, sasa_blocks = 0, scan_blocks = 0;
     int scan_fused = 0;  // cell scan by the last block of the count kernel (cell_cap <= kScanFusedMaxCells)
+    int stencil = 1;     // cells searched on either side of the home cell: 1 (edge >= largest range) or 2 (>= half of it)
     kcm_params prm{};
     // derived constants
     double rcut2 = 0, rvdw2 = 0;  // squared pair cutoffs
     double rmax = 0;              // largest interaction range (pair cutoffs, solvation neighbour range)
     double roff_max = 0;          // largest offset-sphere radius
-    double s_base = 0;            // cell edge before its extent-dependent margin: rmax (1 + 1e-5) + 0.01 A
+    double s_base = 0;            // cell edge before its extent-dependent margin: rmax (1 + 1e-5) + 0.01 A;
+                                  // with the two-cell stencil the edge may be half of it
     // the same constants in float for the mixed kernels (no FP64 instruction per warp)
     float f_K = 0, f_w14e = 0, f_w14v = 0, f_rc2 = 0, f_rv2 = 0, f_rall2 = 0, f_dr = 0, f_invN = 0;
 

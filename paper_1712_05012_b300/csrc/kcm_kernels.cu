@@ -5,7 +5,7 @@
 //      App. B; atom centres r = M_link(r^0)
 //   A2 binning: bounding box, uniform grid (Sec. 3.2), counting sort by cell with warp-aggregated
 //      atomics, cells ordered by atom index for determinism
-//   A3-A5 pair forces over the 27-cell neighbourhood (eq. 02_2, 03_2, 03_8, 03_9) and the
+//   A3-A5 pair forces over the 27- or 125-cell neighbourhood (eq. 02_2, 03_2, 03_8, 03_9) and the
 //      solvation neighbour lists A'_i (Sec. 3.2 "neighbourhood matrix")
 //   A6 surface enumeration, Algorithm 1 (Sec. 3.4), one warp per atom
 //   A7-A8 link wrenches (eq. KCM_01/02) and the suffix sum of Sec. 3.5, tau_k = J_k^T P^agg_k
@@ -225,7 +225,7 @@ __global__ void k_bin_place(const DevChain d) {
         float oy = (float)(y - (g.oy + cy * g.s));
         float oz = (float)(z - (g.oz + cz * g.s));
         float4 p = d.aprm32[a];
-        d.spos32[sl] = make_float4(ox, oy, oz, p.x);
+        d.spos32[sl] = make_float4(ox, oy, oz, (float)cx);  // w: the cell's x index (exact), for the pair shifts
         d.sprm32[sl] = p;
     } else {
         dbl4 p = d.aprm64[a];
@@ -235,22 +235,27 @@ __global__ void k_bin_place(const DevChain d) {
 }
 
 // ================================================================ A3-A5: pair forces + lists
-// One warp per home atom i (sorted slot). Lane t < 27 reads neighbour cell t of the home cell;
-// the candidates of the 27 cells are then taken in strides of 32 over their concatenation, so
-// every lane has the same trip count. Each ordered pair (i, j) is evaluated by i's warp; the pair
-// term is computed symmetrically, so the term j's warp gets is exactly its negative. Mixed mode
-// sums the FP32 terms in fixed point (units of 2^-23, see fx_add): the sum is exact and
-// order-free, and the forces of a pair cancel exactly, so no net force or moment builds up over
-// the chain. Terms of 2^22 kcal/mol/A or more (near-overlapping atoms) go to a float side sum. The
-// per-atom results stay integers here; the thread-per-atom consumers convert them to FP64 (a
-// warp-per-atom kernel would spend a whole FP64 warp instruction on each atom's lane 0).
-template <bool MIXED>
+// One warp per home atom i (sorted slot). The neighbourhood is the (2 KR + 1)^3 cells around the home
+// cell (KR = 1 for cells at least as wide as the largest interaction range, KR = 2 for cells down to
+// half of it). Cells adjacent in x are adjacent in slot order, so the stencil is walked as
+// (2 KR + 1)^2 x-rows, lane t taking row t: each row is one slot range, trimmed at both ends to the
+// cells that lie within reach of the home atom. The candidates of the rows are then taken in strides
+// of 32 over their concatenation, so every lane has the same trip count. Each ordered pair (i, j) is
+// evaluated by i's warp; the pair term is computed symmetrically, so the term j's warp gets is
+// exactly its negative. Mixed mode sums the FP32 terms in fixed point (units of 2^-23, see fx_add):
+// the sum is exact and order-free, and the forces of a pair cancel exactly, so no net force or
+// moment builds up over the chain. Terms of 2^22 kcal/mol/A or more (near-overlapping atoms) go to a
+// float side sum. The per-atom results stay integers here; the thread-per-atom consumers convert
+// them to FP64 (a warp-per-atom kernel would spend a whole FP64 warp instruction on each atom's lane 0).
+template <bool MIXED, int KR>
 __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
     typedef typename std::conditional<MIXED, float, double>::type R;
     typedef typename std::conditional<MIXED, float4, dbl4>::type QV;
+    constexpr int kW = 2 * KR + 1;  // cells per row
+    static_assert(kW * kW <= 32, "one lane per row");
     __shared__ int s_beg[kPairWarps][32];
     __shared__ int s_off[kPairWarps][32];
-    __shared__ float4 s_sh[kPairWarps][27];
+    __shared__ float2 s_sh[kPairWarps][32];
     __shared__ QV s_qv[kPairWarps][kPairQueue];   // queued pairs: r_i - r_j, d^2
     __shared__ int s_qts[kPairWarps][kPairQueue];  // queued pairs: sorted slot of j
     __shared__ R sE[2][kPairWarps];
@@ -270,16 +275,16 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         const GridInfo g = d.grid[ca];  // the home atom's chain: its candidates are that chain's atoms
         const int cell = d.slot_cell[sl] - g.cbase;
         const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
-        // the non-empty cells among the 27 neighbours, compacted in stencil order: first slot, offset
-        // of their candidates in the concatenation, and (mixed) the shift (c_j - c_i) s
-        // A neighbour cell whose box lies farther from the home atom than the largest interaction
-        // range (less a margin over the FP32 cell assignment) holds no candidate and is skipped:
-        // that drops about a quarter of the candidates (corner and edge cells).
+        // The non-empty rows, compacted in stencil order: first slot, offset of their candidates in
+        // the concatenation, and (mixed) the row's shift ((cy_j - cy_i) s, (cz_j - cz_i) s). A cell
+        // whose box lies farther from the home atom than the largest interaction range (less a margin
+        // over the FP32 cell assignment) holds no candidate: whole rows, and the cells at either end
+        // of a row, are dropped that way.
         int beg = 0, len = 0;
-        const int dxc = lane % 3 - 1, dyc = (lane / 3) % 3 - 1, dzc = lane / 9 - 1;
-        if (lane < 27) {
-            int ncx = cx + dxc, ncy = cy + dyc, ncz = cz + dzc;
-            if (ncx >= 0 && ncx < g.nx && ncy >= 0 && ncy < g.ny && ncz >= 0 && ncz < g.nz) {
+        const int dyc = lane % kW - KR, dzc = lane / kW - KR;
+        if (lane < kW * kW) {
+            const int ncy = cy + dyc, ncz = cz + dzc;
+            if (ncy >= 0 && ncy < g.ny && ncz >= 0 && ncz < g.nz) {
                 R hx, hy, hz, es, reach2;
                 if constexpr (MIXED) {
                     const float4 hp = d.spos32[sl];  // offset from the home cell's corner
@@ -290,13 +295,24 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                     es = g.s; reach2 = d.rmax * d.rmax;
                 }
                 const R mg = (R)0.02;
-                const R gx = fmax(dxc > 0 ? es - hx - mg : (dxc < 0 ? hx - mg : (R)0), (R)0);
-                const R gy = fmax(dyc > 0 ? es - hy - mg : (dyc < 0 ? hy - mg : (R)0), (R)0);
-                const R gz = fmax(dzc > 0 ? es - hz - mg : (dzc < 0 ? hz - mg : (R)0), (R)0);
-                if (gx * gx + gy * gy + gz * gz <= reach2) {
-                    int nc = g.cbase + (ncz * g.ny + ncy) * g.nx + ncx;
-                    beg = d.cell_start[nc];
-                    len = d.cell_start[nc + 1] - beg;
+                // gap between the home atom and the cell at offset k along one axis (0 inside)
+                auto gap = [&](int k, R h) -> R {
+                    return k > 0 ? fmax((R)k * es - h - mg, (R)0) : (k < 0 ? fmax(h - (R)(k + 1) * es - mg, (R)0) : (R)0);
+                };
+                const R gy = gap(dyc, hy), gz = gap(dzc, hz);
+                const R rem = reach2 - (gy * gy + gz * gz);
+                if (rem >= (R)0) {
+                    // the gap grows with |dx|: the cells within reach are one run around the home cell
+                    int xlo = max(cx - KR, 0), xhi = min(cx + KR, g.nx - 1);
+#pragma unroll
+                    for (int k = 1; k <= KR; ++k) {
+                        const R gl = gap(-k, hx), gr = gap(k, hx);
+                        if (gl * gl > rem) xlo = max(xlo, cx - k + 1);
+                        if (gr * gr > rem) xhi = min(xhi, cx + k - 1);
+                    }
+                    const int rb = g.cbase + (ncz * g.ny + ncy) * g.nx;
+                    beg = d.cell_start[rb + xlo];
+                    len = d.cell_start[rb + xhi + 1] - beg;
                 }
             }
         }
@@ -312,7 +328,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             const int cslot = __popc(nem & ((1u << lane) - 1u));
             s_beg[w][cslot] = beg;
             s_off[w][cslot] = incl - len;
-            s_sh[w][cslot] = make_float4((float)dxc * g.sf, (float)dyc * g.sf, (float)dzc * g.sf, 0.0f);
+            s_sh[w][cslot] = make_float2((float)dyc * g.sf, (float)dzc * g.sf);
         }
         __syncwarp();
         R K, w14e, w14v, rc2, rv2, rall2, gp, dr, pad;
@@ -326,9 +342,10 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         const bool solv = d.prm.solvation != 0;
         const R sf = (R)g.sf;
         R px, py, pz, qi, sei, Ri, Roi;
+        float fcx = 0.0f;  // mixed: the home cell's x index
         if constexpr (MIXED) {
             float4 p = d.spos32[sl], q = d.sprm32[sl];
-            px = p.x; py = p.y; pz = p.z; qi = p.w; sei = q.y; Ri = q.z; Roi = q.w;
+            px = p.x; py = p.y; pz = p.z; fcx = p.w; qi = q.x; sei = q.y; Ri = q.z; Roi = q.w;
         } else {
             dbl4 p = d.spos64[sl], q = d.sprm64[sl];
             px = p.x; py = p.y; pz = p.z; qi = p.w; sei = q.y; Ri = q.z; Roi = q.w;
@@ -459,9 +476,9 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                     R ddx, ddy, ddz;
                     if constexpr (MIXED) {
                         const float4 p = d.spos32[ts];
-                        const float4 sh = s_sh[w][t];
-                        // r_i - r_j = (o_i - o_j) - (c_j - c_i) s
-                        ddx = (px - p.x) - sh.x; ddy = (py - p.y) - sh.y; ddz = (pz - p.z) - sh.z;
+                        const float2 sh = s_sh[w][t];
+                        // r_i - r_j = (o_i - o_j) - (c_j - c_i) s; (cx_j - cx_i) s is exact
+                        ddx = (px - p.x) - (p.w - fcx) * sf; ddy = (py - p.y) - sh.x; ddz = (pz - p.z) - sh.y;
                     } else {
                         dbl4 p = d.spos64[ts];
                         ddx = __dsub_rn(px, p.x); ddy = __dsub_rn(py, p.y); ddz = __dsub_rn(pz, p.z);
@@ -676,15 +693,17 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
 // / (2 Roff_i). A displacement can change a point's state only where the two squared distances
 // straddle Roff_j^2, i.e. within |m_kj| <= (2 dr Roff_j + 3 dr^2) / (2 Roff_i) of the cap boundary.
 //
-// Step 1 keeps, per point, min_j |m_kj| and the number of neighbours with m_kj > band (counted on the
-// FMA pipe as saturate((m - band) 2^100), which is exactly 0 or 1). A point whose minimum is outside
-// the band takes no part in step 2 and is covered iff that count is >= 1; a point inside the band
-// that still has two such neighbours has C >= 2 and takes no part in step 2 either. Only the few
-// remaining points are re-scanned, one at a time with the neighbours spread over the lanes: exact
-// C, the critical neighbour, FP64 re-decisions of guard-band tests (covers64, as in the FP64
-// kernel), and step 2 on the near-boundary neighbours. The exchanges are exactly Algorithm 1's: an
-// exposed point gains coverage only from a near neighbour, and a critically overlapped point loses
-// it only if its critical neighbour is near.
+// Step 1 keeps, per point, only M_k = max_j m_kj (three FFMA and one FMNMX per test). The band is
+// wider than the FP32 error of m (the guard gd), so:
+//  * M_k > band: some neighbour covers the point robustly. It is covered, and it takes no part in
+//    step 2: with C >= 2 no single displacement uncovers it, and with C = 1 the critical neighbour
+//    is the robust one, which no displacement by dr moves off the point;
+//  * M_k <= -band: every neighbour misses it robustly, even displaced: exposed, no exchange;
+//  * otherwise the point is re-scanned, one at a time with the neighbours spread over the lanes:
+//    exact C, the critical neighbour, FP64 re-decisions of guard-band tests (covers64, as in the
+//    FP64 kernel), and step 2 on the near-boundary neighbours.
+// The exchanges are exactly Algorithm 1's: an exposed point gains coverage only from a near
+// neighbour, and a critically overlapped point loses it only if its critical neighbour is near.
 constexpr int kPtsPerLane = 8;                  // sample points each lane holds in registers
 constexpr int kBatch = 32 * kPtsPerLane;         // points per batch (256)
 
@@ -732,7 +751,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 return covers64(qx, qy, qz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
             };
             for (int kb = 0; kb < d.N; kb += kBatch) {
-                float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane], nc[kPtsPerLane], mn[kPtsPerLane];
+                float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane], mx[kPtsPerLane];
                 unsigned valid = 0;
 #pragma unroll
                 for (int p = 0; p < kPtsPerLane; ++p) {
@@ -743,19 +762,16 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                     qy[p] = qk.y;
                     qz[p] = qk.z;
                     valid |= v ? (1u << p) : 0u;
-                    nc[p] = 0.0f;
-                    mn[p] = INFINITY;
+                    mx[p] = -INFINITY;
                 }
-                // step 1: min |m| and the count of m > band of each point over all neighbours
-                const float bandx = -band * 0x1p100f;
+                // step 1: the largest m of each point over all neighbours
 #pragma unroll 2
                 for (int j = 0; j < cnt; ++j) {
                     const float4 o = s_o[w][j];
 #pragma unroll
                     for (int p = 0; p < kPtsPerLane; ++p) {
                         const float m = fmaf(qz[p], o.z, fmaf(qy[p], o.y, fmaf(qx[p], o.x, -o.w)));
-                        nc[p] += __saturatef(fmaf(m, 0x1p100f, bandx));
-                        mn[p] = fminf(mn[p], fabsf(m));
+                        mx[p] = fmaxf(mx[p], m);
                     }
                 }
                 ntest += (unsigned long long)__popc(valid) * cnt;
@@ -765,8 +781,8 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
 #pragma unroll
                 for (int p = 0; p < kPtsPerLane; ++p) {
                     const bool v = (valid >> p) & 1u;
-                    const bool res = v && mn[p] <= band && nc[p] < 2.0f;
-                    if (v && !res) ncov += nc[p] >= 1.0f;
+                    const bool res = v && mx[p] > -band && mx[p] <= band;
+                    if (v && mx[p] > band) ++ncov;
                     const unsigned bm = __ballot_sync(0xffffffffu, res);
                     if (res) s_near[w][nres + __popc(bm & lt)] = (unsigned short)(lane + 32 * p);
                     nres += __popc(bm);
@@ -907,10 +923,14 @@ void launch_binning(DevChain& d, cudaStream_t s) {
 }
 
 void launch_pairs(DevChain& d, cudaStream_t s) {
-    if (d.prm.precision == KCM_MIXED)
-        k_pair<true><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
-    else
-        k_pair<false><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
+    const bool mixed = d.prm.precision == KCM_MIXED;
+    if (d.stencil == 2) {
+        if (mixed) k_pair<true, 2><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
+        else k_pair<false, 2><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
+    } else {
+        if (mixed) k_pair<true, 1><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
+        else k_pair<false, 1><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
+    }
 }
 
 void launch_forces(DevChain& d, cudaStream_t s) {

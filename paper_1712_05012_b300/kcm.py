@@ -73,8 +73,12 @@ EXPORTS = [
     "kcm_topology_natoms", "kcm_strerror", "kcm_last_error", "kcm_step_timed", "kcm_torques_noalloc",
     "kcm_create_batch", "kcm_nchains", "kcm_chain_offsets", "kcm_chain_energies", "kcm_chain_state",
     "kcm_set_chain_max_iters", "kcm_device_bytes", "kcm_server_create", "kcm_server_destroy", "kcm_server_submit",
-    "kcm_server_tick", "kcm_server_poll", "kcm_server_job", "kcm_server_device_bytes",
+    "kcm_server_tick", "kcm_server_poll", "kcm_server_job", "kcm_server_device_bytes", "kcm_autotune_cell",
 ]
+AUTOTUNE_MAX = 64
+# candidate cell edges of the autotuner (A): 0 is the smallest 27-cell edge; edges below the largest
+# interaction range use the 125-cell stencil and are raised to the smallest legal edge for it
+CELL_CANDIDATES = (0.0, 12.0, 9.0, 8.0, 7.0, 6.0, 5.0)
 JOB_WAITING, JOB_RUNNING, JOB_DONE = 0, 1, 2
 NOALLOC_MAX_LINKS = 32768
 NUM_STAGES = 5
@@ -114,6 +118,7 @@ def load():
             "kcm_step_async": (C.c_int, [h, C.c_int32]),
             "kcm_step_status": (C.c_int, [h, _ip, _dp]),
             "kcm_get_stats": (C.c_int, [h, C.POINTER(Stats)]),
+            "kcm_autotune_cell": (C.c_int, [h, _dp, C.c_int32, C.c_int32, _dp, _dp]),
             "kcm_stream": (C.c_void_p, [h]),
             "kcm_sample_points": (C.c_int, [C.c_int32, _dp]),
             "kcm_build_zp": (C.c_int, [C.POINTER(Topology), _dp, _ip, C.c_int64]),
@@ -361,6 +366,14 @@ class Chain:
         tot = C.c_float()
         _check(load().kcm_step_timed(self._h, st, NUM_STAGES, C.byref(tot)), self._h)
         return float(tot.value), dict(zip(STAGES, [float(x) for x in st]))
+
+    def autotune_cell(self, candidates=CELL_CANDIDATES, reps: int = 3):
+        """Time an evaluation at each candidate cell edge and keep the fastest: (chosen, times_ms)."""
+        cand = np.ascontiguousarray(candidates, dtype=np.float64)
+        t = np.zeros(len(cand))
+        ch = np.zeros(1)
+        _check(load().kcm_autotune_cell(self._h, _dptr(cand), len(cand), int(reps), _dptr(t), _dptr(ch)), self._h)
+        return float(ch[0]), t
 
     def stats(self) -> dict:
         s = Stats()
