@@ -91,13 +91,21 @@ __device__ __forceinline__ int warp_max(int v) {
 // so the pieces of the (i, j) and (j, i) terms are exact negatives.
 constexpr float kMagic23 = 12582912.0f;  // 1.5 * 2^23
 constexpr int kMagic23Bits = 0x4B400000;
-__device__ __forceinline__ void fx_add(float v, int& hi, int& lo) {
+__device__ __forceinline__ void fx_pieces(float v, int& n, int& f) {
     const float t = v + kMagic23;
-    const float f = v - (t - kMagic23);
-    const float u = fmaf(f, 8388608.0f, kMagic23);
-    hi += __float_as_int(t) - kMagic23Bits;
-    lo += __float_as_int(u) - kMagic23Bits;
+    const float fr = v - (t - kMagic23);
+    const float u = fmaf(fr, 8388608.0f, kMagic23);
+    n = __float_as_int(t) - kMagic23Bits;
+    f = __float_as_int(u) - kMagic23Bits;
 }
+__device__ __forceinline__ void fx_add(float v, int& hi, int& lo) {
+    int n, f;
+    fx_pieces(v, n, f);
+    hi += n;
+    lo += f;
+}
+// the whole term n 2^23 + f in units of 2^-23
+__device__ __forceinline__ long long fx_units(int n, int f) { return (long long)n * 8388608LL + f; }
 
 // The FP64 overlap test of Algorithm 1: || (r_a + Roff_a q_k) - r_b - dr e_s ||^2 <= Roff_b^2,
 // written with explicit roundings so that the FP64 kernel and the FP32 guard-band recheck take

@@ -140,6 +140,11 @@ struct DevChain {
     int* nbr = nullptr;            // [n*kMaxNbr]
     float4* nbr_off = nullptr;     // r_j - r_i and Roff_j^2 [n*kMaxNbr]
     int* covered = nullptr;        // [n]
+    // per-atom results that the wrench kernel sums per chain and per launch (the pair and solvation
+    // kernels then need no atomics on shared totals)
+    double* epair = nullptr;       // Coulomb and LJ energy of the atom's pairs [n*2] (mixed: a float pair per atom)
+    int2* pstat = nullptr;         // pair kernel: pairs counted, guard-band re-decisions [n]
+    int2* sstat = nullptr;         // Algorithm 1: overlap tests, guard-band re-decisions [n]
     // batches: chain of each atom, joint and link; joint offsets; per-chain cell caps, bounding
     // boxes (order-preserving keys: min x, y, z then max x, y, z), loop state and energies
     int nchains = 1;

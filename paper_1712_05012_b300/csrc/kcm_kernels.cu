@@ -219,6 +219,10 @@ __global__ void k_bin_place(const DevChain d) {
     d.smask[sl] = make_ulonglong2(d.exm[a], d.m14m[a]);  // bond classes in slot order (no dependent load later)
     double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
     if (MIXED) {
+        // the pair kernel adds each pair's share to both atoms: zero the sums and the list counters
+        d.Fpx[3 * a] = 0; d.Fpx[3 * a + 1] = 0; d.Fpx[3 * a + 2] = 0;
+        d.Fov[3 * a] = 0.0f; d.Fov[3 * a + 1] = 0.0f; d.Fov[3 * a + 2] = 0.0f;
+        d.nbr_cnt[a] = 0;
         const int lk = key - g.cbase;
         int cx = lk % g.nx, cy = (lk / g.nx) % g.ny, cz = lk / (g.nx * g.ny);
         float ox = (float)(x - (g.ox + cx * g.s));
@@ -237,31 +241,37 @@ __global__ void k_bin_place(const DevChain d) {
 // ================================================================ A3-A5: pair forces + lists
 // One warp per home atom i (sorted slot). The neighbourhood is the (2 KR + 1)^3 cells around the home
 // cell (KR = 1 for cells at least as wide as the largest interaction range, KR = 2 for cells down to
-// half of it). Cells adjacent in x are adjacent in slot order, so the stencil is walked as
-// (2 KR + 1)^2 x-rows, lane t taking row t: each row is one slot range, trimmed at both ends to the
-// cells that lie within reach of the home atom. The candidates of the rows are then taken in strides
-// of 32 over their concatenation, so every lane has the same trip count. Each ordered pair (i, j) is
-// evaluated by i's warp; the pair term is computed symmetrically, so the term j's warp gets is
-// exactly its negative. Mixed mode sums the FP32 terms in fixed point (units of 2^-23, see fx_add):
-// the sum is exact and order-free, and the forces of a pair cancel exactly, so no net force or
-// moment builds up over the chain. Terms of 2^22 kcal/mol/A or more (near-overlapping atoms) go to a
-// float side sum. The per-atom results stay integers here; the thread-per-atom consumers convert
-// them to FP64 (a warp-per-atom kernel would spend a whole FP64 warp instruction on each atom's lane 0).
+// half of it). Cells adjacent in x are adjacent in slot order, so the stencil is walked as x-rows,
+// lane t taking row t: each row is one slot range, trimmed at both ends to the cells that lie within
+// reach of the home atom. The candidates of the rows are then taken in strides of 32 over their
+// concatenation, so every lane has the same trip count.
+//
+// FP64 mode walks the whole stencil and evaluates every ordered pair (i, j) in i's warp, so each
+// atom's force is one warp's sum in a fixed order. Mixed mode evaluates each unordered pair once
+// (Newton's third law): the home row from the atom after i up to +KR cells, the rows (dy > 0, dz = 0)
+// and the rows with dz > 0, i.e. half the stencil. Its FP32 terms are summed in fixed point (units of
+// 2^-23, see fx_add): the pair term is computed symmetrically and its fixed-point pieces are rounded
+// symmetrically, so i keeps the pieces and j receives their exact negative by one 64-bit integer
+// atomic add per component. The sums are exact and order-free, hence bitwise what the full-stencil
+// evaluation gives, and the forces of a pair cancel exactly, so no net force or moment builds up over
+// the chain. Terms of 2^22 kcal/mol/A or more (near-overlapping atoms) go to float side sums. The
+// solvation neighbour lists take both directions of each pair, at slots drawn by atomic counters;
+// Algorithm 1's mixed kernel does not depend on the order of a list. The per-atom results stay
+// integers here; the thread-per-atom consumers convert them to FP64 (a warp-per-atom kernel would
+// spend a whole FP64 warp instruction on each atom's lane 0).
 template <bool MIXED, int KR>
-__global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
+__global__ void __launch_bounds__(kPairWarps * 32, 6) k_pair(const DevChain d) {
     typedef typename std::conditional<MIXED, float, double>::type R;
     typedef typename std::conditional<MIXED, float4, dbl4>::type QV;
     constexpr int kW = 2 * KR + 1;  // cells per row
-    static_assert(kW * kW <= 32, "one lane per row");
+    constexpr bool HALF = MIXED;    // half stencil, each unordered pair once
+    constexpr int kRows = HALF ? 1 + KR + KR * kW : kW * kW;
+    static_assert(kRows <= 32, "one lane per row");
     __shared__ int s_beg[kPairWarps][32];
     __shared__ int s_off[kPairWarps][32];
     __shared__ float2 s_sh[kPairWarps][32];
     __shared__ QV s_qv[kPairWarps][kPairQueue];   // queued pairs: r_i - r_j, d^2
     __shared__ int s_qts[kPairWarps][kPairQueue];  // queued pairs: sorted slot of j
-    __shared__ R sE[2][kPairWarps];
-    __shared__ unsigned long long sC[3][kPairWarps];
-    __shared__ int sM[kPairWarps];
-    __shared__ int sCh[kPairWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sl = blockIdx.x * kPairWarps + w;
     R Eel = 0, Evdw = 0;
@@ -281,8 +291,17 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         // over the FP32 cell assignment) holds no candidate: whole rows, and the cells at either end
         // of a row, are dropped that way.
         int beg = 0, len = 0;
-        const int dyc = lane % kW - KR, dzc = lane / kW - KR;
-        if (lane < kW * kW) {
+        // row of this lane: (dy, dz) and the lowest x offset it takes
+        int dyc, dzc, dxlo = -KR;
+        if constexpr (HALF) {
+            if (lane == 0) { dyc = 0; dzc = 0; dxlo = 0; }                  // home row: i's cell onwards
+            else if (lane <= KR) { dyc = lane; dzc = 0; }                    // dy > 0, dz = 0
+            else { const int r = lane - 1 - KR; dyc = r % kW - KR; dzc = 1 + r / kW; }  // dz > 0
+        } else {
+            dyc = lane % kW - KR;
+            dzc = lane / kW - KR;
+        }
+        if (lane < kRows) {
             const int ncy = cy + dyc, ncz = cz + dzc;
             if (ncy >= 0 && ncy < g.ny && ncz >= 0 && ncz < g.nz) {
                 R hx, hy, hz, es, reach2;
@@ -303,7 +322,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                 const R rem = reach2 - (gy * gy + gz * gz);
                 if (rem >= (R)0) {
                     // the gap grows with |dx|: the cells within reach are one run around the home cell
-                    int xlo = max(cx - KR, 0), xhi = min(cx + KR, g.nx - 1);
+                    int xlo = max(cx + dxlo, 0), xhi = min(cx + KR, g.nx - 1);
 #pragma unroll
                     for (int k = 1; k <= KR; ++k) {
                         const R gl = gap(-k, hx), gr = gap(k, hx);
@@ -311,7 +330,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                         if (gr * gr > rem) xhi = min(xhi, cx + k - 1);
                     }
                     const int rb = g.cbase + (ncz * g.ny + ncy) * g.nx;
-                    beg = d.cell_start[rb + xlo];
+                    // the home row of the half stencil starts after i itself
+                    beg = (HALF && lane == 0) ? sl + 1 : d.cell_start[rb + xlo];
                     len = d.cell_start[rb + xhi + 1] - beg;
                 }
             }
@@ -363,19 +383,20 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         // with every lane busy instead of the ~30 % of candidates that are in range.
         int qhead = 0, qtail = 0, nround = 0;
         bool folded = false;  // uniform
+        bool ovf = false;     // half stencil: a list slot beyond kMaxNbr
         auto phase_b = [&](int nvalid) {
             const int e = (qhead + lane) & (kPairQueue - 1);
+            const bool act = lane < nvalid;
             bool isn = false;
-            int b = -1;
-            R ddx = 0, ddy = 0, ddz = 0, Roj = 0;
-            if (lane < nvalid) {
-                const int ts = s_qts[w][e];
+            int b = -1, ts = 0;
+            R ddx = 0, ddy = 0, ddz = 0, d2 = 0, qj = 0, sej = 0, Rj = 0, Roj = 0;
+            ulonglong2 mk = make_ulonglong2(0ULL, 0ULL);
+            if (act) {
+                ts = s_qts[w][e];
                 const QV v = s_qv[w][e];
-                ddx = v.x; ddy = v.y; ddz = v.z;
-                const R d2 = v.w;
-                R qj, sej, Rj;
+                ddx = v.x; ddy = v.y; ddz = v.z; d2 = v.w;
                 b = d.sorted[ts];
-                const ulonglong2 mk = d.smask[ts];  // j's bond-class masks, loaded beside its index
+                mk = d.smask[ts];  // j's bond-class masks, loaded beside its index
                 if constexpr (MIXED) {
                     float4 q = d.sprm32[ts];
                     qj = q.x; sej = q.y; Rj = q.z; Roj = q.w;
@@ -387,6 +408,18 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                     R lim = Roi + Roj + dr + pad;
                     isn = d2 <= lim * lim;
                 }
+            }
+            const unsigned bm = __ballot_sync(0xffffffffu, isn);
+            // half stencil: list slots of both directions, requested before the pair term so that the
+            // atomics' latency overlaps it
+            int base_slot = 0, rslot = 0;
+            if constexpr (HALF) {
+                if (bm) {  // uniform
+                    if (lane == 0) base_slot = atomicAdd(&d.nbr_cnt[a], __popc(bm));
+                    if (isn) rslot = atomicAdd(&d.nbr_cnt[b], 1);
+                }
+            }
+            if (act) {
                 int lo = min(a, b), off = max(a, b) - lo;
                 bool excl = false, is14 = false;
                 if (off <= kMaskWindow) {
@@ -426,16 +459,26 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                         coef += (R)12 * eij * (t12 - t6) * inv2;
                         e_vd = eij * (t12 - (R)2 * t6);
                     }
-                    const bool count_e = a < b;
+                    const bool count_e = HALF || a < b;  // each unordered pair's energy once
                     if (count_e && (we != (R)0 || wv != (R)0)) ++npairs;
                     if constexpr (MIXED) {
                         const float fx1 = coef * ddx, fy1 = coef * ddy, fz1 = coef * ddz;
+                        unsigned long long* Fj = reinterpret_cast<unsigned long long*>(&d.Fpx[3 * b]);
                         if (fabsf(fx1) < kPairFxMax && fabsf(fy1) < kPairFxMax && fabsf(fz1) < kPairFxMax) {
-                            fx_add(fx1, hix, lox);
-                            fx_add(fy1, hiy, loy);
-                            fx_add(fz1, hiz, loz);
-                        } else {  // clash-sized (or non-finite) term: plain float sum
+                            int n0, f0, n1, f1, n2, f2;
+                            fx_pieces(fx1, n0, f0);
+                            fx_pieces(fy1, n1, f1);
+                            fx_pieces(fz1, n2, f2);
+                            hix += n0; lox += f0; hiy += n1; loy += f1; hiz += n2; loz += f2;
+                            // j's term is exactly the negative (two's complement adds)
+                            atomicAdd(Fj, (unsigned long long)(-fx_units(n0, f0)));
+                            atomicAdd(Fj + 1, (unsigned long long)(-fx_units(n1, f1)));
+                            atomicAdd(Fj + 2, (unsigned long long)(-fx_units(n2, f2)));
+                        } else {  // clash-sized (or non-finite) term: plain float sums
                             ovx += fx1; ovy += fy1; ovz += fz1;
+                            atomicAdd(&d.Fov[3 * b], -fx1);
+                            atomicAdd(&d.Fov[3 * b + 1], -fy1);
+                            atomicAdd(&d.Fov[3 * b + 2], -fz1);
                         }
                         if (count_e) { ove += e_el; ovv += e_vd; }
                     } else {
@@ -444,15 +487,33 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
                     }
                 }
             }
-            const unsigned bm = __ballot_sync(0xffffffffu, isn);
-            if (isn) {
-                const int slot = ncount + __popc(bm & lt);
-                if (slot < kMaxNbr) {
-                    d.nbr[(size_t)a * kMaxNbr + slot] = b;
-                    if (MIXED) d.nbr_off[(size_t)a * kMaxNbr + slot] = make_float4(-(float)ddx, -(float)ddy, -(float)ddz, (float)(Roj * Roj));
+            if constexpr (HALF) {
+                if (bm) {  // uniform
+                    base_slot = __shfl_sync(0xffffffffu, base_slot, 0);
+                    if (isn) {
+                        const int slot = base_slot + __popc(bm & lt);
+                        if (slot < kMaxNbr) {  // j in i's list: r_j - r_i, Roff_j^2
+                            d.nbr[(size_t)a * kMaxNbr + slot] = b;
+                            d.nbr_off[(size_t)a * kMaxNbr + slot] = make_float4(-(float)ddx, -(float)ddy, -(float)ddz, (float)(Roj * Roj));
+                        }
+                        if (rslot < kMaxNbr) {  // i in j's list: r_i - r_j, Roff_i^2
+                            d.nbr[(size_t)b * kMaxNbr + rslot] = a;
+                            d.nbr_off[(size_t)b * kMaxNbr + rslot] = make_float4((float)ddx, (float)ddy, (float)ddz, (float)(Roi * Roi));
+                        }
+                        ovf |= slot >= kMaxNbr || rslot >= kMaxNbr;
+                    }
+                    ncount += 2 * __popc(bm);
                 }
+            } else {
+                if (isn) {
+                    const int slot = ncount + __popc(bm & lt);
+                    if (slot < kMaxNbr) {
+                        d.nbr[(size_t)a * kMaxNbr + slot] = b;
+                        if (MIXED) d.nbr_off[(size_t)a * kMaxNbr + slot] = make_float4(-(float)ddx, -(float)ddy, -(float)ddz, (float)(Roj * Roj));
+                    }
+                }
+                ncount += __popc(bm);
             }
-            ncount += __popc(bm);
             qhead += 32;
             if constexpr (MIXED) {
                 // at most one term per lane and round: kPairFoldRounds terms of |piece| <= 2^22 fit in int32
@@ -513,13 +574,17 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
             }
             Hx += warp_sum_i32(hix); Hy += warp_sum_i32(hiy); Hz += warp_sum_i32(hiz);
             Lx += warp_sum_i32(lox); Ly += warp_sum_i32(loy); Lz += warp_sum_i32(loz);
-            ovx = warp_sum(ovx); ovy = warp_sum(ovy); ovz = warp_sum(ovz);
             ove = warp_sum(ove); ovv = warp_sum(ovv);
-            if (lane == 0) {  // converted to FP64 by the thread-per-atom consumers
-                d.Fpx[3 * a] = Hx * 8388608LL + Lx;
-                d.Fpx[3 * a + 1] = Hy * 8388608LL + Ly;
-                d.Fpx[3 * a + 2] = Hz * 8388608LL + Lz;
-                d.Fov[3 * a] = ovx; d.Fov[3 * a + 1] = ovy; d.Fov[3 * a + 2] = ovz;
+            if (lane == 0) {  // added to the partners' shares; converted to FP64 by the thread-per-atom consumers
+                unsigned long long* Fi = reinterpret_cast<unsigned long long*>(&d.Fpx[3 * a]);
+                atomicAdd(Fi, (unsigned long long)(Hx * 8388608LL + Lx));
+                atomicAdd(Fi + 1, (unsigned long long)(Hy * 8388608LL + Ly));
+                atomicAdd(Fi + 2, (unsigned long long)(Hz * 8388608LL + Lz));
+            }
+            if (ovx != 0.0f || ovy != 0.0f || ovz != 0.0f) {  // clash-sized terms only
+                atomicAdd(&d.Fov[3 * a], ovx);
+                atomicAdd(&d.Fov[3 * a + 1], ovy);
+                atomicAdd(&d.Fov[3 * a + 2], ovz);
             }
             Eel = ove;
             Evdw = ovv;
@@ -530,40 +595,26 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair(const DevChain d) {
         }
         npairs = __reduce_add_sync(0xffffffffu, npairs);
         nguard = __reduce_add_sync(0xffffffffu, nguard);
+        if constexpr (HALF) {
+            ovf = __any_sync(0xffffffffu, ovf);
+        } else {
+            ovf = ncount > kMaxNbr;
+        }
         if (lane == 0) {
-            d.nbr_cnt[a] = ncount;
-            if (ncount > kMaxNbr) {
+            if (!HALF) d.nbr_cnt[a] = ncount;
+            if (ovf) {
                 atomicOr(&d.status->error, kErrOverflow);
                 atomicOr(&d.chain_err[ca], kErrOverflow);
             }
         }
         }
-    }
-    if (lane == 0) { sE[0][w] = Eel; sE[1][w] = Evdw; sC[0][w] = npairs; sC[1][w] = nguard; sC[2][w] = (unsigned long long)ncount; sM[w] = ncount; sCh[w] = ca; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        R e0 = 0, e1 = 0;
-        unsigned long long c0 = 0, c1 = 0, c2 = 0;
-        int m = 0;
-        bool one = true;  // all home atoms of the block in one chain: one atomic per energy
-        for (int k2 = 0; k2 < kPairWarps; ++k2) {
-            e0 += sE[0][k2]; e1 += sE[1][k2]; c0 += sC[0][k2]; c1 += sC[1][k2]; c2 += sC[2][k2]; m = max(m, sM[k2]);
-            one = one && (sCh[k2] == sCh[0] || sCh[k2] < 0);
+        // the atom's pair energies and counters (zero for a converged chain), summed per chain by the
+        // wrench kernel: no atomics on shared totals here
+        if (lane == 0) {
+            if constexpr (MIXED) reinterpret_cast<float2*>(d.epair)[a] = make_float2(Eel, Evdw);
+            else reinterpret_cast<double2*>(d.epair)[a] = make_double2(Eel, Evdw);
+            d.pstat[a] = make_int2((int)npairs, (int)nguard);
         }
-        if (one && sCh[0] >= 0) {
-            if (e0 != (R)0) atomicAdd(&d.chain_E[3 * sCh[0]], (double)e0);
-            if (e1 != (R)0) atomicAdd(&d.chain_E[3 * sCh[0] + 1], (double)e1);
-        } else if (!one) {
-            for (int k2 = 0; k2 < kPairWarps; ++k2) {
-                if (sCh[k2] < 0) continue;
-                if (sE[0][k2] != (R)0) atomicAdd(&d.chain_E[3 * sCh[k2]], (double)sE[0][k2]);
-                if (sE[1][k2] != (R)0) atomicAdd(&d.chain_E[3 * sCh[k2] + 1], (double)sE[1][k2]);
-            }
-        }
-        if (c0) atomicAdd(&d.status->pairs, c0);
-        if (c1) atomicAdd(&d.status->guard, c1);
-        if (c2) atomicAdd(&d.status->nbr_total, c2);
-        if (m) atomicMax(&d.status->max_nbr, m);
     }
 }
 
@@ -582,9 +633,11 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
     __shared__ dbl4 s_pos[kSasaWarps][MIXED ? 1 : kMaxNbr];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
-    if (a < d.n && !d.status->done && !d.chain_done[atom_chain(d, a)]) {
-        if (!d.gflag[a]) {
-            if (lane == 0) d.covered[a] = 0;
+    if (a < d.n && !d.status->done) {
+        if (d.chain_done[atom_chain(d, a)]) {  // a converged chain takes no more steps
+            if (lane == 0) d.sstat[a] = make_int2(0, 0);
+        } else if (!d.gflag[a]) {
+            if (lane == 0) { d.covered[a] = 0; d.sstat[a] = make_int2(0, 0); }
         } else {
             const int cnt = min(d.nbr_cnt[a], kMaxNbr);
             for (int k = lane; k < cnt; k += 32) {
@@ -679,8 +732,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
                 if (f1) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 1], (unsigned long long)f1);
                 if (f2) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 2], (unsigned long long)f2);
                 d.covered[a] = ncov;
-                if (nguard) atomicAdd(&d.status->guard, (unsigned long long)nguard);
-                atomicAdd(&d.status->sasa_tests, ntest);
+                d.sstat[a] = make_int2((int)ntest, nguard);
             }
         }
     }
@@ -714,9 +766,11 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
     __shared__ unsigned short s_near[kSasaWarps][kBatch];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
-    if (a < d.n && !d.status->done && !d.chain_done[atom_chain(d, a)]) {
-        if (!d.gflag[a]) {
-            if (lane == 0) d.covered[a] = 0;
+    if (a < d.n && !d.status->done) {
+        if (d.chain_done[atom_chain(d, a)]) {  // a converged chain takes no more steps
+            if (lane == 0) d.sstat[a] = make_int2(0, 0);
+        } else if (!d.gflag[a]) {
+            if (lane == 0) { d.covered[a] = 0; d.sstat[a] = make_int2(0, 0); }
         } else {
             const int cnt = min(d.nbr_cnt[a], kMaxNbr);
             const float Ra = d.aprm32[a].w;
@@ -856,8 +910,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 if (s1) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 1], (unsigned long long)(-qa * s1));
                 if (s2) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 2], (unsigned long long)(-qa * s2));
                 d.covered[a] = ncov;
-                if (nguard) atomicAdd(&d.status->guard, (unsigned long long)nguard);
-                atomicAdd(&d.status->sasa_tests, (unsigned long long)nt);
+                d.sstat[a] = make_int2((int)nt, nguard);  // summed by the wrench kernel
             }
         }
     }

@@ -1,7 +1,8 @@
 // A7-A9: link wrenches, suffix sums over links, joint torques and the kinetostatic step: FP64 in
 // FP64 mode, double-float (kcm_df.cuh) in mixed mode; the step itself updates theta in FP64. The
 // wrench kernel, which visits every atom once with one thread each, also converts the mixed-mode
-// fixed-point forces and adds the cavity energy G0_i f_i of its atoms.
+// fixed-point forces, adds the cavity energy G0_i f_i and the pair energies of its atoms per chain,
+// and totals the per-atom counters of the pair and solvation kernels.
 //
 // Wrench of link h about the origin, P_h = [sum r x F ; sum F] (eq. KCM_01/02), and
 // P^agg_k = sum_{h >= k} P_h (Sec. 3.5) as a reverse scan: k_wrench_tile forms P_h from the atoms of
@@ -55,6 +56,8 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     constexpr bool DF = std::is_same<T, df>::value;
     __shared__ T sV[kWrenchTileAtoms][6];
     __shared__ T sP[32][6];
+    __shared__ unsigned long long sSt[kWrenchWarps][4];
+    __shared__ int sMx[kWrenchWarps];
     __shared__ bool last;
     Status* st = d.status;
     if (st->done) return;
@@ -62,21 +65,49 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     const int h0 = 32 * t, h1 = min(h0 + 32, d.L);
     const int a0 = d.link_start[h0], a1 = d.link_start[h1];
     const T* rr = reinterpret_cast<const T*>(DF ? d.rdf : d.r);
-    double Ecav = 0.0;   // FP64 mode
-    float Ecavf = 0.0f;  // mixed mode
-    int cc = -1;         // chain of the energy held
+    // energies of the thread's atoms (Coulomb, LJ, cavity) for the chain cc: FP64 mode / mixed mode
+    double E[3] = {0.0, 0.0, 0.0};
+    float Ef[3] = {0.0f, 0.0f, 0.0f};
+    int cc = -1;
+    // per-atom counters of the pair and solvation kernels: pairs, guard re-decisions, overlap tests,
+    // list entries; the largest list
+    unsigned long long cnt[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+    int mxn = 0;
     for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
         T f[3];
         const int ca = atom_chain(d, a);
-        if (ca != cc && d.prm.solvation) {  // the thread's atoms move on to the next chain
+        if (ca != cc) {  // the thread's atoms move on to the next chain
             if (cc >= 0) {
-                if constexpr (DF) { if (Ecavf != 0.0f) atomicAdd(&d.chain_E[3 * cc + 2], (double)Ecavf); }
-                else { if (Ecav != 0.0) atomicAdd(&d.chain_E[3 * cc + 2], Ecav); }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    if constexpr (DF) { if (Ef[k] != 0.0f) atomicAdd(&d.chain_E[3 * cc + k], (double)Ef[k]); }
+                    else { if (E[k] != 0.0) atomicAdd(&d.chain_E[3 * cc + k], E[k]); }
+                    E[k] = 0.0;
+                    Ef[k] = 0.0f;
+                }
             }
-            Ecav = 0.0;
-            Ecavf = 0.0f;
         }
         cc = ca;
+        if constexpr (DF) {
+            const float2 ep = reinterpret_cast<const float2*>(d.epair)[a];
+            Ef[0] += ep.x;
+            Ef[1] += ep.y;
+        } else {
+            const double2 ep = reinterpret_cast<const double2*>(d.epair)[a];
+            E[0] += ep.x;
+            E[1] += ep.y;
+        }
+        const int2 ps = d.pstat[a];
+        cnt[0] += ps.x;
+        cnt[1] += ps.y;
+        if (d.prm.solvation) {
+            const int2 ss = d.sstat[a];
+            const int nl = d.nbr_cnt[a];
+            cnt[1] += ss.y;
+            cnt[2] += (unsigned)ss.x;
+            cnt[3] += nl;
+            mxn = max(mxn, nl);
+        }
         if constexpr (DF) {  // pair forces in fixed point (2^-23) plus oversized terms, solvation (2^-40)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -84,7 +115,7 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
                 if (d.prm.solvation) f[k] = add(f[k], ldexp2(df_from_i64(d.Fcav[3 * a + k]), 0x1p-40f));
             }
             if (d.prm.solvation && d.gflag[a])  // G^cav_i = G0_i f_i, f_i = 1 - covered_i / N (Sec. 3.4)
-                Ecavf += d.G0f[a] * (1.0f - (float)d.covered[a] * d.f_invN);
+                Ef[2] += d.G0f[a] * (1.0f - (float)d.covered[a] * d.f_invN);
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -93,7 +124,7 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
             }
             if (d.prm.solvation) {
                 const double G0a = d.G0[a];
-                if (G0a != 0.0) Ecav += G0a - G0a * (double)d.covered[a] / (double)d.N;
+                if (G0a != 0.0) E[2] += G0a - G0a * (double)d.covered[a] / (double)d.N;
             }
         }
         const T x = rr[3 * a], y = rr[3 * a + 1], z = rr[3 * a + 2];
@@ -103,11 +134,33 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
         v[2] = sub(mul(x, f[1]), mul(y, f[0]));
         v[3] = f[0]; v[4] = f[1]; v[5] = f[2];
     }
-    if (d.prm.solvation) {  // cavity energy of the block's atoms, per chain
-        if constexpr (DF) chain_add(d.chain_E + 2, 3, cc, Ecavf);
-        else chain_add(d.chain_E + 2, 3, cc, Ecav);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // energies of the block's atoms, per chain
+        if constexpr (DF) chain_add(d.chain_E + k, 3, cc, Ef[k]);
+        else chain_add(d.chain_E + k, 3, cc, E[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cnt[k] = warp_sum(cnt[k]);
+    mxn = __reduce_max_sync(0xffffffffu, mxn);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sSt[w][k] = cnt[k];
+        sMx[w] = mxn;
     }
     __syncthreads();
+    if (threadIdx.x == 0) {  // the block's counters: one atomic each
+        unsigned long long s[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+        int m = 0;
+        for (int q = 0; q < kWrenchWarps; ++q) {
+            for (int k = 0; k < 4; ++k) s[k] += sSt[q][k];
+            m = max(m, sMx[q]);
+        }
+        if (s[0]) atomicAdd(&st->pairs, s[0]);
+        if (s[1]) atomicAdd(&st->guard, s[1]);
+        if (s[2]) atomicAdd(&st->sasa_tests, s[2]);
+        if (s[3]) atomicAdd(&st->nbr_total, s[3]);
+        if (m) atomicMax(&st->max_nbr, m);
+    }
     for (int u = threadIdx.x; u < 6 * 32; u += blockDim.x) {  // P_h component u / 32 of link h0 + u % 32
         const int k = u >> 5, h = h0 + (u & 31);
         T s = num_f<T>(0.0f);
