@@ -260,7 +260,7 @@ __global__ void k_bin_place(const DevChain d) {
 // integers here; the thread-per-atom consumers convert them to FP64 (a warp-per-atom kernel would
 // spend a whole FP64 warp instruction on each atom's lane 0).
 template <bool MIXED, int KR>
-__global__ void __launch_bounds__(kPairWarps * 32, 6) k_pair(const DevChain d) {
+__global__ void __launch_bounds__(kPairWarps * 32, MIXED ? 8 : 6) k_pair(const DevChain d) {
     typedef typename std::conditional<MIXED, float, double>::type R;
     typedef typename std::conditional<MIXED, float4, dbl4>::type QV;
     constexpr int kW = 2 * KR + 1;  // cells per row
@@ -371,10 +371,9 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) k_pair(const DevChain d) {
             px = p.x; py = p.y; pz = p.z; qi = p.w; sei = q.y; Ri = q.z; Roi = q.w;
         }
         const unsigned long long exa = d.exm[a], m14a = d.m14m[a];
-        long long Hx = 0, Hy = 0, Hz = 0, Lx = 0, Ly = 0, Lz = 0;  // mixed: folded fixed-point sums
         int hix = 0, hiy = 0, hiz = 0;                           // mixed: integer parts (kcal/mol/A)
         int lox = 0, loy = 0, loz = 0;                           // mixed: fractions in units of 2^-23
-        float ovx = 0, ovy = 0, ovz = 0, ove = 0, ovv = 0;      // mixed: oversized terms; energies
+        float ove = 0, ovv = 0;                                  // mixed: energies
         double dfx = 0, dfy = 0, dfz = 0;                        // FP64 mode
         int t = 0;
         const unsigned lt = (1u << lane) - 1u;
@@ -382,8 +381,21 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) k_pair(const DevChain d) {
         // in a ring of kPairQueue; phase B evaluates 32 queued pairs at a time, so the pair terms run
         // with every lane busy instead of the ~30 % of candidates that are in range.
         int qhead = 0, qtail = 0, nround = 0;
-        bool folded = false;  // uniform
         bool ovf = false;     // half stencil: a list slot beyond kMaxNbr
+        // mixed: the home atom's lane sums, reduced exactly (int32 pieces |.| <= 2^30 by 32-bit warp
+        // reductions of their biased 16-bit halves) and added to its fixed-point force, at the end and
+        // after every kPairFoldRounds pair rounds (so that the int32 lane sums cannot overflow)
+        auto flush_sums = [&]() {
+            const long long Hx = warp_sum_i32(hix), Hy = warp_sum_i32(hiy), Hz = warp_sum_i32(hiz);
+            const long long Lx = warp_sum_i32(lox), Ly = warp_sum_i32(loy), Lz = warp_sum_i32(loz);
+            if (lane == 0) {
+                unsigned long long* Fi = reinterpret_cast<unsigned long long*>(&d.Fpx[3 * a]);
+                atomicAdd(Fi, (unsigned long long)(Hx * 8388608LL + Lx));
+                atomicAdd(Fi + 1, (unsigned long long)(Hy * 8388608LL + Ly));
+                atomicAdd(Fi + 2, (unsigned long long)(Hz * 8388608LL + Lz));
+            }
+            hix = hiy = hiz = lox = loy = loz = 0;
+        };
         auto phase_b = [&](int nvalid) {
             const int e = (qhead + lane) & (kPairQueue - 1);
             const bool act = lane < nvalid;
@@ -475,7 +487,9 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) k_pair(const DevChain d) {
                             atomicAdd(Fj + 1, (unsigned long long)(-fx_units(n1, f1)));
                             atomicAdd(Fj + 2, (unsigned long long)(-fx_units(n2, f2)));
                         } else {  // clash-sized (or non-finite) term: plain float sums
-                            ovx += fx1; ovy += fy1; ovz += fz1;
+                            atomicAdd(&d.Fov[3 * a], fx1);
+                            atomicAdd(&d.Fov[3 * a + 1], fy1);
+                            atomicAdd(&d.Fov[3 * a + 2], fz1);
                             atomicAdd(&d.Fov[3 * b], -fx1);
                             atomicAdd(&d.Fov[3 * b + 1], -fy1);
                             atomicAdd(&d.Fov[3 * b + 2], -fz1);
@@ -518,10 +532,8 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) k_pair(const DevChain d) {
             if constexpr (MIXED) {
                 // at most one term per lane and round: kPairFoldRounds terms of |piece| <= 2^22 fit in int32
                 if (++nround == kPairFoldRounds) {
-                    Hx += hix; Hy += hiy; Hz += hiz; Lx += lox; Ly += loy; Lz += loz;
-                    hix = hiy = hiz = lox = loy = loz = 0;
+                    flush_sums();
                     nround = 0;
-                    folded = true;
                 }
             }
         };
@@ -564,28 +576,8 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) k_pair(const DevChain d) {
         }
         if (qtail > qhead) phase_b(qtail - qhead);
         if constexpr (MIXED) {
-            // lane sums: int32 pieces (|.| <= 2^30) by 32-bit warp reductions of their biased 16-bit
-            // halves; the int64 folds (more than kPairFoldRounds rounds) only where they happened
-            if (folded) {  // uniform
-                Hx = warp_sum(Hx); Hy = warp_sum(Hy); Hz = warp_sum(Hz);
-                Lx = warp_sum(Lx); Ly = warp_sum(Ly); Lz = warp_sum(Lz);
-            } else {
-                Hx = Hy = Hz = Lx = Ly = Lz = 0;
-            }
-            Hx += warp_sum_i32(hix); Hy += warp_sum_i32(hiy); Hz += warp_sum_i32(hiz);
-            Lx += warp_sum_i32(lox); Ly += warp_sum_i32(loy); Lz += warp_sum_i32(loz);
+            flush_sums();  // added to the partners' shares; converted to FP64 by the thread-per-atom consumers
             ove = warp_sum(ove); ovv = warp_sum(ovv);
-            if (lane == 0) {  // added to the partners' shares; converted to FP64 by the thread-per-atom consumers
-                unsigned long long* Fi = reinterpret_cast<unsigned long long*>(&d.Fpx[3 * a]);
-                atomicAdd(Fi, (unsigned long long)(Hx * 8388608LL + Lx));
-                atomicAdd(Fi + 1, (unsigned long long)(Hy * 8388608LL + Ly));
-                atomicAdd(Fi + 2, (unsigned long long)(Hz * 8388608LL + Lz));
-            }
-            if (ovx != 0.0f || ovy != 0.0f || ovz != 0.0f) {  // clash-sized terms only
-                atomicAdd(&d.Fov[3 * a], ovx);
-                atomicAdd(&d.Fov[3 * a + 1], ovy);
-                atomicAdd(&d.Fov[3 * a + 2], ovz);
-            }
             Eel = ove;
             Evdw = ovv;
         } else {
