@@ -352,7 +352,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.exm, nn)) || (rc = dalloc(h, &d.m14m, nn)) || (rc = dalloc(h, &d.Q64, 3 * N)) ||
         (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.Q4, N)) || (rc = dalloc(h, &d.theta, l)) || (rc = dalloc(h, &d.dtheta, l)) ||
         (rc = dalloc(h, &d.tau, l)) || (rc = dalloc(h, &d.G, 12 * (size_t)l)) ||
-        (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.u0df, 3 * l)) ||
+        (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.tileE, 12 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.u0df, 3 * l)) ||
         (rc = dalloc(h, &d.step0df, 3 * l)) || (rc = dalloc(h, &d.r0df, 3 * nn)) || (rc = dalloc(h, &d.rdf, 3 * nn)) ||
         (rc = dalloc(h, &d.ucurdf, 3 * l)) || (rc = dalloc(h, &d.pcurdf, 3 * l)) || (rc = dalloc(h, &d.G0f, nn)) ||
         (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||

@@ -48,7 +48,7 @@ struct Status {
     int max_nbr;
     unsigned int ticket_w;  // last-block detection in the wrench / suffix-scan kernel
     unsigned int ticket_bin;  // last-block detection in the cell-count kernel
-    int pad;
+    unsigned int ticket_fk;   // last-block detection in the transform-scan kernel
 };
 
 // Launch shapes.
@@ -69,7 +69,7 @@ constexpr int kWrenchWarps = 6;        // warps per 32-link tile of the wrench k
 struct DevChain {
     int m = 0, n = 0, l = 0, L = 0, N = 0;
     int fk_j = 1;        // joints per quad (four-lane transform slot) in the transform scan
-    int ntiles = 0;      // transform-scan blocks of 64 * fk_j joints
+    int ntiles = 0;      // transform-scan blocks of 32 * fk_j joints
     int ltiles = 0;      // suffix-sum tiles of 32 links
     int cell_cap = 0;     // cells of all chains' caps
     long long cell_alloc = 0;  // cells the cell arrays hold
@@ -113,6 +113,7 @@ struct DevChain {
     double* tau = nullptr;         // [l]
     double* G = nullptr;           // pose of link j+1 relative to the first frame of its scan block [l*12]
     double* tileP = nullptr;       // scan block products [ntiles*12]
+    double* tileE = nullptr;       // exclusive segmented prefixes of the scan block products [ntiles*12]
     double* M = nullptr;           // link frame poses [L*12] (double-float pairs in mixed mode)
     double* ucur = nullptr;        // current joint axes [l*3]
     double* pcur = nullptr;        // current axis points [l*3]

@@ -15,12 +15,13 @@
 // 32 J (b + 1)), J consecutive joints per quad. Each quad forms its joints' local transforms and their
 // running product (kept in G), the warp scans its eight quad products (Kogge-Stone, 3 levels), warp 0
 // scans the four warp products, and each quad stores its exclusive prefix within the block; the
-// block product goes to tileP. k_fk_apply: block b first reduces the block products 0 .. b-1 to its
-// block prefix (a tree over at most 64 products per round, every block at once), then composes block
-// prefix, quad prefix and running products into the link poses, the current axes u_j and axis
-// points p_j, moves the atoms of its links and adds them to their chain's bounding box; its last
-// block to finish (ticket, no waiting) sets the grids of the cell lists. A batch of chains is their
-// concatenation: every product is segmented at the first joint of a chain.
+// block product goes to tileP; with more than kFkTreeTiles blocks the last block to finish (ticket,
+// no waiting) scans the block products into every block's exclusive prefix (tileE), with fewer every
+// apply block reduces the products before it in one tree. k_fk_apply: block b composes its prefix,
+// quad prefix and running products into the link poses, the current axes u_j and axis points p_j,
+// moves the atoms of its links and adds them to their chain's bounding box; its last block to finish
+// sets the grids of the cell lists. A batch of chains is their concatenation: every product is
+// segmented at the first joint of a chain.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -36,6 +37,8 @@ using namespace dev;
 
 constexpr int kFkWarps = 4;               // warps per block of the transform scan (one per sub-partition)
 constexpr int kFkQuads = 8 * kFkWarps;    // quads (transform slots) per block
+constexpr int kFkMaxTiles = 40 * kFkQuads;  // scan blocks whose products the last block scans (40 per quad)
+constexpr int kFkTreeTiles = 2 * kFkQuads;  // up to this many, every apply block reduces the earlier products itself
 
 // row rr of the identity
 template <class T>
@@ -128,6 +131,20 @@ __device__ __forceinline__ void load_rows(const T* M, T* B) {
     }
 }
 
+// row rr of a transform written by another block of the running kernel (L2, not a stale L1 line)
+__device__ __forceinline__ void load_row_cg(const double* M, int rr, double* a) {
+    a[0] = __ldcg(&M[3 * rr]);
+    a[1] = __ldcg(&M[3 * rr + 1]);
+    a[2] = __ldcg(&M[3 * rr + 2]);
+    a[3] = __ldcg(&M[9 + rr]);
+}
+__device__ __forceinline__ void load_row_cg(const df* M, int rr, df* a) {
+    const double* m = reinterpret_cast<const double*>(M);
+    double t[4] = {__ldcg(&m[3 * rr]), __ldcg(&m[3 * rr + 1]), __ldcg(&m[3 * rr + 2]), __ldcg(&m[9 + rr])};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = *reinterpret_cast<const df*>(&t[k]);
+}
+
 // Segmented products: a quad carries (f, A) with f set when a chain starts within the range A covers;
 // (f1, A1) followed by (f2, A2) combine to (f1 | f2, f2 ? A2 : A1 o A2), so products never reach
 // across the first joint of a chain.
@@ -186,6 +203,7 @@ template <int J, class T>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
     __shared__ T sW[kFkWarps][12];
     __shared__ int sF[kFkWarps];
+    __shared__ bool sLast;
     if (d.status->done) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
@@ -265,10 +283,64 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
         if ((lane & 3) < 3) store_row(&G[12 * (size_t)jl], rr, incl);
         if ((lane & 3) == 0) d.gseg[jl] = (unsigned char)f;
     }
+    T* tP = reinterpret_cast<T*>(d.tileP);
     if (threadIdx.x < 32 && q == 0) {
-        if ((lane & 3) < 3) store_row(&reinterpret_cast<T*>(d.tileP)[12 * (size_t)blockIdx.x], rr, tot);
+        if ((lane & 3) < 3) store_row(&tP[12 * (size_t)blockIdx.x], rr, tot);
         if (lane == 0) d.tileF[blockIdx.x] = tf;
     }
+    // Many blocks: the last block scans the block products, E_b = segmented product of blocks 0 .. b-1.
+    // Few: every apply block reduces the products before it in one tree (a shorter critical path).
+    if (gridDim.x <= kFkTreeTiles) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sLast = atomicAdd(&d.status->ticket_fk, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!sLast) return;
+    __threadfence();
+    const int nt = gridDim.x;
+    const int per = (nt + kFkQuads - 1) / kFkQuads;  // block products per quad, in order
+    const int t0 = slot * per;
+    T run[4];
+    bool rf = false;
+    row_identity(rr, run);
+    for (int i = 0; i < per; ++i) {  // the quad's running product (every lane takes part in the shuffles)
+        const int tt = t0 + i;
+        T p[4], B[12];
+        bool pf = false;
+        if (tt < nt) { load_row_cg(&tP[12 * (size_t)tt], rr, p); pf = __ldcg(&d.tileF[tt]) != 0; }
+        else row_identity(rr, p);
+        quad_rows(p, base, B);
+        if (pf) { for (int m = 0; m < 4; ++m) run[m] = p[m]; }
+        else row_compose(run, B, run);
+        rf = rf || pf;
+    }
+    bool xf = rf;
+    block_scan_quads(run, xf, tot, tf, sW, sF, w, q, rr, base, lane);
+    // exclusive prefix of the quad: the inclusive prefix of the quad before it
+#pragma unroll
+    for (int m = 0; m < 4; ++m) ex[m] = shfl_up(run[m], 4);
+    exf = __shfl_up_sync(0xffffffffu, xf, 4);
+    if (q == 0) {
+        if (w == 0) { row_identity(rr, ex); exf = false; }
+        else { load_row(sW[w - 1], rr, ex); exf = sF[w - 1] != 0; }
+    }
+    T* tE = reinterpret_cast<T*>(d.tileE);
+    for (int i = 0; i < per; ++i) {
+        const int tt = t0 + i;
+        T p[4], B[12];
+        bool pf = false;
+        if (tt < nt) {
+            if ((lane & 3) < 3) store_row(&tE[12 * (size_t)tt], rr, ex);
+            load_row_cg(&tP[12 * (size_t)tt], rr, p);
+            pf = __ldcg(&d.tileF[tt]) != 0;
+        } else {
+            row_identity(rr, p);
+        }
+        quad_rows(p, base, B);
+        if (pf) { for (int m = 0; m < 4; ++m) ex[m] = p[m]; }
+        else row_compose(ex, B, ex);
+    }
+    if (threadIdx.x == 0) d.status->ticket_fk = 0u;
 }
 
 // row rr (and flag) of the segmented product of the block products b0 .. b1 - 1 (identity, no flag,
@@ -354,18 +426,14 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     const int j0 = (blockIdx.x * kFkQuads + slot) * J;
     T* M = reinterpret_cast<T*>(d.M);
     const T* G = reinterpret_cast<const T*>(d.G);
-    // block prefix: segmented product of the block products before this block, 2 * kFkQuads per round
+    // block prefix: the segmented product of the earlier blocks, scanned by the scan kernel's last
+    // block, or (few blocks) reduced here in one tree
     T bE[4];
-    bool bf = false;
-    row_identity(rr, bE);
-    for (int b0 = 0; b0 < (int)blockIdx.x; b0 += 2 * kFkQuads) {
-        T part[4], B[12];
+    if (gridDim.x > kFkTreeTiles) {
+        load_row(&reinterpret_cast<const T*>(d.tileE)[12 * (size_t)blockIdx.x], rr, bE);
+    } else {
         bool pf;
-        block_prefix(d, b0, min(b0 + 2 * kFkQuads, (int)blockIdx.x), sW, sF, w, q, rr, base, lane, part, pf);
-        quad_rows(part, base, B);
-        if (b0 == 0 || pf) { for (int m = 0; m < 4; ++m) bE[m] = part[m]; }
-        else row_compose(bE, B, bE);
-        bf = bf || pf;
+        block_prefix(d, 0, (int)blockIdx.x, sW, sF, w, q, rr, base, lane, bE, pf);
     }
 #pragma unroll
     for (int i = 0; i < J; ++i) {
@@ -531,11 +599,11 @@ void launch_fk_j(DevChain& d, cudaStream_t s) {
 
 }  // namespace
 
-// joints per quad: the smallest J that keeps the block count within one round (2 * kFkQuads) of the
-// block-prefix reduction
+// joints per quad: the smallest J that keeps the block count within what the scan kernel's last
+// block scans (kFkMaxTiles)
 int fk_joints_per_lane(int l) {
     int J = 1;
-    while (J < 32 && (l + kFkQuads * J - 1) / (kFkQuads * J) > 2 * kFkQuads) J *= 2;
+    while (J < 32 && (l + kFkQuads * J - 1) / (kFkQuads * J) > kFkMaxTiles) J *= 2;
     return J;
 }
 
