@@ -269,6 +269,39 @@ def run_reference(args):
     return 0
 
 
+def time_steps(c, prep, stream, steps):
+    """Device time (ms) of each of `steps` whole iterations: the loop-state reset and every kernel of one
+    iteration, between two CUDA events on the library's stream. The restore of the start conformation
+    and the L2 flush before each step are outside the events."""
+    import torch
+
+    evs = []
+    for _ in range(steps):
+        prep()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.step_async(1)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    c.step_status()  # raises if the device flagged an error
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def stage_breakdown(c, prep, steps):
+    """Mean per-stage device time (ms) over `steps` instrumented iterations (a CUDA event between stages;
+    each event node adds about 3 us to the iteration, so these stages sum to more than a plain step)."""
+    from paper_1712_05012_b300 import kcm
+
+    stg = {k: 0.0 for k in kcm.STAGES}
+    for _ in range(steps):
+        prep()
+        _, st = c.step_timed()
+        for k, v in st.items():
+            stg[k] += v
+    return {k: v / steps for k, v in stg.items()}
+
+
 def run_ours(args):
     import torch
 
@@ -300,21 +333,22 @@ def run_ours(args):
             flush.add_(1)
 
     clocks = Clocks(local)
+    prep_main = lambda: prepare(ch, lib_stream)  # noqa: E731
     for _ in range(args.warmup):
-        prepare(ch, lib_stream)
+        prep_main()
         ch.step_timed()
-    totals, stages = [], {k: 0.0 for k in kcm.STAGES}
-    for _ in range(args.steps):
-        prepare(ch, lib_stream)
-        tot, st = ch.step_timed()
-        totals.append(tot)
-        for k, v in st.items():
-            stages[k] += v
+        prep_main()
+        ch.step(1)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    totals = time_steps(ch, prep_main, lib_stream, args.steps)
+    ms_stage = stage_breakdown(ch, prep_main, args.steps)
     clk = clocks.stop()
     stats = ch.stats()
     t_sum = max_over_ranks(sum(totals) / 1e3, ws)
     value = whole_job_rate(ws, n, args.steps, t_sum)
-    ms_stage = {k: v / args.steps for k, v in stages.items()}
 
     # rooflines of every stage (work counted at the last timed iteration); the dominant one is the
     # headline "roofline"
@@ -354,11 +388,8 @@ def run_ours(args):
             sv = torch.cuda.ExternalStream(cv.stream())
             for _ in range(3):
                 prepare(cv, sv)
-                cv.step_timed()
-            tt = []
-            for _ in range(args.fp64_steps):
-                prepare(cv, sv)
-                tt.append(cv.step_timed()[0])
+                cv.step(1)
+            tt = time_steps(cv, lambda: prepare(cv, sv), sv, args.fp64_steps)
             vacuum_value = n * args.fp64_steps / (sum(tt) / 1e3)
 
     # the batch workload: 512 chains stepped together, one launch per stage, measured the same way
@@ -377,18 +408,15 @@ def run_ours(args):
             for _ in range(3):
                 prep_b()
                 bb.step_timed()
-            tt, stg = [], {k: 0.0 for k in kcm.STAGES}
-            for _ in range(args.batch_steps):
                 prep_b()
-                tot, st = bb.step_timed()
-                tt.append(tot)
-                for k, v in st.items():
-                    stg[k] += v
+                bb.step(1)
+            tt = time_steps(bb, prep_b, sb, args.batch_steps)
+            stg = stage_breakdown(bb, prep_b, args.batch_steps)
             bst = bb.stats()
             batch = {"workload": bwl.name, "chains": bb.nchains, "atoms": bb.n, "residues": int(sum(bwl.m)),
                      "value": ws * bb.n * args.batch_steps / (sum(tt) / 1e3), "unit": UNIT,
                      "ms_per_step": sum(tt) / args.batch_steps,
-                     "stage_ms": {k: v / args.batch_steps for k, v in stg.items()},
+                     "stage_ms": stg,
                      "steps": args.batch_steps, "pairs": bst["pairs"], "sasa_tests": bst["sasa_tests"],
                      "start": "every step from the stored compact starts (theta restored untimed)"}
 
@@ -421,13 +449,10 @@ def run_ours(args):
     if args.fp64_steps > 0 and prec == synth.PRECISION_MIXED:
         with kcm.Chain(seq, table, synth.RunParams(precision=synth.PRECISION_FP64)) as c64:
             s64 = torch.cuda.ExternalStream(c64.stream())
-            for _ in range(2):
+            for _ in range(3):
                 prepare(c64, s64)
-                c64.step_timed()
-            tt = []
-            for _ in range(args.fp64_steps):
-                prepare(c64, s64)
-                tt.append(c64.step_timed()[0])
+                c64.step(1)
+            tt = time_steps(c64, lambda: prepare(c64, s64), s64, args.fp64_steps)
             fp64_value = n * args.fp64_steps / (sum(tt) / 1e3)
 
     # end to end through the C ABI with pinned host buffers: the start theta in, one step, theta out
@@ -476,7 +501,10 @@ def run_ours(args):
                            "n_sample": 256, "solvation": 1, "precision": args.precision,
                            "replicas": ws, "l2": "flushed between timed steps (256 MiB write)",
                            "start": "every step from the stored compact start (theta restored untimed)"},
-                "roofline": roof, "rooflines": rooflines, "stage_ms": ms_stage, "fp64_value": fp64_value,
+                "roofline": roof, "rooflines": rooflines, "stage_ms": ms_stage,
+                "stage_note": "stage_ms from a second pass of the same steps with a CUDA event between stages "
+                              "(each event node adds ~3 us); value and ms_per_step time whole steps only",
+                "fp64_value": fp64_value,
                 "vacuum_value": vacuum_value, "batch": batch, "serving": serving,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,

@@ -17,6 +17,8 @@ struct kcm_ctx {
     kcm::HostChain hc;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;       // the long-list solvation kernel beside the main one
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraphExec_t graph = nullptr;
     cudaGraphExec_t graph_timed = nullptr;
     cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
@@ -70,17 +72,34 @@ int sync(kcm_ctx* h) {
     return KCM_OK;
 }
 
+// Algorithm 1: the atoms with long neighbour lists are taken by a second kernel on a side stream,
+// forked after the pair kernel and joined before the wrenches (a parallel branch of the captured graph)
+void enqueue_sasa(kcm_ctx* h, cudaStream_t s) {
+    if (h->side) {
+        cudaEventRecord(h->fork, s);
+        cudaStreamWaitEvent(h->side, h->fork, 0);
+        kcm::launch_sasa_long(h->d, h->side);
+        cudaEventRecord(h->join, h->side);
+        kcm::launch_sasa(h->d, s);
+        cudaStreamWaitEvent(s, h->join, 0);
+    } else {
+        kcm::launch_sasa(h->d, s);
+    }
+}
+
 void enqueue_evaluation(kcm_ctx* h) {
     kcm::launch_fk(h->d, h->stream);
     kcm::launch_binning(h->d, h->stream);
-    kcm::launch_forces(h->d, h->stream);
+    kcm::launch_pairs(h->d, h->stream);
+    enqueue_sasa(h, h->stream);
     kcm::launch_torques(h->d, h->stream);
 }
 
 void enqueue_iteration(kcm_ctx* h) {
     kcm::launch_fk(h->d, h->stream);
     kcm::launch_binning(h->d, h->stream);
-    kcm::launch_forces(h->d, h->stream);
+    kcm::launch_pairs(h->d, h->stream);
+    enqueue_sasa(h, h->stream);
     kcm::launch_torques_step(h->d, h->stream);
 }
 
@@ -144,7 +163,7 @@ int build_timed_graph(kcm_ctx* h) {
     cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
     kcm::launch_pairs(h->d, s);
     cudaEventRecordWithFlags(h->ev[4], s, cudaEventRecordExternal);
-    kcm::launch_sasa(h->d, s);
+    enqueue_sasa(h, s);
     cudaEventRecordWithFlags(h->ev[5], s, cudaEventRecordExternal);
     kcm::launch_torques_step(h->d, s);
     cudaEventRecordWithFlags(h->ev[6], s, cudaEventRecordExternal);
@@ -310,6 +329,12 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         h->own_stream = true;
     }
 
+    if (prm->solvation) {
+        e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
+        if (e != cudaSuccess) { cuda_fail(h, e, "side stream create"); return bail(KCM_E_CUDA); }
+    }
     const kcm::HostChain& hc = h->hc;
     kcm::DevChain& d = h->d;
     d.prm = *prm;
@@ -362,7 +387,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fpx, 3 * nn)) || (rc = dalloc(h, &d.Fov, 3 * nn)) ||
         (rc = dalloc(h, &d.gflag, nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||
         (rc = dalloc(h, &d.nbr, nn * kcm::kMaxNbr)) || (rc = dalloc(h, &d.nbr_off, nn * kcm::kMaxNbr)) ||
-        (rc = dalloc(h, &d.covered, nn)) || (rc = dalloc(h, &d.epair, 2 * nn)) || (rc = dalloc(h, &d.pstat, nn)) ||
+        (rc = dalloc(h, &d.covered, nn)) || (rc = dalloc(h, &d.long_atoms, nn)) || (rc = dalloc(h, &d.epair, 2 * nn)) || (rc = dalloc(h, &d.pstat, nn)) ||
         (rc = dalloc(h, &d.sstat, nn)) ||
         (rc = dalloc(h, &d.lane_suf, 6 * (size_t)L)) || (rc = dalloc(h, &d.tileS, 6 * (size_t)d.ltiles)) ||
         (rc = dalloc(h, &d.tileSuf, 6 * (size_t)d.ltiles)) ||
@@ -510,10 +535,14 @@ int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* ma
 void kcm_destroy(kcm_handle h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->side) cudaStreamSynchronize(h->side);
     drop_graphs(h);
     for (cudaEvent_t ev : h->ev)
         if (ev) cudaEventDestroy(ev);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     cudaGetLastError();
     delete h;

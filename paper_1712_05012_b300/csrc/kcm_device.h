@@ -49,6 +49,8 @@ struct Status {
     unsigned int ticket_w;  // last-block detection in the wrench / suffix-scan kernel
     unsigned int ticket_bin;  // last-block detection in the cell-count kernel
     unsigned int ticket_fk;   // last-block detection in the transform-scan kernel
+    int nlong;                // atoms with more than kSasaStage solvation neighbours (long_atoms)
+    int pad2;
 };
 
 // Launch shapes.
@@ -62,6 +64,7 @@ constexpr float kPairFxMax = 4194304.0f;        // |pair term| below which it is
 constexpr int kPairFoldRounds = 256;            // pair rounds between folds of the int32 lane sums
 constexpr int kPairQueue = 64;                  // ring of in-range candidates per warp of the pair kernel (power of 2)
 constexpr int kSasaWarps = 4;
+constexpr int kSasaLongBlocks = 32;  // most blocks of the long-list solvation kernels
 constexpr int kApplyTpb = 64;
 constexpr int kWrenchTileAtoms = 352;  // atoms of 32 links of at most 11 atoms (checked at creation)
 constexpr int kWrenchWarps = 6;        // warps per 32-link tile of the wrench kernel (one per wrench component in the scan)
@@ -141,6 +144,7 @@ struct DevChain {
     int* nbr = nullptr;            // [n*kMaxNbr]
     float4* nbr_off = nullptr;     // r_j - r_i and Roff_j^2 [n*kMaxNbr]
     int* covered = nullptr;        // [n]
+    int* long_atoms = nullptr;     // atoms with more than kSasaStage solvation neighbours, in any order [n]
     // per-atom results that the wrench kernel sums per chain and per launch (the pair and solvation
     // kernels then need no atomics on shared totals)
     double* epair = nullptr;       // Coulomb and LJ energy of the atom's pairs [n*2] (mixed: a float pair per atom)
@@ -183,9 +187,9 @@ void launch_init_status(DevChain& d, cudaStream_t s);
 void launch_reset_loop(DevChain& d, cudaStream_t s);
 void launch_fk(DevChain& d, cudaStream_t s);
 void launch_binning(DevChain& d, cudaStream_t s);
-void launch_forces(DevChain& d, cudaStream_t s);
 void launch_pairs(DevChain& d, cudaStream_t s);
 void launch_sasa(DevChain& d, cudaStream_t s);
+void launch_sasa_long(DevChain& d, cudaStream_t s);  // atoms with more than kSasaStage neighbours
 void launch_torques(DevChain& d, cudaStream_t s);
 void launch_torques_step(DevChain& d, cudaStream_t s);
 int fk_joints_per_lane(int l);

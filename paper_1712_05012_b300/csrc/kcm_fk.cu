@@ -583,6 +583,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
         st->guard = 0;
         st->sasa_tests = 0;
         st->max_nbr = 0;
+        st->nlong = 0;
     }
 }
 

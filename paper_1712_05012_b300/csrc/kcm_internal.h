@@ -14,8 +14,12 @@ namespace kcm {
 constexpr double kFxScale = 1099511627776.0;  // 2^40
 constexpr double kFxInv = 1.0 / 1099511627776.0;
 
-// Largest solvation neighbour list per atom; more raises KCM_E_OVERFLOW.
-constexpr int kMaxNbr = 128;
+// Largest solvation neighbour list per atom; more raises KCM_E_OVERFLOW. At protein-like packing
+// (about 0.1 atoms per A^3 with hydrogens) the solvation range of an atom (Roff_i + Roff_j + dr, up to
+// ~6.8 A) holds about 130 atoms. Lists up to kSasaStage are staged in shared memory by Algorithm 1's
+// kernels; longer ones are read from global memory.
+constexpr int kMaxNbr = 256;
+constexpr int kSasaStage = 128;
 
 // Largest sample count per offset sphere.
 constexpr int kMaxSample = 4096;

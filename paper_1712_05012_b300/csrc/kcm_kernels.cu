@@ -16,6 +16,7 @@
 // Every reduction has a fixed order or is integer, so an iteration is bitwise reproducible.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <type_traits>
 
@@ -217,6 +218,9 @@ __global__ void k_bin_place(const DevChain d) {
     d.sorted[sl] = a;
     d.slot_cell[sl] = key;
     d.smask[sl] = make_ulonglong2(d.exm[a], d.m14m[a]);  // bond classes in slot order (no dependent load later)
+    if (d.prm.solvation) {  // Algorithm 1 adds its exchanges to both atoms of a pair: zero the sums (no memset node)
+        d.Fcav[3 * a] = 0; d.Fcav[3 * a + 1] = 0; d.Fcav[3 * a + 2] = 0;
+    }
     double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
     if (MIXED) {
         // the pair kernel adds each pair's share to both atoms: zero the sums and the list counters
@@ -515,6 +519,10 @@ __global__ void __launch_bounds__(kPairWarps * 32, MIXED ? 8 : 6) k_pair(const D
                             d.nbr_off[(size_t)b * kMaxNbr + rslot] = make_float4((float)ddx, (float)ddy, (float)ddz, (float)(Roi * Roi));
                         }
                         ovf |= slot >= kMaxNbr || rslot >= kMaxNbr;
+                        // an atom whose list passes kSasaStage entries goes to the long-list kernels
+                        // (the append that draws slot kSasaStage is unique)
+                        if (slot == kSasaStage) d.long_atoms[atomicAdd(&d.status->nlong, 1)] = a;
+                        if (rslot == kSasaStage) d.long_atoms[atomicAdd(&d.status->nlong, 1)] = b;
                     }
                     ncount += 2 * __popc(bm);
                 }
@@ -593,7 +601,10 @@ __global__ void __launch_bounds__(kPairWarps * 32, MIXED ? 8 : 6) k_pair(const D
             ovf = ncount > kMaxNbr;
         }
         if (lane == 0) {
-            if (!HALF) d.nbr_cnt[a] = ncount;
+            if (!HALF) {
+                d.nbr_cnt[a] = ncount;
+                if (ncount > kSasaStage) d.long_atoms[atomicAdd(&d.status->nlong, 1)] = a;
+            }
             if (ovf) {
                 atomicOr(&d.status->error, kErrOverflow);
                 atomicOr(&d.chain_err[ca], kErrOverflow);
@@ -617,12 +628,10 @@ __global__ void __launch_bounds__(kPairWarps * 32, MIXED ? 8 : 6) k_pair(const D
 // points (C = 1) against their critical neighbour only. Net exchange counts per (j, s) go to
 // shared memory; the force quantum G0_i / (N dr) is applied in fixed point, so
 // F_j += q c_js and F_i -= q c_js are exact integer additions.
-template <bool MIXED>
 __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
-    __shared__ int s_idx[kSasaWarps][kMaxNbr];
-    __shared__ int s_cnt[kSasaWarps][3 * kMaxNbr];
-    __shared__ float4 s_off[kSasaWarps][MIXED ? kMaxNbr : 1];
-    __shared__ dbl4 s_pos[kSasaWarps][MIXED ? 1 : kMaxNbr];
+    __shared__ int s_idx[kSasaWarps][kSasaStage];
+    __shared__ int s_cnt[kSasaWarps][3 * kSasaStage];
+    __shared__ dbl4 s_pos[kSasaWarps][kSasaStage];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
     if (a < d.n && !d.status->done) {
@@ -631,62 +640,31 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
         } else if (!d.gflag[a]) {
             if (lane == 0) { d.covered[a] = 0; d.sstat[a] = make_int2(0, 0); }
         } else {
-            const int cnt = min(d.nbr_cnt[a], kMaxNbr);
+            // a list longer than kSasaStage is k_sasa_long's: nothing to do here, nothing written
+            const bool mine = d.nbr_cnt[a] <= kSasaStage;
+            const int cnt = mine ? d.nbr_cnt[a] : 0;
             for (int k = lane; k < cnt; k += 32) {
                 int b = d.nbr[(size_t)a * kMaxNbr + k];
                 s_idx[w][k] = b;
                 s_cnt[w][3 * k] = 0; s_cnt[w][3 * k + 1] = 0; s_cnt[w][3 * k + 2] = 0;
-                if (MIXED) {
-                    s_off[w][k] = d.nbr_off[(size_t)a * kMaxNbr + k];
-                } else {
-                    double ro = d.aprm64[b].w;
-                    s_pos[w][k] = make_dbl4(d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro));
-                }
+                double ro = d.aprm64[b].w;
+                s_pos[w][k] = make_dbl4(d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro));
             }
             __syncwarp();
             const double Roa = d.aprm64[a].w;
             const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
-            const float Raf = (float)Roa;
             const double dr = d.prm.delta_r;
-            const float drf = (float)dr;
-            // guard band of the FP32 overlap test (A^2): a bound of about 5e-5 A^2 at a 10 A cell edge,
-            // from the cell-relative offsets (error < 7 s 2^-24 per component) and the test's own rounding
-            const float gs = (float)(2e-4 + 4e-5 * d.grid[atom_chain(d, a)].s);
-            int ncov = 0, nguard = 0;
+            int ncov = 0;
             unsigned long long ntest = 0;
             for (int k = lane; k < d.N; k += 32) {
-                // T_i(q_k) = r_i + Roff_i q_k (Sec. 3.4): FP64 always in the FP64 kernel, and only
-                // for guard-band rechecks in the mixed kernel
-                double qx = 0, qy = 0, qz = 0;
-                float vx = 0, vy = 0, vz = 0;
-                if constexpr (MIXED) {
-                    vx = Raf * d.Q32[3 * k]; vy = Raf * d.Q32[3 * k + 1]; vz = Raf * d.Q32[3 * k + 2];
-                } else {
-                    qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
-                    qy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
-                    qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
-                }
+                // T_i(q_k) = r_i + Roff_i q_k (Sec. 3.4)
+                const double qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
+                const double qy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
+                const double qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
                 auto test = [&](int j, int s) -> bool {
                     ++ntest;
-                    if constexpr (MIXED) {
-                        float4 o = s_off[w][j];
-                        float wx = vx - o.x, wy = vy - o.y, wz = vz - o.z;
-                        if (s == 0) wx -= drf;
-                        if (s == 1) wy -= drf;
-                        if (s == 2) wz -= drf;
-                        float diff = wx * wx + wy * wy + wz * wz - o.w;
-                        if (fabsf(diff) > gs) return diff <= 0.0f;
-                        ++nguard;
-                        int b = s_idx[w][j];
-                        double ro = d.aprm64[b].w;
-                        double gx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
-                        double gy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
-                        double gz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
-                        return covers64(gx, gy, gz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
-                    } else {
-                        dbl4 p = s_pos[w][j];
-                        return covers64(qx, qy, qz, p.x, p.y, p.z, p.w, s, dr);
-                    }
+                    dbl4 p = s_pos[w][j];
+                    return covers64(qx, qy, qz, p.x, p.y, p.z, p.w, s, dr);
                 };
                 int C = 0, crit = -1;
                 for (int j = 0; j < cnt; ++j) {
@@ -706,7 +684,6 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
                 }
             }
             ncov = warp_sum(ncov);
-            nguard = warp_sum(nguard);
             ntest = warp_sum(ntest);
             __syncwarp();
             const long long qa = d.qfx[a];
@@ -719,12 +696,84 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
                 if (c2) { atomicAdd((unsigned long long*)&d.Fcav[3 * b + 2], (unsigned long long)(qa * c2)); f2 -= qa * c2; }
             }
             f0 = warp_sum(f0); f1 = warp_sum(f1); f2 = warp_sum(f2);
+            if (lane == 0 && mine) {
+                if (f0) atomicAdd((unsigned long long*)&d.Fcav[3 * a], (unsigned long long)f0);
+                if (f1) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 1], (unsigned long long)f1);
+                if (f2) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 2], (unsigned long long)f2);
+                d.covered[a] = ncov;
+                d.sstat[a] = make_int2((int)ntest, 0);
+            }
+        }
+    }
+}
+
+
+// Algorithm 1 for the atoms with more than kSasaStage solvation neighbours: the steps of k_sasa with
+// the neighbours read from global memory and each exchange added to the partner's fixed-point sum at
+// once. It runs beside k_sasa (a second stream), which skips these atoms; a warp per atom of the list
+// the pair kernel recorded (none, mostly: the kernel then returns at once).
+__global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_long(const DevChain d) {
+    const int lane = threadIdx.x & 31;
+    if (d.status->done) return;
+    const int nlong = d.status->nlong;
+    for (int e = blockIdx.x * kSasaWarps + (threadIdx.x >> 5); e < nlong; e += gridDim.x * kSasaWarps) {  // uniform
+        const int a = d.long_atoms[e];
+        {
+            if (!d.gflag[a] || d.chain_done[atom_chain(d, a)]) continue;  // written by k_sasa
+            const int cnt = min(d.nbr_cnt[a], kMaxNbr);
+            const int* nl = &d.nbr[(size_t)a * kMaxNbr];
+            const long long qa = d.qfx[a];
+            long long f0 = 0, f1 = 0, f2 = 0;  // atom i's share of the exchanges
+            auto exchange = [&](int j, int s, int delta) {
+                atomicAdd((unsigned long long*)&d.Fcav[3 * nl[j] + s], (unsigned long long)(qa * delta));
+                if (s == 0) f0 -= qa * delta;
+                else if (s == 1) f1 -= qa * delta;
+                else f2 -= qa * delta;
+            };
+            const double Roa = d.aprm64[a].w;
+            const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
+            const double dr = d.prm.delta_r;
+            int ncov = 0;
+            unsigned long long ntest = 0;
+            for (int k = lane; k < d.N; k += 32) {
+                // T_i(q_k) = r_i + Roff_i q_k (Sec. 3.4)
+                const double qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
+                const double qy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
+                const double qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
+                auto test = [&](int j, int s) -> bool {
+                    ++ntest;
+                    const int b = nl[j];
+                    const double ro = d.aprm64[b].w;
+                    const dbl4 p = make_dbl4(d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro));
+                    return covers64(qx, qy, qz, p.x, p.y, p.z, p.w, s, dr);
+                };
+                int C = 0, crit = -1;
+                for (int j = 0; j < cnt; ++j) {
+                    if (test(j, -1)) {
+                        if (++C == 1) crit = j;
+                        else break;
+                    }
+                }
+                if (C >= 1) ++ncov;
+                if (C == 0) {
+                    for (int j = 0; j < cnt; ++j)
+                        for (int s = 0; s < 3; ++s)
+                            if (test(j, s)) exchange(j, s, 1);
+                } else if (C == 1) {
+                    for (int s = 0; s < 3; ++s)
+                        if (!test(crit, s)) exchange(crit, s, -1);
+                }
+            }
+            ncov = warp_sum(ncov);
+            ntest = warp_sum(ntest);
+            __syncwarp();
+            f0 = warp_sum(f0); f1 = warp_sum(f1); f2 = warp_sum(f2);
             if (lane == 0) {
                 if (f0) atomicAdd((unsigned long long*)&d.Fcav[3 * a], (unsigned long long)f0);
                 if (f1) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 1], (unsigned long long)f1);
                 if (f2) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 2], (unsigned long long)f2);
                 d.covered[a] = ncov;
-                d.sstat[a] = make_int2((int)ntest, nguard);
+                d.sstat[a] = make_int2((int)ntest, 0);
             }
         }
     }
@@ -752,9 +801,9 @@ constexpr int kPtsPerLane = 8;                  // sample points each lane holds
 constexpr int kBatch = 32 * kPtsPerLane;         // points per batch (256)
 
 __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d) {
-    __shared__ float4 s_o[kSasaWarps][kMaxNbr];   // o_j, h_j
-    __shared__ int s_idx[kSasaWarps][kMaxNbr];
-    __shared__ int s_cnt[kSasaWarps][3 * kMaxNbr];
+    __shared__ float4 s_o[kSasaWarps][kSasaStage];   // o_j, h_j
+    __shared__ int s_idx[kSasaWarps][kSasaStage];
+    __shared__ int s_cnt[kSasaWarps][3 * kSasaStage];
     __shared__ unsigned short s_near[kSasaWarps][kBatch];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * kSasaWarps + w;
@@ -764,7 +813,10 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
         } else if (!d.gflag[a]) {
             if (lane == 0) { d.covered[a] = 0; d.sstat[a] = make_int2(0, 0); }
         } else {
-            const int cnt = min(d.nbr_cnt[a], kMaxNbr);
+            // a list longer than kSasaStage is k_sasa_mixed_long's: nothing to do here, nothing written
+            const int cnt0 = d.nbr_cnt[a];
+            const bool mine = cnt0 <= kSasaStage;
+            const int cnt = min(mine ? cnt0 : 0, kSasaStage);
             const float Ra = d.aprm32[a].w;
             const float inv2R = 0.5f / Ra;
             const float drf = d.f_dr;
@@ -878,7 +930,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 }
                 __syncwarp();
             }
-            // counts of the warp by 32-bit reductions (each below 2^31: at most 4096 points x 128
+            // counts of the warp by 32-bit reductions (each below 2^31: at most 4096 points x kMaxNbr
             // neighbours x 3 axes); atom i's force is minus the quantum times its net exchanges
             ncov = (int)__reduce_add_sync(0xffffffffu, (unsigned)ncov);
             nguard = (int)__reduce_add_sync(0xffffffffu, (unsigned)nguard);
@@ -894,6 +946,162 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d
                 if (c2) atomicAdd((unsigned long long*)&d.Fcav[3 * b + 2], (unsigned long long)(qa * c2));
                 s0 += c0; s1 += c1; s2 += c2;
             }
+            s0 = __reduce_add_sync(0xffffffffu, s0);
+            s1 = __reduce_add_sync(0xffffffffu, s1);
+            s2 = __reduce_add_sync(0xffffffffu, s2);
+            if (lane == 0 && mine) {
+                if (s0) atomicAdd((unsigned long long*)&d.Fcav[3 * a], (unsigned long long)(-qa * s0));
+                if (s1) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 1], (unsigned long long)(-qa * s1));
+                if (s2) atomicAdd((unsigned long long*)&d.Fcav[3 * a + 2], (unsigned long long)(-qa * s2));
+                d.covered[a] = ncov;
+                d.sstat[a] = make_int2((int)nt, nguard);  // summed by the wrench kernel
+            }
+        }
+    }
+}
+
+// Algorithm 1 in mixed precision for the atoms with more than kSasaStage solvation neighbours (compact
+// regions): the steps of k_sasa_mixed, with the list read from global memory (rewritten in place as
+// (o_j, h_j)) and each exchange added to the partner's fixed-point sum at once. It runs beside
+// k_sasa_mixed (a second stream), which skips these atoms; a warp per atom of the list the pair
+// kernel recorded (none, mostly: the kernel then returns at once).
+__global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed_long(const DevChain d) {
+    __shared__ unsigned short s_near[kSasaWarps][kBatch];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (d.status->done) return;
+    const int nlong = d.status->nlong;
+    for (int e = blockIdx.x * kSasaWarps + w; e < nlong; e += gridDim.x * kSasaWarps) {  // uniform in the warp
+        const int a = d.long_atoms[e];
+        {
+            if (!d.gflag[a] || d.chain_done[atom_chain(d, a)]) continue;  // written by k_sasa_mixed
+            const int cnt = min(d.nbr_cnt[a], kMaxNbr);
+            float4* ol = &d.nbr_off[(size_t)a * kMaxNbr];  // rewritten in place as (o_j, h_j)
+            const int* nl = &d.nbr[(size_t)a * kMaxNbr];
+            const float Ra = d.aprm32[a].w;
+            const float inv2R = 0.5f / Ra;
+            const float drf = d.f_dr;
+            const float gd = 1e-4f + 1.2e-5f * d.grid[atom_chain(d, a)].sf;  // guard band in Q.o units (A)
+            float rmax2 = 0.0f;
+            for (int j = lane; j < cnt; j += 32) {
+                const float4 o = ol[j];  // r_j - r_i, Roff_j^2
+                const float oo = o.x * o.x + o.y * o.y + o.z * o.z;
+                ol[j] = make_float4(o.x, o.y, o.z, (Ra * Ra + oo - o.w) * inv2R);
+                rmax2 = fmaxf(rmax2, o.w);
+            }
+            for (int q = 16; q > 0; q >>= 1) rmax2 = fmaxf(rmax2, __shfl_xor_sync(0xffffffffu, rmax2, q));
+            // band of m around 0 where a displacement by dr can change a point's state, widened to the
+            // largest neighbour radius so that it is one number per atom
+            const float band = (2.0f * drf * sqrtf(rmax2) + 3.0f * drf * drf) * inv2R + gd;
+            __syncwarp();
+            const long long qa = d.qfx[a];
+            int ncov = 0, nguard = 0, s0 = 0, s1 = 0, s2 = 0;
+            unsigned long long ntest = 0;
+            // an exchange goes to the partner's fixed-point sum at once; atom i keeps the net count
+            auto exchange = [&](int j, int s, int delta) {
+                atomicAdd((unsigned long long*)&d.Fcav[3 * nl[j] + s], (unsigned long long)(qa * delta));
+                if (s == 0) s0 += delta;
+                else if (s == 1) s1 += delta;
+                else s2 += delta;
+            };
+            auto recheck = [&](int j, int k, int s) -> bool {  // FP64, identical to the FP64 kernel
+                ++nguard;
+                const double Roa = d.aprm64[a].w, dr = d.prm.delta_r;
+                const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
+                const int b = nl[j];
+                const double ro = d.aprm64[b].w;
+                const double qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
+                const double qy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
+                const double qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
+                return covers64(qx, qy, qz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
+            };
+            for (int kb = 0; kb < d.N; kb += kBatch) {
+                float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane], mx[kPtsPerLane];
+                unsigned valid = 0;
+#pragma unroll
+                for (int p = 0; p < kPtsPerLane; ++p) {
+                    const int k = kb + lane + 32 * p;
+                    const bool v = k < d.N;
+                    const float4 qk = v ? d.Q4[k] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    qx[p] = qk.x;
+                    qy[p] = qk.y;
+                    qz[p] = qk.z;
+                    valid |= v ? (1u << p) : 0u;
+                    mx[p] = -INFINITY;
+                }
+                // step 1: the largest m of each point over all neighbours
+#pragma unroll 2
+                for (int j = 0; j < cnt; ++j) {
+                    const float4 o = ol[j];
+#pragma unroll
+                    for (int p = 0; p < kPtsPerLane; ++p) {
+                        const float m = fmaf(qz[p], o.z, fmaf(qy[p], o.y, fmaf(qx[p], o.x, -o.w)));
+                        mx[p] = fmaxf(mx[p], m);
+                    }
+                }
+                ntest += (unsigned long long)__popc(valid) * cnt;
+                // decided points are counted; the rest are listed for the re-scan
+                int nres = 0;
+                const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+                for (int p = 0; p < kPtsPerLane; ++p) {
+                    const bool v = (valid >> p) & 1u;
+                    const bool res = v && mx[p] > -band && mx[p] <= band;
+                    if (v && mx[p] > band) ++ncov;
+                    const unsigned bm = __ballot_sync(0xffffffffu, res);
+                    if (res) s_near[w][nres + __popc(bm & lt)] = (unsigned short)(lane + 32 * p);
+                    nres += __popc(bm);
+                }
+                __syncwarp();
+                // re-scan, one point at a time; lane t takes neighbours t, t + 32, ... (at most 8)
+                for (int e = 0; e < nres; ++e) {
+                    const int k = kb + s_near[w][e];
+                    const float4 qk = d.Q4[k];
+                    const float Qx = qk.x, Qy = qk.y, Qz = qk.z;
+                    unsigned inb = 0, nrb = 0;
+                    for (int r = 0; 32 * r < cnt; ++r) {
+                        const int j = 32 * r + lane;
+                        if (j < cnt) {
+                            const float4 o = ol[j];
+                            const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, -o.w)));
+                            bool in = m > 0.0f;
+                            if (fabsf(m) <= gd) in = recheck(j, k, -1);
+                            inb |= in ? (1u << r) : 0u;
+                            nrb |= fabsf(m) <= band ? (1u << r) : 0u;
+                        }
+                    }
+                    const int C = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(inb));
+                    if (lane == 0) ncov += C >= 1;
+                    // step 2 against neighbour j displaced along s; hs is h_js
+                    auto covers_s = [&](int j, int s) -> bool {
+                        const float4 o = ol[j];
+                        const float os = s == 0 ? o.x : (s == 1 ? o.y : o.z);
+                        const float Qs = s == 0 ? Qx : (s == 1 ? Qy : Qz);
+                        const float hs = o.w + (2.0f * drf * os + drf * drf) * inv2R;
+                        const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, fmaf(drf, Qs, -hs))));
+                        ++ntest;
+                        if (fabsf(m) > gd) return m >= 0.0f;
+                        return recheck(j, k, s);
+                    };
+                    if (C == 0) {  // exposed: every near neighbour may cover it once displaced
+                        for (unsigned b = nrb; b; b &= b - 1) {
+                            const int j = 32 * (__ffs(b) - 1) + lane;
+                            for (int s = 0; s < 3; ++s)
+                                if (covers_s(j, s)) exchange(j, s, 1);
+                        }
+                    } else if (C == 1 && (inb & nrb)) {  // critically overlapped by a near neighbour
+                        const int j = 32 * (__ffs(inb) - 1) + lane;
+                        for (int s = 0; s < 3; ++s)
+                            if (!covers_s(j, s)) exchange(j, s, -1);
+                    }
+                }
+                __syncwarp();
+            }
+            // counts of the warp by 32-bit reductions (each below 2^31: at most 4096 points x kMaxNbr
+            // neighbours x 3 axes); atom i's force is minus the quantum times its net exchanges
+            ncov = (int)__reduce_add_sync(0xffffffffu, (unsigned)ncov);
+            nguard = (int)__reduce_add_sync(0xffffffffu, (unsigned)nguard);
+            const unsigned nt = __reduce_add_sync(0xffffffffu, (unsigned)ntest);
+            __syncwarp();
             s0 = __reduce_add_sync(0xffffffffu, s0);
             s1 = __reduce_add_sync(0xffffffffu, s1);
             s2 = __reduce_add_sync(0xffffffffu, s2);
@@ -923,7 +1131,7 @@ __global__ void k_reset_loop(const DevChain d, int full) {
         st->last_max_dtheta = 0.0;
         if (full) {
             st->ticket_bbox = 0u;
-            st->pairs = 0; st->nbr_total = 0; st->guard = 0; st->sasa_tests = 0; st->max_nbr = 0;
+            st->pairs = 0; st->nbr_total = 0; st->guard = 0; st->sasa_tests = 0; st->max_nbr = 0; st->nlong = 0;
         }
     }
     if (c < d.nchains) {
@@ -955,7 +1163,6 @@ inline int blocks(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 void launch_init_status(DevChain& d, cudaStream_t s) { k_reset_loop<<<blocks(d.nchains, 256), 256, 0, s>>>(d, 1); }
 void launch_reset_loop(DevChain& d, cudaStream_t s) { k_reset_loop<<<blocks(d.nchains, 256), 256, 0, s>>>(d, 0); }
 
-
 void launch_binning(DevChain& d, cudaStream_t s) {
     k_bin_count<<<blocks(d.n, kBinThreads), kBinThreads, 0, s>>>(d);
     if (!d.scan_fused) {
@@ -979,23 +1186,21 @@ void launch_pairs(DevChain& d, cudaStream_t s) {
     }
 }
 
-void launch_forces(DevChain& d, cudaStream_t s) {
-    launch_pairs(d, s);
-    launch_sasa(d, s);
-}
-
 void launch_sasa(DevChain& d, cudaStream_t s) {
     if (d.prm.solvation) {
-        cudaMemsetAsync(d.Fcav, 0, sizeof(long long) * 3 * (size_t)d.n, s);
         if (d.prm.precision == KCM_MIXED)
             k_sasa_mixed<<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
         else
-            k_sasa<false><<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
+            k_sasa<<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
     }
 }
 
-
-
+void launch_sasa_long(DevChain& d, cudaStream_t s) {
+    if (!d.prm.solvation) return;
+    const int nb = std::max(1, std::min((d.n + kSasaWarps - 1) / kSasaWarps, kSasaLongBlocks));
+    if (d.prm.precision == KCM_MIXED) k_sasa_mixed_long<<<nb, kSasaWarps * 32, 0, s>>>(d);
+    else k_sasa_long<<<nb, kSasaWarps * 32, 0, s>>>(d);
+}
 
 void launch_force_out(DevChain& d, cudaStream_t s) { k_force_out<<<blocks(3LL * d.n, 256), 256, 0, s>>>(d); }
 

@@ -28,9 +28,9 @@
 
 namespace {
 
-// device bytes per atom and per joint of a batch (neighbour lists dominate: 128 entries of 20 B per
-// atom), used to admit jobs before their batch exists; the true size is read back after creation
-constexpr int64_t kBytesPerAtom = 3000;
+// device bytes per atom and per joint of a batch (neighbour lists dominate: kMaxNbr entries of 20 B
+// per atom), used to admit jobs before their batch exists; the true size is read back after creation
+constexpr int64_t kBytesPerAtom = 20 * kcm::kMaxNbr + 700;
 constexpr int64_t kBytesPerJoint = 400;
 constexpr int64_t kBytesPerBatch = 8 << 20;
 
