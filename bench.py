@@ -46,7 +46,7 @@ FLOPS_PER_PAIR = 31      # per unordered pair within the cutoff (distance, 1/d^2
 BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques_step": 60}  # algorithmic HBM bytes per atom
 # DRAM bytes (read + write) per launch of the stage's kernels on this workload, from one ncu capture
 # of the current kernels (profiles/k_sasa_mixed_chain1000.md); None where not captured
-DRAM_BYTES_PER_LAUNCH = {"solvation": 6.92e6}
+DRAM_BYTES_PER_LAUNCH = {"solvation": 6.84e6}
 KERNELS_PER_ITERATION = {1: 9, 0: 8}  # reset + kinematics 2 + binning 2 + pairs 1 + solvation 1 + wrench-tile 1 + torque-step 1
 
 
