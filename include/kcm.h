@@ -305,6 +305,14 @@ int kcm_step_status(kcm_handle h, int32_t* iters_done, double* max_dtheta);
 
 int kcm_get_stats(kcm_handle h, kcm_stats* st);
 
+/* Joints held fixed (Sec. 4.1: the user may fix as many dihedral angles as desired, so that groups of
+ * residues such as secondary elements or domains move as rigid bodies and only the loops between
+ * them deform). fixed[l] (l = kcm_njoints; a batch's joints in chain order): nonzero holds the joint.
+ * A fixed joint takes no step; its torque is still computed (kcm_torques), but it has no part in the
+ * normalised step's max |tau| nor in the convergence test (max |dtheta| over the moved joints).
+ * NULL clears all flags (the default). Synchronises. Errors: KCM_E_INVAL (l does not match). */
+int kcm_set_fixed_joints(kcm_handle h, const uint8_t* fixed, int64_t l);
+
 /* Cell-edge autotuner. For each candidate edge (A; meaning as kcm_params.cell_size, so 0 is the
  * smallest 27-cell edge) evaluate the chain (forces and torques at the current theta, no step:
  * theta is not changed) once to warm up and then `reps` times, timed with CUDA events on the

@@ -65,11 +65,11 @@ def lib():
             L.orc_sasa_bruteforce.argtypes = [C.c_int, _dp, _dp, _dp, C.c_int, _dp, C.c_double, _dp, _dp, _ip, _ip]
             L.orc_torques_columns.argtypes = [C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp]
             L.orc_torques_rowscan.argtypes = [C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp]
-            L.orc_step.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_void_p]
+            L.orc_step.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p]
             L.orc_step.restype = C.c_double
             L.orc_evaluate.argtypes = [C.c_void_p, _dp, _dp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
-            L.orc_run.argtypes = [C.c_void_p, _dp, _dp, C.c_int, C.c_void_p, C.c_void_p]
+            L.orc_run.argtypes = [C.c_void_p, _dp, _dp, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_run.restype = C.c_int
             L.orc_grow_start.argtypes = [C.c_void_p, C.c_ulonglong, C.c_double, C.c_int, C.c_int, C.c_void_p]
             L.orc_grow_start.restype = C.c_int
@@ -160,10 +160,21 @@ def sasa_bruteforce(xyz, Roff, gamma, Q, dr):
     return dict(F=F, E_atom=Ea, covered=cov, dcount=dcount.reshape(n, n, 3))
 
 
-def step(theta, tau, kappa, dmax, mode=0):
+def _mask(fixed, l):
+    """Joints held fixed as a uint8 array [l] (None: none), kept alive by the caller."""
+    if fixed is None:
+        return None
+    m = np.ascontiguousarray(fixed, dtype=np.uint8)
+    assert m.shape == (l,)
+    return m
+
+
+def step(theta, tau, kappa, dmax, mode=0, fixed=None):
     th = np.array(theta, dtype=np.float64)
     d = np.zeros_like(th)
-    dm = lib().orc_step(len(th), th, np.ascontiguousarray(tau, dtype=np.float64), kappa, dmax, mode, _ptr(d))
+    m = _mask(fixed, len(th))
+    dm = lib().orc_step(len(th), th, np.ascontiguousarray(tau, dtype=np.float64), kappa, dmax, mode, _ptr(d),
+                        None if m is None else _ptr(m))
     return th, d, dm
 
 
@@ -271,10 +282,13 @@ class OracleChain:
             raise RuntimeError("start growth ran out of attempts")
         return codes
 
-    def run(self, params, theta, n_iters):
-        """The KCM loop; returns (theta, iterations taken, E trace [it,3], max|dtheta| trace)."""
+    def run(self, params, theta, n_iters, fixed=None):
+        """The KCM loop; returns (theta, iterations taken, E trace [it,3], max|dtheta| trace).
+        fixed: joints held fixed (uint8 [l]), None for none."""
         th = np.array(theta, dtype=np.float64)
         Et = np.zeros((n_iters, 3))
         dt = np.zeros(n_iters)
-        it = lib().orc_run(self._h, run_params(params), th, int(n_iters), _ptr(Et), _ptr(dt))
+        m = _mask(fixed, self.l)
+        it = lib().orc_run(self._h, run_params(params), th, int(n_iters), _ptr(Et), _ptr(dt),
+                           None if m is None else _ptr(m))
         return th, int(it), Et[:it], dt[:it]

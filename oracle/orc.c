@@ -972,13 +972,18 @@ void orc_torques_rowscan(int n, int l, const int* link, const double* xyz, const
 /* ---------------------------------------------------------------- kinetostatic step */
 /* mode 0: dtheta_k = clamp(kappa tau_k, -dmax, +dmax); mode 1: the paper's normalised step
  * dtheta_k = kappa tau_k / max_j |tau_j| (eq. KCM_07). theta_{t+1} = theta_t + dtheta (Sec. 3.1).
+ * fixed (may be NULL): joints held fixed (Sec. 4.1, the option of fixing dihedral angles so that
+ * groups of residues move as rigid bodies); they take no step and do not enter max_j |tau_j|.
  * Returns max_k |dtheta_k|. */
-double orc_step(int l, double* theta, const double* tau, double kappa, double dmax, int mode, double* dtheta) {
+double orc_step(int l, double* theta, const double* tau, double kappa, double dmax, int mode, double* dtheta,
+                const unsigned char* fixed) {
     double tmax = 0.0, dm = 0.0;
-    for (int k = 0; k < l; k++) tmax = fmax(tmax, fabs(tau[k]));
+    for (int k = 0; k < l; k++)
+        if (!(fixed && fixed[k])) tmax = fmax(tmax, fabs(tau[k]));
     for (int k = 0; k < l; k++) {
         double d;
-        if (mode == 1) d = tmax > 0.0 ? kappa * tau[k] / tmax : 0.0;
+        if (fixed && fixed[k]) d = 0.0;
+        else if (mode == 1) d = tmax > 0.0 ? kappa * tau[k] / tmax : 0.0;
         else {
             d = kappa * tau[k];
             if (d > dmax) d = dmax;
@@ -1042,9 +1047,10 @@ void orc_evaluate(void* p, const double* prm, const double* theta, double* xyz, 
 }
 
 /* The KCM loop (Sec. 4.1 steps 4-9): evaluate, step, stop once max |dtheta| < conv_tol.
- * theta is updated in place; E_trace [n_iters*3] and dmax_trace [n_iters] are optional.
- * Returns the number of iterations taken. */
-int orc_run(void* p, const double* prm, double* theta, int n_iters, double* E_trace, double* dmax_trace) {
+ * theta is updated in place; E_trace [n_iters*3], dmax_trace [n_iters] and fixed [l] (joints held
+ * fixed) are optional. Returns the number of iterations taken. */
+int orc_run(void* p, const double* prm, double* theta, int n_iters, double* E_trace, double* dmax_trace,
+            const unsigned char* fixed) {
     Chain* c = (Chain*)p;
     int l = 2 * c->m;
     double* tau = (double*)malloc(sizeof(double) * l);
@@ -1052,7 +1058,7 @@ int orc_run(void* p, const double* prm, double* theta, int n_iters, double* E_tr
     for (it = 0; it < n_iters; it++) {
         double E[3];
         orc_evaluate(p, prm, theta, NULL, NULL, NULL, tau, E, NULL, NULL);
-        double dm = orc_step(l, theta, tau, prm[7], prm[8], (int)prm[12], NULL);
+        double dm = orc_step(l, theta, tau, prm[7], prm[8], (int)prm[12], NULL, fixed);
         if (E_trace) memcpy(&E_trace[3 * it], E, sizeof E);
         if (dmax_trace) dmax_trace[it] = dm;
         if (dm < prm[9]) { it++; break; }

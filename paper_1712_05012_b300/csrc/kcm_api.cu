@@ -400,7 +400,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.chain_err, hc.nchains)) || (rc = dalloc(h, &d.chain_maxdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_maxtau, hc.nchains)) || (rc = dalloc(h, &d.chain_lastdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_E, 3 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.gseg, l)) ||
-        (rc = dalloc(h, &d.jhead, l)) || (rc = dalloc(h, &d.lflag, L)) ||
+        (rc = dalloc(h, &d.jhead, l)) || (rc = dalloc(h, &d.jfixed, l)) || (rc = dalloc(h, &d.lflag, L)) ||
         (rc = dalloc(h, &d.tileF, d.ntiles)) || (rc = dalloc(h, &d.ltail, L)) || (rc = dalloc(h, &d.tileT, d.ltiles)))
         return bail(rc);
 
@@ -454,6 +454,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         return bail(rc);
     if ((rc = set_cell_size(h, prm->cell_size))) return bail(rc);  // cell caps and arrays
     e = cudaMemsetAsync(d.theta, 0, sizeof(double) * l, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.jfixed, 0, l, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.Fcav, 0, sizeof(long long) * 3 * nn, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.covered, 0, sizeof(int) * nn, h->stream);
     if (e != cudaSuccess) { cuda_fail(h, e, "memset"); return bail(KCM_E_CUDA); }
@@ -512,6 +513,16 @@ int kcm_set_chain_max_iters(kcm_handle h, const int32_t* max_iters) {
 }
 
 int64_t kcm_device_bytes(kcm_handle h) { return h ? static_cast<int64_t>(h->bytes) : -1; }
+
+int kcm_set_fixed_joints(kcm_handle h, const uint8_t* fixed, int64_t l) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (fixed && l != h->d.l) return set_err(h, KCM_E_INVAL, "fixed must hold one flag per joint");
+    std::vector<unsigned char> m(h->d.l, 0);
+    if (fixed)
+        for (int j = 0; j < h->d.l; ++j) m[j] = fixed[j] ? 1 : 0;
+    int rc = upload(h, h->d.jfixed, m.data(), m.size());
+    return rc ? rc : sync(h);
+}
 
 int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta, int32_t* errors) {
     if (check_handle(h)) return KCM_E_INVAL;

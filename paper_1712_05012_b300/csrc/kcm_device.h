@@ -168,6 +168,7 @@ struct DevChain {
     double* chain_lastdt = nullptr;              // max |dtheta| of the chain's last step
     double* chain_E = nullptr;     // Coulomb, LJ, solvation energies [nchains * 3]
     unsigned char* jhead = nullptr;  // the joint is the first of its chain [l]
+    unsigned char* jfixed = nullptr; // the joint is held fixed: it takes no step (kcm_set_fixed_joints) [l]
     unsigned char* lflag = nullptr;  // 1: a chain's base link (no joint), 2: the last link of a chain [L]
     unsigned char* gseg = nullptr; // FK: a chain starts in the joint's scan block at or before it [l]
     int* tileF = nullptr;          // FK: a chain starts in the scan block [ntiles]

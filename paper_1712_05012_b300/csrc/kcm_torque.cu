@@ -309,12 +309,13 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
         d.tau[jj] = t;
         bad = !isfinite(t);
         if (bad) atomicOr(&d.chain_err[cj], kErrNonfinite);
-        atau = (unsigned long long)__double_as_longlong(fabs(t));
+        const bool fx = d.jfixed[jj] != 0;  // a fixed joint takes no step and has no say in max |tau|
+        atau = fx ? 0ULL : (unsigned long long)__double_as_longlong(fabs(t));
         if (d.chain_done[cj] || d.chain_err[cj]) {
             cj = -1;  // a converged or failed chain takes no more steps
         } else if (STEP && !bad) {
-            const double dt = fmin(fmax(d.prm.kappa * t, -d.prm.dtheta_max), d.prm.dtheta_max);
-            d.theta[jj] += dt;
+            const double dt = fx ? 0.0 : fmin(fmax(d.prm.kappa * t, -d.prm.dtheta_max), d.prm.dtheta_max);
+            if (!fx) d.theta[jj] += dt;
             d.dtheta[jj] = dt;
             adt = (unsigned long long)__double_as_longlong(fabs(dt));
         }
@@ -332,7 +333,8 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
     close_iteration(d, st);
 }
 
-// the paper's normalised step (eq. KCM_07): dtheta_k = kappa tau_k / max |tau| over the joint's chain
+// the paper's normalised step (eq. KCM_07): dtheta_k = kappa tau_k / max |tau| over the free joints of
+// the joint's chain (a fixed joint takes none)
 __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
     __shared__ bool last;
     Status* st = d.status;
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
             cj = -1;
         } else {
             const double tm = __longlong_as_double((long long)__ldcg(&d.chain_maxtau[cj]));
-            const double dt = tm > 0.0 ? d.prm.kappa * d.tau[jj] / tm : 0.0;
+            const double dt = (tm > 0.0 && !d.jfixed[jj]) ? d.prm.kappa * d.tau[jj] / tm : 0.0;
             d.theta[jj] += dt;
             d.dtheta[jj] = dt;
             adt = (unsigned long long)__double_as_longlong(fabs(dt));

@@ -74,6 +74,7 @@ EXPORTS = [
     "kcm_create_batch", "kcm_nchains", "kcm_chain_offsets", "kcm_chain_energies", "kcm_chain_state",
     "kcm_set_chain_max_iters", "kcm_device_bytes", "kcm_server_create", "kcm_server_destroy", "kcm_server_submit",
     "kcm_server_tick", "kcm_server_poll", "kcm_server_job", "kcm_server_device_bytes", "kcm_autotune_cell",
+    "kcm_set_fixed_joints",
 ]
 AUTOTUNE_MAX = 64
 # candidate cell edges of the autotuner (A): 0 is the smallest 27-cell edge; edges below the largest
@@ -119,6 +120,7 @@ def load():
             "kcm_step_status": (C.c_int, [h, _ip, _dp]),
             "kcm_get_stats": (C.c_int, [h, C.POINTER(Stats)]),
             "kcm_autotune_cell": (C.c_int, [h, _dp, C.c_int32, C.c_int32, _dp, _dp]),
+            "kcm_set_fixed_joints": (C.c_int, [h, C.c_void_p, C.c_int64]),
             "kcm_stream": (C.c_void_p, [h]),
             "kcm_sample_points": (C.c_int, [C.c_int32, _dp]),
             "kcm_build_zp": (C.c_int, [C.POINTER(Topology), _dp, _ip, C.c_int64]),
@@ -366,6 +368,16 @@ class Chain:
         tot = C.c_float()
         _check(load().kcm_step_timed(self._h, st, NUM_STAGES, C.byref(tot)), self._h)
         return float(tot.value), dict(zip(STAGES, [float(x) for x in st]))
+
+    def set_fixed_joints(self, fixed=None):
+        """Hold the joints flagged in fixed [l] (None releases all): they take no step."""
+        if fixed is None:
+            _check(load().kcm_set_fixed_joints(self._h, None, self.l), self._h)
+        else:
+            m = np.ascontiguousarray(fixed, dtype=np.uint8)
+            if m.shape != (self.l,):
+                raise ValueError(f"fixed must have {self.l} entries")
+            _check(load().kcm_set_fixed_joints(self._h, m.ctypes.data_as(C.c_void_p), self.l), self._h)
 
     def autotune_cell(self, candidates=CELL_CANDIDATES, reps: int = 3):
         """Time an evaluation at each candidate cell edge and keep the fastest: (chosen, times_ms)."""

@@ -245,40 +245,24 @@ def test_chain8000_cut12_sampled(kcm, table):
     assert got["stats"]["pairs"] == ref["stats"]["pairs"]
 
 
-def serve_start(i):
-    """Job i of the stored serving pool: sequence and compact start."""
-    man = json.load(open(os.path.join(GOLDEN, "starts.json")))["serve256"]
-    lens = man["residues"]
-    codes = np.load(os.path.join(GOLDEN, "start_serve256.npy"))
-    off = 2 * sum(lens[:i])
-    wl = synth.workload(5)
-    return synth.sequence(lens[i], synth.chain_seed(wl.seed, i)), synth.theta_from_codes(codes[off:off + 2 * lens[i]])
-
-
 def test_long_neighbour_lists(kcm, table):
-    """A 1,772-residue chain from the serving pool, stepped until its densest atoms have more solvation
-    neighbours than the solvation kernels stage in shared memory (128): those atoms are taken by the
-    long-list kernels beside the main ones. FP64 against the oracle, mixed classifications and
-    exchange sums equal to FP64's."""
-    seq, th = serve_start(128)
-    pf = synth.RunParams(precision=synth.PRECISION_FP64)
-    pm = synth.RunParams(precision=synth.PRECISION_MIXED)
-    with kcm.Chain(seq, table, pm) as ch:  # the chain compacts as it steps: run it until a list is long
-        ch.set_theta(th)
-        for _ in range(40):
-            ch.step(5)
-            if ch.stats()["max_neighbors"] > 128:
-                break
-        th = ch.get_theta()
+    """Lists longer than the solvation kernels stage in shared memory (128): the 1,000-residue compact
+    start with a 3.2 A solvent probe gives 88 atoms with gamma != 0 more than 128 solvation neighbours
+    (largest 168). They are taken by the long-list kernels beside the main ones. FP64 against the
+    oracle; mixed classifications and exchange sums equal to FP64's."""
+    seq, th = start("chain1000")
     och = O.OracleChain(seq, table, synth.GEOMETRY)
+    pf = synth.RunParams(precision=synth.PRECISION_FP64, r_probe=3.2)
+    pm = synth.RunParams(precision=synth.PRECISION_MIXED, r_probe=3.2)
     ref = och.evaluate(pf, th)
     f64 = gpu_eval(kcm, seq, table, pf, th)
     mix = gpu_eval(kcm, seq, table, pm, th)
-    assert f64["stats"]["max_neighbors"] > 128
+    assert f64["stats"]["max_neighbors"] == 168
     g = och.gamma != 0
     assert np.array_equal(f64["covered"][g], ref["covered"][g])
     assert rel_inf(f64["F_cav"], ref["F_cav"]) < TOL_FP64
     assert rel_inf(f64["tau"], ref["tau"]) < TOL_FP64
+    np.testing.assert_allclose(f64["E"], ref["E"], rtol=TOL_FP64, atol=1e-9)
     assert np.array_equal(mix["covered"], f64["covered"])
     assert np.array_equal(mix["F_cav"], f64["F_cav"])
     assert rel_inf(mix["tau"], ref["tau"]) < TOL_MIXED

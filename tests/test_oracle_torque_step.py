@@ -76,6 +76,49 @@ def test_step_clamp_and_normalised():
     assert dm == pytest.approx(0.05)
 
 
+def test_step_with_fixed_joints():
+    """Sec. 4.1: fixed dihedral angles take no step, and the normalised step's max |tau| runs over
+    the free joints only (here 5.0, not 100.0)."""
+    tau = np.array([5.0, -40.0, 0.001, 100.0, -3.0])
+    th0 = np.array([0.1, 0.2, 0.3, 0.4, 0.5])
+    fixed = [0, 1, 0, 1, 0]
+    th, d, dm = O.step(th0, tau, 1e-3, 0.02, mode=0, fixed=fixed)
+    assert np.array_equal(d, [0.005, 0.0, 1e-6, 0.0, -0.003])
+    assert th[1] == th0[1] and th[3] == th0[3]
+    assert dm == 0.005
+    th, d, dm = O.step(th0, tau, 0.05, 0.02, mode=1, fixed=fixed)
+    assert np.allclose(d, [0.05, 0.0, 1e-5, 0.0, -0.03], rtol=1e-15, atol=0)
+    assert dm == pytest.approx(0.05)
+
+
+def test_fixed_domain_moves_rigidly(table):
+    """Fixing every joint between links 8 and 20 makes those links one rigid body: after a run the
+    distances between their atoms are unchanged, while the free joints moved. A property of the
+    kinematics, independent of the step rule."""
+    m = 15
+    seq = synth.sequence(m, 21)
+    ch = O.OracleChain(seq, table, synth.GEOMETRY)
+    th0 = synth.theta_from_codes(ch.grow_start(5))
+    fixed = np.zeros(ch.l, dtype=np.uint8)
+    fixed[8:20] = 1  # joints 8 .. 19 join links 8 .. 20
+    p = synth.RunParams(solvation=0)
+    th, it, _, _ = ch.run(p, th0, 10, fixed=fixed)
+    assert it == 10
+    assert np.array_equal(th[8:20], th0[8:20])
+    assert np.max(np.abs(th - th0)) > 1e-4
+    x0, _, _ = ch.fk(th0)
+    x1, _, _ = ch.fk(th)
+    g = (ch.link >= 8) & (ch.link <= 20)
+    d0 = np.linalg.norm(x0[g][:, None] - x0[g][None], axis=-1)
+    d1 = np.linalg.norm(x1[g][:, None] - x1[g][None], axis=-1)
+    assert np.max(np.abs(d1 - d0)) < 1e-10
+    # without the mask the same links deform
+    th2, _, _, _ = ch.run(p, th0, 10)
+    x2, _, _ = ch.fk(th2)
+    d2 = np.linalg.norm(x2[g][:, None] - x2[g][None], axis=-1)
+    assert np.max(np.abs(d2 - d0)) > 1e-3
+
+
 def test_run_stops_on_convergence(table):
     m = 6
     seq = synth.sequence(m, 8)
