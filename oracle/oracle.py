@@ -65,6 +65,8 @@ def lib():
             L.orc_sasa_bruteforce.argtypes = [C.c_int, _dp, _dp, _dp, C.c_int, _dp, C.c_double, _dp, _dp, _ip, _ip]
             L.orc_torques_columns.argtypes = [C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp]
             L.orc_torques_rowscan.argtypes = [C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp]
+            L.orc_sasa_pairwise.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp]
+            L.orc_sasa_pairwise.restype = None
             L.orc_step.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p]
             L.orc_step.restype = C.c_double
             L.orc_evaluate.argtypes = [C.c_void_p, _dp, _dp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -145,6 +147,17 @@ def sasa(xyz, Roff, gamma, Q, dr, literal_break=False, want_counts=False):
     if want_counts:
         out.update(cand_start=cs, cand=cand[:cs[-1]], counts=cnt[:3 * cs[-1]].reshape(-1, 3))
     return out
+
+
+def sasa_pairwise(xyz, Roff, gamma):
+    """The pairwise solvation surrogate: returns (F [n,3], E_atom [n])."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    F = np.zeros((n, 3))
+    Ea = np.zeros(n)
+    lib().orc_sasa_pairwise(n, xyz.reshape(-1), np.ascontiguousarray(Roff, dtype=np.float64),
+                            np.ascontiguousarray(gamma, dtype=np.float64), F.reshape(-1), Ea)
+    return F, Ea
 
 
 def sasa_bruteforce(xyz, Roff, gamma, Q, dr):

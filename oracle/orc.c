@@ -969,6 +969,79 @@ void orc_torques_rowscan(int n, int l, const int* link, const double* xyz, const
     free(P);
 }
 
+/* ---------------------------------------------------------------- pairwise solvation surrogate */
+/* The smooth pairwise approximation of the solvent-accessible area that preceded surface enumeration
+ * (Sec. 3.4: probabilistic pairwise formulae): the exposed area of atom i is
+ *   A_i = S_i prod_{j != i} (1 - b_ij / S_i),   S_i = 4 pi Roff_i^2,
+ * with b_ij the area of the offset sphere of i inside that of j,
+ *   b_ij = pi Roff_i (Roff_i + Roff_j - d) (1 + (Roff_j - Roff_i) / d)   for d < Roff_i + Roff_j,
+ * clamped to [0, S_i] (j inside i: 0; i inside j: S_i), and every overlap parameter of the
+ * probabilistic formulae equal to 1. Energy G^cav = sum_i gamma_i A_i (eq. 04 with the areas A_i).
+ * Forces are the exact negative gradient: with c_ij = dE_i/dd_ij = E_i (-db_ij/dd) / (S_i f_ij),
+ * f_ij = 1 - b_ij/S_i and -db/dd = pi Roff_i (1 + (Roff_j^2 - Roff_i^2) / d^2), the pair (i, j)
+ * adds c_ij e_ij to F_i and -c_ij e_ij to F_j, e_ij = (r_j - r_i) / d. Where a factor is clamped
+ * (f_ij = 0 or b_ij = 0 inside the overlap range) its derivative is taken as 0.
+ * Inputs: centres xyz [n*3], Roff [n], gamma [n]; outputs F [n*3], E_atom [n] (may be NULL). */
+static double pw_dist(const double* a, const double* b) {
+    const double x = a[0] - b[0], y = a[1] - b[1], z = a[2] - b[2];
+    return sqrt(x * x + y * y + z * z);
+}
+
+void orc_sasa_pairwise(int n, const double* xyz, const double* Roff, const double* gamma, double* F, double* E_atom) {
+    memset(F, 0, sizeof(double) * 3 * n);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int i = 0; i < n; i++) {
+        const double Ri = Roff[i], Si = 4.0 * ORC_PI * Ri * Ri;
+        double A = Si;
+        for (int j = 0; j < n; j++) {
+            if (j == i) continue;
+            const double d = pw_dist(&xyz[3 * i], &xyz[3 * j]);
+            if (d >= Ri + Roff[j]) continue;
+            double b = ORC_PI * Ri * (Ri + Roff[j] - d) * (1.0 + (Roff[j] - Ri) / d);
+            if (b < 0.0) b = 0.0;
+            double f = 1.0 - b / Si;
+            if (f < 0.0) f = 0.0;
+            A *= f;
+        }
+        if (E_atom) E_atom[i] = gamma[i] * A;
+    }
+    /* forces: a second pass needs every A_i; E_i = gamma_i A_i (serial over i: each pair writes to j) */
+    for (int i = 0; i < n; i++) {
+        const double Ri = Roff[i], Si = 4.0 * ORC_PI * Ri * Ri;
+        double A = Si;
+        int clamped = 0;
+        for (int j = 0; j < n; j++) {
+            if (j == i) continue;
+            const double d = pw_dist(&xyz[3 * i], &xyz[3 * j]);
+            if (d >= Ri + Roff[j]) continue;
+            double b = ORC_PI * Ri * (Ri + Roff[j] - d) * (1.0 + (Roff[j] - Ri) / d);
+            if (b < 0.0) b = 0.0;
+            double f = 1.0 - b / Si;
+            if (f <= 0.0) { clamped = 1; f = 0.0; }
+            A *= f;
+        }
+        const double Ei = gamma[i] * A;
+        if (Ei == 0.0 || clamped) continue;
+        for (int j = 0; j < n; j++) {
+            if (j == i) continue;
+            const double d = pw_dist(&xyz[3 * i], &xyz[3 * j]);
+            if (d >= Ri + Roff[j]) continue;
+            const double b = ORC_PI * Ri * (Ri + Roff[j] - d) * (1.0 + (Roff[j] - Ri) / d);
+            if (b <= 0.0) continue;  /* j inside i: no burial, no derivative */
+            const double f = 1.0 - b / Si;
+            const double mdb = ORC_PI * Ri * (1.0 + (Roff[j] * Roff[j] - Ri * Ri) / (d * d));
+            const double cij = Ei * mdb / (Si * f);
+            for (int x = 0; x < 3; x++) {
+                const double e = (xyz[3 * j + x] - xyz[3 * i + x]) / d;
+                F[3 * i + x] += cij * e;
+                F[3 * j + x] -= cij * e;
+            }
+        }
+    }
+}
+
 /* ---------------------------------------------------------------- kinetostatic step */
 /* mode 0: dtheta_k = clamp(kappa tau_k, -dmax, +dmax); mode 1: the paper's normalised step
  * dtheta_k = kappa tau_k / max_j |tau_j| (eq. KCM_07). theta_{t+1} = theta_t + dtheta (Sec. 3.1).
@@ -1016,7 +1089,16 @@ void orc_evaluate(void* p, const double* prm, const double* theta, double* xyz, 
     long long npairs = orc_pair_forces_chain(p, X, pprm, Fp, Ep);
     double Ecav = 0.0;
     long long st[3] = {0, 0, 0};
-    if (prm[10] != 0.0) {
+    if (prm[10] == 2.0) {  /* the pairwise surrogate */
+        double* Roff = (double*)malloc(sizeof(double) * n);
+        double* gam = (double*)malloc(sizeof(double) * n);
+        double* Ea = (double*)malloc(sizeof(double) * n);
+        for (int a = 0; a < n; a++) { Roff[a] = c->R[a] + prm[5]; gam[a] = gamma_of_class(c->cls[a]); }
+        orc_sasa_pairwise(n, X, Roff, gam, Fc, Ea);
+        for (int a = 0; a < n; a++) Ecav += Ea[a];
+        if (covered) memset(covered, 0, sizeof(int) * n);
+        free(Roff); free(gam); free(Ea);
+    } else if (prm[10] != 0.0) {
         double* Roff = (double*)malloc(sizeof(double) * n);
         double* gam = (double*)malloc(sizeof(double) * n);
         double* Ea = (double*)malloc(sizeof(double) * n);
