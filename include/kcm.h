@@ -117,7 +117,10 @@ typedef struct {
  * atom's cell; an edge below rmax switches the pair search to the 125 cells two cells out, and
  * is raised to rmax / 2 plus a rounding margin if smaller; a grid that would exceed its cell cap
  * is coarsened);
- * n_sample: sample points per offset sphere N; solvation: 0/1; precision: KCM_FP64/KCM_MIXED;
+ * n_sample: sample points per offset sphere N; solvation: 0 off, 1 surface enumeration (Algorithm 1),
+ * 2 the pairwise surrogate that preceded it (Sec. 3.4: A_i = S_i prod_j (1 - b_ij / S_i), b_ij the
+ * area of offset sphere i inside offset sphere j, S_i = 4 pi Roff_i^2; smooth, with exact gradient
+ * forces); precision: KCM_FP64/KCM_MIXED;
  * step_mode: KCM_STEP_CLAMP/KCM_STEP_NORMALIZED. */
 typedef struct {
     double cutoff;
@@ -289,7 +292,8 @@ int kcm_torques_dev(kcm_handle h, double* tau_dev, int64_t l);
 int kcm_energy(kcm_handle h, double E[3]);
 
 /* Covered sample counts per atom (f_i = 1 - covered_i / N, Sec. 3.4), int32[n]. Atoms with
- * gamma = 0 contribute neither energy nor force and are not enumerated: their count reads 0. */
+ * gamma = 0 contribute neither energy nor force and are not enumerated: their count reads 0; with
+ * the pairwise surrogate (solvation = 2) nothing is enumerated and every count reads 0. */
 int kcm_sasa_counts(kcm_handle h, int32_t* covered, int64_t n);
 
 /* Run up to n_iters KCM iterations from the current theta (evaluate, then theta += dtheta); stop

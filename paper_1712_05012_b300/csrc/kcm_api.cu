@@ -329,7 +329,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         h->own_stream = true;
     }
 
-    if (prm->solvation) {
+    if (prm->solvation == 1) {
         e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
@@ -388,7 +388,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.gflag, nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||
         (rc = dalloc(h, &d.nbr, nn * kcm::kMaxNbr)) || (rc = dalloc(h, &d.nbr_off, nn * kcm::kMaxNbr)) ||
         (rc = dalloc(h, &d.covered, nn)) || (rc = dalloc(h, &d.long_atoms, nn)) || (rc = dalloc(h, &d.epair, 2 * nn)) || (rc = dalloc(h, &d.pstat, nn)) ||
-        (rc = dalloc(h, &d.sstat, nn)) ||
+        (rc = dalloc(h, &d.sstat, nn)) || (rc = dalloc(h, &d.esolv, nn)) ||
         (rc = dalloc(h, &d.lane_suf, 6 * (size_t)L)) || (rc = dalloc(h, &d.tileS, 6 * (size_t)d.ltiles)) ||
         (rc = dalloc(h, &d.tileSuf, 6 * (size_t)d.ltiles)) ||
         (rc = dalloc(h, &d.Ftot, 3 * nn)) || (rc = dalloc(h, &d.Fcav64, 3 * nn)) ||

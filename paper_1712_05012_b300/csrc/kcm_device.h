@@ -150,6 +150,7 @@ struct DevChain {
     double* epair = nullptr;       // Coulomb and LJ energy of the atom's pairs [n*2] (mixed: a float pair per atom)
     int2* pstat = nullptr;         // pair kernel: pairs counted, guard-band re-decisions [n]
     int2* sstat = nullptr;         // Algorithm 1: overlap tests, guard-band re-decisions [n]
+    double* esolv = nullptr;       // pairwise solvation surrogate: energy gamma_i A_i of each atom [n]
     // batches: chain of each atom, joint and link; joint offsets; per-chain cell caps, bounding
     // boxes (order-preserving keys: min x, y, z then max x, y, z), loop state and energies
     int nchains = 1;

@@ -60,7 +60,7 @@ int validate_params(const kcm_params* p, std::string* err) {
     if (p->n_sample < 1 || p->n_sample > kMaxSample) { *err = "n_sample must be in [1, 4096]"; return KCM_E_INVAL; }
     if (p->precision != KCM_FP64 && p->precision != KCM_MIXED) { *err = "bad precision"; return KCM_E_INVAL; }
     if (p->step_mode != KCM_STEP_CLAMP && p->step_mode != KCM_STEP_NORMALIZED) { *err = "bad step_mode"; return KCM_E_INVAL; }
-    if (p->solvation != 0 && p->solvation != 1) { *err = "solvation must be 0 or 1"; return KCM_E_INVAL; }
+    if (p->solvation < 0 || p->solvation > 2) { *err = "solvation must be 0, 1 or 2"; return KCM_E_INVAL; }
     return KCM_OK;
 }
 

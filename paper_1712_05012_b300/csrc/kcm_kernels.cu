@@ -1116,6 +1116,120 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed_long(const DevCh
     }
 }
 
+// ================================================================ pairwise solvation surrogate
+// The smooth pairwise area approximation of Sec. 3.4 (solvation = 2): A_i = S_i prod_j f_ij with
+// f_ij = 1 - b_ij / S_i, b_ij = pi Roff_i (Roff_i + Roff_j - d) (1 + (Roff_j - Roff_i) / d) (the area of
+// sphere i inside sphere j, clamped to [0, S_i]), S_i = 4 pi Roff_i^2, E_i = gamma_i A_i. One warp per
+// atom with gamma != 0, lanes over its solvation neighbours: pass 1 forms the product, pass 2 the pair
+// forces c_ij e_ij (c_ij = E_i pi Roff_i (1 + (Roff_j^2 - Roff_i^2) / d^2) / (S_i f_ij), e_ij the unit
+// vector from i to j), added to F_i and subtracted from F_j in the int64 fixed point of the solvation
+// sums (2^-40), so they cancel exactly. A clamped factor (f_ij = 0: i inside j) zeroes E_i and its
+// forces; j inside i buries nothing. Mixed mode: FP32 on the list offsets, the overlap decision
+// d < Roff_i + Roff_j re-decided in FP64 inside the guard band (the force jumps there).
+template <bool MIXED>
+__global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_pw(const DevChain d) {
+    typedef typename std::conditional<MIXED, float, double>::type R;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a = blockIdx.x * kSasaWarps + w;
+    if (a >= d.n || d.status->done) return;
+    if (d.chain_done[atom_chain(d, a)] || !d.gflag[a]) {
+        if (lane == 0) { d.esolv[a] = 0.0; d.covered[a] = 0; d.sstat[a] = make_int2(0, 0); }
+        return;
+    }
+    const int cnt = min(d.nbr_cnt[a], kMaxNbr);
+    const int* nl = &d.nbr[(size_t)a * kMaxNbr];
+    const float4* ol = &d.nbr_off[(size_t)a * kMaxNbr];
+    const R Ri = MIXED ? (R)d.aprm32[a].w : (R)d.aprm64[a].w;
+    const R Si = (R)(4.0 * 3.14159265358979323846) * Ri * Ri;
+    const R kPi = (R)3.14159265358979323846;
+    const float gp = d.grid[atom_chain(d, a)].gpf;
+    int nguard = 0;
+    // neighbour j: offset r_j - r_i, Roff_j, and whether the spheres overlap (d < Roff_i + Roff_j)
+    auto geom = [&](int j, R& ox, R& oy, R& oz, R& d2, R& Rj) -> bool {
+        const int b = nl[j];
+        if constexpr (MIXED) {
+            const float4 o = ol[j];
+            ox = o.x; oy = o.y; oz = o.z;
+            Rj = sqrtf(o.w);
+            d2 = ox * ox + oy * oy + oz * oz;
+            const float s = Ri + Rj;
+            if (fabsf(d2 - s * s) > gp) return d2 < s * s;
+            ++nguard;  // guard band: the FP64 decision of the FP64 path
+        } else {
+            ox = d.r[3 * b] - d.r[3 * a]; oy = d.r[3 * b + 1] - d.r[3 * a + 1]; oz = d.r[3 * b + 2] - d.r[3 * a + 2];
+            Rj = d.aprm64[b].w;
+            d2 = ox * ox + oy * oy + oz * oz;
+            return d2 < (Ri + Rj) * (Ri + Rj);
+        }
+        const double ex = d.r[3 * b] - d.r[3 * a], ey = d.r[3 * b + 1] - d.r[3 * a + 1], ez = d.r[3 * b + 2] - d.r[3 * a + 2];
+        const double s64 = d.aprm64[a].w + d.aprm64[b].w;
+        return ex * ex + ey * ey + ez * ez < s64 * s64;
+    };
+    // a force term in the solvation sums' fixed point, round(q 2^40): in mixed mode from FP32 pieces
+    // of q 2^17 (exact scaling; see fx_add), FP64 only for terms of 32 kcal/mol/A or more
+    auto fx40 = [&](R q) -> long long {
+        if constexpr (MIXED) {
+            const float v = q * 131072.0f;
+            if (fabsf(v) < kPairFxMax) {
+                int n, fr;
+                fx_pieces(v, n, fr);
+                return fx_units(n, fr);
+            }
+            return llrint((double)q * kFxScale);
+        } else {
+            return llrint(q * kFxScale);
+        }
+    };
+    // pass 1: A_i / S_i = prod f_ij
+    R prod = (R)1;
+    bool clamped = false;
+    for (int j = lane; j < cnt; j += 32) {
+        R ox, oy, oz, d2, Rj;
+        if (!geom(j, ox, oy, oz, d2, Rj)) continue;
+        const R dd = sqrt(d2);
+        const R b = fmax(kPi * Ri * (Ri + Rj - dd) * ((R)1 + (Rj - Ri) / dd), (R)0);
+        const R f = (R)1 - b / Si;
+        if (f <= (R)0) clamped = true;
+        prod *= fmax(f, (R)0);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) prod *= __shfl_xor_sync(0xffffffffu, prod, o);
+    clamped = __any_sync(0xffffffffu, clamped);
+    const R Ei = (R)d.G0[a] * prod;  // G0_i = gamma_i S_i
+    long long fi[3] = {0, 0, 0};
+    if (!clamped && Ei != (R)0) {
+        // pass 2: pair forces
+        for (int j = lane; j < cnt; j += 32) {
+            R ox, oy, oz, d2, Rj;
+            if (!geom(j, ox, oy, oz, d2, Rj)) continue;
+            const R dd = sqrt(d2);
+            const R b = kPi * Ri * (Ri + Rj - dd) * ((R)1 + (Rj - Ri) / dd);
+            if (b <= (R)0) continue;  // j inside i: no burial
+            const R f = (R)1 - b / Si;
+            const R mdb = kPi * Ri * ((R)1 + (Rj * Rj - Ri * Ri) / d2);
+            const R cij = Ei * mdb / (Si * f) / dd;  // times r_j - r_i
+            const long long qx = fx40(cij * ox), qy = fx40(cij * oy), qz = fx40(cij * oz);
+            fi[0] += qx; fi[1] += qy; fi[2] += qz;
+            unsigned long long* Fj = reinterpret_cast<unsigned long long*>(&d.Fcav[3 * nl[j]]);
+            atomicAdd(Fj, (unsigned long long)(-qx));
+            atomicAdd(Fj + 1, (unsigned long long)(-qy));
+            atomicAdd(Fj + 2, (unsigned long long)(-qz));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fi[k] = warp_sum(fi[k]);
+    nguard = (int)__reduce_add_sync(0xffffffffu, (unsigned)nguard);
+    if (lane == 0) {
+        unsigned long long* Fa = reinterpret_cast<unsigned long long*>(&d.Fcav[3 * a]);
+        if (fi[0]) atomicAdd(Fa, (unsigned long long)fi[0]);
+        if (fi[1]) atomicAdd(Fa + 1, (unsigned long long)fi[1]);
+        if (fi[2]) atomicAdd(Fa + 2, (unsigned long long)fi[2]);
+        d.esolv[a] = (double)Ei;
+        d.covered[a] = 0;
+        d.sstat[a] = make_int2(cnt, nguard);
+    }
+}
+
 // loop state of a batch; with full, also the statistics and the chains' bounding boxes
 __global__ void k_reset_loop(const DevChain d, int full) {
     Status* st = d.status;
@@ -1187,7 +1301,10 @@ void launch_pairs(DevChain& d, cudaStream_t s) {
 }
 
 void launch_sasa(DevChain& d, cudaStream_t s) {
-    if (d.prm.solvation) {
+    if (d.prm.solvation == 2) {
+        if (d.prm.precision == KCM_MIXED) k_sasa_pw<true><<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
+        else k_sasa_pw<false><<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
+    } else if (d.prm.solvation) {
         if (d.prm.precision == KCM_MIXED)
             k_sasa_mixed<<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
         else
@@ -1196,7 +1313,7 @@ void launch_sasa(DevChain& d, cudaStream_t s) {
 }
 
 void launch_sasa_long(DevChain& d, cudaStream_t s) {
-    if (!d.prm.solvation) return;
+    if (d.prm.solvation != 1) return;
     const int nb = std::max(1, std::min((d.n + kSasaWarps - 1) / kSasaWarps, kSasaLongBlocks));
     if (d.prm.precision == KCM_MIXED) k_sasa_mixed_long<<<nb, kSasaWarps * 32, 0, s>>>(d);
     else k_sasa_long<<<nb, kSasaWarps * 32, 0, s>>>(d);

@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
                 f[k] = add(ldexp2(df_from_i64(d.Fpx[3 * a + k]), 0x1p-23f), df{d.Fov[3 * a + k], 0.0f});
                 if (d.prm.solvation) f[k] = add(f[k], ldexp2(df_from_i64(d.Fcav[3 * a + k]), 0x1p-40f));
             }
-            if (d.prm.solvation && d.gflag[a])  // G^cav_i = G0_i f_i, f_i = 1 - covered_i / N (Sec. 3.4)
+            if (d.prm.solvation == 2) Ef[2] += (float)d.esolv[a];  // pairwise surrogate: gamma_i A_i
+            else if (d.prm.solvation && d.gflag[a])  // G^cav_i = G0_i f_i, f_i = 1 - covered_i / N (Sec. 3.4)
                 Ef[2] += d.G0f[a] * (1.0f - (float)d.covered[a] * d.f_invN);
         } else {
 #pragma unroll
@@ -122,7 +123,9 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
                 f[k] = d.Fpair[3 * a + k];
                 if (d.prm.solvation) f[k] += (double)d.Fcav[3 * a + k] * kFxInv;
             }
-            if (d.prm.solvation) {
+            if (d.prm.solvation == 2) {
+                E[2] += d.esolv[a];
+            } else if (d.prm.solvation) {
                 const double G0a = d.G0[a];
                 if (G0a != 0.0) E[2] += G0a - G0a * (double)d.covered[a] / (double)d.N;
             }
