@@ -73,6 +73,14 @@ def lib():
                                        C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_run.argtypes = [C.c_void_p, _dp, _dp, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_run.restype = C.c_int
+            L.orc_fk_x.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp, C.c_void_p, C.c_void_p]
+            L.orc_nside_joints.argtypes = [C.c_void_p]
+            L.orc_nside_joints.restype = C.c_int
+            L.orc_side_torques.argtypes = [C.c_void_p, _dp, _dp, _dp]
+            L.orc_evaluate_x.argtypes = [C.c_void_p, _dp, _dp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_run_x.argtypes = [C.c_void_p, _dp, _dp, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_run_x.restype = C.c_int
             L.orc_grow_start.argtypes = [C.c_void_p, C.c_ulonglong, C.c_double, C.c_int, C.c_int, C.c_void_p]
             L.orc_grow_start.restype = C.c_int
             L.orc_num_threads.restype = C.c_int
@@ -207,6 +215,7 @@ class OracleChain:
                                       np.ascontiguousarray(table.cls, dtype=np.int32).reshape(-1), geom)
         self.n = int(lib().orc_natoms(self._h))
         self.l = 2 * self.m
+        self.nside_joints = int(lib().orc_nside_joints(self._h))  # chi joints, residue by residue
         self.res = np.zeros(self.n, dtype=np.int32)
         self.kind = np.zeros(self.n, dtype=np.int32)
         self.link = np.zeros(self.n, dtype=np.int32)
@@ -243,15 +252,30 @@ class OracleChain:
     def bond_distance(self, a, b):
         return int(lib().orc_bond_distance(self._h, int(a), int(b)))
 
-    def fk(self, theta):
-        """eq. kin_04 + eq. r1/r2: returns (xyz [n,3], u [l,3] current axes, p [l,3] axis points)."""
+    def _side(self, side):
+        if side is None:
+            return None
+        s = np.ascontiguousarray(side, dtype=np.float64)
+        assert s.shape == (self.nside_joints,)
+        return s
+
+    def fk(self, theta, side=None):
+        """eq. kin_04/05 + eq. r1/r2: returns (xyz [n,3], u [l,3] current axes, p [l,3] axis points) of
+        the main-chain joints; side: the side-chain joint angles (None: the ZP side groups)."""
         th = np.ascontiguousarray(theta, dtype=np.float64)
         assert th.shape == (self.l,)
+        s = self._side(side)
         xyz = np.zeros((self.n, 3))
         u = np.zeros((self.l, 3))
         p = np.zeros((self.l, 3))
-        lib().orc_fk(self._h, th, xyz.reshape(-1), u.reshape(-1), p.reshape(-1))
+        lib().orc_fk_x(self._h, th, _ptr(s), xyz.reshape(-1), _ptr(u), _ptr(p))
         return xyz, u, p
+
+    def side_torques(self, xyz, F):
+        t = np.zeros(self.nside_joints)
+        lib().orc_side_torques(self._h, np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1),
+                               np.ascontiguousarray(F, dtype=np.float64).reshape(-1), t)
+        return t
 
     def pair_forces(self, xyz, params):
         F = np.zeros((self.n, 3))
@@ -270,9 +294,12 @@ class OracleChain:
            np.ascontiguousarray(u).reshape(-1), np.ascontiguousarray(p).reshape(-1), tau)
         return tau
 
-    def evaluate(self, params, theta):
-        """Everything at theta: dict(xyz, F_pair, F_cav, tau, E[3], covered, stats)."""
+    def evaluate(self, params, theta, side=None):
+        """Everything at theta: dict(xyz, F_pair, F_cav, tau, E[3], covered, stats); with side (the
+        side-chain joint angles) also tau_side."""
         th = np.ascontiguousarray(theta, dtype=np.float64)
+        s = self._side(side)
+        ts = None if s is None else np.zeros(self.nside_joints)
         xyz = np.zeros((self.n, 3))
         Fp = np.zeros((self.n, 3))
         Fc = np.zeros((self.n, 3))
@@ -280,11 +307,14 @@ class OracleChain:
         E = np.zeros(3)
         cov = np.zeros(self.n, dtype=np.int32)
         stats = np.zeros(4, dtype=np.int64)
-        lib().orc_evaluate(self._h, run_params(params), th, _ptr(xyz), _ptr(Fp), _ptr(Fc), _ptr(tau), _ptr(E),
-                           _ptr(cov), _ptr(stats))
-        return dict(xyz=xyz, F_pair=Fp, F_cav=Fc, tau=tau, E=E, covered=cov,
-                    stats=dict(pairs=int(stats[0]), sasa_tests1=int(stats[1]), sasa_tests2=int(stats[2]),
-                               sasa_cand=int(stats[3])))
+        lib().orc_evaluate_x(self._h, run_params(params), th, _ptr(s), _ptr(xyz), _ptr(Fp), _ptr(Fc), _ptr(tau),
+                             _ptr(ts), _ptr(E), _ptr(cov), _ptr(stats))
+        out = dict(xyz=xyz, F_pair=Fp, F_cav=Fc, tau=tau, E=E, covered=cov,
+                   stats=dict(pairs=int(stats[0]), sasa_tests1=int(stats[1]), sasa_tests2=int(stats[2]),
+                              sasa_cand=int(stats[3])))
+        if ts is not None:
+            out["tau_side"] = ts
+        return out
 
     def grow_start(self, seed, min_dist=2.5, max_retries=100, backtrack=5):
         """Compact self-avoiding random-walk start as 16-bit angle codes [2m] (input generation)."""
@@ -295,13 +325,19 @@ class OracleChain:
             raise RuntimeError("start growth ran out of attempts")
         return codes
 
-    def run(self, params, theta, n_iters, fixed=None):
-        """The KCM loop; returns (theta, iterations taken, E trace [it,3], max|dtheta| trace).
-        fixed: joints held fixed (uint8 [l]), None for none."""
+    def run(self, params, theta, n_iters, fixed=None, side=None):
+        """The KCM loop; returns (theta, iterations taken, E trace [it,3], max|dtheta| trace), and with
+        side (the side-chain joint angles, stepped together with theta) (theta, side, it, Et, dt).
+        fixed: main-chain joints held fixed (uint8 [l]), None for none."""
         th = np.array(theta, dtype=np.float64)
+        s = None if side is None else np.array(side, dtype=np.float64)
+        if s is not None:
+            assert s.shape == (self.nside_joints,)
         Et = np.zeros((n_iters, 3))
         dt = np.zeros(n_iters)
         m = _mask(fixed, self.l)
-        it = lib().orc_run(self._h, run_params(params), th, int(n_iters), _ptr(Et), _ptr(dt),
-                           None if m is None else _ptr(m))
+        it = lib().orc_run_x(self._h, run_params(params), th, _ptr(s), int(n_iters), _ptr(Et), _ptr(dt),
+                             None if m is None else _ptr(m))
+        if s is not None:
+            return th, s, int(it), Et[:it], dt[:it]
         return th, int(it), Et[:it], dt[:it]

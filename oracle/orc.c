@@ -107,6 +107,8 @@ typedef struct {
     int* near_j;
     int* near_d;
     double geom[11];
+    int* nchi;       /* side-chain joints chi_1 .. chi_nchi of residue i (eq. kin_05: at most 4) */
+    int* chi_first;  /* index of residue i's chi_1 among all side-chain joints [m+1] */
 } Chain;
 
 /* atom index helpers: per residue order N, H, CA, side 1..k, C, O */
@@ -295,13 +297,20 @@ void* orc_chain_new(int m, const int* res_type, const int* n_side, const double*
     memcpy(c->geom, geom, sizeof c->geom);
     c->first = (int*)malloc(sizeof(int) * m);
     c->nside = (int*)malloc(sizeof(int) * m);
+    c->nchi = (int*)malloc(sizeof(int) * m);
+    c->chi_first = (int*)malloc(sizeof(int) * (m + 1));
     int n = 0;
     for (int i = 0; i < m; i++) {
         c->first[i] = n;
         c->nside[i] = n_side[res_type[i]];
+        /* a side-chain joint turns about the bond to side atom k - 1 (CA -> CB for k = 1) and moves
+         * the side atoms beyond it: at most 4 (eq. kin_05), and one fewer than the side atoms */
+        c->nchi[i] = c->nside[i] >= 2 ? (c->nside[i] - 1 < 4 ? c->nside[i] - 1 : 4) : 0;
         n += 5 + c->nside[i];
     }
     c->n = n;
+    c->chi_first[0] = 0;
+    for (int i = 0; i < m; i++) c->chi_first[i + 1] = c->chi_first[i] + c->nchi[i];
     c->res = (int*)malloc(sizeof(int) * n);
     c->kind = (int*)malloc(sizeof(int) * n);
     c->slot = (int*)malloc(sizeof(int) * n);
@@ -344,6 +353,7 @@ void orc_chain_free(void* p) {
     Chain* c = (Chain*)p;
     if (!c) return;
     free(c->res); free(c->kind); free(c->slot); free(c->link); free(c->first); free(c->nside);
+    free(c->nchi); free(c->chi_first);
     free(c->q); free(c->eps); free(c->R); free(c->cls); free(c->zp); free(c->loc); free(c->nstep);
     free(c->adj_start); free(c->adj); free(c->near_start); free(c->near_j); free(c->near_d);
     free(c);
@@ -417,8 +427,28 @@ static void zp_from_ca(const Chain* c, int i, int a, double* v) {
     }
 }
 
-static void fk_residue(const Chain* c, int i, double th_phi, double th_psi, const double M[9], const double* rN,
-                       double* xyz, double Mout[9], double* rN_out, double* u2, double* p2) {
+/* ZP offset from CA_i of side atom s of residue i after the side-chain rotations th_side[0 ..
+ * nchi-1] (eq. kin_05, r2): chi_k turns by th_side[k-1] about the ZP bond from side atom k - 2 (CA
+ * for k = 1) to side atom k - 1 and moves side atoms s >= k; in the ZP frame the rotations compose
+ * from the most distal: x = T_1(T_2(... T_min(s, nchi)(x0))), T_k(x) = R_k (x - a_k) + a_k. */
+static void side_offset(const Chain* c, int i, int s, const double* th_side, double* x) {
+    zp_from_ca(c, i, at_S(c, i, s), x);
+    const int kmax = s < c->nchi[i] ? s : c->nchi[i];
+    for (int k = kmax; k >= 1; k--) {
+        double a[3] = {0, 0, 0}, b[3], u[3], R[9], t[3], r[3];
+        if (k >= 2) zp_from_ca(c, i, at_S(c, i, k - 2), a);
+        zp_from_ca(c, i, at_S(c, i, k - 1), b);
+        v_sub(b, a, u);
+        v_unit(u, u);
+        rot_matrix(u, th_side[k - 1], R);
+        v_sub(x, a, t);
+        mat_vec(R, t, r);
+        v_add(r, a, x);
+    }
+}
+
+static void fk_residue(const Chain* c, int i, double th_phi, double th_psi, const double* th_side, const double M[9],
+                       const double* rN, double* xyz, double Mout[9], double* rN_out, double* u2, double* p2) {
     int aCA = at_CA(c, i), aC = at_C(c, i);
     double u0[3], b0[3], R[9], Mphi[9], Mpsi[9], b[3], rCA[3], v0[3], v[3];
     /* phi_i: rotation about the ZP axis N_i -> CA_i (eq. kin_04) */
@@ -433,7 +463,8 @@ static void fk_residue(const Chain* c, int i, double th_phi, double th_psi, cons
     memcpy(&xyz[3 * aCA], rCA, sizeof rCA);
     for (int s = 0; s < c->nside[i]; s++) { /* eq. r2 */
         int aS = at_S(c, i, s);
-        zp_from_ca(c, i, aS, v0);
+        if (th_side) side_offset(c, i, s, th_side, v0);
+        else zp_from_ca(c, i, aS, v0);
         mat_vec(Mphi, v0, v);
         v_add(rCA, v, &xyz[3 * aS]);
     }
@@ -462,7 +493,8 @@ static void fk_residue(const Chain* c, int i, double th_phi, double th_psi, cons
  * N_1 anchored at the origin. Joint 2i+1 (phi of residue i) turns about N_i -> CA_i, joint 2i+2
  * (psi) about CA_i -> C_i. Outputs: atom centres [n*3]; optionally the current joint axes
  * u [2m*3] and a point on each axis p [2m*3] (N_i for phi, CA_i for psi). */
-void orc_fk(void* p, const double* theta, double* xyz, double* u_out, double* p_out) {
+/* the same with the side-chain joints at theta_side [orc_nside_joints] (NULL: the ZP side groups) */
+void orc_fk_x(void* p, const double* theta, const double* theta_side, double* xyz, double* u_out, double* p_out) {
     Chain* c = (Chain*)p;
     double M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     double rN[3] = {0, 0, 0};
@@ -471,10 +503,40 @@ void orc_fk(void* p, const double* theta, double* xyz, double* u_out, double* p_
     memcpy(&xyz[3 * at_H(c, 0)], &c->zp[3 * at_H(c, 0)], 3 * sizeof(double));
     for (int i = 0; i < c->m; i++) {
         double Mn[9], rn[3] = {0, 0, 0};
-        fk_residue(c, i, theta[2 * i], theta[2 * i + 1], M, rN, xyz, Mn, rn,
-                   u_out ? &u_out[6 * i] : NULL, p_out ? &p_out[6 * i] : NULL);
+        fk_residue(c, i, theta[2 * i], theta[2 * i + 1], theta_side ? &theta_side[c->chi_first[i]] : NULL, M, rN,
+                   xyz, Mn, rn, u_out ? &u_out[6 * i] : NULL, p_out ? &p_out[6 * i] : NULL);
         memcpy(M, Mn, sizeof M);
         memcpy(rN, rn, sizeof rN);
+    }
+}
+
+void orc_fk(void* p, const double* theta, double* xyz, double* u_out, double* p_out) {
+    orc_fk_x(p, theta, NULL, xyz, u_out, p_out);
+}
+
+int orc_nside_joints(void* p) { return ((Chain*)p)->chi_first[((Chain*)p)->m]; }
+
+/* Torques of the side-chain joints (eq. KCM_06 for the branches of Sec. 3.5): the moment, about the
+ * joint's current axis (its bond, from side atom k - 2 or CA to side atom k - 1), of the forces on
+ * the side atoms it moves, tau = u . sum_s (r_s - a) x F_s. */
+void orc_side_torques(void* p, const double* xyz, const double* F, double* tau_side) {
+    Chain* c = (Chain*)p;
+    for (int i = 0; i < c->m; i++) {
+        for (int k = 1; k <= c->nchi[i]; k++) {
+            const double* a = &xyz[3 * (k >= 2 ? at_S(c, i, k - 2) : at_CA(c, i))];
+            const double* b = &xyz[3 * at_S(c, i, k - 1)];
+            double u[3];
+            v_sub(b, a, u);
+            v_unit(u, u);
+            double t = 0.0;
+            for (int s = k; s < c->nside[i]; s++) {
+                double r[3], m[3];
+                v_sub(&xyz[3 * at_S(c, i, s)], a, r);
+                v_cross(r, &F[3 * at_S(c, i, s)], m);
+                t += v_dot(u, m);
+            }
+            tau_side[c->chi_first[i] + k - 1] = t;
+        }
     }
 }
 
@@ -563,7 +625,7 @@ int orc_grow_start(void* p, unsigned long long seed, double min_dist, int max_re
             unsigned short cp = (unsigned short)(splitmix64(&st) >> 48), cs = (unsigned short)(splitmix64(&st) >> 48);
             double tp = (double)cp * (2.0 * ORC_PI / 65536.0), ts = (double)cs * (2.0 * ORC_PI / 65536.0);
             double Mn[9], rn[3] = {0, 0, 0};
-            fk_residue(c, i, tp, ts, &Ms[9 * i], &rNs[3 * i], xyz, Mn, rn, NULL, NULL);
+            fk_residue(c, i, tp, ts, NULL, &Ms[9 * i], &rNs[3 * i], xyz, Mn, rn, NULL, NULL);
             int cand[16], nc = 0;
             cand[nc++] = at_CA(c, i);
             for (int s = 0; s < c->nside[i]; s++) cand[nc++] = at_S(c, i, s);
@@ -1074,8 +1136,9 @@ double orc_step(int l, double* theta, const double* tau, double kappa, double dm
  *        conv_tol, solvation, n_sample, step_mode}
  * Evaluates at theta: positions, pair and solvation forces, torques, energies E[3] (elec, vdw,
  * cav). Optional outputs may be NULL. */
-void orc_evaluate(void* p, const double* prm, const double* theta, double* xyz, double* F_pair, double* F_cav,
-                  double* tau, double* E, int* covered, long long* stats) {
+void orc_evaluate_x(void* p, const double* prm, const double* theta, const double* theta_side, double* xyz,
+                    double* F_pair, double* F_cav, double* tau, double* tau_side, double* E, int* covered,
+                    long long* stats) {
     Chain* c = (Chain*)p;
     int n = c->n, l = 2 * c->m, N = (int)prm[11];
     double* X = xyz ? xyz : (double*)malloc(sizeof(double) * 3 * n);
@@ -1084,7 +1147,7 @@ void orc_evaluate(void* p, const double* prm, const double* theta, double* xyz, 
     double* u = (double*)malloc(sizeof(double) * 3 * l);
     double* pk = (double*)malloc(sizeof(double) * 3 * l);
     double Ep[2];
-    orc_fk(p, theta, X, u, pk);
+    orc_fk_x(p, theta, theta_side, X, u, pk);
     double pprm[5] = {prm[0], prm[1], prm[2], prm[3], prm[4]};
     long long npairs = orc_pair_forces_chain(p, X, pprm, Fp, Ep);
     double Ecav = 0.0;
@@ -1114,10 +1177,11 @@ void orc_evaluate(void* p, const double* prm, const double* theta, double* xyz, 
         memset(Fc, 0, sizeof(double) * 3 * n);
         if (covered) memset(covered, 0, sizeof(int) * n);
     }
-    if (tau) {
+    if (tau || tau_side) {
         double* Ft = (double*)malloc(sizeof(double) * 3 * n);
         for (int x = 0; x < 3 * n; x++) Ft[x] = Fp[x] + Fc[x];
-        orc_torques_columns(n, l, c->link, X, Ft, u, pk, tau);
+        if (tau) orc_torques_columns(n, l, c->link, X, Ft, u, pk, tau);
+        if (tau_side) orc_side_torques(p, X, Ft, tau_side);
         free(Ft);
     }
     if (E) { E[0] = Ep[0]; E[1] = Ep[1]; E[2] = Ecav; }
@@ -1128,25 +1192,46 @@ void orc_evaluate(void* p, const double* prm, const double* theta, double* xyz, 
     free(u); free(pk);
 }
 
+void orc_evaluate(void* p, const double* prm, const double* theta, double* xyz, double* F_pair, double* F_cav,
+                  double* tau, double* E, int* covered, long long* stats) {
+    orc_evaluate_x(p, prm, theta, NULL, xyz, F_pair, F_cav, tau, NULL, E, covered, stats);
+}
+
 /* The KCM loop (Sec. 4.1 steps 4-9): evaluate, step, stop once max |dtheta| < conv_tol.
  * theta is updated in place; E_trace [n_iters*3], dmax_trace [n_iters] and fixed [l] (joints held
- * fixed) are optional. Returns the number of iterations taken. */
-int orc_run(void* p, const double* prm, double* theta, int n_iters, double* E_trace, double* dmax_trace,
-            const unsigned char* fixed) {
+ * fixed) are optional; with theta_side (NULL: none) the side-chain joints are stepped together with
+ * the main-chain joints, as one vector of joint angles. Returns the number of iterations taken. */
+int orc_run_x(void* p, const double* prm, double* theta, double* theta_side, int n_iters, double* E_trace,
+              double* dmax_trace, const unsigned char* fixed) {
     Chain* c = (Chain*)p;
-    int l = 2 * c->m;
-    double* tau = (double*)malloc(sizeof(double) * l);
+    const int l = 2 * c->m, ls = theta_side ? orc_nside_joints(p) : 0;
+    double* tau = (double*)malloc(sizeof(double) * (l + ls + 1));
+    double* all = (double*)malloc(sizeof(double) * (l + ls + 1));
+    unsigned char* fx = NULL;
+    if (fixed) {
+        fx = (unsigned char*)calloc(l + ls + 1, 1);
+        memcpy(fx, fixed, l);
+    }
     int it;
     for (it = 0; it < n_iters; it++) {
         double E[3];
-        orc_evaluate(p, prm, theta, NULL, NULL, NULL, tau, E, NULL, NULL);
-        double dm = orc_step(l, theta, tau, prm[7], prm[8], (int)prm[12], NULL, fixed);
+        orc_evaluate_x(p, prm, theta, theta_side, NULL, NULL, NULL, tau, ls ? tau + l : NULL, E, NULL, NULL);
+        memcpy(all, theta, sizeof(double) * l);
+        if (ls) memcpy(all + l, theta_side, sizeof(double) * ls);
+        double dm = orc_step(l + ls, all, tau, prm[7], prm[8], (int)prm[12], NULL, fx);
+        memcpy(theta, all, sizeof(double) * l);
+        if (ls) memcpy(theta_side, all + l, sizeof(double) * ls);
         if (E_trace) memcpy(&E_trace[3 * it], E, sizeof E);
         if (dmax_trace) dmax_trace[it] = dm;
         if (dm < prm[9]) { it++; break; }
     }
-    free(tau);
+    free(tau); free(all); free(fx);
     return it;
+}
+
+int orc_run(void* p, const double* prm, double* theta, int n_iters, double* E_trace, double* dmax_trace,
+            const unsigned char* fixed) {
+    return orc_run_x(p, prm, theta, NULL, n_iters, E_trace, dmax_trace, fixed);
 }
 
 int orc_num_threads(void) {
