@@ -403,6 +403,24 @@ def run_ours(args):
             tt = time_steps(cs, lambda: prepare(cs, ss), ss, args.fp64_steps)
             surrogate_value = n * args.fp64_steps / (sum(tt) / 1e3)
 
+    # the same step with the side-chain joints on (chi_1..chi_4 per residue, stepped with the main chain),
+    # each step from the same start (chi = 0), measured the same way
+    side_value = None
+    if args.fp64_steps > 0:
+        with kcm.Chain(seq, table, synth.RunParams(precision=prec, side_joints=1)) as cx:
+            sx = torch.cuda.ExternalStream(cx.stream())
+            chi0 = np.zeros(cx.ls)
+
+            def prep_x():
+                cx.set_side_theta(chi0)
+                prepare(cx, sx)
+
+            for _ in range(3):
+                prep_x()
+                cx.step(1)
+            tt = time_steps(cx, prep_x, sx, args.fp64_steps)
+            side_value = n * args.fp64_steps / (sum(tt) / 1e3)
+
     # the batch workload: 512 chains stepped together, one launch per stage, measured the same way
     batch = None
     if args.batch_steps > 0:
@@ -515,7 +533,7 @@ def run_ours(args):
                 "roofline": roof, "rooflines": rooflines, "stage_ms": ms_stage,
                 "stage_note": "stage_ms from a second pass of the same steps with a CUDA event between stages "
                               "(each event node adds ~3 us); value and ms_per_step time whole steps only",
-                "fp64_value": fp64_value, "surrogate_value": surrogate_value,
+                "fp64_value": fp64_value, "surrogate_value": surrogate_value, "side_joints_value": side_value,
                 "vacuum_value": vacuum_value, "batch": batch, "serving": serving,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,

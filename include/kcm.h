@@ -121,7 +121,11 @@ typedef struct {
  * 2 the pairwise surrogate that preceded it (Sec. 3.4: A_i = S_i prod_j (1 - b_ij / S_i), b_ij the
  * area of offset sphere i inside offset sphere j, S_i = 4 pi Roff_i^2; smooth, with exact gradient
  * forces); precision: KCM_FP64/KCM_MIXED;
- * step_mode: KCM_STEP_CLAMP/KCM_STEP_NORMALIZED. */
+ * step_mode: KCM_STEP_CLAMP/KCM_STEP_NORMALIZED; side_joints: 1 adds the side-chain joints (eq. kin_05,
+ * r2: residue i gets chi_1 .. chi_k, k = min(4, side atoms - 1); chi_k turns about the bond from side
+ * atom k - 2 (CA for k = 1) to side atom k - 1 and moves side atoms k, k + 1, ...), stepped by the
+ * loop together with the main-chain joints as one vector (kcm_set_side_theta and the calls after
+ * it); 0 (the default) holds every side group in its ZP form. */
 typedef struct {
     double cutoff;
     double vdw_cutoff;
@@ -138,6 +142,7 @@ typedef struct {
     int32_t solvation;
     int32_t precision;
     int32_t step_mode;
+    int32_t side_joints;
 } kcm_params;
 
 /* Counters of the last evaluation (device-side, read back by kcm_get_stats). */
@@ -156,7 +161,7 @@ typedef struct kcm_ctx* kcm_handle;
 
 /* Fill `p` with the defaults: cutoff 10, vdw_cutoff 0, kappa 1e-3, dtheta_max 0.02,
  * w14 0.5/0.5, r_probe 1.4, delta_r 0.02, coulomb_k 332.0636, conv_tol 1e-4, cell_size 0,
- * n_sample 256, solvation 1, KCM_FP64, KCM_STEP_CLAMP. */
+ * n_sample 256, solvation 1, KCM_FP64, KCM_STEP_CLAMP, side_joints 0. */
 int kcm_params_default(kcm_params* p);
 
 /* Build the chain (ZP geometry, bond-class tables, sample set) on the host and upload it to the
@@ -316,6 +321,25 @@ int kcm_get_stats(kcm_handle h, kcm_stats* st);
  * normalised step's max |tau| nor in the convergence test (max |dtheta| over the moved joints).
  * NULL clears all flags (the default). Synchronises. Errors: KCM_E_INVAL (l does not match). */
 int kcm_set_fixed_joints(kcm_handle h, const uint8_t* fixed, int64_t l);
+
+/* Side-chain joints (kcm_params.side_joints = 1; eq. kin_05, r2 and the branch torques of Sec. 3.5).
+ * Joint chi_k of residue i turns the side atoms beyond the bond (side atom k - 2, or CA for k = 1) ->
+ * (side atom k - 1) about that bond; chi = 0 is the ZP side group. The side-chain joints of a handle
+ * are numbered residue by residue, chi_1 first (a batch: chain by chain); there are
+ * kcm_nside_joints of them (0 when side_joints = 0, -1 for a NULL handle). They start at 0; the
+ * loop (kcm_step) steps them with the main-chain joints as one vector of joint angles: the same
+ * clamp or normalisation (max |tau| over the main and side joints of a chain) and the same
+ * convergence test (max |dtheta| over both). They are never held fixed (kcm_set_fixed_joints covers
+ * the main-chain joints). Arrays are host memory of ls = kcm_nside_joints doubles (rad; kcal/mol per
+ * rad); errors: KCM_E_INVAL (ls does not match, NULL array, a non-finite angle). */
+int64_t kcm_nside_joints(kcm_handle h);
+int kcm_set_side_theta(kcm_handle h, const double* chi, int64_t ls);
+int kcm_get_side_theta(kcm_handle h, double* chi, int64_t ls);
+/* torques of the side-chain joints at the current angles: tau = u . sum_s (r_s - a) x F_s over the side
+ * atoms s the joint moves, u its current unit bond axis and a the bond's first atom (evaluates) */
+int kcm_side_torques(kcm_handle h, double* tau, int64_t ls);
+/* side-chain joints of chain c: [side_off[c], side_off[c+1]) (kcm_nchains + 1 entries, host memory) */
+int kcm_side_offsets(kcm_handle h, int64_t* side_off);
 
 /* Cell-edge autotuner. For each candidate edge (A; meaning as kcm_params.cell_size, so 0 is the
  * smallest 27-cell edge) evaluate the chain (forces and torques at the current theta, no step:

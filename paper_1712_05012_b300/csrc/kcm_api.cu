@@ -277,6 +277,7 @@ int kcm_params_default(kcm_params* p) {
     p->solvation = 1;
     p->precision = KCM_FP64;
     p->step_mode = KCM_STEP_CLAMP;
+    p->side_joints = 0;
     return KCM_OK;
 }
 
@@ -339,6 +340,8 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
     kcm::DevChain& d = h->d;
     d.prm = *prm;
     d.m = hc.m; d.n = hc.n; d.l = hc.l; d.L = hc.L; d.N = prm->n_sample;
+    d.ls = prm->side_joints ? hc.ls : 0;
+    d.nmv = prm->side_joints ? static_cast<int>(hc.mv_atom.size()) : 0;
     for (int h0 = 0; h0 < hc.L; h0 += 32) {  // the wrench kernel stages one 32-link tile in shared memory
         const int h1 = std::min(h0 + 32, hc.L);
         if (hc.link_start[h1] - hc.link_start[h0] > kcm::kWrenchTileAtoms)
@@ -375,8 +378,8 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.u0, 3 * l)) || (rc = dalloc(h, &d.step0, 3 * l)) || (rc = dalloc(h, &d.aprm64, nn)) ||
         (rc = dalloc(h, &d.aprm32, nn)) || (rc = dalloc(h, &d.G0, nn)) || (rc = dalloc(h, &d.qfx, nn)) ||
         (rc = dalloc(h, &d.exm, nn)) || (rc = dalloc(h, &d.m14m, nn)) || (rc = dalloc(h, &d.Q64, 3 * N)) ||
-        (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.Q4, N)) || (rc = dalloc(h, &d.theta, l)) || (rc = dalloc(h, &d.dtheta, l)) ||
-        (rc = dalloc(h, &d.tau, l)) || (rc = dalloc(h, &d.G, 12 * (size_t)l)) ||
+        (rc = dalloc(h, &d.Q32, 3 * N)) || (rc = dalloc(h, &d.Q4, N)) || (rc = dalloc(h, &d.theta, l + d.ls)) || (rc = dalloc(h, &d.dtheta, l + d.ls)) ||
+        (rc = dalloc(h, &d.tau, l + d.ls)) || (rc = dalloc(h, &d.G, 12 * (size_t)l)) ||
         (rc = dalloc(h, &d.tileP, 12 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.tileE, 12 * (size_t)d.ntiles)) || (rc = dalloc(h, &d.u0df, 3 * l)) ||
         (rc = dalloc(h, &d.step0df, 3 * l)) || (rc = dalloc(h, &d.r0df, 3 * nn)) || (rc = dalloc(h, &d.rdf, 3 * nn)) ||
         (rc = dalloc(h, &d.ucurdf, 3 * l)) || (rc = dalloc(h, &d.pcurdf, 3 * l)) || (rc = dalloc(h, &d.G0f, nn)) ||
@@ -400,7 +403,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.chain_err, hc.nchains)) || (rc = dalloc(h, &d.chain_maxdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_maxtau, hc.nchains)) || (rc = dalloc(h, &d.chain_lastdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_E, 3 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.gseg, l)) ||
-        (rc = dalloc(h, &d.jhead, l)) || (rc = dalloc(h, &d.jfixed, l)) || (rc = dalloc(h, &d.lflag, L)) ||
+        (rc = dalloc(h, &d.jhead, l)) || (rc = dalloc(h, &d.jfixed, l + d.ls)) || (rc = dalloc(h, &d.lflag, L)) ||
         (rc = dalloc(h, &d.tileF, d.ntiles)) || (rc = dalloc(h, &d.ltail, L)) || (rc = dalloc(h, &d.tileT, d.ltiles)))
         return bail(rc);
 
@@ -453,8 +456,28 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = upload(h, d.step0df, step0df.data(), 3 * l)) || (rc = upload(h, d.r0df, r0df.data(), 3 * nn)))
         return bail(rc);
     if ((rc = set_cell_size(h, prm->cell_size))) return bail(rc);  // cell caps and arrays
-    e = cudaMemsetAsync(d.theta, 0, sizeof(double) * l, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.jfixed, 0, l, h->stream);
+    // the offsets the FK reads: the static ones, or with side-chain joints a copy that k_side_fk
+    // rewrites for the side atoms they move
+    double* r0mode = prm->precision == KCM_MIXED ? d.r0df : d.r0;
+    if (d.ls > 0) {
+        std::vector<int2> mv(d.nmv);
+        for (int k = 0; k < d.nmv; ++k) mv[k] = make_int2(hc.mv_chi0[k], hc.mv_nk[k]);
+        const size_t ls = static_cast<size_t>(d.ls);
+        if ((rc = dalloc(h, &d.r0fk, 3 * nn)) || (rc = dalloc(h, &d.chi_a, ls)) || (rc = dalloc(h, &d.chi_b, ls)) ||
+            (rc = dalloc(h, &d.chi_end, ls)) || (rc = dalloc(h, &d.chi_p0, 3 * ls)) || (rc = dalloc(h, &d.chi_u0, 3 * ls)) ||
+            (rc = dalloc(h, &d.mv_atom, d.nmv)) || (rc = dalloc(h, &d.mv_chi, d.nmv)) ||
+            (rc = upload(h, d.chi_a, hc.chi_a.data(), ls)) || (rc = upload(h, d.chi_b, hc.chi_b.data(), ls)) ||
+            (rc = upload(h, d.chi_end, hc.chi_end.data(), ls)) || (rc = upload(h, d.chi_p0, hc.chi_p0.data(), 3 * ls)) ||
+            (rc = upload(h, d.chi_u0, hc.chi_u0.data(), 3 * ls)) || (rc = upload(h, d.mv_atom, hc.mv_atom.data(), d.nmv)) ||
+            (rc = upload(h, d.mv_chi, mv.data(), d.nmv)))
+            return bail(rc);
+        e = cudaMemcpyAsync(d.r0fk, r0mode, sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) { cuda_fail(h, e, "offset copy"); return bail(KCM_E_CUDA); }
+    } else {
+        d.r0fk = r0mode;
+    }
+    e = cudaMemsetAsync(d.theta, 0, sizeof(double) * (l + d.ls), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.jfixed, 0, l + d.ls, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.Fcav, 0, sizeof(long long) * 3 * nn, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.covered, 0, sizeof(int) * nn, h->stream);
     if (e != cudaSuccess) { cuda_fail(h, e, "memset"); return bail(KCM_E_CUDA); }
@@ -522,6 +545,44 @@ int kcm_set_fixed_joints(kcm_handle h, const uint8_t* fixed, int64_t l) {
         for (int j = 0; j < h->d.l; ++j) m[j] = fixed[j] ? 1 : 0;
     int rc = upload(h, h->d.jfixed, m.data(), m.size());
     return rc ? rc : sync(h);
+}
+
+int64_t kcm_nside_joints(kcm_handle h) { return h ? h->d.ls : -1; }
+
+int kcm_side_offsets(kcm_handle h, int64_t* side_off) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!side_off) return set_err(h, KCM_E_INVAL, "side_off is NULL");
+    for (int c = 0; c <= h->hc.nchains; ++c) side_off[c] = h->d.ls ? h->hc.side_off[c] : 0;
+    return KCM_OK;
+}
+
+int kcm_set_side_theta(kcm_handle h, const double* chi, int64_t ls) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (ls != h->d.ls || (ls > 0 && !chi)) return set_err(h, KCM_E_INVAL, "chi length must equal the side-chain joint count");
+    for (int64_t k = 0; k < ls; ++k)
+        if (!std::isfinite(chi[k])) return set_err(h, KCM_E_INVAL, "chi is not finite");
+    if (ls == 0) return KCM_OK;
+    int rc = upload(h, h->d.theta + h->d.l, chi, static_cast<size_t>(ls));
+    return rc ? rc : sync(h);
+}
+
+int kcm_get_side_theta(kcm_handle h, double* chi, int64_t ls) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (ls != h->d.ls || (ls > 0 && !chi)) return set_err(h, KCM_E_INVAL, "chi length must equal the side-chain joint count");
+    if (ls == 0) return KCM_OK;
+    cudaError_t e = cudaMemcpyAsync(chi, h->d.theta + h->d.l, sizeof(double) * ls, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "chi copy");
+    return sync(h);
+}
+
+int kcm_side_torques(kcm_handle h, double* tau, int64_t ls) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (ls != h->d.ls || (ls > 0 && !tau)) return set_err(h, KCM_E_INVAL, "ls must equal the side-chain joint count");
+    int rc = evaluate(h);
+    if (rc || ls == 0) return rc;
+    cudaError_t e = cudaMemcpyAsync(tau, h->d.tau + h->d.l, sizeof(double) * ls, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "torque copy");
+    return sync(h);
 }
 
 int kcm_chain_state(kcm_handle h, int32_t* iters, int32_t* converged, double* max_dtheta, int32_t* errors) {

@@ -71,6 +71,9 @@ constexpr int kWrenchWarps = 6;        // warps per 32-link tile of the wrench k
 
 struct DevChain {
     int m = 0, n = 0, l = 0, L = 0, N = 0;
+    int ls = 0;          // side-chain joints (0 unless kcm_params.side_joints); theta, dtheta, tau and
+                         // jfixed hold the l main-chain joints and then the ls side-chain joints
+    int nmv = 0;         // atoms moved by side-chain joints
     int fk_j = 1;        // joints per quad (four-lane transform slot) in the transform scan
     int ntiles = 0;      // transform-scan blocks of 32 * fk_j joints
     int ltiles = 0;      // suffix-sum tiles of 32 links
@@ -97,6 +100,15 @@ struct DevChain {
     double* u0df = nullptr;        // the same as double-float pairs (float hi, lo) for the mixed kernels [l*3]
     double* step0df = nullptr;     // [l*3]
     double* r0df = nullptr;        // [n*3]
+    double* r0fk = nullptr;        // the offsets the FK reads: r0 (FP64) or r0df (mixed), or with side-chain
+                                   // joints a copy whose moved side atoms k_side_fk rewrites [n*3]
+    int* chi_a = nullptr;          // side-chain joint c turns about the bond chi_a -> chi_b [ls]
+    int* chi_b = nullptr;          // [ls]
+    int* chi_end = nullptr;        // it moves atoms chi_b + 1 .. chi_end - 1 [ls]
+    double* chi_p0 = nullptr;      // the bond's first atom in its link frame (ZP) [ls*3]
+    double* chi_u0 = nullptr;      // the bond's unit direction in its link frame (ZP) [ls*3]
+    int* mv_atom = nullptr;        // atom moved by side-chain joints [nmv]
+    int2* mv_chi = nullptr;        // its residue's first side-chain joint, how many joints act on it [nmv]
     double* step0 = nullptr;       // link frame steps p0_j - p0_{j-1} [l*3]
     dbl4* aprm64 = nullptr;     // per atom: q, sqrt(eps), R, Roff
     float4* aprm32 = nullptr;      // the same in float
@@ -111,9 +123,9 @@ struct DevChain {
     float4* Q4 = nullptr;          // the same as (x, y, z, 0) [N]
 
     // per-iteration data
-    double* theta = nullptr;       // [l]
-    double* dtheta = nullptr;      // [l]
-    double* tau = nullptr;         // [l]
+    double* theta = nullptr;       // [l + ls]
+    double* dtheta = nullptr;      // [l + ls]
+    double* tau = nullptr;         // [l + ls]
     double* G = nullptr;           // pose of link j+1 relative to the first frame of its scan block [l*12]
     double* tileP = nullptr;       // scan block products [ntiles*12]
     double* tileE = nullptr;       // exclusive segmented prefixes of the scan block products [ntiles*12]
@@ -169,7 +181,7 @@ struct DevChain {
     double* chain_lastdt = nullptr;              // max |dtheta| of the chain's last step
     double* chain_E = nullptr;     // Coulomb, LJ, solvation energies [nchains * 3]
     unsigned char* jhead = nullptr;  // the joint is the first of its chain [l]
-    unsigned char* jfixed = nullptr; // the joint is held fixed: it takes no step (kcm_set_fixed_joints) [l]
+    unsigned char* jfixed = nullptr; // the joint is held fixed: it takes no step (kcm_set_fixed_joints) [l + ls]
     unsigned char* lflag = nullptr;  // 1: a chain's base link (no joint), 2: the last link of a chain [L]
     unsigned char* gseg = nullptr; // FK: a chain starts in the joint's scan block at or before it [l]
     int* tileF = nullptr;          // FK: a chain starts in the scan block [ntiles]

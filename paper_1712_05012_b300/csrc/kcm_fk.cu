@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     const int hfirst = blockIdx.x == 0 ? 0 : jb0 + joint_chain(d, jb0 - 1) + 1;
     const int hlast = blockIdx.x == gridDim.x - 1 ? d.L : jb1 + joint_chain(d, jb1 - 1) + 1;
     const int a1 = d.link_start[hlast];
-    const T* r0 = reinterpret_cast<const T*>(std::is_same<T, double>::value ? (const void*)d.r0 : (const void*)d.r0df);
+    const T* r0 = reinterpret_cast<const T*>(d.r0fk);
     unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0ULL, 0ULL, 0ULL};
     int cc = -1;  // chain of the keys held in mn, mx
     for (int a = d.link_start[hfirst] + threadIdx.x; a < a1; a += blockDim.x) {
@@ -587,8 +587,44 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     }
 }
 
+// Side-chain joints (eq. kin_05, r2): the offsets, in the frame of their CA link, of the side atoms
+// that chi_1 .. chi_k turn. In the ZP frame the rotations compose from the most distal joint inward,
+// x = T_1(T_2(... T_k(x0))) with T_c(x) = a_c + Rot(u_c, chi_c)(x - a_c) about the ZP bond (a_c, u_c):
+// each T_c then turns about its bond where the ZP has it, and the link pose (the main-chain joints)
+// takes the result to the current frame like every other atom of the link. One thread per moved
+// atom (at most four rotations, in FP64; written as double-float pairs in mixed mode).
+template <class T>
+__global__ void __launch_bounds__(128) k_side_fk(const DevChain d) {
+    if (d.status->done) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= d.nmv) return;
+    const int a = d.mv_atom[t];
+    const int2 mc = d.mv_chi[t];
+    double x = d.r0[3 * a], y = d.r0[3 * a + 1], z = d.r0[3 * a + 2];
+    for (int k = mc.y - 1; k >= 0; --k) {
+        const int c = mc.x + k;
+        double sn, cs;
+        sincos(d.theta[d.l + c], &sn, &cs);
+        const double ux = d.chi_u0[3 * c], uy = d.chi_u0[3 * c + 1], uz = d.chi_u0[3 * c + 2];
+        const double px = d.chi_p0[3 * c], py = d.chi_p0[3 * c + 1], pz = d.chi_p0[3 * c + 2];
+        const double vx = x - px, vy = y - py, vz = z - pz;
+        const double w = (ux * vx + uy * vy + uz * vz) * (1.0 - cs);  // Rodrigues: v cos + (u x v) sin + u (u.v)(1 - cos)
+        x = px + vx * cs + (uy * vz - uz * vy) * sn + ux * w;
+        y = py + vy * cs + (uz * vx - ux * vz) * sn + uy * w;
+        z = pz + vz * cs + (ux * vy - uy * vx) * sn + uz * w;
+    }
+    T* out = reinterpret_cast<T*>(d.r0fk);
+    out[3 * a] = num<T>(x);
+    out[3 * a + 1] = num<T>(y);
+    out[3 * a + 2] = num<T>(z);
+}
+
 template <int J>
 void launch_fk_j(DevChain& d, cudaStream_t s) {
+    if (d.nmv > 0) {
+        if (d.prm.precision == KCM_MIXED) k_side_fk<df><<<(d.nmv + 127) / 128, 128, 0, s>>>(d);
+        else k_side_fk<double><<<(d.nmv + 127) / 128, 128, 0, s>>>(d);
+    }
     if (d.prm.precision == KCM_MIXED) {
         k_fk_scan<J, df><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
         k_fk_apply<J, df><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);

@@ -61,6 +61,7 @@ int validate_params(const kcm_params* p, std::string* err) {
     if (p->precision != KCM_FP64 && p->precision != KCM_MIXED) { *err = "bad precision"; return KCM_E_INVAL; }
     if (p->step_mode != KCM_STEP_CLAMP && p->step_mode != KCM_STEP_NORMALIZED) { *err = "bad step_mode"; return KCM_E_INVAL; }
     if (p->solvation < 0 || p->solvation > 2) { *err = "solvation must be 0, 1 or 2"; return KCM_E_INVAL; }
+    if (p->side_joints != 0 && p->side_joints != 1) { *err = "side_joints must be 0 or 1"; return KCM_E_INVAL; }
     return KCM_OK;
 }
 
@@ -293,6 +294,29 @@ int build_host_chain(const kcm_topology* top, HostChain* hc, std::string* err) {
             put(hc->zp_rel, iH(i + 1), nstep[i] + loc[iH(i + 1)] - loc[iCA(i)]);
         }
     }
+    // side-chain joints: chi_k of residue i (k = 1 .. min(4, nside - 1)) about the ZP bond from CA
+    // (k = 1) or side atom k - 2 to side atom k - 1, in the frame of link 2i+1 (origin N_i, where
+    // zp_rel of CA and the side atoms is loc)
+    for (int i = 0; i < m; ++i) {
+        const int nchi = std::min(4, nside[i] - 1);
+        const int c0 = hc->ls;
+        for (int k = 1; k <= nchi; ++k) {
+            const int a = k == 1 ? iCA(i) : iS(i, k - 2), b = iS(i, k - 1);
+            const V3 u = unit(loc[b] - loc[a]);
+            hc->chi_a.push_back(a);
+            hc->chi_b.push_back(b);
+            hc->chi_end.push_back(iS(i, 0) + nside[i]);
+            hc->chi_p0.insert(hc->chi_p0.end(), {loc[a].x, loc[a].y, loc[a].z});
+            hc->chi_u0.insert(hc->chi_u0.end(), {u.x, u.y, u.z});
+            ++hc->ls;
+        }
+        for (int s = 1; s < nside[i] && nchi > 0; ++s) {  // side atom s turns with chi_1 .. chi_min(s, nchi)
+            hc->mv_atom.push_back(iS(i, s));
+            hc->mv_chi0.push_back(c0);
+            hc->mv_nk.push_back(std::min(s, nchi));
+        }
+    }
+    hc->side_off = {0, hc->ls};
     // bond-class masks over the window (lo, lo + d), d = 1..63; every pair within three bonds
     // must fall inside the window (a pair with a residue gap of two or more is never that close)
     hc->ex_mask.assign(n, 0);
@@ -317,8 +341,9 @@ void concat_chains(const std::vector<HostChain>& parts, HostChain* out) {
     b.atom_off.assign(1, 0);
     b.joint_off.assign(1, 0);
     b.link_off.assign(1, 0);
+    b.side_off.assign(1, 0);
     for (const HostChain& p : parts) {
-        const int a0 = b.n, h0 = b.L;
+        const int a0 = b.n, h0 = b.L, c0 = b.ls;
         b.m += p.m;
         b.n += p.n;
         b.l += p.l;
@@ -326,6 +351,20 @@ void concat_chains(const std::vector<HostChain>& parts, HostChain* out) {
         b.atom_off.push_back(b.n);
         b.joint_off.push_back(b.l);
         b.link_off.push_back(b.L);
+        for (int c = 0; c < p.ls; ++c) {
+            b.chi_a.push_back(p.chi_a[c] + a0);
+            b.chi_b.push_back(p.chi_b[c] + a0);
+            b.chi_end.push_back(p.chi_end[c] + a0);
+        }
+        b.chi_p0.insert(b.chi_p0.end(), p.chi_p0.begin(), p.chi_p0.end());
+        b.chi_u0.insert(b.chi_u0.end(), p.chi_u0.begin(), p.chi_u0.end());
+        for (size_t k = 0; k < p.mv_atom.size(); ++k) {
+            b.mv_atom.push_back(p.mv_atom[k] + a0);
+            b.mv_chi0.push_back(p.mv_chi0[k] + c0);
+            b.mv_nk.push_back(p.mv_nk[k]);
+        }
+        b.ls += p.ls;
+        b.side_off.push_back(b.ls);
         b.zp.insert(b.zp.end(), p.zp.begin(), p.zp.end());
         for (int a = 0; a < p.n; ++a) {
             b.link.push_back(p.link[a] + h0);

@@ -42,10 +42,20 @@ struct HostChain {
     std::vector<double> step0;       // frame step: axis point of joint j minus that of joint j-1 [l*3]
     std::vector<double> zp_rel;      // ZP offset of each atom from its link frame origin [n*3]
     std::vector<uint64_t> ex_mask, m14_mask;  // bond-class masks [n]
+    // side-chain joints (eq. kin_05, r2), residue by residue: joint c turns about the bond
+    // chi_a[c] -> chi_b[c] (CA or side atom k - 2 -> side atom k - 1) and moves atoms
+    // chi_b[c] + 1 .. chi_end[c] - 1 (the side atoms beyond it); chi_p0 / chi_u0 give the bond's first
+    // atom and unit direction in the frame of the residue's CA link (the frame of zp_rel)
+    int ls = 0;
+    std::vector<int> chi_a, chi_b, chi_end;  // [ls]
+    std::vector<double> chi_p0, chi_u0;      // [ls*3]
+    // atoms that side-chain joints move: the atom, the first joint of its residue, how many act on it
+    std::vector<int> mv_atom, mv_chi0, mv_nk;
     // a batch of chains is their concatenation (atoms, links and joints in chain order); chain c
     // owns atoms [atom_off[c], atom_off[c+1]), joints [joint_off[c], ...) and links [link_off[c], ...)
     int nchains = 1;
     std::vector<int> atom_off, joint_off, link_off;  // [nchains + 1]
+    std::vector<int> side_off;                       // side-chain joints of chain c [nchains + 1]
 };
 
 double gamma_of_class(int cls);

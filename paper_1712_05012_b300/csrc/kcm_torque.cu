@@ -280,8 +280,38 @@ __device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
     }
 }
 
-// tau_k from P^agg; with STEP the clamped step of the chains still running and the end of the
-// iteration
+// torque of side-chain joint c (the branch sums of Sec. 3.5 over its side group): the moment about
+// its current bond axis of the forces on the atoms it moves, tau = u . sum_s (r_s - a) x F_s, a the
+// bond's first atom and u its unit direction (at most nine atoms; FP64 in both modes)
+__device__ double side_torque(const DevChain& d, int c) {
+    const int a = d.chi_a[c], b = d.chi_b[c], e = d.chi_end[c];
+    const double ax = d.r[3 * a], ay = d.r[3 * a + 1], az = d.r[3 * a + 2];
+    double ux = d.r[3 * b] - ax, uy = d.r[3 * b + 1] - ay, uz = d.r[3 * b + 2] - az;
+    const double inv = 1.0 / sqrt(ux * ux + uy * uy + uz * uz);
+    ux *= inv;
+    uy *= inv;
+    uz *= inv;
+    double mx = 0.0, my = 0.0, mz = 0.0;
+    for (int s = b + 1; s < e; ++s) {
+        double f[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (d.prm.precision == KCM_MIXED)
+                f[k] = (double)d.Fpx[3 * s + k] * kPairFxInv + (double)d.Fov[3 * s + k];
+            else
+                f[k] = d.Fpair[3 * s + k];
+            if (d.prm.solvation) f[k] += (double)d.Fcav[3 * s + k] * kFxInv;
+        }
+        const double rx = d.r[3 * s] - ax, ry = d.r[3 * s + 1] - ay, rz = d.r[3 * s + 2] - az;
+        mx += ry * f[2] - rz * f[1];
+        my += rz * f[0] - rx * f[2];
+        mz += rx * f[1] - ry * f[0];
+    }
+    return ux * mx + uy * my + uz * mz;
+}
+
+// tau_k from P^agg (main-chain joints) or from its side group (side-chain joints, after them); with
+// STEP the clamped step of the chains still running and the end of the iteration
 template <bool STEP, class T>
 __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
     constexpr bool DF = std::is_same<T, df>::value;
@@ -292,23 +322,30 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
     unsigned long long adt = 0ULL, atau = 0ULL;  // bit patterns of non-negative doubles
     bool bad = false;
     int cj = -1;
-    if (jj < d.l) {
-        cj = joint_chain(d, jj);
-        const int h = jj + cj + 1, tile = h >> 5;  // joint jj moves links h .. the chain's last link
-        const T* ls = reinterpret_cast<const T*>(d.lane_suf);
-        const T* ts = reinterpret_cast<const T*>(d.tileSuf);
-        const bool own = d.ltail[h] != 0;  // the chain ends within this tile
-        T A[6];
+    if (jj < d.l + d.ls) {
+        double t;
+        if (jj < d.l) {
+            cj = joint_chain(d, jj);
+            const int h = jj + cj + 1, tile = h >> 5;  // joint jj moves links h .. the chain's last link
+            const T* ls = reinterpret_cast<const T*>(d.lane_suf);
+            const T* ts = reinterpret_cast<const T*>(d.tileSuf);
+            const bool own = d.ltail[h] != 0;  // the chain ends within this tile
+            T A[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) A[k] = own ? ls[6 * (size_t)h + k] : add(ls[6 * (size_t)h + k], ts[6 * (size_t)tile + k]);
-        const T* u = reinterpret_cast<const T*>(DF ? d.ucurdf : d.ucur) + 3 * jj;
-        const T* p = reinterpret_cast<const T*>(DF ? d.pcurdf : d.pcur) + 3 * jj;
-        const T px = sub(mul(p[1], u[2]), mul(p[2], u[1]));
-        const T py = sub(mul(p[2], u[0]), mul(p[0], u[2]));
-        const T pz = sub(mul(p[0], u[1]), mul(p[1], u[0]));
-        const T tt = add(add(add(mul(u[0], A[0]), mul(u[1], A[1])), add(mul(u[2], A[2]), mul(px, A[3]))),
-                         add(mul(py, A[4]), mul(pz, A[5])));
-        const double t = to_double(tt);
+            for (int k = 0; k < 6; ++k) A[k] = own ? ls[6 * (size_t)h + k] : add(ls[6 * (size_t)h + k], ts[6 * (size_t)tile + k]);
+            const T* u = reinterpret_cast<const T*>(DF ? d.ucurdf : d.ucur) + 3 * jj;
+            const T* p = reinterpret_cast<const T*>(DF ? d.pcurdf : d.pcur) + 3 * jj;
+            const T px = sub(mul(p[1], u[2]), mul(p[2], u[1]));
+            const T py = sub(mul(p[2], u[0]), mul(p[0], u[2]));
+            const T pz = sub(mul(p[0], u[1]), mul(p[1], u[0]));
+            const T tt = add(add(add(mul(u[0], A[0]), mul(u[1], A[1])), add(mul(u[2], A[2]), mul(px, A[3]))),
+                             add(mul(py, A[4]), mul(pz, A[5])));
+            t = to_double(tt);
+        } else {
+            const int c = jj - d.l;
+            cj = atom_chain(d, d.chi_b[c]);
+            t = side_torque(d, c);
+        }
         d.tau[jj] = t;
         bad = !isfinite(t);
         if (bad) atomicOr(&d.chain_err[cj], kErrNonfinite);
@@ -337,7 +374,7 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
 }
 
 // the paper's normalised step (eq. KCM_07): dtheta_k = kappa tau_k / max |tau| over the free joints of
-// the joint's chain (a fixed joint takes none)
+// the joint's chain, main and side (a fixed joint takes none)
 __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
     __shared__ bool last;
     Status* st = d.status;
@@ -345,8 +382,8 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
     const int jj = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long adt = 0ULL;
     int cj = -1;
-    if (jj < d.l && !st->error) {
-        cj = joint_chain(d, jj);
+    if (jj < d.l + d.ls && !st->error) {
+        cj = jj < d.l ? joint_chain(d, jj) : atom_chain(d, d.chi_b[jj - d.l]);
         if (d.chain_done[cj]) {
             cj = -1;
         } else {
@@ -372,10 +409,10 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
 void launch_torques(DevChain& d, cudaStream_t s) {
     if (d.prm.precision == KCM_MIXED) {
         k_wrench_tile<df><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
-        k_torque<false, df><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+        k_torque<false, df><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
     } else {
         k_wrench_tile<double><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
-        k_torque<false, double><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+        k_torque<false, double><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
     }
 }
 
@@ -383,10 +420,10 @@ template <class T>
 void launch_torques_step_t(DevChain& d, cudaStream_t s) {
     k_wrench_tile<T><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
     if (d.prm.step_mode == KCM_STEP_CLAMP) {
-        k_torque<true, T><<<(d.l + 127) / 128, 128, 0, s>>>(d);
+        k_torque<true, T><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
     } else {
-        k_torque<false, T><<<(d.l + 127) / 128, 128, 0, s>>>(d);
-        k_step_normalized<<<(d.l + 127) / 128, 128, 0, s>>>(d);
+        k_torque<false, T><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
+        k_step_normalized<<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
     }
 }
 

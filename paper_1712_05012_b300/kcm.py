@@ -56,7 +56,8 @@ class Params(C.Structure):
                 ("dtheta_max", C.c_double), ("w14_elec", C.c_double), ("w14_vdw", C.c_double),
                 ("r_probe", C.c_double), ("delta_r", C.c_double), ("coulomb_k", C.c_double),
                 ("conv_tol", C.c_double), ("cell_size", C.c_double), ("n_sample", C.c_int32),
-                ("solvation", C.c_int32), ("precision", C.c_int32), ("step_mode", C.c_int32)]
+                ("solvation", C.c_int32), ("precision", C.c_int32), ("step_mode", C.c_int32),
+                ("side_joints", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -74,7 +75,8 @@ EXPORTS = [
     "kcm_create_batch", "kcm_nchains", "kcm_chain_offsets", "kcm_chain_energies", "kcm_chain_state",
     "kcm_set_chain_max_iters", "kcm_device_bytes", "kcm_server_create", "kcm_server_destroy", "kcm_server_submit",
     "kcm_server_tick", "kcm_server_poll", "kcm_server_job", "kcm_server_device_bytes", "kcm_autotune_cell",
-    "kcm_set_fixed_joints",
+    "kcm_set_fixed_joints", "kcm_nside_joints", "kcm_set_side_theta", "kcm_get_side_theta", "kcm_side_torques",
+    "kcm_side_offsets",
 ]
 AUTOTUNE_MAX = 64
 # candidate cell edges of the autotuner (A): 0 is the smallest 27-cell edge; edges below the largest
@@ -121,6 +123,11 @@ def load():
             "kcm_get_stats": (C.c_int, [h, C.POINTER(Stats)]),
             "kcm_autotune_cell": (C.c_int, [h, _dp, C.c_int32, C.c_int32, _dp, _dp]),
             "kcm_set_fixed_joints": (C.c_int, [h, C.c_void_p, C.c_int64]),
+            "kcm_nside_joints": (C.c_int64, [h]),
+            "kcm_set_side_theta": (C.c_int, [h, _dp, C.c_int64]),
+            "kcm_get_side_theta": (C.c_int, [h, _dp, C.c_int64]),
+            "kcm_side_torques": (C.c_int, [h, _dp, C.c_int64]),
+            "kcm_side_offsets": (C.c_int, [h, C.POINTER(C.c_int64)]),
             "kcm_stream": (C.c_void_p, [h]),
             "kcm_sample_points": (C.c_int, [C.c_int32, _dp]),
             "kcm_build_zp": (C.c_int, [C.POINTER(Topology), _dp, _ip, C.c_int64]),
@@ -276,6 +283,10 @@ class Chain:
         jo = np.zeros(self.nchains + 1, dtype=np.int64)
         _check(L.kcm_chain_offsets(h, ao.ctypes.data_as(C.POINTER(C.c_int64)), jo.ctypes.data_as(C.POINTER(C.c_int64))), h)
         self.atom_off, self.joint_off = ao, jo
+        self.ls = int(L.kcm_nside_joints(h))
+        so = np.zeros(self.nchains + 1, dtype=np.int64)
+        _check(L.kcm_side_offsets(h, so.ctypes.data_as(C.POINTER(C.c_int64))), h)
+        self.side_off = so
 
     def close(self):
         if getattr(self, "_h", None):
@@ -306,6 +317,21 @@ class Chain:
         th = np.zeros(self.l)
         _check(load().kcm_get_theta(self._h, _dptr(th), self.l), self._h)
         return th
+
+    def set_side_theta(self, chi):
+        """Side-chain joint angles chi [ls] (params.side_joints = 1)."""
+        c = np.ascontiguousarray(chi, dtype=np.float64)
+        _check(load().kcm_set_side_theta(self._h, _dptr(c), len(c)), self._h)
+
+    def get_side_theta(self):
+        c = np.zeros(self.ls)
+        _check(load().kcm_get_side_theta(self._h, _dptr(c), self.ls), self._h)
+        return c
+
+    def side_torques(self):
+        t = np.zeros(self.ls)
+        _check(load().kcm_side_torques(self._h, _dptr(t), self.ls), self._h)
+        return t
 
     def set_theta_dev(self, ptr: int, l: int):
         _check(load().kcm_set_theta_dev(self._h, C.c_void_p(ptr), l), self._h)
@@ -439,8 +465,8 @@ class Batch(Chain):
         self._init_handle(h)
 
     def split(self, x, per="atom"):
-        """The per-chain pieces of a batch array (per atom or per joint)."""
-        off = self.atom_off if per == "atom" else self.joint_off
+        """The per-chain pieces of a batch array (per atom, joint or side-chain joint)."""
+        off = {"atom": self.atom_off, "joint": self.joint_off, "side": self.side_off}[per]
         return [x[off[c]:off[c + 1]] for c in range(self.nchains)]
 
 

@@ -159,6 +159,7 @@ class RunParams:
     solvation: int = 1
     precision: int = 0  # 0 = FP64, 1 = mixed (FP32 pair/solvation arithmetic, FP64 scans)
     step_mode: int = 0  # 0 = per-joint clamp of kappa*tau, 1 = the paper's kappa*tau/max|tau|
+    side_joints: int = 0  # 1 = side-chain joints chi_1..chi_4 (eq. kin_05), stepped with the main chain
 
 
 PRECISION_FP64 = 0

@@ -80,6 +80,9 @@ def test_error_paths(table):
     with pytest.raises(kcm.KcmError) as e:
         kcm.Chain(seq, table, synth.RunParams(n_sample=0))
     assert e.value.code == kcm.KCM_E_INVAL
+    with pytest.raises(kcm.KcmError) as e:
+        kcm.Chain(seq, table, synth.RunParams(side_joints=2))
+    assert e.value.code == kcm.KCM_E_INVAL
     bad = seq.copy()
     bad[1] = 99
     with pytest.raises(kcm.KcmError) as e:
@@ -94,3 +97,17 @@ def test_create_without_device_fails_loudly(table):
     with pytest.raises(kcm.KcmError) as e:
         kcm.Chain(synth.sequence(4, 1), table, synth.RunParams())
     assert e.value.code == kcm.KCM_E_NODEVICE
+
+
+def test_params_layout_and_defaults():
+    """The binding's kcm_params has the C struct's size (eleven doubles, five int32, padded to 8) and
+    kcm_params_default fills every field, the last one included."""
+    import ctypes
+    assert ctypes.sizeof(kcm.Params) == 112
+    p = kcm.Params()
+    for name, _ in kcm.Params._fields_:
+        setattr(p, name, 7)
+    assert kcm.load().kcm_params_default(ctypes.byref(p)) == kcm.KCM_OK
+    d = synth.RunParams()
+    for name, _ in kcm.Params._fields_:
+        assert getattr(p, name) == getattr(d, name), name
