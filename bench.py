@@ -409,10 +409,11 @@ def run_ours(args):
     if args.fp64_steps > 0:
         with kcm.Chain(seq, table, synth.RunParams(precision=prec, side_joints=1)) as cx:
             sx = torch.cuda.ExternalStream(cx.stream())
-            chi0 = np.zeros(cx.ls)
+            chi0 = torch.zeros(cx.ls, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
 
             def prep_x():
-                cx.set_side_theta(chi0)
+                cx.set_side_theta_dev(chi0.data_ptr())
                 prepare(cx, sx)
 
             for _ in range(3):

@@ -335,6 +335,9 @@ int kcm_set_fixed_joints(kcm_handle h, const uint8_t* fixed, int64_t l);
 int64_t kcm_nside_joints(kcm_handle h);
 int kcm_set_side_theta(kcm_handle h, const double* chi, int64_t ls);
 int kcm_get_side_theta(kcm_handle h, double* chi, int64_t ls);
+/* The same with device pointers (stream-ordered, no synchronisation; no finiteness check). */
+int kcm_set_side_theta_dev(kcm_handle h, const double* chi_dev, int64_t ls);
+int kcm_get_side_theta_dev(kcm_handle h, double* chi_dev, int64_t ls);
 /* torques of the side-chain joints at the current angles: tau = u . sum_s (r_s - a) x F_s over the side
  * atoms s the joint moves, u its current unit bond axis and a the bond's first atom (evaluates) */
 int kcm_side_torques(kcm_handle h, double* tau, int64_t ls);

@@ -75,7 +75,7 @@ int sync(kcm_ctx* h) {
 // Algorithm 1: the atoms with long neighbour lists are taken by a second kernel on a side stream,
 // forked after the pair kernel and joined before the wrenches (a parallel branch of the captured graph)
 void enqueue_sasa(kcm_ctx* h, cudaStream_t s) {
-    if (h->side) {
+    if (h->side && h->d.prm.solvation == 1) {
         cudaEventRecord(h->fork, s);
         cudaStreamWaitEvent(h->side, h->fork, 0);
         kcm::launch_sasa_long(h->d, h->side);
@@ -330,7 +330,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         h->own_stream = true;
     }
 
-    if (prm->solvation == 1) {
+    if (prm->solvation == 1) {  // the long solvation lists run beside the main solvation kernel
         e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
@@ -463,13 +463,23 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         std::vector<int2> mv(d.nmv);
         for (int k = 0; k < d.nmv; ++k) mv[k] = make_int2(hc.mv_chi0[k], hc.mv_nk[k]);
         const size_t ls = static_cast<size_t>(d.ls);
+        std::vector<int> chi_tile(d.ltiles + 1, d.ls);  // side-chain joints by the wrench tile of their link
+        for (int c = d.ls - 1; c >= 0; --c) chi_tile[hc.link[hc.chi_b[c]] / 32] = c;
+        for (int t = d.ltiles - 1; t >= 0; --t) chi_tile[t] = std::min(chi_tile[t], chi_tile[t + 1]);
+        for (int t = 0; t < d.ltiles; ++t)  // one thread of the wrench kernel per side-chain joint of a tile
+            if (chi_tile[t + 1] - chi_tile[t] > kcm::kWrenchWarps * 32)
+                return bail(set_err(h, KCM_E_INVAL, "internal: a wrench tile holds too many side-chain joints"));
+        const bool mixed = prm->precision == KCM_MIXED;  // the bond tables in the kernels' number format
+        const std::vector<double> p0 = mixed ? pack_df(hc.chi_p0) : hc.chi_p0, u0 = mixed ? pack_df(hc.chi_u0) : hc.chi_u0,
+                                  inv = mixed ? pack_df(hc.chi_inv) : hc.chi_inv;
         if ((rc = dalloc(h, &d.r0fk, 3 * nn)) || (rc = dalloc(h, &d.chi_a, ls)) || (rc = dalloc(h, &d.chi_b, ls)) ||
             (rc = dalloc(h, &d.chi_end, ls)) || (rc = dalloc(h, &d.chi_p0, 3 * ls)) || (rc = dalloc(h, &d.chi_u0, 3 * ls)) ||
-            (rc = dalloc(h, &d.mv_atom, d.nmv)) || (rc = dalloc(h, &d.mv_chi, d.nmv)) ||
+            (rc = dalloc(h, &d.chi_inv, ls)) || (rc = dalloc(h, &d.mv_atom, d.nmv)) || (rc = dalloc(h, &d.mv_chi, d.nmv)) ||
             (rc = upload(h, d.chi_a, hc.chi_a.data(), ls)) || (rc = upload(h, d.chi_b, hc.chi_b.data(), ls)) ||
-            (rc = upload(h, d.chi_end, hc.chi_end.data(), ls)) || (rc = upload(h, d.chi_p0, hc.chi_p0.data(), 3 * ls)) ||
-            (rc = upload(h, d.chi_u0, hc.chi_u0.data(), 3 * ls)) || (rc = upload(h, d.mv_atom, hc.mv_atom.data(), d.nmv)) ||
-            (rc = upload(h, d.mv_chi, mv.data(), d.nmv)))
+            (rc = upload(h, d.chi_end, hc.chi_end.data(), ls)) || (rc = upload(h, d.chi_p0, p0.data(), 3 * ls)) ||
+            (rc = upload(h, d.chi_u0, u0.data(), 3 * ls)) || (rc = upload(h, d.chi_inv, inv.data(), ls)) ||
+            (rc = upload(h, d.mv_atom, hc.mv_atom.data(), d.nmv)) || (rc = upload(h, d.mv_chi, mv.data(), d.nmv)) ||
+            (rc = dalloc(h, &d.chi_tile, d.ltiles + 1)) || (rc = upload(h, d.chi_tile, chi_tile.data(), d.ltiles + 1)))
             return bail(rc);
         e = cudaMemcpyAsync(d.r0fk, r0mode, sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, h->stream);
         if (e != cudaSuccess) { cuda_fail(h, e, "offset copy"); return bail(KCM_E_CUDA); }
@@ -573,6 +583,22 @@ int kcm_get_side_theta(kcm_handle h, double* chi, int64_t ls) {
     cudaError_t e = cudaMemcpyAsync(chi, h->d.theta + h->d.l, sizeof(double) * ls, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "chi copy");
     return sync(h);
+}
+
+int kcm_set_side_theta_dev(kcm_handle h, const double* chi_dev, int64_t ls) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (ls != h->d.ls || (ls > 0 && !chi_dev)) return set_err(h, KCM_E_INVAL, "chi length must equal the side-chain joint count");
+    if (ls == 0) return KCM_OK;
+    cudaError_t e = cudaMemcpyAsync(h->d.theta + h->d.l, chi_dev, sizeof(double) * ls, cudaMemcpyDeviceToDevice, h->stream);
+    return e == cudaSuccess ? KCM_OK : cuda_fail(h, e, "chi copy");
+}
+
+int kcm_get_side_theta_dev(kcm_handle h, double* chi_dev, int64_t ls) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (ls != h->d.ls || (ls > 0 && !chi_dev)) return set_err(h, KCM_E_INVAL, "chi length must equal the side-chain joint count");
+    if (ls == 0) return KCM_OK;
+    cudaError_t e = cudaMemcpyAsync(chi_dev, h->d.theta + h->d.l, sizeof(double) * ls, cudaMemcpyDeviceToDevice, h->stream);
+    return e == cudaSuccess ? KCM_OK : cuda_fail(h, e, "chi copy");
 }
 
 int kcm_side_torques(kcm_handle h, double* tau, int64_t ls) {

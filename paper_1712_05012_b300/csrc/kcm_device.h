@@ -67,6 +67,7 @@ constexpr int kSasaWarps = 4;
 constexpr int kSasaLongBlocks = 32;  // most blocks of the long-list solvation kernels
 constexpr int kApplyTpb = 64;
 constexpr int kWrenchTileAtoms = 352;  // atoms of 32 links of at most 11 atoms (checked at creation)
+constexpr int kSideFkThreads = 128;  // moved side atoms per block of the side-chain kinematics
 constexpr int kWrenchWarps = 6;        // warps per 32-link tile of the wrench kernel (one per wrench component in the scan)
 
 struct DevChain {
@@ -105,10 +106,13 @@ struct DevChain {
     int* chi_a = nullptr;          // side-chain joint c turns about the bond chi_a -> chi_b [ls]
     int* chi_b = nullptr;          // [ls]
     int* chi_end = nullptr;        // it moves atoms chi_b + 1 .. chi_end - 1 [ls]
+    // in the mode's number format (double, or double-float pairs in mixed mode):
     double* chi_p0 = nullptr;      // the bond's first atom in its link frame (ZP) [ls*3]
     double* chi_u0 = nullptr;      // the bond's unit direction in its link frame (ZP) [ls*3]
+    double* chi_inv = nullptr;     // 1 / the bond's length [ls]
     int* mv_atom = nullptr;        // atom moved by side-chain joints [nmv]
     int2* mv_chi = nullptr;        // its residue's first side-chain joint, how many joints act on it [nmv]
+    int* chi_tile = nullptr;       // side-chain joints of the links of wrench tile t: [chi_tile[t], chi_tile[t+1]) [ltiles+1]
     double* step0 = nullptr;       // link frame steps p0_j - p0_{j-1} [l*3]
     dbl4* aprm64 = nullptr;     // per atom: q, sqrt(eps), R, Roff
     float4* aprm32 = nullptr;      // the same in float

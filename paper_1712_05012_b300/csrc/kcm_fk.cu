@@ -199,12 +199,72 @@ __device__ __forceinline__ void block_scan_quads(T* a, bool& f, T* tot, bool& tf
     __syncthreads();
 }
 
+// Side-chain joints (eq. kin_05, r2): the offsets, in the frame of their CA link, of the side atoms
+// that chi_1 .. chi_k turn. In the ZP frame the rotations compose from the most distal joint inward,
+// x = T_1(T_2(... T_k(x0))) with T_c(x) = a_c + Rot(u_c, chi_c)(x - a_c) about the ZP bond (a_c, u_c):
+// each T_c then turns about its bond where the ZP has it, and the link pose (the main-chain joints)
+// takes the result to the current frame like every other atom of the link. Run by extra blocks of
+// the transform-scan kernel, beside the scan (the apply kernel reads the result). Block b takes 128
+// moved atoms (residue by residue); its threads first form sin and cos of the joints those atoms need
+// (at most 128 + 3: a residue has no more joints than moved atoms, so only the block's first residue
+// can bring joints beyond its atoms) into shared memory, then each thread turns its atom (at most four
+// rotations). FP64, or double-float on the FP32 pipe in mixed mode, as the main-chain kinematics.
+template <class T>
+__device__ __forceinline__ void side_fk_block(const DevChain& d, int b) {
+    constexpr bool DF = std::is_same<T, df>::value;
+    constexpr int kJ = kSideFkThreads + 4;
+    __shared__ T sS[kJ], sC[kJ];
+    const int t0 = b * kSideFkThreads, t = t0 + threadIdx.x;
+    const int2 last = d.mv_chi[min(t0 + kSideFkThreads, d.nmv) - 1];
+    const int j0 = d.mv_chi[t0].x, j1 = last.x + last.y;  // the joints of the block's atoms
+    // the thread's atom, loaded before the barrier
+    const T* r0 = reinterpret_cast<const T*>(DF ? d.r0df : d.r0);
+    const bool act = t < d.nmv;
+    const int a = act ? d.mv_atom[t] : 0;
+    const int2 mc = act ? d.mv_chi[t] : make_int2(0, 0);
+    T x = r0[3 * a], y = r0[3 * a + 1], z = r0[3 * a + 2];
+    for (int j = j0 + threadIdx.x; j < j1; j += kSideFkThreads) {
+        T sn, cs;
+        if constexpr (DF) {
+            df_sincos(d.theta[d.l + j], &sn, &cs);
+        } else {
+            sincos(d.theta[d.l + j], &sn, &cs);
+        }
+        sS[j - j0] = sn;
+        sC[j - j0] = cs;
+    }
+    __syncthreads();
+    if (!act) return;
+    const T* P = reinterpret_cast<const T*>(d.chi_p0);
+    const T* U = reinterpret_cast<const T*>(d.chi_u0);
+    for (int k = mc.y - 1; k >= 0; --k) {
+        const int c = mc.x + k;
+        const T sn = sS[c - j0], cs = sC[c - j0];
+        const T ux = U[3 * c], uy = U[3 * c + 1], uz = U[3 * c + 2];
+        const T px = P[3 * c], py = P[3 * c + 1], pz = P[3 * c + 2];
+        const T vx = sub(x, px), vy = sub(y, py), vz = sub(z, pz);
+        // Rodrigues: v cos + (u x v) sin + u (u . v)(1 - cos)
+        const T w = mul(fma(ux, vx, fma(uy, vy, mul(uz, vz))), sub(num_f<T>(1.0f), cs));
+        x = add(add(px, mul(vx, cs)), fma(sub(mul(uy, vz), mul(uz, vy)), sn, mul(ux, w)));
+        y = add(add(py, mul(vy, cs)), fma(sub(mul(uz, vx), mul(ux, vz)), sn, mul(uy, w)));
+        z = add(add(pz, mul(vz, cs)), fma(sub(mul(ux, vy), mul(uy, vx)), sn, mul(uz, w)));
+    }
+    T* out = reinterpret_cast<T*>(d.r0fk);
+    out[3 * a] = x;
+    out[3 * a + 1] = y;
+    out[3 * a + 2] = z;
+}
+
 template <int J, class T>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
     __shared__ T sW[kFkWarps][12];
     __shared__ int sF[kFkWarps];
     __shared__ bool sLast;
     if (d.status->done) return;
+    if (blockIdx.x >= d.ntiles) {  // the blocks after the scan's: side-chain joints
+        side_fk_block<T>(d, blockIdx.x - d.ntiles);
+        return;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
     const int slot = w * 8 + q;
@@ -290,14 +350,14 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
     }
     // Many blocks: the last block scans the block products, E_b = segmented product of blocks 0 .. b-1.
     // Few: every apply block reduces the products before it in one tree (a shorter critical path).
-    if (gridDim.x <= kFkTreeTiles) return;
+    if (d.ntiles <= kFkTreeTiles) return;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) sLast = atomicAdd(&d.status->ticket_fk, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) sLast = atomicAdd(&d.status->ticket_fk, 1u) == (unsigned)d.ntiles - 1;
     __syncthreads();
     if (!sLast) return;
     __threadfence();
-    const int nt = gridDim.x;
+    const int nt = d.ntiles;
     const int per = (nt + kFkQuads - 1) / kFkQuads;  // block products per quad, in order
     const int t0 = slot * per;
     T run[4];
@@ -587,49 +647,15 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     }
 }
 
-// Side-chain joints (eq. kin_05, r2): the offsets, in the frame of their CA link, of the side atoms
-// that chi_1 .. chi_k turn. In the ZP frame the rotations compose from the most distal joint inward,
-// x = T_1(T_2(... T_k(x0))) with T_c(x) = a_c + Rot(u_c, chi_c)(x - a_c) about the ZP bond (a_c, u_c):
-// each T_c then turns about its bond where the ZP has it, and the link pose (the main-chain joints)
-// takes the result to the current frame like every other atom of the link. One thread per moved
-// atom (at most four rotations, in FP64; written as double-float pairs in mixed mode).
-template <class T>
-__global__ void __launch_bounds__(128) k_side_fk(const DevChain d) {
-    if (d.status->done) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= d.nmv) return;
-    const int a = d.mv_atom[t];
-    const int2 mc = d.mv_chi[t];
-    double x = d.r0[3 * a], y = d.r0[3 * a + 1], z = d.r0[3 * a + 2];
-    for (int k = mc.y - 1; k >= 0; --k) {
-        const int c = mc.x + k;
-        double sn, cs;
-        sincos(d.theta[d.l + c], &sn, &cs);
-        const double ux = d.chi_u0[3 * c], uy = d.chi_u0[3 * c + 1], uz = d.chi_u0[3 * c + 2];
-        const double px = d.chi_p0[3 * c], py = d.chi_p0[3 * c + 1], pz = d.chi_p0[3 * c + 2];
-        const double vx = x - px, vy = y - py, vz = z - pz;
-        const double w = (ux * vx + uy * vy + uz * vz) * (1.0 - cs);  // Rodrigues: v cos + (u x v) sin + u (u.v)(1 - cos)
-        x = px + vx * cs + (uy * vz - uz * vy) * sn + ux * w;
-        y = py + vy * cs + (uz * vx - ux * vz) * sn + uy * w;
-        z = pz + vz * cs + (ux * vy - uy * vx) * sn + uz * w;
-    }
-    T* out = reinterpret_cast<T*>(d.r0fk);
-    out[3 * a] = num<T>(x);
-    out[3 * a + 1] = num<T>(y);
-    out[3 * a + 2] = num<T>(z);
-}
-
 template <int J>
 void launch_fk_j(DevChain& d, cudaStream_t s) {
-    if (d.nmv > 0) {
-        if (d.prm.precision == KCM_MIXED) k_side_fk<df><<<(d.nmv + 127) / 128, 128, 0, s>>>(d);
-        else k_side_fk<double><<<(d.nmv + 127) / 128, 128, 0, s>>>(d);
-    }
+    // the scan kernel's grid: ntiles scan blocks, then the side-chain joints' blocks
+    const int nscan = d.ntiles + (d.nmv + kSideFkThreads - 1) / kSideFkThreads;
     if (d.prm.precision == KCM_MIXED) {
-        k_fk_scan<J, df><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+        k_fk_scan<J, df><<<nscan, kFkWarps * 32, 0, s>>>(d);
         k_fk_apply<J, df><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
     } else {
-        k_fk_scan<J, double><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+        k_fk_scan<J, double><<<nscan, kFkWarps * 32, 0, s>>>(d);
         k_fk_apply<J, double><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
     }
 }

@@ -302,7 +302,9 @@ int build_host_chain(const kcm_topology* top, HostChain* hc, std::string* err) {
         const int c0 = hc->ls;
         for (int k = 1; k <= nchi; ++k) {
             const int a = k == 1 ? iCA(i) : iS(i, k - 2), b = iS(i, k - 1);
-            const V3 u = unit(loc[b] - loc[a]);
+            const V3 ab = loc[b] - loc[a];
+            const V3 u = unit(ab);
+            hc->chi_inv.push_back(1.0 / std::sqrt(dot(ab, ab)));
             hc->chi_a.push_back(a);
             hc->chi_b.push_back(b);
             hc->chi_end.push_back(iS(i, 0) + nside[i]);
@@ -358,6 +360,7 @@ void concat_chains(const std::vector<HostChain>& parts, HostChain* out) {
         }
         b.chi_p0.insert(b.chi_p0.end(), p.chi_p0.begin(), p.chi_p0.end());
         b.chi_u0.insert(b.chi_u0.end(), p.chi_u0.begin(), p.chi_u0.end());
+        b.chi_inv.insert(b.chi_inv.end(), p.chi_inv.begin(), p.chi_inv.end());
         for (size_t k = 0; k < p.mv_atom.size(); ++k) {
             b.mv_atom.push_back(p.mv_atom[k] + a0);
             b.mv_chi0.push_back(p.mv_chi0[k] + c0);

@@ -49,6 +49,7 @@ struct HostChain {
     int ls = 0;
     std::vector<int> chi_a, chi_b, chi_end;  // [ls]
     std::vector<double> chi_p0, chi_u0;      // [ls*3]
+    std::vector<double> chi_inv;             // 1 / bond length (the kinematics keep it) [ls]
     // atoms that side-chain joints move: the atom, the first joint of its residue, how many act on it
     std::vector<int> mv_atom, mv_chi0, mv_nk;
     // a batch of chains is their concatenation (atoms, links and joints in chain order); chain c

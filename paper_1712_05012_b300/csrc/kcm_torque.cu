@@ -51,7 +51,7 @@ __device__ __forceinline__ void chain_add(double* arr, int stride, int c, V v) {
 // the tile's P_h from the end (Kogge-Stone, segmented at the last link of each chain: a chain's
 // sums never take in the next chain), and the last block to finish (ticket, no waiting) forms the
 // segmented exclusive suffix sums of the tile totals.
-template <class T>
+template <class T, bool SIDE>
 __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChain d) {
     constexpr bool DF = std::is_same<T, df>::value;
     __shared__ T sV[kWrenchTileAtoms][6];
@@ -65,6 +65,26 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     const int h0 = 32 * t, h1 = min(h0 + 32, d.L);
     const int a0 = d.link_start[h0], a1 = d.link_start[h1];
     const T* rr = reinterpret_cast<const T*>(DF ? d.rdf : d.r);
+    // side-chain joint of the thread among those of the tile's links (at most 64: four per CA link):
+    // its bond a -> b, the end of the atoms it moves, the bond's first atom and unit direction
+    // u = (b - a) / |b - a| (the ZP bond length), loaded here so that they arrive during the atom loop
+    int sc = 0, sc1 = 0, sb = 0, se = 0;
+    T sA[3], sU[3];
+    if (SIDE) {
+        sc = d.chi_tile[t] + threadIdx.x;
+        sc1 = d.chi_tile[t + 1];
+        if (sc < sc1) {
+            const int a = d.chi_a[sc];
+            sb = d.chi_b[sc];
+            se = d.chi_end[sc];
+            const T inv = reinterpret_cast<const T*>(d.chi_inv)[sc];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                sA[k] = rr[3 * a + k];
+                sU[k] = mul(sub(rr[3 * sb + k], sA[k]), inv);
+            }
+        }
+    }
     // energies of the thread's atoms (Coulomb, LJ, cavity) for the chain cc: FP64 mode / mixed mode
     double E[3] = {0.0, 0.0, 0.0};
     float Ef[3] = {0.0f, 0.0f, 0.0f};
@@ -170,6 +190,21 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
         if (h < h1 && !(d.lflag[h] & 1))  // a chain's base link has no joint
             for (int a = d.link_start[h]; a < d.link_start[h + 1]; ++a) s = add(s, sV[a - a0][k]);
         sP[u & 31][k] = s;
+    }
+    // side-chain joints of the tile's links: the branch sums of Sec. 3.5 over the side atoms each one
+    // moves, tau = u . (sum_s r_s x F_s - a x sum_s F_s) from the atoms' r x F and F above (the bond
+    // and its atoms were loaded at the start)
+    if (SIDE && sc < sc1) {
+        T S[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) S[k] = num_f<T>(0.0f);
+        for (int s = sb + 1; s < se; ++s)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) S[k] = add(S[k], sV[s - a0][k]);
+        const T mx = sub(S[0], sub(mul(sA[1], S[5]), mul(sA[2], S[4])));
+        const T my = sub(S[1], sub(mul(sA[2], S[3]), mul(sA[0], S[5])));
+        const T mz = sub(S[2], sub(mul(sA[0], S[4]), mul(sA[1], S[3])));
+        d.tau[d.l + sc] = to_double(add(add(mul(sU[0], mx), mul(sU[1], my)), mul(sU[2], mz)));
     }
     __syncthreads();
     T* lane_suf = reinterpret_cast<T*>(d.lane_suf);
@@ -280,38 +315,8 @@ __device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
     }
 }
 
-// torque of side-chain joint c (the branch sums of Sec. 3.5 over its side group): the moment about
-// its current bond axis of the forces on the atoms it moves, tau = u . sum_s (r_s - a) x F_s, a the
-// bond's first atom and u its unit direction (at most nine atoms; FP64 in both modes)
-__device__ double side_torque(const DevChain& d, int c) {
-    const int a = d.chi_a[c], b = d.chi_b[c], e = d.chi_end[c];
-    const double ax = d.r[3 * a], ay = d.r[3 * a + 1], az = d.r[3 * a + 2];
-    double ux = d.r[3 * b] - ax, uy = d.r[3 * b + 1] - ay, uz = d.r[3 * b + 2] - az;
-    const double inv = 1.0 / sqrt(ux * ux + uy * uy + uz * uz);
-    ux *= inv;
-    uy *= inv;
-    uz *= inv;
-    double mx = 0.0, my = 0.0, mz = 0.0;
-    for (int s = b + 1; s < e; ++s) {
-        double f[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (d.prm.precision == KCM_MIXED)
-                f[k] = (double)d.Fpx[3 * s + k] * kPairFxInv + (double)d.Fov[3 * s + k];
-            else
-                f[k] = d.Fpair[3 * s + k];
-            if (d.prm.solvation) f[k] += (double)d.Fcav[3 * s + k] * kFxInv;
-        }
-        const double rx = d.r[3 * s] - ax, ry = d.r[3 * s + 1] - ay, rz = d.r[3 * s + 2] - az;
-        mx += ry * f[2] - rz * f[1];
-        my += rz * f[0] - rx * f[2];
-        mz += rx * f[1] - ry * f[0];
-    }
-    return ux * mx + uy * my + uz * mz;
-}
-
-// tau_k from P^agg (main-chain joints) or from its side group (side-chain joints, after them); with
-// STEP the clamped step of the chains still running and the end of the iteration
+// tau_k from P^agg (main-chain joints; the side-chain joints after them have theirs from the wrench
+// kernel); with STEP the clamped step of the chains still running and the end of the iteration
 template <bool STEP, class T>
 __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
     constexpr bool DF = std::is_same<T, df>::value;
@@ -342,9 +347,8 @@ __global__ void __launch_bounds__(128) k_torque(const DevChain d) {
                              add(mul(py, A[4]), mul(pz, A[5])));
             t = to_double(tt);
         } else {
-            const int c = jj - d.l;
-            cj = atom_chain(d, d.chi_b[c]);
-            t = side_torque(d, c);
+            cj = atom_chain(d, d.chi_b[jj - d.l]);
+            t = d.tau[jj];  // formed by the wrench kernel
         }
         d.tau[jj] = t;
         bad = !isfinite(t);
@@ -406,19 +410,25 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
 
 }  // namespace
 
+template <class T>
+void launch_wrench(DevChain& d, cudaStream_t s) {
+    if (d.ls) k_wrench_tile<T, true><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+    else k_wrench_tile<T, false><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+}
+
 void launch_torques(DevChain& d, cudaStream_t s) {
     if (d.prm.precision == KCM_MIXED) {
-        k_wrench_tile<df><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+        launch_wrench<df>(d, s);
         k_torque<false, df><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
     } else {
-        k_wrench_tile<double><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+        launch_wrench<double>(d, s);
         k_torque<false, double><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
     }
 }
 
 template <class T>
 void launch_torques_step_t(DevChain& d, cudaStream_t s) {
-    k_wrench_tile<T><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+    launch_wrench<T>(d, s);
     if (d.prm.step_mode == KCM_STEP_CLAMP) {
         k_torque<true, T><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
     } else {

@@ -76,7 +76,7 @@ EXPORTS = [
     "kcm_set_chain_max_iters", "kcm_device_bytes", "kcm_server_create", "kcm_server_destroy", "kcm_server_submit",
     "kcm_server_tick", "kcm_server_poll", "kcm_server_job", "kcm_server_device_bytes", "kcm_autotune_cell",
     "kcm_set_fixed_joints", "kcm_nside_joints", "kcm_set_side_theta", "kcm_get_side_theta", "kcm_side_torques",
-    "kcm_side_offsets",
+    "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev",
 ]
 AUTOTUNE_MAX = 64
 # candidate cell edges of the autotuner (A): 0 is the smallest 27-cell edge; edges below the largest
@@ -127,6 +127,8 @@ def load():
             "kcm_set_side_theta": (C.c_int, [h, _dp, C.c_int64]),
             "kcm_get_side_theta": (C.c_int, [h, _dp, C.c_int64]),
             "kcm_side_torques": (C.c_int, [h, _dp, C.c_int64]),
+            "kcm_set_side_theta_dev": (C.c_int, [h, C.c_void_p, C.c_int64]),
+            "kcm_get_side_theta_dev": (C.c_int, [h, C.c_void_p, C.c_int64]),
             "kcm_side_offsets": (C.c_int, [h, C.POINTER(C.c_int64)]),
             "kcm_stream": (C.c_void_p, [h]),
             "kcm_sample_points": (C.c_int, [C.c_int32, _dp]),
@@ -327,6 +329,12 @@ class Chain:
         c = np.zeros(self.ls)
         _check(load().kcm_get_side_theta(self._h, _dptr(c), self.ls), self._h)
         return c
+
+    def set_side_theta_dev(self, ptr: int):
+        _check(load().kcm_set_side_theta_dev(self._h, C.c_void_p(ptr), self.ls), self._h)
+
+    def get_side_theta_dev(self, ptr: int):
+        _check(load().kcm_get_side_theta_dev(self._h, C.c_void_p(ptr), self.ls), self._h)
 
     def side_torques(self):
         t = np.zeros(self.ls)

@@ -176,3 +176,18 @@ def test_zero_side_angles_and_arguments(kcm, table):
         assert L.kcm_set_side_theta(a.handle, x.ctypes.data_as(kcm._dp), a.ls) == kcm.KCM_E_INVAL
         assert b.get_side_theta().shape == (0,)
         b.set_side_theta(np.zeros(0))
+
+
+def test_side_theta_device_pointers(kcm, table):
+    import torch
+    seq, och, th, chi = case(table, 9, 62, 1.0)
+    with kcm.Chain(seq, table, synth.RunParams(side_joints=1)) as ch:
+        src = torch.tensor(chi, dtype=torch.float64, device="cuda")
+        dst = torch.zeros_like(src)
+        torch.cuda.synchronize()
+        ch.set_side_theta_dev(src.data_ptr())
+        ch.get_side_theta_dev(dst.data_ptr())
+        torch.cuda.synchronize()
+        assert np.array_equal(ch.get_side_theta(), chi)
+        assert np.array_equal(dst.cpu().numpy(), chi)
+
