@@ -307,6 +307,14 @@ int kcm_sasa_counts(kcm_handle h, int32_t* covered, int64_t n);
  * Errors: KCM_E_NONFINITE, KCM_E_OVERFLOW (results of that iteration are not valid), KCM_E_CUDA. */
 int kcm_step(kcm_handle h, int32_t n_iters, int32_t* iters_done, double* max_dtheta);
 
+/* kcm_set_theta, kcm_step and kcm_get_theta in one call with one wait: theta_in[l] (host, NULL: the
+ * current theta) is copied to the device, up to n_iters iterations run as in kcm_step, and the final
+ * theta is copied to theta_out[l] (host, may be NULL). With page-locked host buffers the copies are
+ * asynchronous and the call waits once, for the status record; this is the host round trip of a
+ * caller that owns theta on the host. Errors as kcm_set_theta and kcm_step. */
+int kcm_step_host(kcm_handle h, const double* theta_in, double* theta_out, int64_t l, int32_t n_iters,
+                  int32_t* iters_done, double* max_dtheta);
+
 /* Enqueue n_iters iterations without synchronising (for timing with CUDA events on the stream);
  * read the outcome later with kcm_step_status. */
 int kcm_step_async(kcm_handle h, int32_t n_iters);

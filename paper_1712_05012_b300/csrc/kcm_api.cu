@@ -795,6 +795,33 @@ int kcm_step(kcm_handle h, int32_t n_iters, int32_t* iters_done, double* max_dth
     return kcm_step_status(h, iters_done, max_dtheta);
 }
 
+int kcm_step_host(kcm_handle h, const double* theta_in, double* theta_out, int64_t l, int32_t n_iters,
+                  int32_t* iters_done, double* max_dtheta) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (n_iters < 0) return set_err(h, KCM_E_INVAL, "n_iters < 0");
+    if ((theta_in || theta_out) && l != h->d.l) return set_err(h, KCM_E_INVAL, "theta length must equal the joint count");
+    for (int64_t k = 0; theta_in && k < l; ++k)
+        if (!std::isfinite(theta_in[k])) return set_err(h, KCM_E_INVAL, "theta is not finite");
+    int rc = build_graph(h);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    if (theta_in) e = cudaMemcpyAsync(h->d.theta, theta_in, sizeof(double) * l, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "theta copy");
+    kcm::launch_reset_loop(h->d, h->stream);
+    for (int32_t i = 0; i < n_iters; ++i) {
+        e = cudaGraphLaunch(h->graph, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    }
+    if (theta_out) e = cudaMemcpyAsync(theta_out, h->d.theta, sizeof(double) * l, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "theta copy");
+    kcm::Status st;
+    rc = read_status(h, &st);  // the one wait of the call
+    if (rc) return rc;
+    if (iters_done) *iters_done = st.iters;
+    if (max_dtheta) *max_dtheta = st.last_max_dtheta;
+    return status_code(h, st);
+}
+
 int kcm_autotune_cell(kcm_handle h, const double* candidates, int32_t n_candidates, int32_t reps, double* times_ms,
                       double* chosen) {
     if (check_handle(h)) return KCM_E_INVAL;

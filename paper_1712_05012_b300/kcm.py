@@ -76,7 +76,7 @@ EXPORTS = [
     "kcm_set_chain_max_iters", "kcm_device_bytes", "kcm_server_create", "kcm_server_destroy", "kcm_server_submit",
     "kcm_server_tick", "kcm_server_poll", "kcm_server_job", "kcm_server_device_bytes", "kcm_autotune_cell",
     "kcm_set_fixed_joints", "kcm_nside_joints", "kcm_set_side_theta", "kcm_get_side_theta", "kcm_side_torques",
-    "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev",
+    "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev", "kcm_step_host",
 ]
 AUTOTUNE_MAX = 64
 # candidate cell edges of the autotuner (A): 0 is the smallest 27-cell edge; edges below the largest
@@ -119,6 +119,7 @@ def load():
             "kcm_sasa_counts": (C.c_int, [h, _ip, C.c_int64]),
             "kcm_step": (C.c_int, [h, C.c_int32, _ip, _dp]),
             "kcm_step_async": (C.c_int, [h, C.c_int32]),
+            "kcm_step_host": (C.c_int, [h, _dp, _dp, C.c_int64, C.c_int32, _ip, _dp]),
             "kcm_step_status": (C.c_int, [h, _ip, _dp]),
             "kcm_get_stats": (C.c_int, [h, C.POINTER(Stats)]),
             "kcm_autotune_cell": (C.c_int, [h, _dp, C.c_int32, C.c_int32, _dp, _dp]),
@@ -386,6 +387,17 @@ class Chain:
         dm = np.zeros(1)
         _check(load().kcm_step(self._h, int(n_iters), _iptr(it), _dptr(dm)), self._h)
         return int(it[0]), float(dm[0])
+
+    def step_host(self, theta, n_iters: int):
+        """From theta (host) run up to n_iters iterations and return (theta after, iterations, max
+        |dtheta|), with one wait."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        out = np.zeros(self.l)
+        it = np.zeros(1, dtype=np.int32)
+        dm = np.zeros(1)
+        _check(load().kcm_step_host(self._h, _dptr(th), _dptr(out), len(th), int(n_iters), _iptr(it), _dptr(dm)),
+               self._h)
+        return out, int(it[0]), float(dm[0])
 
     def step_async(self, n_iters: int):
         _check(load().kcm_step_async(self._h, int(n_iters)), self._h)

@@ -209,6 +209,28 @@ def test_invalid_theta_rejected(kcm, table):
             ch.set_theta(th[:-1])
 
 
+def test_step_host_round_trip(kcm, table):
+    """kcm_step_host (theta in, iterations, theta out, one wait) equals kcm_set_theta + kcm_step +
+    kcm_get_theta (bitwise: the mixed path sums its forces in fixed point), and refuses a non-finite
+    theta."""
+    import torch
+    seq, och, th = small_case(table, 20, 7)
+    p = synth.RunParams(precision=synth.PRECISION_MIXED)
+    with kcm.Chain(seq, table, p) as a, kcm.Chain(seq, table, p) as b:
+        pin = torch.tensor(th, dtype=torch.float64).pin_memory()
+        out, it, dm = a.step_host(pin.numpy(), 5)
+        b.set_theta(th)
+        it2, dm2 = b.step(5)
+        assert (it, dm) == (it2, dm2)
+        assert np.array_equal(out, b.get_theta())
+        assert np.array_equal(a.get_theta(), out)
+        bad = th.copy()
+        bad[3] = np.inf
+        with pytest.raises(kcm.KcmError) as e:
+            a.step_host(bad, 1)
+        assert e.value.code == kcm.KCM_E_INVAL
+
+
 def test_device_pointer_calls(kcm, table):
     import torch
     seq, och, th = small_case(table, 20, 6)
