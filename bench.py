@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--chain8000-steps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-iters", type=int, default=200)
     return ap.parse_args()
@@ -302,6 +303,31 @@ def stage_breakdown(c, prep, steps):
     return {k: v / steps for k, v in stg.items()}
 
 
+def stage_rooflines(ms_stage, stats, n, fp32_peak, peaks):
+    """Achieved rate of every stage against its bound: the FP32 pipes for the pair terms and Algorithm 1's
+    tests (work counted at the last timed iteration), HBM for the rest (algorithmic bytes per atom)."""
+    rooflines = {}
+    for stage, ms in ms_stage.items():
+        sec = ms / 1e3
+        if stage == "solvation":
+            work = stats["sasa_tests"] * FLOPS_PER_SASA_TEST
+            r = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"}
+        elif stage == "pairs":
+            work = stats["pairs"] * FLOPS_PER_PAIR
+            r = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"}
+        else:
+            work = BYTES_PER_ATOM[stage] * n
+            r = {"bound": "hbm", "achieved": work / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+        r["frac"] = r["achieved"] / r["peak"]
+        r["ms_per_launch"] = ms
+        r["work_per_launch"] = work
+        rooflines[stage] = r
+    return rooflines
+
+
 def run_ours(args):
     import torch
 
@@ -357,25 +383,7 @@ def run_ours(args):
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6400.0}
-    rooflines = {}
-    for stage, ms in ms_stage.items():
-        sec = ms / 1e3
-        if stage == "solvation":
-            work = stats["sasa_tests"] * FLOPS_PER_SASA_TEST
-            r = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"}
-        elif stage == "pairs":
-            work = stats["pairs"] * FLOPS_PER_PAIR
-            r = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"}
-        else:
-            work = BYTES_PER_ATOM[stage] * n
-            r = {"bound": "hbm", "achieved": work / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
-        r["frac"] = r["achieved"] / r["peak"]
-        r["ms_per_launch"] = ms
-        r["work_per_launch"] = work
-        rooflines[stage] = r
+    rooflines = stage_rooflines(ms_stage, stats, n, fp32_peak, peaks)
     dom = max(ms_stage, key=ms_stage.get)
     roof = {k: v for k, v in rooflines[dom].items()}
     roof["kernel"] = dom
@@ -421,6 +429,46 @@ def run_ours(args):
                 cx.step(1)
             tt = time_steps(cx, prep_x, sx, args.fp64_steps)
             side_value = n * args.fp64_steps / (sum(tt) / 1e3)
+
+    # the 8,000-residue chain (83,746 atoms, 12 A cutoff), the cell edge chosen by the autotuner among
+    # 6-12 A, measured the same way, with its FP64 path beside it
+    chain8000 = None
+    if args.chain8000_steps > 0:
+        man8 = json.load(open(os.path.join(GOLDEN, "starts.json")))["chain8000"]
+        seq8 = synth.sequence(man8["residues"], man8["sequence_seed"])
+        th8 = torch.tensor(synth.theta_from_codes(np.load(os.path.join(GOLDEN, "start_chain8000.npy"))),
+                           dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        leg = {"workload": "chain8000_compact_cut12", "residues": man8["residues"]}
+        for name, pr in (("mixed", synth.PRECISION_MIXED), ("fp64", synth.PRECISION_FP64)):
+            with kcm.Chain(seq8, table, synth.RunParams(precision=pr, cutoff=12.0)) as c8:
+                s8 = torch.cuda.ExternalStream(c8.stream())
+
+                def prep8():
+                    c8.set_theta_dev(th8.data_ptr(), c8.l)
+                    with torch.cuda.stream(s8):
+                        flush.add_(1)
+
+                prep8()
+                cell, cand_ms = c8.autotune_cell(candidates=(6.0, 7.0, 8.0, 9.0, 10.0, 12.0), reps=3)
+                steps8 = args.chain8000_steps if name == "mixed" else max(2, args.chain8000_steps // 10)
+                for _ in range(3):
+                    prep8()
+                    c8.step(1)
+                tt = time_steps(c8, prep8, s8, steps8)
+                st8 = c8.stats()
+                r = {"value": ws * c8.n * steps8 / (sum(tt) / 1e3), "ms_per_step": sum(tt) / steps8,
+                     "steps": steps8, "cell_size": cell, "autotune_ms": dict(zip(("6", "7", "8", "9", "10", "12"),
+                                                                             [float(x) for x in cand_ms])),
+                     "pairs": st8["pairs"], "sasa_tests": st8["sasa_tests"]}
+                if name == "mixed":
+                    stg8 = stage_breakdown(c8, prep8, steps8)
+                    r["stage_ms"] = stg8
+                    r["rooflines"] = stage_rooflines(stg8, st8, c8.n, fp32_peak, peaks)
+                leg["atoms"] = c8.n
+                leg[name] = r
+        leg["speedup_vs_fp64"] = leg["mixed"]["value"] / leg["fp64"]["value"]
+        chain8000 = leg
 
     # the batch workload: 512 chains stepped together, one launch per stage, measured the same way
     batch = None
@@ -541,7 +589,7 @@ def run_ours(args):
                 "stage_note": "stage_ms from a second pass of the same steps with a CUDA event between stages "
                               "(each event node adds ~3 us); value and ms_per_step time whole steps only",
                 "fp64_value": fp64_value, "surrogate_value": surrogate_value, "side_joints_value": side_value,
-                "vacuum_value": vacuum_value, "batch": batch, "serving": serving,
+                "vacuum_value": vacuum_value, "chain8000": chain8000, "batch": batch, "serving": serving,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,
                 "clocks": clk, "stats": {k: stats[k] for k in ("pairs", "sasa_tests", "sasa_neighbors",
