@@ -358,6 +358,10 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             flush.add_(1)
 
+    # tile shapes (atoms per block of the pair and solvation kernels) by the library's autotuner
+    prepare(ch, lib_stream)
+    tiles_main, tiles_ms = ch.autotune_tiles(reps=5)
+    tiles = {"chosen": list(tiles_main), "times_ms": tiles_ms.round(5).tolist(), "choices": list(kcm.TILE_CHOICES)}
     clocks = Clocks(local)
     prep_main = lambda: prepare(ch, lib_stream)  # noqa: E731
     for _ in range(args.warmup):
@@ -451,6 +455,7 @@ def run_ours(args):
 
                 prep8()
                 cell, cand_ms = c8.autotune_cell(candidates=(6.0, 7.0, 8.0, 9.0, 10.0, 12.0), reps=3)
+                tiles8, _ = c8.autotune_tiles(reps=3)
                 steps8 = args.chain8000_steps if name == "mixed" else max(2, args.chain8000_steps // 10)
                 for _ in range(3):
                     prep8()
@@ -460,7 +465,7 @@ def run_ours(args):
                 r = {"value": ws * c8.n * steps8 / (sum(tt) / 1e3), "ms_per_step": sum(tt) / steps8,
                      "steps": steps8, "cell_size": cell, "autotune_ms": dict(zip(("6", "7", "8", "9", "10", "12"),
                                                                              [float(x) for x in cand_ms])),
-                     "pairs": st8["pairs"], "sasa_tests": st8["sasa_tests"]}
+                     "pairs": st8["pairs"], "sasa_tests": st8["sasa_tests"], "tiles": list(tiles8)}
                 if name == "mixed":
                     stg8 = stage_breakdown(c8, prep8, steps8)
                     r["stage_ms"] = stg8
@@ -483,6 +488,8 @@ def run_ours(args):
                 with torch.cuda.stream(sb):
                     flush.add_(1)
 
+            prep_b()
+            btiles, btiles_ms = bb.autotune_tiles(reps=2)
             for _ in range(3):
                 prep_b()
                 bb.step_timed()
@@ -496,6 +503,7 @@ def run_ours(args):
                      "ms_per_step": sum(tt) / args.batch_steps,
                      "stage_ms": stg,
                      "steps": args.batch_steps, "pairs": bst["pairs"], "sasa_tests": bst["sasa_tests"],
+                     "tiles": {"chosen": list(btiles), "times_ms": btiles_ms.round(4).tolist()},
                      "start": "every step from the stored compact starts (theta restored untimed)"}
 
     # serving: Poisson arrivals into the continuous-batching server, next to the same jobs one at a time
@@ -589,7 +597,7 @@ def run_ours(args):
                 "stage_note": "stage_ms from a second pass of the same steps with a CUDA event between stages "
                               "(each event node adds ~3 us); value and ms_per_step time whole steps only",
                 "fp64_value": fp64_value, "surrogate_value": surrogate_value, "side_joints_value": side_value,
-                "vacuum_value": vacuum_value, "chain8000": chain8000, "batch": batch, "serving": serving,
+                "vacuum_value": vacuum_value, "tiles": tiles, "chain8000": chain8000, "batch": batch, "serving": serving,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,
                 "clocks": clk, "stats": {k: stats[k] for k in ("pairs", "sasa_tests", "sasa_neighbors",

@@ -365,6 +365,21 @@ int kcm_side_offsets(kcm_handle h, int64_t* side_off);
 int kcm_autotune_cell(kcm_handle h, const double* candidates, int32_t n_candidates, int32_t reps,
                       double* times_ms, double* chosen);
 
+/* Tile shapes of the two warp-per-atom kernels: atoms (warps) per thread block of the pair kernel and
+ * of Algorithm 1's mixed-precision kernel, each 1, 2 or 4 (default 1 and 1). The result does not depend
+ * on them (each atom's work is its warp's; sums are exact or the same per atom), only the scheduling
+ * does. kcm_set_tiles sets them (synchronises; KCM_E_INVAL for another value); kcm_get_tiles reads them
+ * (either pointer may be NULL). kcm_autotune_tiles evaluates the chain at the current theta and cell
+ * edge with every pair of shapes (a warm-up, then `reps` evaluations timed with CUDA events on the
+ * handle's stream) and keeps the fastest: times_ms[9] (may be NULL) in the order (pair, solvation) =
+ * (1,1), (1,2), (1,4), (2,1), ..., (4,4); the chosen pair in *pair_warps and *sasa_warps (may be NULL).
+ * Synchronises. Errors: KCM_E_INVAL (reps not in [1, 1000]), the errors of an evaluation (the
+ * previous shapes are then restored). */
+#define KCM_TILE_CHOICES 3
+int kcm_set_tiles(kcm_handle h, int32_t pair_warps, int32_t sasa_warps);
+int kcm_get_tiles(kcm_handle h, int32_t* pair_warps, int32_t* sasa_warps);
+int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pair_warps, int32_t* sasa_warps);
+
 /* Stages of one iteration, in launch order, as timed by kcm_step_timed. */
 #define KCM_STAGE_KINEMATICS 0 /* transform scan and atom centres (eq. kin_04, r1, r2) */
 #define KCM_STAGE_BINNING 1    /* bounding box, grid, counting sort (Sec. 3.2) */

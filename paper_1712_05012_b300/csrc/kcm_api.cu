@@ -352,8 +352,6 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
     d.ntiles = (d.l + fkq * d.fk_j - 1) / (fkq * d.fk_j);
     d.ltiles = (d.L + 31) / 32;
     d.nchains = hc.nchains;
-    d.pair_blocks = (d.n + kcm::kPairWarps - 1) / kcm::kPairWarps;
-    d.sasa_blocks = (d.n + kcm::kSasaWarps - 1) / kcm::kSasaWarps;
     d.rcut2 = prm->cutoff * prm->cutoff;
     double rv = prm->vdw_cutoff > 0.0 ? prm->vdw_cutoff : prm->cutoff;
     d.rvdw2 = rv * rv;
@@ -882,6 +880,88 @@ int kcm_autotune_cell(kcm_handle h, const double* candidates, int32_t n_candidat
         for (int i = 0; i < n_candidates; ++i) times_ms[i] = t[i];
     if (chosen) *chosen = candidates[best];
     return set_cell_size(h, candidates[best]);
+}
+
+static bool tile_ok(int32_t w) {
+    for (int t : kcm::kTileWarps)
+        if (w == t) return true;
+    return false;
+}
+
+int kcm_set_tiles(kcm_handle h, int32_t pair_warps, int32_t sasa_warps) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!tile_ok(pair_warps) || !tile_ok(sasa_warps)) return set_err(h, KCM_E_INVAL, "atoms per block must be 1, 2 or 4");
+    int rc = sync(h);  // no launch of the old shape is pending when the graphs go
+    if (rc) return rc;
+    drop_graphs(h);
+    h->d.pair_warps = pair_warps;
+    h->d.sasa_warps = sasa_warps;
+    return KCM_OK;
+}
+
+int kcm_get_tiles(kcm_handle h, int32_t* pair_warps, int32_t* sasa_warps) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (pair_warps) *pair_warps = h->d.pair_warps;
+    if (sasa_warps) *sasa_warps = h->d.sasa_warps;
+    return KCM_OK;
+}
+
+int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pair_warps, int32_t* sasa_warps) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (reps < 1 || reps > 1000) return set_err(h, KCM_E_INVAL, "reps must be in [1, 1000]");
+    const int old_p = h->d.pair_warps, old_s = h->d.sasa_warps;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(h, e, "event create");
+    }
+    constexpr int nt = sizeof(kcm::kTileWarps) / sizeof(kcm::kTileWarps[0]);
+    std::vector<double> t(nt * nt, 0.0);
+    int rc = KCM_OK;
+    for (int i = 0; i < nt * nt && rc == KCM_OK; ++i) {
+        // one evaluation at the current theta (no step) per launch of a graph captured for this shape
+        rc = kcm_set_tiles(h, kcm::kTileWarps[i / nt], kcm::kTileWarps[i % nt]);
+        if (rc) break;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            kcm::launch_reset_loop(h->d, h->stream);
+            enqueue_evaluation(h);
+            e = cudaStreamEndCapture(h->stream, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->stream);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(ge, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (ge) cudaGraphExecDestroy(ge);
+        if (e != cudaSuccess) { rc = cuda_fail(h, e, "autotune run"); break; }
+        kcm::Status st;
+        rc = read_status(h, &st);
+        if (rc == KCM_OK) rc = status_code(h, st);
+        t[i] = static_cast<double>(ms) / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        kcm_set_tiles(h, old_p, old_s);
+        return rc;
+    }
+    int best = 0;
+    for (int i = 1; i < nt * nt; ++i)
+        if (t[i] < t[best]) best = i;
+    if (times_ms)
+        for (int i = 0; i < nt * nt; ++i) times_ms[i] = t[i];
+    if (pair_warps) *pair_warps = kcm::kTileWarps[best / nt];
+    if (sasa_warps) *sasa_warps = kcm::kTileWarps[best % nt];
+    return kcm_set_tiles(h, kcm::kTileWarps[best / nt], kcm::kTileWarps[best % nt]);
 }
 
 int kcm_get_stats(kcm_handle h, kcm_stats* out) {

@@ -54,7 +54,10 @@ struct Status {
 };
 
 // Launch shapes.
-constexpr int kPairWarps = 4;         // home atoms (warps) per block of the pair kernel
+// tile shapes of the two warp-per-atom kernels (pair kernel, mixed Algorithm 1): atoms (warps) per
+// block, one of kTileWarps, chosen by kcm_autotune_tiles (default 1: a finished warp's slot is taken
+// by the next atom at once instead of waiting for the rest of its block)
+constexpr int kTileWarps[3] = {1, 2, 4};
 constexpr int kScanCells = 2048;      // cells per block of the cell-count scan
 constexpr int kScanThreadsBig = 256;
 constexpr int kBinThreads = 1024;     // block of the cell-count kernel (its last block scans small grids)
@@ -80,7 +83,8 @@ struct DevChain {
     int ltiles = 0;      // suffix-sum tiles of 32 links
     int cell_cap = 0;     // cells of all chains' caps
     long long cell_alloc = 0;  // cells the cell arrays hold
-    int pair_blocks = 0, sasa_blocks = 0, scan_blocks = 0;
+    int pair_warps = 1, sasa_warps = 1;  // tile shapes: atoms per block of k_pair and k_sasa_mixed
+    int scan_blocks = 0;
     int scan_fused = 0;  // cell scan by the last block of the count kernel (cell_cap <= kScanFusedMaxCells)
     int stencil = 1;     // cells searched on either side of the home cell: 1 (edge >= largest range) or 2 (>= half of it)
     kcm_params prm{};

@@ -263,21 +263,21 @@ __global__ void k_bin_place(const DevChain d) {
 // Algorithm 1's mixed kernel does not depend on the order of a list. The per-atom results stay
 // integers here; the thread-per-atom consumers convert them to FP64 (a warp-per-atom kernel would
 // spend a whole FP64 warp instruction on each atom's lane 0).
-template <bool MIXED, int KR>
-__global__ void __launch_bounds__(kPairWarps * 32, MIXED ? 8 : 6) k_pair(const DevChain d) {
+template <bool MIXED, int KR, int W>
+__global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const DevChain d) {
     typedef typename std::conditional<MIXED, float, double>::type R;
     typedef typename std::conditional<MIXED, float4, dbl4>::type QV;
     constexpr int kW = 2 * KR + 1;  // cells per row
     constexpr bool HALF = MIXED;    // half stencil, each unordered pair once
     constexpr int kRows = HALF ? 1 + KR + KR * kW : kW * kW;
     static_assert(kRows <= 32, "one lane per row");
-    __shared__ int s_beg[kPairWarps][32];
-    __shared__ int s_off[kPairWarps][32];
-    __shared__ float2 s_sh[kPairWarps][32];
-    __shared__ QV s_qv[kPairWarps][kPairQueue];   // queued pairs: r_i - r_j, d^2
-    __shared__ int s_qts[kPairWarps][kPairQueue];  // queued pairs: sorted slot of j
+    __shared__ int s_beg[W][32];
+    __shared__ int s_off[W][32];
+    __shared__ float2 s_sh[W][32];
+    __shared__ QV s_qv[W][kPairQueue];   // queued pairs: r_i - r_j, d^2
+    __shared__ int s_qts[W][kPairQueue];  // queued pairs: sorted slot of j
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sl = blockIdx.x * kPairWarps + w;
+    const int sl = blockIdx.x * W + w;
     R Eel = 0, Evdw = 0;
     unsigned npairs = 0, nguard = 0;
     int ncount = 0;
@@ -800,13 +800,14 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_long(const DevChain d)
 constexpr int kPtsPerLane = 8;                  // sample points each lane holds in registers
 constexpr int kBatch = 32 * kPtsPerLane;         // points per batch (256)
 
-__global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed(const DevChain d) {
-    __shared__ float4 s_o[kSasaWarps][kSasaStage];   // o_j, h_j
-    __shared__ int s_idx[kSasaWarps][kSasaStage];
-    __shared__ int s_cnt[kSasaWarps][3 * kSasaStage];
-    __shared__ unsigned short s_near[kSasaWarps][kBatch];
+template <int W>
+__global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
+    __shared__ float4 s_o[W][kSasaStage];   // o_j, h_j
+    __shared__ int s_idx[W][kSasaStage];
+    __shared__ int s_cnt[W][3 * kSasaStage];
+    __shared__ unsigned short s_near[W][kBatch];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int a = blockIdx.x * kSasaWarps + w;
+    const int a = blockIdx.x * W + w;
     if (a < d.n && !d.status->done) {
         if (d.chain_done[atom_chain(d, a)]) {  // a converged chain takes no more steps
             if (lane == 0) d.sstat[a] = make_int2(0, 0);
@@ -1289,26 +1290,43 @@ void launch_binning(DevChain& d, cudaStream_t s) {
         k_bin_place<false><<<blocks(d.n, 256), 256, 0, s>>>(d);
 }
 
-void launch_pairs(DevChain& d, cudaStream_t s) {
+template <int W>
+void launch_pairs_w(DevChain& d, cudaStream_t s) {
     const bool mixed = d.prm.precision == KCM_MIXED;
+    const int nb = (d.n + W - 1) / W;
     if (d.stencil == 2) {
-        if (mixed) k_pair<true, 2><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
-        else k_pair<false, 2><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
+        if (mixed) k_pair<true, 2, W><<<nb, W * 32, 0, s>>>(d);
+        else k_pair<false, 2, W><<<nb, W * 32, 0, s>>>(d);
     } else {
-        if (mixed) k_pair<true, 1><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
-        else k_pair<false, 1><<<d.pair_blocks, kPairWarps * 32, 0, s>>>(d);
+        if (mixed) k_pair<true, 1, W><<<nb, W * 32, 0, s>>>(d);
+        else k_pair<false, 1, W><<<nb, W * 32, 0, s>>>(d);
+    }
+}
+
+// the pair kernel with pair_warps home atoms per block (a tile shape of kTileWarps)
+void launch_pairs(DevChain& d, cudaStream_t s) {
+    switch (d.pair_warps) {
+        case 1: launch_pairs_w<1>(d, s); break;
+        case 2: launch_pairs_w<2>(d, s); break;
+        default: launch_pairs_w<4>(d, s); break;
     }
 }
 
 void launch_sasa(DevChain& d, cudaStream_t s) {
+    const int nb4 = (d.n + kSasaWarps - 1) / kSasaWarps;
     if (d.prm.solvation == 2) {
-        if (d.prm.precision == KCM_MIXED) k_sasa_pw<true><<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
-        else k_sasa_pw<false><<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
+        if (d.prm.precision == KCM_MIXED) k_sasa_pw<true><<<nb4, kSasaWarps * 32, 0, s>>>(d);
+        else k_sasa_pw<false><<<nb4, kSasaWarps * 32, 0, s>>>(d);
     } else if (d.prm.solvation) {
-        if (d.prm.precision == KCM_MIXED)
-            k_sasa_mixed<<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
-        else
-            k_sasa<<<d.sasa_blocks, kSasaWarps * 32, 0, s>>>(d);
+        if (d.prm.precision == KCM_MIXED) {  // sasa_warps atoms per block (a tile shape of kTileWarps)
+            const int W = d.sasa_warps;
+            const int nb = (d.n + W - 1) / W;
+            if (W == 1) k_sasa_mixed<1><<<nb, 32, 0, s>>>(d);
+            else if (W == 2) k_sasa_mixed<2><<<nb, 64, 0, s>>>(d);
+            else k_sasa_mixed<4><<<nb, 128, 0, s>>>(d);
+        } else {
+            k_sasa<<<nb4, kSasaWarps * 32, 0, s>>>(d);
+        }
     }
 }
 

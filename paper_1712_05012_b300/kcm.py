@@ -77,7 +77,9 @@ EXPORTS = [
     "kcm_server_tick", "kcm_server_poll", "kcm_server_job", "kcm_server_device_bytes", "kcm_autotune_cell",
     "kcm_set_fixed_joints", "kcm_nside_joints", "kcm_set_side_theta", "kcm_get_side_theta", "kcm_side_torques",
     "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev", "kcm_step_host",
+    "kcm_set_tiles", "kcm_get_tiles", "kcm_autotune_tiles",
 ]
+TILE_CHOICES = (1, 2, 4)
 AUTOTUNE_MAX = 64
 # candidate cell edges of the autotuner (A): 0 is the smallest 27-cell edge; edges below the largest
 # interaction range use the 125-cell stencil and are raised to the smallest legal edge for it
@@ -123,6 +125,9 @@ def load():
             "kcm_step_status": (C.c_int, [h, _ip, _dp]),
             "kcm_get_stats": (C.c_int, [h, C.POINTER(Stats)]),
             "kcm_autotune_cell": (C.c_int, [h, _dp, C.c_int32, C.c_int32, _dp, _dp]),
+            "kcm_set_tiles": (C.c_int, [h, C.c_int32, C.c_int32]),
+            "kcm_get_tiles": (C.c_int, [h, _ip, _ip]),
+            "kcm_autotune_tiles": (C.c_int, [h, C.c_int32, _dp, _ip, _ip]),
             "kcm_set_fixed_joints": (C.c_int, [h, C.c_void_p, C.c_int64]),
             "kcm_nside_joints": (C.c_int64, [h]),
             "kcm_set_side_theta": (C.c_int, [h, _dp, C.c_int64]),
@@ -432,6 +437,25 @@ class Chain:
         ch = np.zeros(1)
         _check(load().kcm_autotune_cell(self._h, _dptr(cand), len(cand), int(reps), _dptr(t), _dptr(ch)), self._h)
         return float(ch[0]), t
+
+    def set_tiles(self, pair_warps: int, sasa_warps: int):
+        """Atoms per thread block of the pair kernel and of the mixed Algorithm-1 kernel (1, 2 or 4)."""
+        _check(load().kcm_set_tiles(self._h, int(pair_warps), int(sasa_warps)), self._h)
+
+    def get_tiles(self):
+        p = np.zeros(1, dtype=np.int32)
+        q = np.zeros(1, dtype=np.int32)
+        _check(load().kcm_get_tiles(self._h, _iptr(p), _iptr(q)), self._h)
+        return int(p[0]), int(q[0])
+
+    def autotune_tiles(self, reps: int = 3):
+        """Time an evaluation with every pair of tile shapes and keep the fastest:
+        ((pair_warps, sasa_warps), times_ms[3, 3] indexed by the shapes' positions in TILE_CHOICES)."""
+        t = np.zeros(len(TILE_CHOICES) ** 2)
+        p = np.zeros(1, dtype=np.int32)
+        q = np.zeros(1, dtype=np.int32)
+        _check(load().kcm_autotune_tiles(self._h, int(reps), _dptr(t), _iptr(p), _iptr(q)), self._h)
+        return (int(p[0]), int(q[0])), t.reshape(len(TILE_CHOICES), len(TILE_CHOICES))
 
     def stats(self) -> dict:
         s = Stats()

@@ -137,3 +137,56 @@ def test_autotune_rejects_bad_arguments(kcm, table):
             assert e.value.code == kcm.KCM_E_INVAL
         ch.autotune_cell([0.0, 6.0], reps=1)  # still usable
         ch.step(1)
+
+
+@pytest.mark.parametrize("prec", [synth.PRECISION_MIXED, synth.PRECISION_FP64])
+def test_tile_shapes_give_identical_results(kcm, table, prec):
+    """Every tile shape (atoms per block of the pair kernel and of the mixed Algorithm-1 kernel) gives
+    the same torques: each atom's work is its own warp's. Mixed mode: bitwise, trajectory included
+    (its shared sums are integers); FP64 mode: to rounding, since the order of the atoms within a cell
+    (drawn by atomic counters) orders its FP64 force sums."""
+    from test_gpu_parity import start
+    seq, th = start("chain1000")
+    p = synth.RunParams(precision=prec)
+    ref_tau = ref_th = None
+    with kcm.Chain(seq, table, p) as ch:
+        assert ch.get_tiles() == (1, 1)
+        for pw in kcm.TILE_CHOICES:
+            for sw in kcm.TILE_CHOICES:
+                ch.set_tiles(pw, sw)
+                assert ch.get_tiles() == (pw, sw)
+                ch.set_theta(th)
+                tau = ch.torques()
+                if prec == synth.PRECISION_MIXED:
+                    ch.step(2)
+                    tt = ch.get_theta()
+                if ref_tau is None:
+                    ref_tau = tau
+                    ref_th = tt if prec == synth.PRECISION_MIXED else None
+                    continue
+                if prec == synth.PRECISION_MIXED:
+                    assert np.array_equal(tau, ref_tau), (pw, sw)
+                    assert np.array_equal(tt, ref_th), (pw, sw)
+                else:
+                    assert rel_inf(tau, ref_tau) < 1e-12, (pw, sw)
+
+
+def test_autotune_tiles(kcm, table):
+    from test_gpu_parity import start
+    seq, th = start("chain1000")
+    with kcm.Chain(seq, table, synth.RunParams(precision=synth.PRECISION_MIXED)) as ch:
+        ch.set_theta(th)
+        tau0 = ch.torques()
+        (pw, sw), times = ch.autotune_tiles(reps=2)
+        assert times.shape == (3, 3) and np.all(np.isfinite(times)) and np.all(times > 0)
+        i, j = kcm.TILE_CHOICES.index(pw), kcm.TILE_CHOICES.index(sw)
+        assert times[i, j] == times.min()
+        assert ch.get_tiles() == (pw, sw)
+        assert np.array_equal(ch.get_theta(), th)  # evaluations only
+        assert np.array_equal(ch.torques(), tau0)
+        L = kcm.load()
+        for bad in ((3, 1), (1, 0), (8, 4)):
+            assert L.kcm_set_tiles(ch.handle, *bad) == kcm.KCM_E_INVAL
+        assert ch.get_tiles() == (pw, sw)
+        with pytest.raises(kcm.KcmError):
+            ch.autotune_tiles(reps=0)
