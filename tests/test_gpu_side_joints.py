@@ -191,3 +191,33 @@ def test_side_theta_device_pointers(kcm, table):
         assert np.array_equal(ch.get_side_theta(), chi)
         assert np.array_equal(dst.cpu().numpy(), chi)
 
+
+
+def test_degenerate_side_joint_sets(kcm, table):
+    """side_joints = 1 on a chain whose groups are all single atoms (no side-chain joint: the path runs
+    as with the joints off) and on one residue with the largest group (four joints, nine moved atoms)."""
+    one = [t for t in range(len(table.n_side)) if table.n_side[t] == 1]
+    seq = np.array([one[i % len(one)] for i in range(9)], dtype=np.int32)
+    th = synth.theta_uniform(9, 4)
+    p = synth.RunParams(precision=synth.PRECISION_FP64, side_joints=1)
+    with kcm.Chain(seq, table, p) as a, kcm.Chain(seq, table, synth.RunParams(precision=synth.PRECISION_FP64)) as b:
+        assert a.ls == 0
+        a.set_theta(th)
+        b.set_theta(th)
+        assert np.array_equal(a.positions(), b.positions())
+        assert rel_inf(a.torques(), b.torques()) < 1e-12
+        assert a.side_torques().shape == (0,)
+        it, _ = a.step(3)
+        assert it == 3
+    big = int(np.argmax(table.n_side))
+    seq1 = np.array([big], dtype=np.int32)
+    och = O.OracleChain(seq1, table, synth.GEOMETRY)
+    assert och.nside_joints == 4
+    th1 = synth.theta_uniform(1, 5)
+    chi = np.array([0.7, -1.1, 2.0, -0.4])
+    ref = och.evaluate(p, th1, side=chi)
+    with kcm.Chain(seq1, table, p) as c:
+        c.set_theta(th1)
+        c.set_side_theta(chi)
+        assert np.max(np.abs(c.positions() - ref["xyz"])) < 1e-12
+        assert rel_inf(c.side_torques(), ref["tau_side"]) < TOL_FP64

@@ -100,3 +100,35 @@ def test_run_steps_side_joints(table):
     assert np.max(np.abs(s1 - (s + 1e-9 * r["tau_side"]))) < 1e-15
     assert np.max(np.abs(th1 - (th + 1e-9 * r["tau"]))) < 1e-14
     assert np.max(np.abs(s1 - s)) > 1e-9
+
+
+def test_side_torques_with_surrogate_solvation(table):
+    """With the smooth pairwise solvation surrogate on (solvation = 2) the side-chain torques still equal
+    -dE/dchi, solvation energy included: the branch sums take the solvation forces too."""
+    seq, ch = chain(table, 5, 17)
+    th = synth.theta_from_codes(ch.grow_start(17))
+    s = np.random.default_rng(17).uniform(-0.3, 0.3, ch.nside_joints)
+    p = synth.RunParams(cutoff=500.0, solvation=2)
+    r = ch.evaluate(p, th, side=s)
+    assert np.abs(r["F_cav"]).max() > 0
+    h = 1e-6
+    g = np.zeros(ch.nside_joints)
+    for k in range(ch.nside_joints):
+        sp = s.copy(); sp[k] += h
+        sm = s.copy(); sm[k] -= h
+        g[k] = (ch.evaluate(p, th, side=sp)["E"].sum() - ch.evaluate(p, th, side=sm)["E"].sum()) / (2 * h)
+    assert rel_inf(r["tau_side"], -g) < 1e-5
+
+
+def test_no_side_joints_for_one_atom_groups(table):
+    """Residue types whose side group is a single atom have no side-chain joint (nothing beyond the
+    first bond to turn): a chain of them has none, and its side atoms do not move with chi."""
+    one = [t for t in range(len(table.n_side)) if table.n_side[t] == 1]
+    assert one
+    seq = np.array([one[i % len(one)] for i in range(6)], dtype=np.int32)
+    ch = O.OracleChain(seq, table, synth.GEOMETRY)
+    assert ch.nside_joints == 0
+    th = synth.theta_uniform(6, 3)
+    x0, _, _ = ch.fk(th)
+    x1, _, _ = ch.fk(th, side=np.zeros(0))
+    assert np.array_equal(x0, x1)
