@@ -245,7 +245,9 @@ int kcm_server_create(const kcm_params* params, int64_t hbm_budget_bytes, int32_
 void kcm_server_destroy(kcm_server* s);
 
 /* Queue a job: the chain `top` (copied), its start theta0[l] (l = 2 n_res, host memory, copied) and
- * its iteration cap. *job_id > 0 names it. Errors: KCM_E_INVAL (bad topology, sizes or cap). */
+ * its iteration cap. *job_id > 0 names it. With params.side_joints = 1 the job's side-chain joints
+ * start at 0 and are stepped with its main chain; kcm_server_job reports the main-chain angles.
+ * Errors: KCM_E_INVAL (bad topology, sizes or cap). */
 int kcm_server_submit(kcm_server* s, const kcm_topology* top, const double* theta0, int64_t l, int32_t max_iters,
                       int64_t* job_id);
 

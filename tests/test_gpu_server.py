@@ -79,6 +79,20 @@ def test_server_results_equal_alone(kcm, table):
         assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
 
 
+def test_server_side_joints_equal_alone(kcm, table):
+    """With side-chain joints on, every job's side groups start at chi = 0 and are stepped with its
+    main chain, in the mix as alone (FP64, 1e-9 rad on the main-chain angles it reports)."""
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=0, side_joints=1)
+    items = jobs(8, seed0=71)
+    caps = [12, 20, 7, 20, 15, 9, 20, 11]
+    got = run_server(kcm, table, p, items, caps)
+    for (seq, th), cap, r in zip(items, caps, got):
+        it, dm, th1 = alone(kcm, table, p, seq, th, cap)
+        assert r["state"] == kcm.JOB_DONE and r["error"] == 0
+        assert r["iters"] == it
+        assert np.max(np.abs(r["theta"] - th1)) < 1e-9
+
+
 def test_server_mixed_steps_equal_alone(kcm, table):
     """Mixed mode, within its per-iteration tolerance: the torques of a job in the mix and alone may
     differ by 1e-4 of the largest (rounding of the double-float kinematics depends on where the
