@@ -47,7 +47,9 @@ BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques_step": 60}  # algori
 # DRAM bytes (read + write) per launch of the stage's kernels on this workload, from one ncu capture
 # of the current kernels (profiles/k_sasa_mixed_chain1000.md); None where not captured
 DRAM_BYTES_PER_LAUNCH = {"solvation": 6.84e6}
-KERNELS_PER_ITERATION = {1: 9, 0: 8}  # reset + kinematics 2 + binning 2 + pairs 1 + solvation 1 + wrench-tile 1 + torque-step 1
+# launches of one mixed-precision iteration with solvation on: reset + kinematics 2 + binning 2 + pairs 1 +
+# solvation 2 (the main kernel and the long-list kernel beside it) + wrench-tile 1 + torque-step 1
+KERNELS_PER_ITERATION = 10
 
 
 def parse():
@@ -599,7 +601,7 @@ def run_ours(args):
                 "fp64_value": fp64_value, "surrogate_value": surrogate_value, "side_joints_value": side_value,
                 "vacuum_value": vacuum_value, "tiles": tiles, "chain8000": chain8000, "batch": batch, "serving": serving,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION[1] * args.steps,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION * args.steps,
                 "clocks": clk, "stats": {k: stats[k] for k in ("pairs", "sasa_tests", "sasa_neighbors",
                                                                  "max_neighbors", "guard_rechecks", "cells")},
                 "cell_size": stats["cell_size"]}
