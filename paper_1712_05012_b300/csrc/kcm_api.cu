@@ -19,8 +19,10 @@ struct kcm_ctx {
     bool own_stream = false;
     cudaStream_t side = nullptr;       // the long-list solvation kernel beside the main one
     cudaEvent_t fork = nullptr, join = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;        // one iteration
+    cudaGraphExec_t graph_first = nullptr;  // the loop-state reset and one iteration (a step call's first)
     cudaGraphExec_t graph_timed = nullptr;
+    kcm::Status* st_host = nullptr;          // page-locked copy of the status record (read back by the calls)
     cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
     std::vector<void*> allocs;
     size_t bytes = 0;  // device memory held
@@ -104,9 +106,12 @@ void enqueue_iteration(kcm_ctx* h) {
 }
 
 int read_status(kcm_ctx* h, kcm::Status* st) {
-    cudaError_t e = cudaMemcpyAsync(st, h->d.status, sizeof(kcm::Status), cudaMemcpyDeviceToHost, h->stream);
+    kcm::Status* dst = h->st_host ? h->st_host : st;  // page-locked: an asynchronous copy, one wait
+    cudaError_t e = cudaMemcpyAsync(dst, h->d.status, sizeof(kcm::Status), cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "status copy");
-    return sync(h);
+    int rc = sync(h);
+    if (rc == KCM_OK && dst != st) *st = *dst;
+    return rc;
 }
 
 int status_code(kcm_ctx* h, const kcm::Status& st) {
@@ -126,19 +131,38 @@ int evaluate(kcm_ctx* h) {
     return status_code(h, st);
 }
 
+// the iteration graph, and the same preceded by the loop-state reset (the first launch of a step call)
 int build_graph(kcm_ctx* h) {
-    if (h->graph) return KCM_OK;
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
-    enqueue_iteration(h);
-    e = cudaStreamEndCapture(h->stream, &g);
-    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
-    e = cudaGraphInstantiate(&h->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        h->graph = nullptr;
-        return cuda_fail(h, e, "graph instantiate");
+    if (h->graph && h->graph_first) return KCM_OK;
+    for (int first = 0; first < 2; ++first) {
+        cudaGraphExec_t* out = first ? &h->graph_first : &h->graph;
+        if (*out) continue;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+        if (first) kcm::launch_reset_loop(h->d, h->stream);
+        enqueue_iteration(h);
+        e = cudaStreamEndCapture(h->stream, &g);
+        if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+        e = cudaGraphInstantiate(out, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            *out = nullptr;
+            return cuda_fail(h, e, "graph instantiate");
+        }
+    }
+    return KCM_OK;
+}
+
+// the loop-state reset and n_iters iterations: the first with the reset in one graph launch
+int launch_steps(kcm_ctx* h, int32_t n_iters) {
+    if (n_iters == 0) {
+        kcm::launch_reset_loop(h->d, h->stream);
+        return KCM_OK;
+    }
+    for (int32_t i = 0; i < n_iters; ++i) {
+        cudaError_t e = cudaGraphLaunch(i == 0 ? h->graph_first : h->graph, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
     }
     return KCM_OK;
 }
@@ -202,8 +226,10 @@ void dfree(kcm_ctx* h, void* p, size_t bytes) {
 
 void drop_graphs(kcm_ctx* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph_first) cudaGraphExecDestroy(h->graph_first);
     if (h->graph_timed) cudaGraphExecDestroy(h->graph_timed);
     h->graph = nullptr;
+    h->graph_first = nullptr;
     h->graph_timed = nullptr;
 }
 
@@ -330,6 +356,10 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         h->own_stream = true;
     }
 
+    if (cudaMallocHost(reinterpret_cast<void**>(&h->st_host), sizeof(kcm::Status)) != cudaSuccess) {
+        cudaGetLastError();
+        h->st_host = nullptr;  // status reads then go through pageable memory
+    }
     if (prm->solvation == 1) {  // the long solvation lists run beside the main solvation kernel
         e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
@@ -640,6 +670,7 @@ void kcm_destroy(kcm_handle h) {
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->st_host) cudaFreeHost(h->st_host);
     cudaGetLastError();
     delete h;
 }
@@ -769,12 +800,7 @@ int kcm_step_async(kcm_handle h, int32_t n_iters) {
     if (n_iters < 0) return set_err(h, KCM_E_INVAL, "n_iters < 0");
     int rc = build_graph(h);
     if (rc) return rc;
-    kcm::launch_reset_loop(h->d, h->stream);
-    for (int32_t i = 0; i < n_iters; ++i) {
-        cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
-    }
-    return KCM_OK;
+    return launch_steps(h, n_iters);
 }
 
 int kcm_step_status(kcm_handle h, int32_t* iters_done, double* max_dtheta) {
@@ -805,11 +831,8 @@ int kcm_step_host(kcm_handle h, const double* theta_in, double* theta_out, int64
     cudaError_t e = cudaSuccess;
     if (theta_in) e = cudaMemcpyAsync(h->d.theta, theta_in, sizeof(double) * l, cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "theta copy");
-    kcm::launch_reset_loop(h->d, h->stream);
-    for (int32_t i = 0; i < n_iters; ++i) {
-        e = cudaGraphLaunch(h->graph, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
-    }
+    rc = launch_steps(h, n_iters);
+    if (rc) return rc;
     if (theta_out) e = cudaMemcpyAsync(theta_out, h->d.theta, sizeof(double) * l, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "theta copy");
     kcm::Status st;
