@@ -22,7 +22,7 @@
  *     matrix eq. 04_9, plus the row-scan (suffix sum) form of Sec. 3.5 for comparison;
  *   - the kinetostatic step (eq. KCM_07) in the per-joint clamped form and the normalised form.
  *
- * Readings of the paper used here (every one is listed in the design doc):
+ * Readings of the paper used here (the CUDA library takes the same ones):
  *   energies sum unordered pairs once; F = -grad E with eps = 4 d, so the Coulomb force is
  *   K q_i q_j / (2 d^3) along e_ij; a single cutoff (optionally a separate LJ cutoff), d <= r_c
  *   included; w = 0 for 1-2 and 1-3 pairs, w14 for pairs exactly 3 bonds apart, 1 otherwise;
