@@ -367,8 +367,9 @@ int kcm_side_offsets(kcm_handle h, int64_t* side_off);
 int kcm_autotune_cell(kcm_handle h, const double* candidates, int32_t n_candidates, int32_t reps,
                       double* times_ms, double* chosen);
 
-/* Tile shapes of the two warp-per-atom kernels: atoms (warps) per thread block of the pair kernel and
- * of Algorithm 1's mixed-precision kernel, each 1, 2 or 4 (default 1 and 1). The result does not depend
+/* Tile shapes of the warp-per-atom kernels: atoms (warps) per thread block of the pair kernel and of
+ * the solvation kernel (Algorithm 1's mixed-precision kernel, or the pairwise surrogate's kernel in
+ * either precision), each 1, 2 or 4 (default 1 and 1). The result does not depend
  * on them (each atom's work is its warp's; sums are exact or the same per atom), only the scheduling
  * does. kcm_set_tiles sets them (synchronises; KCM_E_INVAL for another value); kcm_get_tiles reads them
  * (either pointer may be NULL). kcm_autotune_tiles evaluates the chain at the current theta and cell

@@ -54,8 +54,8 @@ struct Status {
 };
 
 // Launch shapes.
-// tile shapes of the two warp-per-atom kernels (pair kernel, mixed Algorithm 1): atoms (warps) per
-// block, one of kTileWarps, chosen by kcm_autotune_tiles (default 1: a finished warp's slot is taken
+// tile shapes of the warp-per-atom kernels (pair kernel; mixed Algorithm 1 or the pairwise solvation
+// surrogate): atoms (warps) per block, one of kTileWarps, chosen by kcm_autotune_tiles (default 1: a finished warp's slot is taken
 // by the next atom at once instead of waiting for the rest of its block)
 constexpr int kTileWarps[3] = {1, 2, 4};
 constexpr int kScanCells = 2048;      // cells per block of the cell-count scan
@@ -83,7 +83,7 @@ struct DevChain {
     int ltiles = 0;      // suffix-sum tiles of 32 links
     int cell_cap = 0;     // cells of all chains' caps
     long long cell_alloc = 0;  // cells the cell arrays hold
-    int pair_warps = 1, sasa_warps = 1;  // tile shapes: atoms per block of k_pair and k_sasa_mixed
+    int pair_warps = 1, sasa_warps = 1;  // tile shapes: atoms per block of k_pair and of k_sasa_mixed / k_sasa_pw
     int scan_blocks = 0;
     int scan_fused = 0;  // cell scan by the last block of the count kernel (cell_cap <= kScanFusedMaxCells)
     int stencil = 1;     // cells searched on either side of the home cell: 1 (edge >= largest range) or 2 (>= half of it)

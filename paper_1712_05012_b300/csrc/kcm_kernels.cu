@@ -1127,11 +1127,11 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed_long(const DevCh
 // sums (2^-40), so they cancel exactly. A clamped factor (f_ij = 0: i inside j) zeroes E_i and its
 // forces; j inside i buries nothing. Mixed mode: FP32 on the list offsets, the overlap decision
 // d < Roff_i + Roff_j re-decided in FP64 inside the guard band (the force jumps there).
-template <bool MIXED>
-__global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_pw(const DevChain d) {
+template <bool MIXED, int W>
+__global__ void __launch_bounds__(W * 32) k_sasa_pw(const DevChain d) {
     typedef typename std::conditional<MIXED, float, double>::type R;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int a = blockIdx.x * kSasaWarps + w;
+    const int a = blockIdx.x * W + w;
     if (a >= d.n || d.status->done) return;
     if (d.chain_done[atom_chain(d, a)] || !d.gflag[a]) {
         if (lane == 0) { d.esolv[a] = 0.0; d.covered[a] = 0; d.sstat[a] = make_int2(0, 0); }
@@ -1314,9 +1314,18 @@ void launch_pairs(DevChain& d, cudaStream_t s) {
 
 void launch_sasa(DevChain& d, cudaStream_t s) {
     const int nb4 = (d.n + kSasaWarps - 1) / kSasaWarps;
-    if (d.prm.solvation == 2) {
-        if (d.prm.precision == KCM_MIXED) k_sasa_pw<true><<<nb4, kSasaWarps * 32, 0, s>>>(d);
-        else k_sasa_pw<false><<<nb4, kSasaWarps * 32, 0, s>>>(d);
+    if (d.prm.solvation == 2) {  // sasa_warps atoms per block here too
+        const int W = d.sasa_warps;
+        const int nb = (d.n + W - 1) / W;
+        if (d.prm.precision == KCM_MIXED) {
+            if (W == 1) k_sasa_pw<true, 1><<<nb, 32, 0, s>>>(d);
+            else if (W == 2) k_sasa_pw<true, 2><<<nb, 64, 0, s>>>(d);
+            else k_sasa_pw<true, 4><<<nb, 128, 0, s>>>(d);
+        } else {
+            if (W == 1) k_sasa_pw<false, 1><<<nb, 32, 0, s>>>(d);
+            else if (W == 2) k_sasa_pw<false, 2><<<nb, 64, 0, s>>>(d);
+            else k_sasa_pw<false, 4><<<nb, 128, 0, s>>>(d);
+        }
     } else if (d.prm.solvation) {
         if (d.prm.precision == KCM_MIXED) {  // sasa_warps atoms per block (a tile shape of kTileWarps)
             const int W = d.sasa_warps;
