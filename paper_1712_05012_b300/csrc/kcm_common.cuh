@@ -128,10 +128,16 @@ __device__ __forceinline__ bool covers64(double qx, double qy, double qz, double
 // coarsened when the box would need more cells than the chain's cap. Leaves cbase to the caller and
 // clears the box. Returns false for a non-finite box.
 __device__ __forceinline__ bool chain_grid(const DevChain& d, int c, GridInfo* out) {
+    // every load before the first store (the box is reset for the next evaluation)
+    unsigned long long kb[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) kb[i] = __ldcg(&d.cbox[6 * c + i]);
+    const long long cap = d.ccap[c];
     double lo[3], hi[3];
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
-        lo[i] = dkey_inv(__ldcg(&d.cbox[6 * c + i]));
-        hi[i] = dkey_inv(__ldcg(&d.cbox[6 * c + 3 + i]));
+        lo[i] = dkey_inv(kb[i]);
+        hi[i] = dkey_inv(kb[3 + i]);
         d.cbox[6 * c + i] = ~0ULL;
         d.cbox[6 * c + 3 + i] = 0ULL;
     }
@@ -142,7 +148,6 @@ __device__ __forceinline__ bool chain_grid(const DevChain& d, int c, GridInfo* o
     const double ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
     double s = fmax(fma(1e-6, fmax(ext[0], fmax(ext[1], ext[2])), d.s_base) / d.stencil, d.prm.cell_size);
     s = ceil(s * 1024.0) * (1.0 / 1024.0);
-    const long long cap = d.ccap[c];
     for (;;) {
         // n_i = floor(ext_i / s) + 1 estimated in float, then raised until n_i s > ext_i holds exactly
         // (n_i s is exact: s is a multiple of 2^-10), so the cells cover the box

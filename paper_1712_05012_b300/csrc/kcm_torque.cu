@@ -266,22 +266,26 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
 __device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
     __shared__ int s_run;
     __shared__ unsigned long long s_dm;
-    if (d.nchains == 1) {  // one chain: one thread closes it
+    if (d.nchains == 1) {  // one chain: one thread closes it, with every load issued before any store
         if (threadIdx.x == 0) {
             const unsigned long long m = __ldcg(&d.chain_maxdt[0]);
+            const int err = __ldcg(&st->error), done0 = __ldcg(&d.chain_done[0]);
+            const int it0 = __ldcg(&d.chain_iters[0]), maxit = __ldcg(&d.chain_maxit[0]), sit = __ldcg(&st->iters);
             d.chain_maxdt[0] = 0ULL;
             d.chain_maxtau[0] = 0ULL;
-            if (st->error) {
-                st->done = 1;
-            } else if (!d.chain_done[0]) {
+            bool done = done0 != 0;
+            if (!err && !done) {
                 const double mc = __longlong_as_double((long long)m);
                 d.chain_lastdt[0] = mc;
-                d.chain_iters[0] += 1;
+                d.chain_iters[0] = it0 + 1;
                 st->last_max_dtheta = mc;
-                st->iters += 1;
-                if (mc < d.prm.conv_tol || d.chain_iters[0] >= d.chain_maxit[0]) d.chain_done[0] = 1;
+                st->iters = sit + 1;
+                if (mc < d.prm.conv_tol || it0 + 1 >= maxit) {
+                    d.chain_done[0] = 1;
+                    done = true;
+                }
             }
-            if (d.chain_done[0]) st->done = 1;
+            if (err || done) st->done = 1;
             st->ticket = 0u;
         }
         return;
