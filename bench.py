@@ -507,7 +507,8 @@ def run_ours(args):
                      "ms_per_step": sum(tt) / args.batch_steps,
                      "stage_ms": stg,
                      "steps": args.batch_steps, "pairs": bst["pairs"], "sasa_tests": bst["sasa_tests"],
-                     "tiles": {"chosen": list(btiles), "times_ms": btiles_ms.round(4).tolist()},
+                     "tiles": {"chosen": list(btiles), "order": "[persistent pair grid][pair warps][solvation warps]",
+                               "times_ms": btiles_ms.round(4).tolist()},
                      "start": "every step from the stored compact starts (theta restored untimed)"}
 
     # serving: Poisson arrivals into the continuous-batching server, next to the same jobs one at a time

@@ -369,19 +369,21 @@ int kcm_autotune_cell(kcm_handle h, const double* candidates, int32_t n_candidat
 
 /* Tile shapes of the warp-per-atom kernels: atoms (warps) per thread block of the pair kernel and of
  * the solvation kernel (Algorithm 1's mixed-precision kernel, or the pairwise surrogate's kernel in
- * either precision), each 1, 2 or 4 (default 1 and 1). The result does not depend
- * on them (each atom's work is its warp's; sums are exact or the same per atom), only the scheduling
- * does. kcm_set_tiles sets them (synchronises; KCM_E_INVAL for another value); kcm_get_tiles reads them
- * (either pointer may be NULL). kcm_autotune_tiles evaluates the chain at the current theta and cell
- * edge with every pair of shapes (a warm-up, then `reps` evaluations timed with CUDA events on the
- * handle's stream) and keeps the fastest: times_ms[9] (may be NULL) in the order (pair, solvation) =
- * (1,1), (1,2), (1,4), (2,1), ..., (4,4); the chosen pair in *pair_warps and *sasa_warps (may be NULL).
- * Synchronises. Errors: KCM_E_INVAL (reps not in [1, 1000]), the errors of an evaluation (the
- * previous shapes are then restored). */
+ * either precision), each 1, 2 or 4, and the pair kernel's grid: one block per group of atoms
+ * (pair_persistent = 0) or a persistent grid of one block per resident slot, each block taking every
+ * so-many-th group (1). Defaults 1, 1, 0. The result does not depend on them (each atom's work is its
+ * warp's; sums are exact or the same per atom), only the scheduling does. kcm_set_tiles sets them
+ * (synchronises; KCM_E_INVAL for another value); kcm_get_tiles reads them (any pointer may be NULL).
+ * kcm_autotune_tiles evaluates the chain at the current theta and cell edge with every combination (a
+ * warm-up, then `reps` evaluations timed with CUDA events on the handle's stream) and keeps the
+ * fastest: times_ms[18] (may be NULL) indexed [persistent][pair shape][solvation shape], shapes in the
+ * order 1, 2, 4; the choice in the three outputs (may be NULL). Synchronises. Errors: KCM_E_INVAL
+ * (reps not in [1, 1000]), the errors of an evaluation (the previous shapes are then restored). */
 #define KCM_TILE_CHOICES 3
-int kcm_set_tiles(kcm_handle h, int32_t pair_warps, int32_t sasa_warps);
-int kcm_get_tiles(kcm_handle h, int32_t* pair_warps, int32_t* sasa_warps);
-int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pair_warps, int32_t* sasa_warps);
+int kcm_set_tiles(kcm_handle h, int32_t pair_warps, int32_t sasa_warps, int32_t pair_persistent);
+int kcm_get_tiles(kcm_handle h, int32_t* pair_warps, int32_t* sasa_warps, int32_t* pair_persistent);
+int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pair_warps, int32_t* sasa_warps,
+                       int32_t* pair_persistent);
 
 /* Stages of one iteration, in launch order, as timed by kcm_step_timed. */
 #define KCM_STAGE_KINEMATICS 0 /* transform scan and atom centres (eq. kin_04, r1, r2) */

@@ -24,6 +24,7 @@ struct kcm_ctx {
     cudaGraphExec_t graph_timed = nullptr;
     kcm::Status* st_host = nullptr;          // page-locked copy of the status record (read back by the calls)
     cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
+    int sm_count = 148;
     std::vector<void*> allocs;
     size_t bytes = 0;  // device memory held
     std::string err;
@@ -233,6 +234,18 @@ void drop_graphs(kcm_ctx* h) {
     h->graph_timed = nullptr;
 }
 
+// the pair kernel's grid: one block per W atoms, or with pair_persistent one block per resident slot
+// (SMs x resident blocks per SM of the kernel's current form)
+int set_pair_grid(kcm_ctx* h) {
+    kcm::DevChain& d = h->d;
+    d.pair_grid_cap = 0;
+    if (!d.pair_persistent) return KCM_OK;
+    const int b = kcm::pair_resident_blocks(d);
+    if (b <= 0) return cuda_fail(h, cudaGetLastError(), "occupancy query");
+    d.pair_grid_cap = b * h->sm_count;
+    return KCM_OK;
+}
+
 // Applies a requested cell edge: the stencil (one cell on either side when the edge reaches the
 // largest interaction range, two when it is smaller; the device raises the edge to the smallest
 // legal one for that stencil), each chain's cell cap (a chain's grid is coarsened to fit it; half
@@ -278,6 +291,7 @@ int set_cell_size(kcm_ctx* h, double cell_size) {
     d.scan_fused = d.cell_cap <= kcm::kScanFusedMaxCells;
     d.stencil = stencil;
     d.prm.cell_size = cell_size;
+    if (int prc = set_pair_grid(h)) return prc;  // the stencil picks the pair kernel's form
     int rc = upload(h, d.ccap, ccap.data(), hc.nchains);
     return rc ? rc : sync(h);
 }
@@ -342,6 +356,10 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         cudaGetLastError();
         set_err(h, KCM_E_NODEVICE, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
         return bail(KCM_E_NODEVICE);
+    }
+    if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        h->sm_count = 148;
     }
     if (major != 10 || minor != 3) {
         set_err(h, KCM_E_NODEVICE, "this library is built for sm_103 (B300); device is sm_" + std::to_string(major) +
@@ -911,28 +929,32 @@ static bool tile_ok(int32_t w) {
     return false;
 }
 
-int kcm_set_tiles(kcm_handle h, int32_t pair_warps, int32_t sasa_warps) {
+int kcm_set_tiles(kcm_handle h, int32_t pair_warps, int32_t sasa_warps, int32_t pair_persistent) {
     if (check_handle(h)) return KCM_E_INVAL;
     if (!tile_ok(pair_warps) || !tile_ok(sasa_warps)) return set_err(h, KCM_E_INVAL, "atoms per block must be 1, 2 or 4");
+    if (pair_persistent != 0 && pair_persistent != 1) return set_err(h, KCM_E_INVAL, "pair_persistent must be 0 or 1");
     int rc = sync(h);  // no launch of the old shape is pending when the graphs go
     if (rc) return rc;
     drop_graphs(h);
     h->d.pair_warps = pair_warps;
     h->d.sasa_warps = sasa_warps;
-    return KCM_OK;
+    h->d.pair_persistent = pair_persistent;
+    return set_pair_grid(h);
 }
 
-int kcm_get_tiles(kcm_handle h, int32_t* pair_warps, int32_t* sasa_warps) {
+int kcm_get_tiles(kcm_handle h, int32_t* pair_warps, int32_t* sasa_warps, int32_t* pair_persistent) {
     if (check_handle(h)) return KCM_E_INVAL;
     if (pair_warps) *pair_warps = h->d.pair_warps;
     if (sasa_warps) *sasa_warps = h->d.sasa_warps;
+    if (pair_persistent) *pair_persistent = h->d.pair_persistent;
     return KCM_OK;
 }
 
-int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pair_warps, int32_t* sasa_warps) {
+int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pair_warps, int32_t* sasa_warps,
+                       int32_t* pair_persistent) {
     if (check_handle(h)) return KCM_E_INVAL;
     if (reps < 1 || reps > 1000) return set_err(h, KCM_E_INVAL, "reps must be in [1, 1000]");
-    const int old_p = h->d.pair_warps, old_s = h->d.sasa_warps;
+    const int old_p = h->d.pair_warps, old_s = h->d.sasa_warps, old_pp = h->d.pair_persistent;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -941,11 +963,19 @@ int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pa
         return cuda_fail(h, e, "event create");
     }
     constexpr int nt = sizeof(kcm::kTileWarps) / sizeof(kcm::kTileWarps[0]);
-    std::vector<double> t(nt * nt, 0.0);
+    constexpr int ncomb = 2 * nt * nt;  // (persistent, pair shape, solvation shape)
+    auto shape = [&](int i, int* pp, int* pw, int* sw) {
+        *pp = i / (nt * nt);
+        *pw = kcm::kTileWarps[(i / nt) % nt];
+        *sw = kcm::kTileWarps[i % nt];
+    };
+    std::vector<double> t(ncomb, 0.0);
     int rc = KCM_OK;
-    for (int i = 0; i < nt * nt && rc == KCM_OK; ++i) {
+    for (int i = 0; i < ncomb && rc == KCM_OK; ++i) {
         // one evaluation at the current theta (no step) per launch of a graph captured for this shape
-        rc = kcm_set_tiles(h, kcm::kTileWarps[i / nt], kcm::kTileWarps[i % nt]);
+        int pp, pw, sw;
+        shape(i, &pp, &pw, &sw);
+        rc = kcm_set_tiles(h, pw, sw, pp);
         if (rc) break;
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
@@ -974,17 +1004,20 @@ int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pa
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) {
-        kcm_set_tiles(h, old_p, old_s);
+        kcm_set_tiles(h, old_p, old_s, old_pp);
         return rc;
     }
     int best = 0;
-    for (int i = 1; i < nt * nt; ++i)
+    for (int i = 1; i < ncomb; ++i)
         if (t[i] < t[best]) best = i;
     if (times_ms)
-        for (int i = 0; i < nt * nt; ++i) times_ms[i] = t[i];
-    if (pair_warps) *pair_warps = kcm::kTileWarps[best / nt];
-    if (sasa_warps) *sasa_warps = kcm::kTileWarps[best % nt];
-    return kcm_set_tiles(h, kcm::kTileWarps[best / nt], kcm::kTileWarps[best % nt]);
+        for (int i = 0; i < ncomb; ++i) times_ms[i] = t[i];
+    int pp, pw, sw;
+    shape(best, &pp, &pw, &sw);
+    if (pair_warps) *pair_warps = pw;
+    if (sasa_warps) *sasa_warps = sw;
+    if (pair_persistent) *pair_persistent = pp;
+    return kcm_set_tiles(h, pw, sw, pp);
 }
 
 int kcm_get_stats(kcm_handle h, kcm_stats* out) {

@@ -84,6 +84,8 @@ struct DevChain {
     int cell_cap = 0;     // cells of all chains' caps
     long long cell_alloc = 0;  // cells the cell arrays hold
     int pair_warps = 1, sasa_warps = 1;  // tile shapes: atoms per block of k_pair and of k_sasa_mixed / k_sasa_pw
+    int pair_persistent = 0;   // the pair kernel on a persistent grid (one block per resident slot)
+    int pair_grid_cap = 0;     // its block count then (SMs x resident blocks per SM); 0: one block per W atoms
     int scan_blocks = 0;
     int scan_fused = 0;  // cell scan by the last block of the count kernel (cell_cap <= kScanFusedMaxCells)
     int stencil = 1;     // cells searched on either side of the home cell: 1 (edge >= largest range) or 2 (>= half of it)
@@ -210,6 +212,7 @@ void launch_reset_loop(DevChain& d, cudaStream_t s);
 void launch_fk(DevChain& d, cudaStream_t s);
 void launch_binning(DevChain& d, cudaStream_t s);
 void launch_pairs(DevChain& d, cudaStream_t s);
+int pair_resident_blocks(const DevChain& d);  // resident blocks per SM of the current pair kernel (-1: error)
 void launch_sasa(DevChain& d, cudaStream_t s);
 void launch_sasa_long(DevChain& d, cudaStream_t s);  // atoms with more than kSasaStage neighbours
 void launch_torques(DevChain& d, cudaStream_t s);

@@ -277,7 +277,9 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
     __shared__ QV s_qv[W][kPairQueue];   // queued pairs: r_i - r_j, d^2
     __shared__ int s_qts[W][kPairQueue];  // queued pairs: sorted slot of j
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sl = blockIdx.x * W + w;
+    // a block takes atoms sl, sl + (blocks) W, ...: one round with the full grid, several with the
+    // persistent grid (one block per resident slot); the loop form also compiles better for one round
+    for (int sl = blockIdx.x * W + w; sl < d.n; sl += gridDim.x * W) {
     R Eel = 0, Evdw = 0;
     unsigned npairs = 0, nguard = 0;
     int ncount = 0;
@@ -618,6 +620,8 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
             else reinterpret_cast<double2*>(d.epair)[a] = make_double2(Eel, Evdw);
             d.pstat[a] = make_int2((int)npairs, (int)nguard);
         }
+    }
+    __syncwarp();  // the warp's shared rows and queue are reused by its next atom
     }
 }
 
@@ -1293,13 +1297,37 @@ void launch_binning(DevChain& d, cudaStream_t s) {
 template <int W>
 void launch_pairs_w(DevChain& d, cudaStream_t s) {
     const bool mixed = d.prm.precision == KCM_MIXED;
-    const int nb = (d.n + W - 1) / W;
+    int nb = (d.n + W - 1) / W;
+    if (d.pair_grid_cap > 0) nb = std::min(nb, d.pair_grid_cap);  // persistent grid
     if (d.stencil == 2) {
         if (mixed) k_pair<true, 2, W><<<nb, W * 32, 0, s>>>(d);
         else k_pair<false, 2, W><<<nb, W * 32, 0, s>>>(d);
     } else {
         if (mixed) k_pair<true, 1, W><<<nb, W * 32, 0, s>>>(d);
         else k_pair<false, 1, W><<<nb, W * 32, 0, s>>>(d);
+    }
+}
+
+template <int W>
+int pair_resident_w(const DevChain& d) {
+    int b = 0;
+    const bool mixed = d.prm.precision == KCM_MIXED;
+    cudaError_t e;
+    if (d.stencil == 2) {
+        e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pair<true, 2, W>, W * 32, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pair<false, 2, W>, W * 32, 0);
+    } else {
+        e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pair<true, 1, W>, W * 32, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pair<false, 1, W>, W * 32, 0);
+    }
+    return e == cudaSuccess ? b : -1;
+}
+
+int pair_resident_blocks(const DevChain& d) {
+    switch (d.pair_warps) {
+        case 1: return pair_resident_w<1>(d);
+        case 2: return pair_resident_w<2>(d);
+        default: return pair_resident_w<4>(d);
     }
 }
 

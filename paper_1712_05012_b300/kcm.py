@@ -125,9 +125,9 @@ def load():
             "kcm_step_status": (C.c_int, [h, _ip, _dp]),
             "kcm_get_stats": (C.c_int, [h, C.POINTER(Stats)]),
             "kcm_autotune_cell": (C.c_int, [h, _dp, C.c_int32, C.c_int32, _dp, _dp]),
-            "kcm_set_tiles": (C.c_int, [h, C.c_int32, C.c_int32]),
-            "kcm_get_tiles": (C.c_int, [h, _ip, _ip]),
-            "kcm_autotune_tiles": (C.c_int, [h, C.c_int32, _dp, _ip, _ip]),
+            "kcm_set_tiles": (C.c_int, [h, C.c_int32, C.c_int32, C.c_int32]),
+            "kcm_get_tiles": (C.c_int, [h, _ip, _ip, _ip]),
+            "kcm_autotune_tiles": (C.c_int, [h, C.c_int32, _dp, _ip, _ip, _ip]),
             "kcm_set_fixed_joints": (C.c_int, [h, C.c_void_p, C.c_int64]),
             "kcm_nside_joints": (C.c_int64, [h]),
             "kcm_set_side_theta": (C.c_int, [h, _dp, C.c_int64]),
@@ -438,24 +438,27 @@ class Chain:
         _check(load().kcm_autotune_cell(self._h, _dptr(cand), len(cand), int(reps), _dptr(t), _dptr(ch)), self._h)
         return float(ch[0]), t
 
-    def set_tiles(self, pair_warps: int, sasa_warps: int):
-        """Atoms per thread block of the pair kernel and of the mixed Algorithm-1 kernel (1, 2 or 4)."""
-        _check(load().kcm_set_tiles(self._h, int(pair_warps), int(sasa_warps)), self._h)
+    def set_tiles(self, pair_warps: int, sasa_warps: int, pair_persistent: int = 0):
+        """Atoms per thread block of the pair kernel and of the solvation kernel (1, 2 or 4), and whether
+        the pair kernel runs on a persistent grid."""
+        _check(load().kcm_set_tiles(self._h, int(pair_warps), int(sasa_warps), int(pair_persistent)), self._h)
 
     def get_tiles(self):
-        p = np.zeros(1, dtype=np.int32)
-        q = np.zeros(1, dtype=np.int32)
-        _check(load().kcm_get_tiles(self._h, _iptr(p), _iptr(q)), self._h)
-        return int(p[0]), int(q[0])
+        """(pair_warps, sasa_warps, pair_persistent)."""
+        p = np.zeros(3, dtype=np.int32)
+        _check(load().kcm_get_tiles(self._h, _iptr(p[0:1]), _iptr(p[1:2]), _iptr(p[2:3])), self._h)
+        return int(p[0]), int(p[1]), int(p[2])
 
     def autotune_tiles(self, reps: int = 3):
-        """Time an evaluation with every pair of tile shapes and keep the fastest:
-        ((pair_warps, sasa_warps), times_ms[3, 3] indexed by the shapes' positions in TILE_CHOICES)."""
-        t = np.zeros(len(TILE_CHOICES) ** 2)
-        p = np.zeros(1, dtype=np.int32)
-        q = np.zeros(1, dtype=np.int32)
-        _check(load().kcm_autotune_tiles(self._h, int(reps), _dptr(t), _iptr(p), _iptr(q)), self._h)
-        return (int(p[0]), int(q[0])), t.reshape(len(TILE_CHOICES), len(TILE_CHOICES))
+        """Time an evaluation with every combination of tile shapes and keep the fastest:
+        ((pair_warps, sasa_warps, pair_persistent), times_ms[2, 3, 3] indexed [persistent][pair shape]
+        [solvation shape], shapes by their positions in TILE_CHOICES)."""
+        nt = len(TILE_CHOICES)
+        t = np.zeros(2 * nt * nt)
+        p = np.zeros(3, dtype=np.int32)
+        _check(load().kcm_autotune_tiles(self._h, int(reps), _dptr(t), _iptr(p[0:1]), _iptr(p[1:2]), _iptr(p[2:3])),
+               self._h)
+        return (int(p[0]), int(p[1]), int(p[2])), t.reshape(2, nt, nt)
 
     def stats(self) -> dict:
         s = Stats()

@@ -152,26 +152,27 @@ def test_tile_shapes_give_identical_results(kcm, table, prec, solv):
     seq, th = start("chain1000")
     p = synth.RunParams(precision=prec, solvation=solv)
     ref_tau = ref_th = None
+    shapes = [(pw, sw, 0) for pw in kcm.TILE_CHOICES for sw in kcm.TILE_CHOICES] + \
+             [(pw, 1, 1) for pw in kcm.TILE_CHOICES]
     with kcm.Chain(seq, table, p) as ch:
-        assert ch.get_tiles() == (1, 1)
-        for pw in kcm.TILE_CHOICES:
-            for sw in kcm.TILE_CHOICES:
-                ch.set_tiles(pw, sw)
-                assert ch.get_tiles() == (pw, sw)
-                ch.set_theta(th)
-                tau = ch.torques()
-                if prec == synth.PRECISION_MIXED:
-                    ch.step(2)
-                    tt = ch.get_theta()
-                if ref_tau is None:
-                    ref_tau = tau
-                    ref_th = tt if prec == synth.PRECISION_MIXED else None
-                    continue
-                if prec == synth.PRECISION_MIXED and solv == 1:
-                    assert np.array_equal(tau, ref_tau), (pw, sw)
-                    assert np.array_equal(tt, ref_th), (pw, sw)
-                else:
-                    assert rel_inf(tau, ref_tau) < (1e-12 if prec == synth.PRECISION_FP64 else 1e-5), (pw, sw)
+        assert ch.get_tiles() == (1, 1, 0)
+        for pw, sw, pp in shapes:
+            ch.set_tiles(pw, sw, pp)
+            assert ch.get_tiles() == (pw, sw, pp)
+            ch.set_theta(th)
+            tau = ch.torques()
+            if prec == synth.PRECISION_MIXED:
+                ch.step(2)
+                tt = ch.get_theta()
+            if ref_tau is None:
+                ref_tau = tau
+                ref_th = tt if prec == synth.PRECISION_MIXED else None
+                continue
+            if prec == synth.PRECISION_MIXED and solv == 1:
+                assert np.array_equal(tau, ref_tau), (pw, sw, pp)
+                assert np.array_equal(tt, ref_th), (pw, sw, pp)
+            else:
+                assert rel_inf(tau, ref_tau) < (1e-12 if prec == synth.PRECISION_FP64 else 1e-5), (pw, sw, pp)
 
 
 def test_autotune_tiles(kcm, table):
@@ -180,16 +181,16 @@ def test_autotune_tiles(kcm, table):
     with kcm.Chain(seq, table, synth.RunParams(precision=synth.PRECISION_MIXED)) as ch:
         ch.set_theta(th)
         tau0 = ch.torques()
-        (pw, sw), times = ch.autotune_tiles(reps=2)
-        assert times.shape == (3, 3) and np.all(np.isfinite(times)) and np.all(times > 0)
+        (pw, sw, pp), times = ch.autotune_tiles(reps=2)
+        assert times.shape == (2, 3, 3) and np.all(np.isfinite(times)) and np.all(times > 0)
         i, j = kcm.TILE_CHOICES.index(pw), kcm.TILE_CHOICES.index(sw)
-        assert times[i, j] == times.min()
-        assert ch.get_tiles() == (pw, sw)
+        assert times[pp, i, j] == times.min()
+        assert ch.get_tiles() == (pw, sw, pp)
         assert np.array_equal(ch.get_theta(), th)  # evaluations only
         assert np.array_equal(ch.torques(), tau0)
         L = kcm.load()
-        for bad in ((3, 1), (1, 0), (8, 4)):
+        for bad in ((3, 1, 0), (1, 0, 0), (8, 4, 0), (1, 1, 2)):
             assert L.kcm_set_tiles(ch.handle, *bad) == kcm.KCM_E_INVAL
-        assert ch.get_tiles() == (pw, sw)
+        assert ch.get_tiles() == (pw, sw, pp)
         with pytest.raises(kcm.KcmError):
             ch.autotune_tiles(reps=0)
