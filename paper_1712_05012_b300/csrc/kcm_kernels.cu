@@ -868,7 +868,7 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
                     mx[p] = -INFINITY;
                 }
                 // step 1: the largest m of each point over all neighbours
-#pragma unroll 2
+#pragma unroll 4
                 for (int j = 0; j < cnt; ++j) {
                     const float4 o = s_o[w][j];
 #pragma unroll
