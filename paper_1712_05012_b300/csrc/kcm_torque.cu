@@ -45,6 +45,61 @@ __device__ __forceinline__ void chain_add(double* arr, int stride, int c, V v) {
     }
 }
 
+// Segmented exclusive suffix sums of the tile totals (component w) by the wrench kernel's last block:
+// R_t = x_t + (a chain ends in tile t ? 0 : R_{t+1}), the suffix of tile totals from t to the first
+// chain end; tileSuf_t = R_{t+1}. A lane takes K consecutive tiles (their loads issued together): its
+// own segmented suffix over them, then a warp scan of the lanes' aggregates, then the tiles' R from
+// the next lane's first R; rounds of 32 K tiles from the end, carrying R of the first tile of the
+// later round. K = 1 for a few tiles (one round of single tiles is the shortest path), 8 for many.
+template <int kSufK, class T>
+__device__ __forceinline__ void tile_suffix(const DevChain& d, T* tileSuf, int w, int lane) {
+    T carry = num_f<T>(0.0f);
+    for (int top = d.ltiles; top > 0; top -= 32 * kSufK) {
+        const int b = top - 32 * kSufK + lane * kSufK;  // the lane's first tile
+        T x[kSufK];
+        bool tl[kSufK];
+#pragma unroll
+        for (int k = 0; k < kSufK; ++k) {
+            const int tt = b + k;
+            x[k] = num_f<T>(0.0f);
+            tl[k] = true;
+            if (tt >= 0) {
+                const double raw = __ldcg(&d.tileS[6 * (size_t)tt + w]);  // the slot of a T, read past L1
+                x[k] = *reinterpret_cast<const T*>(&raw);
+                tl[k] = __ldcg(&d.tileT[tt]) != 0;
+            }
+        }
+        T r[kSufK];      // in-lane suffix from tile b + k to the first chain end or the lane's last tile
+        bool op[kSufK];  // no chain end in tiles b + k .. of the lane: the next lane's R continues it
+        r[kSufK - 1] = x[kSufK - 1];
+        op[kSufK - 1] = !tl[kSufK - 1];
+#pragma unroll
+        for (int k = kSufK - 2; k >= 0; --k) {
+            r[k] = tl[k] ? x[k] : add(x[k], r[k + 1]);
+            op[k] = !tl[k] && op[k + 1];
+        }
+        T X = r[0];
+        bool TL = !op[0];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const T y = shfl_down(X, off);
+            const bool yt = __shfl_down_sync(0xffffffffu, TL, off);
+            if (lane + off < 32 && !TL) { X = add(X, y); TL = yt; }
+        }
+        const T RL = TL ? X : add(X, carry);  // R of the lane's first tile
+        T Rn = shfl_down(RL, 1);                // R of the next lane's first tile
+        if (lane == 31) Rn = carry;
+#pragma unroll
+        for (int k = 0; k < kSufK; ++k) {
+            const int tt = b + k;
+            // tileSuf_t = R_{t+1}: the in-lane suffix of the next tile, continued by the next lane's R
+            const T e = k + 1 < kSufK ? (op[k + 1] ? add(r[k + 1], Rn) : r[k + 1]) : Rn;
+            if (tt >= 0) tileSuf[6 * (size_t)tt + w] = e;
+        }
+        carry = shfl(RL, 0);
+    }
+}
+
 // One block per tile of 32 links h in [32 t, 32 t + 32). The block's threads take the tile's atoms
 // (r x F and F, with the conversion of the mixed-mode fixed-point forces) into shared memory; one
 // thread per (component, link) adds the link's atoms in atom order; warp q then scans component q of
@@ -235,29 +290,9 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
     if (!last) return;
     __threadfence();
     T* tileSuf = reinterpret_cast<T*>(d.tileSuf);
-    if (w < 6) {  // segmented exclusive suffix sums of the tile totals, 32 tiles per round from the end
-        T carry = num_f<T>(0.0f);  // R of the first tile of the later round
-        for (int top = d.ltiles; top > 0; top -= 32) {
-            const int tt = top - 32 + lane;
-            T x = num_f<T>(0.0f);
-            bool tl = true;
-            if (tt >= 0) {
-                const double raw = __ldcg(&d.tileS[6 * (size_t)tt + w]);  // the slot of a T, read past L1
-                x = *reinterpret_cast<const T*>(&raw);
-                tl = __ldcg(&d.tileT[tt]) != 0;
-            }
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const T y = shfl_down(x, off);
-                const bool yt = __shfl_down_sync(0xffffffffu, tl, off);
-                if (lane + off < 32 && !tl) { x = add(x, y); tl = yt; }
-            }
-            const T R = tl ? x : add(x, carry);  // R_t = sum of tiles t .. the first chain end, across rounds
-            T e = shfl_down(R, 1);
-            if (lane == 31) e = carry;
-            if (tt >= 0) tileSuf[6 * (size_t)tt + w] = e;
-            carry = shfl(R, 0);
-        }
+    if (w < 6) {  // segmented exclusive suffix sums of the tile totals
+        if (d.ltiles <= 64) tile_suffix<1>(d, tileSuf, w, lane);
+        else tile_suffix<8>(d, tileSuf, w, lane);
     }
     if (threadIdx.x == 0) st->ticket_w = 0u;
 }
