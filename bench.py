@@ -104,7 +104,7 @@ def serve_pool():
     return seqs, thetas, wl
 
 
-def run_serving(kcm, table, params, rate, seconds, max_iters, budget, chunk, seed=0):
+def run_serving(kcm, table, params, rate, seconds, max_iters, budget, chunk, seed=0, admission=(1, 0.0)):
     """Poisson arrivals at `rate` jobs/s for `seconds` (jobs drawn from the pool), each run until
     converged or `max_iters`; returns latencies and throughput from the server's own clock."""
     seqs, thetas, _ = serve_pool()
@@ -114,6 +114,7 @@ def run_serving(kcm, table, params, rate, seconds, max_iters, budget, chunk, see
     pick = rng.integers(0, len(seqs), size=len(t_arr))
     ids = []
     with kcm.Server(params, budget, 512, chunk) as s:
+        s.set_admission(*admission)
         t0 = time.perf_counter()
         k = 0
         while True:
@@ -134,7 +135,8 @@ def run_serving(kcm, table, params, rate, seconds, max_iters, budget, chunk, see
             "wall_s": wall, "chains_per_s": len(ids) / wall, "atom_iterations_per_s": atom_its / wall,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "p50_queue_s": float(np.percentile(queue, 50)), "converged": int(sum(x["converged"] for x in info)),
-            "errors": int(sum(x["error"] != 0 for x in info))}
+            "errors": int(sum(x["error"] != 0 for x in info)),
+            "admission": {"min_jobs": admission[0], "max_wait_s": admission[1]}}
 
 
 def max_over_ranks(t_local: float, ws: int, device: str = "cuda") -> float:

@@ -256,6 +256,13 @@ int kcm_server_submit(kcm_server* s, const kcm_topology* top, const double* thet
  * budget allows. Reports the jobs still waiting and running (either pointer may be NULL). */
 int kcm_server_tick(kcm_server* s, int32_t* n_waiting, int32_t* n_running);
 
+/* Admission waves: a tick admits waiting jobs once min_jobs of them wait, once the oldest has waited
+ * max_wait_s seconds, or at once when no job is running (default 1 and 0: every tick admits what
+ * waits). Larger waves make fewer, larger batches (each batch's creation and per-iteration launches
+ * are paid once for all its jobs) at the price of queueing. Errors: KCM_E_INVAL (min_jobs < 1,
+ * max_wait_s negative or not finite). */
+int kcm_server_set_admission(kcm_server* s, int32_t min_jobs, double max_wait_s);
+
 /* Ids of jobs retired since the last poll (at most `capacity`; *n of them written to ids). */
 int kcm_server_poll(kcm_server* s, int64_t* ids, int32_t capacity, int32_t* n);
 

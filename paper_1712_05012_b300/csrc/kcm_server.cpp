@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdint>
 #include <cstring>
@@ -69,6 +70,8 @@ struct kcm_server {
     int64_t used = 0;
     int32_t max_chains = 0;
     int32_t chunk = 0;
+    int32_t min_wave = 1;     // admission: wait for this many jobs ...
+    double max_wait = 0.0;    // ... or until the oldest waiting job has waited this long (s)
     int64_t next_id = 1;
     std::deque<Job*> pending;
     std::vector<std::unique_ptr<Batch>> active;
@@ -167,8 +170,13 @@ int collect(kcm_server* s, Batch* b) {
     return launch_chunk(s, b);
 }
 
-// admit waiting jobs (in arrival order) that fit the budget into one new batch
+// admit waiting jobs (in arrival order) that fit the budget into one new batch: once min_wave jobs
+// wait, once the oldest has waited max_wait, or at once when nothing runs
 int admit(kcm_server* s) {
+    if (s->pending.empty()) return KCM_OK;
+    if (static_cast<int32_t>(s->pending.size()) < s->min_wave && !s->active.empty() &&
+        now(s) - s->pending.front()->t_submit < s->max_wait)
+        return KCM_OK;
     std::vector<Job*> take;
     int64_t bytes = kBytesPerBatch;
     while (!s->pending.empty() && static_cast<int32_t>(take.size()) < s->max_chains) {
@@ -314,6 +322,13 @@ int kcm_server_tick(kcm_server* s, int32_t* n_waiting, int32_t* n_running) {
         for (Job* j : b->jobs) running += j->state == KCM_JOB_RUNNING;
     if (n_waiting) *n_waiting = static_cast<int32_t>(s->pending.size());
     if (n_running) *n_running = running;
+    return KCM_OK;
+}
+
+int kcm_server_set_admission(kcm_server* s, int32_t min_jobs, double max_wait_s) {
+    if (!s || min_jobs < 1 || !(max_wait_s >= 0.0) || !std::isfinite(max_wait_s)) return KCM_E_INVAL;
+    s->min_wave = min_jobs;
+    s->max_wait = max_wait_s;
     return KCM_OK;
 }
 

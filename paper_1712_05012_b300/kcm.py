@@ -77,7 +77,7 @@ EXPORTS = [
     "kcm_server_tick", "kcm_server_poll", "kcm_server_job", "kcm_server_device_bytes", "kcm_autotune_cell",
     "kcm_set_fixed_joints", "kcm_nside_joints", "kcm_set_side_theta", "kcm_get_side_theta", "kcm_side_torques",
     "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev", "kcm_step_host",
-    "kcm_set_tiles", "kcm_get_tiles", "kcm_autotune_tiles",
+    "kcm_set_tiles", "kcm_get_tiles", "kcm_autotune_tiles", "kcm_server_set_admission",
 ]
 TILE_CHOICES = (1, 2, 4)
 AUTOTUNE_MAX = 64
@@ -163,6 +163,7 @@ def load():
             "kcm_server_poll": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int32, _ip]),
             "kcm_server_job": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(JobInfo), _dp, C.c_int64]),
             "kcm_server_device_bytes": (C.c_int64, [C.c_void_p]),
+            "kcm_server_set_admission": (C.c_int, [C.c_void_p, C.c_int32, C.c_double]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -550,6 +551,10 @@ class Server:
         _check(load().kcm_server_submit(self._s, t.ptr(), _dptr(th), len(th), int(max_iters), C.byref(jid)))
         self._tops[int(jid.value)] = len(th)
         return int(jid.value)
+
+    def set_admission(self, min_jobs: int = 1, max_wait_s: float = 0.0):
+        """Admit waiting jobs once min_jobs wait or the oldest has waited max_wait_s (or nothing runs)."""
+        _check(load().kcm_server_set_admission(self._s, int(min_jobs), float(max_wait_s)))
 
     def tick(self):
         w = np.zeros(1, dtype=np.int32)

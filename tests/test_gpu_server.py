@@ -29,11 +29,13 @@ def jobs(n, seed0=31):
     return out
 
 
-def run_server(kcm, table, p, items, caps, budget=8 << 30, max_chains=4, chunk=7, waves=3):
+def run_server(kcm, table, p, items, caps, budget=8 << 30, max_chains=4, chunk=7, waves=3, admission=None):
     """Submit the jobs in `waves` groups with ticks in between (later jobs arrive while earlier ones
     run), then tick until every job is done."""
     res = {}
     with kcm.Server(p, budget, max_chains, chunk) as s:
+        if admission:
+            s.set_admission(*admission)
         ids = []
         per = (len(items) + waves - 1) // waves
         for w in range(waves):
@@ -77,6 +79,24 @@ def test_server_results_equal_alone(kcm, table):
         assert r["iters"] == it
         assert np.max(np.abs(r["theta"] - th1)) < 1e-9
         assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+
+
+def test_server_admission_waves(kcm, table):
+    """Admission in waves (at least 5 waiting jobs, or 30 ms, or nothing running): every job still
+    runs and equals the job alone; bad settings are refused."""
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=0)
+    items = jobs(9, seed0=81)
+    caps = [12, 9, 20, 7, 15, 20, 11, 8, 14]
+    got = run_server(kcm, table, p, items, caps, admission=(5, 0.03))
+    for (seq, th), cap, r in zip(items, caps, got):
+        it, dm, th1 = alone(kcm, table, p, seq, th, cap)
+        assert r["state"] == kcm.JOB_DONE and r["error"] == 0
+        assert r["iters"] == it
+        assert np.max(np.abs(r["theta"] - th1)) < 1e-9
+    with kcm.Server(p, 1 << 30, 4, 5) as s:
+        for bad in ((0, 0.0), (1, -1.0), (1, float("inf"))):
+            with pytest.raises(kcm.KcmError):
+                s.set_admission(*bad)
 
 
 def test_server_side_joints_equal_alone(kcm, table):
