@@ -136,6 +136,7 @@ def run_serving(kcm, table, params, rate, seconds, max_iters, budget, chunk, see
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "p50_queue_s": float(np.percentile(queue, 50)), "converged": int(sum(x["converged"] for x in info)),
             "errors": int(sum(x["error"] != 0 for x in info)),
+            "error_codes": sorted({int(x["error"]) for x in info if x["error"] != 0}),
             "admission": {"min_jobs": admission[0], "max_wait_s": admission[1]}}
 
 

@@ -64,6 +64,8 @@ constexpr int kBinThreads = 1024;     // block of the cell-count kernel (its las
 constexpr int kScanFusedMaxCells = 128 * kBinThreads;  // largest cell array scanned by one block
 constexpr double kPairFxInv = 1.0 / 8388608.0;  // unit of the fraction sums of mixed-mode pair forces
 constexpr float kPairFxMax = 4194304.0f;        // |pair term| below which it is summed in fixed point (2^22)
+constexpr float kPairCoefMax = 1e32f;           // mixed: largest pair force coefficient (kcal/mol/A^2); the
+                                                // terms, r x F and their sums then stay below FP32's range
 constexpr int kPairFoldRounds = 256;            // pair rounds between folds of the int32 lane sums
 constexpr int kPairQueue = 64;                  // ring of in-range candidates per warp of the pair kernel (power of 2)
 constexpr int kSasaWarps = 4;

@@ -477,6 +477,10 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
                         coef += (R)12 * eij * (t12 - t6) * inv2;
                         e_vd = eij * (t12 - (R)2 * t6);
                     }
+                    // mixed: a near-coincident pair (d of a few thousandths of an A) overflows the FP32
+                    // term, or makes it NaN from inf - inf; it is held at a large finite repulsion, so the
+                    // torques stay finite and the clamped step goes ahead as on the FP64 path
+                    if constexpr (MIXED) { if (!(coef <= kPairCoefMax)) coef = kPairCoefMax; }
                     const bool count_e = HALF || a < b;  // each unordered pair's energy once
                     if (count_e && (we != (R)0 || wv != (R)0)) ++npairs;
                     if constexpr (MIXED) {

@@ -288,3 +288,45 @@ def test_long_neighbour_lists(kcm, table):
     assert np.array_equal(mix["covered"], f64["covered"])
     assert np.array_equal(mix["F_cav"], f64["F_cav"])
     assert rel_inf(mix["tau"], ref["tau"]) < TOL_MIXED
+
+
+def clash_conformation(table, target=0.05):
+    """A 6-residue chain bent until two atoms (CA of residue 1 and an atom of residue 6) are `target` A
+    apart (oracle kinematics: a Nelder-Mead walk to the overlap, then bisection back along the path)."""
+    from scipy.optimize import minimize
+    seq = synth.sequence(6, 7)
+    och = O.OracleChain(seq, table, synth.GEOMETRY)
+    th0 = np.random.default_rng(3).uniform(-np.pi, np.pi, och.l)
+    i, j = 2, och.n - 2
+
+    def dist(th):
+        x, _, _ = och.fk(th)
+        return float(np.linalg.norm(x[i] - x[j]))
+
+    r = minimize(lambda th: dist(th) ** 2, th0, method="Nelder-Mead",
+                 options={"maxiter": 4000, "xatol": 1e-10, "fatol": 1e-14})
+    lo, hi = 0.0, 1.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if dist(th0 + mid * (r.x - th0)) > target:
+            lo = mid
+        else:
+            hi = mid
+    th = th0 + hi * (r.x - th0)
+    assert abs(dist(th) - target) < 1e-6 * max(target, 1.0)
+    return seq, och, th
+
+
+def test_near_coincident_atoms_stay_finite(kcm, table):
+    """Atoms 0.003 A apart: the FP32 pair term overflows (measured: without a bound the mixed torques
+    come out non-finite, KCM_E_NONFINITE, from about this distance down); the mixed path holds it at a
+    large finite repulsion, so its torques stay finite and the clamped step goes ahead, like the FP64
+    path's (whose terms stay finite in double)."""
+    seq, och, th = clash_conformation(table, 0.003)
+    for prec in (synth.PRECISION_MIXED, synth.PRECISION_FP64):
+        with kcm.Chain(seq, table, synth.RunParams(precision=prec)) as ch:
+            ch.set_theta(th)
+            tau = ch.torques()
+            assert np.all(np.isfinite(tau)) and np.abs(tau).max() > 1e10
+            it, dm = ch.step(1)
+            assert it == 1 and dm == pytest.approx(0.02)
