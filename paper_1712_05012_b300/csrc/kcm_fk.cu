@@ -15,8 +15,8 @@
 // 32 J (b + 1)), J consecutive joints per quad. Each quad forms its joints' local transforms and their
 // running product (kept in G), the warp scans its eight quad products (Kogge-Stone, 3 levels), warp 0
 // scans the four warp products, and each quad stores its exclusive prefix within the block; the
-// block product goes to tileP; with more than kFkTreeTiles blocks the last block to finish (ticket,
-// no waiting) scans the block products into every block's exclusive prefix (tileE), with fewer every
+// block product goes to tileP; with more than kFkTreeTiles blocks a one-block kernel of eight warps
+// (k_fk_tiles) scans the block products into every block's exclusive prefix (tileE), with fewer every
 // apply block reduces the products before it in one tree. k_fk_apply: block b composes its prefix,
 // quad prefix and running products into the link poses, the current axes u_j and axis points p_j,
 // moves the atoms of its links and adds them to their chain's bounding box; its last block to finish
@@ -37,7 +37,7 @@ using namespace dev;
 
 constexpr int kFkWarps = 4;               // warps per block of the transform scan (one per sub-partition)
 constexpr int kFkQuads = 8 * kFkWarps;    // quads (transform slots) per block
-constexpr int kFkMaxTiles = 40 * kFkQuads;  // scan blocks whose products the last block scans (40 per quad)
+constexpr int kFkMaxTiles = 40 * kFkQuads;  // most scan blocks (k_fk_tiles' quads run through up to 20 products each)
 constexpr int kFkTreeTiles = 2 * kFkQuads;  // up to this many, every apply block reduces the earlier products itself
 
 // row rr of the identity
@@ -168,8 +168,8 @@ __device__ __forceinline__ void warp_scan_quads(T* a, bool& f, int q, int base) 
 
 // Scans the transforms held by the block's quads (row a of slot 8 w + q, flag f) in place into
 // inclusive segmented block prefixes; the block total is returned in (tf, tot) on every lane.
-// sW: [kFkWarps][12], sF: [kFkWarps] shared.
-template <class T>
+// sW: [NW][12], sF: [NW] shared (NW warps, at most 8).
+template <class T, int NW = kFkWarps>
 __device__ __forceinline__ void block_scan_quads(T* a, bool& f, T* tot, bool& tf, T (*sW)[12], int* sF, int w, int q,
                                                  int rr, int base, int lane) {
     warp_scan_quads(a, f, q, base);
@@ -179,12 +179,12 @@ __device__ __forceinline__ void block_scan_quads(T* a, bool& f, T* tot, bool& tf
     if (w == 0) {  // scan of the warp totals, quad q <- warp q
         T t[4];
         bool tfl = false;
-        if (q < kFkWarps) { load_row(sW[q], rr, t); tfl = sF[q] != 0; }
+        if (q < NW) { load_row(sW[q], rr, t); tfl = sF[q] != 0; }
         else row_identity(rr, t);
-        warp_scan_quads<kFkWarps>(t, tfl, q, base);
+        warp_scan_quads<NW>(t, tfl, q, base);
         __syncwarp();
-        if (q < kFkWarps && (lane & 3) < 3) store_row(sW[q], rr, t);  // inclusive prefix of warps 0..q
-        if (q < kFkWarps && (lane & 3) == 0) sF[q] = tfl;
+        if (q < NW && (lane & 3) < 3) store_row(sW[q], rr, t);  // inclusive prefix of warps 0..q
+        if (q < NW && (lane & 3) == 0) sF[q] = tfl;
     }
     __syncthreads();
     if (w > 0) {  // prefix of the earlier warps o own warp prefix, unless a chain starts in between
@@ -194,8 +194,8 @@ __device__ __forceinline__ void block_scan_quads(T* a, bool& f, T* tot, bool& tf
         if (!f) row_compose(P, B, a);
         f = f || sF[w - 1] != 0;
     }
-    load_row(sW[kFkWarps - 1], rr, tot);
-    tf = sF[kFkWarps - 1] != 0;
+    load_row(sW[NW - 1], rr, tot);
+    tf = sF[NW - 1] != 0;
     __syncthreads();
 }
 
@@ -259,7 +259,6 @@ template <int J, class T>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
     __shared__ T sW[kFkWarps][12];
     __shared__ int sF[kFkWarps];
-    __shared__ bool sLast;
     if (d.status->done) return;
     if (blockIdx.x >= d.ntiles) {  // the blocks after the scan's: side-chain joints
         side_fk_block<T>(d, blockIdx.x - d.ntiles);
@@ -350,15 +349,28 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
     }
     // Many blocks: the last block scans the block products, E_b = segmented product of blocks 0 .. b-1.
     // Few: every apply block reduces the products before it in one tree (a shorter critical path).
-    if (d.ntiles <= kFkTreeTiles) return;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) sLast = atomicAdd(&d.status->ticket_fk, 1u) == (unsigned)d.ntiles - 1;
-    __syncthreads();
-    if (!sLast) return;
-    __threadfence();
+}
+
+// Many scan blocks (more than kFkTreeTiles): one block of kTileWarps warps scans the block products
+// into every block's exclusive segmented prefix (tileE); each of its quads runs through
+// ceil(blocks / quads) products in order, then the quads' totals are scanned and each quad runs
+// through its products again, writing the prefixes. Eight warps (64 quads) halve the serial runs
+// of the scan kernel's own four-warp blocks.
+constexpr int kTileWarps = 8;
+constexpr int kTileQuads = 8 * kTileWarps;
+template <class T>
+__global__ void __launch_bounds__(kTileWarps * 32) k_fk_tiles(const DevChain d) {
+    __shared__ T sW[kTileWarps][12];
+    __shared__ int sF[kTileWarps];
+    if (d.status->done) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = lane >> 2, rr = min(lane & 3, 2), base = lane & ~3;
+    const int slot = w * 8 + q;
+    const T* tP = reinterpret_cast<const T*>(d.tileP);
+    T tot[4], ex[4];
+    bool tf = false, exf = false;
     const int nt = d.ntiles;
-    const int per = (nt + kFkQuads - 1) / kFkQuads;  // block products per quad, in order
+    const int per = (nt + kTileQuads - 1) / kTileQuads;  // block products per quad, in order
     const int t0 = slot * per;
     T run[4];
     bool rf = false;
@@ -375,7 +387,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
         rf = rf || pf;
     }
     bool xf = rf;
-    block_scan_quads(run, xf, tot, tf, sW, sF, w, q, rr, base, lane);
+    block_scan_quads<T, kTileWarps>(run, xf, tot, tf, sW, sF, w, q, rr, base, lane);
     // exclusive prefix of the quad: the inclusive prefix of the quad before it
 #pragma unroll
     for (int m = 0; m < 4; ++m) ex[m] = shfl_up(run[m], 4);
@@ -400,7 +412,6 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
         if (pf) { for (int m = 0; m < 4; ++m) ex[m] = p[m]; }
         else row_compose(ex, B, ex);
     }
-    if (threadIdx.x == 0) d.status->ticket_fk = 0u;
 }
 
 // row rr (and flag) of the segmented product of the block products b0 .. b1 - 1 (identity, no flag,
@@ -651,11 +662,14 @@ template <int J>
 void launch_fk_j(DevChain& d, cudaStream_t s) {
     // the scan kernel's grid: ntiles scan blocks, then the side-chain joints' blocks
     const int nscan = d.ntiles + (d.nmv + kSideFkThreads - 1) / kSideFkThreads;
+    const bool tiles = d.ntiles > kFkTreeTiles;  // the block products scanned by k_fk_tiles
     if (d.prm.precision == KCM_MIXED) {
         k_fk_scan<J, df><<<nscan, kFkWarps * 32, 0, s>>>(d);
+        if (tiles) k_fk_tiles<df><<<1, kTileWarps * 32, 0, s>>>(d);
         k_fk_apply<J, df><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
     } else {
         k_fk_scan<J, double><<<nscan, kFkWarps * 32, 0, s>>>(d);
+        if (tiles) k_fk_tiles<double><<<1, kTileWarps * 32, 0, s>>>(d);
         k_fk_apply<J, double><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
     }
 }
