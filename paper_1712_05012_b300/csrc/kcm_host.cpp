@@ -319,18 +319,53 @@ int build_host_chain(const kcm_topology* top, HostChain* hc, std::string* err) {
         }
     }
     hc->side_off = {0, hc->ls};
-    // bond-class masks over the window (lo, lo + d), d = 1..63; every pair within three bonds
-    // must fall inside the window (a pair with a residue gap of two or more is never that close)
+    // bond-class masks over the window (lo, lo + d), d = 1..63, from a breadth-first walk of at most
+    // three bonds out of every atom over the bond tree (parent and children): pairs one or two bonds
+    // apart are excluded, three bonds apart are 1-4; every such pair must fall inside the window (a
+    // pair with a residue gap of two or more is never that close)
     hc->ex_mask.assign(n, 0);
     hc->m14_mask.assign(n, 0);
+    std::vector<int> coff(n + 1, 0), kids(n > 0 ? n - 1 : 0);
+    for (int a = 0; a < hc->n; ++a)
+        if (hc->parent[a] >= 0) ++coff[hc->parent[a] + 1];
+    for (int a = 0; a < hc->n; ++a) coff[a + 1] += coff[a];
+    {
+        std::vector<int> fill(coff.begin(), coff.end() - 1);
+        for (int a = 0; a < hc->n; ++a)
+            if (hc->parent[a] >= 0) kids[fill[hc->parent[a]]++] = a;
+    }
+    int frontier[2][64], nf[2];
     for (int a = 0; a < hc->n; ++a) {
-        for (int d = 1; d <= kMaskWindow && a + d < hc->n; ++d) {
-            int c = bond_class_tree(*hc, a, a + d);
-            if (c == 1) hc->ex_mask[a] |= (1ULL << d);
-            if (c == 2) hc->m14_mask[a] |= (1ULL << d);
-        }
-        for (int b = a + kMaskWindow + 1; b < hc->n && b <= a + kMaskWindow + 40; ++b) {
-            if (bond_class_tree(*hc, a, b) != 0) { *err = "internal: bonded pair outside the class window"; return KCM_E_INVAL; }
+        // depth 1..3 from a, never stepping back to the atom it came from (the graph is a tree)
+        int from[2][64];
+        nf[0] = 1;
+        frontier[0][0] = a;
+        from[0][0] = -1;
+        for (int depth = 1; depth <= 3; ++depth) {
+            const int cur = (depth - 1) & 1, nxt = depth & 1;
+            nf[nxt] = 0;
+            for (int k = 0; k < nf[cur]; ++k) {
+                const int x = frontier[cur][k], back = from[cur][k];
+                auto visit = [&](int y) {
+                    if (y == back || nf[nxt] >= 64) return;
+                    frontier[nxt][nf[nxt]] = y;
+                    from[nxt][nf[nxt]] = x;
+                    ++nf[nxt];
+                    if (y > a) {
+                        const int d = y - a;
+                        if (d > kMaskWindow) return;  // reported below
+                        if (depth <= 2) hc->ex_mask[a] |= (1ULL << d);
+                        else hc->m14_mask[a] |= (1ULL << d);
+                    }
+                };
+                if (hc->parent[x] >= 0) visit(hc->parent[x]);
+                for (int c = coff[x]; c < coff[x + 1]; ++c) visit(kids[c]);
+            }
+            for (int k = 0; k < nf[nxt]; ++k)
+                if (frontier[nxt][k] - a > kMaskWindow) {
+                    *err = "internal: bonded pair outside the class window";
+                    return KCM_E_INVAL;
+                }
         }
     }
     return KCM_OK;
