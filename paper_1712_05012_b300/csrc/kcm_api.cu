@@ -25,7 +25,9 @@ struct kcm_ctx {
     kcm::Status* st_host = nullptr;          // page-locked copy of the status record (read back by the calls)
     cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
     int sm_count = 148;
-    std::vector<void*> allocs;
+    std::vector<void*> allocs;       // every cudaMalloc of the handle (arena chunks included)
+    char* arena = nullptr;           // small arrays are carved from chunks of kArenaChunk bytes
+    size_t arena_left = 0;
     size_t bytes = 0;  // device memory held
     std::string err;
 };
@@ -47,9 +49,35 @@ int cuda_fail(kcm_ctx* h, cudaError_t e, const char* what) {
     return set_err(h, KCM_E_CUDA, msg);
 }
 
+// Device arrays of a handle: arrays up to kArenaMax bytes are carved (256-byte aligned) from shared
+// chunks, so a handle makes a few allocations instead of one per array (creation time matters to the
+// serving loop); larger arrays, and those that are freed and reallocated (own = true), get their own.
+constexpr size_t kArenaChunk = 8u << 20;
+constexpr size_t kArenaMax = 1u << 20;
+
 template <typename T>
-int dalloc(kcm_ctx* h, T** p, size_t count) {
+int dalloc(kcm_ctx* h, T** p, size_t count, bool own = false) {
     size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+    if (!own && bytes <= kArenaMax) {
+        const size_t need = (bytes + 255) & ~static_cast<size_t>(255);
+        if (need > h->arena_left) {
+            void* c = nullptr;
+            cudaError_t e = cudaMalloc(&c, kArenaChunk);
+            if (e != cudaSuccess) {
+                *p = nullptr;
+                cudaGetLastError();
+                return set_err(h, KCM_E_NOMEM, "device allocation of " + std::to_string(kArenaChunk) + " bytes failed");
+            }
+            h->allocs.push_back(c);
+            h->bytes += kArenaChunk;
+            h->arena = static_cast<char*>(c);
+            h->arena_left = kArenaChunk;
+        }
+        *p = reinterpret_cast<T*>(h->arena);
+        h->arena += need;
+        h->arena_left -= need;
+        return KCM_OK;
+    }
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -279,8 +307,8 @@ int set_cell_size(kcm_ctx* h, double cell_size) {
         d.cell_alloc = 0;
         const size_t nb = (static_cast<size_t>(tot) + kcm::kScanCells - 1) / kcm::kScanCells;
         int rc;
-        if ((rc = dalloc(h, &d.cell_count, static_cast<size_t>(tot))) || (rc = dalloc(h, &d.cell_start, static_cast<size_t>(tot) + 1)) ||
-            (rc = dalloc(h, &d.scan_part, nb)))
+        if ((rc = dalloc(h, &d.cell_count, static_cast<size_t>(tot), true)) ||
+            (rc = dalloc(h, &d.cell_start, static_cast<size_t>(tot) + 1, true)) || (rc = dalloc(h, &d.scan_part, nb, true)))
             return rc;
         cudaError_t e = cudaMemsetAsync(d.cell_count, 0, sizeof(int) * static_cast<size_t>(tot), h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "memset");
