@@ -914,27 +914,25 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
                     }
                     const int C = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(inb));
                     if (lane == 0) ncov += C >= 1;
-                    // step 2 against neighbour j displaced along s; hs is h_js
-                    auto covers_s = [&](int j, int s) -> bool {
+                    // step 2 against neighbour j displaced along each axis s: m_s = m + dr Q_s - (2 dr o_s +
+                    // dr^2) / (2 R_i), the test at rest with j moved by dr e_s (FP64 inside the guard band)
+                    auto covers3 = [&](int j, bool want, int delta) {
                         const float4 o = s_o[w][j];
-                        const float os = s == 0 ? o.x : (s == 1 ? o.y : o.z);
-                        const float Qs = s == 0 ? Qx : (s == 1 ? Qy : Qz);
-                        const float hs = o.w + (2.0f * drf * os + drf * drf) * inv2R;
-                        const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, fmaf(drf, Qs, -hs))));
-                        ++ntest;
-                        if (fabsf(m) > gd) return m >= 0.0f;
-                        return recheck(j, k, s);
+                        const float m = fmaf(Qz, o.z, fmaf(Qy, o.y, fmaf(Qx, o.x, -o.w)));
+#pragma unroll
+                        for (int s = 0; s < 3; ++s) {
+                            const float os = s == 0 ? o.x : (s == 1 ? o.y : o.z);
+                            const float Qs = s == 0 ? Qx : (s == 1 ? Qy : Qz);
+                            const float ms = fmaf(drf, Qs, m) - (2.0f * drf * os + drf * drf) * inv2R;
+                            ++ntest;
+                            const bool cov = fabsf(ms) > gd ? ms >= 0.0f : recheck(j, k, s);
+                            if (cov == want) atomicAdd(&s_cnt[w][3 * j + s], delta);
+                        }
                     };
                     if (C == 0) {  // exposed: every near neighbour may cover it once displaced
-                        for (unsigned b = nrb; b; b &= b - 1) {
-                            const int j = 32 * (__ffs(b) - 1) + lane;
-                            for (int s = 0; s < 3; ++s)
-                                if (covers_s(j, s)) atomicAdd(&s_cnt[w][3 * j + s], 1);
-                        }
+                        for (unsigned b = nrb; b; b &= b - 1) covers3(32 * (__ffs(b) - 1) + lane, true, 1);
                     } else if (C == 1 && (inb & nrb)) {  // critically overlapped by a near neighbour
-                        const int j = 32 * (__ffs(inb) - 1) + lane;
-                        for (int s = 0; s < 3; ++s)
-                            if (!covers_s(j, s)) atomicAdd(&s_cnt[w][3 * j + s], -1);
+                        covers3(32 * (__ffs(inb) - 1) + lane, false, -1);
                     }
                 }
                 __syncwarp();
