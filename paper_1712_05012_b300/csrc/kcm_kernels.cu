@@ -808,6 +808,14 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_long(const DevChain d)
 constexpr int kPtsPerLane = 8;                  // sample points each lane holds in registers
 constexpr int kBatch = 32 * kPtsPerLane;         // points per batch (256)
 
+static_assert(kSasaStage % 2 == 0, "an odd staged list has room for the pad entry of step 1");
+// max(a, b, c) in one instruction (the three-input form of max.f32, sm_100 and later); exact, like fmaxf
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 template <int W>
 __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
     __shared__ float4 s_o[W][kSasaStage];   // o_j, h_j
@@ -843,6 +851,8 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
             // band of m around 0 where a displacement by dr can change a point's state, widened to the
             // largest neighbour radius so that it is one number per atom
             const float band = (2.0f * drf * sqrtf(rmax2) + 3.0f * drf * drf) * inv2R + gd;
+            // an odd list is padded with a neighbour no point touches (m = -inf) for the paired step 1
+            if (lane == 0 && (cnt & 1)) s_o[w][cnt] = make_float4(0.0f, 0.0f, 0.0f, INFINITY);
             __syncwarp();
             int ncov = 0, nguard = 0;
             unsigned long long ntest = 0;
@@ -872,13 +882,14 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
                     mx[p] = -INFINITY;
                 }
                 // step 1: the largest m of each point over all neighbours
-#pragma unroll 4
-                for (int j = 0; j < cnt; ++j) {
-                    const float4 o = s_o[w][j];
+#pragma unroll 2
+                for (int j = 0; j < cnt; j += 2) {  // two neighbours per round, one max over both
+                    const float4 o = s_o[w][j], o2 = s_o[w][j + 1];
 #pragma unroll
                     for (int p = 0; p < kPtsPerLane; ++p) {
                         const float m = fmaf(qz[p], o.z, fmaf(qy[p], o.y, fmaf(qx[p], o.x, -o.w)));
-                        mx[p] = fmaxf(mx[p], m);
+                        const float m2 = fmaf(qz[p], o2.z, fmaf(qy[p], o2.y, fmaf(qx[p], o2.x, -o2.w)));
+                        mx[p] = fmax3f(mx[p], m, m2);
                     }
                 }
                 ntest += (unsigned long long)__popc(valid) * cnt;
