@@ -85,6 +85,27 @@ def test_fp64_parity_small(kcm, table, m, seed, kind):
     assert got["stats"]["pairs"] == ref["stats"]["pairs"]
 
 
+@pytest.mark.parametrize("m,seed,kind", [(1, 1, "uniform"), (2, 2, "uniform"), (3, 3, "compact"),
+                                         (40, 1235, "compact")])
+def test_mixed_solvation_small(kcm, table, m, seed, kind):
+    """Algorithm 1 in the mixed kernel on chains whose atoms have from one to a few dozen solvation
+    neighbours (odd and even list lengths; step 1 takes the neighbours two at a time): classifications,
+    exchange counts and forces equal the FP64 kernel's bit for bit, and the oracle's."""
+    seq, och, th = small_case(table, m, seed, kind)
+    pf = synth.RunParams(precision=synth.PRECISION_FP64)
+    ref = och.evaluate(pf, th)
+    mixed = gpu_eval(kcm, seq, table, synth.RunParams(precision=synth.PRECISION_MIXED), th)
+    fp64 = gpu_eval(kcm, seq, table, pf, th)
+    # the mixed lists also hold the pairs within the guard band of the range test (decided later)
+    assert mixed["stats"]["sasa_neighbors"] >= fp64["stats"]["sasa_neighbors"] > 0
+    assert np.array_equal(mixed["covered"], fp64["covered"])
+    assert np.array_equal(mixed["F_cav"], fp64["F_cav"])
+    g = och.gamma != 0
+    assert np.array_equal(mixed["covered"][g], ref["covered"][g])
+    if np.any(ref["F_cav"]):
+        assert rel_inf(mixed["F_cav"], ref["F_cav"]) < TOL_FP64
+
+
 @pytest.mark.parametrize("solvation", [0, 1])
 def test_mixed_parity_chain1000(kcm, table, solvation):
     """The 1,000-residue compact workload in the launch configuration the benchmark times."""
