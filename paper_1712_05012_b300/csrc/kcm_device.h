@@ -48,7 +48,6 @@ struct Status {
     int max_nbr;
     unsigned int ticket_w;  // last-block detection in the wrench / suffix-scan kernel
     unsigned int ticket_bin;  // last-block detection in the cell-count kernel
-    unsigned int ticket_fk;   // unused (kept so that the record keeps its layout)
     int nlong;                // atoms with more than kSasaStage solvation neighbours (long_atoms)
     int pad2;
 };

@@ -1259,7 +1259,6 @@ __global__ void k_reset_loop(const DevChain d, int full) {
         st->ticket = 0u;
         st->ticket_w = 0u;
         st->ticket_bin = 0u;
-        st->ticket_fk = 0u;
         st->last_max_dtheta = 0.0;
         if (full) {
             st->ticket_bbox = 0u;
