@@ -16,9 +16,10 @@ constexpr double kFxInv = 1.0 / 1099511627776.0;
 
 // Largest solvation neighbour list per atom; more raises KCM_E_OVERFLOW. At protein-like packing
 // (about 0.1 atoms per A^3 with hydrogens) the solvation range of an atom (Roff_i + Roff_j + dr, up to
-// ~6.8 A) holds about 130 atoms. Lists up to kSasaStage are staged in shared memory by Algorithm 1's
-// kernels; longer ones are read from global memory.
-constexpr int kMaxNbr = 256;
+// ~6.8 A) holds about 130 atoms; chains that the iteration packs more densely reach a little over 256
+// (one served job in several hundred after 200 iterations), hence half as much room again. Lists up to
+// kSasaStage are staged in shared memory by Algorithm 1's kernels; longer ones are read from global memory.
+constexpr int kMaxNbr = 384;
 constexpr int kSasaStage = 128;
 
 // Largest sample count per offset sphere.

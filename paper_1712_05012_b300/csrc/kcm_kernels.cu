@@ -1070,7 +1070,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed_long(const DevCh
                     nres += __popc(bm);
                 }
                 __syncwarp();
-                // re-scan, one point at a time; lane t takes neighbours t, t + 32, ... (at most 8)
+                // re-scan, one point at a time; lane t takes neighbours t, t + 32, ... (at most kMaxNbr / 32 = 12)
                 for (int e = 0; e < nres; ++e) {
                     const int k = kb + s_near[w][e];
                     const float4 qk = d.Q4[k];

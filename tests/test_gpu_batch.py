@@ -158,12 +158,13 @@ def test_batch512_mixed_vs_fp64_and_oracle(kcm, table):
 
 
 def test_batch_chain_fails_alone(kcm, table):
-    """A chain whose solvation lists overflow (probe radius 9 A: far more than 128 neighbours) stops
-    with KCM_E_OVERFLOW; a 3-residue chain in the same batch (fewer than 128 atoms, it cannot
-    overflow) takes all its iterations and ends where it ends alone."""
-    big = synth.sequence(30, 8)
+    """A chain whose solvation lists overflow (a compact ~1,000-atom chain with probe radius 9 A: far
+    more neighbours than the list holds) stops with KCM_E_OVERFLOW; a 3-residue chain in the same batch
+    (fewer atoms than the list holds, it cannot overflow) takes all its iterations and ends where it
+    ends alone."""
+    big = synth.sequence(97, 9)
     small = synth.sequence(3, 13)
-    th_big = synth.theta_from_codes(O.OracleChain(big, table, synth.GEOMETRY).grow_start(8))
+    th_big = synth.theta_from_codes(O.OracleChain(big, table, synth.GEOMETRY).grow_start(9))
     th_small = synth.theta_uniform(3, 13)
     p = synth.RunParams(precision=synth.PRECISION_FP64, r_probe=9.0)
     with kcm.Batch([big, small], table, p) as b:

@@ -208,8 +208,9 @@ def test_deterministic(kcm, table):
 
 
 def test_overflow_is_reported(kcm, table):
-    """A huge probe radius gives every atom far more solvation neighbours than the list holds."""
-    seq, och, th = small_case(table, 30, 8)
+    """A huge probe radius gives the atoms of a compact ~1,000-atom chain far more solvation neighbours
+    than the list holds."""
+    seq, och, th = small_case(table, 97, 9, "compact")
     p = synth.RunParams(r_probe=9.0)
     with kcm.Chain(seq, table, p) as ch:
         ch.set_theta(th)
