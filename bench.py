@@ -3,7 +3,7 @@
 
 Workload (default): the 1,000-residue synthetic chain (10,506 atoms) from its stored compact
 random-walk start, 10 A cutoff, N = 256 solvation samples, mixed precision (FP32 pair and
-solvation arithmetic, FP64 kinematics and torque scans). A step is one KCM iteration (forward
+solvation arithmetic; kinematics, wrenches and torque scans in double-float, ~48 significant bits). A step is one KCM iteration (forward
 kinematics, binning, pair forces, Algorithm 1, wrenches and torque suffix sums, energies, step),
 launched as a CUDA graph. Metric: atom-iterations per second, whole job (all ranks).
 
@@ -46,9 +46,11 @@ FP32_LANES_PER_SM = 128
 FLOPS_PER_SASA_TEST = 9  # w = v - o (3), |w|^2 (1 mul + 2 FMA = 5), compare with Roff^2 (1)
 FLOPS_PER_PAIR = 31      # per unordered pair within the cutoff (distance, 1/d^2, Coulomb, LJ, weights, accumulate)
 BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques_step": 60}  # algorithmic HBM bytes per atom
-# DRAM bytes (read + write) per launch of the stage's kernels on this workload, from one ncu capture
-# of the current kernels (profiles/k_sasa_mixed_chain1000.md); None where not captured
+# DRAM bytes (read + write) per launch of the stage's main kernel on the 1,000-residue workload, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it is built now; a stage
+# left out has no capture of its current kernel
 DRAM_BYTES_PER_LAUNCH = {"solvation": 6.84e6}
+MIXED_DTYPE = "f32 pair/solvation; double-float (~48-bit) kinematics, wrenches and torque scans"
 # launches of one mixed-precision iteration with solvation on: reset + kinematics 2 + binning 2 + pairs 1 +
 # solvation 2 (the main kernel and the long-list kernel beside it) + wrench-tile 1 + torque-step 1
 KERNELS_PER_ITERATION = 10
@@ -157,6 +159,11 @@ def whole_job_rate(ws: int, units_per_rank: int, steps: int, t_max: float) -> fl
     """Units processed by all ranks (every rank runs its own replica of the workload) per second of
     the slowest rank."""
     return ws * units_per_rank * steps / t_max
+
+
+def rel_err(got, ref):
+    """max |got - ref| / max |ref|"""
+    return float(np.max(np.abs(np.asarray(got) - np.asarray(ref))) / np.max(np.abs(ref)))
 
 
 def dist_env():
@@ -310,16 +317,22 @@ def stage_breakdown(c, prep, steps):
     return {k: v / steps for k, v in stg.items()}
 
 
-def stage_rooflines(ms_stage, stats, n, fp32_peak, peaks):
+def stage_rooflines(ms_stage, stats, n, fp32_peak, peaks, sasa_tests=None):
     """Achieved rate of every stage against its bound: the FP32 pipes for the pair terms and Algorithm 1's
-    tests (work counted at the last timed iteration), HBM for the rest (algorithmic bytes per atom)."""
+    tests, HBM for the rest (algorithmic bytes per atom). Algorithm 1's work is its overlap tests as the
+    algorithm performs them (step 1 stopping at the second overlap, step 2's re-tests), counted by the
+    oracle at the same conformation when `sasa_tests` is given; otherwise the kernel's own count (every
+    valid point against every neighbour, no early exit: an upper bound on the algorithm's tests)."""
     rooflines = {}
     for stage, ms in ms_stage.items():
         sec = ms / 1e3
         if stage == "solvation":
-            work = stats["sasa_tests"] * FLOPS_PER_SASA_TEST
+            tests = sasa_tests if sasa_tests is not None else stats["sasa_tests"]
+            work = tests * FLOPS_PER_SASA_TEST
             r = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"}
+                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 x max SM clock",
+                 "work_source": ("Algorithm 1 tests as performed (oracle count)" if sasa_tests is not None
+                                 else "kernel count (every valid point x every neighbour)")}
         elif stage == "pairs":
             work = stats["pairs"] * FLOPS_PER_PAIR
             r = {"bound": "alu", "achieved": work / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -365,10 +378,16 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             flush.add_(1)
 
-    # tile shapes (atoms per block of the pair and solvation kernels): the library's default, which its
-    # autotuner finds best or within noise on this workload (the batch and 8,000-residue legs run the
-    # tuner); left fixed here so that the profiled launches are the timed ones
-    tiles = {"used": list(ch.get_tiles()), "choices": list(kcm.TILE_CHOICES), "source": "default"}
+    # pair kernel (warp per atom or cell-pair tiles) and tile shapes from the library's autotuner, at the
+    # start conformation, before the warm-up
+    prepare(ch, lib_stream)
+    kind, kind_ms = ch.autotune_pair_kernel(reps=3)
+    tiles = {"used": list(ch.get_tiles()), "choices": list(kcm.TILE_CHOICES), "source": "autotuner",
+             "pair_kernel": ("cell_tiles" if kind == kcm.PAIR_CELL_TILES else "warp_per_atom"),
+             "pair_kernel_ms": {"warp_per_atom": float(kind_ms[0]), "cell_tiles": float(kind_ms[1])}}
+    # the torques at the start conformation, compared with the oracle's in the oracle leg
+    prepare(ch, lib_stream)
+    tau_start = ch.torques()
     clocks = Clocks(local)
     prep_main = lambda: prepare(ch, lib_stream)  # noqa: E731
     for _ in range(args.warmup):
@@ -387,18 +406,13 @@ def run_ours(args):
     t_sum = max_over_ranks(sum(totals) / 1e3, ws)
     value = whole_job_rate(ws, n, args.steps, t_sum)
 
-    # rooflines of every stage (work counted at the last timed iteration); the dominant one is the
-    # headline "roofline"
+    # roofline denominators (the rooflines themselves are formed after the oracle leg, which counts
+    # Algorithm 1's tests at the start conformation)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sm_max = (clk or {}).get("sm_max_mhz") or 2032.0
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6400.0}
-    rooflines = stage_rooflines(ms_stage, stats, n, fp32_peak, peaks)
-    dom = max(ms_stage, key=ms_stage.get)
-    roof = {k: v for k, v in rooflines[dom].items()}
-    roof["kernel"] = dom
-    roof["traffic"] = DRAM_BYTES_PER_LAUNCH.get(dom)
 
     # the same step with solvation off (the paper's vacuum runs), measured the same way
     vacuum_value = None
@@ -462,7 +476,11 @@ def run_ours(args):
 
                 prep8()
                 cell, cand_ms = c8.autotune_cell(candidates=(6.0, 7.0, 8.0, 9.0, 10.0, 12.0), reps=3)
-                tiles8, _ = c8.autotune_tiles(reps=3)
+                kind8, _ = c8.autotune_pair_kernel(reps=3)
+                tiles8 = c8.get_tiles()
+                if name == "mixed":
+                    prep8()
+                    tau8_start = c8.torques()
                 steps8 = args.chain8000_steps if name == "mixed" else max(2, args.chain8000_steps // 10)
                 for _ in range(3):
                     prep8()
@@ -472,7 +490,8 @@ def run_ours(args):
                 r = {"value": ws * c8.n * steps8 / (sum(tt) / 1e3), "ms_per_step": sum(tt) / steps8,
                      "steps": steps8, "cell_size": cell, "autotune_ms": dict(zip(("6", "7", "8", "9", "10", "12"),
                                                                              [float(x) for x in cand_ms])),
-                     "pairs": st8["pairs"], "sasa_tests": st8["sasa_tests"], "tiles": list(tiles8)}
+                     "pairs": st8["pairs"], "sasa_tests": st8["sasa_tests"], "tiles": list(tiles8),
+                     "pair_kernel": "cell_tiles" if kind8 == kcm.PAIR_CELL_TILES else "warp_per_atom"}
                 if name == "mixed":
                     stg8 = stage_breakdown(c8, prep8, steps8)
                     r["stage_ms"] = stg8
@@ -496,7 +515,8 @@ def run_ours(args):
                     flush.add_(1)
 
             prep_b()
-            btiles, btiles_ms = bb.autotune_tiles(reps=2)
+            bkind, bkind_ms = bb.autotune_pair_kernel(reps=2)
+            btiles = bb.get_tiles()
             for _ in range(3):
                 prep_b()
                 bb.step_timed()
@@ -510,8 +530,10 @@ def run_ours(args):
                      "ms_per_step": sum(tt) / args.batch_steps,
                      "stage_ms": stg,
                      "steps": args.batch_steps, "pairs": bst["pairs"], "sasa_tests": bst["sasa_tests"],
-                     "tiles": {"chosen": list(btiles), "order": "[persistent pair grid][pair warps][solvation warps]",
-                               "times_ms": btiles_ms.round(4).tolist()},
+                     "rooflines": stage_rooflines(stg, bst, bb.n, fp32_peak, peaks),
+                     "tiles": {"chosen": list(btiles), "order": "[pair warps or tile split][solvation warps][persistent pair grid]",
+                               "pair_kernel": "cell_tiles" if bkind == kcm.PAIR_CELL_TILES else "warp_per_atom",
+                               "pair_kernel_ms": {"warp_per_atom": float(bkind_ms[0]), "cell_tiles": float(bkind_ms[1])}},
                      "start": "every step from the stored compact starts (theta restored untimed)"}
 
     # serving: Poisson arrivals into the continuous-batching server, next to the same jobs one at a time
@@ -584,9 +606,35 @@ def run_ours(args):
                    "host wall clock. value_three_calls: kcm_set_theta, kcm_step, kcm_get_theta"}
     ch.close()
 
-    cpu = None
+    # the oracle leg (rank 0, one GPU, host cores): the CPU baseline, and one FP64 oracle evaluation at
+    # the start conformation of the timed workloads, for the torque error of the GPU path's result and
+    # Algorithm 1's test count
+    cpu, accuracy, sasa_oracle = None, None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu, _ = oracle_baseline(seq, theta, synth.RunParams(precision=synth.PRECISION_FP64))
+        cpu, och = oracle_baseline(seq, theta, synth.RunParams(precision=synth.PRECISION_FP64))
+        t0 = time.perf_counter()
+        ref = och.evaluate(synth.RunParams(precision=synth.PRECISION_FP64), theta)
+        accuracy = {"reference": "FP64 oracle at the start conformation (max-norm relative torque error)",
+                    "chain1000": {"torque_rel_err": rel_err(tau_start, ref["tau"]),
+                                  "oracle_s": time.perf_counter() - t0}}
+        sasa_oracle = ref["stats"]["sasa_tests1"] + ref["stats"]["sasa_tests2"]
+        if chain8000 is not None:
+            from oracle import oracle as O
+            t0 = time.perf_counter()
+            o8 = O.OracleChain(seq8, table, synth.GEOMETRY)
+            ref8 = o8.evaluate(synth.RunParams(precision=synth.PRECISION_FP64, cutoff=12.0), th8.cpu().numpy())
+            accuracy["chain8000"] = {"torque_rel_err": rel_err(tau8_start, ref8["tau"]),
+                                     "oracle_s": time.perf_counter() - t0}
+            chain8000["mixed"]["rooflines"] = stage_rooflines(
+                chain8000["mixed"]["stage_ms"], {"pairs": chain8000["mixed"]["pairs"]}, chain8000["atoms"],
+                fp32_peak, peaks, ref8["stats"]["sasa_tests1"] + ref8["stats"]["sasa_tests2"])
+
+    # rooflines of every stage; the dominant one is the headline "roofline"
+    rooflines = stage_rooflines(ms_stage, stats, n, fp32_peak, peaks, sasa_oracle)
+    dom = max(ms_stage, key=ms_stage.get)
+    roof = {k: v for k, v in rooflines[dom].items()}
+    roof["kernel"] = dom
+    roof["traffic"] = DRAM_BYTES_PER_LAUNCH.get(dom)
 
     if ws > 1:
         import torch.distributed as dist
@@ -595,7 +643,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32 pair/solvation, f64 kinematics/scans" if prec == synth.PRECISION_MIXED else "f64",
+                "dtype": MIXED_DTYPE if prec == synth.PRECISION_MIXED else "f64",
                 "data": "synthetic",
                 "config": {"workload": "chain1000_compact_cut10", "residues": 1000, "atoms": n, "cutoff": 10.0,
                            "n_sample": 256, "solvation": 1, "precision": args.precision,
@@ -607,7 +655,7 @@ def run_ours(args):
                 "fp64_value": fp64_value, "surrogate_value": surrogate_value, "side_joints_value": side_value,
                 "vacuum_value": vacuum_value, "tiles": tiles, "chain8000": chain8000, "batch": batch, "serving": serving,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION * args.steps,
+                "cpu_baseline": cpu, "accuracy": accuracy, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION * args.steps,
                 "clocks": clk, "stats": {k: stats[k] for k in ("pairs", "sasa_tests", "sasa_neighbors",
                                                                  "max_neighbors", "guard_rechecks", "cells")},
                 "cell_size": stats["cell_size"]}

@@ -384,13 +384,37 @@ int kcm_autotune_cell(kcm_handle h, const double* candidates, int32_t n_candidat
  * kcm_autotune_tiles evaluates the chain at the current theta and cell edge with every combination (a
  * warm-up, then `reps` evaluations timed with CUDA events on the handle's stream) and keeps the
  * fastest: times_ms[18] (may be NULL) indexed [persistent][pair shape][solvation shape], shapes in the
- * order 1, 2, 4; the choice in the three outputs (may be NULL). Synchronises. Errors: KCM_E_INVAL
- * (reps not in [1, 1000]), the errors of an evaluation (the previous shapes are then restored). */
+ * order 1, 2, 4; the choice in the three outputs (may be NULL). With the cell-pair tile kernel
+ * (KCM_PAIR_CELL_TILES, below) the pair shape is its split instead: the warps that share one window of
+ * 32 home slots and one stencil row (each taking every pair_warps-th staged group of 32 candidates);
+ * that kernel has no persistent grid, so the other grid's entries repeat the current one's times.
+ * Synchronises. Errors: KCM_E_INVAL (reps not in [1, 1000]), the errors of an evaluation (the previous
+ * shapes are then restored). */
 #define KCM_TILE_CHOICES 3
 int kcm_set_tiles(kcm_handle h, int32_t pair_warps, int32_t sasa_warps, int32_t pair_persistent);
 int kcm_get_tiles(kcm_handle h, int32_t* pair_warps, int32_t* sasa_warps, int32_t* pair_persistent);
 int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pair_warps, int32_t* sasa_warps,
                        int32_t* pair_persistent);
+
+/* Pair kernel of mixed precision (A3-A5: Coulomb and LJ forces, exclusions, solvation neighbour
+ * lists; eq. 02_2, 03_2, 03_8 / 03_9 and the grid of Sec. 3.2). KCM_PAIR_CELL_TILES (the mixed-mode
+ * default): a home cell's atoms against one row of its half stencil staged in shared memory, in-range
+ * pairs compacted and evaluated with every lane busy, per-tile fixed-point sums added to the global
+ * forces once per atom and tile. KCM_PAIR_WARP_PER_ATOM: one warp per home atom (the FP64 path's
+ * kernel; its mixed form takes the tile shapes above). Both give bitwise the same pair forces and
+ * solvation lists (up to the order of a list's entries, which no result depends on); energies agree to
+ * FP32 rounding. kcm_set_pair_kernel synchronises and drops the captured graphs; KCM_E_INVAL for
+ * another value, or for KCM_PAIR_CELL_TILES on an FP64 handle. kcm_get_pair_kernel reads it. */
+#define KCM_PAIR_WARP_PER_ATOM 0
+#define KCM_PAIR_CELL_TILES 1
+int kcm_set_pair_kernel(kcm_handle h, int32_t kind);
+int kcm_get_pair_kernel(kcm_handle h, int32_t* kind);
+/* Pair-kernel autotuner: runs kcm_autotune_tiles with each pair kernel (mixed precision; an FP64
+ * handle has only the warp-per-atom kernel) and keeps the kernel and tile shapes of the fastest
+ * evaluation. times_ms[2] (may be NULL): the best evaluation time of each kernel, indexed by
+ * KCM_PAIR_* (0 for a kernel not tried); *kind (may be NULL): the choice. Synchronises; errors as
+ * kcm_autotune_tiles (the previous kernel is then restored). */
+int kcm_autotune_pair_kernel(kcm_handle h, int32_t reps, double* times_ms, int32_t* kind);
 
 /* Stages of one iteration, in launch order, as timed by kcm_step_timed. */
 #define KCM_STAGE_KINEMATICS 0 /* transform scan and atom centres (eq. kin_04, r1, r2) */
@@ -432,8 +456,11 @@ void* kcm_stream(kcm_handle h);
  *
  * Scratch: a fixed array of about 2 MB that is part of the library image; every GPU that loads the
  * library holds it until the process exits, which is what limits L. The first call on a device,
- * with that device current, looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture. All calls on a device share the array and each call
+ * with that device current, looks up the array's device address (cudaGetSymbolAddress) and keeps it
+ * for the life of the process; make that first call before any stream capture. Do not call this
+ * entry point again on a device after cudaDeviceReset (or after its primary context was released
+ * and made again) in the same process: the library reloads with the new context and the kept address
+ * may no longer be the array's. All calls on a device share the array and each call
  * writes every scratch word it reads, so nothing carries over from an earlier call; calls that
  * overlap on the GPU (different streams, or different host threads) race on it. */
 #define KCM_NOALLOC_MAX_LINKS 32768

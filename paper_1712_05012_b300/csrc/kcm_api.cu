@@ -415,6 +415,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
     const kcm::HostChain& hc = h->hc;
     kcm::DevChain& d = h->d;
     d.prm = *prm;
+    d.pair_tile = prm->precision == KCM_MIXED ? KCM_PAIR_CELL_TILES : KCM_PAIR_WARP_PER_ATOM;
     d.m = hc.m; d.n = hc.n; d.l = hc.l; d.L = hc.L; d.N = prm->n_sample;
     d.ls = prm->side_joints ? hc.ls : 0;
     d.nmv = prm->side_joints ? static_cast<int>(hc.mv_atom.size()) : 0;
@@ -978,6 +979,26 @@ int kcm_get_tiles(kcm_handle h, int32_t* pair_warps, int32_t* sasa_warps, int32_
     return KCM_OK;
 }
 
+int kcm_set_pair_kernel(kcm_handle h, int32_t kind) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (kind != KCM_PAIR_WARP_PER_ATOM && kind != KCM_PAIR_CELL_TILES)
+        return set_err(h, KCM_E_INVAL, "pair kernel must be KCM_PAIR_WARP_PER_ATOM or KCM_PAIR_CELL_TILES");
+    if (kind == KCM_PAIR_CELL_TILES && h->d.prm.precision != KCM_MIXED)
+        return set_err(h, KCM_E_INVAL, "the cell-pair tile kernel is the mixed-precision pair kernel");
+    int rc = sync(h);  // no launch of the old kernel is pending when the graphs go
+    if (rc) return rc;
+    drop_graphs(h);
+    h->d.pair_tile = kind;
+    return KCM_OK;
+}
+
+int kcm_get_pair_kernel(kcm_handle h, int32_t* kind) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!kind) return set_err(h, KCM_E_INVAL, "kind is NULL");
+    *kind = h->d.pair_tile;
+    return KCM_OK;
+}
+
 int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pair_warps, int32_t* sasa_warps,
                        int32_t* pair_persistent) {
     if (check_handle(h)) return KCM_E_INVAL;
@@ -997,12 +1018,17 @@ int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pa
         *pw = kcm::kTileWarps[(i / nt) % nt];
         *sw = kcm::kTileWarps[i % nt];
     };
+    auto shape_pp = [&](int i) { return i / (nt * nt); };
     std::vector<double> t(ncomb, 0.0);
+    // the cell-pair tile kernel takes the pair shape as its split (warps per window and stencil row) and has
+    // no persistent grid: the combinations of the other grid take the time of the same shapes on this one
+    const bool pair_fixed = h->d.pair_tile && h->d.prm.precision == KCM_MIXED;
     int rc = KCM_OK;
     for (int i = 0; i < ncomb && rc == KCM_OK; ++i) {
         // one evaluation at the current theta (no step) per launch of a graph captured for this shape
         int pp, pw, sw;
         shape(i, &pp, &pw, &sw);
+        if (pair_fixed && pp != old_pp) continue;
         rc = kcm_set_tiles(h, pw, sw, pp);
         if (rc) break;
         cudaGraph_t g = nullptr;
@@ -1035,9 +1061,21 @@ int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pa
         kcm_set_tiles(h, old_p, old_s, old_pp);
         return rc;
     }
+    if (pair_fixed) {
+        for (int i = 0; i < ncomb; ++i) {
+            int pp, pw, sw;
+            shape(i, &pp, &pw, &sw);
+            if (pp == old_pp) continue;
+            for (int k = 0; k < ncomb; ++k) {
+                int pp2, pw2, sw2;
+                shape(k, &pp2, &pw2, &sw2);
+                if (pp2 == old_pp && pw2 == pw && sw2 == sw) t[i] = t[k];
+            }
+        }
+    }
     int best = 0;
     for (int i = 1; i < ncomb; ++i)
-        if (t[i] < t[best]) best = i;
+        if (t[i] < t[best] || (pair_fixed && t[i] == t[best] && shape_pp(i) == old_pp && shape_pp(best) != old_pp)) best = i;
     if (times_ms)
         for (int i = 0; i < ncomb; ++i) times_ms[i] = t[i];
     int pp, pw, sw;
@@ -1046,6 +1084,34 @@ int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pa
     if (sasa_warps) *sasa_warps = sw;
     if (pair_persistent) *pair_persistent = pp;
     return kcm_set_tiles(h, pw, sw, pp);
+}
+
+int kcm_autotune_pair_kernel(kcm_handle h, int32_t reps, double* times_ms, int32_t* kind) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (reps < 1 || reps > 1000) return set_err(h, KCM_E_INVAL, "reps must be in [1, 1000]");
+    const int old_kind = h->d.pair_tile;
+    const int nkind = h->d.prm.precision == KCM_MIXED ? 2 : 1;
+    double best_t[2] = {0.0, 0.0};
+    int32_t shapes[2][3] = {{1, 1, 0}, {1, 1, 0}};
+    for (int k = 0; k < nkind; ++k) {
+        // the warp-per-atom kernel first, then the cell-pair tile kernel, each with its best tile shapes
+        const int kk = nkind == 1 ? KCM_PAIR_WARP_PER_ATOM : k;
+        int rc = kcm_set_pair_kernel(h, kk);
+        double t[18];
+        if (rc == KCM_OK) rc = kcm_autotune_tiles(h, reps, t, &shapes[k][0], &shapes[k][1], &shapes[k][2]);
+        if (rc) {
+            kcm_set_pair_kernel(h, old_kind);
+            return rc;
+        }
+        best_t[k] = *std::min_element(t, t + 18);
+    }
+    const int win = nkind == 2 && best_t[1] < best_t[0] ? 1 : 0;
+    if (times_ms)
+        for (int k = 0; k < 2; ++k) times_ms[k] = k < nkind ? best_t[k] : 0.0;
+    if (kind) *kind = nkind == 1 ? KCM_PAIR_WARP_PER_ATOM : win;
+    int rc = kcm_set_pair_kernel(h, nkind == 1 ? KCM_PAIR_WARP_PER_ATOM : win);
+    if (rc) return rc;
+    return kcm_set_tiles(h, shapes[win][0], shapes[win][1], shapes[win][2]);
 }
 
 int kcm_get_stats(kcm_handle h, kcm_stats* out) {

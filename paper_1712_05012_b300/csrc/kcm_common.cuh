@@ -107,6 +107,56 @@ __device__ __forceinline__ void fx_add(float v, int& hi, int& lo) {
 // the whole term n 2^23 + f in units of 2^-23
 __device__ __forceinline__ long long fx_units(int n, int f) { return (long long)n * 8388608LL + f; }
 
+// Mixed-precision pair geometry with every FP32 rounding written out, so that each pair kernel that
+// evaluates a pair forms the same bits (a compiler left to itself may fuse these operations
+// differently in different kernels). Offsets are from the corners of the atoms' cells; the x shift
+// (cx_j - cx_i) s and the row shifts (dy s, dz s) are exact.
+// r_i - r_j = (o_i - o_j) - shift, component by component
+__device__ __forceinline__ float pair_delta_f32(float oi, float oj, float shift) {
+    return __fsub_rn(__fsub_rn(oi, oj), shift);
+}
+__device__ __forceinline__ float pair_d2_f32(float dx, float dy, float dz) {
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+// solvation neighbour range (A'_i, reading c11) with the FP32 cell-offset margin pad
+__device__ __forceinline__ bool solv_near_f32(float d2, float Roi, float Roj, float dr, float pad) {
+    const float lim = __fadd_rn(__fadd_rn(__fadd_rn(Roi, Roj), dr), pad);
+    return d2 <= __fmul_rn(lim, lim);
+}
+
+// Force coefficient c (F_i = c (r_i - r_j) = -F_j) and energies of one pair in FP32: Coulomb with
+// the dielectric 4d, E = K q_i q_j / (4 d^2) (eq. 02_2 with reading c2), and Lennard-Jones in the
+// AMBER form eps_ij [(D/d)^12 - 2 (D/d)^6], D = R_i + R_j, eps_ij = sqrt(eps_i) sqrt(eps_j) (eq. 03_2,
+// reading c5), each weighted by its 1-4 factor (eq. 03_8 / 03_9). Every product of the two atoms'
+// constants is formed symmetrically, so (i, j) and (j, i) give the same bits. A near-coincident pair
+// (d of a few thousandths of an A) would overflow the FP32 coefficient, or make it NaN from
+// inf - inf: it is held at kPairCoefMax, a huge finite repulsion.
+struct PairTermF {
+    float coef, e_el, e_vd;
+};
+__device__ __forceinline__ PairTermF pair_term_f32(float d2, float qi, float qj, float sei, float sej, float Ri,
+                                                   float Rj, float K, float we, float wv, bool inE, bool inV) {
+    const float inv2 = __frcp_rn(d2);
+    float cE = 0.0f, cV = 0.0f, eel = 0.0f, evd = 0.0f;
+    if (inE) {
+        const float qq = __fmul_rn(__fmul_rn(we, K), __fmul_rn(qi, qj));
+        cE = __fmul_rn(__fmul_rn(0.5f, qq), __fmul_rn(inv2, inv2));
+        eel = __fmul_rn(__fmul_rn(0.25f, qq), inv2);
+    }
+    if (inV) {
+        const float D = __fadd_rn(Ri, Rj);
+        const float x2 = __fmul_rn(__fmul_rn(D, D), inv2);
+        const float t6 = __fmul_rn(__fmul_rn(x2, x2), x2);
+        const float t12 = __fmul_rn(t6, t6);
+        const float eij = __fmul_rn(wv, __fmul_rn(sei, sej));
+        cV = __fmul_rn(__fmul_rn(__fmul_rn(12.0f, eij), __fsub_rn(t12, t6)), inv2);
+        evd = __fmul_rn(eij, __fsub_rn(t12, __fmul_rn(2.0f, t6)));
+    }
+    float coef = __fadd_rn(cE, cV);
+    if (!(coef <= kPairCoefMax)) coef = kPairCoefMax;
+    return PairTermF{coef, eel, evd};
+}
+
 // The FP64 overlap test of Algorithm 1: || (r_a + Roff_a q_k) - r_b - dr e_s ||^2 <= Roff_b^2,
 // written with explicit roundings so that the FP64 kernel and the FP32 guard-band recheck take
 // identical decisions.

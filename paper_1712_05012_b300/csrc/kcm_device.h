@@ -85,6 +85,8 @@ struct DevChain {
     int cell_cap = 0;     // cells of all chains' caps
     long long cell_alloc = 0;  // cells the cell arrays hold
     int pair_warps = 1, sasa_warps = 1;  // tile shapes: atoms per block of k_pair and of k_sasa_mixed / k_sasa_pw
+    int pair_tile = 0;         // mixed mode: the cell-pair tile kernel (k_pair_tile) instead of the warp-per-atom
+                               // kernel; its pair energies and counters go straight to the chain and status totals
     int pair_persistent = 0;   // the pair kernel on a persistent grid (one block per resident slot)
     int pair_grid_cap = 0;     // its block count then (SMs x resident blocks per SM); 0: one block per W atoms
     int scan_blocks = 0;
@@ -213,6 +215,8 @@ void launch_reset_loop(DevChain& d, cudaStream_t s);
 void launch_fk(DevChain& d, cudaStream_t s);
 void launch_binning(DevChain& d, cudaStream_t s);
 void launch_pairs(DevChain& d, cudaStream_t s);
+void launch_pairs_tile(DevChain& d, cudaStream_t s);  // kcm_pair_tile.cu
+int pair_tile_rows(int stencil);                      // warps per window of 32 slots of k_pair_tile
 int pair_resident_blocks(const DevChain& d);  // resident blocks per SM of the current pair kernel (-1: error)
 void launch_sasa(DevChain& d, cudaStream_t s);
 void launch_sasa_long(DevChain& d, cudaStream_t s);  // atoms with more than kSasaStage neighbours

@@ -423,8 +423,12 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
                     qj = q.x; sej = q.y; Rj = q.z; Roj = q.w;
                 }
                 if (solv) {  // solvation neighbour A'_i: d_ij <= Roff_i + Roff_j + dr
-                    R lim = Roi + Roj + dr + pad;
-                    isn = d2 <= lim * lim;
+                    if constexpr (MIXED) {
+                        isn = solv_near_f32(d2, Roi, Roj, dr, pad);
+                    } else {
+                        R lim = Roi + Roj + dr + pad;
+                        isn = d2 <= lim * lim;
+                    }
                 }
             }
             const unsigned bm = __ballot_sync(0xffffffffu, isn);
@@ -459,9 +463,12 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
                 if (inE || inV) {
                     // symmetric in (i, j): products of the two atoms' constants are formed first
                     const R we = is14 ? w14e : (R)1, wv = is14 ? w14v : (R)1;
-                    R inv2;
-                    if constexpr (MIXED) inv2 = __frcp_rn(d2); else inv2 = 1.0 / d2;
                     R coef = 0, e_el = 0, e_vd = 0;
+                    if constexpr (MIXED) {
+                        const PairTermF pt = pair_term_f32(d2, qi, qj, sei, sej, Ri, Rj, K, we, wv, inE, inV);
+                        coef = pt.coef; e_el = pt.e_el; e_vd = pt.e_vd;
+                    } else {
+                    const R inv2 = 1.0 / d2;
                     if (inE) {
                         const R qq = (we * K) * (qi * qj);
                         coef += (R)0.5 * qq * (inv2 * inv2);
@@ -477,14 +484,14 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
                         coef += (R)12 * eij * (t12 - t6) * inv2;
                         e_vd = eij * (t12 - (R)2 * t6);
                     }
-                    // mixed: a near-coincident pair (d of a few thousandths of an A) overflows the FP32
-                    // term, or makes it NaN from inf - inf; it is held at a large finite repulsion, so the
-                    // torques stay finite and the clamped step goes ahead as on the FP64 path
-                    if constexpr (MIXED) { if (!(coef <= kPairCoefMax)) coef = kPairCoefMax; }
+                    }
+                    // mixed: a near-coincident pair (d of a few thousandths of an A) would overflow the FP32
+                    // term; pair_term_f32 holds it at a large finite repulsion, so the torques stay finite
+                    // and the clamped step goes ahead as on the FP64 path
                     const bool count_e = HALF || a < b;  // each unordered pair's energy once
                     if (count_e && (we != (R)0 || wv != (R)0)) ++npairs;
                     if constexpr (MIXED) {
-                        const float fx1 = coef * ddx, fy1 = coef * ddy, fz1 = coef * ddz;
+                        const float fx1 = __fmul_rn(coef, ddx), fy1 = __fmul_rn(coef, ddy), fz1 = __fmul_rn(coef, ddz);
                         unsigned long long* Fj = reinterpret_cast<unsigned long long*>(&d.Fpx[3 * b]);
                         if (fabsf(fx1) < kPairFxMax && fabsf(fy1) < kPairFxMax && fabsf(fz1) < kPairFxMax) {
                             int n0, f0, n1, f1, n2, f2;
@@ -518,11 +525,11 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
                         const int slot = base_slot + __popc(bm & lt);
                         if (slot < kMaxNbr) {  // j in i's list: r_j - r_i, Roff_j^2
                             d.nbr[(size_t)a * kMaxNbr + slot] = b;
-                            d.nbr_off[(size_t)a * kMaxNbr + slot] = make_float4(-(float)ddx, -(float)ddy, -(float)ddz, (float)(Roj * Roj));
+                            d.nbr_off[(size_t)a * kMaxNbr + slot] = make_float4(-(float)ddx, -(float)ddy, -(float)ddz, __fmul_rn((float)Roj, (float)Roj));
                         }
                         if (rslot < kMaxNbr) {  // i in j's list: r_i - r_j, Roff_i^2
                             d.nbr[(size_t)b * kMaxNbr + rslot] = a;
-                            d.nbr_off[(size_t)b * kMaxNbr + rslot] = make_float4((float)ddx, (float)ddy, (float)ddz, (float)(Roi * Roi));
+                            d.nbr_off[(size_t)b * kMaxNbr + rslot] = make_float4((float)ddx, (float)ddy, (float)ddz, __fmul_rn((float)Roi, (float)Roi));
                         }
                         ovf |= slot >= kMaxNbr || rslot >= kMaxNbr;
                         // an atom whose list passes kSasaStage entries goes to the long-list kernels
@@ -565,13 +572,15 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
                         const float4 p = d.spos32[ts];
                         const float2 sh = s_sh[w][t];
                         // r_i - r_j = (o_i - o_j) - (c_j - c_i) s; (cx_j - cx_i) s is exact
-                        ddx = (px - p.x) - (p.w - fcx) * sf; ddy = (py - p.y) - sh.x; ddz = (pz - p.z) - sh.y;
+                        ddx = pair_delta_f32(px, p.x, __fmul_rn(__fsub_rn(p.w, fcx), sf));
+                        ddy = pair_delta_f32(py, p.y, sh.x);
+                        ddz = pair_delta_f32(pz, p.z, sh.y);
                     } else {
                         dbl4 p = d.spos64[ts];
                         ddx = __dsub_rn(px, p.x); ddy = __dsub_rn(py, p.y); ddz = __dsub_rn(pz, p.z);
                     }
                     R d2;
-                    if constexpr (MIXED) d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    if constexpr (MIXED) d2 = pair_d2_f32(ddx, ddy, ddz);
                     else d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
                     inr = d2 <= rall2;
                     v.x = ddx; v.y = ddy; v.z = ddz; v.w = d2;
@@ -1343,8 +1352,13 @@ int pair_resident_blocks(const DevChain& d) {
     }
 }
 
-// the pair kernel with pair_warps home atoms per block (a tile shape of kTileWarps)
+// the pair kernel: in mixed mode the cell-pair tile kernel when chosen, else the warp-per-atom kernel
+// with pair_warps home atoms per block (a tile shape of kTileWarps)
 void launch_pairs(DevChain& d, cudaStream_t s) {
+    if (d.pair_tile && d.prm.precision == KCM_MIXED) {
+        launch_pairs_tile(d, s);
+        return;
+    }
     switch (d.pair_warps) {
         case 1: launch_pairs_w<1>(d, s); break;
         case 2: launch_pairs_w<2>(d, s); break;

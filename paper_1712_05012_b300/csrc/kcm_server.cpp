@@ -209,7 +209,7 @@ int admit(kcm_server* s) {
         cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         destroy_batch(s, b.get());
-        for (Job* j : take) s->pending.push_front(j);
+        s->pending.insert(s->pending.begin(), take.begin(), take.end());  // back in arrival order
         return KCM_E_CUDA;
     }
     int rc = kcm_create_batch(tops.data(), static_cast<int32_t>(tops.size()), &s->prm, b->stream, &b->h);

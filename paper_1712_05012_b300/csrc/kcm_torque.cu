@@ -163,18 +163,20 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
             }
         }
         cc = ca;
-        if constexpr (DF) {
-            const float2 ep = reinterpret_cast<const float2*>(d.epair)[a];
-            Ef[0] += ep.x;
-            Ef[1] += ep.y;
-        } else {
-            const double2 ep = reinterpret_cast<const double2*>(d.epair)[a];
-            E[0] += ep.x;
-            E[1] += ep.y;
+        if (!d.pair_tile) {  // the cell-pair tile kernel adds its energies and counters to the totals itself
+            if constexpr (DF) {
+                const float2 ep = reinterpret_cast<const float2*>(d.epair)[a];
+                Ef[0] += ep.x;
+                Ef[1] += ep.y;
+            } else {
+                const double2 ep = reinterpret_cast<const double2*>(d.epair)[a];
+                E[0] += ep.x;
+                E[1] += ep.y;
+            }
+            const int2 ps = d.pstat[a];
+            cnt[0] += ps.x;
+            cnt[1] += ps.y;
         }
-        const int2 ps = d.pstat[a];
-        cnt[0] += ps.x;
-        cnt[1] += ps.y;
         if (d.prm.solvation) {
             const int2 ss = d.sstat[a];
             const int nl = d.nbr_cnt[a];

@@ -78,7 +78,9 @@ EXPORTS = [
     "kcm_set_fixed_joints", "kcm_nside_joints", "kcm_set_side_theta", "kcm_get_side_theta", "kcm_side_torques",
     "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev", "kcm_step_host",
     "kcm_set_tiles", "kcm_get_tiles", "kcm_autotune_tiles", "kcm_server_set_admission",
+    "kcm_set_pair_kernel", "kcm_get_pair_kernel", "kcm_autotune_pair_kernel",
 ]
+PAIR_WARP_PER_ATOM, PAIR_CELL_TILES = 0, 1
 TILE_CHOICES = (1, 2, 4)
 AUTOTUNE_MAX = 64
 # candidate cell edges of the autotuner (A): 0 is the smallest 27-cell edge; edges below the largest
@@ -128,6 +130,9 @@ def load():
             "kcm_set_tiles": (C.c_int, [h, C.c_int32, C.c_int32, C.c_int32]),
             "kcm_get_tiles": (C.c_int, [h, _ip, _ip, _ip]),
             "kcm_autotune_tiles": (C.c_int, [h, C.c_int32, _dp, _ip, _ip, _ip]),
+            "kcm_set_pair_kernel": (C.c_int, [h, C.c_int32]),
+            "kcm_get_pair_kernel": (C.c_int, [h, _ip]),
+            "kcm_autotune_pair_kernel": (C.c_int, [h, C.c_int32, _dp, _ip]),
             "kcm_set_fixed_joints": (C.c_int, [h, C.c_void_p, C.c_int64]),
             "kcm_nside_joints": (C.c_int64, [h]),
             "kcm_set_side_theta": (C.c_int, [h, _dp, C.c_int64]),
@@ -443,6 +448,23 @@ class Chain:
         """Atoms per thread block of the pair kernel and of the solvation kernel (1, 2 or 4), and whether
         the pair kernel runs on a persistent grid."""
         _check(load().kcm_set_tiles(self._h, int(pair_warps), int(sasa_warps), int(pair_persistent)), self._h)
+
+    def set_pair_kernel(self, kind: int):
+        """PAIR_CELL_TILES (mixed-mode default) or PAIR_WARP_PER_ATOM."""
+        _check(load().kcm_set_pair_kernel(self._h, int(kind)), self._h)
+
+    def autotune_pair_kernel(self, reps: int = 3):
+        """Both pair kernels (mixed precision), each with its best tile shapes; keeps the fastest:
+        (kind, times_ms[2] indexed by kind)."""
+        t = np.zeros(2)
+        k = np.zeros(1, dtype=np.int32)
+        _check(load().kcm_autotune_pair_kernel(self._h, int(reps), _dptr(t), _iptr(k)), self._h)
+        return int(k[0]), t
+
+    def get_pair_kernel(self) -> int:
+        p = np.zeros(1, dtype=np.int32)
+        _check(load().kcm_get_pair_kernel(self._h, _iptr(p)), self._h)
+        return int(p[0])
 
     def get_tiles(self):
         """(pair_warps, sasa_warps, pair_persistent)."""

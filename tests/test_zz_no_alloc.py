@@ -14,13 +14,15 @@ pytestmark = pytest.mark.gpu
 TOL_FP64 = 1e-10  # the FP64 torque bar of the parity tests
 
 
-def case(kcm, table, m, seed):
+def case(kcm, table, m, seed, solvation=1):
     """Positions, forces and torques of one chain from the regular entry points, plus the inputs
-    the no-allocation call needs (link ranges, current joint axes and axis points)."""
+    the no-allocation call needs (link ranges, current joint axes and axis points), at a compact
+    start. (An extended start of 16,000 residues puts atoms 57,000 A from the origin, and the two
+    entry points' different summation orders then differ by 2e-10 of the largest torque.)"""
     seq = synth.sequence(m, seed)
-    och = O.OracleChain(seq, table, synth.GEOMETRY)
-    theta = synth.theta_from_codes(och.grow_start(seed))
-    with kcm.Chain(seq, table, synth.RunParams(precision=synth.PRECISION_FP64)) as ch:
+    theta = synth.theta_from_codes(O.OracleChain(seq, table, synth.GEOMETRY).grow_start(seed))
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=solvation)
+    with kcm.Chain(seq, table, p) as ch:
         ch.set_theta(theta)
         xyz = ch.positions()
         F = ch.forces()
@@ -59,6 +61,27 @@ def test_two_calls_in_a_row_match_kcm_torques(table):
     tb = run_noalloc(kcm, b)
     assert rel_inf(ta, a["tau"]) < TOL_FP64
     assert rel_inf(tb, b["tau"]) < TOL_FP64
+
+
+def test_largest_and_chunked_sizes(table):
+    """The sizes that stress the fixed array: L = KCM_NOALLOC_MAX_LINKS exactly (16,383 residues and one
+    empty link: the chunk sums fill their part of the array to the last word, and each scan thread takes
+    64 chunks),
+    then L = 601, where scan threads take more than one chunk, reusing what the larger call left."""
+    from paper_1712_05012_b300 import kcm
+    big = case(kcm, table, (kcm.NOALLOC_MAX_LINKS - 1) // 2, 33, solvation=0)
+    # a chain has L = 2m + 1 links (odd): one more link without atoms reaches the limit exactly; its
+    # joint moves nothing, so its torque is 0 and every other joint's is unchanged
+    assert big["L"] == kcm.NOALLOC_MAX_LINKS - 1
+    big["L"] += 1
+    big["link_start"] = np.append(big["link_start"], big["link_start"][-1]).astype(np.int32)
+    big["axis"] = np.vstack([big["axis"], [0.0, 0.0, 1.0]])
+    big["point"] = np.vstack([big["point"], [1.0, 2.0, 3.0]])
+    big["tau"] = np.append(big["tau"], 0.0)
+    mid = case(kcm, table, 300, 34)
+    assert mid["L"] == 601
+    assert rel_inf(run_noalloc(kcm, big), big["tau"]) < TOL_FP64
+    assert rel_inf(run_noalloc(kcm, mid), mid["tau"]) < TOL_FP64
 
 
 def test_size_limit_is_refused(table):
