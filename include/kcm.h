@@ -45,6 +45,7 @@ extern "C" {
 #define KCM_E_NONFINITE (-5) /* a torque came out NaN or infinite */
 #define KCM_E_OVERFLOW (-6)  /* an atom had more solvation neighbours than the list holds */
 #define KCM_E_NODEVICE (-8)  /* no CUDA device, or the device is not sm_103 */
+#define KCM_E_CANCELLED (-9) /* a served job was cancelled (kcm_server_cancel) */
 
 /* precision of the pair and solvation arithmetic; kinematics and torque scans are FP64 always */
 #define KCM_FP64 0
@@ -214,12 +215,15 @@ int64_t kcm_device_bytes(kcm_handle h);
 /* ---------------------------------------------------------------- serving loop
  * A request loop for folding jobs (no counterpart in the paper, which folds one chain at a time):
  * jobs of any chain length are submitted at any time, admitted as device memory frees up under a
- * budget, stepped with all other admitted jobs on the device (continuous batching: every admission
- * wave is a batch on a stream of its own; batches advance in chunks of iterations launched without
- * waiting), and retired when they converge (max |dtheta| < conv_tol) or reach their iteration cap.
- * Coordinates, cell lists and theta stay on the device from admission to retirement. Single-threaded:
- * one thread calls the kcm_server_* functions of a server. Times are seconds since creation (host
- * clock). */
+ * budget, stepped with all other admitted jobs on the device (continuous batching: a batch on a stream
+ * of its own advances in chunks of iterations launched without waiting), and retired when they
+ * converge (max |dtheta| < conv_tol) or reach their iteration cap. Free slots are refilled by
+ * compaction: the next batch takes the waiting jobs together with the running jobs of the batch with
+ * the most retired slots, which move over with the angles they reached at its next chunk boundary;
+ * the old batch is then freed, so the memory of retired jobs returns to the budget. New batches are
+ * made on worker threads (up to four admission waves and one compaction at a time) while ticks go on. Coordinates, cell lists and theta stay
+ * on the device from admission to retirement (a move copies theta once). Single-threaded: one thread
+ * calls the kcm_server_* functions of a server. Times are seconds since creation (host clock). */
 typedef struct kcm_server kcm_server;
 
 #define KCM_JOB_WAITING 0
@@ -238,7 +242,7 @@ typedef struct {
 
 /* params: as kcm_create (all jobs of a server share them); hbm_budget_bytes: device memory the
  * server's batches may hold together (a job that cannot fit even alone ends with KCM_E_NOMEM);
- * max_chains_per_batch: largest admission wave; chunk_iters: iterations a batch takes between two
+ * max_chains_per_batch: most chains a batch holds; chunk_iters: iterations a batch takes between two
  * looks at its chains. Errors: KCM_E_INVAL, KCM_E_NOMEM. */
 int kcm_server_create(const kcm_params* params, int64_t hbm_budget_bytes, int32_t max_chains_per_batch,
                       int32_t chunk_iters, kcm_server** out);
@@ -263,11 +267,19 @@ int kcm_server_tick(kcm_server* s, int32_t* n_waiting, int32_t* n_running);
  * max_wait_s negative or not finite). */
 int kcm_server_set_admission(kcm_server* s, int32_t min_jobs, double max_wait_s);
 
-/* Ids of jobs retired since the last poll (at most `capacity`; *n of them written to ids). */
+/* Ids of jobs retired since the last poll (at most `capacity`; *n of them written to ids). The
+ * server keeps the records of the last 65,536 polled jobs; older ones are dropped. */
 int kcm_server_poll(kcm_server* s, int64_t* ids, int32_t capacity, int32_t* n);
 
-/* State of a job and, once it is done, its final theta (theta may be NULL; l = 2 n_res). */
+/* State of a job and, once it is done, its final theta (theta may be NULL; l = 2 n_res). Errors:
+ * KCM_E_INVAL (unknown id, a record already dropped, l mismatch). */
 int kcm_server_job(kcm_server* s, int64_t job_id, kcm_job_info* info, double* theta, int64_t l);
+
+/* Cancel a job: a waiting job retires at once; a job that has a slot takes no step after the chunk
+ * that is running and retires at the end of it, with the angles it reached. Either way it ends with
+ * error KCM_E_CANCELLED (a job that converges or reaches its cap in that chunk ends as it would have).
+ * The other jobs are not affected. Errors: KCM_E_INVAL (unknown id, or the job has finished). */
+int kcm_server_cancel(kcm_server* s, int64_t job_id);
 
 /* Device memory held by the server's batches, in bytes (-1 for NULL). */
 int64_t kcm_server_device_bytes(kcm_server* s);

@@ -6,11 +6,13 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "kcm_device.h"
+#include "nvtx3/nvToolsExt.h"
 
 struct kcm_ctx {
     kcm::DevChain d;
@@ -25,7 +27,7 @@ struct kcm_ctx {
     kcm::Status* st_host = nullptr;          // page-locked copy of the status record (read back by the calls)
     cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
     int sm_count = 148;
-    std::vector<void*> allocs;       // every cudaMalloc of the handle (arena chunks included)
+    std::vector<void*> allocs;       // every allocation of the handle from the pool (arena chunks included)
     char* arena = nullptr;           // small arrays are carved from chunks of kArenaChunk bytes
     size_t arena_left = 0;
     size_t bytes = 0;  // device memory held
@@ -49,6 +51,76 @@ int cuda_fail(kcm_ctx* h, cudaError_t e, const char* what) {
     return set_err(h, KCM_E_CUDA, msg);
 }
 
+// Device memory of the handles comes from one stream-ordered memory pool per device that the library
+// owns (cudaMallocFromPoolAsync and cudaFreeAsync on the handle's stream). Freed blocks stay in the pool
+// for the next handle, so making and freeing a handle never calls cudaMalloc or cudaFree, which wait for
+// or serialise with the work of every other stream on the device (the serving loop makes and frees
+// batches while others run). The pool lives until the process exits.
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kPoolDevices] = {};
+
+cudaError_t device_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;  // keep freed memory in the pool
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+cudaError_t pool_alloc(kcm_ctx* h, void** p, size_t bytes) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, h->stream);
+    return e;
+}
+
+// Page-locked status records (one per handle), carved from chunks that live until the process exits: a
+// cudaMallocHost / cudaFreeHost per handle would synchronise the device.
+std::mutex g_pin_mu;
+std::vector<kcm::Status*> g_pin_free;
+
+kcm::Status* pinned_status() {
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    if (g_pin_free.empty()) {
+        constexpr int kPerChunk = 64;
+        void* c = nullptr;
+        if (cudaMallocHost(&c, kPerChunk * sizeof(kcm::Status)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = kPerChunk - 1; i >= 0; --i) g_pin_free.push_back(static_cast<kcm::Status*>(c) + i);
+    }
+    kcm::Status* r = g_pin_free.back();
+    g_pin_free.pop_back();
+    return r;
+}
+
+void release_status(kcm::Status* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
 // Device arrays of a handle: arrays up to kArenaMax bytes are carved (256-byte aligned) from shared
 // chunks, so a handle makes a few allocations instead of one per array (creation time matters to the
 // serving loop); larger arrays, and those that are freed and reallocated (own = true), get their own.
@@ -62,7 +134,7 @@ int dalloc(kcm_ctx* h, T** p, size_t count, bool own = false) {
         const size_t need = (bytes + 255) & ~static_cast<size_t>(255);
         if (need > h->arena_left) {
             void* c = nullptr;
-            cudaError_t e = cudaMalloc(&c, kArenaChunk);
+            cudaError_t e = pool_alloc(h, &c, kArenaChunk);
             if (e != cudaSuccess) {
                 *p = nullptr;
                 cudaGetLastError();
@@ -78,7 +150,9 @@ int dalloc(kcm_ctx* h, T** p, size_t count, bool own = false) {
         h->arena_left -= need;
         return KCM_OK;
     }
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    void* q = nullptr;
+    cudaError_t e = pool_alloc(h, &q, bytes);
+    *p = static_cast<T*>(q);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
@@ -118,21 +192,35 @@ void enqueue_sasa(kcm_ctx* h, cudaStream_t s) {
     }
 }
 
-void enqueue_evaluation(kcm_ctx* h) {
-    kcm::launch_fk(h->d, h->stream);
-    kcm::launch_binning(h->d, h->stream);
-    kcm::launch_pairs(h->d, h->stream);
-    enqueue_sasa(h, h->stream);
-    kcm::launch_torques(h->d, h->stream);
+// An NVTX range around the host-side enqueue of one stage (named by the KCM_STAGE_* order), so that a
+// profiler's timeline groups each stage's kernels, in the captured graphs too (their nodes are made
+// inside the ranges). Without a profiler attached the calls return at once.
+struct StageRange {
+    explicit StageRange(int stage) {
+        static const char* kNames[KCM_NUM_STAGES] = {"kcm:kinematics", "kcm:binning", "kcm:pairs", "kcm:solvation",
+                                                     "kcm:torques_step"};
+        nvtxRangePushA(kNames[stage]);
+    }
+    ~StageRange() { nvtxRangePop(); }
+    StageRange(const StageRange&) = delete;
+    StageRange& operator=(const StageRange&) = delete;
+};
+
+void enqueue_stages(kcm_ctx* h, bool step) {
+    { StageRange r(KCM_STAGE_KINEMATICS); kcm::launch_fk(h->d, h->stream); }
+    { StageRange r(KCM_STAGE_BINNING); kcm::launch_binning(h->d, h->stream); }
+    { StageRange r(KCM_STAGE_PAIRS); kcm::launch_pairs(h->d, h->stream); }
+    { StageRange r(KCM_STAGE_SOLVATION); enqueue_sasa(h, h->stream); }
+    {
+        StageRange r(KCM_STAGE_TORQUES);
+        if (step) kcm::launch_torques_step(h->d, h->stream);
+        else kcm::launch_torques(h->d, h->stream);
+    }
 }
 
-void enqueue_iteration(kcm_ctx* h) {
-    kcm::launch_fk(h->d, h->stream);
-    kcm::launch_binning(h->d, h->stream);
-    kcm::launch_pairs(h->d, h->stream);
-    enqueue_sasa(h, h->stream);
-    kcm::launch_torques_step(h->d, h->stream);
-}
+void enqueue_evaluation(kcm_ctx* h) { enqueue_stages(h, false); }
+
+void enqueue_iteration(kcm_ctx* h) { enqueue_stages(h, true); }
 
 int read_status(kcm_ctx* h, kcm::Status* st) {
     kcm::Status* dst = h->st_host ? h->st_host : st;  // page-locked: an asynchronous copy, one wait
@@ -210,15 +298,15 @@ int build_timed_graph(kcm_ctx* h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
     cudaStream_t s = h->stream;
     cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
-    kcm::launch_fk(h->d, s);
+    { StageRange r(KCM_STAGE_KINEMATICS); kcm::launch_fk(h->d, s); }
     cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
-    kcm::launch_binning(h->d, s);
+    { StageRange r(KCM_STAGE_BINNING); kcm::launch_binning(h->d, s); }
     cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
-    kcm::launch_pairs(h->d, s);
+    { StageRange r(KCM_STAGE_PAIRS); kcm::launch_pairs(h->d, s); }
     cudaEventRecordWithFlags(h->ev[4], s, cudaEventRecordExternal);
-    enqueue_sasa(h, s);
+    { StageRange r(KCM_STAGE_SOLVATION); enqueue_sasa(h, s); }
     cudaEventRecordWithFlags(h->ev[5], s, cudaEventRecordExternal);
-    kcm::launch_torques_step(h->d, s);
+    { StageRange r(KCM_STAGE_TORQUES); kcm::launch_torques_step(h->d, s); }
     cudaEventRecordWithFlags(h->ev[6], s, cudaEventRecordExternal);
     e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
@@ -248,7 +336,7 @@ std::vector<double> pack_df(const std::vector<double>& v) {
 
 void dfree(kcm_ctx* h, void* p, size_t bytes) {
     if (!p) return;
-    cudaFree(p);
+    cudaFreeAsync(p, h->stream);  // back to the pool after the stream's earlier work
     h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
     h->bytes -= bytes;
 }
@@ -402,10 +490,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         h->own_stream = true;
     }
 
-    if (cudaMallocHost(reinterpret_cast<void**>(&h->st_host), sizeof(kcm::Status)) != cudaSuccess) {
-        cudaGetLastError();
-        h->st_host = nullptr;  // status reads then go through pageable memory
-    }
+    h->st_host = pinned_status();  // NULL: status reads then go through pageable memory
     if (prm->solvation == 1) {  // the long solvation lists run beside the main solvation kernel
         e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
@@ -460,7 +545,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.ucurdf, 3 * l)) || (rc = dalloc(h, &d.pcurdf, 3 * l)) || (rc = dalloc(h, &d.G0f, nn)) ||
         (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||
         (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.rank, nn)) ||
-        (rc = dalloc(h, &d.sorted, nn)) || (rc = dalloc(h, &d.slot_cell, nn)) || (rc = dalloc(h, &d.smask, nn)) || (rc = dalloc(h, &d.spos64, nn)) ||
+        (rc = dalloc(h, &d.sorted, nn)) || (rc = dalloc(h, &d.sorted_tmp, nn)) || (rc = dalloc(h, &d.slot_cell, nn)) || (rc = dalloc(h, &d.smask, nn)) || (rc = dalloc(h, &d.spos64, nn)) ||
         (rc = dalloc(h, &d.spos32, nn)) || (rc = dalloc(h, &d.sprm32, nn)) || (rc = dalloc(h, &d.sprm64, nn)) ||
         (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fpx, 3 * nn)) || (rc = dalloc(h, &d.Fov, 3 * nn)) ||
         (rc = dalloc(h, &d.gflag, nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||
@@ -712,12 +797,12 @@ void kcm_destroy(kcm_handle h) {
     drop_graphs(h);
     for (cudaEvent_t ev : h->ev)
         if (ev) cudaEventDestroy(ev);
-    for (void* p : h->allocs) cudaFree(p);
+    for (void* p : h->allocs) cudaFreeAsync(p, h->stream);  // back to the pool; the stream has no work left
     if (h->side) cudaStreamDestroy(h->side);
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
-    if (h->st_host) cudaFreeHost(h->st_host);
+    release_status(h->st_host);
     cudaGetLastError();
     delete h;
 }
@@ -1213,6 +1298,7 @@ const char* kcm_strerror(int code) {
         case KCM_E_NONFINITE: return "non-finite torque";
         case KCM_E_OVERFLOW: return "solvation neighbour list overflow";
         case KCM_E_NODEVICE: return "no sm_103 CUDA device";
+        case KCM_E_CANCELLED: return "cancelled";
         default: return "unknown status";
     }
 }

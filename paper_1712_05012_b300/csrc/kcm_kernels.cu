@@ -207,20 +207,28 @@ __global__ void k_scan_cells(const DevChain d) {
 }
 
 // sorted slot = start of the cell + rank; sorted copies: FP64 centres, or FP32 offsets from the
-// cell corner (|offset| <= s plus the assignment margin, rounding below s 2^-24)
+// cell corner (|offset| <= s plus the assignment margin, rounding below s 2^-24). The ranks come from
+// atomics, so the order within a cell depends on timing: mixed mode sums its pair terms in exact fixed
+// point and does not depend on it; FP64 mode only records the slot here and k_bin_stable puts each
+// cell's atoms in atom order, so that its floating-point sums, and with them the torques, are the same
+// from run to run.
 template <bool MIXED>
 __global__ void k_bin_place(const DevChain d) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= d.n || d.status->done) return;
-    const GridInfo g = d.grid[atom_chain(d, a)];
     int key = d.key[a];
     int sl = d.cell_start[key] + d.rank[a];
-    d.sorted[sl] = a;
-    d.slot_cell[sl] = key;
-    d.smask[sl] = make_ulonglong2(d.exm[a], d.m14m[a]);  // bond classes in slot order (no dependent load later)
     if (d.prm.solvation) {  // Algorithm 1 adds its exchanges to both atoms of a pair: zero the sums (no memset node)
         d.Fcav[3 * a] = 0; d.Fcav[3 * a + 1] = 0; d.Fcav[3 * a + 2] = 0;
     }
+    if (!MIXED) {
+        d.sorted_tmp[sl] = a;
+        return;
+    }
+    const GridInfo g = d.grid[atom_chain(d, a)];
+    d.sorted[sl] = a;
+    d.slot_cell[sl] = key;
+    d.smask[sl] = make_ulonglong2(d.exm[a], d.m14m[a]);  // bond classes in slot order (no dependent load later)
     double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
     if (MIXED) {
         // the pair kernel adds each pair's share to both atoms: zero the sums and the list counters
@@ -235,11 +243,26 @@ __global__ void k_bin_place(const DevChain d) {
         float4 p = d.aprm32[a];
         d.spos32[sl] = make_float4(ox, oy, oz, (float)cx);  // w: the cell's x index (exact), for the pair shifts
         d.sprm32[sl] = p;
-    } else {
-        dbl4 p = d.aprm64[a];
-        d.spos64[sl] = make_dbl4(x, y, z, p.x);
-        d.sprm64[sl] = p;
     }
+}
+
+// FP64 mode: the atoms of each cell in atom order (a stable counting sort): the atom at slot s of the
+// placement by atomic ranks takes slot (cell start) + (atoms of its cell with a smaller index)
+__global__ void k_bin_stable(const DevChain d) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.n || d.status->done) return;
+    const int a = d.sorted_tmp[s];
+    const int key = d.key[a];
+    const int cs = d.cell_start[key], ce = d.cell_start[key + 1];
+    int r = 0;
+    for (int t = cs; t < ce; ++t) r += d.sorted_tmp[t] < a;
+    const int sl = cs + r;
+    d.sorted[sl] = a;
+    d.slot_cell[sl] = key;
+    d.smask[sl] = make_ulonglong2(d.exm[a], d.m14m[a]);
+    const dbl4 p = d.aprm64[a];
+    d.spos64[sl] = make_dbl4(d.r[3 * a], d.r[3 * a + 1], d.r[3 * a + 2], p.x);
+    d.sprm64[sl] = p;
 }
 
 // ================================================================ A3-A5: pair forces + lists
@@ -1309,10 +1332,12 @@ void launch_binning(DevChain& d, cudaStream_t s) {
         k_scan_sums<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
         k_scan_cells<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
     }
-    if (d.prm.precision == KCM_MIXED)
+    if (d.prm.precision == KCM_MIXED) {
         k_bin_place<true><<<blocks(d.n, 256), 256, 0, s>>>(d);
-    else
+    } else {
         k_bin_place<false><<<blocks(d.n, 256), 256, 0, s>>>(d);
+        k_bin_stable<<<blocks(d.n, 256), 256, 0, s>>>(d);
+    }
 }
 
 template <int W>

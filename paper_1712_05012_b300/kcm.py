@@ -18,6 +18,7 @@ KCM_E_CUDA = -3
 KCM_E_NONFINITE = -5
 KCM_E_OVERFLOW = -6
 KCM_E_NODEVICE = -8
+KCM_E_CANCELLED = -9
 KCM_FP64 = 0
 KCM_MIXED = 1
 KCM_STEP_CLAMP = 0
@@ -78,7 +79,7 @@ EXPORTS = [
     "kcm_set_fixed_joints", "kcm_nside_joints", "kcm_set_side_theta", "kcm_get_side_theta", "kcm_side_torques",
     "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev", "kcm_step_host",
     "kcm_set_tiles", "kcm_get_tiles", "kcm_autotune_tiles", "kcm_server_set_admission",
-    "kcm_set_pair_kernel", "kcm_get_pair_kernel", "kcm_autotune_pair_kernel",
+    "kcm_set_pair_kernel", "kcm_get_pair_kernel", "kcm_autotune_pair_kernel", "kcm_server_cancel",
 ]
 PAIR_WARP_PER_ATOM, PAIR_CELL_TILES = 0, 1
 TILE_CHOICES = (1, 2, 4)
@@ -169,6 +170,7 @@ def load():
             "kcm_server_job": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(JobInfo), _dp, C.c_int64]),
             "kcm_server_device_bytes": (C.c_int64, [C.c_void_p]),
             "kcm_server_set_admission": (C.c_int, [C.c_void_p, C.c_int32, C.c_double]),
+            "kcm_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -577,6 +579,10 @@ class Server:
     def set_admission(self, min_jobs: int = 1, max_wait_s: float = 0.0):
         """Admit waiting jobs once min_jobs wait or the oldest has waited max_wait_s (or nothing runs)."""
         _check(load().kcm_server_set_admission(self._s, int(min_jobs), float(max_wait_s)))
+
+    def cancel(self, job_id: int):
+        """Cancel a waiting or running job (it ends with KCM_E_CANCELLED)."""
+        _check(load().kcm_server_cancel(self._s, int(job_id)))
 
     def tick(self):
         w = np.zeros(1, dtype=np.int32)

@@ -2,7 +2,7 @@
 
 Tolerances:
   * positions: FP64 kinematics in both. The oracle multiplies the l rotations in sequence, whose
-    rounding grows with l (bound: kcm_testutil.tol_positions, 16 eps l^1.5 A, checked against an
+    rounding grows with l (bound: kcm_testutil.tol_positions, 4 eps l^1.5 A, checked against an
     80-bit evaluation); the library composes local link-frame transforms in a chunked scan and is
     checked against the 80-bit evaluation directly, to the same bound (measured: 3e-10 A at 16,000
     joints, where the oracle itself is 5e-10 A from it).
@@ -352,3 +352,21 @@ def test_near_coincident_atoms_stay_finite(kcm, table):
             assert np.all(np.isfinite(tau)) and np.abs(tau).max() > 1e10
             it, dm = ch.step(1)
             assert it == 1 and dm == pytest.approx(0.02)
+
+
+def test_deterministic_fp64(kcm, table):
+    """FP64 mode puts each cell's atoms in atom order (a stable counting sort), so its floating-point
+    pair sums, the torques and a trajectory are bitwise the same from run to run and handle to handle."""
+    seq, th = start("chain1000")
+    p = synth.RunParams(precision=synth.PRECISION_FP64)
+    runs = []
+    for _ in range(2):
+        with kcm.Chain(seq, table, p) as ch:
+            ch.set_theta(th)
+            t1 = ch.torques()
+            t2 = ch.torques()
+            ch.step(5)
+            runs.append((t1, t2, ch.get_theta()))
+    (a1, a2, ath), (b1, b2, bth) = runs
+    assert np.array_equal(a1, a2) and np.array_equal(a1, b1) and np.array_equal(b1, b2)
+    assert np.array_equal(ath, bth)

@@ -170,3 +170,123 @@ def test_server_budget(kcm, table):
             assert r["error"] == 0 and r["iters"] == 10
             it, dm, th1 = alone(kcm, table, p, seq, th, 10)
             assert np.max(np.abs(r["theta"] - th1)) < 1e-9
+
+
+def test_served_fp64_surrogate_follows_oracle_loop(kcm, table):
+    """Served FP64 jobs with the pairwise solvation surrogate (smooth, solvation = 2), several sharing
+    batches, 25 iterations each: theta against the oracle's own loop from the same start to 1e-8 rad."""
+    from oracle import oracle as O
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=2)
+    items = []
+    for i, m in enumerate((15, 30, 40, 9, 22, 33)):
+        items.append((synth.sequence(m, 71 + i), synth.theta_extended(m)))
+    caps = [25] * len(items)
+    got = run_server(kcm, table, p, items, caps, max_chains=3, chunk=6, waves=2)
+    for (seq, th), r in zip(items, got):
+        assert r["state"] == kcm.JOB_DONE and r["error"] == 0 and r["iters"] == 25
+        th_ref, it_ref, _, _ = O.OracleChain(seq, table, synth.GEOMETRY).run(p, th, 25)
+        assert it_ref == 25
+        assert np.max(np.abs(r["theta"] - th_ref)) < 1e-8
+
+
+def test_served_mixed_enumeration_torque_parity(kcm, table):
+    """Served mixed-precision jobs with Algorithm 1 (solvation = 1) from compact starts, in a mix, 20
+    iterations each: at the conformation each served job reached, the mixed torques agree with the FP64
+    oracle's to 1e-4 (per-iteration parity; the trajectories themselves are chaotic from compact starts)."""
+    from oracle import oracle as O
+    p = synth.RunParams(precision=synth.PRECISION_MIXED, solvation=1)
+    items, ochs = [], []
+    for i, m in enumerate((24, 60, 37, 12, 80)):
+        seq = synth.sequence(m, 91 + i)
+        och = O.OracleChain(seq, table, synth.GEOMETRY)
+        items.append((seq, synth.theta_from_codes(och.grow_start(91 + i))))
+        ochs.append(och)
+    caps = [20] * len(items)
+    got = run_server(kcm, table, p, items, caps, max_chains=3, chunk=7, waves=2)
+    pf = synth.RunParams(precision=synth.PRECISION_FP64, solvation=1)
+    for (seq, _), och, r in zip(items, ochs, got):
+        assert r["state"] == kcm.JOB_DONE and r["error"] == 0 and r["iters"] == 20
+        ref = och.evaluate(pf, r["theta"])
+        with kcm.Chain(seq, table, p) as ch:
+            ch.set_theta(r["theta"])
+            tau = ch.torques()
+        assert np.max(np.abs(tau - ref["tau"])) / np.max(np.abs(ref["tau"])) < 1e-4
+
+
+def drive(s, ids, on_tick=None, limit=120):
+    """Tick until every job is done; on_tick(s) runs after every tick."""
+    t0 = time.time()
+    while True:
+        wt, rn = s.tick()
+        if on_tick:
+            on_tick(s)
+        if wt == 0 and rn == 0 and set(ids) <= set(j for j in ids if s.job(j, with_theta=False)["state"] == 2):
+            break
+        assert time.time() - t0 < limit
+        time.sleep(0.0005)
+
+
+def test_freed_slots_are_refilled(kcm, table):
+    """Slots, not waves: two jobs arrive while a batch of four runs and wait (the admission wave asks for
+    three); when the batch's first two jobs retire after one chunk, the next batch takes the two waiting
+    jobs into the freed slots together with the batch's two running jobs, which move over with the angles
+    they reached, and the old batch is freed. Every job, moved or admitted into a freed slot, equals the
+    job run alone (FP64, 1e-9 rad), and the device memory held falls when jobs retire."""
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=0)
+    items = jobs(6, seed0=51)
+    caps = [5, 5, 40, 40, 30, 30]
+    with kcm.Server(p, 8 << 30, 4, 5) as s:
+        s.set_admission(3, 30.0)
+        ids = [s.submit(seq, table, th, cap) for (seq, th), cap in zip(items[:4], caps[:4])]
+        while s.tick()[1] == 0:  # the first batch is made on the worker thread (nothing ran: admitted)
+            time.sleep(0.0005)
+        first = s.device_bytes()
+        assert first > 0
+        ids += [s.submit(seq, table, th, cap) for (seq, th), cap in zip(items[4:], caps[4:])]
+        seen = []
+        for _ in range(200):  # the new jobs wait while all four slots are taken
+            w, r = s.tick()
+            if s.job(ids[0], with_theta=False)["state"] == kcm.JOB_DONE:
+                break
+            assert w == 2 and r == 4
+            time.sleep(0.0005)
+        seen = []
+        drive(s, ids, on_tick=lambda srv: seen.append(srv.device_bytes()))
+        assert s.device_bytes() == 0
+        # memory returns while jobs still run (a compacted batch replaces one with retired slots)
+        assert any(0 < b < a for a, b in zip(seen, seen[1:]))
+        got = [s.job(j) for j in ids]
+    for (seq, th), cap, r in zip(items, caps, got):
+        it, dm, th1 = alone(kcm, table, p, seq, th, cap)
+        assert r["state"] == kcm.JOB_DONE and r["error"] == 0 and r["iters"] == it == cap
+        assert np.max(np.abs(r["theta"] - th1)) < 1e-9
+
+
+def test_cancel(kcm, table):
+    """kcm_server_cancel: a waiting job retires at once, a running job at the end of its chunk, both with
+    KCM_E_CANCELLED; the other jobs are unaffected (equal to alone, FP64, 1e-9 rad)."""
+    p = synth.RunParams(precision=synth.PRECISION_FP64, solvation=0)
+    items = jobs(5, seed0=61)
+    caps = [30, 30, 30, 30, 30]
+    with kcm.Server(p, 8 << 30, 3, 4) as s:
+        ids = [s.submit(seq, table, th, cap) for (seq, th), cap in zip(items, caps)]
+        s.cancel(ids[4])  # still waiting
+        assert s.job(ids[4], with_theta=False)["error"] == kcm.KCM_E_CANCELLED
+        while s.job(ids[1], with_theta=False)["state"] != kcm.JOB_RUNNING:
+            s.tick()
+            time.sleep(0.0005)
+        s.cancel(ids[1])  # running: stops at the end of its chunk
+        with pytest.raises(kcm.KcmError):
+            s.cancel(ids[4])  # already finished
+        drive(s, ids)
+        got = [s.job(j) for j in ids]
+    c = got[1]
+    assert c["state"] == kcm.JOB_DONE and c["error"] == kcm.KCM_E_CANCELLED and 0 < c["iters"] < caps[1]
+    seq, th = items[1]
+    _, _, th_c = alone(kcm, table, p, seq, th, c["iters"])  # the angles it had reached
+    assert np.max(np.abs(c["theta"] - th_c)) < 1e-9
+    for k in (0, 2, 3):
+        seq, th = items[k]
+        it, dm, th1 = alone(kcm, table, p, seq, th, caps[k])
+        assert got[k]["error"] == 0 and got[k]["iters"] == it
+        assert np.max(np.abs(got[k]["theta"] - th1)) < 1e-9
