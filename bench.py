@@ -52,8 +52,8 @@ BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques_step": 60}  # algori
 DRAM_BYTES_PER_LAUNCH = {"solvation": 6.84e6}
 MIXED_DTYPE = "f32 pair/solvation; double-float (~48-bit) kinematics, wrenches and torque scans"
 # launches of one mixed-precision iteration with solvation on: reset + kinematics 2 + binning 2 + pairs 1 +
-# solvation 2 (the main kernel and the long-list kernel beside it) + wrench-tile 1 + torque-step 1
-KERNELS_PER_ITERATION = 10
+# solvation 2 (the main kernel and the long-list kernel beside it) + wrenches, torques and step 1
+KERNELS_PER_ITERATION = 9
 
 
 def parse():

@@ -42,6 +42,7 @@ extern "C" {
 #define KCM_E_INVAL (-1)     /* invalid argument or size mismatch */
 #define KCM_E_NOMEM (-2)     /* device or host allocation failed */
 #define KCM_E_CUDA (-3)      /* a CUDA runtime call failed */
+#define KCM_E_TIMEOUT (-4)   /* a bounded device wait gave up (the torque kernel's blocks wait for later tiles' totals) */
 #define KCM_E_NONFINITE (-5) /* a torque came out NaN or infinite */
 #define KCM_E_OVERFLOW (-6)  /* an atom had more solvation neighbours than the list holds */
 #define KCM_E_NODEVICE (-8)  /* no CUDA device, or the device is not sm_103 */
@@ -427,6 +428,13 @@ int kcm_get_pair_kernel(kcm_handle h, int32_t* kind);
  * KCM_PAIR_* (0 for a kernel not tried); *kind (may be NULL): the choice. Synchronises; errors as
  * kcm_autotune_tiles (the previous kernel is then restored). */
 int kcm_autotune_pair_kernel(kcm_handle h, int32_t reps, double* times_ms, int32_t* kind);
+
+/* Test only: the torque kernel never publishes the total of link tile `tile` (tiles of 32 links; -1,
+ * the default, publishes all), so that the blocks waiting for it give up after their bounded wait
+ * (about 0.2 s) and the call reports KCM_E_TIMEOUT, with the device context still usable. It exists to
+ * test that failure path; a handle with it set yields no valid torques. Synchronises and drops the
+ * captured graphs. Errors: KCM_E_INVAL (tile out of range). */
+int kcm_set_test_withhold(kcm_handle h, int32_t tile);
 
 /* Stages of one iteration, in launch order, as timed by kcm_step_timed. */
 #define KCM_STAGE_KINEMATICS 0 /* transform scan and atom centres (eq. kin_04, r1, r2) */

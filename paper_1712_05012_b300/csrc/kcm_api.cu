@@ -233,6 +233,7 @@ int read_status(kcm_ctx* h, kcm::Status* st) {
 
 int status_code(kcm_ctx* h, const kcm::Status& st) {
     if (st.error & kcm::kErrNonfinite) return set_err(h, KCM_E_NONFINITE, "a torque or coordinate is not finite");
+    if (st.error & kcm::kErrTimeout) return set_err(h, KCM_E_TIMEOUT, "a bounded device wait gave up");
     if (st.error & kcm::kErrOverflow)
         return set_err(h, KCM_E_OVERFLOW, "an atom has more than " + std::to_string(kcm::kMaxNbr) + " solvation neighbours");
     return KCM_OK;
@@ -552,8 +553,8 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.nbr, nn * kcm::kMaxNbr)) || (rc = dalloc(h, &d.nbr_off, nn * kcm::kMaxNbr)) ||
         (rc = dalloc(h, &d.covered, nn)) || (rc = dalloc(h, &d.long_atoms, nn)) || (rc = dalloc(h, &d.epair, 2 * nn)) || (rc = dalloc(h, &d.pstat, nn)) ||
         (rc = dalloc(h, &d.sstat, nn)) || (rc = dalloc(h, &d.esolv, nn)) ||
-        (rc = dalloc(h, &d.lane_suf, 6 * (size_t)L)) || (rc = dalloc(h, &d.tileS, 6 * (size_t)d.ltiles)) ||
-        (rc = dalloc(h, &d.tileSuf, 6 * (size_t)d.ltiles)) ||
+        (rc = dalloc(h, &d.tileS, 6 * (size_t)d.ltiles)) || (rc = dalloc(h, &d.tileStat, d.ltiles)) ||
+        (rc = dalloc(h, &d.lb_epoch, 1)) ||
         (rc = dalloc(h, &d.Ftot, 3 * nn)) || (rc = dalloc(h, &d.Fcav64, 3 * nn)) ||
         (rc = dalloc(h, &d.grid, hc.nchains)) || (rc = dalloc(h, &d.status, 1)) ||
         (rc = dalloc(h, &d.atom_chain, nn)) || (rc = dalloc(h, &d.joint_chain, l)) || (rc = dalloc(h, &d.link_chain, L)) ||
@@ -564,7 +565,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.chain_maxtau, hc.nchains)) || (rc = dalloc(h, &d.chain_lastdt, hc.nchains)) ||
         (rc = dalloc(h, &d.chain_E, 3 * (size_t)hc.nchains)) || (rc = dalloc(h, &d.gseg, l)) ||
         (rc = dalloc(h, &d.jhead, l)) || (rc = dalloc(h, &d.jfixed, l + d.ls)) || (rc = dalloc(h, &d.lflag, L)) ||
-        (rc = dalloc(h, &d.tileF, d.ntiles)) || (rc = dalloc(h, &d.ltail, L)) || (rc = dalloc(h, &d.tileT, d.ltiles)))
+        (rc = dalloc(h, &d.tileF, d.ntiles)) || (rc = dalloc(h, &d.tileT, d.ltiles)))
         return bail(rc);
 
     // per-atom constants
@@ -647,6 +648,9 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         d.r0fk = r0mode;
     }
     e = cudaMemsetAsync(d.theta, 0, sizeof(double) * (l + d.ls), h->stream);
+    // no tile total published yet, launch number 0 (the torque kernel's flags are launch numbers)
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.tileStat, 0, sizeof(unsigned int) * d.ltiles, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.lb_epoch, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.jfixed, 0, l + d.ls, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.Fcav, 0, sizeof(long long) * 3 * nn, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.covered, 0, sizeof(int) * nn, h->stream);
@@ -1077,6 +1081,16 @@ int kcm_set_pair_kernel(kcm_handle h, int32_t kind) {
     return KCM_OK;
 }
 
+int kcm_set_test_withhold(kcm_handle h, int32_t tile) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (tile < -1 || tile >= h->d.ltiles) return set_err(h, KCM_E_INVAL, "tile out of range");
+    int rc = sync(h);  // the captured graphs hold the old setting
+    if (rc) return rc;
+    drop_graphs(h);
+    h->d.lb_withhold = tile;
+    return KCM_OK;
+}
+
 int kcm_get_pair_kernel(kcm_handle h, int32_t* kind) {
     if (check_handle(h)) return KCM_E_INVAL;
     if (!kind) return set_err(h, KCM_E_INVAL, "kind is NULL");
@@ -1299,6 +1313,7 @@ const char* kcm_strerror(int code) {
         case KCM_E_OVERFLOW: return "solvation neighbour list overflow";
         case KCM_E_NODEVICE: return "no sm_103 CUDA device";
         case KCM_E_CANCELLED: return "cancelled";
+        case KCM_E_TIMEOUT: return "a bounded device wait gave up";
         default: return "unknown status";
     }
 }

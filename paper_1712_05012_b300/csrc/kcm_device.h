@@ -31,6 +31,7 @@ struct GridInfo {
 // Error bits in Status::error.
 constexpr int kErrNonfinite = 1;
 constexpr int kErrOverflow = 2;
+constexpr int kErrTimeout = 4;  // a bounded wait of a kernel on another block gave up
 
 // Device-resident loop state; the host reads it back only when asked.
 struct Status {
@@ -49,7 +50,7 @@ struct Status {
     unsigned int ticket_w;  // last-block detection in the wrench / suffix-scan kernel
     unsigned int ticket_bin;  // last-block detection in the cell-count kernel
     int nlong;                // atoms with more than kSasaStage solvation neighbours (long_atoms)
-    int pad2;
+    unsigned int ticket_lb;   // tiles handed out by the torque kernel (from the last one down)
 };
 
 // Launch shapes.
@@ -200,11 +201,13 @@ struct DevChain {
     unsigned char* lflag = nullptr;  // 1: a chain's base link (no joint), 2: the last link of a chain [L]
     unsigned char* gseg = nullptr; // FK: a chain starts in the joint's scan block at or before it [l]
     int* tileF = nullptr;          // FK: a chain starts in the scan block [ntiles]
-    unsigned char* ltail = nullptr;   // torques: a chain ends in the link's tile at or after it [L]
     int* tileT = nullptr;          // torques: a chain ends in the tile [ltiles]
-    double* lane_suf = nullptr;    // suffix sums within tiles of 32 links [L*6]
     double* tileS = nullptr;       // tile sums [ltiles*6]
-    double* tileSuf = nullptr;     // exclusive suffix sums of the tile sums [ltiles*6]
+    unsigned int* tileStat = nullptr;  // torque kernel: launch number with which the tile's total was
+                                       // published (k_wrench_step waits for it) [ltiles]
+    unsigned int* lb_epoch = nullptr;  // the torque kernel's launch number (never reset)
+    int lb_withhold = -1;              // test only (kcm_set_test_withhold): a tile whose total is never
+                                       // published, so that the waits on it time out
     double* Ftot = nullptr;        // [n*3] (on request)
     double* Fcav64 = nullptr;      // [n*3] (on request)
     GridInfo* grid = nullptr;      // [nchains]

@@ -1290,6 +1290,7 @@ __global__ void k_reset_loop(const DevChain d, int full) {
         st->error = 0;
         st->ticket = 0u;
         st->ticket_w = 0u;
+        st->ticket_lb = 0u;
         st->ticket_bin = 0u;
         st->last_max_dtheta = 0.0;
         if (full) {

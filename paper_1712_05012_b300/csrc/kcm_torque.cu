@@ -1,15 +1,20 @@
 // A7-A9: link wrenches, suffix sums over links, joint torques and the kinetostatic step: FP64 in
 // FP64 mode, double-float (kcm_df.cuh) in mixed mode; the step itself updates theta in FP64. The
-// wrench kernel, which visits every atom once with one thread each, also converts the mixed-mode
-// fixed-point forces, adds the cavity energy G0_i f_i and the pair energies of its atoms per chain,
-// and totals the per-atom counters of the pair and solvation kernels.
+// kernel visits every atom once with one thread each, so it also converts the mixed-mode fixed-point
+// forces, adds the cavity energy G0_i f_i (and the warp-per-atom pair kernel's pair energies) of its
+// atoms per chain, and totals the per-atom counters of the pair and solvation kernels.
 //
 // Wrench of link h about the origin, P_h = [sum r x F ; sum F] (eq. KCM_01/02), and
-// P^agg_k = sum_{h >= k} P_h (Sec. 3.5) as a reverse scan: k_wrench_tile forms P_h from the atoms of
-// a 32-link tile and scans the tile, its last block scans the tile totals, and k_torque takes
-// tau_k = u_k . T^agg_k + (p_k x u_k) . F^agg_k (eq. KCM_05/06).
-// In the clamped step mode the same thread applies dtheta_k = clamp(kappa tau_k, +-dtheta_max)
-// (eq. KCM_07); the last block to finish closes the iteration.
+// P^agg_k = sum_{h >= k} P_h (Sec. 3.5) as a reverse scan, then tau_k = u_k . T^agg_k +
+// (p_k x u_k) . F^agg_k (eq. KCM_05/06) and, in the clamped step mode, dtheta_k = clamp(kappa tau_k,
+// +-dtheta_max) (eq. KCM_07), all in one kernel (k_wrench_step): a block per tile of 32 links forms
+// the tile's P_h and their in-tile suffix sums, publishes the tile's total, sums the totals of the
+// later tiles of its chain (published by blocks that took them earlier: tiles are handed out from the
+// last one down, so a block only waits for blocks already running), and takes the tile's torques and
+// steps; the last block to finish closes the iteration. Each block sums the later totals itself, in a
+// fixed order, rather than taking a running prefix from whichever later block finished first, so the
+// result does not depend on timing: the torques stay bitwise reproducible. Every wait is bounded: a
+// block that waits too long sets the timeout error, and the kernel ends without torques.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -45,78 +50,131 @@ __device__ __forceinline__ void chain_add(double* arr, int stride, int c, V v) {
     }
 }
 
-// Segmented exclusive suffix sums of the tile totals (component w) by the wrench kernel's last block:
-// R_t = x_t + (a chain ends in tile t ? 0 : R_{t+1}), the suffix of tile totals from t to the first
-// chain end; tileSuf_t = R_{t+1}. A lane takes K consecutive tiles (their loads issued together): its
-// own segmented suffix over them, then a warp scan of the lanes' aggregates, then the tiles' R from
-// the next lane's first R; rounds of 32 K tiles from the end, carrying R of the first tile of the
-// later round. K = 1 for a few tiles (one round of single tiles is the shortest path), 8 for many.
-template <int kSufK, class T>
-__device__ __forceinline__ void tile_suffix(const DevChain& d, T* tileSuf, int w, int lane) {
-    T carry = num_f<T>(0.0f);
-    for (int top = d.ltiles; top > 0; top -= 32 * kSufK) {
-        const int b = top - 32 * kSufK + lane * kSufK;  // the lane's first tile
-        T x[kSufK];
-        bool tl[kSufK];
-#pragma unroll
-        for (int k = 0; k < kSufK; ++k) {
-            const int tt = b + k;
-            x[k] = num_f<T>(0.0f);
-            tl[k] = true;
-            if (tt >= 0) {
-                const double raw = __ldcg(&d.tileS[6 * (size_t)tt + w]);  // the slot of a T, read past L1
-                x[k] = *reinterpret_cast<const T*>(&raw);
-                tl[k] = __ldcg(&d.tileT[tt]) != 0;
+// the last block of the step: close the iteration of every chain that took a step
+__device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
+    __shared__ int s_run;
+    __shared__ unsigned long long s_dm;
+    if (d.nchains == 1) {  // one chain: one thread closes it, with every load issued before any store
+        if (threadIdx.x == 0) {
+            const unsigned long long m = __ldcg(&d.chain_maxdt[0]);
+            const int err = __ldcg(&st->error), done0 = __ldcg(&d.chain_done[0]);
+            const int it0 = __ldcg(&d.chain_iters[0]), maxit = __ldcg(&d.chain_maxit[0]), sit = __ldcg(&st->iters);
+            d.chain_maxdt[0] = 0ULL;
+            d.chain_maxtau[0] = 0ULL;
+            bool done = done0 != 0;
+            if (!err && !done) {
+                const double mc = __longlong_as_double((long long)m);
+                d.chain_lastdt[0] = mc;
+                d.chain_iters[0] = it0 + 1;
+                st->last_max_dtheta = mc;
+                st->iters = sit + 1;
+                if (mc < d.prm.conv_tol || it0 + 1 >= maxit) {
+                    d.chain_done[0] = 1;
+                    done = true;
+                }
             }
+            if (err || done) st->done = 1;
+            st->ticket = 0u;
         }
-        T r[kSufK];      // in-lane suffix from tile b + k to the first chain end or the lane's last tile
-        bool op[kSufK];  // no chain end in tiles b + k .. of the lane: the next lane's R continues it
-        r[kSufK - 1] = x[kSufK - 1];
-        op[kSufK - 1] = !tl[kSufK - 1];
-#pragma unroll
-        for (int k = kSufK - 2; k >= 0; --k) {
-            r[k] = tl[k] ? x[k] : add(x[k], r[k + 1]);
-            op[k] = !tl[k] && op[k + 1];
-        }
-        T X = r[0];
-        bool TL = !op[0];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const T y = shfl_down(X, off);
-            const bool yt = __shfl_down_sync(0xffffffffu, TL, off);
-            if (lane + off < 32 && !TL) { X = add(X, y); TL = yt; }
-        }
-        const T RL = TL ? X : add(X, carry);  // R of the lane's first tile
-        T Rn = shfl_down(RL, 1);                // R of the next lane's first tile
-        if (lane == 31) Rn = carry;
-#pragma unroll
-        for (int k = 0; k < kSufK; ++k) {
-            const int tt = b + k;
-            // tileSuf_t = R_{t+1}: the in-lane suffix of the next tile, continued by the next lane's R
-            const T e = k + 1 < kSufK ? (op[k + 1] ? add(r[k + 1], Rn) : r[k + 1]) : Rn;
-            if (tt >= 0) tileSuf[6 * (size_t)tt + w] = e;
-        }
-        carry = shfl(RL, 0);
+        return;
+    }
+    if (threadIdx.x == 0) { s_run = 0; s_dm = 0ULL; }
+    __syncthreads();
+    int run = 0;
+    unsigned long long dm = 0ULL;
+    for (int c = threadIdx.x; c < d.nchains; c += blockDim.x) {
+        const unsigned long long m = __ldcg(&d.chain_maxdt[c]);
+        d.chain_maxdt[c] = 0ULL;
+        d.chain_maxtau[c] = 0ULL;
+        if (__ldcg(&d.chain_err[c])) d.chain_done[c] = 1;  // a failed chain stops; the others go on
+        if (d.chain_done[c]) continue;
+        const double mc = __longlong_as_double((long long)m);
+        d.chain_lastdt[c] = mc;
+        const int it = d.chain_iters[c] + 1;
+        d.chain_iters[c] = it;
+        dm = max(dm, m);
+        if (mc < d.prm.conv_tol || it >= d.chain_maxit[c]) d.chain_done[c] = 1;  // converged or out of iterations
+        else ++run;
+    }
+    if (run) atomicAdd(&s_run, run);
+    if (dm) atomicMax(&s_dm, dm);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->last_max_dtheta = __longlong_as_double((long long)s_dm);
+        st->iters += 1;
+        if (s_run == 0) st->done = 1;  // every chain converged, reached its cap or failed
+        st->ticket = 0u;
     }
 }
 
-// One block per tile of 32 links h in [32 t, 32 t + 32). The block's threads take the tile's atoms
-// (r x F and F, with the conversion of the mixed-mode fixed-point forces) into shared memory; one
-// thread per (component, link) adds the link's atoms in atom order; warp q then scans component q of
-// the tile's P_h from the end (Kogge-Stone, segmented at the last link of each chain: a chain's
-// sums never take in the next chain), and the last block to finish (ticket, no waiting) forms the
-// segmented exclusive suffix sums of the tile totals.
-template <class T, bool SIDE>
-__global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChain d) {
+// Waits of k_wrench_step on later tiles' totals poll with a growing pause and give up after kSpinLimit
+// polls (about 0.2 s), which sets kErrTimeout: the kernel then ends without torques and the host reads
+// KCM_E_TIMEOUT.
+constexpr int kSpinLimit = 200000;
+
+__device__ __forceinline__ bool wait_published(const unsigned int* flag, unsigned int want) {
+    unsigned ns = 32;
+    for (int it = 0; it < kSpinLimit; ++it) {
+        if (__ldcg(flag) == want) return true;
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+    }
+    return false;
+}
+
+// sum over the warp in a fixed tree (lane 0 holds it)
+template <class T>
+__device__ __forceinline__ T warp_reduce(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = add(v, shfl_down(v, o));
+    return v;
+}
+
+// one step of a segmented reverse scan over the 32 lanes (component x, "a chain ends here" flag tl)
+template <class T>
+__device__ __forceinline__ void reverse_scan32(T& x, bool& tl, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T y = shfl_down(x, off);
+        const bool yt = __shfl_down_sync(0xffffffffu, tl, off);
+        if (lane + off < 32 && !tl) { x = add(x, y); tl = yt; }
+    }
+}
+
+// One block per tile of 32 links h in [32 t, 32 t + 32), the tiles taken from the last one down
+// (ticket). The block's threads take the tile's atoms (r x F and F, with the conversion of the
+// mixed-mode fixed-point forces) into shared memory; one thread per (component, link) adds the link's
+// atoms in atom order; warp q scans component q of the tile's P_h from the end (segmented at the last
+// link of each chain: a chain's sums never take in the next chain) and the tile's total is published.
+// The block then sums, in a fixed order, the totals of the later tiles up to the first one in which a
+// chain ends (rounds of blockDim tiles, a tree within each round), which is the part of P^agg of its
+// links that lies beyond the tile, and forms tau, and with STEP the clamped step, of the tile's joints
+// (side-chain joints from their branch sums). The last block to finish closes the iteration.
+template <class T, bool SIDE, bool STEP>
+__global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_step(const DevChain d) {
     constexpr bool DF = std::is_same<T, df>::value;
     __shared__ T sV[kWrenchTileAtoms][6];
-    __shared__ T sP[32][6];
+    __shared__ T sP[32][6];  // link wrenches, then their in-tile suffix sums
+    __shared__ bool sTL[32];  // a chain ends in the tile at or after the link
+    __shared__ T sW[kWrenchWarps][6];
+    __shared__ T sSuf[6];
     __shared__ unsigned long long sSt[kWrenchWarps][4];
     __shared__ int sMx[kWrenchWarps];
-    __shared__ bool last;
+    __shared__ int sTile, sEnd;
+    __shared__ unsigned int sEpoch;
+    __shared__ bool sLast, sTimeout;
     Status* st = d.status;
     if (st->done) return;
-    const int t = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        sTile = d.ltiles - 1 - (int)atomicAdd(&st->ticket_lb, 1u);  // later tiles first
+        sEpoch = __ldcg(d.lb_epoch) + 1u;
+        sTimeout = false;
+        sEnd = 0x7fffffff;
+    }
+    __syncthreads();
+    const int t = sTile, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned int epoch = sEpoch;
+    double side_tau = 0.0;
     const int h0 = 32 * t, h1 = min(h0 + 32, d.L);
     const int a0 = d.link_start[h0], a1 = d.link_start[h1];
     const T* rr = reinterpret_cast<const T*>(DF ? d.rdf : d.r);
@@ -261,161 +319,150 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_tile(const DevChai
         const T mx = sub(S[0], sub(mul(sA[1], S[5]), mul(sA[2], S[4])));
         const T my = sub(S[1], sub(mul(sA[2], S[3]), mul(sA[0], S[5])));
         const T mz = sub(S[2], sub(mul(sA[0], S[4]), mul(sA[1], S[3])));
-        d.tau[d.l + sc] = to_double(add(add(mul(sU[0], mx), mul(sU[1], my)), mul(sU[2], mz)));
+        side_tau = to_double(add(add(mul(sU[0], mx), mul(sU[1], my)), mul(sU[2], mz)));
     }
     __syncthreads();
-    T* lane_suf = reinterpret_cast<T*>(d.lane_suf);
     T* tileS = reinterpret_cast<T*>(d.tileS);
     if (w < 6) {  // segmented reverse inclusive scan of component w over the tile
         const int h = h0 + lane;
         T x = sP[lane][w];
         bool tl = h >= d.L - 1 || (h < h1 && (d.lflag[h] & 2));  // last link of a chain
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const T y = shfl_down(x, off);
-            const bool yt = __shfl_down_sync(0xffffffffu, tl, off);
-            if (lane + off < 32 && !tl) { x = add(x, y); tl = yt; }
-        }
-        if (h < d.L) {
-            lane_suf[6 * (size_t)h + w] = x;
-            if (w == 0) d.ltail[h] = (unsigned char)tl;  // a chain ends in the tile at or after h
-        }
+        reverse_scan32(x, tl, lane);
+        sP[lane][w] = x;  // warp w alone reads and writes column w
+        if (w == 0) sTL[lane] = tl;
         if (lane == 0) {
             tileS[6 * (size_t)t + w] = x;
             if (w == 0) d.tileT[t] = tl;
+            __threadfence();  // the total before its flag
         }
     }
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&st->ticket_w, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    T* tileSuf = reinterpret_cast<T*>(d.tileSuf);
-    if (w < 6) {  // segmented exclusive suffix sums of the tile totals
-        if (d.ltiles <= 64) tile_suffix<1>(d, tileSuf, w, lane);
-        else tile_suffix<8>(d, tileSuf, w, lane);
+    if (threadIdx.x == 0 && t != d.lb_withhold) atomicExch(&d.tileStat[t], epoch);  // published
+    // the joint of link h0 + lane (warp 0): its current axis and point, loaded before the wait
+    int jj_l = -1, ch_l = 0;
+    T uj[3], pj[3];
+    if (w == 0) {
+        const int h = h0 + lane;
+        if (h < h1 && !(d.lflag[h] & 1)) {  // a chain's base link has no joint
+            ch_l = d.nchains == 1 ? 0 : d.link_chain[h];
+            jj_l = h - ch_l - 1;  // the joint that moves links h .. the chain's last link
+            const T* u = reinterpret_cast<const T*>(DF ? d.ucurdf : d.ucur) + 3 * jj_l;
+            const T* p = reinterpret_cast<const T*>(DF ? d.pcurdf : d.pcur) + 3 * jj_l;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { uj[k] = u[k]; pj[k] = p[k]; }
+        }
     }
-    if (threadIdx.x == 0) st->ticket_w = 0u;
-}
-
-// the last block of the step: close the iteration of every chain that took a step
-__device__ __forceinline__ void close_iteration(const DevChain& d, Status* st) {
-    __shared__ int s_run;
-    __shared__ unsigned long long s_dm;
-    if (d.nchains == 1) {  // one chain: one thread closes it, with every load issued before any store
-        if (threadIdx.x == 0) {
-            const unsigned long long m = __ldcg(&d.chain_maxdt[0]);
-            const int err = __ldcg(&st->error), done0 = __ldcg(&d.chain_done[0]);
-            const int it0 = __ldcg(&d.chain_iters[0]), maxit = __ldcg(&d.chain_maxit[0]), sit = __ldcg(&st->iters);
-            d.chain_maxdt[0] = 0ULL;
-            d.chain_maxtau[0] = 0ULL;
-            bool done = done0 != 0;
-            if (!err && !done) {
-                const double mc = __longlong_as_double((long long)m);
-                d.chain_lastdt[0] = mc;
-                d.chain_iters[0] = it0 + 1;
-                st->last_max_dtheta = mc;
-                st->iters = sit + 1;
-                if (mc < d.prm.conv_tol || it0 + 1 >= maxit) {
-                    d.chain_done[0] = 1;
-                    done = true;
+    // P^agg beyond the tile: the totals of the later tiles up to the first chain end, in a fixed order
+    T acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = num_f<T>(0.0f);
+    // uniform: needed unless a chain ends at the tile's last link (then no link of the tile reaches past it)
+    if (!sTL[h1 - h0 - 1]) {
+        for (int base = t + 1; base < d.ltiles; base += blockDim.x) {  // uniform
+            const int tt = base + threadIdx.x;
+            T v[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[k] = num_f<T>(0.0f);
+            bool ends = false;
+            if (tt < d.ltiles) {
+                if (!wait_published(&d.tileStat[tt], epoch)) {
+                    sTimeout = true;
+                } else {
+                    __threadfence();
+                    ends = __ldcg(&d.tileT[tt]) != 0;
+                    const double* raw = &d.tileS[6 * (size_t)tt];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        const double r = __ldcg(&raw[k]);
+                        v[k] = *reinterpret_cast<const T*>(&r);
+                    }
                 }
             }
-            if (err || done) st->done = 1;
-            st->ticket = 0u;
+            if (ends) atomicMin(&sEnd, tt);
+            __syncthreads();
+            const int e = sEnd;
+            const bool out = sTimeout;
+            if (tt > e) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) v[k] = num_f<T>(0.0f);
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const T r = warp_reduce(v[k]);
+                if (lane == 0) sW[w][k] = r;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int q = 0; q < kWrenchWarps; ++q)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) acc[k] = add(acc[k], sW[q][k]);
+            __syncthreads();
+            if (out || e != 0x7fffffff) break;  // uniform
         }
-        return;
     }
-    if (threadIdx.x == 0) { s_run = 0; s_dm = 0ULL; }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sSuf[k] = acc[k];
     __syncthreads();
-    int run = 0;
-    unsigned long long dm = 0ULL;
-    for (int c = threadIdx.x; c < d.nchains; c += blockDim.x) {
-        const unsigned long long m = __ldcg(&d.chain_maxdt[c]);
-        d.chain_maxdt[c] = 0ULL;
-        d.chain_maxtau[c] = 0ULL;
-        if (__ldcg(&d.chain_err[c])) d.chain_done[c] = 1;  // a failed chain stops; the others go on
-        if (d.chain_done[c]) continue;
-        const double mc = __longlong_as_double((long long)m);
-        d.chain_lastdt[c] = mc;
-        const int it = d.chain_iters[c] + 1;
-        d.chain_iters[c] = it;
-        dm = max(dm, m);
-        if (mc < d.prm.conv_tol || it >= d.chain_maxit[c]) d.chain_done[c] = 1;  // converged or out of iterations
-        else ++run;
-    }
-    if (run) atomicAdd(&s_run, run);
-    if (dm) atomicMax(&s_dm, dm);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        st->last_max_dtheta = __longlong_as_double((long long)s_dm);
-        st->iters += 1;
-        if (s_run == 0) st->done = 1;  // every chain converged, reached its cap or failed
-        st->ticket = 0u;
-    }
-}
-
-// tau_k from P^agg (main-chain joints; the side-chain joints after them have theirs from the wrench
-// kernel); with STEP the clamped step of the chains still running and the end of the iteration
-template <bool STEP, class T>
-__global__ void __launch_bounds__(128) k_torque(const DevChain d) {
-    constexpr bool DF = std::is_same<T, df>::value;
-    __shared__ bool last;
-    Status* st = d.status;
-    if (st->done) return;
-    const int jj = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long adt = 0ULL, atau = 0ULL;  // bit patterns of non-negative doubles
+    // torques (and steps) of the tile's joints: link h's joint from P^agg_h = in-tile suffix (+ the
+    // later tiles' part unless its chain ends in the tile), side-chain joints from their branch sums
+    unsigned long long atau1 = 0ULL, adt1 = 0ULL, atau2 = 0ULL, adt2 = 0ULL;  // bit patterns of |.|
+    int cj1 = -1, cj2 = -1;
     bool bad = false;
-    int cj = -1;
-    if (jj < d.l + d.ls) {
-        double t;
-        if (jj < d.l) {
-            cj = joint_chain(d, jj);
-            const int h = jj + cj + 1, tile = h >> 5;  // joint jj moves links h .. the chain's last link
-            const T* ls = reinterpret_cast<const T*>(d.lane_suf);
-            const T* ts = reinterpret_cast<const T*>(d.tileSuf);
-            const bool own = d.ltail[h] != 0;  // the chain ends within this tile
+    auto step_joint = [&](int jj, int cj, double tq, int& cjo, unsigned long long& atau, unsigned long long& adt) {
+        d.tau[jj] = tq;
+        const bool nf = !isfinite(tq);
+        bad = bad || nf;
+        if (nf) atomicOr(&d.chain_err[cj], kErrNonfinite);
+        const bool fx = d.jfixed[jj] != 0;  // a fixed joint takes no step and has no say in max |tau|
+        atau = fx ? 0ULL : (unsigned long long)__double_as_longlong(fabs(tq));
+        cjo = cj;
+        if (d.chain_done[cj] || d.chain_err[cj]) {
+            cjo = -1;  // a converged or failed chain takes no more steps
+        } else if (STEP && !nf) {
+            const double dt = fx ? 0.0 : fmin(fmax(d.prm.kappa * tq, -d.prm.dtheta_max), d.prm.dtheta_max);
+            if (!fx) d.theta[jj] += dt;
+            d.dtheta[jj] = dt;
+            adt = (unsigned long long)__double_as_longlong(fabs(dt));
+        }
+    };
+    if (!sTimeout) {
+        if (jj_l >= 0) {
             T A[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) A[k] = own ? ls[6 * (size_t)h + k] : add(ls[6 * (size_t)h + k], ts[6 * (size_t)tile + k]);
-            const T* u = reinterpret_cast<const T*>(DF ? d.ucurdf : d.ucur) + 3 * jj;
-            const T* p = reinterpret_cast<const T*>(DF ? d.pcurdf : d.pcur) + 3 * jj;
+            for (int k = 0; k < 6; ++k) A[k] = sTL[lane] ? sP[lane][k] : add(sP[lane][k], sSuf[k]);
+            const T* u = uj;
+            const T* p = pj;
             const T px = sub(mul(p[1], u[2]), mul(p[2], u[1]));
             const T py = sub(mul(p[2], u[0]), mul(p[0], u[2]));
             const T pz = sub(mul(p[0], u[1]), mul(p[1], u[0]));
             const T tt = add(add(add(mul(u[0], A[0]), mul(u[1], A[1])), add(mul(u[2], A[2]), mul(px, A[3]))),
                              add(mul(py, A[4]), mul(pz, A[5])));
-            t = to_double(tt);
-        } else {
-            cj = atom_chain(d, d.chi_b[jj - d.l]);
-            t = d.tau[jj];  // formed by the wrench kernel
+            step_joint(jj_l, ch_l, to_double(tt), cj1, atau1, adt1);
         }
-        d.tau[jj] = t;
-        bad = !isfinite(t);
-        if (bad) atomicOr(&d.chain_err[cj], kErrNonfinite);
-        const bool fx = d.jfixed[jj] != 0;  // a fixed joint takes no step and has no say in max |tau|
-        atau = fx ? 0ULL : (unsigned long long)__double_as_longlong(fabs(t));
-        if (d.chain_done[cj] || d.chain_err[cj]) {
-            cj = -1;  // a converged or failed chain takes no more steps
-        } else if (STEP && !bad) {
-            const double dt = fx ? 0.0 : fmin(fmax(d.prm.kappa * t, -d.prm.dtheta_max), d.prm.dtheta_max);
-            if (!fx) d.theta[jj] += dt;
-            d.dtheta[jj] = dt;
-            adt = (unsigned long long)__double_as_longlong(fabs(dt));
-        }
+        if (SIDE && sc < sc1) step_joint(d.l + sc, atom_chain(d, sb), side_tau, cj2, atau2, adt2);
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->error, kErrNonfinite);
-    chain_max(d.chain_maxtau, cj, atau);
-    if (!STEP) return;
-    chain_max(d.chain_maxdt, cj, adt);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->error, kErrNonfinite);
+    chain_max(d.chain_maxtau, cj1, atau1);
+    chain_max(d.chain_maxtau, cj2, atau2);
+    if (STEP) {
+        chain_max(d.chain_maxdt, cj1, adt1);
+        chain_max(d.chain_maxdt, cj2, adt2);
+    }
+    if (threadIdx.x == 0 && sTimeout) atomicOr(&st->error, kErrTimeout);
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) sLast = atomicAdd(&st->ticket_w, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (!last) return;
+    if (!sLast) return;
     __threadfence();
-    close_iteration(d, st);
+    if (threadIdx.x == 0) {  // every block is done: the next launch takes fresh tickets and flags
+        st->ticket_w = 0u;
+        st->ticket_lb = 0u;
+        *d.lb_epoch = epoch;
+    }
+    if (STEP) close_iteration(d, st);
+    if (threadIdx.x == 0 && (__ldcg(&st->error) & kErrTimeout)) st->done = 1;  // a timed-out iteration ends the loop
 }
 
 // the paper's normalised step (eq. KCM_07): dtheta_k = kappa tau_k / max |tau| over the free joints of
@@ -451,29 +498,23 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
 
 }  // namespace
 
-template <class T>
-void launch_wrench(DevChain& d, cudaStream_t s) {
-    if (d.ls) k_wrench_tile<T, true><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
-    else k_wrench_tile<T, false><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+template <class T, bool STEP>
+void launch_wrench_step(DevChain& d, cudaStream_t s) {
+    if (d.ls) k_wrench_step<T, true, STEP><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+    else k_wrench_step<T, false, STEP><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
 }
 
 void launch_torques(DevChain& d, cudaStream_t s) {
-    if (d.prm.precision == KCM_MIXED) {
-        launch_wrench<df>(d, s);
-        k_torque<false, df><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
-    } else {
-        launch_wrench<double>(d, s);
-        k_torque<false, double><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
-    }
+    if (d.prm.precision == KCM_MIXED) launch_wrench_step<df, false>(d, s);
+    else launch_wrench_step<double, false>(d, s);
 }
 
 template <class T>
 void launch_torques_step_t(DevChain& d, cudaStream_t s) {
-    launch_wrench<T>(d, s);
     if (d.prm.step_mode == KCM_STEP_CLAMP) {
-        k_torque<true, T><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
+        launch_wrench_step<T, true>(d, s);
     } else {
-        k_torque<false, T><<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
+        launch_wrench_step<T, false>(d, s);
         k_step_normalized<<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
     }
 }

@@ -15,6 +15,7 @@ KCM_OK = 0
 KCM_E_INVAL = -1
 KCM_E_NOMEM = -2
 KCM_E_CUDA = -3
+KCM_E_TIMEOUT = -4
 KCM_E_NONFINITE = -5
 KCM_E_OVERFLOW = -6
 KCM_E_NODEVICE = -8
@@ -80,6 +81,7 @@ EXPORTS = [
     "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev", "kcm_step_host",
     "kcm_set_tiles", "kcm_get_tiles", "kcm_autotune_tiles", "kcm_server_set_admission",
     "kcm_set_pair_kernel", "kcm_get_pair_kernel", "kcm_autotune_pair_kernel", "kcm_server_cancel",
+    "kcm_set_test_withhold",
 ]
 PAIR_WARP_PER_ATOM, PAIR_CELL_TILES = 0, 1
 TILE_CHOICES = (1, 2, 4)
@@ -134,6 +136,7 @@ def load():
             "kcm_set_pair_kernel": (C.c_int, [h, C.c_int32]),
             "kcm_get_pair_kernel": (C.c_int, [h, _ip]),
             "kcm_autotune_pair_kernel": (C.c_int, [h, C.c_int32, _dp, _ip]),
+            "kcm_set_test_withhold": (C.c_int, [h, C.c_int32]),
             "kcm_set_fixed_joints": (C.c_int, [h, C.c_void_p, C.c_int64]),
             "kcm_nside_joints": (C.c_int64, [h]),
             "kcm_set_side_theta": (C.c_int, [h, _dp, C.c_int64]),
@@ -462,6 +465,11 @@ class Chain:
         k = np.zeros(1, dtype=np.int32)
         _check(load().kcm_autotune_pair_kernel(self._h, int(reps), _dptr(t), _iptr(k)), self._h)
         return int(k[0]), t
+
+    def set_test_withhold(self, tile: int):
+        """Test only: the torque kernel never publishes this link tile's total (-1: none), so the
+        waits on it time out and calls report KCM_E_TIMEOUT."""
+        _check(load().kcm_set_test_withhold(self._h, int(tile)), self._h)
 
     def get_pair_kernel(self) -> int:
         p = np.zeros(1, dtype=np.int32)

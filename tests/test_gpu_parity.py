@@ -370,3 +370,27 @@ def test_deterministic_fp64(kcm, table):
     (a1, a2, ath), (b1, b2, bth) = runs
     assert np.array_equal(a1, a2) and np.array_equal(a1, b1) and np.array_equal(b1, b2)
     assert np.array_equal(ath, bth)
+
+
+def test_bounded_wait_times_out(kcm, table):
+    """The torque kernel's blocks wait for the totals of later link tiles with a bounded wait. With the
+    last tile's publication withheld (test hook) every other block gives up after its bound and the
+    call reports KCM_E_TIMEOUT, without hanging; the handle and the context stay usable, and the next
+    evaluation is correct again."""
+    seq, och, th = small_case(table, 40, 1235, "compact")  # 81 links: three tiles of 32
+    p = synth.RunParams(precision=synth.PRECISION_FP64)
+    ref = och.evaluate(p, th)
+    with kcm.Chain(seq, table, p) as ch:
+        ch.set_theta(th)
+        ch.set_test_withhold(2)
+        with pytest.raises(kcm.KcmError) as e:
+            ch.torques()
+        assert e.value.code == kcm.KCM_E_TIMEOUT
+        with pytest.raises(kcm.KcmError) as e:
+            ch.step(3)
+        assert e.value.code == kcm.KCM_E_TIMEOUT
+        ch.set_test_withhold(-1)
+        ch.set_theta(th)
+        assert rel_inf(ch.torques(), ref["tau"]) < TOL_FP64
+        with pytest.raises(kcm.KcmError):
+            ch.set_test_withhold(3)  # out of range
