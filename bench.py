@@ -419,7 +419,7 @@ def run_ours(args):
     # pair kernel (warp per atom or cell-pair tiles) and tile shapes from the library's autotuner, at the
     # start conformation, before the warm-up
     prepare(ch, lib_stream)
-    kind, kind_ms = ch.autotune_pair_kernel(reps=3)
+    kind, kind_ms = ch.autotune_pair_kernel(reps=10)
     tiles = {"used": list(ch.get_tiles()), "choices": list(kcm.TILE_CHOICES), "source": "autotuner",
              "pair_kernel": ("cell_tiles" if kind == kcm.PAIR_CELL_TILES else "warp_per_atom"),
              "pair_kernel_ms": {"warp_per_atom": float(kind_ms[0]), "cell_tiles": float(kind_ms[1])}}
