@@ -16,8 +16,8 @@
 // atomics into per-tile sums; a tile's sums go to the global fixed-point forces with one 64-bit integer
 // add per atom and tile instead of one per pair. The integer sums do not depend on the order of the
 // terms, so the forces are bitwise those of every other evaluation order (the warp-per-atom kernel's
-// among them). The solvation pairs of a tile take their ranks among the tile's list entries of each atom
-// from shared counters; one global reservation per atom and tile then gives the list slots, so no global
+// among them). The solvation pairs of a tile are counted per atom with shared counters; one global
+// reservation per atom and tile then gives the list slots, which the entries take in turn, so no global
 // atomic waits inside the pair loop. Home atoms that a short segment leaves idle are replaced by copies:
 // with H home atoms (rounded up to a power of two) the 32 / H lane groups each test a different part of
 // the staged row.
@@ -37,9 +37,11 @@ constexpr int kPtFlushChunks = 8;     // staged rows between flushes of the home
                                       // |.| <= 2^22 stay within int32
 constexpr float kPtFilterPad = 0.02f; // A^2 added to the filter's squared range: its rounded shifted
                                       // offsets differ from the exact ones by ~1e-5 A at most
-// queue entry: staged index (bits 0-4), home index (5-9); after the evaluation, for a solvation pair, a flag
-// (10) and the pair's ranks among the chunk's list entries of the home atom (11-15) and of the staged one (16-20)
+// queue entry: staged index (bits 0-4), home index (5-9); the evaluation sets bit 10 for a solvation pair
 constexpr unsigned kQNear = 1u << 10;
+#ifndef KCM_PT_MIN_BLOCKS
+#define KCM_PT_MIN_BLOCKS 7  // resident blocks per SM the register budget is set for (shared memory allows 7)
+#endif
 
 // one warp's shared memory
 struct PtSmem {
@@ -57,13 +59,14 @@ struct PtSmem {
     int jacc[6][32];       // of the staged atoms (their negated terms)
     int icnt[32], jcnt[32];    // solvation-list entries of the chunk per home / staged atom
     int ibase[32], jbase[32];  // their first list slots, reserved once per chunk
-    unsigned queue[kPtQueue];  // in-range pairs (kQNear layout)
+    int iput[32], jput[32];    // entries written so far (each entry takes the next reserved slot)
+    unsigned short queue[kPtQueue];  // in-range pairs (kQNear layout)
 };
 
 // SPLIT warps share one window and stencil row: warp s takes staged rows s, s + SPLIT, ... (more and
 // shorter warps for small workloads; chosen by the tile autotuner)
 template <int KR, int SPLIT>
-__global__ void __launch_bounds__(kPtWarps * 32) k_pair_tile(const DevChain d) {
+__global__ void __launch_bounds__(kPtWarps * 32, KCM_PT_MIN_BLOCKS) k_pair_tile(const DevChain d) {
     constexpr int kW = 2 * KR + 1;
     constexpr int kRows = 1 + KR + KR * kW;  // rows of the half stencil
     __shared__ PtSmem smem[kPtWarps];
@@ -263,6 +266,8 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_pair_tile(const DevChain d) {
             for (int k = 0; k < 6; ++k) S.jacc[k][lane] = 0;
             S.icnt[lane] = 0;
             S.jcnt[lane] = 0;
+            S.iput[lane] = 0;
+            S.jput[lane] = 0;
             __syncwarp();
             if (jc + 32 * SPLIT < tjend) fetch(jc + 32 * SPLIT);  // the next staged row, in flight during this one
             // filter: lane (hi, gi) tests home atom hi against staged atoms gi H .. gi H + H - 1, two at a
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_pair_tile(const DevChain d) {
             {
                 int pos = incl - c;
                 const unsigned tag = ((unsigned)hi << 5) | (unsigned)(gi * H);
-                for (unsigned mm = mask; mm; mm &= mm - 1) S.queue[pos++] = tag + (unsigned)(__ffs(mm) - 1);
+                for (unsigned mm = mask; mm; mm &= mm - 1) S.queue[pos++] = (unsigned short)(tag + (unsigned)(__ffs(mm) - 1));
             }
             __syncwarp();
             // evaluation: lane L takes the queue entries L R .. L R + R - 1, R = ceil(T / 32), so the
@@ -327,9 +332,10 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_pair_tile(const DevChain d) {
                 if (!(d2 <= rall2)) continue;  // the filter's margin let it through
                 const float4 hq = S.hprm[ih], jq = S.jprm[jj];
                 if (solv && solv_near_f32(d2, hq.w, jq.w, dr, pad)) {
-                    // ranks among the chunk's list entries of both atoms; the slots are reserved below
-                    const unsigned li = (unsigned)atomicAdd(&S.icnt[ih], 1), lj = (unsigned)atomicAdd(&S.jcnt[jj], 1);
-                    S.queue[e] = en | kQNear | (li << 11) | (lj << 16);
+                    // counted here, the slots reserved below, the entries written after that
+                    atomicAdd(&S.icnt[ih], 1);
+                    atomicAdd(&S.jcnt[jj], 1);
+                    S.queue[e] = (unsigned short)(en | kQNear);
                 }
                 const int a = S.hatom[ih], b = S.jatom[jj];
                 const int lo = min(a, b), off = max(a, b) - lo;
@@ -418,8 +424,9 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_pair_tile(const DevChain d) {
                     const float ddy = pair_delta_f32(hp.y, jp.y, shy);
                     const float ddz = pair_delta_f32(hp.z, jp.z, shz);
                     const int a = S.hatom[ih], b = S.jatom[jj];
-                    const int slot = S.ibase[ih] + (int)((en >> 11) & 31u);
-                    const int rslot = S.jbase[jj] + (int)((en >> 16) & 31u);
+                    // each entry takes the next of its atoms' reserved slots (a list's order is free)
+                    const int slot = S.ibase[ih] + atomicAdd(&S.iput[ih], 1);
+                    const int rslot = S.jbase[jj] + atomicAdd(&S.jput[jj], 1);
                     if (slot < kMaxNbr) {
                         d.nbr[(size_t)a * kMaxNbr + slot] = b;
                         d.nbr_off[(size_t)a * kMaxNbr + slot] = make_float4(-ddx, -ddy, -ddz, __fmul_rn(S.jprm[jj].w, S.jprm[jj].w));
