@@ -429,6 +429,22 @@ int kcm_get_pair_kernel(kcm_handle h, int32_t* kind);
  * kcm_autotune_tiles (the previous kernel is then restored). */
 int kcm_autotune_pair_kernel(kcm_handle h, int32_t reps, double* times_ms, int32_t* kind);
 
+/* Binning kernel (A2, Sec. 3.2: cell counts, their scan, the atoms in slot order). KCM_BIN_CLUSTER (the
+ * default): a single chain of up to 32,768 atoms in mixed precision is binned in one launch of one
+ * thread-block cluster of up to 16 CTAs, the cell counts kept in the CTAs' shared memory (atomics through distributed shared
+ * memory) and the stages joined by cluster barriers; it applies when the chain's cell cap split over
+ * the cluster fits in shared memory (at most 53,248 cells per CTA) and the device can place the
+ * cluster. Otherwise, and for batches and FP64, KCM_BIN_BLOCKS: a count kernel whose last block scans
+ * the counts, then a placement kernel. The cluster kernel forms an atom's cell and its offset from the
+ * cell corner in double-float and rounds once to float, where the blocks round the FP64 difference, so
+ * pair forces agree to FP32 rounding, not bit for bit. kcm_set_binning_kernel synchronises and drops
+ * the captured graphs; KCM_E_INVAL for another value. kcm_get_binning_kernel reads the kernel in use
+ * and the CTAs of its cluster (0 for the blocks; `ctas` may be NULL). */
+#define KCM_BIN_BLOCKS 0
+#define KCM_BIN_CLUSTER 1
+int kcm_set_binning_kernel(kcm_handle h, int32_t kind);
+int kcm_get_binning_kernel(kcm_handle h, int32_t* kind, int32_t* ctas);
+
 /* Test only: the torque kernel never publishes the total of link tile `tile` (tiles of 32 links; -1,
  * the default, publishes all), so that the blocks waiting for it give up after their bounded wait
  * (about 0.2 s) and the call reports KCM_E_TIMEOUT, with the device context still usable. It exists to

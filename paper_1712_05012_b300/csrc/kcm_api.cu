@@ -27,6 +27,7 @@ struct kcm_ctx {
     kcm::Status* st_host = nullptr;          // page-locked copy of the status record (read back by the calls)
     cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
     int sm_count = 148;
+    bool bin_cluster = true;         // the cluster binning kernel where the chain qualifies (kcm_set_binning_kernel)
     std::vector<void*> allocs;       // every allocation of the handle from the pool (arena chunks included)
     char* arena = nullptr;           // small arrays are carved from chunks of kArenaChunk bytes
     size_t arena_left = 0;
@@ -409,6 +410,8 @@ int set_cell_size(kcm_ctx* h, double cell_size) {
     d.stencil = stencil;
     d.prm.cell_size = cell_size;
     if (int prc = set_pair_grid(h)) return prc;  // the stencil picks the pair kernel's form
+    cudaError_t fe = kcm::plan_bin_cluster(d, h->bin_cluster);  // the cell cap sizes its cell ranges
+    if (fe != cudaSuccess) return cuda_fail(h, fe, "binning kernel attributes");
     int rc = upload(h, d.ccap, ccap.data(), hc.nchains);
     return rc ? rc : sync(h);
 }
@@ -1088,6 +1091,26 @@ int kcm_set_test_withhold(kcm_handle h, int32_t tile) {
     if (rc) return rc;
     drop_graphs(h);
     h->d.lb_withhold = tile;
+    return KCM_OK;
+}
+
+int kcm_set_binning_kernel(kcm_handle h, int32_t kind) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (kind != KCM_BIN_BLOCKS && kind != KCM_BIN_CLUSTER)
+        return set_err(h, KCM_E_INVAL, "binning kernel must be KCM_BIN_BLOCKS or KCM_BIN_CLUSTER");
+    int rc = sync(h);  // no launch of the old kernels is pending when the graphs go
+    if (rc) return rc;
+    drop_graphs(h);
+    h->bin_cluster = kind == KCM_BIN_CLUSTER;
+    cudaError_t e = kcm::plan_bin_cluster(h->d, h->bin_cluster);
+    return e == cudaSuccess ? KCM_OK : cuda_fail(h, e, "binning kernel attributes");
+}
+
+int kcm_get_binning_kernel(kcm_handle h, int32_t* kind, int32_t* ctas) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (!kind) return set_err(h, KCM_E_INVAL, "kind is NULL");
+    *kind = h->d.bin_c ? KCM_BIN_CLUSTER : KCM_BIN_BLOCKS;
+    if (ctas) *ctas = h->d.bin_c;
     return KCM_OK;
 }
 

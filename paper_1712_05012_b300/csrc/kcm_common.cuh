@@ -22,6 +22,14 @@ __device__ __forceinline__ double dkey_inv(unsigned long long k) {
     return __longlong_as_double(static_cast<long long>(b));
 }
 
+// Mixed mode: coordinate i of atom a in FP64, from the double-float centres the kinematics keep (the
+// exact double of hi + lo, as the FP64 centres are formed); the mixed kernels need it only on their rare
+// FP64 re-decisions, so the kinematics need not store FP64 centres in this mode.
+__device__ __forceinline__ double centre64(const DevChain& d, int a, int i) {
+    const float2 v = reinterpret_cast<const float2*>(d.rdf)[3 * a + i];
+    return __dadd_rn((double)v.x, (double)v.y);
+}
+
 // affine transform: rows of the rotation a[0..8], translation a[9..11]; C = A o B
 __device__ __forceinline__ void aff_compose(const double* A, const double* B, double* C) {
     double T[12];
@@ -171,32 +179,20 @@ __device__ __forceinline__ bool covers64(double qx, double qy, double qz, double
 }
 
 
-// Grid of chain c's cell list from its bounding box d.cbox[6c..6c+5] (order-preserving keys):
-// cube cells of edge s with d.stencil * s >= every interaction range (plus a margin that absorbs
-// FP32 cell assignment, so that two atoms within range are at most d.stencil cells apart on every
-// axis), and s >= the requested edge; s a multiple of 2^-10 A so that it is exact in float;
-// coarsened when the box would need more cells than the chain's cap. Leaves cbase to the caller and
-// clears the box. Returns false for a non-finite box.
-__device__ __forceinline__ bool chain_grid(const DevChain& d, int c, GridInfo* out) {
-    // every load before the first store (the box is reset for the next evaluation)
-    unsigned long long kb[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) kb[i] = __ldcg(&d.cbox[6 * c + i]);
-    const long long cap = d.ccap[c];
-    double lo[3], hi[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        lo[i] = dkey_inv(kb[i]);
-        hi[i] = dkey_inv(kb[3 + i]);
-        d.cbox[6 * c + i] = ~0ULL;
-        d.cbox[6 * c + 3 + i] = 0ULL;
-    }
+// Grid of a chain's cell list from its bounding box (lo, hi; or kb, order-preserving keys: min x, y, z
+// then max x, y, z): cube cells of edge s with d.stencil * s >= every interaction range (plus a margin that
+// absorbs FP32 cell assignment, so that two atoms within range are at most d.stencil cells apart on
+// every axis), and s >= the requested edge; s a multiple of 2^-10 A so that it is exact in float;
+// coarsened when the box would need more cells than the chain's cap. Leaves cbase to the caller.
+// Returns false for a non-finite box (the grid is then one cell at the origin).
+__device__ __forceinline__ bool grid_from_bounds(const DevChain& d, double* lo, double* hi, long long cap, GridInfo* out) {
     GridInfo g;
     const bool finite = isfinite(hi[0] - lo[0]) && isfinite(hi[1] - lo[1]) && isfinite(hi[2] - lo[2]);
     if (!finite)
         for (int i = 0; i < 3; ++i) { lo[i] = 0.0; hi[i] = 0.0; }
     const double ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
-    double s = fmax(fma(1e-6, fmax(ext[0], fmax(ext[1], ext[2])), d.s_base) / d.stencil, d.prm.cell_size);
+    // (the division by the stencil, 1 or 2, is exact: a multiplication)
+    double s = fmax(fma(1e-6, fmax(ext[0], fmax(ext[1], ext[2])), d.s_base) * (d.stencil == 2 ? 0.5 : 1.0), d.prm.cell_size);
     s = ceil(s * 1024.0) * (1.0 / 1024.0);
     for (;;) {
         // n_i = floor(ext_i / s) + 1 estimated in float, then raised until n_i s > ext_i holds exactly
@@ -225,6 +221,30 @@ __device__ __forceinline__ bool chain_grid(const DevChain& d, int c, GridInfo* o
     g.pad = 0;
     *out = g;
     return finite;
+}
+
+__device__ __forceinline__ bool grid_from_box(const DevChain& d, const unsigned long long* kb, long long cap,
+                                              GridInfo* out) {
+    double lo[3], hi[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = dkey_inv(kb[i]);
+        hi[i] = dkey_inv(kb[3 + i]);
+    }
+    return grid_from_bounds(d, lo, hi, cap, out);
+}
+
+// the grid of chain c from the box its atoms were added to (cbox), which is reset for the next evaluation
+__device__ __forceinline__ bool chain_grid(const DevChain& d, int c, GridInfo* out) {
+    unsigned long long kb[6];  // every load before the first store
+#pragma unroll
+    for (int i = 0; i < 6; ++i) kb[i] = __ldcg(&d.cbox[6 * c + i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        d.cbox[6 * c + i] = ~0ULL;
+        d.cbox[6 * c + 3 + i] = 0ULL;
+    }
+    return grid_from_box(d, kb, d.ccap[c], out);
 }
 
 }  // namespace dev

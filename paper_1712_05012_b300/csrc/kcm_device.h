@@ -81,6 +81,9 @@ struct DevChain {
                          // jfixed hold the l main-chain joints and then the ls side-chain joints
     int nmv = 0;         // atoms moved by side-chain joints
     int fk_j = 1;        // joints per quad (four-lane transform slot) in the transform scan
+    int bin_c = 0;       // single chain, mixed mode: CTAs of the cluster kernel that bins the atoms in one
+                         // launch (k_bin_cluster); 0: the count and placement kernels
+    int bin_capc = 0;    // its cells per CTA in shared memory (a multiple of 4, >= ceil(cell cap / bin_c))
     int ntiles = 0;      // transform-scan blocks of 32 * fk_j joints
     int ltiles = 0;      // suffix-sum tiles of 32 links
     int cell_cap = 0;     // cells of all chains' caps
@@ -218,7 +221,11 @@ struct DevChain {
 void launch_init_status(DevChain& d, cudaStream_t s);
 void launch_reset_loop(DevChain& d, cudaStream_t s);
 void launch_fk(DevChain& d, cudaStream_t s);
-void launch_binning(DevChain& d, cudaStream_t s);
+void launch_binning(DevChain& d, cudaStream_t s);  // with bin_c: k_bin_cluster
+void launch_bin_cluster(DevChain& d, cudaStream_t s);  // kcm_bin_cluster.cu
+// the cluster shape of k_bin_cluster for the chain and its cell cap (bin_c, bin_capc; bin_c = 0 when not
+// wanted, when the chain does not qualify or when no such cluster fits the device)
+cudaError_t plan_bin_cluster(DevChain& d, bool want);
 void launch_pairs(DevChain& d, cudaStream_t s);
 void launch_pairs_tile(DevChain& d, cudaStream_t s);  // kcm_pair_tile.cu
 int pair_tile_rows(int stencil);                      // warps per window of 32 slots of k_pair_tile

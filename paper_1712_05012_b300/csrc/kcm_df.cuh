@@ -71,6 +71,17 @@ __device__ __forceinline__ df df_from_i64(long long x) {
     return two_sum(__fmul_rn(h, 16777216.0f), l);
 }
 
+// Order-preserving 64-bit key of a normalized double-float (hi = the float nearest to hi + lo, which the
+// operations above keep): the order of the keys is the order of the values, and the key decodes to the
+// same pair, so minima and maxima of exact double-float values need no FP64 arithmetic.
+__device__ __forceinline__ unsigned fkey(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k); }
+__device__ __forceinline__ unsigned long long dfkey(df v) { return ((unsigned long long)fkey(v.hi) << 32) | fkey(v.lo); }
+__device__ __forceinline__ df dfkey_inv(unsigned long long k) { return {fkey_inv((unsigned)(k >> 32)), fkey_inv((unsigned)k)}; }
+
 __device__ __forceinline__ df shfl(df a, int src) {
     return {__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src)};
 }
@@ -86,7 +97,10 @@ __device__ __forceinline__ df shfl_down(df a, int off) {
 // a second 33-bit and a remainder double, so k P1 and k P2 are exact for |k| < 2^20. Then the Taylor
 // series of sin and cos in x = r^2 (|r| <= pi/4; the first omitted terms are below 5e-17), evaluated
 // by Horner's rule in double-float, and the quadrant k mod 4.
-__device__ __forceinline__ void df_sincos(double th, df* s_out, df* c_out) {
+struct df_sc {
+    df s, c;
+};
+__device__ __forceinline__ df_sc df_sincos_v(double th) {
     // 1/n! as float pairs (hi + lo within 2e-16 relative of the exact rational)
     constexpr float kInvFact[18][2] = {
         {1.0f, 0.0f}, {1.0f, 0.0f}, {0x1p-1f, 0.0f},
@@ -125,8 +139,15 @@ __device__ __forceinline__ void df_sincos(double th, df* s_out, df* c_out) {
     const int q = (int)((long long)k & 3LL);
     const df s = (q & 1) ? cr : sr;
     const df c = (q & 1) ? sr : cr;
-    *s_out = (q & 2) ? neg(s) : s;
-    *c_out = ((q + 1) & 2) ? neg(c) : c;
+    return {(q & 2) ? neg(s) : s, ((q + 1) & 2) ? neg(c) : c};
+}
+// not inlined: the kernels that call it run it once or a few times per thread, and one copy of its
+// ~300 instructions is fetched once per SM instead of at every call site
+static __device__ __noinline__ df_sc df_sincos_nl(double th) { return df_sincos_v(th); }
+__device__ __forceinline__ void df_sincos(double th, df* s_out, df* c_out) {
+    const df_sc r = df_sincos_nl(th);
+    *s_out = r.s;
+    *c_out = r.c;
 }
 
 // ---- the same interface for double (FP64 mode)

@@ -59,15 +59,47 @@ __device__ __forceinline__ void quad_rows(const T* b, int base, T* B) {
     }
 }
 
-// row of C = A o B from row a of A and the full B (rows B[0..3], B[4..7], B[8..11])
+// A row and a whole transform (rows B[0..3], B[4..7], B[8..11]) passed by value.
+template <class T>
+struct Row4 {
+    T v[4];
+};
+template <class T>
+struct Mat34 {
+    T v[12];
+};
+
+// row of C = A o B from row a of A and the full B
+template <class T>
+__device__ __forceinline__ Row4<T> row_compose_v(const Row4<T>& a, const Mat34<T>& B) {
+    Row4<T> c;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) c.v[m] = fma(a.v[2], B.v[8 + m], fma(a.v[1], B.v[4 + m], mul(a.v[0], B.v[m])));
+    c.v[3] = fma(a.v[2], B.v[11], fma(a.v[1], B.v[7], fma(a.v[0], B.v[3], a.v[3])));
+    return c;
+}
+
+// The double-float composition (~150 float instructions) as one function that is not inlined. These
+// kernels run their straight-line code once per SM, so their time goes largely to fetching it: the
+// instruction caches start cold after other kernels (and after an L2 flush the code comes from DRAM),
+// and a composition inlined at every site is fetched at every site. One shared copy is fetched once
+// and then runs from the cache (measured on B300: a composition costs ~0.5 us as fresh inline code
+// from L2, ~1.1 us from DRAM, ~0.3 us as a call).
+__device__ __noinline__ Row4<df> row_compose_df(Row4<df> a, Mat34<df> B) { return row_compose_v(a, B); }
+
 template <class T>
 __device__ __forceinline__ void row_compose(const T* a, const T* B, T* c) {
-    T t[4];
+    Row4<T> ra;
+    Mat34<T> mb;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) t[m] = fma(a[2], B[8 + m], fma(a[1], B[4 + m], mul(a[0], B[m])));
-    t[3] = fma(a[2], B[11], fma(a[1], B[7], fma(a[0], B[3], a[3])));
+    for (int m = 0; m < 4; ++m) ra.v[m] = a[m];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) c[m] = t[m];
+    for (int m = 0; m < 12; ++m) mb.v[m] = B[m];
+    Row4<T> rc;
+    if constexpr (std::is_same<T, df>::value) rc = row_compose_df(ra, mb);
+    else rc = row_compose_v(ra, mb);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) c[m] = rc.v[m];
 }
 
 // row rr of the local joint transform L_j = Tr(step_j) o Rot(u_j, th) with

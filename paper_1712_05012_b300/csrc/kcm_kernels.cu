@@ -476,8 +476,9 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
                 bool inE = !excl && d2 <= rc2, inV = !excl && d2 <= rv2;
                 if (MIXED && !excl && (fabs(d2 - rc2) <= gp || fabs(d2 - rv2) <= gp)) {
                     // guard band: decide the cutoff in FP64 exactly as the FP64 path does
-                    double ex = __dsub_rn(d.r[3 * a], d.r[3 * b]), ey = __dsub_rn(d.r[3 * a + 1], d.r[3 * b + 1]),
-                           ez = __dsub_rn(d.r[3 * a + 2], d.r[3 * b + 2]);
+                    double ex = __dsub_rn(centre64(d, a, 0), centre64(d, b, 0)),
+                           ey = __dsub_rn(centre64(d, a, 1), centre64(d, b, 1)),
+                           ez = __dsub_rn(centre64(d, a, 2), centre64(d, b, 2));
                     double d64 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
                     inE = d64 <= d.rcut2;
                     inV = d64 <= d.rvdw2;
@@ -891,13 +892,14 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
             auto recheck = [&](int j, int k, int s) -> bool {  // FP64, identical to the FP64 kernel
                 ++nguard;
                 const double Roa = d.aprm64[a].w, dr = d.prm.delta_r;
-                const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
+                const double rax = centre64(d, a, 0), ray = centre64(d, a, 1), raz = centre64(d, a, 2);
                 const int b = s_idx[w][j];
                 const double ro = d.aprm64[b].w;
                 const double qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
                 const double qy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
                 const double qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
-                return covers64(qx, qy, qz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
+                return covers64(qx, qy, qz, centre64(d, b, 0), centre64(d, b, 1), centre64(d, b, 2), __dmul_rn(ro, ro),
+                                s, dr);
             };
             for (int kb = 0; kb < d.N; kb += kBatch) {
                 float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane], mx[kPtsPerLane];
@@ -1056,13 +1058,14 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed_long(const DevCh
             auto recheck = [&](int j, int k, int s) -> bool {  // FP64, identical to the FP64 kernel
                 ++nguard;
                 const double Roa = d.aprm64[a].w, dr = d.prm.delta_r;
-                const double rax = d.r[3 * a], ray = d.r[3 * a + 1], raz = d.r[3 * a + 2];
+                const double rax = centre64(d, a, 0), ray = centre64(d, a, 1), raz = centre64(d, a, 2);
                 const int b = nl[j];
                 const double ro = d.aprm64[b].w;
                 const double qx = __dadd_rn(rax, __dmul_rn(Roa, d.Q64[3 * k]));
                 const double qy = __dadd_rn(ray, __dmul_rn(Roa, d.Q64[3 * k + 1]));
                 const double qz = __dadd_rn(raz, __dmul_rn(Roa, d.Q64[3 * k + 2]));
-                return covers64(qx, qy, qz, d.r[3 * b], d.r[3 * b + 1], d.r[3 * b + 2], __dmul_rn(ro, ro), s, dr);
+                return covers64(qx, qy, qz, centre64(d, b, 0), centre64(d, b, 1), centre64(d, b, 2), __dmul_rn(ro, ro),
+                                s, dr);
             };
             for (int kb = 0; kb < d.N; kb += kBatch) {
                 float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane], mx[kPtsPerLane];
@@ -1211,7 +1214,8 @@ __global__ void __launch_bounds__(W * 32) k_sasa_pw(const DevChain d) {
             d2 = ox * ox + oy * oy + oz * oz;
             return d2 < (Ri + Rj) * (Ri + Rj);
         }
-        const double ex = d.r[3 * b] - d.r[3 * a], ey = d.r[3 * b + 1] - d.r[3 * a + 1], ez = d.r[3 * b + 2] - d.r[3 * a + 2];
+        const double ex = centre64(d, b, 0) - centre64(d, a, 0), ey = centre64(d, b, 1) - centre64(d, a, 1),
+                     ez = centre64(d, b, 2) - centre64(d, a, 2);
         const double s64 = d.aprm64[a].w + d.aprm64[b].w;
         return ex * ex + ey * ey + ez * ez < s64 * s64;
     };
@@ -1328,6 +1332,10 @@ void launch_init_status(DevChain& d, cudaStream_t s) { k_reset_loop<<<blocks(d.n
 void launch_reset_loop(DevChain& d, cudaStream_t s) { k_reset_loop<<<blocks(d.nchains, 256), 256, 0, s>>>(d, 0); }
 
 void launch_binning(DevChain& d, cudaStream_t s) {
+    if (d.bin_c) {  // a single chain in mixed mode: one cluster
+        launch_bin_cluster(d, s);
+        return;
+    }
     k_bin_count<<<blocks(d.n, kBinThreads), kBinThreads, 0, s>>>(d);
     if (!d.scan_fused) {
         k_scan_sums<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);

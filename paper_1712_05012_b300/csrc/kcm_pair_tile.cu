@@ -348,8 +348,9 @@ __global__ void __launch_bounds__(kPtWarps * 32, KCM_PT_MIN_BLOCKS) k_pair_tile(
                 bool inE = !excl && d2 <= rc2, inV = !excl && d2 <= rv2;
                 if (!excl && (fabsf(d2 - rc2) <= tgp || fabsf(d2 - rv2) <= tgp)) {
                     // guard band: the cutoff decided in FP64 exactly as the FP64 path decides it
-                    const double ex = __dsub_rn(d.r[3 * a], d.r[3 * b]), ey = __dsub_rn(d.r[3 * a + 1], d.r[3 * b + 1]),
-                                 ez = __dsub_rn(d.r[3 * a + 2], d.r[3 * b + 2]);
+                    const double ex = __dsub_rn(centre64(d, a, 0), centre64(d, b, 0)),
+                                 ey = __dsub_rn(centre64(d, a, 1), centre64(d, b, 1)),
+                                 ez = __dsub_rn(centre64(d, a, 2), centre64(d, b, 2));
                     const double d64 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
                     inE = d64 <= d.rcut2;
                     inV = d64 <= d.rvdw2;

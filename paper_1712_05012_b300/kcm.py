@@ -81,9 +81,10 @@ EXPORTS = [
     "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev", "kcm_step_host",
     "kcm_set_tiles", "kcm_get_tiles", "kcm_autotune_tiles", "kcm_server_set_admission",
     "kcm_set_pair_kernel", "kcm_get_pair_kernel", "kcm_autotune_pair_kernel", "kcm_server_cancel",
-    "kcm_set_test_withhold",
+    "kcm_set_test_withhold", "kcm_set_binning_kernel", "kcm_get_binning_kernel",
 ]
 PAIR_WARP_PER_ATOM, PAIR_CELL_TILES = 0, 1
+BIN_BLOCKS, BIN_CLUSTER = 0, 1
 TILE_CHOICES = (1, 2, 4)
 AUTOTUNE_MAX = 64
 # candidate cell edges of the autotuner (A): 0 is the smallest 27-cell edge; edges below the largest
@@ -137,6 +138,8 @@ def load():
             "kcm_get_pair_kernel": (C.c_int, [h, _ip]),
             "kcm_autotune_pair_kernel": (C.c_int, [h, C.c_int32, _dp, _ip]),
             "kcm_set_test_withhold": (C.c_int, [h, C.c_int32]),
+            "kcm_set_binning_kernel": (C.c_int, [h, C.c_int32]),
+            "kcm_get_binning_kernel": (C.c_int, [h, _ip, _ip]),
             "kcm_set_fixed_joints": (C.c_int, [h, C.c_void_p, C.c_int64]),
             "kcm_nside_joints": (C.c_int64, [h]),
             "kcm_set_side_theta": (C.c_int, [h, _dp, C.c_int64]),
@@ -475,6 +478,17 @@ class Chain:
         p = np.zeros(1, dtype=np.int32)
         _check(load().kcm_get_pair_kernel(self._h, _iptr(p)), self._h)
         return int(p[0])
+
+    def set_binning_kernel(self, kind: int):
+        """BIN_CLUSTER (default: the binning in one cluster launch where the chain qualifies) or
+        BIN_BLOCKS (the count and placement kernels)."""
+        _check(load().kcm_set_binning_kernel(self._h, int(kind)), self._h)
+
+    def get_binning_kernel(self):
+        """(kind in use, CTAs of the cluster or 0)."""
+        p = np.zeros(2, dtype=np.int32)
+        _check(load().kcm_get_binning_kernel(self._h, _iptr(p[:1]), _iptr(p[1:])), self._h)
+        return int(p[0]), int(p[1])
 
     def get_tiles(self):
         """(pair_warps, sasa_warps, pair_persistent)."""
