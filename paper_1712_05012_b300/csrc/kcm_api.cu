@@ -28,6 +28,7 @@ struct kcm_ctx {
     cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
     int sm_count = 148;
     bool bin_cluster = true;         // the cluster binning kernel where the chain qualifies (kcm_set_binning_kernel)
+    bool pdl = true;                 // captured graphs use programmatic dependent launch (dropped if a capture fails)
     std::vector<void*> allocs;       // every allocation of the handle from the pool (arena chunks included)
     char* arena = nullptr;           // small arrays are carved from chunks of kArenaChunk bytes
     size_t arena_left = 0;
@@ -250,25 +251,47 @@ int evaluate(kcm_ctx* h) {
     return status_code(h, st);
 }
 
+// Captures what `enqueue` launches on the handle's stream into an executable graph. Its kernels allow
+// programmatic dependent launch (each waits for the previous grid of the stream at its start, so only
+// launch latency overlaps); should a capture or instantiation fail that way, it is taken again without
+// and the handle stops asking for it.
+template <class F>
+cudaError_t capture_graph(kcm_ctx* h, F enqueue, cudaGraphExec_t* out) {
+    cudaError_t e = cudaSuccess;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        h->d.pdl = h->pdl ? 1 : 0;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue();
+            e = cudaStreamEndCapture(h->stream, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+        if (g) cudaGraphDestroy(g);
+        h->d.pdl = 0;
+        if (e == cudaSuccess) return e;
+        *out = nullptr;
+        if (!h->pdl) return e;
+        (void)cudaGetLastError();
+        h->pdl = false;
+    }
+    return e;
+}
+
 // the iteration graph, and the same preceded by the loop-state reset (the first launch of a step call)
 int build_graph(kcm_ctx* h) {
     if (h->graph && h->graph_first) return KCM_OK;
     for (int first = 0; first < 2; ++first) {
         cudaGraphExec_t* out = first ? &h->graph_first : &h->graph;
         if (*out) continue;
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
-        if (first) kcm::launch_reset_loop(h->d, h->stream);
-        enqueue_iteration(h);
-        e = cudaStreamEndCapture(h->stream, &g);
-        if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
-        e = cudaGraphInstantiate(out, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            *out = nullptr;
-            return cuda_fail(h, e, "graph instantiate");
-        }
+        const cudaError_t e = capture_graph(
+            h,
+            [&] {
+                if (first) kcm::launch_reset_loop(h->d, h->stream);
+                enqueue_iteration(h);
+            },
+            out);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
     }
     return KCM_OK;
 }
@@ -1005,16 +1028,14 @@ int kcm_autotune_cell(kcm_handle h, const double* candidates, int32_t n_candidat
         // one evaluation at the current theta (no step) per launch of a graph captured for this edge
         rc = set_cell_size(h, candidates[i]);
         if (rc) break;
-        cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
-        e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            kcm::launch_reset_loop(h->d, h->stream);
-            enqueue_evaluation(h);
-            e = cudaStreamEndCapture(h->stream, &g);
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
-        if (g) cudaGraphDestroy(g);
+        e = capture_graph(
+            h,
+            [&] {
+                kcm::launch_reset_loop(h->d, h->stream);
+                enqueue_evaluation(h);
+            },
+            &ge);
         if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->stream);  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
         for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(ge, h->stream);
@@ -1153,16 +1174,14 @@ int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pa
         if (pair_fixed && pp != old_pp) continue;
         rc = kcm_set_tiles(h, pw, sw, pp);
         if (rc) break;
-        cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
-        e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            kcm::launch_reset_loop(h->d, h->stream);
-            enqueue_evaluation(h);
-            e = cudaStreamEndCapture(h->stream, &g);
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
-        if (g) cudaGraphDestroy(g);
+        e = capture_graph(
+            h,
+            [&] {
+                kcm::launch_reset_loop(h->d, h->stream);
+                enqueue_evaluation(h);
+            },
+            &ge);
         if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->stream);  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
         for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(ge, h->stream);

@@ -47,6 +47,7 @@ constexpr int kBcMaxCells = 52 * 1024;            // most cells of a CTA's range
 constexpr int kBcAtomsPerCta = 1024;              // atoms per CTA the plan aims at (one per thread)
 
 __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
+    grid_dep_sync();
     extern __shared__ int4 sCell4[];  // the CTA's cell counts, then their starts within the range
     int* sCell = reinterpret_cast<int*>(sCell4);
     __shared__ int sWs[kBcWarps];
@@ -183,8 +184,10 @@ cudaLaunchConfig_t bin_cluster_config(const DevChain& d, cudaStream_t s, cudaLau
     at[0].val.clusterDim.x = d.bin_c;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // as launch_k
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = d.pdl ? 2 : 1;
     return cfg;
 }
 
@@ -215,7 +218,7 @@ cudaError_t plan_bin_cluster(DevChain& d, bool want) {
     DevChain t = d;
     t.bin_c = C;
     t.bin_capc = (int)capc;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     cudaLaunchConfig_t cfg = bin_cluster_config(t, nullptr, at);
     int clusters = 0;
     if (cudaOccupancyMaxActiveClusters(&clusters, k_bin_cluster, &cfg) != cudaSuccess || clusters < 1) {
@@ -228,7 +231,7 @@ cudaError_t plan_bin_cluster(DevChain& d, bool want) {
 }
 
 void launch_bin_cluster(DevChain& d, cudaStream_t s) {
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     const cudaLaunchConfig_t cfg = bin_cluster_config(d, s, at);
     cudaLaunchKernelEx(&cfg, k_bin_cluster, d);
 }

@@ -8,6 +8,15 @@
 namespace kcm {
 namespace dev {
 
+// Programmatic dependent launch: the first statement of every kernel of the library. It waits until the
+// previous grid of the stream has completed and its memory operations are visible (at once when the
+// kernel was launched without the attribute, or has no such predecessor), then lets the stream's next
+// grid be scheduled, so that its launch overlaps this kernel's run (launch_k).
+__device__ __forceinline__ void grid_dep_sync() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- small helpers
 // chain of an atom or joint (no load for a single chain)
 __device__ __forceinline__ int atom_chain(const DevChain& d, int a) { return d.nchains == 1 ? 0 : d.atom_chain[a]; }

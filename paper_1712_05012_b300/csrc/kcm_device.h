@@ -91,6 +91,8 @@ struct DevChain {
     int pair_warps = 1, sasa_warps = 1;  // tile shapes: atoms per block of k_pair and of k_sasa_mixed / k_sasa_pw
     int pair_tile = 0;         // mixed mode: the cell-pair tile kernel (k_pair_tile) instead of the warp-per-atom
                                // kernel; its pair energies and counters go straight to the chain and status totals
+    int pdl = 0;               // launches allow programmatic dependent launch (set while the iteration graphs
+                               // are captured; every kernel starts with grid_dep_sync)
     int pair_persistent = 0;   // the pair kernel on a persistent grid (one block per resident slot)
     int pair_grid_cap = 0;     // its block count then (SMs x resident blocks per SM); 0: one block per W atoms
     int scan_blocks = 0;

@@ -29,6 +29,7 @@
 #include "kcm_common.cuh"
 #include "kcm_df.cuh"
 #include "kcm_device.h"
+#include "kcm_launch.h"
 
 namespace kcm {
 
@@ -289,6 +290,7 @@ __device__ __forceinline__ void side_fk_block(const DevChain& d, int b) {
 
 template <int J, class T>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
+    grid_dep_sync();
     __shared__ T sW[kFkWarps][12];
     __shared__ int sF[kFkWarps];
     if (d.status->done) return;
@@ -392,6 +394,7 @@ constexpr int kTileWarps = 8;
 constexpr int kTileQuads = 8 * kTileWarps;
 template <class T>
 __global__ void __launch_bounds__(kTileWarps * 32) k_fk_tiles(const DevChain d) {
+    grid_dep_sync();
     __shared__ T sW[kTileWarps][12];
     __shared__ int sF[kTileWarps];
     if (d.status->done) return;
@@ -515,6 +518,7 @@ __device__ __forceinline__ void block_prefix(const DevChain& d, int b0, int b1, 
 // block to finish (ticket, no waiting) sets the chains' grids and their cell bases
 template <int J, class T>
 __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
+    grid_dep_sync();
     __shared__ T sW[kFkWarps][12];
     __shared__ int sF[kFkWarps];
     __shared__ int sScan[kFkWarps];
@@ -696,13 +700,13 @@ void launch_fk_j(DevChain& d, cudaStream_t s) {
     const int nscan = d.ntiles + (d.nmv + kSideFkThreads - 1) / kSideFkThreads;
     const bool tiles = d.ntiles > kFkTreeTiles;  // the block products scanned by k_fk_tiles
     if (d.prm.precision == KCM_MIXED) {
-        k_fk_scan<J, df><<<nscan, kFkWarps * 32, 0, s>>>(d);
-        if (tiles) k_fk_tiles<df><<<1, kTileWarps * 32, 0, s>>>(d);
-        k_fk_apply<J, df><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+        launch_k(k_fk_scan<J, df>, nscan, kFkWarps * 32, 0, s, d.pdl, d);
+        if (tiles) launch_k(k_fk_tiles<df>, 1, kTileWarps * 32, 0, s, d.pdl, d);
+        launch_k(k_fk_apply<J, df>, d.ntiles, kFkWarps * 32, 0, s, d.pdl, d);
     } else {
-        k_fk_scan<J, double><<<nscan, kFkWarps * 32, 0, s>>>(d);
-        if (tiles) k_fk_tiles<double><<<1, kTileWarps * 32, 0, s>>>(d);
-        k_fk_apply<J, double><<<d.ntiles, kFkWarps * 32, 0, s>>>(d);
+        launch_k(k_fk_scan<J, double>, nscan, kFkWarps * 32, 0, s, d.pdl, d);
+        if (tiles) launch_k(k_fk_tiles<double>, 1, kTileWarps * 32, 0, s, d.pdl, d);
+        launch_k(k_fk_apply<J, double>, d.ntiles, kFkWarps * 32, 0, s, d.pdl, d);
     }
 }
 

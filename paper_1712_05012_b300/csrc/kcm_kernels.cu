@@ -22,6 +22,7 @@
 
 #include "kcm_common.cuh"
 #include "kcm_device.h"
+#include "kcm_launch.h"
 
 namespace kcm {
 
@@ -36,6 +37,7 @@ using namespace dev;
 // lanes that share a cell. Ranks depend on timing; nothing downstream depends on the order.
 static_assert(kBinThreads == 1024, "the fused scan of k_bin_count scans 32 warp totals in one warp");
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
+    grid_dep_sync();
     __shared__ int ws[kBinThreads / 32];
     __shared__ bool last;
     if (d.status->done) return;
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
 // then each block adds the sums of the blocks before it and scans its own cells (and zeroes the
 // counts for the next iteration)
 __global__ void k_scan_sums(const DevChain d) {
+    grid_dep_sync();
     __shared__ int ws[32];
     if (d.status->done) return;
     int nc = d.status->ncells;
@@ -145,6 +148,7 @@ __global__ void k_scan_sums(const DevChain d) {
 }
 
 __global__ void k_scan_cells(const DevChain d) {
+    grid_dep_sync();
     __shared__ int ws[32];
     __shared__ int base_s;
     if (d.status->done) return;
@@ -214,6 +218,7 @@ __global__ void k_scan_cells(const DevChain d) {
 // from run to run.
 template <bool MIXED>
 __global__ void k_bin_place(const DevChain d) {
+    grid_dep_sync();
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= d.n || d.status->done) return;
     int key = d.key[a];
@@ -249,6 +254,7 @@ __global__ void k_bin_place(const DevChain d) {
 // FP64 mode: the atoms of each cell in atom order (a stable counting sort): the atom at slot s of the
 // placement by atomic ranks takes slot (cell start) + (atoms of its cell with a smaller index)
 __global__ void k_bin_stable(const DevChain d) {
+    grid_dep_sync();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= d.n || d.status->done) return;
     const int a = d.sorted_tmp[s];
@@ -288,6 +294,7 @@ __global__ void k_bin_stable(const DevChain d) {
 // spend a whole FP64 warp instruction on each atom's lane 0).
 template <bool MIXED, int KR, int W>
 __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const DevChain d) {
+    grid_dep_sync();
     typedef typename std::conditional<MIXED, float, double>::type R;
     typedef typename std::conditional<MIXED, float4, dbl4>::type QV;
     constexpr int kW = 2 * KR + 1;  // cells per row
@@ -670,6 +677,7 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
 // shared memory; the force quantum G0_i / (N dr) is applied in fixed point, so
 // F_j += q c_js and F_i -= q c_js are exact integer additions.
 __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
+    grid_dep_sync();
     __shared__ int s_idx[kSasaWarps][kSasaStage];
     __shared__ int s_cnt[kSasaWarps][3 * kSasaStage];
     __shared__ dbl4 s_pos[kSasaWarps][kSasaStage];
@@ -754,6 +762,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa(const DevChain d) {
 // once. It runs beside k_sasa (a second stream), which skips these atoms; a warp per atom of the list
 // the pair kernel recorded (none, mostly: the kernel then returns at once).
 __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_long(const DevChain d) {
+    grid_dep_sync();
     const int lane = threadIdx.x & 31;
     if (d.status->done) return;
     const int nlong = d.status->nlong;
@@ -851,6 +860,7 @@ __device__ __forceinline__ float fmax3f(float a, float b, float c) {
 
 template <int W>
 __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
+    grid_dep_sync();
     __shared__ float4 s_o[W][kSasaStage];   // o_j, h_j
     __shared__ int s_idx[W][kSasaStage];
     __shared__ int s_cnt[W][3 * kSasaStage];
@@ -1018,6 +1028,7 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
 // k_sasa_mixed (a second stream), which skips these atoms; a warp per atom of the list the pair
 // kernel recorded (none, mostly: the kernel then returns at once).
 __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed_long(const DevChain d) {
+    grid_dep_sync();
     __shared__ unsigned short s_near[kSasaWarps][kBatch];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (d.status->done) return;
@@ -1181,6 +1192,7 @@ __global__ void __launch_bounds__(kSasaWarps * 32) k_sasa_mixed_long(const DevCh
 // d < Roff_i + Roff_j re-decided in FP64 inside the guard band (the force jumps there).
 template <bool MIXED, int W>
 __global__ void __launch_bounds__(W * 32) k_sasa_pw(const DevChain d) {
+    grid_dep_sync();
     typedef typename std::conditional<MIXED, float, double>::type R;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * W + w;
@@ -1286,6 +1298,7 @@ __global__ void __launch_bounds__(W * 32) k_sasa_pw(const DevChain d) {
 
 // loop state of a batch; with full, also the statistics and the chains' bounding boxes
 __global__ void k_reset_loop(const DevChain d, int full) {
+    grid_dep_sync();
     Status* st = d.status;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c == 0) {
@@ -1316,6 +1329,7 @@ __global__ void k_reset_loop(const DevChain d, int full) {
 }
 
 __global__ void k_force_out(const DevChain d) {
+    grid_dep_sync();
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= 3 * d.n) return;
     double fc = d.prm.solvation ? (double)d.Fcav[x] * kFxInv : 0.0;
@@ -1328,24 +1342,24 @@ inline int blocks(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 
 }  // namespace
 
-void launch_init_status(DevChain& d, cudaStream_t s) { k_reset_loop<<<blocks(d.nchains, 256), 256, 0, s>>>(d, 1); }
-void launch_reset_loop(DevChain& d, cudaStream_t s) { k_reset_loop<<<blocks(d.nchains, 256), 256, 0, s>>>(d, 0); }
+void launch_init_status(DevChain& d, cudaStream_t s) { launch_k(k_reset_loop, blocks(d.nchains, 256), 256, 0, s, d.pdl, d, 1); }
+void launch_reset_loop(DevChain& d, cudaStream_t s) { launch_k(k_reset_loop, blocks(d.nchains, 256), 256, 0, s, d.pdl, d, 0); }
 
 void launch_binning(DevChain& d, cudaStream_t s) {
     if (d.bin_c) {  // a single chain in mixed mode: one cluster
         launch_bin_cluster(d, s);
         return;
     }
-    k_bin_count<<<blocks(d.n, kBinThreads), kBinThreads, 0, s>>>(d);
+    launch_k(k_bin_count, blocks(d.n, kBinThreads), kBinThreads, 0, s, d.pdl, d);
     if (!d.scan_fused) {
-        k_scan_sums<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
-        k_scan_cells<<<d.scan_blocks, kScanThreadsBig, 0, s>>>(d);
+        launch_k(k_scan_sums, d.scan_blocks, kScanThreadsBig, 0, s, d.pdl, d);
+        launch_k(k_scan_cells, d.scan_blocks, kScanThreadsBig, 0, s, d.pdl, d);
     }
     if (d.prm.precision == KCM_MIXED) {
-        k_bin_place<true><<<blocks(d.n, 256), 256, 0, s>>>(d);
+        launch_k(k_bin_place<true>, blocks(d.n, 256), 256, 0, s, d.pdl, d);
     } else {
-        k_bin_place<false><<<blocks(d.n, 256), 256, 0, s>>>(d);
-        k_bin_stable<<<blocks(d.n, 256), 256, 0, s>>>(d);
+        launch_k(k_bin_place<false>, blocks(d.n, 256), 256, 0, s, d.pdl, d);
+        launch_k(k_bin_stable, blocks(d.n, 256), 256, 0, s, d.pdl, d);
     }
 }
 
@@ -1355,11 +1369,11 @@ void launch_pairs_w(DevChain& d, cudaStream_t s) {
     int nb = (d.n + W - 1) / W;
     if (d.pair_grid_cap > 0) nb = std::min(nb, d.pair_grid_cap);  // persistent grid
     if (d.stencil == 2) {
-        if (mixed) k_pair<true, 2, W><<<nb, W * 32, 0, s>>>(d);
-        else k_pair<false, 2, W><<<nb, W * 32, 0, s>>>(d);
+        if (mixed) launch_k(k_pair<true, 2, W>, nb, W * 32, 0, s, d.pdl, d);
+        else launch_k(k_pair<false, 2, W>, nb, W * 32, 0, s, d.pdl, d);
     } else {
-        if (mixed) k_pair<true, 1, W><<<nb, W * 32, 0, s>>>(d);
-        else k_pair<false, 1, W><<<nb, W * 32, 0, s>>>(d);
+        if (mixed) launch_k(k_pair<true, 1, W>, nb, W * 32, 0, s, d.pdl, d);
+        else launch_k(k_pair<false, 1, W>, nb, W * 32, 0, s, d.pdl, d);
     }
 }
 
@@ -1406,23 +1420,23 @@ void launch_sasa(DevChain& d, cudaStream_t s) {
         const int W = d.sasa_warps;
         const int nb = (d.n + W - 1) / W;
         if (d.prm.precision == KCM_MIXED) {
-            if (W == 1) k_sasa_pw<true, 1><<<nb, 32, 0, s>>>(d);
-            else if (W == 2) k_sasa_pw<true, 2><<<nb, 64, 0, s>>>(d);
-            else k_sasa_pw<true, 4><<<nb, 128, 0, s>>>(d);
+            if (W == 1) launch_k(k_sasa_pw<true, 1>, nb, 32, 0, s, d.pdl, d);
+            else if (W == 2) launch_k(k_sasa_pw<true, 2>, nb, 64, 0, s, d.pdl, d);
+            else launch_k(k_sasa_pw<true, 4>, nb, 128, 0, s, d.pdl, d);
         } else {
-            if (W == 1) k_sasa_pw<false, 1><<<nb, 32, 0, s>>>(d);
-            else if (W == 2) k_sasa_pw<false, 2><<<nb, 64, 0, s>>>(d);
-            else k_sasa_pw<false, 4><<<nb, 128, 0, s>>>(d);
+            if (W == 1) launch_k(k_sasa_pw<false, 1>, nb, 32, 0, s, d.pdl, d);
+            else if (W == 2) launch_k(k_sasa_pw<false, 2>, nb, 64, 0, s, d.pdl, d);
+            else launch_k(k_sasa_pw<false, 4>, nb, 128, 0, s, d.pdl, d);
         }
     } else if (d.prm.solvation) {
         if (d.prm.precision == KCM_MIXED) {  // sasa_warps atoms per block (a tile shape of kTileWarps)
             const int W = d.sasa_warps;
             const int nb = (d.n + W - 1) / W;
-            if (W == 1) k_sasa_mixed<1><<<nb, 32, 0, s>>>(d);
-            else if (W == 2) k_sasa_mixed<2><<<nb, 64, 0, s>>>(d);
-            else k_sasa_mixed<4><<<nb, 128, 0, s>>>(d);
+            if (W == 1) launch_k(k_sasa_mixed<1>, nb, 32, 0, s, d.pdl, d);
+            else if (W == 2) launch_k(k_sasa_mixed<2>, nb, 64, 0, s, d.pdl, d);
+            else launch_k(k_sasa_mixed<4>, nb, 128, 0, s, d.pdl, d);
         } else {
-            k_sasa<<<nb4, kSasaWarps * 32, 0, s>>>(d);
+            launch_k(k_sasa, nb4, kSasaWarps * 32, 0, s, d.pdl, d);
         }
     }
 }
@@ -1430,10 +1444,10 @@ void launch_sasa(DevChain& d, cudaStream_t s) {
 void launch_sasa_long(DevChain& d, cudaStream_t s) {
     if (d.prm.solvation != 1) return;
     const int nb = std::max(1, std::min((d.n + kSasaWarps - 1) / kSasaWarps, kSasaLongBlocks));
-    if (d.prm.precision == KCM_MIXED) k_sasa_mixed_long<<<nb, kSasaWarps * 32, 0, s>>>(d);
-    else k_sasa_long<<<nb, kSasaWarps * 32, 0, s>>>(d);
+    if (d.prm.precision == KCM_MIXED) launch_k(k_sasa_mixed_long, nb, kSasaWarps * 32, 0, s, d.pdl, d);
+    else launch_k(k_sasa_long, nb, kSasaWarps * 32, 0, s, d.pdl, d);
 }
 
-void launch_force_out(DevChain& d, cudaStream_t s) { k_force_out<<<blocks(3LL * d.n, 256), 256, 0, s>>>(d); }
+void launch_force_out(DevChain& d, cudaStream_t s) { launch_k(k_force_out, blocks(3LL * d.n, 256), 256, 0, s, d.pdl, d); }
 
 }  // namespace kcm

@@ -25,6 +25,7 @@
 
 #include "kcm_common.cuh"
 #include "kcm_device.h"
+#include "kcm_launch.h"
 
 namespace kcm {
 
@@ -67,6 +68,7 @@ struct PtSmem {
 // shorter warps for small workloads; chosen by the tile autotuner)
 template <int KR, int SPLIT>
 __global__ void __launch_bounds__(kPtWarps * 32, KCM_PT_MIN_BLOCKS) k_pair_tile(const DevChain d) {
+    grid_dep_sync();
     constexpr int kW = 2 * KR + 1;
     constexpr int kRows = 1 + KR + KR * kW;  // rows of the half stencil
     __shared__ PtSmem smem[kPtWarps];
@@ -459,9 +461,9 @@ void launch_pairs_tile_kr(DevChain& d, cudaStream_t s) {
     const int split = d.pair_warps;  // the tile autotuner's pair shape
     const long long warps = (long long)((d.n + 31) / 32) * pair_tile_rows(d.stencil) * split;
     const int nb = (int)((warps + kPtWarps - 1) / kPtWarps);
-    if (split == 1) k_pair_tile<KR, 1><<<nb, kPtWarps * 32, 0, s>>>(d);
-    else if (split == 2) k_pair_tile<KR, 2><<<nb, kPtWarps * 32, 0, s>>>(d);
-    else k_pair_tile<KR, 4><<<nb, kPtWarps * 32, 0, s>>>(d);
+    if (split == 1) launch_k(k_pair_tile<KR, 1>, nb, kPtWarps * 32, 0, s, d.pdl, d);
+    else if (split == 2) launch_k(k_pair_tile<KR, 2>, nb, kPtWarps * 32, 0, s, d.pdl, d);
+    else launch_k(k_pair_tile<KR, 4>, nb, kPtWarps * 32, 0, s, d.pdl, d);
 }
 
 void launch_pairs_tile(DevChain& d, cudaStream_t s) {

@@ -22,6 +22,7 @@
 #include "kcm_common.cuh"
 #include "kcm_df.cuh"
 #include "kcm_device.h"
+#include "kcm_launch.h"
 
 namespace kcm {
 
@@ -152,6 +153,7 @@ __device__ __forceinline__ void reverse_scan32(T& x, bool& tl, int lane) {
 // (side-chain joints from their branch sums). The last block to finish closes the iteration.
 template <class T, bool SIDE, bool STEP>
 __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_step(const DevChain d) {
+    grid_dep_sync();
     constexpr bool DF = std::is_same<T, df>::value;
     __shared__ T sV[kWrenchTileAtoms][6];
     __shared__ T sP[32][6];  // link wrenches, then their in-tile suffix sums
@@ -468,6 +470,7 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_step(const DevChai
 // the paper's normalised step (eq. KCM_07): dtheta_k = kappa tau_k / max |tau| over the free joints of
 // the joint's chain, main and side (a fixed joint takes none)
 __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
+    grid_dep_sync();
     __shared__ bool last;
     Status* st = d.status;
     if (st->done) return;
@@ -500,8 +503,8 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
 
 template <class T, bool STEP>
 void launch_wrench_step(DevChain& d, cudaStream_t s) {
-    if (d.ls) k_wrench_step<T, true, STEP><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
-    else k_wrench_step<T, false, STEP><<<d.ltiles, kWrenchWarps * 32, 0, s>>>(d);
+    if (d.ls) launch_k(k_wrench_step<T, true, STEP>, d.ltiles, kWrenchWarps * 32, 0, s, d.pdl, d);
+    else launch_k(k_wrench_step<T, false, STEP>, d.ltiles, kWrenchWarps * 32, 0, s, d.pdl, d);
 }
 
 void launch_torques(DevChain& d, cudaStream_t s) {
@@ -515,7 +518,7 @@ void launch_torques_step_t(DevChain& d, cudaStream_t s) {
         launch_wrench_step<T, true>(d, s);
     } else {
         launch_wrench_step<T, false>(d, s);
-        k_step_normalized<<<(d.l + d.ls + 127) / 128, 128, 0, s>>>(d);
+        launch_k(k_step_normalized, (d.l + d.ls + 127) / 128, 128, 0, s, d.pdl, d);
     }
 }
 
