@@ -51,9 +51,15 @@ BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques_step": 60}  # algori
 # left out has no capture of its current kernel
 DRAM_BYTES_PER_LAUNCH = {"solvation": 6.84e6}
 MIXED_DTYPE = "f32 pair/solvation; double-float (~48-bit) kinematics, wrenches and torque scans"
-# launches of one mixed-precision iteration with solvation on: reset + kinematics 2 + binning 2 + pairs 1 +
-# solvation 2 (the main kernel and the long-list kernel beside it) + wrenches, torques and step 1
-KERNELS_PER_ITERATION = 9
+
+
+def kernels_per_iteration(binning_kind):
+    """Launches of one mixed-precision iteration of a single chain with solvation on: reset + kinematics 2
+    + binning (1 with the cluster kernel, 2 with the count and placement kernels) + pairs 1 + solvation 2
+    (the main kernel and the long-list kernel beside it) + wrenches, torques and step 1."""
+    from paper_1712_05012_b300 import kcm
+
+    return 1 + 2 + (1 if binning_kind == kcm.BIN_CLUSTER else 2) + 1 + 2 + 1
 
 
 def parse():
@@ -420,9 +426,11 @@ def run_ours(args):
     # start conformation, before the warm-up
     prepare(ch, lib_stream)
     kind, kind_ms = ch.autotune_pair_kernel(reps=10)
+    bin_kind, bin_ctas = ch.get_binning_kernel()
     tiles = {"used": list(ch.get_tiles()), "choices": list(kcm.TILE_CHOICES), "source": "autotuner",
              "pair_kernel": ("cell_tiles" if kind == kcm.PAIR_CELL_TILES else "warp_per_atom"),
-             "pair_kernel_ms": {"warp_per_atom": float(kind_ms[0]), "cell_tiles": float(kind_ms[1])}}
+             "pair_kernel_ms": {"warp_per_atom": float(kind_ms[0]), "cell_tiles": float(kind_ms[1])},
+             "binning_kernel": {"kind": "cluster" if bin_kind == kcm.BIN_CLUSTER else "blocks", "ctas": bin_ctas}}
     # the torques at the start conformation, compared with the oracle's in the oracle leg
     prepare(ch, lib_stream)
     tau_start = ch.torques()
@@ -694,7 +702,7 @@ def run_ours(args):
                 "fp64_value": fp64_value, "surrogate_value": surrogate_value, "side_joints_value": side_value,
                 "vacuum_value": vacuum_value, "tiles": tiles, "chain8000": chain8000, "batch": batch, "serving": serving,
                 "speedup_vs_fp64": (value / ws / fp64_value) if fp64_value else None,
-                "cpu_baseline": cpu, "accuracy": accuracy, "e2e": e2e, "gpu_launches": KERNELS_PER_ITERATION * args.steps,
+                "cpu_baseline": cpu, "accuracy": accuracy, "e2e": e2e, "gpu_launches": kernels_per_iteration(bin_kind) * args.steps,
                 "clocks": clk, "stats": {k: stats[k] for k in ("pairs", "sasa_tests", "sasa_neighbors",
                                                                  "max_neighbors", "guard_rechecks", "cells")},
                 "cell_size": stats["cell_size"]}
