@@ -877,6 +877,7 @@ int kcm_positions(kcm_handle h, double* xyz, int64_t n) {
     if (!xyz || n != h->d.n) return set_err(h, KCM_E_INVAL, "n must equal the atom count");
     kcm::launch_reset_loop(h->d, h->stream);
     kcm::launch_fk(h->d, h->stream);
+    kcm::launch_centres64(h->d, h->stream);
     cudaError_t e = cudaMemcpyAsync(xyz, h->d.r, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "positions copy");
     return sync(h);

@@ -18,16 +18,15 @@
 //
 // The cell of an atom and its offset from the cell corner are formed in double-float from the
 // double-float centre (the grid origin, the box minimum, is an exact double-float: it is one of the
-// centres) and rounded once to float; the multi-block kernels round the FP64 difference instead, so a
-// cell assignment or an offset can differ by one float rounding, which the cell margin absorbs. On
-// B300 an FP64 warp instruction holds a sub-partition's FP64 pipe for ~84 cycles, and a cluster has
-// 16 SMs: the double-float form keeps the per-atom work on the FP32 pipe.
+// centres) and rounded once to float, as the multi-block kernels do in mixed mode (mixed_cell,
+// mixed_offset): the two give the same cells and offsets.
 #include <cuda_runtime.h>
 
 #include <cooperative_groups.h>
 
 #include <algorithm>
 
+#include "kcm_cells.cuh"
 #include "kcm_common.cuh"
 #include "kcm_df.cuh"
 #include "kcm_device.h"
@@ -53,20 +52,17 @@ __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
     __shared__ int sWs[kBcWarps];
     __shared__ int sRange;  // atoms in the CTA's cells (read by every CTA)
     __shared__ int sOff[kBcMaxCtas + 1];
-    __shared__ df sOrg[3];
+
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), b = (int)cl.block_rank();
     if (d.status->done) return;  // the same for every CTA: nothing writes it while the kernel runs
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < d.bin_capc / 4; i += blockDim.x) sCell4[i] = make_int4(0, 0, 0, 0);
     const GridInfo g = d.grid[0];
-    if (threadIdx.x < 3)  // the grid origin, exact as a double-float (a centre)
-        sOrg[threadIdx.x] = df_from(threadIdx.x == 0 ? g.ox : threadIdx.x == 1 ? g.oy : g.oz);
     const int nc = g.ncells, per = (nc + C - 1) / C;
     const int a0 = (int)((long long)d.n * b / C), a1 = (int)((long long)d.n * (b + 1) / C);  // <= kBcAtoms each
     const df* rdf = reinterpret_cast<const df*>(d.rdf);
     cl.sync();  // (1) every CTA's counts are zero
-    const df ox = sOrg[0], oy = sOrg[1], oz = sOrg[2];
 
     // ---- cell counts
     int key0[kBcAtoms], rank0[kBcAtoms];
@@ -77,9 +73,9 @@ __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
             const int at = a0 + k * kBcThreads + (int)threadIdx.x;
             if (at >= a1) continue;
             const df px = rdf[3 * at], py = rdf[3 * at + 1], pz = rdf[3 * at + 2];
-            const int cx = min(max((int)floorf(sub(px, ox).hi * g.inv_sf), 0), g.nx - 1);
-            const int cy = min(max((int)floorf(sub(py, oy).hi * g.inv_sf), 0), g.ny - 1);
-            const int cz = min(max((int)floorf(sub(pz, oz).hi * g.inv_sf), 0), g.nz - 1);
+            const int cx = mixed_cell_axis(px, g.of[0], g.inv_sf, g.nx);
+            const int cy = mixed_cell_axis(py, g.of[1], g.inv_sf, g.ny);
+            const int cz = mixed_cell_axis(pz, g.of[2], g.inv_sf, g.nz);
             const int key = (cz * g.ny + cy) * g.nx + cx;
             const int owner = key / per;
             const unsigned peers = __match_any_sync(__activemask(), key);
@@ -142,7 +138,6 @@ __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
 
     // ---- the atoms in slot order (as k_bin_place; the offsets from the cell corner in double-float, the
     // corner's multiple of the edge exact as a product of two floats)
-    const df sf = df_from(g.sf);
     {
 #pragma unroll
         for (int k = 0; k < kBcAtoms; ++k) {
@@ -160,9 +155,9 @@ __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
             d.Fov[3 * at] = 0.0f; d.Fov[3 * at + 1] = 0.0f; d.Fov[3 * at + 2] = 0.0f;
             d.nbr_cnt[at] = 0;
             const int cx = key % g.nx, cy = (key / g.nx) % g.ny, cz = key / (g.nx * g.ny);
-            const float fx = sub(sub(px, ox), mul(df_from((float)cx), sf)).hi;
-            const float fy = sub(sub(py, oy), mul(df_from((float)cy), sf)).hi;
-            const float fz = sub(sub(pz, oz), mul(df_from((float)cz), sf)).hi;
+            const float fx = mixed_offset(px, g.of[0], cx, g.sf);
+            const float fy = mixed_offset(py, g.of[1], cy, g.sf);
+            const float fz = mixed_offset(pz, g.of[2], cz, g.sf);
             d.spos32[sl] = make_float4(fx, fy, fz, (float)cx);
             d.sprm32[sl] = d.aprm32[at];
         }

@@ -222,6 +222,11 @@ __device__ __forceinline__ bool grid_from_bounds(const DevChain& d, double* lo, 
         s = ceil(s * 1.25 * 1024.0) * (1.0 / 1024.0);
     }
     g.ox = lo[0]; g.oy = lo[1]; g.oz = lo[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {  // hi + lo of each coordinate of the origin (as df_from(double))
+        const float h = __double2float_rn(lo[i]);
+        g.of[i] = make_float2(h, __double2float_rn(__dsub_rn(lo[i], (double)h)));
+    }
     g.s = s;
     g.sf = (float)s;
     g.gpf = (float)(1e-3 + 2e-4 * s);

@@ -26,6 +26,7 @@ struct GridInfo {
     int ncells;
     int cbase;
     int pad;
+    float2 of[3];       // mixed mode: the origin as double-floats (hi, lo); exact, the origin being a centre
 };
 
 // Error bits in Status::error.
@@ -153,7 +154,7 @@ struct DevChain {
     double* pcur = nullptr;        // current axis points [l*3]
     double* ucurdf = nullptr;      // mixed mode: the same as double-float pairs [l*3]
     double* pcurdf = nullptr;      // [l*3]
-    double* r = nullptr;           // centres [n*3]
+    double* r = nullptr;           // centres [n*3] (mixed mode: formed on request from rdf)
     double* rdf = nullptr;         // mixed mode: centres as double-float pairs [n*3]
     int* key = nullptr;            // cell of each atom [n]
     int* cell_count = nullptr;     // [cell_cap]
@@ -223,6 +224,8 @@ struct DevChain {
 void launch_init_status(DevChain& d, cudaStream_t s);
 void launch_reset_loop(DevChain& d, cudaStream_t s);
 void launch_fk(DevChain& d, cudaStream_t s);
+// the FP64 centres r from the double-float ones (mixed mode keeps only those); nothing in FP64 mode
+void launch_centres64(DevChain& d, cudaStream_t s);
 void launch_binning(DevChain& d, cudaStream_t s);  // with bin_c: k_bin_cluster
 void launch_bin_cluster(DevChain& d, cudaStream_t s);  // kcm_bin_cluster.cu
 // the cluster shape of k_bin_cluster for the chain and its cell cap (bin_c, bin_capc; bin_c = 0 when not

@@ -41,6 +41,34 @@ constexpr int kFkQuads = 8 * kFkWarps;    // quads (transform slots) per block
 constexpr int kFkMaxTiles = 40 * kFkQuads;  // most scan blocks (k_fk_tiles' quads run through up to 20 products each)
 constexpr int kFkTreeTiles = 2 * kFkQuads;  // up to this many, every apply block reduces the earlier products itself
 
+// the grid of chain c from its box keys (chain_grid; mixed mode: keys of double-float pairs)
+template <class T>
+__device__ __forceinline__ bool chain_grid_t(const DevChain& d, int c, GridInfo* out) {
+    if constexpr (std::is_same<T, double>::value) {
+        return chain_grid(d, c, out);
+    } else {
+        unsigned long long kb[6];  // every load before the first store
+#pragma unroll
+        for (int i = 0; i < 6; ++i) kb[i] = __ldcg(&d.cbox[6 * c + i]);
+        double lo[3], hi[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            lo[i] = to_double(dfkey_inv(kb[i]));
+            hi[i] = to_double(dfkey_inv(kb[3 + i]));
+            d.cbox[6 * c + i] = ~0ULL;
+            d.cbox[6 * c + 3 + i] = 0ULL;
+        }
+        return grid_from_bounds(d, lo, hi, d.ccap[c], out);
+    }
+}
+
+// FP64 centres from the double-float ones (mixed mode keeps only those), for the callers that read them
+__global__ void k_centres64(const DevChain d) {
+    grid_dep_sync();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < 3 * d.n) d.r[x] = centre64(d, x / 3, x % 3);
+}
+
 // row rr of the identity
 template <class T>
 __device__ __forceinline__ void row_identity(int rr, T* a) {
@@ -554,12 +582,15 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
                 row_compose(bE, Gj, Ma);
             }
             if ((lane & 3) < 3) {
-                const double* u = &d.u0[3 * j];
-                const T uc = fma(Ma[2], num<T>(u[2]), fma(Ma[1], num<T>(u[1]), mul(Ma[0], num<T>(u[0]))));
-                d.ucur[3 * j + rr] = to_double(uc);
+                // mixed mode keeps the axes and axis points as double-floats only (the torque kernel's
+                // form): no FP64 conversion per joint
+                const T* u = reinterpret_cast<const T*>(std::is_same<T, double>::value ? d.u0 : d.u0df) + 3 * j;
+                const T uc = fma(Ma[2], u[2], fma(Ma[1], u[1], mul(Ma[0], u[0])));
                 store_row(&M[12 * ((size_t)j + joint_chain(d, j) + 1)], rr, Ma);
-                d.pcur[3 * j + rr] = to_double(Ma[3]);
-                if constexpr (!std::is_same<T, double>::value) {  // for the double-float torque kernel
+                if constexpr (std::is_same<T, double>::value) {
+                    d.ucur[3 * j + rr] = uc;
+                    d.pcur[3 * j + rr] = Ma[3];
+                } else {
                     reinterpret_cast<T*>(d.ucurdf)[3 * j + rr] = uc;
                     reinterpret_cast<T*>(d.pcurdf)[3 * j + rr] = Ma[3];
                 }
@@ -589,10 +620,16 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const T vt = fma(Ml[3 * i + 2], z, fma(Ml[3 * i + 1], y, fma(Ml[3 * i], x, Ml[9 + i])));
-            const double v = to_double(vt);
-            d.r[3 * a + i] = v;
-            if constexpr (!std::is_same<T, double>::value) reinterpret_cast<T*>(d.rdf)[3 * a + i] = vt;
-            const unsigned long long key = dkey(v);  // bounding box as order-preserving integer keys
+            // bounding box as order-preserving integer keys; mixed mode keeps the centres as double-floats
+            // only, keyed as pairs (no FP64 conversion per atom; FP64 centres are formed on request)
+            unsigned long long key;
+            if constexpr (std::is_same<T, double>::value) {
+                d.r[3 * a + i] = vt;
+                key = dkey(vt);
+            } else {
+                reinterpret_cast<T*>(d.rdf)[3 * a + i] = vt;
+                key = dfkey(vt);
+            }
             mn[i] = min(mn[i], key);
             mx[i] = max(mx[i], key);
         }
@@ -653,7 +690,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
         GridInfo g;
         int ncl = 0;
         if (cch < d.nchains) {
-            if (!chain_grid(d, cch, &g)) {  // non-finite centres: the chain fails (alone, in a batch)
+            if (!chain_grid_t<T>(d, cch, &g)) {  // non-finite centres: the chain fails (alone, in a batch)
                 bad = true;
                 d.chain_err[cch] |= kErrNonfinite;
                 d.chain_done[cch] = 1;
@@ -721,6 +758,10 @@ int fk_joints_per_lane(int l) {
 }
 
 int fk_block_joints() { return kFkQuads; }
+
+void launch_centres64(DevChain& d, cudaStream_t s) {
+    if (d.prm.precision == KCM_MIXED && d.n > 0) launch_k(k_centres64, (3 * d.n + 255) / 256, 256, 0, s, d.pdl, d);
+}
 
 void launch_fk(DevChain& d, cudaStream_t s) {
     switch (d.fk_j) {

@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <type_traits>
 
+#include "kcm_cells.cuh"
 #include "kcm_common.cuh"
 #include "kcm_device.h"
 #include "kcm_launch.h"
@@ -45,9 +46,17 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const DevChain d) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (a < d.n) {
         const GridInfo g = d.grid[atom_chain(d, a)];
-        int cx = min(max((int)floorf((float)(d.r[3 * a] - g.ox) * g.inv_sf), 0), g.nx - 1);
-        int cy = min(max((int)floorf((float)(d.r[3 * a + 1] - g.oy) * g.inv_sf), 0), g.ny - 1);
-        int cz = min(max((int)floorf((float)(d.r[3 * a + 2] - g.oz) * g.inv_sf), 0), g.nz - 1);
+        int cx, cy, cz;
+        if (d.prm.precision == KCM_MIXED) {  // from the double-float centres, no FP64 (kcm_cells.cuh)
+            const df* p = reinterpret_cast<const df*>(d.rdf) + 3 * a;
+            cx = mixed_cell_axis(p[0], g.of[0], g.inv_sf, g.nx);
+            cy = mixed_cell_axis(p[1], g.of[1], g.inv_sf, g.ny);
+            cz = mixed_cell_axis(p[2], g.of[2], g.inv_sf, g.nz);
+        } else {
+            cx = min(max((int)floorf((float)(d.r[3 * a] - g.ox) * g.inv_sf), 0), g.nx - 1);
+            cy = min(max((int)floorf((float)(d.r[3 * a + 1] - g.oy) * g.inv_sf), 0), g.ny - 1);
+            cz = min(max((int)floorf((float)(d.r[3 * a + 2] - g.oz) * g.inv_sf), 0), g.nz - 1);
+        }
         int key = g.cbase + (cz * g.ny + cy) * g.nx + cx;
         d.key[a] = key;
         unsigned peers = __match_any_sync(__activemask(), key);
@@ -234,7 +243,6 @@ __global__ void k_bin_place(const DevChain d) {
     d.sorted[sl] = a;
     d.slot_cell[sl] = key;
     d.smask[sl] = make_ulonglong2(d.exm[a], d.m14m[a]);  // bond classes in slot order (no dependent load later)
-    double x = d.r[3 * a], y = d.r[3 * a + 1], z = d.r[3 * a + 2];
     if (MIXED) {
         // the pair kernel adds each pair's share to both atoms: zero the sums and the list counters
         d.Fpx[3 * a] = 0; d.Fpx[3 * a + 1] = 0; d.Fpx[3 * a + 2] = 0;
@@ -242,9 +250,10 @@ __global__ void k_bin_place(const DevChain d) {
         d.nbr_cnt[a] = 0;
         const int lk = key - g.cbase;
         int cx = lk % g.nx, cy = (lk / g.nx) % g.ny, cz = lk / (g.nx * g.ny);
-        float ox = (float)(x - (g.ox + cx * g.s));
-        float oy = (float)(y - (g.oy + cy * g.s));
-        float oz = (float)(z - (g.oz + cz * g.s));
+        const df* pc = reinterpret_cast<const df*>(d.rdf) + 3 * a;  // no FP64 (kcm_cells.cuh)
+        const float ox = mixed_offset(pc[0], g.of[0], cx, g.sf);
+        const float oy = mixed_offset(pc[1], g.of[1], cy, g.sf);
+        const float oz = mixed_offset(pc[2], g.of[2], cz, g.sf);
         float4 p = d.aprm32[a];
         d.spos32[sl] = make_float4(ox, oy, oz, (float)cx);  // w: the cell's x index (exact), for the pair shifts
         d.sprm32[sl] = p;
