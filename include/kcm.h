@@ -429,6 +429,16 @@ int kcm_get_pair_kernel(kcm_handle h, int32_t* kind);
  * kcm_autotune_tiles (the previous kernel is then restored). */
 int kcm_autotune_pair_kernel(kcm_handle h, int32_t reps, double* times_ms, int32_t* kind);
 
+/* Launch overlap in the captured step graphs (on = 1, the default): every kernel of an iteration is
+ * launched with programmatic stream serialization and begins by waiting for the previous kernel to
+ * complete (griddepcontrol.wait), so that each kernel's launch overlaps the previous one's run; results
+ * are unchanged. Worth it when the handle has the GPU to itself (1,000-residue chain: 102.6 -> 101.0 us
+ * per iteration); for handles that share the GPU with other streams' kernels it costs more than it saves
+ * (the next kernel's blocks hold SM slots while they wait: the serving loop's p50 latency 0.13-0.15 s
+ * without, 0.20-0.25 s with), and the serving loop turns it off for its batches. Synchronises and drops
+ * the captured graphs. Errors: KCM_E_INVAL (on not 0 or 1). */
+int kcm_set_graph_overlap(kcm_handle h, int32_t on);
+
 /* Binning kernel (A2, Sec. 3.2: cell counts, their scan, the atoms in slot order). KCM_BIN_CLUSTER (the
  * default): a single chain of up to 32,768 atoms in mixed precision is binned in one launch of one
  * thread-block cluster of up to 16 CTAs, the cell counts kept in the CTAs' shared memory (atomics through distributed shared

@@ -1116,6 +1116,16 @@ int kcm_set_test_withhold(kcm_handle h, int32_t tile) {
     return KCM_OK;
 }
 
+int kcm_set_graph_overlap(kcm_handle h, int32_t on) {
+    if (check_handle(h)) return KCM_E_INVAL;
+    if (on != 0 && on != 1) return set_err(h, KCM_E_INVAL, "on must be 0 or 1");
+    int rc = sync(h);  // no launch of the old graphs is pending when they go
+    if (rc) return rc;
+    drop_graphs(h);
+    h->pdl = on != 0;
+    return KCM_OK;
+}
+
 int kcm_set_binning_kernel(kcm_handle h, int32_t kind) {
     if (check_handle(h)) return KCM_E_INVAL;
     if (kind != KCM_BIN_BLOCKS && kind != KCM_BIN_CLUSTER)

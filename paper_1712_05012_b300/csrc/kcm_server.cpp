@@ -244,6 +244,8 @@ Made make_batch(int device, std::vector<kcm_topology> tops, kcm_params prm) {
         return m;
     }
     m.rc = kcm_create_batch(tops.data(), static_cast<int32_t>(tops.size()), &prm, m.stream, &m.h);
+    // batches run beside each other on their own streams: no launch overlap (kcm_set_graph_overlap)
+    if (m.rc == KCM_OK) m.rc = kcm_set_graph_overlap(m.h, 0);
     return m;
 }
 

@@ -81,7 +81,7 @@ EXPORTS = [
     "kcm_side_offsets", "kcm_set_side_theta_dev", "kcm_get_side_theta_dev", "kcm_step_host",
     "kcm_set_tiles", "kcm_get_tiles", "kcm_autotune_tiles", "kcm_server_set_admission",
     "kcm_set_pair_kernel", "kcm_get_pair_kernel", "kcm_autotune_pair_kernel", "kcm_server_cancel",
-    "kcm_set_test_withhold", "kcm_set_binning_kernel", "kcm_get_binning_kernel",
+    "kcm_set_test_withhold", "kcm_set_binning_kernel", "kcm_get_binning_kernel", "kcm_set_graph_overlap",
 ]
 PAIR_WARP_PER_ATOM, PAIR_CELL_TILES = 0, 1
 BIN_BLOCKS, BIN_CLUSTER = 0, 1
@@ -139,6 +139,7 @@ def load():
             "kcm_autotune_pair_kernel": (C.c_int, [h, C.c_int32, _dp, _ip]),
             "kcm_set_test_withhold": (C.c_int, [h, C.c_int32]),
             "kcm_set_binning_kernel": (C.c_int, [h, C.c_int32]),
+            "kcm_set_graph_overlap": (C.c_int, [h, C.c_int32]),
             "kcm_get_binning_kernel": (C.c_int, [h, _ip, _ip]),
             "kcm_set_fixed_joints": (C.c_int, [h, C.c_void_p, C.c_int64]),
             "kcm_nside_joints": (C.c_int64, [h]),
@@ -478,6 +479,11 @@ class Chain:
         p = np.zeros(1, dtype=np.int32)
         _check(load().kcm_get_pair_kernel(self._h, _iptr(p)), self._h)
         return int(p[0])
+
+    def set_graph_overlap(self, on: bool):
+        """Programmatic dependent launch in the captured step graphs (default on; off for handles that
+        share the GPU with other streams' kernels)."""
+        _check(load().kcm_set_graph_overlap(self._h, int(bool(on))), self._h)
 
     def set_binning_kernel(self, kind: int):
         """BIN_CLUSTER (default: the binning in one cluster launch where the chain qualifies) or

@@ -372,6 +372,36 @@ def test_deterministic_fp64(kcm, table):
     assert np.array_equal(ath, bth)
 
 
+@pytest.mark.parametrize("precision", [synth.PRECISION_MIXED, synth.PRECISION_FP64])
+def test_graph_overlap_changes_nothing(kcm, table, precision):
+    """Programmatic dependent launch in the step graphs (kcm_set_graph_overlap, on by default) only lets
+    each kernel's launch overlap the previous kernel's run: the trajectory is bitwise that of the graphs
+    without it, on a single chain and on a batch."""
+    seq, th = start("chain1000")
+    p = synth.RunParams(precision=precision)
+    out = []
+    for on in (True, False):
+        with kcm.Chain(seq, table, p) as ch:
+            ch.set_graph_overlap(on)
+            ch.set_theta(th)
+            it, dm = ch.step(4)
+            out.append((it, dm, ch.get_theta()))
+    assert out[0][:2] == out[1][:2]
+    assert np.array_equal(out[0][2], out[1][2])
+    seqs = [synth.sequence(m, 7 + m) for m in (5, 40, 97)]
+    ths = [synth.theta_uniform(len(q), 3) for q in seqs]
+    res = []
+    for on in (True, False):
+        with kcm.Batch(seqs, table, p) as b:
+            b.set_graph_overlap(on)
+            b.set_theta(np.concatenate(ths))
+            b.step(3)
+            res.append(b.get_theta())
+    assert np.array_equal(res[0], res[1])
+    with kcm.Chain(seq, table, p) as ch:
+        assert kcm.load().kcm_set_graph_overlap(ch.handle, 2) == kcm.KCM_E_INVAL
+
+
 def test_bounded_wait_times_out(kcm, table):
     """The torque kernel's blocks wait for the totals of later link tiles with a bounded wait. With the
     last tile's publication withheld (test hook) every other block gives up after its bound and the
