@@ -17,6 +17,37 @@ __device__ __forceinline__ void grid_dep_sync() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// The loop state of a step call (k_reset_loop, or the first kernel of the first iteration's graph):
+// thread c of nthreads; c = 0 resets the status record, and the chains are taken in strides.
+__device__ __forceinline__ void reset_loop_state(const DevChain& d, int c, int nthreads, bool full) {
+    Status* st = d.status;
+    if (c == 0) {
+        st->iters = 0;
+        st->done = 0;
+        st->error = 0;
+        st->ticket = 0u;
+        st->ticket_w = 0u;
+        st->ticket_lb = 0u;
+        st->ticket_bin = 0u;
+        st->last_max_dtheta = 0.0;
+        if (full) {
+            st->ticket_bbox = 0u;
+            st->pairs = 0; st->nbr_total = 0; st->guard = 0; st->sasa_tests = 0; st->max_nbr = 0; st->nlong = 0;
+        }
+    }
+    for (; c < d.nchains; c += nthreads) {
+        d.chain_done[c] = d.chain_maxit[c] <= 0;  // a chain without iterations to take is done from the start
+        d.chain_err[c] = 0;
+        d.chain_iters[c] = 0;
+        d.chain_maxdt[c] = 0ULL;
+        d.chain_maxtau[c] = 0ULL;
+        d.chain_lastdt[c] = 0.0;
+        d.chain_E[3 * c] = 0.0; d.chain_E[3 * c + 1] = 0.0; d.chain_E[3 * c + 2] = 0.0;
+        if (full)
+            for (int i = 0; i < 3; ++i) { d.cbox[6 * c + i] = ~0ULL; d.cbox[6 * c + 3 + i] = 0ULL; }
+    }
+}
+
 // ---------------------------------------------------------------- small helpers
 // chain of an atom or joint (no load for a single chain)
 __device__ __forceinline__ int atom_chain(const DevChain& d, int a) { return d.nchains == 1 ? 0 : d.atom_chain[a]; }

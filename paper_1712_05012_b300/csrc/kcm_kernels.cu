@@ -1308,33 +1308,7 @@ __global__ void __launch_bounds__(W * 32) k_sasa_pw(const DevChain d) {
 // loop state of a batch; with full, also the statistics and the chains' bounding boxes
 __global__ void k_reset_loop(const DevChain d, int full) {
     grid_dep_sync();
-    Status* st = d.status;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c == 0) {
-        st->iters = 0;
-        st->done = 0;
-        st->error = 0;
-        st->ticket = 0u;
-        st->ticket_w = 0u;
-        st->ticket_lb = 0u;
-        st->ticket_bin = 0u;
-        st->last_max_dtheta = 0.0;
-        if (full) {
-            st->ticket_bbox = 0u;
-            st->pairs = 0; st->nbr_total = 0; st->guard = 0; st->sasa_tests = 0; st->max_nbr = 0; st->nlong = 0;
-        }
-    }
-    if (c < d.nchains) {
-        d.chain_done[c] = d.chain_maxit[c] <= 0;  // a chain without iterations to take is done from the start
-        d.chain_err[c] = 0;
-        d.chain_iters[c] = 0;
-        d.chain_maxdt[c] = 0ULL;
-        d.chain_maxtau[c] = 0ULL;
-        d.chain_lastdt[c] = 0.0;
-        d.chain_E[3 * c] = 0.0; d.chain_E[3 * c + 1] = 0.0; d.chain_E[3 * c + 2] = 0.0;
-        if (full)
-            for (int i = 0; i < 3; ++i) { d.cbox[6 * c + i] = ~0ULL; d.cbox[6 * c + 3 + i] = 0ULL; }
-    }
+    reset_loop_state(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, full != 0);
 }
 
 __global__ void k_force_out(const DevChain d) {
