@@ -539,6 +539,15 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
     d.fk_j = kcm::fk_joints_per_lane(d.l);
     const int fkq = kcm::fk_block_joints();
     d.ntiles = (d.l + fkq * d.fk_j - 1) / (fkq * d.fk_j);
+    {  // every chain within kcm::kFkTreeTiles scan blocks: the apply kernel reduces its chain's earlier block
+       // products itself, and no kernel scans all of them
+        int span = 0;
+        for (int c = 0; c < hc.nchains; ++c) {
+            const int j0 = hc.joint_off[c], j1 = hc.joint_off[c + 1];
+            if (j1 > j0) span = std::max(span, (j1 - 1) / (fkq * d.fk_j) - j0 / (fkq * d.fk_j) + 1);
+        }
+        d.fk_chain_tree = span <= kcm::fk_tree_tiles() ? 1 : 0;
+    }
     d.ltiles = (d.L + 31) / 32;
     d.nchains = hc.nchains;
     d.rcut2 = prm->cutoff * prm->cutoff;

@@ -86,6 +86,8 @@ struct DevChain {
                          // launch (k_bin_cluster); 0: the count and placement kernels
     int bin_capc = 0;    // its cells per CTA in shared memory (a multiple of 4, >= ceil(cell cap / bin_c))
     int ntiles = 0;      // transform-scan blocks of 32 * fk_j joints
+    int fk_chain_tree = 0;  // every chain spans at most fk_tree_tiles() scan blocks: each apply block reduces
+                            // the block products of its own chain before it (no scan of all of them)
     int ltiles = 0;      // suffix-sum tiles of 32 links
     int cell_cap = 0;     // cells of all chains' caps
     long long cell_alloc = 0;  // cells the cell arrays hold
@@ -241,6 +243,7 @@ void launch_torques(DevChain& d, cudaStream_t s);
 void launch_torques_step(DevChain& d, cudaStream_t s);
 int fk_joints_per_lane(int l);
 int fk_block_joints();  // quads per transform-scan block
+int fk_tree_tiles();    // most block products an apply block reduces itself
 void launch_force_out(DevChain& d, cudaStream_t s);
 
 }  // namespace kcm

@@ -15,9 +15,10 @@
 // 32 J (b + 1)), J consecutive joints per quad. Each quad forms its joints' local transforms and their
 // running product (kept in G), the warp scans its eight quad products (Kogge-Stone, 3 levels), warp 0
 // scans the four warp products, and each quad stores its exclusive prefix within the block; the
-// block product goes to tileP; with more than kFkTreeTiles blocks a one-block kernel of eight warps
-// (k_fk_tiles) scans the block products into every block's exclusive prefix (tileE), with fewer every
-// apply block reduces the products before it in one tree. k_fk_apply: block b composes its prefix,
+// block product goes to tileP. When every chain lies within kFkTreeTiles blocks (a single chain of up to
+// 2,048 J joints; the chains of a batch), every apply block reduces in one tree the products of the
+// blocks before it back to the one where its chain starts; otherwise a one-block kernel of eight warps
+// (k_fk_tiles) scans all block products into every block's exclusive prefix (tileE). k_fk_apply: block b composes its prefix,
 // quad prefix and running products into the link poses, the current axes u_j and axis points p_j,
 // moves the atoms of its links and adds them to their chain's bounding box; its last block to finish
 // sets the grids of the cell lists. A batch of chains is their concatenation: every product is
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
     // Few: every apply block reduces the products before it in one tree (a shorter critical path).
 }
 
-// Many scan blocks (more than kFkTreeTiles): one block of kTileWarps warps scans the block products
+// A chain longer than kFkTreeTiles scan blocks: one block of kTileWarps warps scans the block products
 // into every block's exclusive segmented prefix (tileE); each of its quads runs through
 // ceil(blocks / quads) products in order, then the quads' totals are scanned and each quad runs
 // through its products again, writing the prefixes. Eight warps (64 quads) halve the serial runs
@@ -564,11 +565,13 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
     // block prefix: the segmented product of the earlier blocks, scanned by the scan kernel's last
     // block, or (few blocks) reduced here in one tree
     T bE[4];
-    if (gridDim.x > kFkTreeTiles) {
+    if (!d.fk_chain_tree) {
         load_row(&reinterpret_cast<const T*>(d.tileE)[12 * (size_t)blockIdx.x], rr, bE);
-    } else {
+    } else {  // the products of the blocks from the one where the chain of this block's first joint starts
+        const int jb = (int)blockIdx.x * kFkQuads * J;
+        const int t0 = d.nchains == 1 ? 0 : d.joint_off[joint_chain(d, jb)] / (kFkQuads * J);
         bool pf;
-        block_prefix(d, 0, (int)blockIdx.x, sW, sF, w, q, rr, base, lane, bE, pf);
+        block_prefix(d, t0, (int)blockIdx.x, sW, sF, w, q, rr, base, lane, bE, pf);
     }
 #pragma unroll
     for (int i = 0; i < J; ++i) {
@@ -735,7 +738,7 @@ template <int J>
 void launch_fk_j(DevChain& d, cudaStream_t s) {
     // the scan kernel's grid: ntiles scan blocks, then the side-chain joints' blocks
     const int nscan = d.ntiles + (d.nmv + kSideFkThreads - 1) / kSideFkThreads;
-    const bool tiles = d.ntiles > kFkTreeTiles;  // the block products scanned by k_fk_tiles
+    const bool tiles = !d.fk_chain_tree;  // the block products scanned by k_fk_tiles
     if (d.prm.precision == KCM_MIXED) {
         launch_k(k_fk_scan<J, df>, nscan, kFkWarps * 32, 0, s, d.pdl, d);
         if (tiles) launch_k(k_fk_tiles<df>, 1, kTileWarps * 32, 0, s, d.pdl, d);
@@ -758,6 +761,8 @@ int fk_joints_per_lane(int l) {
 }
 
 int fk_block_joints() { return kFkQuads; }
+
+int fk_tree_tiles() { return kFkTreeTiles; }
 
 void launch_centres64(DevChain& d, cudaStream_t s) {
     if (d.prm.precision == KCM_MIXED && d.n > 0) launch_k(k_centres64, (3 * d.n + 255) / 256, 256, 0, s, d.pdl, d);
