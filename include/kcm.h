@@ -330,10 +330,15 @@ int kcm_sasa_counts(kcm_handle h, int32_t* covered, int64_t n);
 int kcm_step(kcm_handle h, int32_t n_iters, int32_t* iters_done, double* max_dtheta);
 
 /* kcm_set_theta, kcm_step and kcm_get_theta in one call with one wait: theta_in[l] (host, NULL: the
- * current theta) is copied to the device, up to n_iters iterations run as in kcm_step, and the final
- * theta is copied to theta_out[l] (host, may be NULL). With page-locked host buffers the copies are
- * asynchronous and the call waits once, for the status record; this is the host round trip of a
- * caller that owns theta on the host. Errors as kcm_set_theta and kcm_step. */
+ * current theta) goes to the device, up to n_iters iterations run as in kcm_step, and the final theta
+ * comes back in theta_out[l] (host, may be NULL); this is the host round trip of a caller that owns
+ * theta on the host. With both buffers and n_iters >= 1 the angles pass through a page-locked, mapped
+ * buffer of the handle (made at the first such call, l doubles): the first iteration's transform scan
+ * reads them from it and every step writes the angles it changes back, and the kernel that ends an
+ * iteration writes the status record to page-locked host memory, so the call is a host copy in, one
+ * graph launch per iteration, one wait and a host copy out, with no copy on the stream. Otherwise the
+ * copies are enqueued on the handle's stream (asynchronous for page-locked buffers). Errors as
+ * kcm_set_theta and kcm_step. */
 int kcm_step_host(kcm_handle h, const double* theta_in, double* theta_out, int64_t l, int32_t n_iters,
                   int32_t* iters_done, double* max_dtheta);
 
@@ -410,11 +415,13 @@ int kcm_autotune_tiles(kcm_handle h, int32_t reps, double* times_ms, int32_t* pa
                        int32_t* pair_persistent);
 
 /* Pair kernel of mixed precision (A3-A5: Coulomb and LJ forces, exclusions, solvation neighbour
- * lists; eq. 02_2, 03_2, 03_8 / 03_9 and the grid of Sec. 3.2). KCM_PAIR_CELL_TILES (the mixed-mode
- * default): a home cell's atoms against one row of its half stencil staged in shared memory, in-range
- * pairs compacted and evaluated with every lane busy, per-tile fixed-point sums added to the global
- * forces once per atom and tile. KCM_PAIR_WARP_PER_ATOM: one warp per home atom (the FP64 path's
- * kernel; its mixed form takes the tile shapes above). Both give bitwise the same pair forces and
+ * lists; eq. 02_2, 03_2, 03_8 / 03_9 and the grid of Sec. 3.2). KCM_PAIR_CELL_TILES: a home cell's
+ * atoms against one row of its half stencil staged in shared memory, in-range pairs compacted and
+ * evaluated with every lane busy, per-tile fixed-point sums added to the global forces once per atom and
+ * tile. KCM_PAIR_WARP_PER_ATOM: one warp per home atom (the FP64 path's kernel; its mixed form takes the
+ * tile shapes above). A mixed handle starts with the tile kernel from 65,536 atoms on (batches, long
+ * chains) and with the warp-per-atom kernel below (the tile kernel's warps fill the SMs only on large
+ * inputs); kcm_autotune_pair_kernel measures both. Both give bitwise the same pair forces and
  * solvation lists (up to the order of a list's entries, which no result depends on); energies agree to
  * FP32 rounding. kcm_set_pair_kernel synchronises and drops the captured graphs; KCM_E_INVAL for
  * another value, or for KCM_PAIR_CELL_TILES on an FP64 handle. kcm_get_pair_kernel reads it. */

@@ -24,7 +24,12 @@ struct kcm_ctx {
     cudaGraphExec_t graph = nullptr;        // one iteration
     cudaGraphExec_t graph_first = nullptr;  // the loop-state reset and one iteration (a step call's first)
     cudaGraphExec_t graph_timed = nullptr;
+    cudaGraphExec_t graph_io_first = nullptr;  // kcm_step_host: graph_first and graph with the host exchange
+    cudaGraphExec_t graph_io = nullptr;
     kcm::Status* st_host = nullptr;          // page-locked copy of the status record (read back by the calls)
+    double* theta_io = nullptr;              // kcm_step_host's page-locked angles [l] (made at its first call)
+    double* theta_io_dev = nullptr;          // the device addresses of theta_io and st_host
+    kcm::Status* st_io_dev = nullptr;
     cudaEvent_t ev[KCM_NUM_STAGES + 2] = {};
     int sm_count = 148;
     bool bin_cluster = true;         // the cluster binning kernel where the chain qualifies (kcm_set_binning_kernel)
@@ -296,6 +301,55 @@ int build_graph(kcm_ctx* h) {
     return KCM_OK;
 }
 
+// kcm_step_host's graphs: graph_first and graph again, with the host exchange of DevChain (theta_io,
+// status_io, io_import) set during their capture only. Returns false (and the call copies instead) where
+// the page-locked buffers are not to be had.
+int build_io_graphs(kcm_ctx* h, bool* ok) {
+    *ok = false;
+    if (!h->st_host) return KCM_OK;
+    if (!h->theta_io) {
+        void* p = nullptr;
+        cudaError_t e = cudaHostAlloc(&p, sizeof(double) * std::max(h->d.l, 1), cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            h->theta_io = static_cast<double*>(p);
+            void* dp = nullptr;
+            e = cudaHostGetDevicePointer(&dp, p, 0);
+            h->theta_io_dev = static_cast<double*>(dp);
+        }
+        if (e == cudaSuccess) {
+            void* dp = nullptr;
+            e = cudaHostGetDevicePointer(&dp, h->st_host, 0);
+            h->st_io_dev = static_cast<kcm::Status*>(dp);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (h->theta_io) cudaFreeHost(h->theta_io);
+            h->theta_io = nullptr;
+            return KCM_OK;
+        }
+    }
+    for (int first = 0; first < 2; ++first) {
+        cudaGraphExec_t* out = first ? &h->graph_io_first : &h->graph_io;
+        if (*out) continue;
+        h->d.theta_io = h->theta_io_dev;
+        h->d.status_io = h->st_io_dev;
+        h->d.io_import = first;
+        const cudaError_t e = capture_graph(
+            h,
+            [&] {
+                if (first) kcm::launch_reset_loop(h->d, h->stream);
+                enqueue_iteration(h);
+            },
+            out);
+        h->d.theta_io = nullptr;
+        h->d.status_io = nullptr;
+        h->d.io_import = 0;
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+    }
+    *ok = true;
+    return KCM_OK;
+}
+
 // the loop-state reset and n_iters iterations: the first with the reset in one graph launch
 int launch_steps(kcm_ctx* h, int32_t n_iters) {
     if (n_iters == 0) {
@@ -370,9 +424,13 @@ void drop_graphs(kcm_ctx* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->graph_first) cudaGraphExecDestroy(h->graph_first);
     if (h->graph_timed) cudaGraphExecDestroy(h->graph_timed);
+    if (h->graph_io_first) cudaGraphExecDestroy(h->graph_io_first);
+    if (h->graph_io) cudaGraphExecDestroy(h->graph_io);
     h->graph = nullptr;
     h->graph_first = nullptr;
     h->graph_timed = nullptr;
+    h->graph_io_first = nullptr;
+    h->graph_io = nullptr;
 }
 
 // the pair kernel's grid: one block per W atoms, or with pair_persistent one block per resident slot
@@ -527,7 +585,8 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
     const kcm::HostChain& hc = h->hc;
     kcm::DevChain& d = h->d;
     d.prm = *prm;
-    d.pair_tile = prm->precision == KCM_MIXED ? KCM_PAIR_CELL_TILES : KCM_PAIR_WARP_PER_ATOM;
+    d.pair_tile = prm->precision == KCM_MIXED && hc.n >= kcm::kPairTileDefaultAtoms ? KCM_PAIR_CELL_TILES
+                                                                                 : KCM_PAIR_WARP_PER_ATOM;
     d.m = hc.m; d.n = hc.n; d.l = hc.l; d.L = hc.L; d.N = prm->n_sample;
     d.ls = prm->side_joints ? hc.ls : 0;
     d.nmv = prm->side_joints ? static_cast<int>(hc.mv_atom.size()) : 0;
@@ -842,6 +901,7 @@ void kcm_destroy(kcm_handle h) {
     if (h->join) cudaEventDestroy(h->join);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     release_status(h->st_host);
+    if (h->theta_io) cudaFreeHost(h->theta_io);
     cudaGetLastError();
     delete h;
 }
@@ -996,6 +1056,40 @@ int kcm_step_host(kcm_handle h, const double* theta_in, double* theta_out, int64
     if (check_handle(h)) return KCM_E_INVAL;
     if (n_iters < 0) return set_err(h, KCM_E_INVAL, "n_iters < 0");
     if ((theta_in || theta_out) && l != h->d.l) return set_err(h, KCM_E_INVAL, "theta length must equal the joint count");
+    bool io = false;
+    if (theta_in && theta_out && n_iters >= 1) {
+        const int rc = build_io_graphs(h, &io);
+        if (rc) return rc;
+    }
+    if (io) {
+        // the angles go through the page-locked buffer that the graphs read and write: no copies on the
+        // stream, and the status record arrives with the last iteration (an iters of -1 left in it means
+        // that nothing exported it, and the record is then read from the device)
+        for (int64_t k = 0; k < l; ++k) {
+            const double v = theta_in[k];
+            if (!std::isfinite(v)) return set_err(h, KCM_E_INVAL, "theta is not finite");
+            h->theta_io[k] = v;
+        }
+        h->st_host->iters = -1;
+        for (int32_t i = 0; i < n_iters; ++i) {
+            const cudaError_t e = cudaGraphLaunch(i == 0 ? h->graph_io_first : h->graph_io, h->stream);
+            if (e != cudaSuccess) {
+                cudaStreamSynchronize(h->stream);  // nothing may still read theta_io when the call returns
+                return cuda_fail(h, e, "graph launch");
+            }
+        }
+        int rc = sync(h);
+        if (rc) return rc;
+        kcm::Status st = *h->st_host;
+        if (st.iters < 0) {
+            rc = read_status(h, &st);
+            if (rc) return rc;
+        }
+        std::memcpy(theta_out, h->theta_io, sizeof(double) * l);
+        if (iters_done) *iters_done = st.iters;
+        if (max_dtheta) *max_dtheta = st.last_max_dtheta;
+        return status_code(h, st);
+    }
     for (int64_t k = 0; theta_in && k < l; ++k)
         if (!std::isfinite(theta_in[k])) return set_err(h, KCM_E_INVAL, "theta is not finite");
     int rc = build_graph(h);

@@ -17,6 +17,23 @@ __device__ __forceinline__ void grid_dep_sync() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// kcm_step_host's graphs: the status record to the caller's page-locked copy (one thread, after the
+// iteration's last update of the record; 8-byte words read from L2, where other blocks' atomics landed).
+// The host reads it after the stream's work has completed, which makes the writes visible.
+__device__ __forceinline__ void export_status(const DevChain& d) {
+    if (!d.status_io) return;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(d.status);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(d.status_io);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(Status) / 8); ++i) dst[i] = __ldcg(src + i);
+}
+
+// a step's new angle of joint jj (main chain or side chain), and kcm_step_host's copy of a main-chain one
+__device__ __forceinline__ void set_theta(const DevChain& d, int jj, double th) {
+    d.theta[jj] = th;
+    if (d.theta_io && jj < d.l) d.theta_io[jj] = th;
+}
+
 // The loop state of a step call (k_reset_loop, or the first kernel of the first iteration's graph):
 // thread c of nthreads; c = 0 resets the status record, and the chains are taken in strides.
 __device__ __forceinline__ void reset_loop_state(const DevChain& d, int c, int nthreads, bool full) {

@@ -220,7 +220,16 @@ struct DevChain {
     double* Fcav64 = nullptr;      // [n*3] (on request)
     GridInfo* grid = nullptr;      // [nchains]
     Status* status = nullptr;
+    // Host exchange of kcm_step_host (device addresses of page-locked, mapped host memory; null in every
+    // other graph): the first iteration's transform scan takes the main-chain angles from theta_io
+    // (io_import) into theta, every step writes the angles it changes back to both, and the status record
+    // goes to status_io when an iteration's last update of it is made (the step's last block, or the
+    // kinematics when they end the loop), so that the call reads theta and its outcome without copies.
+    double* theta_io = nullptr;    // [l]
+    Status* status_io = nullptr;
+    int io_import = 0;
 };
+static_assert(sizeof(Status) % 8 == 0, "the status record is exported in 8-byte words");
 
 // launchers (kcm_kernels.cu)
 void launch_init_status(DevChain& d, cudaStream_t s);

@@ -134,10 +134,10 @@ __device__ __forceinline__ void row_compose(const T* a, const T* B, T* c) {
 
 // row rr of the local joint transform L_j = Tr(step_j) o Rot(u_j, th) with
 // R = cos I + sin [u]x + (1 - cos) u u^T (right-hand rule); the same arithmetic as joint_tf
-__device__ __forceinline__ void joint_row(const DevChain& d, int j, int rr, double* g) {
+__device__ __forceinline__ void joint_row(const DevChain& d, int j, double th, int rr, double* g) {
     const double* u = &d.u0[3 * j];
     double s, c;
-    sincos(d.theta[j], &s, &c);
+    sincos(th, &s, &c);
     const double C = 1.0 - c;
     if (rr == 0) {
         g[0] = c + u[0] * u[0] * C; g[1] = u[0] * u[1] * C - u[2] * s; g[2] = u[0] * u[2] * C + u[1] * s;
@@ -148,10 +148,10 @@ __device__ __forceinline__ void joint_row(const DevChain& d, int j, int rr, doub
     }
     g[3] = d.step0[3 * j + rr];
 }
-__device__ __forceinline__ void joint_row(const DevChain& d, int j, int rr, df* g) {
+__device__ __forceinline__ void joint_row(const DevChain& d, int j, double th, int rr, df* g) {
     const df* u = reinterpret_cast<const df*>(d.u0df) + 3 * j;
     df s, c;
-    df_sincos(d.theta[j], &s, &c);
+    df_sincos(th, &s, &c);
     const df C = sub(df{1.0f, 0.0f}, c);
     const df ur = u[rr];
     const df urC = mul(ur, C);
@@ -344,7 +344,14 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_scan(const DevChain d) {
         T g[4];  // joints past the end act as the identity (every lane takes part in the shuffles)
         bool head = false;
         if (j < d.l) {
-            joint_row(d, j, rr, g);
+            double th;
+            if (d.io_import) {  // kcm_step_host's first iteration: the angles from the caller's buffer
+                th = d.theta_io[j];
+                if ((lane & 3) == 0) d.theta[j] = th;
+            } else {
+                th = d.theta[j];
+            }
+            joint_row(d, j, th, rr, g);
             head = d.jhead[j] != 0;
         } else {
             row_identity(rr, g);
@@ -718,7 +725,8 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
         cbase += total;
         __syncthreads();
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+    const bool bad_any = __syncthreads_or(bad);
+    if (bad_any && threadIdx.x == 0) {
         atomicOr(&st->error, kErrNonfinite);
         if (d.nchains == 1) st->done = 1;
     }
@@ -731,6 +739,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
         st->sasa_tests = 0;
         st->max_nbr = 0;
         st->nlong = 0;
+        if (bad_any && d.nchains == 1) export_status(d);  // the loop ends here: no step block closes it
     }
 }
 

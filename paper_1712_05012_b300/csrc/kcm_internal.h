@@ -25,6 +25,12 @@ constexpr int kSasaStage = 128;
 // Largest sample count per offset sphere.
 constexpr int kMaxSample = 4096;
 
+// Mixed handles of at least this many atoms start with the cell-pair tile kernel, smaller ones with the
+// warp-per-atom kernel. The tile kernel's warps (one per 32 sorted slots and stencil row) fill the SMs
+// only on large inputs: measured on a B300, 26.6 against 36.5 us on 10,506 atoms, about equal on
+// 83,746, 2.03 against 2.5 ms on 1.63 M atoms (the pair-kernel autotuner decides per handle).
+constexpr int kPairTileDefaultAtoms = 65536;
+
 // Bond classes are stored as two 64-bit masks per atom `lo`: bit d set means the pair
 // (lo, lo + d) is excluded (1-2 / 1-3) or is a 1-4 pair. Pairs within three bonds always lie
 // within this window for the chains built here (checked at build time).

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_step(const DevChai
             cjo = -1;  // a converged or failed chain takes no more steps
         } else if (STEP && !nf) {
             const double dt = fx ? 0.0 : fmin(fmax(d.prm.kappa * tq, -d.prm.dtheta_max), d.prm.dtheta_max);
-            if (!fx) d.theta[jj] += dt;
+            if (!fx) set_theta(d, jj, d.theta[jj] + dt);
             d.dtheta[jj] = dt;
             adt = (unsigned long long)__double_as_longlong(fabs(dt));
         }
@@ -464,7 +464,10 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_step(const DevChai
         *d.lb_epoch = epoch;
     }
     if (STEP) close_iteration(d, st);
-    if (threadIdx.x == 0 && (__ldcg(&st->error) & kErrTimeout)) st->done = 1;  // a timed-out iteration ends the loop
+    if (threadIdx.x == 0) {
+        if (__ldcg(&st->error) & kErrTimeout) st->done = 1;  // a timed-out iteration ends the loop
+        export_status(d);  // (the normalised step's kernel exports it again when it closes the iteration)
+    }
 }
 
 // the paper's normalised step (eq. KCM_07): dtheta_k = kappa tau_k / max |tau| over the free joints of
@@ -484,7 +487,7 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
         } else {
             const double tm = __longlong_as_double((long long)__ldcg(&d.chain_maxtau[cj]));
             const double dt = (tm > 0.0 && !d.jfixed[jj]) ? d.prm.kappa * d.tau[jj] / tm : 0.0;
-            d.theta[jj] += dt;
+            set_theta(d, jj, d.theta[jj] + dt);
             d.dtheta[jj] = dt;
             adt = (unsigned long long)__double_as_longlong(fabs(dt));
         }
@@ -497,6 +500,7 @@ __global__ void __launch_bounds__(128) k_step_normalized(const DevChain d) {
     if (!last) return;
     __threadfence();
     close_iteration(d, st);
+    if (threadIdx.x == 0) export_status(d);
 }
 
 }  // namespace

@@ -459,7 +459,8 @@ class Chain:
         _check(load().kcm_set_tiles(self._h, int(pair_warps), int(sasa_warps), int(pair_persistent)), self._h)
 
     def set_pair_kernel(self, kind: int):
-        """PAIR_CELL_TILES (mixed-mode default) or PAIR_WARP_PER_ATOM."""
+        """PAIR_CELL_TILES or PAIR_WARP_PER_ATOM (the default of mixed handles below 65,536 atoms and of
+        FP64 handles)."""
         _check(load().kcm_set_pair_kernel(self._h, int(kind)), self._h)
 
     def autotune_pair_kernel(self, reps: int = 3):

@@ -1,4 +1,4 @@
-"""The cell-pair tile kernel of the mixed path (KCM_PAIR_CELL_TILES, the mixed default) against the
+"""The cell-pair tile kernel of the mixed path (KCM_PAIR_CELL_TILES, the default from 65,536 atoms on) against the
 warp-per-atom kernel (KCM_PAIR_WARP_PER_ATOM) on the same inputs, and against the FP64 oracle.
 
 Both kernels form every pair term with the same explicitly rounded FP32 operations and add it to both
@@ -165,6 +165,8 @@ def test_tiles_batch(kcm, table):
 def test_pair_kernel_choice_rules(kcm, table):
     seq, _, th = small(table, 5, 3, "uniform")
     with kcm.Chain(seq, table, synth.RunParams(precision=synth.PRECISION_MIXED)) as ch:
+        assert ch.get_pair_kernel() == kcm.PAIR_WARP_PER_ATOM  # small handles: the warp-per-atom kernel
+        ch.set_pair_kernel(kcm.PAIR_CELL_TILES)
         assert ch.get_pair_kernel() == kcm.PAIR_CELL_TILES
         with pytest.raises(kcm.KcmError) as e:
             ch.set_pair_kernel(7)
@@ -174,3 +176,14 @@ def test_pair_kernel_choice_rules(kcm, table):
         with pytest.raises(kcm.KcmError) as e:
             ch.set_pair_kernel(kcm.PAIR_CELL_TILES)
         assert e.value.code == kcm.KCM_E_INVAL
+    # from 65,536 atoms on (the 8,000-residue chain: 83,746; a batch of eight of them) the tile kernel
+    seq8, _ = start("chain8000")
+    mixed = synth.RunParams(precision=synth.PRECISION_MIXED, cutoff=12.0)
+    with kcm.Chain(seq8, table, mixed) as ch:
+        assert ch.n >= 65536 and ch.get_pair_kernel() == kcm.PAIR_CELL_TILES
+    with kcm.Chain(seq8, table, synth.RunParams(precision=synth.PRECISION_FP64, cutoff=12.0)) as ch:
+        assert ch.get_pair_kernel() == kcm.PAIR_WARP_PER_ATOM
+    with kcm.Batch([seq8[:3000]] * 3, table, mixed) as b:  # 3 x ~31,000 atoms
+        assert b.get_pair_kernel() == kcm.PAIR_CELL_TILES
+    with kcm.Batch([seq8[:3000]] * 2, table, mixed) as b:  # ~63,000 atoms
+        assert b.get_pair_kernel() == kcm.PAIR_WARP_PER_ATOM

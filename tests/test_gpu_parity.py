@@ -253,6 +253,67 @@ def test_step_host_round_trip(kcm, table):
         assert e.value.code == kcm.KCM_E_INVAL
 
 
+def host_vs_device(kcm, make, theta, n_iters, prepare=None):
+    """kcm_step_host with both buffers (the angles and the status record through page-locked mapped
+    memory, no copies on the stream) against kcm_set_theta + kcm_step + kcm_get_theta on a second handle:
+    theta, iterations and max |dtheta| bitwise; then the first handle's device state agrees."""
+    with make() as a, make() as b:
+        if prepare:
+            prepare(a)
+            prepare(b)
+        out, it, dm = a.step_host(theta, n_iters)
+        b.set_theta(theta)
+        it2, dm2 = b.step(n_iters)
+        assert (it, dm) == (it2, dm2)
+        assert np.array_equal(out, b.get_theta())
+        assert np.array_equal(a.get_theta(), out)
+        assert np.array_equal(a.torques(), b.torques())
+        # the ordinary graphs after the exchange graphs, and the exchange graphs again
+        a.set_theta(theta)
+        assert a.step(n_iters) == (it2, dm2)
+        assert np.array_equal(a.get_theta(), out)
+        out2, it3, dm3 = a.step_host(theta, n_iters)
+        assert (it3, dm3) == (it2, dm2) and np.array_equal(out2, out)
+        return it
+
+
+@pytest.mark.parametrize("precision,step_mode,n_iters", [(synth.PRECISION_MIXED, 0, 1),
+                                                         (synth.PRECISION_FP64, 1, 4),
+                                                         (synth.PRECISION_MIXED, 1, 3)])
+def test_step_host_exchange(kcm, table, precision, step_mode, n_iters):
+    """Both step rules and precisions, with fixed joints (they take no step: their angle in the
+    exchange buffer is the one read in)."""
+    seq, och, th = small_case(table, 30, 11)
+    p = synth.RunParams(precision=precision, step_mode=step_mode)
+    fixed = (np.arange(len(th)) % 5 == 0).astype(np.uint8)
+    host_vs_device(kcm, lambda: kcm.Chain(seq, table, p), th, n_iters, lambda c: c.set_fixed_joints(fixed))
+
+
+def test_step_host_exchange_batch_convergence(kcm, table):
+    """A batch whose chains stop at different iterations of one call (iteration caps and convergence):
+    a stopped chain's angles stay as its last step left them, and the call's iteration count and max
+    |dtheta| are those of the device loop; a call whose chains all stop early reports the iterations
+    taken."""
+    seqs, ths = [], []
+    for m, seed in ((12, 3), (25, 4), (40, 5)):
+        seq, och, th = small_case(table, m, seed)
+        seqs.append(seq)
+        ths.append(th)
+    th = np.concatenate(ths)
+    p = synth.RunParams(precision=synth.PRECISION_MIXED, solvation=0, conv_tol=1e-6)
+    it = host_vs_device(kcm, lambda: kcm.Batch(seqs, table, p), th, 6,
+                        lambda c: c.set_chain_max_iters(np.array([2, 6, 4], dtype=np.int32)))
+    assert it == 6
+    it = host_vs_device(kcm, lambda: kcm.Batch(seqs, table, p), th, 8,
+                        lambda c: c.set_chain_max_iters(np.array([1, 3, 2], dtype=np.int32)))
+    assert it == 3  # every chain at its cap after three iterations; the rest of the call is no-ops
+    # a single chain that converges in the call (conv_tol above the first steps' max |dtheta|)
+    seq, och, th1 = small_case(table, 15, 9)
+    pc = synth.RunParams(precision=synth.PRECISION_MIXED, solvation=0, conv_tol=0.05)
+    it = host_vs_device(kcm, lambda: kcm.Chain(seq, table, pc), th1, 5)
+    assert it == 1
+
+
 def test_device_pointer_calls(kcm, table):
     import torch
     seq, och, th = small_case(table, 20, 6)
@@ -418,6 +479,9 @@ def test_bounded_wait_times_out(kcm, table):
         assert e.value.code == kcm.KCM_E_TIMEOUT
         with pytest.raises(kcm.KcmError) as e:
             ch.step(3)
+        assert e.value.code == kcm.KCM_E_TIMEOUT
+        with pytest.raises(kcm.KcmError) as e:  # the status record exported by the timed-out iteration
+            ch.step_host(th, 3)
         assert e.value.code == kcm.KCM_E_TIMEOUT
         ch.set_test_withhold(-1)
         ch.set_theta(th)
