@@ -873,7 +873,6 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
     __shared__ float4 s_o[W][kSasaStage];   // o_j, h_j
     __shared__ int s_idx[W][kSasaStage];
     __shared__ int s_cnt[W][3 * kSasaStage];
-    __shared__ unsigned short s_near[W][kBatch];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * W + w;
     if (a < d.n && !d.status->done) {
@@ -920,19 +919,33 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
                 return covers64(qx, qy, qz, centre64(d, b, 0), centre64(d, b, 1), centre64(d, b, 2), __dmul_rn(ro, ro),
                                 s, dr);
             };
+            bool exch = false;  // this lane added an exchange count
             for (int kb = 0; kb < d.N; kb += kBatch) {
                 float qx[kPtsPerLane], qy[kPtsPerLane], qz[kPtsPerLane], mx[kPtsPerLane];
                 unsigned valid = 0;
+                if (kb + kBatch <= d.N) {  // a whole batch (N a multiple of 256, the default among them)
+                    valid = (1u << kPtsPerLane) - 1u;
+                    const float4* Qb = d.Q4 + kb + lane;
 #pragma unroll
-                for (int p = 0; p < kPtsPerLane; ++p) {
-                    const int k = kb + lane + 32 * p;
-                    const bool v = k < d.N;
-                    const float4 qk = v ? d.Q4[k] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    qx[p] = qk.x;
-                    qy[p] = qk.y;
-                    qz[p] = qk.z;
-                    valid |= v ? (1u << p) : 0u;
-                    mx[p] = -INFINITY;
+                    for (int p = 0; p < kPtsPerLane; ++p) {
+                        const float4 qk = Qb[32 * p];
+                        qx[p] = qk.x;
+                        qy[p] = qk.y;
+                        qz[p] = qk.z;
+                        mx[p] = -INFINITY;
+                    }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < kPtsPerLane; ++p) {
+                        const int k = kb + lane + 32 * p;
+                        const bool v = k < d.N;
+                        const float4 qk = v ? d.Q4[k] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        qx[p] = qk.x;
+                        qy[p] = qk.y;
+                        qz[p] = qk.z;
+                        valid |= v ? (1u << p) : 0u;
+                        mx[p] = -INFINITY;  // a missing point stays at -inf: neither covered nor near
+                    }
                 }
                 // step 1: the largest m of each point over all neighbours
 #pragma unroll 2
@@ -946,22 +959,19 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
                     }
                 }
                 ntest += (unsigned long long)__popc(valid) * cnt;
-                // decided points are counted; the rest are listed for the re-scan
-                int nres = 0;
-                const unsigned lt = (1u << lane) - 1u;
+                // decided points are counted; the rest (bits p of each lane) are re-scanned
+                unsigned cov = 0, res = 0;
 #pragma unroll
                 for (int p = 0; p < kPtsPerLane; ++p) {
-                    const bool v = (valid >> p) & 1u;
-                    const bool res = v && mx[p] > -band && mx[p] <= band;
-                    if (v && mx[p] > band) ++ncov;
-                    const unsigned bm = __ballot_sync(0xffffffffu, res);
-                    if (res) s_near[w][nres + __popc(bm & lt)] = (unsigned short)(lane + 32 * p);
-                    nres += __popc(bm);
+                    cov |= mx[p] > band ? (1u << p) : 0u;
+                    res |= (mx[p] > -band && mx[p] <= band) ? (1u << p) : 0u;
                 }
-                __syncwarp();
-                // re-scan, one point at a time; lane t takes neighbours t, t + 32, ... (at most 4)
-                for (int e = 0; e < nres; ++e) {
-                    const int k = kb + s_near[w][e];
+                ncov += __popc(cov);
+                // re-scan, one point at a time (lane by lane, then by p); lane t takes neighbours t, t + 32,
+                // ... (at most 4)
+                for (unsigned rl = __ballot_sync(0xffffffffu, res != 0u); rl; rl &= rl - 1u)
+                for (unsigned pb = __shfl_sync(0xffffffffu, res, __ffs(rl) - 1); pb; pb &= pb - 1u) {
+                    const int k = kb + (__ffs(rl) - 1) + 32 * (__ffs(pb) - 1);
                     const float4 qk = d.Q4[k];
                     const float Qx = qk.x, Qy = qk.y, Qz = qk.z;
                     unsigned inb = 0, nrb = 0;
@@ -989,8 +999,11 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
                             const float Qs = s == 0 ? Qx : (s == 1 ? Qy : Qz);
                             const float ms = fmaf(drf, Qs, m) - (2.0f * drf * os + drf * drf) * inv2R;
                             ++ntest;
-                            const bool cov = fabsf(ms) > gd ? ms >= 0.0f : recheck(j, k, s);
-                            if (cov == want) atomicAdd(&s_cnt[w][3 * j + s], delta);
+                            const bool cv = fabsf(ms) > gd ? ms >= 0.0f : recheck(j, k, s);
+                            if (cv == want) {
+                                atomicAdd(&s_cnt[w][3 * j + s], delta);
+                                exch = true;
+                            }
                         }
                     };
                     if (C == 0) {  // exposed: every near neighbour may cover it once displaced
@@ -1009,7 +1022,8 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
             __syncwarp();
             const long long qa = d.qfx[a];
             int s0 = 0, s1 = 0, s2 = 0;
-            for (int j = lane; j < cnt; j += 32) {
+            const bool any_exch = __any_sync(0xffffffffu, exch);  // most atoms have none
+            for (int j = lane; any_exch && j < cnt; j += 32) {
                 const int b = s_idx[w][j];
                 const int c0 = s_cnt[w][3 * j], c1 = s_cnt[w][3 * j + 1], c2 = s_cnt[w][3 * j + 2];
                 if (c0) atomicAdd((unsigned long long*)&d.Fcav[3 * b], (unsigned long long)(qa * c0));
