@@ -214,8 +214,10 @@ struct StageRange {
 };
 
 void enqueue_stages(kcm_ctx* h, bool step) {
-    { StageRange r(KCM_STAGE_KINEMATICS); kcm::launch_fk(h->d, h->stream); }
-    { StageRange r(KCM_STAGE_BINNING); kcm::launch_binning(h->d, h->stream); }
+    kcm::DevChain d = h->d;  // the cluster binning kernel, where it bins, forms the grid
+    d.grid_in_bin = d.bin_c ? 1 : 0;
+    { StageRange r(KCM_STAGE_KINEMATICS); kcm::launch_fk(d, h->stream); }
+    { StageRange r(KCM_STAGE_BINNING); kcm::launch_binning(d, h->stream); }
     { StageRange r(KCM_STAGE_PAIRS); kcm::launch_pairs(h->d, h->stream); }
     { StageRange r(KCM_STAGE_SOLVATION); enqueue_sasa(h, h->stream); }
     {
@@ -377,9 +379,11 @@ int build_timed_graph(kcm_ctx* h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
     cudaStream_t s = h->stream;
     cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
-    { StageRange r(KCM_STAGE_KINEMATICS); kcm::launch_fk(h->d, s); }
+    kcm::DevChain d = h->d;  // as in enqueue_stages
+    d.grid_in_bin = d.bin_c ? 1 : 0;
+    { StageRange r(KCM_STAGE_KINEMATICS); kcm::launch_fk(d, s); }
     cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
-    { StageRange r(KCM_STAGE_BINNING); kcm::launch_binning(h->d, s); }
+    { StageRange r(KCM_STAGE_BINNING); kcm::launch_binning(d, s); }
     cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
     { StageRange r(KCM_STAGE_PAIRS); kcm::launch_pairs(h->d, s); }
     cudaEventRecordWithFlags(h->ev[4], s, cudaEventRecordExternal);

@@ -1,7 +1,11 @@
 // A2 binning of a single chain in one launch: the counting sort of Sec. 3.2 (cell counts, their
 // exclusive scan, the atoms in slot order) run by one thread-block cluster of C CTAs (C <= 16), where
 // the multi-block path takes a count kernel whose last block scans the counts and a placement kernel.
-// The grid and the double-float centres come from the kinematics (k_fk_apply); mixed mode only.
+// The double-float centres and the box keys come from the kinematics (k_fk_apply); mixed mode only.
+// In the step and evaluation graphs the cluster also forms the grid from the box (every CTA, one thread
+// each), which the kinematics' last block does for the other binning kernels: the kinematics then end
+// without that block's tail, and the grid code, run once on a dummy box before the wait for the
+// kinematics (programmatic dependent launch), is already fetched when the real box arrives.
 //
 // CTA b holds atoms [b n / C, (b + 1) n / C) and the cells [b P, (b + 1) P) of the grid
 // (P = ceil(cells / C)), whose counts, then starts within the range, live in its shared memory:
@@ -38,6 +42,17 @@ namespace cg = cooperative_groups;
 namespace {
 using namespace dev;
 
+// the grid of the chain from its six box keys (lowest x, y, z, then highest; keys of double-float
+// values), the arithmetic of the kinematics' last block (grid_from_bounds_df); not inlined, so that the
+// run on a dummy box executes the very instructions of the real one
+__device__ __noinline__ bool cluster_grid(unsigned long long k0, unsigned long long k1, unsigned long long k2,
+                                          unsigned long long k3, unsigned long long k4, unsigned long long k5,
+                                          double s_base, int stencil, double cell, long long cap, GridInfo* out) {
+    df lo[3] = {dfkey_inv(k0), dfkey_inv(k1), dfkey_inv(k2)};
+    const df hi[3] = {dfkey_inv(k3), dfkey_inv(k4), dfkey_inv(k5)};
+    return grid_from_bounds_df(s_base, stencil, cell, lo, hi, cap, out);
+}
+
 constexpr int kBcThreads = 1024;
 constexpr int kBcWarps = kBcThreads / 32;
 constexpr int kBcAtoms = 2;                       // most atoms per thread
@@ -46,23 +61,66 @@ constexpr int kBcMaxCells = 52 * 1024;            // most cells of a CTA's range
 constexpr int kBcAtomsPerCta = 1024;              // atoms per CTA the plan aims at (one per thread)
 
 __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
-    grid_dep_sync();
     extern __shared__ int4 sCell4[];  // the CTA's cell counts, then their starts within the range
     int* sCell = reinterpret_cast<int*>(sCell4);
     __shared__ int sWs[kBcWarps];
     __shared__ int sRange;  // atoms in the CTA's cells (read by every CTA)
     __shared__ int sOff[kBcMaxCtas + 1];
+    __shared__ GridInfo sG;
+    __shared__ bool sFinite;
+    if (d.grid_in_bin && threadIdx.x == 0) {  // the dummy box (1 A wide), before the wait; sG is rewritten
+        const unsigned long long z = dfkey(df{0.0f, 0.0f}), o = dfkey(df{1.0f, 0.0f});
+        sFinite = cluster_grid(z, z, z, o, o, o, d.s_base, d.stencil, d.prm.cell_size, 1 << 16, &sG);
+    }
+    grid_dep_sync();
 
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), b = (int)cl.block_rank();
     if (d.status->done) return;  // the same for every CTA: nothing writes it while the kernel runs
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    Status* st = d.status;
+    if (!d.grid_in_bin) {
+        if (threadIdx.x == 0) { sG = d.grid[0]; sFinite = true; }
+    } else if (threadIdx.x == 0) {
+        unsigned long long k[6];  // every CTA reads the box before the cluster barrier; CTA 0 resets it after
+#pragma unroll
+        for (int i = 0; i < 6; ++i) k[i] = __ldcg(&d.cbox[i]);
+        GridInfo gg;
+        const bool fin = cluster_grid(k[0], k[1], k[2], k[3], k[4], k[5], d.s_base, d.stencil, d.prm.cell_size,
+                                      d.ccap[0], &gg);
+        sG = gg;
+        sFinite = fin;
+    }
     for (int i = threadIdx.x; i < d.bin_capc / 4; i += blockDim.x) sCell4[i] = make_int4(0, 0, 0, 0);
-    const GridInfo g = d.grid[0];
-    const int nc = g.ncells, per = (nc + C - 1) / C;
     const int a0 = (int)((long long)d.n * b / C), a1 = (int)((long long)d.n * (b + 1) / C);  // <= kBcAtoms each
     const df* rdf = reinterpret_cast<const df*>(d.rdf);
-    cl.sync();  // (1) every CTA's counts are zero
+    cl.sync();  // (1) every CTA's counts are zero, and every CTA has the grid
+    const GridInfo g = sG;
+    if (d.grid_in_bin && b == 0) {
+        // after the barrier (every CTA has read the box): the box reset for the next evaluation, and what
+        // the kinematics' last block records for the other binning kernels
+        if (threadIdx.x < 6) d.cbox[threadIdx.x] = threadIdx.x < 3 ? ~0ULL : 0ULL;
+        if (threadIdx.x == 32) d.grid[0] = g;
+        if (threadIdx.x == 64) {
+            d.chain_E[0] = 0.0; d.chain_E[1] = 0.0; d.chain_E[2] = 0.0;
+            st->ncells = g.ncells;
+            st->pairs = 0;
+            st->nbr_total = 0;
+            st->guard = 0;
+            st->sasa_tests = 0;
+            st->max_nbr = 0;
+            st->nlong = 0;
+            if (!sFinite) {  // non-finite centres: the chain fails and the loop ends
+                d.chain_err[0] |= kErrNonfinite;
+                d.chain_done[0] = 1;
+                atomicOr(&st->error, kErrNonfinite);
+                st->done = 1;
+                export_status(d);
+            }
+        }
+    }
+    if (!sFinite) return;  // the same in every CTA (one box)
+    const int nc = g.ncells, per = (nc + C - 1) / C;
 
     // ---- cell counts
     int key0[kBcAtoms], rank0[kBcAtoms];

@@ -242,14 +242,16 @@ __device__ __forceinline__ bool covers64(double qx, double qy, double qz, double
 // every axis), and s >= the requested edge; s a multiple of 2^-10 A so that it is exact in float;
 // coarsened when the box would need more cells than the chain's cap. Leaves cbase to the caller.
 // Returns false for a non-finite box (the grid is then one cell at the origin).
-__device__ __forceinline__ bool grid_from_bounds(const DevChain& d, double* lo, double* hi, long long cap, GridInfo* out) {
+// (s_base, stencil and cell: DevChain's s_base, stencil and prm.cell_size)
+__device__ __forceinline__ bool grid_from_bounds_s(double s_base, int stencil, double cell, double* lo, double* hi,
+                                                   long long cap, GridInfo* out) {
     GridInfo g;
     const bool finite = isfinite(hi[0] - lo[0]) && isfinite(hi[1] - lo[1]) && isfinite(hi[2] - lo[2]);
     if (!finite)
         for (int i = 0; i < 3; ++i) { lo[i] = 0.0; hi[i] = 0.0; }
     const double ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
     // (the division by the stencil, 1 or 2, is exact: a multiplication)
-    double s = fmax(fma(1e-6, fmax(ext[0], fmax(ext[1], ext[2])), d.s_base) * (d.stencil == 2 ? 0.5 : 1.0), d.prm.cell_size);
+    double s = fmax(fma(1e-6, fmax(ext[0], fmax(ext[1], ext[2])), s_base) * (stencil == 2 ? 0.5 : 1.0), cell);
     s = ceil(s * 1024.0) * (1.0 / 1024.0);
     for (;;) {
         // n_i = floor(ext_i / s) + 1 estimated in float, then raised until n_i s > ext_i holds exactly
@@ -283,6 +285,9 @@ __device__ __forceinline__ bool grid_from_bounds(const DevChain& d, double* lo, 
     g.pad = 0;
     *out = g;
     return finite;
+}
+__device__ __forceinline__ bool grid_from_bounds(const DevChain& d, double* lo, double* hi, long long cap, GridInfo* out) {
+    return grid_from_bounds_s(d.s_base, d.stencil, d.prm.cell_size, lo, hi, cap, out);
 }
 
 __device__ __forceinline__ bool grid_from_box(const DevChain& d, const unsigned long long* kb, long long cap,

@@ -18,7 +18,7 @@ __host__ __device__ inline dbl4 make_dbl4(double x, double y, double z, double w
 // Uniform binning grid of Sec. 3.2 of one chain, rebuilt on the device every iteration. The cells
 // of all chains of a batch are numbered consecutively: chain c owns [cbase, cbase + ncells).
 struct GridInfo {
-    double ox, oy, oz;  // grid origin (bounding-box minimum)
+    double ox, oy, oz;  // FP64 mode: the grid origin (bounding-box minimum); mixed mode: 0 (the origin is of)
     double s;           // cell edge, a multiple of 2^-10 A so that it is exact in float
     float sf, inv_sf;   // the edge in float and its reciprocal
     float gpf;          // guard band of the FP32 cutoff tests (A^2), grows with the cell edge
@@ -88,6 +88,9 @@ struct DevChain {
     int ntiles = 0;      // transform-scan blocks of 32 * fk_j joints
     int fk_chain_tree = 0;  // every chain spans at most fk_tree_tiles() scan blocks: each apply block reduces
                             // the block products of its own chain before it (no scan of all of them)
+    int grid_in_bin = 0;    // set on the kinematics and binning launches of the step and evaluation graphs when
+                            // the cluster kernel bins: it forms the grid from the box (k_fk_apply has no
+                            // last-block tail then)
     int ltiles = 0;      // suffix-sum tiles of 32 links
     int cell_cap = 0;     // cells of all chains' caps
     long long cell_alloc = 0;  // cells the cell arrays hold

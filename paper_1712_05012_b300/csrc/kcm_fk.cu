@@ -27,6 +27,7 @@
 
 #include <type_traits>
 
+#include "kcm_cells.cuh"
 #include "kcm_common.cuh"
 #include "kcm_df.cuh"
 #include "kcm_device.h"
@@ -51,15 +52,15 @@ __device__ __forceinline__ bool chain_grid_t(const DevChain& d, int c, GridInfo*
         unsigned long long kb[6];  // every load before the first store
 #pragma unroll
         for (int i = 0; i < 6; ++i) kb[i] = __ldcg(&d.cbox[6 * c + i]);
-        double lo[3], hi[3];
+        df lo[3], hi[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            lo[i] = to_double(dfkey_inv(kb[i]));
-            hi[i] = to_double(dfkey_inv(kb[3 + i]));
+            lo[i] = dfkey_inv(kb[i]);
+            hi[i] = dfkey_inv(kb[3 + i]);
             d.cbox[6 * c + i] = ~0ULL;
             d.cbox[6 * c + 3 + i] = 0ULL;
         }
-        return grid_from_bounds(d, lo, hi, d.ccap[c], out);
+        return grid_from_bounds_df(d.s_base, d.stencil, d.prm.cell_size, lo, hi, d.ccap[c], out);
     }
 }
 
@@ -686,6 +687,7 @@ __global__ void __launch_bounds__(kFkWarps * 32) k_fk_apply(const DevChain d) {
             }
         }
     }
+    if (d.grid_in_bin) return;  // the cluster binning kernel forms the grid from the box
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) sLast = atomicAdd(&st->ticket_bbox, 1u) == gridDim.x - 1;
