@@ -32,7 +32,10 @@ namespace kcm {
 namespace {
 using namespace dev;
 
-constexpr int kPtWarps = 4;           // warps (independent work units) per block
+constexpr int kPtWarps = 1;           // warps (independent work units) per block: one, so that a
+                                      // finished warp's slot takes the next unit at once (with four, a
+                                      // block held its slots until its slowest unit ended: chain8000
+                                      // pairs 170 -> 145 us, batch 2.05 -> 1.61 ms)
 constexpr int kPtQueue = 32 * 32;     // in-range pairs of one tile at most
 constexpr int kPtFlushChunks = 8;     // staged rows between flushes of the home sums: 8 x 32 pieces of
                                       // |.| <= 2^22 stay within int32
@@ -41,7 +44,8 @@ constexpr float kPtFilterPad = 0.02f; // A^2 added to the filter's squared range
 // queue entry: staged index (bits 0-4), home index (5-9); the evaluation sets bit 10 for a solvation pair
 constexpr unsigned kQNear = 1u << 10;
 #ifndef KCM_PT_MIN_BLOCKS
-#define KCM_PT_MIN_BLOCKS 7  // resident blocks per SM the register budget is set for (shared memory allows 7)
+#define KCM_PT_MIN_BLOCKS 28  // resident blocks per SM the register budget is set for (72 registers;
+                              // shared memory allows 25 blocks of 8 KB)
 #endif
 
 // one warp's shared memory
