@@ -194,3 +194,44 @@ def test_autotune_tiles(kcm, table):
         assert ch.get_tiles() == (pw, sw, pp)
         with pytest.raises(kcm.KcmError):
             ch.autotune_tiles(reps=0)
+
+
+# A 600-residue chain, extended but for two kinks of three residues each, so that its three straight
+# segments point in different directions: its box (about 1,100 x 1,300 x 940 A) needs ~1.35 M cells of
+# the default edge against the chain's cap of 65,536, and the grid is coarsened (edge x 1.25 per step)
+# until it fits. (joint index, angle in rad) of the kinks; every other joint at the extended value.
+SPARSE_KINKS = [(400, -0.9104), (401, -0.0214), (402, -0.6128), (403, -0.2325), (404, 2.2295), (405, -0.5433),
+                (800, 1.5295), (801, 2.2393), (802, -0.5749), (803, -1.0016), (804, -2.5707), (805, 1.0907)]
+
+
+def test_sparse_box_coarsens(kcm, table):
+    """The coarsening path of both grid forms (FP64, and the mixed one in double-float and integer
+    arithmetic): the cell edge grows until the cells fit the cap, the pair set and the classification
+    stay the oracle's, torques within each precision's bar, and the mixed path's two binning kernels
+    (each forming the same grid) agree bit for bit."""
+    m = 600
+    seq = synth.sequence(m, 77)
+    th = synth.theta_extended(m).copy()
+    for j, v in SPARSE_KINKS:
+        th[j] = v
+    och = O.OracleChain(seq, table, synth.GEOMETRY)
+    ref = och.evaluate(synth.RunParams(precision=synth.PRECISION_FP64), th)
+    f64 = evaluate(kcm, seq, table, synth.RunParams(precision=synth.PRECISION_FP64), th)
+    mix = evaluate(kcm, seq, table, synth.RunParams(precision=synth.PRECISION_MIXED), th)
+    for o in (f64, mix):
+        assert o["stats"]["pairs"] == ref["stats"]["pairs"]
+        assert o["stats"]["cell_size"] > 15.0  # coarsened from ~10 A
+        assert o["stats"]["cells"] <= 65536
+    g = och.gamma != 0
+    assert np.array_equal(f64["covered"][g], ref["covered"][g])
+    assert np.array_equal(mix["covered"], f64["covered"])
+    assert rel_inf(f64["tau"], ref["tau"]) < TOL_FP64
+    assert rel_inf(mix["tau"], ref["tau"]) < TOL_MIXED
+    p = synth.RunParams(precision=synth.PRECISION_MIXED)
+    res = []
+    for kind in (kcm.BIN_CLUSTER, kcm.BIN_BLOCKS):
+        with kcm.Chain(seq, table, p) as ch:
+            ch.set_binning_kernel(kind)
+            ch.set_theta(th)
+            res.append((ch.torques(), ch.stats()["cell_size"], ch.stats()["cells"]))
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1:] == res[1][1:]
