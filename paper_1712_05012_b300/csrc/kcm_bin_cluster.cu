@@ -68,7 +68,9 @@ __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
     __shared__ int sOff[kBcMaxCtas + 1];
     __shared__ GridInfo sG;
     __shared__ bool sFinite;
-    if (d.grid_in_bin && threadIdx.x == 0) {  // the dummy box (1 A wide), before the wait; sG is rewritten
+    // the dummy box (1 A wide), before the wait for the kinematics (only with programmatic dependent
+    // launch: otherwise the kernel starts after them and the run would only add its time); sG is rewritten
+    if (d.grid_in_bin && d.pdl && threadIdx.x == 0) {
         const unsigned long long z = dfkey(df{0.0f, 0.0f}), o = dfkey(df{1.0f, 0.0f});
         sFinite = cluster_grid(z, z, z, o, o, o, d.s_base, d.stencil, d.prm.cell_size, 1 << 16, &sG);
     }
