@@ -289,6 +289,25 @@ def test_step_host_exchange(kcm, table, precision, step_mode, n_iters):
     host_vs_device(kcm, lambda: kcm.Chain(seq, table, p), th, n_iters, lambda c: c.set_fixed_joints(fixed))
 
 
+def test_step_host_exchange_side_joints(kcm, table):
+    """With side-chain joints the exchange carries the main-chain angles only; the side-chain angles
+    stay on the device and step with them (equal to the device loop's, bitwise)."""
+    seq, och, th = small_case(table, 25, 12)
+    p = synth.RunParams(precision=synth.PRECISION_MIXED, side_joints=1)
+    with kcm.Chain(seq, table, p) as a, kcm.Chain(seq, table, p) as b:
+        chi = np.linspace(-0.3, 0.3, a.ls)
+        a.set_side_theta(chi)
+        b.set_side_theta(chi)
+        out, it, dm = a.step_host(th, 3)
+        b.set_theta(th)
+        assert b.step(3) == (it, dm)
+        assert np.array_equal(out, b.get_theta())
+        assert np.array_equal(a.get_side_theta(), b.get_side_theta())
+        assert not np.array_equal(a.get_side_theta(), chi)  # the side-chain joints took steps
+        out0, it0, _ = a.step_host(th, 0)  # no iteration: the copies' path, theta back unchanged
+        assert it0 == 0 and np.array_equal(out0, th)
+
+
 def test_step_host_exchange_batch_convergence(kcm, table):
     """A batch whose chains stop at different iterations of one call (iteration caps and convergence):
     a stopped chain's angles stay as its last step left them, and the call's iteration count and max
