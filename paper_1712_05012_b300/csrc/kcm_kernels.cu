@@ -325,10 +325,11 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
     int ca = -1;  // chain of the home atom
     if (sl < d.n && !d.status->done) {
         const int a = d.sorted[sl];
+        const int scell = d.slot_cell[sl];  // loaded beside the atom (independent of it)
         ca = atom_chain(d, a);
-        if (!d.chain_done[ca]) {  // a converged chain takes no more steps: no forces needed
         const GridInfo g = d.grid[ca];  // the home atom's chain: its candidates are that chain's atoms
-        const int cell = d.slot_cell[sl] - g.cbase;
+        if (!d.chain_done[ca]) {  // a converged chain takes no more steps: no forces needed
+        const int cell = scell - g.cbase;
         const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
         // The non-empty rows, compacted in stencil order: first slot, offset of their candidates in
         // the concatenation, and (mixed) the row's shift ((cy_j - cy_i) s, (cz_j - cz_i) s). A cell
@@ -876,16 +877,16 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * W + w;
     if (a < d.n && !d.status->done) {
+        const int cnt0 = d.nbr_cnt[a];  // loaded beside the flags below (independent of them)
+        const float Ra = d.aprm32[a].w;
         if (d.chain_done[atom_chain(d, a)]) {  // a converged chain takes no more steps
             if (lane == 0) d.sstat[a] = make_int2(0, 0);
         } else if (!d.gflag[a]) {
             if (lane == 0) { d.covered[a] = 0; d.sstat[a] = make_int2(0, 0); }
         } else {
             // a list longer than kSasaStage is k_sasa_mixed_long's: nothing to do here, nothing written
-            const int cnt0 = d.nbr_cnt[a];
             const bool mine = cnt0 <= kSasaStage;
             const int cnt = min(mine ? cnt0 : 0, kSasaStage);
-            const float Ra = d.aprm32[a].w;
             const float inv2R = 0.5f / Ra;
             const float drf = d.f_dr;
             const float gd = 1e-4f + 1.2e-5f * d.grid[atom_chain(d, a)].sf;  // guard band in Q.o units (A)
