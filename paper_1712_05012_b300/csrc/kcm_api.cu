@@ -644,7 +644,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.ucurdf, 3 * l)) || (rc = dalloc(h, &d.pcurdf, 3 * l)) || (rc = dalloc(h, &d.G0f, nn)) ||
         (rc = dalloc(h, &d.M, 12 * (size_t)L)) || (rc = dalloc(h, &d.ucur, 3 * l)) || (rc = dalloc(h, &d.pcur, 3 * l)) ||
         (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.rank, nn)) ||
-        (rc = dalloc(h, &d.sorted, nn)) || (rc = dalloc(h, &d.sorted_tmp, nn)) || (rc = dalloc(h, &d.slot_cell, nn)) || (rc = dalloc(h, &d.smask, nn)) || (rc = dalloc(h, &d.spos64, nn)) ||
+        (rc = dalloc(h, &d.sorted, nn)) || (hc.nchains > 1 && (rc = dalloc(h, &d.slot_chain, nn))) || (rc = dalloc(h, &d.sorted_tmp, nn)) || (rc = dalloc(h, &d.slot_cell, nn)) || (rc = dalloc(h, &d.smask, nn)) || (rc = dalloc(h, &d.spos64, nn)) ||
         (rc = dalloc(h, &d.spos32, nn)) || (rc = dalloc(h, &d.sprm32, nn)) || (rc = dalloc(h, &d.sprm64, nn)) ||
         (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fpx, 3 * nn)) || (rc = dalloc(h, &d.Fov, 3 * nn)) ||
         (rc = dalloc(h, &d.gflag, nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||

@@ -68,6 +68,7 @@ __device__ __forceinline__ void reset_loop_state(const DevChain& d, int c, int n
 // ---------------------------------------------------------------- small helpers
 // chain of an atom or joint (no load for a single chain)
 __device__ __forceinline__ int atom_chain(const DevChain& d, int a) { return d.nchains == 1 ? 0 : d.atom_chain[a]; }
+__device__ __forceinline__ int slot_chain(const DevChain& d, int sl) { return d.nchains == 1 ? 0 : d.slot_chain[sl]; }
 __device__ __forceinline__ int joint_chain(const DevChain& d, int j) { return d.nchains == 1 ? 0 : d.joint_chain[j]; }
 
 __device__ __forceinline__ unsigned long long dkey(double x) {

@@ -167,6 +167,7 @@ struct DevChain {
     int* rank = nullptr;           // rank of each atom within its cell [n]
     int* scan_part = nullptr;      // block sums of the cell scan [scan_blocks]
     int* sorted = nullptr;         // slot -> atom [n]
+    int* slot_chain = nullptr;     // batches: slot -> chain [n] (the pair kernels' first load, beside the atom)
     int* sorted_tmp = nullptr;     // FP64 mode: slot -> atom in the order of the atomic ranks, before the
                                    // atoms of each cell are put in atom order [n]
     int* slot_cell = nullptr;      // slot -> cell [n]

@@ -239,8 +239,10 @@ __global__ void k_bin_place(const DevChain d) {
         d.sorted_tmp[sl] = a;
         return;
     }
-    const GridInfo g = d.grid[atom_chain(d, a)];
+    const int ca = atom_chain(d, a);
+    const GridInfo g = d.grid[ca];
     d.sorted[sl] = a;
+    if (d.nchains > 1) d.slot_chain[sl] = ca;
     d.slot_cell[sl] = key;
     d.smask[sl] = make_ulonglong2(d.exm[a], d.m14m[a]);  // bond classes in slot order (no dependent load later)
     if (MIXED) {
@@ -273,6 +275,7 @@ __global__ void k_bin_stable(const DevChain d) {
     for (int t = cs; t < ce; ++t) r += d.sorted_tmp[t] < a;
     const int sl = cs + r;
     d.sorted[sl] = a;
+    if (d.nchains > 1) d.slot_chain[sl] = atom_chain(d, a);
     d.slot_cell[sl] = key;
     d.smask[sl] = make_ulonglong2(d.exm[a], d.m14m[a]);
     const dbl4 p = d.aprm64[a];
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
     if (sl < d.n && !d.status->done) {
         const int a = d.sorted[sl];
         const int scell = d.slot_cell[sl];  // loaded beside the atom (independent of it)
-        ca = atom_chain(d, a);
+        ca = slot_chain(d, sl);
         const GridInfo g = d.grid[ca];  // the home atom's chain: its candidates are that chain's atoms
         if (!d.chain_done[ca]) {  // a converged chain takes no more steps: no forces needed
         const int cell = scell - g.cbase;

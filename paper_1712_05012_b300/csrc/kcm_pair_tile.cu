@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kPtWarps * 32, KCM_PT_MIN_BLOCKS) k_pair_tile(
     bool done = true;
     if (valid) {
         key = d.slot_cell[sl];
-        ca = atom_chain(d, d.sorted[sl]);
+        ca = slot_chain(d, sl);
         done = d.chain_done[ca] != 0;
         const GridInfo* gp = &d.grid[ca];
         nx = gp->nx; ny = gp->ny; nz = gp->nz; cbase = gp->cbase;
