@@ -880,11 +880,14 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * W + w;
     if (a < d.n && !d.status->done) {
+        const int ca = atom_chain(d, a);
         const int cnt0 = d.nbr_cnt[a];  // loaded beside the flags below (independent of them)
         const float Ra = d.aprm32[a].w;
-        if (d.chain_done[atom_chain(d, a)]) {  // a converged chain takes no more steps
+        const bool gam = d.gflag[a] != 0;
+        const float gsf = d.grid[ca].sf;
+        if (d.chain_done[ca]) {  // a converged chain takes no more steps
             if (lane == 0) d.sstat[a] = make_int2(0, 0);
-        } else if (!d.gflag[a]) {
+        } else if (!gam) {
             if (lane == 0) { d.covered[a] = 0; d.sstat[a] = make_int2(0, 0); }
         } else {
             // a list longer than kSasaStage is k_sasa_mixed_long's: nothing to do here, nothing written
@@ -892,7 +895,7 @@ __global__ void __launch_bounds__(W * 32) k_sasa_mixed(const DevChain d) {
             const int cnt = min(mine ? cnt0 : 0, kSasaStage);
             const float inv2R = 0.5f / Ra;
             const float drf = d.f_dr;
-            const float gd = 1e-4f + 1.2e-5f * d.grid[atom_chain(d, a)].sf;  // guard band in Q.o units (A)
+            const float gd = 1e-4f + 1.2e-5f * gsf;  // guard band in Q.o units (A)
             float rmax2 = 0.0f;
             for (int j = lane; j < cnt; j += 32) {
                 const float4 o = d.nbr_off[(size_t)a * kMaxNbr + j];  // r_j - r_i, Roff_j^2
