@@ -612,6 +612,11 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         d.fk_chain_tree = span <= kcm::fk_tree_tiles() ? 1 : 0;
     }
     d.ltiles = (d.L + 31) / 32;
+    {
+        const int rb = kcm::wrench_resident_blocks(d);
+        if (rb < 0) cudaGetLastError();
+        d.wrench_static = rb > 0 && (long long)rb * h->sm_count >= d.ltiles ? 1 : 0;
+    }
     d.nchains = hc.nchains;
     d.rcut2 = prm->cutoff * prm->cutoff;
     double rv = prm->vdw_cutoff > 0.0 ? prm->vdw_cutoff : prm->cutoff;

@@ -92,6 +92,8 @@ struct DevChain {
                             // the cluster kernel bins: it forms the grid from the box (k_fk_apply has no
                             // last-block tail then)
     int ltiles = 0;      // suffix-sum tiles of 32 links
+    int wrench_static = 0;  // every wrench block is resident at once: block b takes tile ltiles - 1 - b
+                            // (no ticket round trip before its first load)
     int cell_cap = 0;     // cells of all chains' caps
     long long cell_alloc = 0;  // cells the cell arrays hold
     int pair_warps = 1, sasa_warps = 1;  // tile shapes: atoms per block of k_pair and of k_sasa_mixed / k_sasa_pw
@@ -250,6 +252,7 @@ void launch_pairs(DevChain& d, cudaStream_t s);
 void launch_pairs_tile(DevChain& d, cudaStream_t s);  // kcm_pair_tile.cu
 int pair_tile_rows(int stencil);                      // warps per window of 32 slots of k_pair_tile
 int pair_resident_blocks(const DevChain& d);  // resident blocks per SM of the current pair kernel (-1: error)
+int wrench_resident_blocks(const DevChain& d);  // resident blocks per SM of the wrench kernels (-1: error)
 void launch_sasa(DevChain& d, cudaStream_t s);
 void launch_sasa_long(DevChain& d, cudaStream_t s);  // atoms with more than kSasaStage neighbours
 void launch_torques(DevChain& d, cudaStream_t s);

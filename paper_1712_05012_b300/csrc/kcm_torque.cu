@@ -168,7 +168,9 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_step(const DevChai
     Status* st = d.status;
     if (st->done) return;
     if (threadIdx.x == 0) {
-        sTile = d.ltiles - 1 - (int)atomicAdd(&st->ticket_lb, 1u);  // later tiles first
+        // later tiles first: by ticket, so that a block that waits for later tiles never holds the slot
+        // one of them needs; by block index where every block is resident at once
+        sTile = d.ltiles - 1 - (d.wrench_static ? (int)blockIdx.x : (int)atomicAdd(&st->ticket_lb, 1u));
         sEpoch = __ldcg(d.lb_epoch) + 1u;
         sTimeout = false;
         sEnd = 0x7fffffff;
@@ -509,6 +511,24 @@ template <class T, bool STEP>
 void launch_wrench_step(DevChain& d, cudaStream_t s) {
     if (d.ls) launch_k(k_wrench_step<T, true, STEP>, d.ltiles, kWrenchWarps * 32, 0, s, d.pdl, d);
     else launch_k(k_wrench_step<T, false, STEP>, d.ltiles, kWrenchWarps * 32, 0, s, d.pdl, d);
+}
+
+// the fewest resident blocks per SM over the wrench kernel's forms (their resources differ a little)
+int wrench_resident_blocks(const DevChain& d) {
+    int best = 1 << 30;
+    auto q = [&](auto kernel) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kWrenchWarps * 32, 0) != cudaSuccess) nb = -1;
+        best = std::min(best, nb);
+    };
+    if (d.prm.precision == KCM_MIXED) {
+        q(k_wrench_step<df, false, false>); q(k_wrench_step<df, false, true>);
+        q(k_wrench_step<df, true, false>); q(k_wrench_step<df, true, true>);
+    } else {
+        q(k_wrench_step<double, false, false>); q(k_wrench_step<double, false, true>);
+        q(k_wrench_step<double, true, false>); q(k_wrench_step<double, true, true>);
+    }
+    return best;
 }
 
 void launch_torques(DevChain& d, cudaStream_t s) {
