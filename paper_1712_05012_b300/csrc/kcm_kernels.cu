@@ -329,6 +329,8 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
     if (sl < d.n && !d.status->done) {
         const int a = d.sorted[sl];
         const int scell = d.slot_cell[sl];  // loaded beside the atom (independent of it)
+        float4 hpos = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // mixed: the home atom's offset, likewise
+        if constexpr (MIXED) hpos = d.spos32[sl];
         ca = slot_chain(d, sl);
         const GridInfo g = d.grid[ca];  // the home atom's chain: its candidates are that chain's atoms
         if (!d.chain_done[ca]) {  // a converged chain takes no more steps: no forces needed
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
             if (ncy >= 0 && ncy < g.ny && ncz >= 0 && ncz < g.nz) {
                 R hx, hy, hz, es, reach2;
                 if constexpr (MIXED) {
-                    const float4 hp = d.spos32[sl];  // offset from the home cell's corner
+                    const float4 hp = hpos;  // offset from the home cell's corner
                     hx = hp.x; hy = hp.y; hz = hp.z; es = g.sf; reach2 = d.f_rall2;
                 } else {
                     const dbl4 hp = d.spos64[sl];
@@ -413,7 +415,7 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
         R px, py, pz, qi, sei, Ri, Roi;
         float fcx = 0.0f;  // mixed: the home cell's x index
         if constexpr (MIXED) {
-            float4 p = d.spos32[sl], q = d.sprm32[sl];
+            float4 p = hpos, q = d.sprm32[sl];
             px = p.x; py = p.y; pz = p.z; fcx = p.w; qi = q.x; sei = q.y; Ri = q.z; Roi = q.w;
         } else {
             dbl4 p = d.spos64[sl], q = d.sprm64[sl];
