@@ -96,6 +96,15 @@ __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
     for (int i = threadIdx.x; i < d.bin_capc / 4; i += blockDim.x) sCell4[i] = make_int4(0, 0, 0, 0);
     const int a0 = (int)((long long)d.n * b / C), a1 = (int)((long long)d.n * (b + 1) / C);  // <= kBcAtoms each
     const df* rdf = reinterpret_cast<const df*>(d.rdf);
+    // the thread's centres, loaded now so that they arrive while the grid is formed
+    df p0[kBcAtoms][3];
+#pragma unroll
+    for (int k = 0; k < kBcAtoms; ++k) {
+        const int at = a0 + k * kBcThreads + (int)threadIdx.x;
+        if (at < a1) {
+            p0[k][0] = rdf[3 * at]; p0[k][1] = rdf[3 * at + 1]; p0[k][2] = rdf[3 * at + 2];
+        }
+    }
     cl.sync();  // (1) every CTA's counts are zero, and every CTA has the grid
     const GridInfo g = sG;
     if (d.grid_in_bin && b == 0) {
@@ -126,13 +135,12 @@ __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
 
     // ---- cell counts
     int key0[kBcAtoms], rank0[kBcAtoms];
-    df p0[kBcAtoms][3];
     {
 #pragma unroll
         for (int k = 0; k < kBcAtoms; ++k) {
             const int at = a0 + k * kBcThreads + (int)threadIdx.x;
             if (at >= a1) continue;
-            const df px = rdf[3 * at], py = rdf[3 * at + 1], pz = rdf[3 * at + 2];
+            const df px = p0[k][0], py = p0[k][1], pz = p0[k][2];
             const int cx = mixed_cell_axis(px, g.of[0], g.inv_sf, g.nx);
             const int cy = mixed_cell_axis(py, g.of[1], g.inv_sf, g.ny);
             const int cz = mixed_cell_axis(pz, g.of[2], g.inv_sf, g.nz);
@@ -145,7 +153,6 @@ __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
             rk = __shfl_sync(peers, rk, leader) + __popc(peers & ((1u << lane) - 1u));
             key0[k] = key;
             rank0[k] = rk;
-            p0[k][0] = px; p0[k][1] = py; p0[k][2] = pz;
         }
     }
     cl.sync();  // (2) every count
