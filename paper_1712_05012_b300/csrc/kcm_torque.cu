@@ -362,13 +362,20 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_step(const DevChai
     for (int k = 0; k < 6; ++k) acc[k] = num_f<T>(0.0f);
     // uniform: needed unless a chain ends at the tile's last link (then no link of the tile reaches past it)
     if (!sTL[h1 - h0 - 1]) {
+        // the tile that holds the last link of the chain of the tile's last link (the last link of chain c
+        // is joint_off[c + 1] + c): no later tile is waited for, although a round may reach past it
+        int te = d.ltiles - 1;
+        if (d.nchains > 1) {
+            const int ce = d.link_chain[h1 - 1];
+            te = (d.joint_off[ce + 1] + ce) >> 5;
+        }
         for (int base = t + 1; base < d.ltiles; base += blockDim.x) {  // uniform
             const int tt = base + threadIdx.x;
             T v[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) v[k] = num_f<T>(0.0f);
             bool ends = false;
-            if (tt < d.ltiles) {
+            if (tt <= te) {
                 if (!wait_published(&d.tileStat[tt], epoch)) {
                     sTimeout = true;
                 } else {
