@@ -719,6 +719,9 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = upload(h, d.lflag, lflag.data(), L)) || (rc = upload(h, d.u0df, u0df.data(), 3 * l)) ||
         (rc = upload(h, d.step0df, step0df.data(), 3 * l)) || (rc = upload(h, d.r0df, r0df.data(), 3 * nn)))
         return bail(rc);
+    if (hc.nchains > 1 && prm->precision == KCM_MIXED &&  // the per-chain binning kernel's chain ranges
+        ((rc = dalloc(h, &d.atom_off, hc.nchains + 1)) || (rc = upload(h, d.atom_off, hc.atom_off.data(), hc.nchains + 1))))
+        return bail(rc);
     if ((rc = set_cell_size(h, prm->cell_size))) return bail(rc);  // cell caps and arrays
     // the offsets the FK reads: the static ones, or with side-chain joints a copy that k_side_fk
     // rewrites for the side atoms they move

@@ -200,6 +200,7 @@ struct DevChain {
     int* joint_chain = nullptr;    // [l]
     int* link_chain = nullptr;     // [L]
     int* joint_off = nullptr;      // [nchains + 1]
+    int* atom_off = nullptr;       // batches in mixed mode: first atom of each chain [nchains + 1]
     int* ccap = nullptr;           // [nchains]
     unsigned long long* cbox = nullptr;       // [nchains * 6]
     int* chain_done = nullptr;     // converged (the chain takes no more steps) [nchains]

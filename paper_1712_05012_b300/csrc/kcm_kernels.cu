@@ -262,6 +262,104 @@ __global__ void k_bin_place(const DevChain d) {
     }
 }
 
+// Mixed-mode batches: the cells, ranks and cell starts of every chain in one launch, one block per
+// chain (in place of the count kernel and the two scan kernels). A chain's cells are consecutive in
+// the global cell numbering and hold exactly its atoms, so its slots are [atom_off[c], atom_off[c + 1])
+// and a block sorts its chain alone: the cell and rank of each atom from atomics on counts in shared
+// memory (in the chain's part of the global counts when its grid has more than kBinChainCells cells,
+// which the scan leaves at zero again), then a block scan of the counts into the cell starts.
+// k_bin_place<true> then places the atoms, one thread each. The cell arithmetic is that of
+// k_bin_count; only the order of the atoms within a cell (from atomics, as there) can differ, and no
+// mixed-mode result depends on it.
+constexpr int kBinChainThreads = 1024;
+constexpr int kBinChainCells = 8192;
+constexpr int kBinChainBatch = 1;  // atoms per thread whose centres are loaded together (two loaded together spill at the
+                                   // 32 registers of two blocks per SM, and measured 1-2 us slower on the batch)
+
+__global__ void __launch_bounds__(kBinChainThreads, 2) k_bin_chains(const DevChain d) {
+    grid_dep_sync();
+    __shared__ int scnt[kBinChainCells];
+    __shared__ int ws[kBinChainThreads / 32];
+    if (d.status->done) return;
+    const int c = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const GridInfo g = d.grid[c];
+    const int a0 = d.atom_off[c], a1 = d.atom_off[c + 1];
+    const int nc = g.ncells;
+    const bool sm = nc <= kBinChainCells;
+    int* cnt = sm ? scnt : d.cell_count + g.cbase;
+    if (sm)
+        for (int k = t; k < nc; k += kBinChainThreads) scnt[k] = 0;
+    __syncthreads();
+    const df* rdf = reinterpret_cast<const df*>(d.rdf);
+    for (int ab = a0; ab < a1; ab += kBinChainBatch * kBinChainThreads) {  // uniform
+        df p[kBinChainBatch][3];
+#pragma unroll
+        for (int i = 0; i < kBinChainBatch; ++i) {
+            const int a = ab + i * kBinChainThreads + t;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) p[i][k] = a < a1 ? rdf[3 * a + k] : df{0.0f, 0.0f};
+        }
+#pragma unroll
+        for (int i = 0; i < kBinChainBatch; ++i) {
+            const int a = ab + i * kBinChainThreads + t;
+            if (a < a1) {
+                const int cx = mixed_cell_axis(p[i][0], g.of[0], g.inv_sf, g.nx);
+                const int cy = mixed_cell_axis(p[i][1], g.of[1], g.inv_sf, g.ny);
+                const int cz = mixed_cell_axis(p[i][2], g.of[2], g.inv_sf, g.nz);
+                const int lk = (cz * g.ny + cy) * g.nx + cx;
+                d.key[a] = g.cbase + lk;
+                const unsigned peers = __match_any_sync(__activemask(), lk);
+                const int leader = __ffs(peers) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&cnt[lk], __popc(peers));
+                base = __shfl_sync(peers, base, leader);
+                d.rank[a] = base + __popc(peers & ((1u << lane) - 1u));
+            }
+        }
+    }
+    __syncthreads();
+    // exclusive scan of the counts, four consecutive cells per thread and pass; cell_start holds slots
+    int carry = 0;
+    for (int c0 = 0; c0 < nc; c0 += 4 * kBinChainThreads) {  // uniform
+        const int cb = c0 + 4 * t;
+        int k[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)  // global counts from L2: a line may be in L1 from a neighbouring chain's block
+            k[q] = cb + q >= nc ? 0 : (sm ? scnt[cb + q] : __ldcg(&cnt[cb + q]));
+        const int local = k[0] + k[1] + k[2] + k[3];
+        int v = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) ws[w] = v;
+        __syncthreads();
+        if (w == 0) {
+            int x = ws[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            ws[lane] = x;
+        }
+        __syncthreads();
+        int run = carry + v - local + (w > 0 ? ws[w - 1] : 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (cb + q < nc) {
+                d.cell_start[g.cbase + cb + q] = a0 + run;
+                if (!sm) cnt[cb + q] = 0;  // global counts are left at zero for the next evaluation
+                run += k[q];
+            }
+        }
+        carry += ws[kBinChainThreads / 32 - 1];
+        __syncthreads();
+    }
+    if (t == 0) d.cell_start[g.cbase + nc] = a0 + carry;  // = a1: the next chain's first cell start
+}
+
 // FP64 mode: the atoms of each cell in atom order (a stable counting sort): the atom at slot s of the
 // placement by atomic ranks takes slot (cell start) + (atoms of its cell with a smaller index)
 __global__ void k_bin_stable(const DevChain d) {
@@ -1354,6 +1452,11 @@ void launch_reset_loop(DevChain& d, cudaStream_t s) { launch_k(k_reset_loop, blo
 void launch_binning(DevChain& d, cudaStream_t s) {
     if (d.bin_c) {  // a single chain in mixed mode: one cluster
         launch_bin_cluster(d, s);
+        return;
+    }
+    if (d.atom_off) {  // a batch in mixed mode: cells and starts by one block per chain, then the placement
+        launch_k(k_bin_chains, d.nchains, kBinChainThreads, 0, s, d.pdl, d);
+        launch_k(k_bin_place<true>, blocks(d.n, 256), 256, 0, s, d.pdl, d);
         return;
     }
     launch_k(k_bin_count, blocks(d.n, kBinThreads), kBinThreads, 0, s, d.pdl, d);

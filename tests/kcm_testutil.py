@@ -125,3 +125,11 @@ def fk_extended(och, theta):
             out[g + 1] = rCA + M @ (nstep[i] + loc[g + 1] - loc[aCA])
             rN = out[g]
     return out
+
+
+# A 600-residue chain, extended but for two kinks of three residues each, so that its three straight
+# segments point in different directions: its box (about 1,100 x 1,300 x 940 A) needs ~1.35 M cells of
+# the default edge against the chain's cap of 65,536, and the grid is coarsened (edge x 1.25 per step)
+# until it fits. (joint index, angle in rad) of the kinks; every other joint at the extended value.
+SPARSE_KINKS = [(400, -0.9104), (401, -0.0214), (402, -0.6128), (403, -0.2325), (404, 2.2295), (405, -0.5433),
+                (800, 1.5295), (801, 2.2393), (802, -0.5749), (803, -1.0016), (804, -2.5707), (805, 1.0907)]

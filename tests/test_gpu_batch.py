@@ -9,7 +9,7 @@ import pytest
 from oracle import oracle as O
 from paper_1712_05012_b300 import synth
 
-from kcm_testutil import rel_inf, tol_positions
+from kcm_testutil import SPARSE_KINKS, rel_inf, tol_positions
 
 pytestmark = pytest.mark.gpu
 
@@ -181,3 +181,38 @@ def test_batch_chain_fails_alone(kcm, table):
         ch.step(4)
         assert np.max(np.abs(th[1] - ch.get_theta())) < 1e-9
 
+
+
+def test_batch_binning_large_grid(kcm, table):
+    """Mixed batches bin each chain in one block, counting its cells in shared memory up to 8,192 cells
+    and in global memory beyond. A 600-residue chain kinked into three straight segments (its grid is
+    coarsened to its cap of 8 x 6,290 cells, far above 8,192) beside two compact chains: the mixed batch
+    finds the FP64 batch's pair set and covered counts exactly (and a superset of its solvation lists), and every chain's torques agree with
+    the FP64 batch within the mixed bar; the compact chains also match their evaluation alone."""
+    m = 600
+    seq_k = synth.sequence(m, 77)
+    th_k = synth.theta_extended(m).copy()
+    for j, v in SPARSE_KINKS:
+        th_k[j] = v
+    seqs, thetas = [seq_k], [th_k]
+    for mm, seed in ((97, 16), (17, 14)):
+        s = synth.sequence(mm, seed)
+        seqs.append(s)
+        thetas.append(synth.theta_from_codes(O.OracleChain(s, table, synth.GEOMETRY).grow_start(seed)))
+    out = {}
+    for prec in (synth.PRECISION_FP64, synth.PRECISION_MIXED):
+        p = synth.RunParams(precision=prec)
+        with kcm.Batch(seqs, table, p) as b:
+            b.set_theta(np.concatenate(thetas))
+            out[prec] = dict(tau=b.split(b.torques(), per="joint"), covered=b.sasa_counts(), stats=b.stats())
+    mix, f64 = out[synth.PRECISION_MIXED], out[synth.PRECISION_FP64]
+    assert mix["stats"]["cells"] > 8192
+    assert mix["stats"]["pairs"] == f64["stats"]["pairs"]
+    assert mix["stats"]["sasa_neighbors"] >= f64["stats"]["sasa_neighbors"]  # FP32 lists keep a margin
+    assert np.array_equal(mix["covered"], f64["covered"])
+    for c in range(len(seqs)):
+        assert rel_inf(mix["tau"][c], f64["tau"][c]) < 1e-4, c
+    pm = synth.RunParams(precision=synth.PRECISION_MIXED)
+    for c in (1, 2):
+        ref = alone(kcm, seqs[c], table, pm, thetas[c])
+        assert rel_inf(mix["tau"][c], ref["tau"]) < 1e-9, c

@@ -11,7 +11,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from kcm_testutil import rel_inf
+from kcm_testutil import SPARSE_KINKS, rel_inf
 from oracle import oracle as O
 from paper_1712_05012_b300 import synth
 
@@ -196,12 +196,6 @@ def test_autotune_tiles(kcm, table):
             ch.autotune_tiles(reps=0)
 
 
-# A 600-residue chain, extended but for two kinks of three residues each, so that its three straight
-# segments point in different directions: its box (about 1,100 x 1,300 x 940 A) needs ~1.35 M cells of
-# the default edge against the chain's cap of 65,536, and the grid is coarsened (edge x 1.25 per step)
-# until it fits. (joint index, angle in rad) of the kinks; every other joint at the extended value.
-SPARSE_KINKS = [(400, -0.9104), (401, -0.0214), (402, -0.6128), (403, -0.2325), (404, 2.2295), (405, -0.5433),
-                (800, 1.5295), (801, 2.2393), (802, -0.5749), (803, -1.0016), (804, -2.5707), (805, 1.0907)]
 
 
 def test_sparse_box_coarsens(kcm, table):
