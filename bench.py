@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--chain8000-steps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-iters", type=int, default=200)
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="K",
+                    help="profiling workload only: the first K chains of the batch workload, mixed precision, "
+                         "stepped from their stored starts four times (a few GB on the device for one-kernel ncu "
+                         "captures); prints one line of sizes, no measurement")
     return ap.parse_args()
 
 
@@ -722,10 +726,30 @@ def run_ours(args):
     return 0
 
 
+def run_profile_batch(k):
+    """The first k chains of the batch workload, stepped four times from their stored starts: a small
+    case of the batch's kernels for ncu captures that collect more than launch times."""
+    import torch
+
+    from paper_1712_05012_b300 import kcm, synth
+
+    torch.cuda.set_device(0)
+    seqs, theta, _ = batch_workload()
+    with kcm.Batch(seqs[:k], synth.type_table(), synth.RunParams(precision=synth.PRECISION_MIXED)) as bb:
+        for _ in range(4):
+            bb.set_theta(theta[:bb.l])  # the chains' joints come first in the concatenated starts
+            bb.step(1)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_batch": {"chains": bb.nchains, "atoms": bb.n, "joints": bb.l, "steps": 4}}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_batch > 0:
+        return run_profile_batch(args.profile_batch)
     return run_ours(args)
 
 
