@@ -51,6 +51,7 @@ BYTES_PER_ATOM = {"kinematics": 80, "binning": 50, "torques_step": 60}  # algori
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it is built now; a stage
 # left out has no capture of its current kernel
 DRAM_BYTES_PER_LAUNCH = {"solvation": 6.84e6}
+BATCH_ORACLE_STRIDE = 32  # chains of the batch checked against the oracle: 16 of 512
 MIXED_DTYPE = "f32 pair/solvation; double-float (~48-bit) kinematics, wrenches and torque scans"
 
 
@@ -609,6 +610,9 @@ def run_ours(args):
             prep_b()
             bkind, bkind_ms = bb.autotune_pair_kernel(reps=2)
             btiles = bb.get_tiles()
+            prep_b()
+            btau_start = bb.split(bb.torques(), per="joint")  # compared with the oracle's in the oracle leg
+            bthetas = bb.split(np.asarray(btheta), per="joint")
             for _ in range(3):
                 prep_b()
                 bb.step_timed()
@@ -688,6 +692,16 @@ def run_ours(args):
             chain8000["mixed"]["rooflines"] = stage_rooflines(
                 chain8000["mixed"]["stage_ms"], {"pairs": chain8000["mixed"]["pairs"]}, chain8000["atoms"],
                 fp32_peak, peaks, ref8["stats"]["sasa_tests1"] + ref8["stats"]["sasa_tests2"])
+        if batch is not None:  # a sample of the batch's chains, each against the oracle alone
+            from oracle import oracle as O
+            t0 = time.perf_counter()
+            sample = list(range(0, len(bseqs), BATCH_ORACLE_STRIDE))
+            errs = [rel_err(btau_start[c], O.OracleChain(bseqs[c], table, synth.GEOMETRY).evaluate(
+                synth.RunParams(precision=synth.PRECISION_FP64), bthetas[c])["tau"]) for c in sample]
+            accuracy["batch"] = {"torque_rel_err": max(errs), "chains": len(sample),
+                                 "sample": f"chains 0, {BATCH_ORACLE_STRIDE}, {2 * BATCH_ORACLE_STRIDE}, ... of the batch, each against the "
+                                           f"FP64 oracle alone; the largest error",
+                                 "oracle_s": time.perf_counter() - t0}
 
     # rooflines of every stage; the dominant one is the headline "roofline"
     rooflines = stage_rooflines(ms_stage, stats, n, fp32_peak, peaks, sasa_oracle)
