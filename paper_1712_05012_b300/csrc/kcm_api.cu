@@ -599,18 +599,24 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         if (hc.link_start[h1] - hc.link_start[h0] > kcm::kWrenchTileAtoms)
             return bail(set_err(h, KCM_E_INVAL, "32 consecutive links hold more atoms than the wrench tile"));
     }
-    d.fk_j = kcm::fk_joints_per_lane(d.l);
     const int fkq = kcm::fk_block_joints();
-    d.ntiles = (d.l + fkq * d.fk_j - 1) / (fkq * d.fk_j);
-    {  // every chain within kcm::kFkTreeTiles scan blocks: the apply kernel reduces its chain's earlier block
-       // products itself, and no kernel scans all of them
+    // scan blocks spanned by the longest chain with J joints per lane
+    auto chain_span = [&](int J) {
         int span = 0;
         for (int c = 0; c < hc.nchains; ++c) {
             const int j0 = hc.joint_off[c], j1 = hc.joint_off[c + 1];
-            if (j1 > j0) span = std::max(span, (j1 - 1) / (fkq * d.fk_j) - j0 / (fkq * d.fk_j) + 1);
+            if (j1 > j0) span = std::max(span, (j1 - 1) / (fkq * J) - j0 / (fkq * J) + 1);
         }
-        d.fk_chain_tree = span <= kcm::fk_tree_tiles() ? 1 : 0;
-    }
+        return span;
+    };
+    // Batches take two joints per lane wherever every chain then lies within kcm::kFkTreeTiles scan blocks
+    // (measured on the 512-chain batch: kinematics 213, 185, 191 and 216 us with 1, 2, 4 and 8 joints per
+    // lane); otherwise, and for a single chain, as few as keep the scan blocks within what k_fk_tiles scans.
+    d.fk_j = hc.nchains > 1 && chain_span(2) <= kcm::fk_tree_tiles() ? 2 : kcm::fk_joints_per_lane(d.l);
+    d.ntiles = (d.l + fkq * d.fk_j - 1) / (fkq * d.fk_j);
+    // every chain within kcm::kFkTreeTiles scan blocks: the apply kernel reduces its chain's earlier block
+    // products itself, and no kernel scans all of them
+    d.fk_chain_tree = chain_span(d.fk_j) <= kcm::fk_tree_tiles() ? 1 : 0;
     d.ltiles = (d.L + 31) / 32;
     {
         const int rb = kcm::wrench_resident_blocks(d);
