@@ -608,6 +608,8 @@ def run_ours(args):
                     flush.add_(1)
 
             prep_b()
+            bcell, bcand_ms = bb.autotune_cell(candidates=(6.0, 7.0, 8.0, 9.0, 10.0, 12.0), reps=2)
+            prep_b()
             bkind, bkind_ms = bb.autotune_pair_kernel(reps=2)
             btiles = bb.get_tiles()
             prep_b()
@@ -626,6 +628,8 @@ def run_ours(args):
                      "ms_per_step": sum(tt) / args.batch_steps,
                      "stage_ms": stg,
                      "steps": args.batch_steps, "pairs": bst["pairs"], "sasa_tests": bst["sasa_tests"],
+                     "cell_size": bcell, "autotune_ms": dict(zip(("6", "7", "8", "9", "10", "12"),
+                                                                  [float(x) for x in bcand_ms])),
                      "rooflines": stage_rooflines(stg, bst, bb.n, fp32_peak, peaks),
                      "tiles": {"chosen": list(btiles), "order": "[pair warps or tile split][solvation warps][persistent pair grid]",
                                "pair_kernel": "cell_tiles" if bkind == kcm.PAIR_CELL_TILES else "warp_per_atom",
