@@ -58,7 +58,10 @@ constexpr int kBcWarps = kBcThreads / 32;
 constexpr int kBcAtoms = 2;                       // most atoms per thread
 constexpr int kBcMaxCtas = 16;
 constexpr int kBcMaxCells = 52 * 1024;            // most cells of a CTA's range (208 KB of shared memory)
-constexpr int kBcAtomsPerCta = 1024;              // atoms per CTA the plan aims at (one per thread)
+constexpr int kBcAtomsPerCta = 512;               // atoms per CTA the plan aims at (half the threads: the
+                                                  // shorter ranges of cells and atoms per CTA end sooner;
+                                                  // 1,000-residue chain with 16 CTAs instead of 11: binning
+                                                  // 16.1 -> 14.4 us, 95.0 -> 93.9 us per iteration)
 
 __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
     extern __shared__ int4 sCell4[];  // the CTA's cell counts, then their starts within the range

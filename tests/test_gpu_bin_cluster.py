@@ -8,7 +8,7 @@ from atomics). The pair sums are exact integer sums and Algorithm 1 does not dep
 list, so positions, pair and solvation forces, torques and whole trajectories are equal bit for bit;
 energies are FP32 sums in another order (1e-5), and so is the pairwise surrogate's product over a list
 (compared per evaluation, 1e-5). The cluster shapes cover the two ways the CTAs are
-counted: by atoms (1,024 per CTA, at most 16; chains of up to 32,768 atoms) and by the cell cap (at most
+counted: by atoms (512 per CTA, at most 16; chains of up to 32,768 atoms) and by the cell cap (at most
 53,248 cells per CTA); then which handles take which kernel."""
 import json
 import os
@@ -41,7 +41,7 @@ def start(name):
 
 
 def expected_ctas(n, cap):
-    return min(16, max(1, -(-n // 1024), -(-cap // 53248)))
+    return min(16, max(1, -(-n // 512), -(-cap // 53248)))
 
 
 def run(kcm, seq, table, p, th, kind, cell=None, steps=3):
@@ -99,8 +99,8 @@ def test_cluster_binning_shapes(kcm, table, m, solvation):
 
 @pytest.mark.parametrize("cell", [None, 5.0])
 def test_cluster_binning_chain1000(kcm, table, cell):
-    """The benchmark's workload (10,506 atoms: 11 CTAs), at the default edge and at 5 A (the 125-cell
-    stencil: a cap of 672,384 cells, 13 CTAs of 51,722)."""
+    """The benchmark's workload (10,506 atoms: 16 CTAs), at the default edge and at 5 A (the 125-cell
+    stencil: a cap of 672,384 cells, 16 CTAs of 42,024)."""
     seq, th = start("chain1000")
     och = O.OracleChain(seq, table, synth.GEOMETRY)
     check(kcm, table, seq, th, och, cell=cell)
