@@ -431,12 +431,15 @@ def run_ours(args):
     # pair kernel (warp per atom or cell-pair tiles) and tile shapes from the library's autotuner, at the
     # start conformation, before the warm-up
     prepare(ch, lib_stream)
+    cell_main, cell_main_ms = ch.autotune_cell(candidates=(6.0, 7.0, 8.0, 9.0, 10.0, 12.0), reps=20)
+    prepare(ch, lib_stream)
     kind, kind_ms = ch.autotune_pair_kernel(reps=10)
     bin_kind, bin_ctas = ch.get_binning_kernel()
     tiles = {"used": list(ch.get_tiles()), "choices": list(kcm.TILE_CHOICES), "source": "autotuner",
              "pair_kernel": ("cell_tiles" if kind == kcm.PAIR_CELL_TILES else "warp_per_atom"),
              "pair_kernel_ms": {"warp_per_atom": float(kind_ms[0]), "cell_tiles": float(kind_ms[1])},
-             "binning_kernel": {"kind": "cluster" if bin_kind == kcm.BIN_CLUSTER else "blocks", "ctas": bin_ctas}}
+             "binning_kernel": {"kind": "cluster" if bin_kind == kcm.BIN_CLUSTER else "blocks", "ctas": bin_ctas},
+             "cell_autotune_ms": dict(zip(("6", "7", "8", "9", "10", "12"), [float(x) for x in cell_main_ms]))}
     # the torques at the start conformation, compared with the oracle's in the oracle leg
     prepare(ch, lib_stream)
     tau_start = ch.torques()
