@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--chain8000-steps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-iters", type=int, default=200)
+    ap.add_argument("--cell-edge", type=float, default=0.0, metavar="A",
+                    help="cell edge (A) of the 1,000-residue and batch legs instead of the cell-edge autotuner's "
+                         "choice (for profiling runs, where ncu's serialised launches distort the autotuner)")
     ap.add_argument("--profile-batch", type=int, default=0, metavar="K",
                     help="profiling workload only: the first K chains of the batch workload, mixed precision, "
                          "stepped from their stored starts four times (a few GB on the device for one-kernel ncu "
@@ -431,7 +434,8 @@ def run_ours(args):
     # pair kernel (warp per atom or cell-pair tiles) and tile shapes from the library's autotuner, at the
     # start conformation, before the warm-up
     prepare(ch, lib_stream)
-    cell_main, cell_main_ms = ch.autotune_cell(candidates=(6.0, 7.0, 8.0, 9.0, 10.0, 12.0), reps=20)
+    cell_cands = (args.cell_edge,) if args.cell_edge > 0 else (6.0, 7.0, 8.0, 9.0, 10.0, 12.0)
+    cell_main, cell_main_ms = ch.autotune_cell(candidates=cell_cands, reps=20)
     prepare(ch, lib_stream)
     kind, kind_ms = ch.autotune_pair_kernel(reps=10)
     bin_kind, bin_ctas = ch.get_binning_kernel()
@@ -439,7 +443,7 @@ def run_ours(args):
              "pair_kernel": ("cell_tiles" if kind == kcm.PAIR_CELL_TILES else "warp_per_atom"),
              "pair_kernel_ms": {"warp_per_atom": float(kind_ms[0]), "cell_tiles": float(kind_ms[1])},
              "binning_kernel": {"kind": "cluster" if bin_kind == kcm.BIN_CLUSTER else "blocks", "ctas": bin_ctas},
-             "cell_autotune_ms": dict(zip(("6", "7", "8", "9", "10", "12"), [float(x) for x in cell_main_ms]))}
+             "cell_autotune_ms": dict(zip([f"{x:g}" for x in cell_cands], [float(x) for x in cell_main_ms]))}
     # the torques at the start conformation, compared with the oracle's in the oracle leg
     prepare(ch, lib_stream)
     tau_start = ch.torques()
@@ -611,7 +615,7 @@ def run_ours(args):
                     flush.add_(1)
 
             prep_b()
-            bcell, bcand_ms = bb.autotune_cell(candidates=(6.0, 7.0, 8.0, 9.0, 10.0, 12.0), reps=2)
+            bcell, bcand_ms = bb.autotune_cell(candidates=cell_cands, reps=2)
             prep_b()
             bkind, bkind_ms = bb.autotune_pair_kernel(reps=2)
             btiles = bb.get_tiles()
@@ -631,7 +635,7 @@ def run_ours(args):
                      "ms_per_step": sum(tt) / args.batch_steps,
                      "stage_ms": stg,
                      "steps": args.batch_steps, "pairs": bst["pairs"], "sasa_tests": bst["sasa_tests"],
-                     "cell_size": bcell, "autotune_ms": dict(zip(("6", "7", "8", "9", "10", "12"),
+                     "cell_size": bcell, "autotune_ms": dict(zip([f"{x:g}" for x in cell_cands],
                                                                   [float(x) for x in bcand_ms])),
                      "rooflines": stage_rooflines(stg, bst, bb.n, fp32_peak, peaks),
                      "tiles": {"chosen": list(btiles), "order": "[pair warps or tile split][solvation warps][persistent pair grid]",
