@@ -664,7 +664,7 @@ static int create_impl(const kcm_topology* tops, int32_t n_chains, const kcm_par
         (rc = dalloc(h, &d.r, 3 * nn)) || (rc = dalloc(h, &d.key, nn)) || (rc = dalloc(h, &d.rank, nn)) ||
         (rc = dalloc(h, &d.sorted, nn)) || (hc.nchains > 1 && (rc = dalloc(h, &d.slot_chain, nn))) || (rc = dalloc(h, &d.sorted_tmp, nn)) || (rc = dalloc(h, &d.slot_cell, nn)) || (rc = dalloc(h, &d.smask, nn)) || (rc = dalloc(h, &d.spos64, nn)) ||
         (rc = dalloc(h, &d.spos32, nn)) || (rc = dalloc(h, &d.sprm32, nn)) || (rc = dalloc(h, &d.sprm64, nn)) ||
-        (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fpx, 3 * nn)) || (rc = dalloc(h, &d.Fov, 3 * nn)) ||
+        (rc = dalloc(h, &d.Fpair, 3 * nn)) || (rc = dalloc(h, &d.Fpx, 3 * nn)) || (rc = dalloc(h, &d.Fov, 3 * nn)) || (rc = dalloc(h, &d.Fox, 3 * nn)) ||
         (rc = dalloc(h, &d.gflag, nn)) || (rc = dalloc(h, &d.Fcav, 3 * nn)) || (rc = dalloc(h, &d.nbr_cnt, nn)) ||
         (rc = dalloc(h, &d.nbr, nn * kcm::kMaxNbr)) || (rc = dalloc(h, &d.nbr_off, nn * kcm::kMaxNbr)) ||
         (rc = dalloc(h, &d.covered, nn)) || (rc = dalloc(h, &d.long_atoms, nn)) || (rc = dalloc(h, &d.epair, 2 * nn)) || (rc = dalloc(h, &d.pstat, nn)) ||

@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(kBcThreads) k_bin_cluster(const DevChain d) {
             d.smask[sl] = make_ulonglong2(d.exm[at], d.m14m[at]);
             d.Fpx[3 * at] = 0; d.Fpx[3 * at + 1] = 0; d.Fpx[3 * at + 2] = 0;
             d.Fov[3 * at] = 0.0f; d.Fov[3 * at + 1] = 0.0f; d.Fov[3 * at + 2] = 0.0f;
+            d.Fox[3 * at] = 0; d.Fox[3 * at + 1] = 0; d.Fox[3 * at + 2] = 0;
             d.nbr_cnt[at] = 0;
             const int cx = key % g.nx, cy = (key / g.nx) % g.ny, cz = key / (g.nx * g.ny);
             const float fx = mixed_offset(px, g.of[0], cx, g.sf);

@@ -173,6 +173,32 @@ __device__ __forceinline__ void fx_add(float v, int& hi, int& lo) {
 // the whole term n 2^23 + f in units of 2^-23
 __device__ __forceinline__ long long fx_units(int n, int f) { return (long long)n * 8388608LL + f; }
 
+// A pair term with a component of 2^22 or more (a clash) on atoms a and b (b takes the negative), summed
+// so that the total does not depend on the order of the additions: a component below 2^22 in the fixed
+// point of the other terms (2^-23), one of 2^22 .. 2^50 exactly in units of 2^-1 (a float of magnitude
+// 2^22 or more is a multiple of 2^-1), and only a larger or non-finite one in a plain float sum.
+__device__ __forceinline__ void add_oversized(const DevChain& d, int a, int b, float fx, float fy, float fz) {
+    const float v[3] = {fx, fy, fz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float m = fabsf(v[k]);
+        if (m < 4194304.0f) {  // 2^22
+            int n, f;
+            fx_pieces(v[k], n, f);
+            const long long u = fx_units(n, f);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&d.Fpx[3 * a + k]), (unsigned long long)u);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&d.Fpx[3 * b + k]), (unsigned long long)(-u));
+        } else if (m < 1125899906842624.0f) {  // 2^50
+            const long long u = __float2ll_rn(v[k] * 2.0f);  // exact
+            atomicAdd(reinterpret_cast<unsigned long long*>(&d.Fox[3 * a + k]), (unsigned long long)u);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&d.Fox[3 * b + k]), (unsigned long long)(-u));
+        } else {
+            atomicAdd(&d.Fov[3 * a + k], v[k]);
+            atomicAdd(&d.Fov[3 * b + k], -v[k]);
+        }
+    }
+}
+
 // Mixed-precision pair geometry with every FP32 rounding written out, so that each pair kernel that
 // evaluates a pair forms the same bits (a compiler left to itself may fuse these operations
 // differently in different kernels). Offsets are from the corners of the atoms' cells; the x shift

@@ -180,7 +180,8 @@ struct DevChain {
     dbl4* sprm64 = nullptr;     // [n]
     double* Fpair = nullptr;       // [n*3] (FP64 mode; mixed mode fills it on request)
     long long* Fpx = nullptr;      // mixed mode: pair forces in fixed point, units of 2^-23 [n*3]
-    float* Fov = nullptr;          // mixed mode: pair terms beyond the fixed-point range [n*3]
+    float* Fov = nullptr;          // mixed mode: non-finite pair terms and those of 2^50 or more [n*3]
+    long long* Fox = nullptr;      // mixed mode: pair terms of 2^22 .. 2^50, units of 2^-1 (exact) [n*3]
     long long* Fcav = nullptr;     // fixed point [n*3]
     int* nbr_cnt = nullptr;        // [n]
     int* nbr = nullptr;            // [n*kMaxNbr]

@@ -249,6 +249,7 @@ __global__ void k_bin_place(const DevChain d) {
         // the pair kernel adds each pair's share to both atoms: zero the sums and the list counters
         d.Fpx[3 * a] = 0; d.Fpx[3 * a + 1] = 0; d.Fpx[3 * a + 2] = 0;
         d.Fov[3 * a] = 0.0f; d.Fov[3 * a + 1] = 0.0f; d.Fov[3 * a + 2] = 0.0f;
+        d.Fox[3 * a] = 0; d.Fox[3 * a + 1] = 0; d.Fox[3 * a + 2] = 0;
         d.nbr_cnt[a] = 0;
         const int lk = key - g.cbase;
         int cx = lk % g.nx, cy = (lk / g.nx) % g.ny, cz = lk / (g.nx * g.ny);
@@ -647,13 +648,8 @@ __global__ void __launch_bounds__(W * 32, (MIXED ? 32 : 24) / W) k_pair(const De
                             atomicAdd(Fj, (unsigned long long)(-fx_units(n0, f0)));
                             atomicAdd(Fj + 1, (unsigned long long)(-fx_units(n1, f1)));
                             atomicAdd(Fj + 2, (unsigned long long)(-fx_units(n2, f2)));
-                        } else {  // clash-sized (or non-finite) term: plain float sums
-                            atomicAdd(&d.Fov[3 * a], fx1);
-                            atomicAdd(&d.Fov[3 * a + 1], fy1);
-                            atomicAdd(&d.Fov[3 * a + 2], fz1);
-                            atomicAdd(&d.Fov[3 * b], -fx1);
-                            atomicAdd(&d.Fov[3 * b + 1], -fy1);
-                            atomicAdd(&d.Fov[3 * b + 2], -fz1);
+                        } else {  // clash-sized (or non-finite) term
+                            add_oversized(d, a, b, fx1, fy1, fz1);
                         }
                         if (count_e) { ove += e_el; ovv += e_vd; }
                     } else {
@@ -1438,7 +1434,7 @@ __global__ void k_force_out(const DevChain d) {
     if (x >= 3 * d.n) return;
     double fc = d.prm.solvation ? (double)d.Fcav[x] * kFxInv : 0.0;
     d.Fcav64[x] = fc;
-    if (d.prm.precision == KCM_MIXED) d.Fpair[x] = (double)d.Fpx[x] * kPairFxInv + (double)d.Fov[x];
+    if (d.prm.precision == KCM_MIXED) d.Fpair[x] = (double)d.Fpx[x] * kPairFxInv + (double)d.Fox[x] * 0.5 + (double)d.Fov[x];
     d.Ftot[x] = d.Fpair[x] + fc;
 }
 

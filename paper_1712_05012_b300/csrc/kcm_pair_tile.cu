@@ -386,13 +386,8 @@ __global__ void __launch_bounds__(kPtWarps * 32, KCM_PT_MIN_BLOCKS) k_pair_tile(
                         atomicAdd(&S.jacc[3][jj], -f0);
                         atomicAdd(&S.jacc[4][jj], -f1);
                         atomicAdd(&S.jacc[5][jj], -f2);
-                    } else {  // clash-sized (or non-finite) term: plain float sums
-                        atomicAdd(&d.Fov[3 * a], fx1);
-                        atomicAdd(&d.Fov[3 * a + 1], fy1);
-                        atomicAdd(&d.Fov[3 * a + 2], fz1);
-                        atomicAdd(&d.Fov[3 * b], -fx1);
-                        atomicAdd(&d.Fov[3 * b + 1], -fy1);
-                        atomicAdd(&d.Fov[3 * b + 2], -fz1);
+                    } else {  // clash-sized (or non-finite) term
+                        add_oversized(d, a, b, fx1, fy1, fz1);
                     }
                     ove += pt.e_el;
                     ovv += pt.e_vd;

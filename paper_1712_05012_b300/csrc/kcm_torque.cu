@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(kWrenchWarps * 32) k_wrench_step(const DevChai
         if constexpr (DF) {  // pair forces in fixed point (2^-23) plus oversized terms, solvation (2^-40)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                f[k] = add(ldexp2(df_from_i64(d.Fpx[3 * a + k]), 0x1p-23f), df{d.Fov[3 * a + k], 0.0f});
+                f[k] = add(add(ldexp2(df_from_i64(d.Fpx[3 * a + k]), 0x1p-23f), ldexp2(df_from_i64(d.Fox[3 * a + k]), 0.5f)),
+                           df{d.Fov[3 * a + k], 0.0f});
                 if (d.prm.solvation) f[k] = add(f[k], ldexp2(df_from_i64(d.Fcav[3 * a + k]), 0x1p-40f));
             }
             if (d.prm.solvation == 2) Ef[2] += (float)d.esolv[a];  // pairwise surrogate: gamma_i A_i

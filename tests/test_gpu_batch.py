@@ -3,6 +3,7 @@
 A batch concatenates its chains; every scan is segmented at chain boundaries and every chain has
 its own cell grid, so each chain's results must equal its results alone up to rounding order
 (the scan blocks fall differently), and its iteration count and convergence must be its own."""
+import os
 import numpy as np
 import pytest
 
@@ -216,3 +217,26 @@ def test_batch_binning_large_grid(kcm, table):
     for c in (1, 2):
         ref = alone(kcm, seqs[c], table, pm, thetas[c])
         assert rel_inf(mix["tau"][c], ref["tau"]) < 1e-9, c
+
+
+def test_mixed_trajectory_reproducible_through_clashes(kcm, table):
+    """Chain 216 of the 512-chain batch workload (425 residues), alone: its clamped
+    steps drive atoms into clashes whose pair terms exceed the 2^-23 fixed point's range (2^22). Those
+    terms are summed in exact integer units of 2^-1, so every run from the same start gives the same
+    angles, bit for bit (a float sum of them varied with the order of the atomics and, through
+    Algorithm 1's coverage decisions, moved joints by whole steps in some runs)."""
+    wl = synth.workload(4)
+    i = 216
+    seq = synth.sequence(wl.m[i], synth.chain_seed(wl.seed, i))
+    codes = np.load(os.path.join(os.path.dirname(__file__), "golden", "start_batch512.npy"))
+    off = 2 * int(np.sum(wl.m[:i]))
+    th = synth.theta_from_codes(codes[off:off + 2 * wl.m[i]])
+    p = synth.RunParams(precision=synth.PRECISION_MIXED)
+    with kcm.Chain(seq, table, p) as c:
+        runs = []
+        for _ in range(6):
+            c.set_theta(th)
+            c.step(8)
+            runs.append(np.asarray(c.get_theta()).copy())
+    for r in runs[1:]:
+        assert np.array_equal(r, runs[0])
